@@ -1,0 +1,91 @@
+"""Overlap correction -- oracle (test infrastructure).
+
+Eq. (overlaps), Sec. 2.3: an overlapping pair (r_12 < sigma) is pushed apart
+along n = (r_2 - r_1)/|r_12|: r_1' = r_1 - delta* n, r_2' = r_2 + delta* n with
+the "bounce" value delta* = sigma - |r_12| (each disk moves by the full
+overlap depth).
+
+Algorithm 2, Sec. 4.4, run on the Delaunay edges: every edge with r < sigma
+adds -delta* n to its first disk's displacement and +delta* n to its second's;
+the displacements are summed (Jacobi style, not Strating's sequential order),
+then each disk moves by its sum, truncated to length sigma/4 (the heuristic
+cap against the oscillating instability of Fig. "overlaps"; the cap scales
+the summed vector), and is reflected at the walls.  The pass repeats until
+no pair is closer than sigma.
+
+Which triangulation each pass uses: Algorithm 1 updates the triangulation
+before correcting, so its last pass sees a stale triangulation.  This build
+reads the stopping test as "no Delaunay edge of the *current* positions is
+shorter than sigma": the closest pair of a point set is a Delaunay edge, so
+that certifies that no pair anywhere overlaps.  The oracle therefore rebuilds
+the triangulation from scratch before every pass.
+"""
+import numpy as np
+
+from . import dynamics, geometry
+
+
+def real_edges(tris, n):
+    e = geometry.edges(tris)
+    return e[(e[:, 0] < n) & (e[:, 1] < n)]
+
+
+def correction_pass(xy, E, sigma, a, L):
+    """One pass of Algorithm 2 over the edge list E (pairs i < j).
+    Returns (new xy, overlapping pairs (k,2), capped mask, raw displacement)."""
+    xy = np.asarray(xy, dtype=np.float64)
+    i, j = E[:, 0], E[:, 1]
+    d = xy[j] - xy[i]                          # r_j - r_i
+    r = np.sqrt(d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1])
+    hit = r < sigma
+    pairs = E[hit]
+    disp = np.zeros_like(xy)
+    if hit.any():
+        nhat = d[hit] / r[hit][:, None]
+        delta = (sigma - r[hit])[:, None]
+        np.add.at(disp, pairs[:, 0], -delta * nhat)
+        np.add.at(disp, pairs[:, 1], delta * nhat)
+    mag = np.sqrt(disp[:, 0] ** 2 + disp[:, 1] ** 2)
+    cap = sigma / 4.0
+    capped = mag > cap
+    scale = np.where(capped, cap / np.where(mag > 0, mag, 1.0), 1.0)
+    new = xy + disp * scale[:, None]
+    new = dynamics.reflect(new, a, L)
+    return new, pairs, capped, disp
+
+
+def reversed_edges(xy0, xy1, E):
+    """Sec. 4.3 first criterion: r0_ij . r1_ij < 0 (the pair passed through
+    each other), evaluated on edges E with before/after positions."""
+    r0 = xy0[E[:, 1]] - xy0[E[:, 0]]
+    r1 = xy1[E[:, 1]] - xy1[E[:, 0]]
+    dot = r0[:, 0] * r1[:, 0] + r0[:, 1] * r1[:, 1]
+    return E[dot < 0]
+
+
+def correct(xy, L, a, max_iters=10000, tris=None, record=None):
+    """Iterate Algorithm 2 until no Delaunay edge is shorter than sigma = 2a.
+    Returns (xy, tris of final positions, iterations that moved disks,
+    total overlapping edges seen, rejected flag)."""
+    sigma = 2.0 * a
+    n = len(xy)
+    xy = np.asarray(xy, dtype=np.float64)
+    it = 0
+    total = 0
+    while True:
+        if tris is None:
+            tris = geometry.delaunay(xy, L)
+        E = real_edges(tris, n)
+        new, pairs, capped, disp = correction_pass(xy, E, sigma, a, L)
+        if len(pairs) == 0:
+            return xy, tris, it, total, False
+        if record is not None:
+            record.append({"pairs": pairs, "capped": capped, "disp": disp})
+        if len(reversed_edges(xy, new, E)):
+            return xy, tris, it, total, True
+        total += len(pairs)
+        it += 1
+        xy = new
+        tris = None
+        if it >= max_iters:
+            return xy, geometry.delaunay(xy, L), it, total, True

@@ -1,0 +1,80 @@
+"""Pins for the oracle's pair forces (Sec. 2.2 and the short-range law)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import forces
+
+A2 = (0.05, 0.2, -0.1, 0.05)    # on A from A, on A from B, on B from A, on B from B
+
+
+def test_two_body_closed_form_and_index_order():
+    # disk 0 (species A) at origin, disk 1 (species B) at (3, 4): r = 5
+    xy = np.array([[0.0, 0.0], [3.0, 4.0]])
+    s = np.array([0, 1], dtype=np.uint8)
+    F = forces.long_range_numpy(xy, s, A2)
+    # force on 0 from 1: A[A][B] * (r0 - r1)/r^3 = 0.2 * (-3,-4)/125
+    assert np.allclose(F[0], 0.2 * np.array([-3.0, -4.0]) / 125.0, rtol=1e-15, atol=0)
+    # force on 1 from 0: A[B][A] * (r1 - r0)/r^3 = -0.1 * (3,4)/125 (attractive)
+    assert np.allclose(F[1], -0.1 * np.array([3.0, 4.0]) / 125.0, rtol=1e-15, atol=0)
+    # magnitude alpha / r^2
+    assert math.isclose(np.hypot(*F[0]), 0.2 / 25.0, rel_tol=1e-14)
+
+
+def test_c_and_numpy_paths_and_newton3_for_reciprocal_law():
+    rng = np.random.default_rng(2)
+    n = 700
+    xy = rng.uniform(0, 60, size=(n, 2))
+    s = rng.integers(0, 2, n).astype(np.uint8)
+    A = (0.1, 0.03, 0.03, -0.07)   # symmetric table = reciprocal pair law
+    F1 = forces.long_range_numpy(xy, s, A)
+    F2 = forces.long_range(xy, s, A, threads=2)
+    assert np.allclose(F1, F2, rtol=1e-12, atol=1e-15)
+    tot = F1.sum(axis=0)
+    assert np.all(np.abs(tot) <= 1e-12 * np.abs(F1).sum())
+
+
+def test_symmetric_ring_cancels():
+    k = 12
+    ang = 2 * math.pi * np.arange(k) / k
+    ring = np.stack([5 * np.cos(ang), 5 * np.sin(ang)], axis=1)
+    xy = np.concatenate([[[0.0, 0.0]], ring])
+    s = np.zeros(k + 1, dtype=np.uint8)
+    F = forces.long_range_numpy(xy, s, (1.0, 0, 0, 0))
+    assert np.all(np.abs(F[0]) < 1e-15)
+    # every ring disk is pushed radially outward
+    radial = (F[1:] * ring).sum(axis=1) / 5.0
+    tang = np.abs(F[1:, 0] * ring[:, 1] - F[1:, 1] * ring[:, 0]) / 5.0
+    assert np.all(radial > 0) and np.all(tang < 1e-14)
+
+
+def test_nonreciprocal_pair_self_propels():
+    # Sec. 2.2: with alpha != mu action and reaction differ; a lone A-B pair
+    # with A[A][B] = -A[B][A] moves as a unit (net force nonzero)
+    xy = np.array([[0.0, 0.0], [2.5, 0.0]])
+    s = np.array([0, 1], dtype=np.uint8)
+    F = forces.long_range_numpy(xy, s, (0.0, 0.3, -0.3, 0.0))
+    assert np.allclose(F[0], F[1])
+    assert abs(F.sum(axis=0)[0]) > 0.09
+
+
+@pytest.mark.parametrize("r", [2.0, 2.1, 2.2, 2.4, 3.0, 4.5])
+def test_short_range_force_is_minus_potential_gradient(r):
+    h = 1e-6
+    dU = (forces.short_range_potential(r + h, 1.0, 1.0, 2.0)
+          - forces.short_range_potential(r - h, 1.0, 1.0, 2.0)) / (2 * h)
+    assert abs(float(forces.short_range_magnitude(r, 1.0, 1.0, 2.0)) + float(dU)) < 1e-6
+
+
+def test_short_range_cutoff_and_newton3():
+    rng = np.random.default_rng(4)
+    xy = rng.uniform(0, 30, size=(300, 2))
+    F = forces.short_range(xy, 1.0, 1.0, 2.0, 5.0)
+    assert np.all(np.abs(F.sum(axis=0)) < 1e-9 * np.abs(F).sum())
+    two = np.array([[0.0, 0.0], [5.0 + 1e-9, 0.0]])
+    assert np.all(forces.short_range(two, 1.0, 1.0, 2.0, 5.0) == 0.0)
+    two = np.array([[0.0, 0.0], [4.9, 0.0]])
+    f = forces.short_range(two, 1.0, 1.0, 2.0, 5.0)
+    # Yukawa tail attracts: force on 0 points toward +x
+    assert f[0, 0] > 0 and f[1, 0] < 0
