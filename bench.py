@@ -1,0 +1,316 @@
+"""Throughput benchmark: particle-steps/s of the full time step at N = 1e5.
+
+Workload: 100,000 two-species active disks (a = 1, area fraction 0.30,
+L = 1023.3, reflecting walls), non-reciprocal long-range law
+A = [[0.05, 0.2], [-0.1, 0.05]] with F = A r_hat / r^2 summed over all pairs,
+self-propulsion v0 = 1, D = 1, D_r = 0.5, dt = 1e-4, Philox seed 100, start by
+random sequential addition.  One step = forces (all pairs) + Euler-Maruyama
++ triangulation check/repair/flips + overlap correction until no overlap.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank advances its own
+independent replica (a different Philox replica stream); `value` sums them.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "particle-steps/s at N=1e5 (all-pairs + Delaunay repair)"
+UNIT = "particle-steps/s"
+WORKLOAD = "n1e5: N=100000 two-species ABP disks, rho=0.30, all-pairs 1/r^2 non-reciprocal, Delaunay overlap correction"
+FLOPS_PER_PAIR = 12      # 2 FADD + 2 FFMA(r^2) + 2 FMUL(s^3) + 2 FFMA(accumulate), FMA = 2 flops
+FP32_INST_PER_PAIR = 8   # the same work counted as FP32-pipe instructions (plus 1 MUFU rsqrt)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The oracle (plain FP64 CPU restatement) on the same workload, host cores.
+
+    Each step is a bounded sample of the N = 1e5 step: exact all-pairs FP64
+    forces for `fsample` disks (time scaled by N / fsample), and the
+    Euler-Maruyama + Delaunay + overlap-correction stages on the disks of one
+    quarter of the box taken as a system of its own (time scaled by N / its
+    size; those stages are O(N))."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import forces as of
+    from oracle import step as ostep
+    from paper_1703_02484_gb300 import workloads
+    cfg = workloads.CONFIGS["n1e5"]
+    xy, sp, th = workloads.initial_state(cfg)
+    L = cfg.L
+    cores = os.cpu_count() or 1
+    fsample = 1000
+    half = 0.5 * L
+    win = (xy[:, 0] < half - cfg.a) & (xy[:, 1] < half - cfg.a)
+    wxy, wsp, wth = xy[win].copy(), sp[win].copy(), th[win].copy()
+    nw = len(wxy)
+    op = ostep.Params(L=half, a=cfg.a, law=cfg.law, alpha=cfg.alpha, D=cfg.D, Dr=cfg.Dr,
+                      v0=cfg.v0, dt=cfg.dt, seed=cfg.seed)
+    rng = np.random.default_rng(0)
+
+    def one(k, wxy, wth):
+        i0 = int(rng.integers(0, cfg.n - fsample))
+        t0 = time.perf_counter()
+        Fs = of.long_range(xy, sp, cfg.alpha, idx=np.arange(i0, i0 + fsample), threads=cores)
+        t_f = (time.perf_counter() - t0) * (cfg.n / fsample)
+        F = np.zeros((nw, 2))
+        F[: min(nw, fsample)] = Fs[: min(nw, fsample)]
+        t1 = time.perf_counter()
+        r = ostep.step(wxy, wth, wsp, k, op, F=F)
+        t_rest = (time.perf_counter() - t1) * (cfg.n / nw)
+        return r["xy"], r["theta"], t_f + t_rest
+
+    for k in range(args.warmup):
+        one(k, wxy, wth)
+    total = 0.0
+    for k in range(args.steps):
+        wxy, wth, t = one(k, wxy, wth)
+        total += t
+    ms = 1e3 * total / max(1, args.steps)
+    value = cfg.n / (ms / 1e3)
+    sample = ("per step: exact all-pairs FP64 forces for %d of %d disks (time x N/%d) and the "
+              "Euler-Maruyama, Delaunay rebuilds and overlap correction of the %d disks of one "
+              "quarter of the box (time x N/%d)" % (fsample, cfg.n, fsample, nw, nw))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": cfg.n, "seed": cfg.seed},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(cfg, xy, sp, th):
+    """One full oracle step of the workload (exact all-pairs forces on all host
+    cores), the oracle as it stands."""
+    from oracle import step as ostep
+    cores = os.cpu_count() or 1
+    op = ostep.Params(L=cfg.L, a=cfg.a, law=cfg.law, alpha=cfg.alpha, D=cfg.D, Dr=cfg.Dr,
+                      v0=cfg.v0, dt=cfg.dt, seed=cfg.seed)
+    t0 = time.perf_counter()
+    ostep.step(xy, th, sp, 0, op, threads=cores)
+    t = time.perf_counter() - t0
+    return {"value": cfg.n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one full FP64 oracle step of the N=1e5 workload (all-pairs forces with "
+                      "OpenMP over %d threads, Delaunay rebuilds and overlap correction): %.2f s" % (cores, t)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    args.warmup = max(3, args.warmup)
+
+    import torch
+    import paper_1703_02484_gb300 as bd
+    from paper_1703_02484_gb300 import workloads
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cfg = workloads.CONFIGS["n1e5"]
+    xy, sp, th = workloads.initial_state(cfg)
+    p = bd.params_from_config(cfg)
+    p.replica = rank
+    stream = torch.cuda.current_stream()
+    system = bd.System(p, xy, sp, th, stream=stream.cuda_stream)
+    N = cfg.n
+
+    # warm-up
+    for _ in range(args.warmup):
+        system.step(1)
+    # L2 flush buffer (> 129 MB of L2): written between timed steps
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    system.force_timing(True, reset=True)
+    launches = 0
+    stats_tot = {}
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            st = system.step(1)
+            ev[k][1].record(stream)
+            launches += system.last_launch_count()
+            for key in ("corr_iters", "flips", "repair_flips", "overlap_pairs", "inverted"):
+                stats_tot[key] = stats_tot.get(key, 0) + st[key]
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    t_ms = float(sum(ms_steps))
+    force_ms, force_n = system.force_timing(False)
+    if ws > 1:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    value = ws * N * args.steps / (t_ms / 1e3)
+
+    # roofline of the dominant kernel (the all-pairs sweep): ALU-bound
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    f_hz = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    peak_tflops = sms * 128 * 2 * f_hz / 1e12
+    avg_force_s = (force_ms / max(1, force_n)) / 1e3
+    pairs = N * (N - 1)
+    achieved = FLOPS_PER_PAIR * pairs / avg_force_s / 1e12
+    pipe_frac = FP32_INST_PER_PAIR * pairs / avg_force_s / (sms * 128 * f_hz)
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "force_long_f32_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                traffic = json.load(f).get("traffic_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        hxy = torch.empty((N, 2), dtype=torch.float64).pin_memory().numpy()
+        hth = torch.empty((N,), dtype=torch.float32).pin_memory().numpy()
+        cur = system.state(want_tri=False)
+        hxy[:] = cur["xy"]
+        hth[:] = cur["theta"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            system.set_state(hxy, hth)          # host -> device (positions, directions)
+            system.step(1)
+            o = system.state(want_tri=False)    # device -> host
+            hxy[:] = o["xy"]
+            hth[:] = o["theta"]
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if ws > 1:
+            tt = torch.tensor([te], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": ws * N * args.e2e_steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": N * (16 + 4), "d2h_bytes_per_step": N * (16 + 4 + 1)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "seed": cfg.seed,
+                       "parallelism": "replicas%d" % ws,
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "per_step_stats": {k: v / args.steps for k, v in stats_tot.items()}},
+            "roofline": {"bound": "alu", "kernel": "k_force_long_f32", "achieved": achieved,
+                         "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                         "traffic": traffic, "fp32_pipe_frac": pipe_frac,
+                         "pair_interactions_per_s": pairs / avg_force_s,
+                         "avg_launch_ms": avg_force_s * 1e3,
+                         "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s max clock); "
+                                      "12 flops/pair caps frac at 0.75" % (sms, f_hz / 1e6, pk_kind)},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(cfg, xy, sp, th)
+        print(json.dumps(line), flush=True)
+    system.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

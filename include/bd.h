@@ -1,0 +1,200 @@
+/*
+ * bd.h -- C ABI of the GB300 Brownian hard-disk time stepper.
+ *
+ * The library advances N hard disks of radius a (diameter sigma = 2a) in a
+ * square box [0, L]^2 with reflecting walls, following the per-step method
+ * of Carter, Hitschfeld, Navarro & Soto, "GPU parallel simulation algorithm
+ * of Brownian particles with excluded volume using Delaunay triangulations"
+ * (arXiv:1703.02484), Algorithm 1 (Sec. 4.1): forces, Euler-Maruyama update
+ * with noise, inverted-triangle check and repair (Sec. 4.3), Delaunay edge
+ * flips, and overlap correction over the triangulation edges (Algorithm 2,
+ * Sec. 4.4).  Every per-step stage runs in CUDA kernels on one GPU; the only
+ * host-side geometry is the initial Delaunay triangulation built once in
+ * bd_init, as in the paper (Sec. 4.1).
+ *
+ * Conventions
+ *  - Every int-returning call returns BD_OK (0) or a negative BD_ERR_* code;
+ *    bd_strerror() names it.
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Output
+ *    arrays are caller-allocated host memory of the documented size.
+ *  - Device memory is owned by the handle and released by bd_free.
+ *  - All work is queued on the CUDA stream given to bd_init (NULL = the
+ *    legacy default stream); each call returns after its work has finished.
+ *  - After any error other than BD_ERR_ARG / BD_ERR_NOMEM at init the handle
+ *    stays usable and holds the last good state (the state before the
+ *    rejected step).
+ *  - Handles are independent; one handle must not be used from two host
+ *    threads at once.
+ *  - Coordinates are stored on a dyadic grid (a multiple of 2^-s with
+ *    2^-s about 1e-12 L): positions passed in are rounded to it.
+ */
+#ifndef BD_H
+#define BD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  BD_OK = 0,
+  BD_ERR_ARG = -1,                 /* invalid argument or parameter */
+  BD_ERR_CUDA = -2,                /* a CUDA runtime call failed */
+  BD_ERR_INIT_OVERLAP = -3,        /* initial disks overlap or leave the box */
+  BD_ERR_STEP_REJECTED = -4,       /* Sec. 4.3: a pair passed through each other,
+                                      or an inverted triangle could not be repaired;
+                                      the step was undone */
+  BD_ERR_OVERLAP_NOT_CONVERGED = -5, /* Algorithm 2 hit max_corr_iters; step undone */
+  BD_ERR_FLIP_NOT_CONVERGED = -6,  /* edge flips hit max_flip_rounds; step undone */
+  BD_ERR_DEVICE_TIMEOUT = -7,      /* a bounded device-side wait gave up */
+  BD_ERR_NOMEM = -8,               /* device or host allocation failed */
+  BD_ERR_TRIANGULATION = -9,       /* the initial triangulation could not be built */
+  BD_ERR_UNSUPPORTED = -10         /* parameter combination not implemented */
+};
+
+enum { BD_LAW_NONE = 0, BD_LAW_LONG = 1, BD_LAW_SHORT = 2 };
+
+/* Simulation parameters.  Sec. 4.2 keeps N, D, dt and sigma in constant
+ * memory; the pair-force charges are those of Sec. 2.2. */
+typedef struct bd_params {
+  int32_t n;             /* number of disks, >= 1 */
+  int32_t n_species;     /* 1 or 2 */
+  double a;              /* disk radius (> 0); sigma = 2a */
+  double box_L;          /* box side; <= 0 => sqrt(n pi a^2 / area_fraction) (Sec. 6) */
+  double area_fraction;  /* used only when box_L <= 0 */
+  int32_t law;           /* BD_LAW_NONE, BD_LAW_LONG (Sec. 2.2, f = r/r^3, all pairs),
+                            BD_LAW_SHORT (WCA core + Yukawa tail, cut at r_cut, Verlet lists) */
+  int32_t precision;     /* 0: forces and increments in FP32; 1: in FP64 */
+  double alpha[4];       /* long range: A[s_i][s_j] row-major, coefficient of the force ON
+                            species s_i FROM species s_j, F_i = sum_j A (r_i - r_j)/|r_ij|^3
+                            (= mu_i alpha_j of Sec. 2.2); A > 0 repels */
+  double eps, kappa;     /* short range: energy scale and Yukawa inverse length */
+  double r_cut, skin;    /* short range: cut-off radius and Verlet skin */
+  double D;              /* translational diffusion coefficient */
+  double Dr;             /* rotational diffusion coefficient (Sec. 7) */
+  double v0;             /* self-propulsion speed (Sec. 7) */
+  double dt;             /* time step */
+  uint64_t seed;         /* Philox key */
+  int32_t replica;       /* xored into the upper key word (independent streams) */
+  int32_t max_corr_iters;  /* cap on Algorithm 2 passes per step (default 1000) */
+  int32_t max_flip_rounds; /* cap on flip rounds per triangulation update (default 4096) */
+  int32_t literal_noise;   /* 1: noise amplitude sqrt(D dt) as printed in Eq. (integration);
+                              0 (default): sqrt(2 D dt) per component */
+  int64_t step0;         /* index of the first step (Philox counter), for resumed runs */
+} bd_params;
+
+/* Counters of one bd_step call (the paper's per-step metrics, Sec. 6). */
+typedef struct bd_step_stats {
+  int64_t steps_done;       /* steps completed by this call */
+  int64_t corr_iters;       /* Algorithm 2 passes that moved disks, summed over steps */
+  int64_t overlap_pairs;    /* overlapping triangulation edges found, summed */
+  int64_t flip_rounds;      /* edge-flip rounds that flipped at least one edge */
+  int64_t flips;            /* Delaunay (Lawson) flips */
+  int64_t repair_flips;     /* inverted-triangle repair flips (Sec. 4.3) */
+  int64_t inverted;         /* inverted triangles detected */
+  int32_t max_corr_iters;   /* largest number of passes in one step */
+  int32_t rejected;         /* 1 if the call stopped at a rejected step */
+  int32_t verlet_rebuilds;  /* short range: neighbour-list rebuilds */
+  int32_t pad;
+  double max_overlap;       /* deepest overlap sigma - r seen */
+} bd_step_stats;
+
+typedef struct bd_handle bd_handle;
+
+/* Fill *p with defaults: n=0, one species, a=1, FP32, no forces, D=1, dt=1e-4,
+ * max_corr_iters=1000, max_flip_rounds=4096.  Returns BD_OK or BD_ERR_ARG
+ * (p == NULL). */
+int bd_default_params(bd_params *p);
+
+/* Algorithm 1 lines 1-2 (Sec. 4.1): take the starting positions and build
+ * the Delaunay triangulation once on the host, then move everything to the
+ * device.
+ *   p        parameters (copied).
+ *   xy       2n doubles (x0, y0, x1, y1, ...), centres in [a, L-a]^2, no two
+ *            closer than 2a; NULL => seeded random sequential addition.
+ *   species  n bytes in {0, .., n_species-1}; NULL => all 0.
+ *   theta    n floats (self-propulsion directions); NULL => all 0.
+ *   stream   cudaStream_t to queue work on; NULL = legacy default stream.
+ *   out      receives the handle.
+ * Errors: BD_ERR_ARG (bad parameter), BD_ERR_INIT_OVERLAP (overlap or centre
+ * outside [a, L-a]), BD_ERR_TRIANGULATION, BD_ERR_NOMEM, BD_ERR_CUDA. */
+int bd_init(const bd_params *p, const double *xy, const uint8_t *species, const float *theta,
+            void *stream, bd_handle **out);
+
+/* Algorithm 1 lines 3-8: advance nsteps time steps.  Each step computes the
+ * forces (Sec. 2.2), applies Eq. (integration) with truncated Philox noise
+ * (Sec. 2.4) and self-propulsion (Sec. 7), reflects at the walls, checks
+ * r0.r1 < 0 on every triangulation edge and repairs inverted triangles
+ * (Sec. 4.3), restores the Delaunay property by edge flips, and iterates
+ * Algorithm 2 (Sec. 4.4) until no triangulation edge is shorter than sigma,
+ * re-checking and flipping after every correction pass.
+ *   stats  optional (NULL allowed): counters of this call.
+ * Returns BD_OK, or BD_ERR_STEP_REJECTED / BD_ERR_OVERLAP_NOT_CONVERGED /
+ * BD_ERR_FLIP_NOT_CONVERGED (the failing step is undone and the call stops;
+ * stats->steps_done says how many steps completed), BD_ERR_DEVICE_TIMEOUT,
+ * BD_ERR_CUDA, BD_ERR_ARG (nsteps < 0). */
+int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats);
+
+/* Copy the current state to host memory ("Ensure P updated to current
+ * time", Algorithm 1).  Any pointer may be NULL to skip that output.
+ *   xy       2n doubles, external disk order.
+ *   theta    n floats.   species  n bytes.
+ *   tri      3*n_tri ints: the current Delaunay triangulation of the disks
+ *            plus four corner points (ids n..n+3 at (-C,-C), (2C,-C),
+ *            (2C,2C), (-C,2C), C = ceil(L)), counter-clockwise; the buffer
+ *            must hold 3*(2n+2) ints.
+ *   n_tri    receives the number of triangles (2n+2).
+ *   step     receives the index of the next step.
+ * Errors: BD_ERR_ARG (h == NULL), BD_ERR_CUDA. */
+int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32_t *tri,
+                 int32_t *n_tri, int64_t *step);
+
+/* Replace positions (and, if theta != NULL, directions) with host values in
+ * external order, e.g. to resume from a checkpoint.  The disks must not
+ * overlap; the triangulation is carried over and repaired on the device
+ * (inverted-triangle repair and edge flips, Sec. 4.3), so moves should be
+ * small compared with the disk spacing.
+ * Errors: BD_ERR_ARG, BD_ERR_INIT_OVERLAP, BD_ERR_STEP_REJECTED (repair
+ * failed; state unchanged), BD_ERR_CUDA. */
+int bd_set_state(bd_handle *h, const double *xy, const float *theta);
+
+/* The pair force of Sec. 2.2 (or the short-range law) at the current
+ * positions, as the step computes it, summed to FP64: F receives 2n doubles
+ * in external order.  Errors: BD_ERR_ARG, BD_ERR_CUDA. */
+int bd_compute_forces(bd_handle *h, double *F);
+
+/* Position-grid step q (coordinates are multiples of q) and box side L. */
+int bd_get_geometry(bd_handle *h, double *q, double *L);
+
+/* Enable (1) or disable (0) CUDA-event timing of the force kernel launches
+ * made by bd_step, and read the accumulated figures: total milliseconds and
+ * number of timed launches since the last reset (reset = 1 clears them). */
+int bd_force_timing(bd_handle *h, int enable, int reset, double *total_ms, int64_t *launches);
+
+/* Number of kernel launches queued by the last bd_step call. */
+int64_t bd_last_launch_count(bd_handle *h);
+
+/* Host only (no GPU needed): the Delaunay triangulation bd_init builds
+ * (Sec. 4.1), for n centres in a box of side L plus the four corner points
+ * (ids n..n+3 at (-C,-C), (2C,-C), (2C,2C), (-C,2C), C = ceil(L)).
+ *   xy         2n doubles; centres inside (-C, 2C)^2, no duplicates.
+ *   xy_grid    optional 2n doubles: the centres rounded to the position grid
+ *              (the coordinates the triangulation is exact for).
+ *   tri        3*(2n+2) ints, counter-clockwise triangles.
+ *   n_tri      receives 2n+2.
+ * Errors: BD_ERR_ARG, BD_ERR_TRIANGULATION (duplicate or outside point). */
+int bd_triangulate(int32_t n, const double *xy, double L, double *xy_grid, int32_t *tri,
+                   int32_t *n_tri);
+
+/* Release the handle and its device memory (NULL is ignored). */
+void bd_free(bd_handle *h);
+
+/* Static description of a status code. */
+const char *bd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BD_H */

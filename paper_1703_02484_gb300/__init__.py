@@ -1,0 +1,7 @@
+"""GB300-native Brownian hard-disk time stepper (arXiv:1703.02484 hot path).
+
+The compute path is libbd_gb300.so (CUDA kernels for sm_103a behind the C ABI
+of include/bd.h); this package only marshals arguments to it."""
+from . import workloads  # noqa: F401
+from .binding import (LAW_LONG, LAW_NONE, LAW_SHORT, BDError, System, load,  # noqa: F401
+                      make_params, params_from_config)

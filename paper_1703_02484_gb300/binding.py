@@ -1,0 +1,221 @@
+"""Thin ctypes binding of the C ABI in include/bd.h (argument marshalling only).
+
+Every computation happens in libbd_gb300.so; if the library cannot be
+loaded the binding raises -- there is no fallback implementation."""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+BD_OK = 0
+ERRORS = {
+    -1: "BD_ERR_ARG", -2: "BD_ERR_CUDA", -3: "BD_ERR_INIT_OVERLAP", -4: "BD_ERR_STEP_REJECTED",
+    -5: "BD_ERR_OVERLAP_NOT_CONVERGED", -6: "BD_ERR_FLIP_NOT_CONVERGED",
+    -7: "BD_ERR_DEVICE_TIMEOUT", -8: "BD_ERR_NOMEM", -9: "BD_ERR_TRIANGULATION",
+    -10: "BD_ERR_UNSUPPORTED",
+}
+LAW_NONE, LAW_LONG, LAW_SHORT = 0, 1, 2
+
+
+class bd_params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("n_species", ctypes.c_int32),
+        ("a", ctypes.c_double), ("box_L", ctypes.c_double), ("area_fraction", ctypes.c_double),
+        ("law", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("alpha", ctypes.c_double * 4),
+        ("eps", ctypes.c_double), ("kappa", ctypes.c_double),
+        ("r_cut", ctypes.c_double), ("skin", ctypes.c_double),
+        ("D", ctypes.c_double), ("Dr", ctypes.c_double), ("v0", ctypes.c_double), ("dt", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("replica", ctypes.c_int32),
+        ("max_corr_iters", ctypes.c_int32), ("max_flip_rounds", ctypes.c_int32),
+        ("literal_noise", ctypes.c_int32), ("step0", ctypes.c_int64),
+    ]
+
+
+class bd_step_stats(ctypes.Structure):
+    _fields_ = [
+        ("steps_done", ctypes.c_int64), ("corr_iters", ctypes.c_int64),
+        ("overlap_pairs", ctypes.c_int64), ("flip_rounds", ctypes.c_int64),
+        ("flips", ctypes.c_int64), ("repair_flips", ctypes.c_int64), ("inverted", ctypes.c_int64),
+        ("max_corr_iters", ctypes.c_int32), ("rejected", ctypes.c_int32),
+        ("verlet_rebuilds", ctypes.c_int32), ("pad", ctypes.c_int32),
+        ("max_overlap", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+# entry points declared in include/bd.h: (name, restype, argtypes)
+_P = ctypes.c_void_p
+SIGNATURES = [
+    ("bd_default_params", ctypes.c_int, [ctypes.POINTER(bd_params)]),
+    ("bd_init", ctypes.c_int, [ctypes.POINTER(bd_params), _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    ("bd_step", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(bd_step_stats)]),
+    ("bd_get_state", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int64)]),
+    ("bd_set_state", ctypes.c_int, [_P, _P, _P]),
+    ("bd_compute_forces", ctypes.c_int, [_P, _P]),
+    ("bd_get_geometry", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    ("bd_force_timing", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int64)]),
+    ("bd_last_launch_count", ctypes.c_int64, [_P]),
+    ("bd_triangulate", ctypes.c_int, [ctypes.c_int32, _P, ctypes.c_double, _P, _P,
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    ("bd_free", None, [_P]),
+    ("bd_strerror", ctypes.c_char_p, [ctypes.c_int]),
+]
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libbd_gb300.so (building it first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libbd_gb300.so is not built; run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class BDError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = load().bd_strerror(code).decode()
+        super().__init__("%s failed: %s (%s)" % (where, ERRORS.get(code, code), msg))
+
+
+def _check(code, where):
+    if code != BD_OK:
+        raise BDError(code, where)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_params(n, L=None, rho=None, a=1.0, law=LAW_NONE, alpha=(0, 0, 0, 0), n_species=1,
+                eps=1.0, kappa=1.0, r_cut=5.0, skin=0.6, D=1.0, Dr=0.0, v0=0.0, dt=1e-4,
+                seed=0, replica=0, precision=0, max_corr_iters=1000, max_flip_rounds=4096,
+                literal_noise=0, step0=0):
+    p = bd_params()
+    _check(load().bd_default_params(ctypes.byref(p)), "bd_default_params")
+    p.n, p.n_species, p.a = int(n), int(n_species), float(a)
+    p.box_L = float(L) if L is not None else 0.0
+    p.area_fraction = float(rho) if rho is not None else 0.0
+    p.law, p.precision = int(law), int(precision)
+    for k in range(4):
+        p.alpha[k] = float(alpha[k])
+    p.eps, p.kappa, p.r_cut, p.skin = float(eps), float(kappa), float(r_cut), float(skin)
+    p.D, p.Dr, p.v0, p.dt = float(D), float(Dr), float(v0), float(dt)
+    p.seed, p.replica = int(seed), int(replica)
+    p.max_corr_iters, p.max_flip_rounds = int(max_corr_iters), int(max_flip_rounds)
+    p.literal_noise, p.step0 = int(literal_noise), int(step0)
+    return p
+
+
+def params_from_config(cfg, n=None, seed=None):
+    return make_params(n=cfg.n if n is None else n, rho=cfg.rho, a=cfg.a, law=cfg.law,
+                       alpha=cfg.alpha, n_species=cfg.n_species, eps=cfg.eps, kappa=cfg.kappa,
+                       r_cut=cfg.r_cut, skin=cfg.skin, D=cfg.D, Dr=cfg.Dr, v0=cfg.v0, dt=cfg.dt,
+                       seed=cfg.seed if seed is None else seed, precision=cfg.precision)
+
+
+class System:
+    """One simulated system behind a bd_handle."""
+
+    def __init__(self, params, xy=None, species=None, theta=None, stream=None):
+        lib = load()
+        self.n = params.n
+        self._xy = None if xy is None else np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+        self._sp = None if species is None else np.ascontiguousarray(species, dtype=np.uint8)
+        self._th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+        h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(int(stream))
+        _check(lib.bd_init(ctypes.byref(params), _ptr(self._xy), _ptr(self._sp), _ptr(self._th),
+                           st, ctypes.byref(h)), "bd_init")
+        self.h = h
+        self.params = params
+
+    def close(self):
+        if self.h:
+            load().bd_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps=1, raise_on_error=True):
+        st = bd_step_stats()
+        code = load().bd_step(self.h, int(nsteps), ctypes.byref(st))
+        if raise_on_error:
+            _check(code, "bd_step")
+        return (st.as_dict(), code) if not raise_on_error else st.as_dict()
+
+    def state(self, want_tri=True):
+        n = self.n
+        xy = np.zeros((n, 2), dtype=np.float64)
+        th = np.zeros(n, dtype=np.float32)
+        sp = np.zeros(n, dtype=np.uint8)
+        tri = np.zeros((2 * n + 2, 3), dtype=np.int32) if want_tri else None
+        nt = ctypes.c_int32()
+        stp = ctypes.c_int64()
+        _check(load().bd_get_state(self.h, _ptr(xy), _ptr(th), _ptr(sp), _ptr(tri),
+                                   ctypes.byref(nt), ctypes.byref(stp)), "bd_get_state")
+        return dict(xy=xy, theta=th, species=sp, tri=tri, n_tri=nt.value, step=stp.value)
+
+    def set_state(self, xy, theta=None):
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+        _check(load().bd_set_state(self.h, _ptr(xy), _ptr(th)), "bd_set_state")
+
+    def forces(self):
+        F = np.zeros((self.n, 2), dtype=np.float64)
+        _check(load().bd_compute_forces(self.h, _ptr(F)), "bd_compute_forces")
+        return F
+
+    def geometry(self):
+        q, L = ctypes.c_double(), ctypes.c_double()
+        _check(load().bd_get_geometry(self.h, ctypes.byref(q), ctypes.byref(L)), "bd_get_geometry")
+        return q.value, L.value
+
+    def force_timing(self, enable=True, reset=False):
+        ms, k = ctypes.c_double(), ctypes.c_int64()
+        _check(load().bd_force_timing(self.h, int(enable), int(reset), ctypes.byref(ms),
+                                      ctypes.byref(k)), "bd_force_timing")
+        return ms.value, k.value
+
+    def last_launch_count(self):
+        return int(load().bd_last_launch_count(self.h))
+
+
+def triangulate(xy, L):
+    """Host-side initial Delaunay triangulation (bd_triangulate): returns
+    (triangles (2n+2, 3), centres rounded to the position grid)."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    n = len(xy)
+    tri = np.zeros((2 * n + 2, 3), dtype=np.int32)
+    grid = np.zeros_like(xy)
+    nt = ctypes.c_int32()
+    _check(load().bd_triangulate(n, _ptr(xy), float(L), _ptr(grid), _ptr(tri), ctypes.byref(nt)),
+           "bd_triangulate")
+    return tri[: nt.value], grid

@@ -1,0 +1,90 @@
+// Internal layout shared by the C-ABI layer and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bd.h"
+
+// tile sizes of the all-pairs sweep (Sec. 4.1 tiling of Nyland et al.)
+#define BD_TJ 256            // j-tile: disks staged per shared-memory stage
+#define BD_FT 128            // threads per force block
+#define BD_IPT 4             // i disks per thread
+#define BD_IB (BD_FT * BD_IPT)  // i disks per force block
+
+// triangle flag bits stored in tv[t].w
+#define BD_TRI_INVERTED 1
+#define BD_TRI_DIRTY 2
+
+// device control block of the triangulation kernel
+struct BdCtl {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int status;
+  int pad0;
+  unsigned long long epoch;        // flip-round counter, grows across launches
+  int cnt[4][8];                   // per-phase counters, rotated every barrier
+  // statistics accumulated over a bd_step call
+  long long st_corr_iters;
+  long long st_overlap_pairs;
+  long long st_flip_rounds;
+  long long st_flips;
+  long long st_repair_flips;
+  long long st_inverted;
+  long long st_steps;
+  int st_max_corr_iters;
+  int st_rejected;
+  unsigned long long st_max_overlap_bits;   // double bits of the deepest overlap (monotone for >= 0)
+  int st_fail_phase;
+  int pad1;
+};
+
+// counter slots within BdCtl::cnt[phase % 4]
+enum { C_INV = 0, C_REJECT = 1, C_FLIPS = 2, C_OVERLAP = 3, C_CAND = 4 };
+
+struct BdDev {
+  // particles (internal order, np slots + 4 corner points at the end)
+  double2 *pos, *prev, *pos0;
+  float4 *work;            // (x_hi, y_hi, x_lo, y_lo) FP32 pair of each coordinate
+  float *theta, *theta0;
+  uint8_t *species;        // 255 = empty slot
+  int *ext_id;             // external index (-1 = empty slot)
+  uint8_t *moved;
+  double2 *disp;
+  // triangulation (corner table)
+  int4 *tv, *tn, *tv_snap, *tn_snap;
+  unsigned long long *claim;
+  unsigned long long *partner;
+  // force sweep
+  int *iperm;              // spatial order of i (np_i slots, -1 = none)
+  float2 *iorigin;         // per i-block origin (integers)
+  uint8_t *tile_species;   // species of each j tile
+  double2 *fpart;          // [nchunk][np] partial forces
+  // short range
+  int *vl_start, *vl_idx, *vl_cnt;
+  double2 *vl_ref;
+  int *cell_start, *cell_idx;
+  BdCtl *ctl;
+};
+
+struct BdConst {
+  int n, np, np_i, nt, ntiles, nchunk, n_iblocks;
+  int law, precision, n_species;
+  double a, sigma, L, wall_lo, wall_hi;
+  double q, inv_q;
+  float alpha[4];
+  double alpha_d[4];
+  double eps, kappa, r_cut, skin;
+  double D, Dr, v0, dt;
+  double amp, amp_r;       // translational / rotational noise amplitude
+  uint64_t seed;
+  uint32_t replica;
+  int max_corr_iters, max_flip_rounds;
+};
+
+// launchers (kernels_*.cu)
+cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t s);
+cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, cudaStream_t s);
+cudaError_t bd_launch_dt(const BdDev &d, const BdConst &c, int mode, cudaStream_t s, int grid, int block);
+int bd_dt_grid(int *grid, int *block);
+cudaError_t bd_launch_work_copy(const BdDev &d, const BdConst &c, cudaStream_t s);
+cudaError_t bd_launch_force_sum(const BdDev &d, const BdConst &c, double2 *out, cudaStream_t s);

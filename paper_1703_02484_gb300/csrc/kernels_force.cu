@@ -1,0 +1,310 @@
+// Long-range all-pairs force sweep and the Euler-Maruyama integrator.
+//
+// Force (Sec. 2.2): F_i = sum_{j != i} A[s_i][s_j] (r_i - r_j) / |r_i - r_j|^3.
+// The paper tiles the O(N^2) sweep through shared memory (Nyland et al.,
+// Sec. 4.1) or warp shuffles (Algorithm 3, Sec. 4.5), one thread per disk.
+// Here each block owns BD_IB disks i (BD_IPT per thread, in registers) and a
+// chunk of j tiles; tiles of BD_TJ disks are staged in shared memory, double
+// buffered, and every shared-memory load feeds BD_IPT pair interactions.
+//
+// Precision (FP32 path):
+//  - Disks are stored in internal order: species-major, each species segment
+//    padded to a whole number of j tiles with inert far-away slots, so every
+//    tile is single-species and A[s_i][s_tile] multiplies the tile's summed
+//    r/r^3 once per tile (8 FP32 instructions + 1 MUFU per pair).
+//  - i blocks follow a Hilbert order over all disks, so a block covers a
+//    compact patch; coordinates are re-centred on the block's origin from
+//    the (hi, lo) FP32 pair of each FP64 coordinate, which keeps near pairs
+//    at FP32 resolution of the patch size rather than of the box size.
+//  - Per-tile FP32 sums are added into (hi, lo) compensated accumulators
+//    (TwoSum); chunk partials are summed in FP64 by the integrator.
+//  - The self pair contributes exactly zero: r^2 gets a 1e-20 a^2 offset, so
+//    its 1/r^3 is finite while its dx is zero.
+//
+// Integrator (Eq. (integration), Sec. 2.4, Sec. 7): Philox4x32-10 words ->
+// Box-Muller -> clamp to [-3, 3]; dr = dt (F + v0 e(theta)) + amp xi in FP32
+// (FP64 when precision = 1), added to the FP64 master position, rounded to
+// the position grid, reflected at the walls; theta += amp_r n.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "bd_internal.h"
+#include "philox.cuh"
+
+namespace {
+
+__device__ __forceinline__ float rsqrt_apx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void two_sum(float &hi, float &lo, float t) {
+  float s = __fadd_rn(hi, t);
+  float bp = __fsub_rn(s, hi);
+  float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(t, bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+__device__ __forceinline__ int ctl_failed(const BdCtl *ctl) { return *(volatile const int *)&ctl->status; }
+
+}  // namespace
+
+__global__ void __launch_bounds__(BD_FT) k_force_long_f32(BdDev d, BdConst c) {
+  if (ctl_failed(d.ctl)) return;
+  __shared__ float4 sj[2][BD_TJ / 2];   // (x_j, y_j, x_j+1, y_j+1) re-centred
+  const int ib = blockIdx.x, jc = blockIdx.y, tid = threadIdx.x;
+  const float2 org = d.iorigin[ib];
+  float xi[BD_IPT], yi[BD_IPT], ax[BD_IPT], ay[BD_IPT];
+  float fxh[BD_IPT], fxl[BD_IPT], fyh[BD_IPT], fyl[BD_IPT], a0[BD_IPT], a1[BD_IPT];
+  int ii[BD_IPT];
+#pragma unroll
+  for (int q = 0; q < BD_IPT; ++q) {
+    int i = d.iperm[ib * BD_IB + q * BD_FT + tid];
+    ii[q] = i;
+    if (i >= 0) {
+      float4 w = d.work[i];
+      xi[q] = __fadd_rn(__fsub_rn(w.x, org.x), w.z);
+      yi[q] = __fadd_rn(__fsub_rn(w.y, org.y), w.w);
+      int s = d.species[i];
+      a0[q] = c.alpha[2 * s + 0];
+      a1[q] = c.alpha[2 * s + 1];
+    } else {
+      xi[q] = 1.0e18f;
+      yi[q] = 1.0e18f;
+      a0[q] = 0.f;
+      a1[q] = 0.f;
+    }
+    ax[q] = ay[q] = 0.f;
+    fxh[q] = fxl[q] = fyh[q] = fyl[q] = 0.f;
+  }
+  const int t_begin = (int)(((long long)c.ntiles * jc) / c.nchunk);
+  const int t_end = (int)(((long long)c.ntiles * (jc + 1)) / c.nchunk);
+  const float eps0 = 1e-20f * (float)(c.a * c.a);
+
+  // stage: each thread re-centres 2 disks of the tile (BD_TJ = 2 * BD_FT)
+  float2 st0, st1;
+  auto fetch = [&](int tile) {
+    int j0 = tile * BD_TJ + 2 * tid;
+    float4 w0 = d.work[j0], w1 = d.work[j0 + 1];
+    st0 = make_float2(__fadd_rn(__fsub_rn(w0.x, org.x), w0.z), __fadd_rn(__fsub_rn(w0.y, org.y), w0.w));
+    st1 = make_float2(__fadd_rn(__fsub_rn(w1.x, org.x), w1.z), __fadd_rn(__fsub_rn(w1.y, org.y), w1.w));
+  };
+  int buf = 0;
+  if (t_begin < t_end) {
+    fetch(t_begin);
+    sj[0][tid] = make_float4(st0.x, st0.y, st1.x, st1.y);
+  }
+  __syncthreads();
+  for (int t = t_begin; t < t_end; ++t) {
+    if (t + 1 < t_end) fetch(t + 1);
+#pragma unroll 4
+    for (int jj = 0; jj < BD_TJ / 2; ++jj) {
+      float4 p = sj[buf][jj];
+#pragma unroll
+      for (int q = 0; q < BD_IPT; ++q) {
+        float dx = __fsub_rn(p.x, xi[q]);
+        float dy = __fsub_rn(p.y, yi[q]);
+        float r2 = __fmaf_rn(dx, dx, eps0);
+        r2 = __fmaf_rn(dy, dy, r2);
+        float s = rsqrt_apx(r2);
+        float s3 = __fmul_rn(__fmul_rn(s, s), s);
+        ax[q] = __fmaf_rn(dx, s3, ax[q]);
+        ay[q] = __fmaf_rn(dy, s3, ay[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < BD_IPT; ++q) {
+        float dx = __fsub_rn(p.z, xi[q]);
+        float dy = __fsub_rn(p.w, yi[q]);
+        float r2 = __fmaf_rn(dx, dx, eps0);
+        r2 = __fmaf_rn(dy, dy, r2);
+        float s = rsqrt_apx(r2);
+        float s3 = __fmul_rn(__fmul_rn(s, s), s);
+        ax[q] = __fmaf_rn(dx, s3, ax[q]);
+        ay[q] = __fmaf_rn(dy, s3, ay[q]);
+      }
+    }
+    // (r_j - r_i) was summed: the force on i is -A[s_i][s_tile] times it
+    const int sp = d.tile_species[t];
+#pragma unroll
+    for (int q = 0; q < BD_IPT; ++q) {
+      float al = sp ? a1[q] : a0[q];
+      two_sum(fxh[q], fxl[q], -al * ax[q]);
+      two_sum(fyh[q], fyl[q], -al * ay[q]);
+      ax[q] = ay[q] = 0.f;
+    }
+    if (t + 1 < t_end) sj[buf ^ 1][tid] = make_float4(st0.x, st0.y, st1.x, st1.y);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int q = 0; q < BD_IPT; ++q) {
+    int i = ii[q];
+    if (i >= 0)
+      d.fpart[(size_t)jc * c.np + i] =
+          make_double2((double)fxh[q] + (double)fxl[q], (double)fyh[q] + (double)fyl[q]);
+  }
+}
+
+// FP64 variant (precision = 1): one disk per thread, FP64 master positions
+__global__ void __launch_bounds__(128) k_force_long_f64(BdDev d, BdConst c) {
+  if (ctl_failed(d.ctl)) return;
+  __shared__ double2 sp[128];
+  __shared__ int ss[128];
+  const int i = blockIdx.x * 128 + threadIdx.x;
+  const int jc = blockIdx.y;
+  const bool live = i < c.np && d.ext_id[i] >= 0;
+  double2 pi = live ? d.pos[i] : make_double2(0.0, 0.0);
+  int si = live ? d.species[i] : 0;
+  double fx = 0.0, fy = 0.0;
+  const int per = (c.np + c.nchunk - 1) / c.nchunk;
+  const int j_begin = jc * per, j_end = min(c.np, j_begin + per);
+  for (int j0 = j_begin; j0 < j_end; j0 += 128) {
+    int j = j0 + threadIdx.x;
+    bool ok = j < j_end && d.ext_id[j] >= 0;
+    sp[threadIdx.x] = ok ? d.pos[j] : make_double2(0.0, 0.0);
+    ss[threadIdx.x] = ok ? (int)d.species[j] : -1;
+    __syncthreads();
+    int m = min(128, j_end - j0);
+    for (int k = 0; k < m; ++k) {
+      int sk = ss[k];
+      if (sk < 0 || j0 + k == i) continue;
+      double rx = pi.x - sp[k].x, ry = pi.y - sp[k].y;
+      double r2 = rx * rx + ry * ry;
+      double cf = c.alpha_d[2 * si + sk] / (r2 * sqrt(r2));
+      fx += cf * rx;
+      fy += cf * ry;
+    }
+    __syncthreads();
+  }
+  if (live) d.fpart[(size_t)jc * c.np + i] = make_double2(fx, fy);
+}
+
+__global__ void k_force_sum(BdDev d, BdConst c, double2 *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.np) return;
+  double fx = 0.0, fy = 0.0;
+  for (int k = 0; k < c.nchunk; ++k) {
+    double2 f = d.fpart[(size_t)k * c.np + i];
+    fx += f.x;
+    fy += f.y;
+  }
+  out[i] = make_double2(fx, fy);
+}
+
+namespace {
+__device__ __forceinline__ double snapd(double v, double q, double inv_q) {
+  return __dmul_rn(rint(__dmul_rn(v, inv_q)), q);
+}
+__device__ __forceinline__ float4 split(double2 p) {
+  float xh = __double2float_rn(p.x), yh = __double2float_rn(p.y);
+  return make_float4(xh, yh, __double2float_rn(p.x - (double)xh), __double2float_rn(p.y - (double)yh));
+}
+}  // namespace
+
+__global__ void k_integrate(BdDev d, BdConst c, long long step) {
+  if (ctl_failed(d.ctl)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.np) return;
+  const int e = d.ext_id[i];
+  if (e < 0) return;
+  double fx = 0.0, fy = 0.0;
+  if (c.law != BD_LAW_NONE) {
+    for (int k = 0; k < c.nchunk; ++k) {
+      double2 f = d.fpart[(size_t)k * c.np + i];
+      fx += f.x;
+      fy += f.y;
+    }
+  }
+  const double2 p = d.pos[i];
+  d.pos0[i] = p;
+  d.prev[i] = p;
+  const float th = d.theta[i];
+  d.theta0[i] = th;
+  bdrng::U4 r = bdrng::draw((uint32_t)e, (int64_t)step, c.seed, c.replica, bdrng::TAG_NOISE);
+  double nx, ny;
+  float thn;
+  if (c.precision == 0) {
+    const float sc = 2.3283064365386963e-10f;  // 2^-32
+    float u0 = __fmaf_rn((float)r.x, sc, 0.5f * sc), u1 = __fmaf_rn((float)r.y, sc, 0.5f * sc);
+    float u2 = __fmaf_rn((float)r.z, sc, 0.5f * sc), u3 = __fmaf_rn((float)r.w, sc, 0.5f * sc);
+    float ra = sqrtf(-2.0f * logf(u0)), rb = sqrtf(-2.0f * logf(u2));
+    float s1, c1, s2, c2;
+    sincospif(2.0f * u1, &s1, &c1);
+    sincospif(2.0f * u3, &s2, &c2);
+    float z0 = fminf(3.0f, fmaxf(-3.0f, ra * c1));
+    float z1 = fminf(3.0f, fmaxf(-3.0f, ra * s1));
+    float z2 = fminf(3.0f, fmaxf(-3.0f, rb * c2));
+    float st, ct;
+    sincosf(th, &st, &ct);
+    const float dt = (float)c.dt, v0 = (float)c.v0, amp = (float)c.amp;
+    float dxf = dt * ((float)fx + v0 * ct) + amp * z0;
+    float dyf = dt * ((float)fy + v0 * st) + amp * z1;
+    nx = p.x + (double)dxf;
+    ny = p.y + (double)dyf;
+    thn = th + (float)c.amp_r * z2;
+  } else {
+    const double sc = 2.3283064365386962890625e-10;
+    double u0 = ((double)r.x + 0.5) * sc, u1 = ((double)r.y + 0.5) * sc;
+    double u2 = ((double)r.z + 0.5) * sc, u3 = ((double)r.w + 0.5) * sc;
+    double ra = sqrt(-2.0 * log(u0)), rb = sqrt(-2.0 * log(u2));
+    double s1, c1, s2, c2;
+    sincospi(2.0 * u1, &s1, &c1);
+    sincospi(2.0 * u3, &s2, &c2);
+    double z0 = fmin(3.0, fmax(-3.0, ra * c1));
+    double z1 = fmin(3.0, fmax(-3.0, ra * s1));
+    double z2 = fmin(3.0, fmax(-3.0, rb * c2));
+    double st, ct;
+    sincos((double)th, &st, &ct);
+    nx = p.x + c.dt * (fx + c.v0 * ct) + c.amp * z0;
+    ny = p.y + c.dt * (fy + c.v0 * st) + c.amp * z1;
+    thn = (float)((double)th + c.amp_r * z2);
+  }
+  nx = snapd(nx, c.q, c.inv_q);
+  ny = snapd(ny, c.q, c.inv_q);
+  if (nx < c.wall_lo) nx = 2.0 * c.wall_lo - nx;
+  if (nx > c.wall_hi) nx = 2.0 * c.wall_hi - nx;
+  if (ny < c.wall_lo) ny = 2.0 * c.wall_lo - ny;
+  if (ny > c.wall_hi) ny = 2.0 * c.wall_hi - ny;
+  const double2 pn = make_double2(nx, ny);
+  d.pos[i] = pn;
+  d.work[i] = split(pn);
+  d.theta[i] = thn;
+  d.moved[i] = 1;
+}
+
+__global__ void k_work_copy(BdDev d, BdConst c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.np) return;
+  if (d.ext_id[i] < 0) {
+    d.work[i] = make_float4(1.0e18f, 1.0e18f, 0.f, 0.f);
+    return;
+  }
+  d.work[i] = split(d.pos[i]);
+}
+
+cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t s) {
+  if (c.precision == 0) {
+    k_force_long_f32<<<dim3(c.n_iblocks, c.nchunk), BD_FT, 0, s>>>(d, c);
+  } else {
+    k_force_long_f64<<<dim3((c.np + 127) / 128, c.nchunk), 128, 0, s>>>(d, c);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, cudaStream_t s) {
+  k_integrate<<<(c.np + 255) / 256, 256, 0, s>>>(d, c, (long long)step);
+  return cudaGetLastError();
+}
+
+cudaError_t bd_launch_work_copy(const BdDev &d, const BdConst &c, cudaStream_t s) {
+  k_work_copy<<<(c.np + 255) / 256, 256, 0, s>>>(d, c);
+  return cudaGetLastError();
+}
+
+cudaError_t bd_launch_force_sum(const BdDev &d, const BdConst &c, double2 *out, cudaStream_t s) {
+  k_force_sum<<<(c.np + 255) / 256, 256, 0, s>>>(d, c, out);
+  return cudaGetLastError();
+}

@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+declared in include/bd.h; host-only entry points run on the CPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1703_02484_gb300 as bd
+from paper_1703_02484_gb300 import binding, workloads
+from oracle import geometry
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(bd_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = bd.load()
+    names = declared_functions()
+    assert "bd_init" in names and "bd_step" in names and "bd_free" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    # the binding covers the same set
+    assert {s[0] for s in binding.SIGNATURES} == names
+
+
+def test_default_params_and_strerror():
+    lib = bd.load()
+    p = binding.bd_params()
+    assert lib.bd_default_params(p) == 0
+    assert p.a == 1.0 and p.max_corr_iters > 0
+    assert b"overlap" in lib.bd_strerror(-3)
+    assert lib.bd_default_params(None) == -1
+
+
+def test_init_argument_errors_without_gpu():
+    lib = bd.load()
+    import ctypes
+    p = binding.make_params(10, rho=0.3)
+    p.n = 0
+    h = ctypes.c_void_p()
+    assert lib.bd_init(ctypes.byref(p), None, None, None, None, ctypes.byref(h)) == -1
+    p = binding.make_params(10, rho=0.3, law=binding.LAW_LONG)
+    p.n_species = 3
+    assert lib.bd_init(ctypes.byref(p), None, None, None, None, ctypes.byref(h)) == -1
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 500, 20000])
+def test_host_triangulation_equals_oracle_delaunay(n):
+    cfg = workloads.CONFIGS["c5"]
+    L = workloads.box_side(max(n, 4), cfg.rho)
+    xy = workloads.initial_positions(n, L, 1.0, cfg.rho, seed=n)
+    tri, grid = binding.triangulate(xy, L)
+    assert len(tri) == 2 * n + 2
+    assert np.max(np.abs(grid - xy)) <= 1e-11 * L
+    ot = geometry.delaunay(grid, L)
+    assert np.array_equal(geometry.edges(tri), geometry.edges(ot))
+    P = geometry.with_ghosts(grid, L)
+    for t in tri[: min(len(tri), 2000)]:
+        assert geometry.orient(P[t[0]], P[t[1]], P[t[2]]) > 0
+
+
+def test_host_triangulation_lattice_start():
+    # the jittered lattice start used at high area fraction
+    cfg = workloads.CONFIGS["c3"]
+    n = 4000
+    L = workloads.box_side(n, cfg.rho)
+    xy = workloads.initial_positions(n, L, 1.0, cfg.rho, seed=3)
+    tri, grid = binding.triangulate(xy, L)
+    ot = geometry.delaunay(grid, L)
+    assert np.array_equal(geometry.edges(tri), geometry.edges(ot))

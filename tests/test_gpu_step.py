@@ -1,0 +1,191 @@
+"""GPU parity: the CUDA time step against the FP64 oracle, through the C ABI.
+
+Tolerances (stated by the task for this method): per-disk force error <= 1e-5
+relative to the force norm (read as the RMS of |F_i| over the system), and
+position error <= 1e-5 a after one step; the Delaunay edge set must match
+exactly for points in general position."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1703_02484_gb300 as bd  # noqa: E402
+from paper_1703_02484_gb300 import workloads  # noqa: E402
+from oracle import forces as oforces  # noqa: E402
+from oracle import geometry, overlap  # noqa: E402
+from oracle import step as ostep  # noqa: E402
+from scipy.spatial import cKDTree  # noqa: E402
+
+POS_TOL = 1e-5
+FORCE_TOL = 1e-5
+
+
+def stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def oracle_params(cfg, L, seed=None):
+    return ostep.Params(L=L, a=cfg.a, law=cfg.law, alpha=cfg.alpha, eps=cfg.eps, kappa=cfg.kappa,
+                        r_cut=cfg.r_cut, D=cfg.D, Dr=cfg.Dr, v0=cfg.v0, dt=cfg.dt,
+                        seed=cfg.seed if seed is None else seed)
+
+
+def force_error(F, ref):
+    scale = math.sqrt(float(np.mean(np.sum(ref ** 2, axis=1))))
+    return float(np.max(np.linalg.norm(F - ref, axis=1))) / scale
+
+
+@pytest.mark.parametrize("cfgname,n", [("c2", 3001), ("c2", 777), ("c1", 1024), ("c5", 4096)])
+def test_forces_match_oracle(cfgname, n):
+    cfg = workloads.CONFIGS[cfgname]
+    xy, sp, th = workloads.initial_state(cfg, n=n)
+    s = bd.System(bd.params_from_config(cfg, n=n), xy, sp, th, stream=stream())
+    F = s.forces()
+    grid = s.state(want_tri=False)["xy"]
+    ref = oforces.long_range_numpy(grid, sp, cfg.alpha if cfg.n_species == 2 else (cfg.alpha[0],) * 4)
+    err = force_error(F, ref)
+    assert err <= FORCE_TOL, err
+    if cfg.precision == 1:
+        assert err <= 1e-12
+
+
+def test_forces_full_size_sampled():
+    cfg = workloads.CONFIGS["n1e5"]
+    xy, sp, th = workloads.initial_state(cfg)
+    s = bd.System(bd.params_from_config(cfg), xy, sp, th, stream=stream())
+    F = s.forces()
+    grid = s.state(want_tri=False)["xy"]
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(cfg.n, 256, replace=False))
+    ref = np.concatenate([oforces.long_range(grid, sp, cfg.alpha, idx=[i], threads=1) for i in idx])
+    # RMS force scale from the sample
+    scale = math.sqrt(float(np.mean(np.sum(ref ** 2, axis=1))))
+    err = float(np.max(np.linalg.norm(F[idx] - ref, axis=1))) / scale
+    assert err <= FORCE_TOL, err
+
+
+def _one_step(cfgname, n, seed_state, step_index=0, near_contact=True):
+    cfg = workloads.CONFIGS[cfgname]
+    L = workloads.box_side(n, cfg.rho)
+    if near_contact:
+        xy = workloads.near_contact_state(n, L, cfg.a, seed=seed_state)
+    else:
+        xy = workloads.initial_positions(n, L, cfg.a, cfg.rho, seed_state)
+    _, sp, th = workloads.initial_state(cfg, n=n)
+    p = bd.params_from_config(cfg, n=n)
+    p.step0 = step_index
+    s = bd.System(p, xy, sp, th, stream=stream())
+    st = s.step(1)
+    out = s.state()
+    ref = ostep.step(xy, th, sp, step_index, oracle_params(cfg, L))
+    return cfg, L, s, st, out, ref
+
+
+@pytest.mark.parametrize("cfgname,n,seed,k", [("c2", 4000, 1, 0), ("c2", 2500, 2, 12345),
+                                               ("c1", 1024, 3, 7), ("c5", 4096, 4, 99)])
+def test_one_step_parity(cfgname, n, seed, k):
+    cfg, L, s, st, out, ref = _one_step(cfgname, n, seed, k)
+    assert not ref["rejected"]
+    assert ref["corr_iters"] >= 1          # the start had overlaps to correct
+    err = float(np.max(np.abs(out["xy"] - ref["xy"])))
+    assert err <= POS_TOL * cfg.a, err
+    assert st["corr_iters"] == ref["corr_iters"]
+    # theta: FP32 director update
+    assert np.max(np.abs(out["theta"] - ref["theta"])) <= 1e-5
+    # Delaunay edge set: the GPU's triangulation equals the oracle's Delaunay
+    # triangulation of the oracle's own final positions
+    assert np.array_equal(geometry.edges(out["tri"]), geometry.edges(ref["tris"]))
+    # and no pair overlaps anywhere
+    assert len(cKDTree(out["xy"]).query_pairs(2 * cfg.a * (1 - 1e-12))) == 0
+
+
+def test_multi_step_invariants():
+    cfg = workloads.CONFIGS["c5"]
+    n = 4096
+    xy, sp, th = workloads.initial_state(cfg, n=n)
+    L = workloads.box_side(n, cfg.rho)
+    s = bd.System(bd.params_from_config(cfg, n=n), xy, sp, th, stream=stream())
+    total = 0
+    for _ in range(10):
+        st = s.step(10)
+        assert st["steps_done"] == 10
+        total += st["corr_iters"]
+        out = s.state()
+        assert len(cKDTree(out["xy"]).query_pairs(2 * cfg.a * (1 - 1e-12))) == 0
+        assert np.all(out["xy"] >= cfg.a) and np.all(out["xy"] <= L - cfg.a)
+        P = geometry.with_ghosts(out["xy"], L)
+        # the maintained triangulation is the Delaunay triangulation of the positions
+        assert np.array_equal(geometry.edges(out["tri"]), geometry.edges(geometry.delaunay(out["xy"], L)))
+    assert out["step"] == 100
+
+
+def test_trajectory_step_parity_from_state():
+    # feed a state reached by the GPU after some steps back to both sides as a
+    # new start (through the public entry points) and compare one more step
+    cfg = workloads.CONFIGS["c2"]
+    n = 3000
+    L = workloads.box_side(n, cfg.rho)
+    xy = workloads.near_contact_state(n, L, 1.0, seed=9)
+    _, sp, th = workloads.initial_state(cfg, n=n)
+    p = bd.params_from_config(cfg, n=n)
+    s = bd.System(p, xy, sp, th, stream=stream())
+    s.step(20)
+    mid = s.state()
+    ref = ostep.step(mid["xy"], mid["theta"], mid["species"], mid["step"], oracle_params(cfg, L))
+    s.step(1)
+    out = s.state()
+    assert np.max(np.abs(out["xy"] - ref["xy"])) <= POS_TOL
+    assert np.array_equal(geometry.edges(out["tri"]), geometry.edges(ref["tris"]))
+
+
+def test_set_state_repairs_triangulation():
+    cfg = workloads.CONFIGS["c5"]
+    n = 2000
+    xy, sp, th = workloads.initial_state(cfg, n=n)
+    L = workloads.box_side(n, cfg.rho)
+    s = bd.System(bd.params_from_config(cfg, n=n), xy, sp, th, stream=stream())
+    rng = np.random.default_rng(5)
+    moved = xy + rng.normal(scale=0.05, size=xy.shape)
+    moved = np.clip(moved, 1.0, L - 1.0)
+    keep = len(cKDTree(moved).query_pairs(2.0)) == 0
+    if not keep:
+        # push overlapping pairs back to the original positions
+        for i, j in cKDTree(moved).query_pairs(2.0):
+            moved[i], moved[j] = xy[i], xy[j]
+    assert len(cKDTree(moved).query_pairs(2.0)) == 0
+    s.set_state(moved)
+    out = s.state()
+    assert np.max(np.abs(out["xy"] - moved)) <= 1e-11 * L
+    assert np.array_equal(geometry.edges(out["tri"]), geometry.edges(geometry.delaunay(out["xy"], L)))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 257, 513])
+def test_tiny_and_ragged_sizes(n):
+    cfg = workloads.CONFIGS["c2"]
+    L = workloads.box_side(max(n, 16), cfg.rho)
+    xy = workloads.initial_positions(n, L, 1.0, cfg.rho, seed=n)
+    sp = (np.arange(n) % 2).astype(np.uint8)
+    th = np.zeros(n, np.float32)
+    p = bd.params_from_config(cfg, n=n)
+    p.box_L = L
+    s = bd.System(p, xy, sp, th, stream=stream())
+    st = s.step(5)
+    assert st["steps_done"] == 5
+    out = s.state()
+    assert len(out["tri"]) == 2 * n + 2
+    assert np.array_equal(geometry.edges(out["tri"]), geometry.edges(geometry.delaunay(out["xy"], L)))
+    if n >= 2:
+        assert len(cKDTree(out["xy"]).query_pairs(2.0 * (1 - 1e-12))) == 0
+
+
+def test_init_rejects_overlap():
+    p = bd.make_params(2, L=20.0)
+    with pytest.raises(bd.BDError) as e:
+        bd.System(p, np.array([[5.0, 5.0], [6.0, 5.0]]))
+    assert e.value.code == -3
