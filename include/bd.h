@@ -187,6 +187,27 @@ int64_t bd_last_launch_count(bd_handle *h);
 int bd_triangulate(int32_t n, const double *xy, double L, double *xy_grid, int32_t *tri,
                    int32_t *n_tri);
 
+/* All-pairs long-range force for callers that cannot allocate device memory
+ * (no counterpart in the paper; it exists for users whose device memory is
+ * owned and budgeted by a host framework's allocator, whose loops cannot
+ * afford the device synchronisation of cudaMalloc/cudaFree, or whose device
+ * footprint must be fixed when the library is loaded).
+ *   n        number of disks, 1 <= n <= 65536 (larger n returns BD_ERR_ARG).
+ *   xy       DEVICE pointer, 2n doubles (x0, y0, x1, y1, ...), caller-owned.
+ *   species  DEVICE pointer, n bytes, 0 or non-zero (= species 1).
+ *   alpha    HOST pointer, 4 doubles A[s_i][s_j] as in bd_params.alpha.
+ *   F        DEVICE pointer, 2n doubles: receives F_i = sum_j A (r_i - r_j)/|r_ij|^3.
+ *   stream   cudaStream_t to queue on (NULL = legacy default stream); the call
+ *            returns once the work is queued.
+ * Allocates nothing: its scratch (about 9 MB) is a static device array that
+ * every GPU loading the library holds until exit.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture.  Every call shares
+ * the array: calls whose work overlaps on the GPU race and must be serialised.
+ * Errors: BD_ERR_ARG (n out of range, NULL pointer), BD_ERR_CUDA. */
+int bd_forces_noalloc(int32_t n, const double *xy, const uint8_t *species, const double alpha[4],
+                      double *F, void *stream);
+
 /* Release the handle and its device memory (NULL is ignored). */
 void bd_free(bd_handle *h);
 

@@ -64,6 +64,8 @@ SIGNATURES = [
     ("bd_last_launch_count", ctypes.c_int64, [_P]),
     ("bd_triangulate", ctypes.c_int, [ctypes.c_int32, _P, ctypes.c_double, _P, _P,
                                       ctypes.POINTER(ctypes.c_int32)]),
+    ("bd_forces_noalloc", ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_double),
+                                         _P, _P]),
     ("bd_free", None, [_P]),
     ("bd_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -219,3 +221,12 @@ def triangulate(xy, L):
     _check(load().bd_triangulate(n, _ptr(xy), float(L), _ptr(grid), _ptr(tri), ctypes.byref(nt)),
            "bd_triangulate")
     return tri[: nt.value], grid
+
+
+def forces_noalloc(n, xy_dev_ptr, species_dev_ptr, alpha, F_dev_ptr, stream=None):
+    """bd_forces_noalloc on caller-owned device buffers (raw pointers)."""
+    A = (ctypes.c_double * 4)(*[float(v) for v in alpha])
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(load().bd_forces_noalloc(int(n), ctypes.c_void_p(int(xy_dev_ptr)),
+                                    ctypes.c_void_p(int(species_dev_ptr)), A,
+                                    ctypes.c_void_p(int(F_dev_ptr)), st), "bd_forces_noalloc")
