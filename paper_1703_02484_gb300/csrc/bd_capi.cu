@@ -98,14 +98,29 @@ int pick_nchunk(const BdConst &c) {
     int want = std::max(1, (4 * sms) / std::max(1, blocks));
     return std::max(1, std::min(want, c.ntiles));
   }
-  // force blocks resident per SM (128 threads, register-limited)
-  const int per_sm = 8;
-  long slots = (long)sms * per_sm;
-  // at least two full waves of (i block, j chunk) pairs, rounded to whole waves
-  long want = (2 * slots + c.n_iblocks - 1) / c.n_iblocks;
-  long waves = (c.n_iblocks * want + slots - 1) / slots;
-  want = (waves * slots) / c.n_iblocks;
-  return (int)std::max(1L, std::min<long>(want, c.ntiles));
+  // resident force blocks per SM from the occupancy calculator; choose the
+  // number of j chunks so the (i block, j chunk) grid fills whole waves
+  int per_sm = bd_force_blocks_per_sm();
+  if (per_sm < 1) per_sm = 1;
+  const long slots = (long)sms * per_sm;
+  const long ib = std::max(1, c.n_iblocks);
+  int best = 1;
+  double best_eff = -1.0;
+  for (int ch = 1; ch <= std::min(c.ntiles, 64); ++ch) {
+    long ctas = ib * ch;
+    long waves = (ctas + slots - 1) / slots;
+    // useful fraction of the last wave, times the tile balance across chunks
+    double fill = (double)ctas / (double)(waves * slots);
+    int tiles_max = (c.ntiles + ch - 1) / ch;
+    double bal = ((double)c.ntiles / ch) / tiles_max;
+    // prefer at least two waves of blocks per SM slot for latency hiding
+    double eff = fill * bal * (waves >= 2 ? 1.0 : 0.9);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = ch;
+    }
+  }
+  return best;
 }
 
 }  // namespace

@@ -86,5 +86,6 @@ cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t 
 cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, cudaStream_t s);
 cudaError_t bd_launch_dt(const BdDev &d, const BdConst &c, int mode, cudaStream_t s, int grid, int block);
 int bd_dt_grid(int *grid, int *block);
+int bd_force_blocks_per_sm();
 cudaError_t bd_launch_work_copy(const BdDev &d, const BdConst &c, cudaStream_t s);
 cudaError_t bd_launch_force_sum(const BdDev &d, const BdConst &c, double2 *out, cudaStream_t s);

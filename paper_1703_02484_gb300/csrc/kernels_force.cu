@@ -285,6 +285,13 @@ __global__ void k_work_copy(BdDev d, BdConst c) {
   d.work[i] = split(d.pos[i]);
 }
 
+int bd_force_blocks_per_sm() {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force_long_f32, BD_FT, 0) != cudaSuccess)
+    return 0;
+  return per;
+}
+
 cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t s) {
   if (c.precision == 0) {
     k_force_long_f32<<<dim3(c.n_iblocks, c.nchunk), BD_FT, 0, s>>>(d, c);
