@@ -164,6 +164,15 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta);
  * in external order.  Errors: BD_ERR_ARG, BD_ERR_CUDA. */
 int bd_compute_forces(bd_handle *h, double *F);
 
+/* Short-range law only: the Verlet lists as last built (Sec. 2.1): disks
+ * within r_cut + skin of each disk at the last rebuild, decided in FP64 as
+ * (x_i - x_j)^2 + (y_i - y_j)^2 < (r_cut + skin)^2.  counts receives n ints;
+ * idx receives, for disk i, its first min(counts[i], max_per) neighbours in
+ * ascending external index at idx[i*max_per ...].  Lists are built on the
+ * first force evaluation (bd_compute_forces or the first step).
+ * Errors: BD_ERR_ARG, BD_ERR_UNSUPPORTED (long-range handle), BD_ERR_CUDA. */
+int bd_get_neighbors(bd_handle *h, int32_t max_per, int32_t *counts, int32_t *idx);
+
 /* Position-grid step q (coordinates are multiples of q) and box side L. */
 int bd_get_geometry(bd_handle *h, double *q, double *L);
 

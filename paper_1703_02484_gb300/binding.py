@@ -66,6 +66,7 @@ SIGNATURES = [
                                       ctypes.POINTER(ctypes.c_int32)]),
     ("bd_forces_noalloc", ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_double),
                                          _P, _P]),
+    ("bd_get_neighbors", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     ("bd_free", None, [_P]),
     ("bd_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -205,6 +206,14 @@ class System:
         _check(load().bd_force_timing(self.h, int(enable), int(reset), ctypes.byref(ms),
                                       ctypes.byref(k)), "bd_force_timing")
         return ms.value, k.value
+
+    def neighbors(self, max_per=64):
+        n = self.n
+        counts = np.zeros(n, dtype=np.int32)
+        idx = np.zeros((n, max_per), dtype=np.int32)
+        _check(load().bd_get_neighbors(self.h, int(max_per), _ptr(counts), _ptr(idx)),
+               "bd_get_neighbors")
+        return [idx[i, : counts[i]].copy() for i in range(n)]
 
     def last_launch_count(self):
         return int(load().bd_last_launch_count(self.h))

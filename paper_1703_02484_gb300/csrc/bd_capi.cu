@@ -81,7 +81,10 @@ int validate(const bd_params *p) {
   for (int k = 0; k < 4; ++k)
     if (!isfinite(p->alpha[k])) return BD_ERR_ARG;
   if (p->max_corr_iters < 1 || p->max_flip_rounds < 1) return BD_ERR_ARG;
-  if (p->law == BD_LAW_SHORT) return BD_ERR_UNSUPPORTED;
+  if (p->law == BD_LAW_SHORT) {
+    if (!(p->r_cut > 2.0 * p->a) || !(p->skin > 0) || !(p->eps >= 0) || !(p->kappa >= 0)) return BD_ERR_ARG;
+    if (p->precision != 0) return BD_ERR_UNSUPPORTED;
+  }
   return BD_OK;
 }
 
@@ -352,6 +355,9 @@ int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_i
   c.kappa = p.kappa;
   c.r_cut = p.r_cut;
   c.skin = p.skin;
+  c.rl2 = (p.r_cut + p.skin) * (p.r_cut + p.skin);
+  c.ncell = std::max(1, std::min(1 << 14, (int)floor(L / (p.r_cut + p.skin))));
+  c.cell_size = L / c.ncell;
   c.D = p.D;
   c.Dr = p.Dr;
   c.v0 = p.v0;
@@ -376,7 +382,7 @@ int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_i
     if (e != cudaSuccess) goto cuda_error; \
   } while (0)
   {
-    c.nchunk = pick_nchunk(c);
+    c.nchunk = p.law == BD_LAW_SHORT ? 1 : pick_nchunk(c);
     BD_TRY(dalloc(h, &d.pos, nv));
     BD_TRY(dalloc(h, &d.prev, nv));
     BD_TRY(dalloc(h, &d.pos0, nv));
@@ -398,6 +404,18 @@ int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_i
     BD_TRY(dalloc(h, &d.tile_species, tile_sp.size()));
     BD_TRY(dalloc(h, &d.fpart, (size_t)c.nchunk * np));
     BD_TRY(dalloc(h, &d.ctl, 1));
+    if (p.law == BD_LAW_SHORT) {
+      const size_t nc2 = (size_t)c.ncell * c.ncell;
+      BD_TRY(dalloc(h, &d.vl_idx, (size_t)BD_VL_MAX * np));
+      BD_TRY(dalloc(h, &d.vl_cnt, (size_t)np));
+      BD_TRY(dalloc(h, &d.vl_ref, (size_t)np));
+      BD_TRY(dalloc(h, &d.cell_count, nc2));
+      BD_TRY(dalloc(h, &d.cell_start, nc2));
+      BD_TRY(dalloc(h, &d.cell_cursor, nc2));
+      BD_TRY(dalloc(h, &d.cell_idx, (size_t)np));
+      BD_TRY(dalloc(h, &d.cell_of, (size_t)np));
+      BD_TRY(dalloc(h, &d.scan_sums, (nc2 + 511) / 512 + 1));
+    }
     BD_TRY(dalloc(h, &h->d_fsum, (size_t)np));
     BD_TRY(cudaMallocHost((void **)&h->h_ctl, sizeof(BdCtl)));
 
@@ -434,6 +452,13 @@ int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_i
     BD_TRY(cudaMemcpyAsync(d.tile_species, tile_sp.data(), tile_sp.size(), cudaMemcpyHostToDevice, st));
     BD_TRY(cudaMemsetAsync(d.fpart, 0, (size_t)c.nchunk * np * sizeof(double2), st));
     BD_TRY(cudaMemsetAsync(d.ctl, 0, sizeof(BdCtl), st));
+    if (p.law == BD_LAW_SHORT) {
+      // reference positions far away: the first force evaluation builds the lists
+      std::vector<double2> far(np, make_double2(1e30, 1e30));
+      BD_TRY(cudaMemcpyAsync(d.vl_ref, far.data(), np * sizeof(double2), cudaMemcpyHostToDevice, st));
+      BD_TRY(cudaMemsetAsync(d.vl_cnt, 0, np * sizeof(int), st));
+      BD_TRY(cudaStreamSynchronize(st));
+    }
     BD_TRY(bd_launch_work_copy(d, c, st));
     BD_TRY(cudaStreamSynchronize(st));
     if (bd_dt_grid(&h->dt_grid, &h->dt_block) != 0) {
@@ -493,6 +518,11 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
       }
       ++launches;
     }
+    if (h->c.law == BD_LAW_SHORT) {
+      e = bd_launch_force_short(h->d, h->c, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+      launches += bd_short_launches();
+    }
     e = bd_launch_integrate(h->d, h->c, h->step + s, st);
     if (e != cudaSuccess) return cuda_fail(e);
     e = bd_launch_dt(h->d, h->c, 0, st, h->dt_grid, h->dt_block);
@@ -520,6 +550,7 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
     stats->repair_flips = k.st_repair_flips;
     stats->inverted = k.st_inverted;
     stats->max_corr_iters = k.st_max_corr_iters;
+    stats->verlet_rebuilds = (int32_t)k.st_verlet_rebuilds;
     stats->rejected = k.status != 0;
     double mo;
     unsigned long long bits = k.st_max_overlap_bits;
@@ -636,16 +667,48 @@ int bd_compute_forces(bd_handle *h, double *F) {
     memset(F, 0, sizeof(double) * 2 * (size_t)n);
     return BD_OK;
   }
-  cudaError_t e = bd_launch_force_long(h->d, h->c, st);
+  cudaError_t e = h->c.law == BD_LAW_SHORT ? bd_launch_force_short(h->d, h->c, st)
+                                           : bd_launch_force_long(h->d, h->c, st);
   if (e == cudaSuccess) e = bd_launch_force_sum(h->d, h->c, h->d_fsum, st);
   std::vector<double2> f(np);
   if (e == cudaSuccess) e = cudaMemcpyAsync(f.data(), h->d_fsum, np * sizeof(double2), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e);
+  int rc = read_ctl(h);
+  if (rc) return rc;
+  if (h->h_ctl->status) {
+    int s = h->h_ctl->status;
+    cudaMemsetAsync(&h->d.ctl->status, 0, sizeof(int), st);
+    cudaStreamSynchronize(st);
+    return s;
+  }
   for (int i = 0; i < n; ++i) {
     double2 v = f[h->int_of_ext[i]];
     F[2 * i] = v.x;
     F[2 * i + 1] = v.y;
+  }
+  return BD_OK;
+}
+
+int bd_get_neighbors(bd_handle *h, int32_t max_per, int32_t *counts, int32_t *idx) {
+  if (!h || !counts || max_per < 0 || (max_per > 0 && !idx)) return BD_ERR_ARG;
+  if (h->c.law != BD_LAW_SHORT) return BD_ERR_UNSUPPORTED;
+  const int np = h->np, n = h->n;
+  std::vector<int> cnt(np), vi((size_t)BD_VL_MAX * np);
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaMemcpyAsync(cnt.data(), h->d.vl_cnt, np * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(vi.data(), h->d.vl_idx, vi.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  for (int x = 0; x < n; ++x) {
+    int i = h->int_of_ext[x];
+    int m = cnt[i];
+    counts[x] = m;
+    std::vector<int> lst(m);
+    for (int t = 0; t < m; ++t) lst[t] = h->ext_of_int[vi[(size_t)t * np + i]];
+    std::sort(lst.begin(), lst.end());
+    for (int t = 0; t < m && t < max_per; ++t) idx[(size_t)x * max_per + t] = lst[t];
   }
   return BD_OK;
 }

@@ -11,6 +11,10 @@
 #define BD_IPT 4             // i disks per thread
 #define BD_IB (BD_FT * BD_IPT)  // i disks per force block
 
+// Verlet list capacity per disk (hard disks of radius a have at most ~40
+// neighbours within 5.6a even at close packing)
+#define BD_VL_MAX 64
+
 // triangle flag bits stored in tv[t].w
 #define BD_TRI_INVERTED 1
 #define BD_TRI_DIRTY 2
@@ -35,7 +39,8 @@ struct BdCtl {
   int st_rejected;
   unsigned long long st_max_overlap_bits;   // double bits of the deepest overlap (monotone for >= 0)
   int st_fail_phase;
-  int pad1;
+  int vl_need;                     // Verlet rebuild requested for this step
+  long long st_verlet_rebuilds;
 };
 
 // counter slots within BdCtl::cnt[phase % 4]
@@ -59,10 +64,10 @@ struct BdDev {
   float2 *iorigin;         // per i-block origin (integers)
   uint8_t *tile_species;   // species of each j tile
   double2 *fpart;          // [nchunk][np] partial forces
-  // short range
-  int *vl_start, *vl_idx, *vl_cnt;
+  // short range: Verlet lists (column-major ELL) and the cell grid
+  int *vl_idx, *vl_cnt;
   double2 *vl_ref;
-  int *cell_start, *cell_idx;
+  int *cell_count, *cell_start, *cell_cursor, *cell_idx, *cell_of, *scan_sums;
   BdCtl *ctl;
 };
 
@@ -74,6 +79,9 @@ struct BdConst {
   float alpha[4];
   double alpha_d[4];
   double eps, kappa, r_cut, skin;
+  double rl2;              // (r_cut + skin)^2
+  double cell_size;
+  int ncell;               // cells per side
   double D, Dr, v0, dt;
   double amp, amp_r;       // translational / rotational noise amplitude
   uint64_t seed;
@@ -88,4 +96,6 @@ cudaError_t bd_launch_dt(const BdDev &d, const BdConst &c, int mode, cudaStream_
 int bd_dt_grid(int *grid, int *block);
 int bd_force_blocks_per_sm();
 cudaError_t bd_launch_work_copy(const BdDev &d, const BdConst &c, cudaStream_t s);
+cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t s);
+int bd_short_launches();
 cudaError_t bd_launch_force_sum(const BdDev &d, const BdConst &c, double2 *out, cudaStream_t s);

@@ -1,0 +1,258 @@
+// Short-range force over Verlet lists (Sec. 2.1, Sec. 5).
+//
+// Pair law: a WCA core plus an attractive Yukawa tail, truncated (not
+// shifted) at r_cut as in Eq. (displacement) / Fig. "cutoff":
+//   U = 4 eps[(s/r)^12 - (s/r)^6] + eps   (r < 2^(1/6) s),  s = 2a
+//     - eps (s/r) exp(-kappa (r - s)),
+//   F_i = sum_j -U'(r_ij) (r_i - r_j)/r_ij   for r_ij < r_cut.
+//
+// Lists: every disk keeps the disks within r_cut + skin of it, decided in
+// FP64 as (x_i - x_j)^2 + (y_i - y_j)^2 < (r_cut + skin)^2 with two products
+// and one sum, each rounded once (the same expression the oracle evaluates).
+// Lists are rebuilt when some disk has moved more than skin/2 since the last
+// build (then no pair can have come within r_cut unseen); the test and the
+// whole rebuild run on the device behind a flag, so a step never waits for the
+// host.  Rebuild: cell grid of side >= r_cut + skin (count, two-level scan,
+// scatter), then one thread per disk scans its 3x3 cells, sorts its list by
+// disk index and writes it column-major (entry k of disk i at k*np + i) so the
+// force kernel's loads are coalesced.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "bd_internal.h"
+
+#define BD_SCAN_B 512
+
+namespace {
+
+__device__ __forceinline__ int failed(const BdCtl *ctl) { return *(volatile const int *)&ctl->status; }
+__device__ __forceinline__ int need(const BdCtl *ctl) { return *(volatile const int *)&ctl->vl_need; }
+
+__device__ __forceinline__ int cell_of(double2 p, const BdConst &c) {
+  int cx = (int)(p.x / c.cell_size);
+  int cy = (int)(p.y / c.cell_size);
+  cx = cx < 0 ? 0 : (cx >= c.ncell ? c.ncell - 1 : cx);
+  cy = cy < 0 ? 0 : (cy >= c.ncell ? c.ncell - 1 : cy);
+  return cy * c.ncell + cx;
+}
+
+}  // namespace
+
+// 1. displacement trigger: some disk moved more than skin/2 since the build
+__global__ void k_vl_check(BdDev d, BdConst c) {
+  if (failed(d.ctl)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool hit = false;
+  if (i < c.np && d.ext_id[i] >= 0) {
+    double2 p = d.pos[i], r = d.vl_ref[i];
+    double dx = p.x - r.x, dy = p.y - r.y;
+    hit = dx * dx + dy * dy > 0.25 * c.skin * c.skin;
+  }
+  if (__any_sync(0xffffffffu, hit) && (threadIdx.x & 31) == 0) atomicExch(&d.ctl->vl_need, 1);
+}
+
+// 2. clear cell counts
+__global__ void k_vl_clear(BdDev d, BdConst c) {
+  if (failed(d.ctl) || !need(d.ctl)) return;
+  const int nc2 = c.ncell * c.ncell;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nc2; k += gridDim.x * blockDim.x)
+    d.cell_count[k] = 0;
+}
+
+// 3. count disks per cell
+__global__ void k_vl_count(BdDev d, BdConst c) {
+  if (failed(d.ctl) || !need(d.ctl)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.np) return;
+  if (d.ext_id[i] < 0) {
+    d.cell_of[i] = -1;
+    return;
+  }
+  int k = cell_of(d.pos[i], c);
+  d.cell_of[i] = k;
+  atomicAdd(&d.cell_count[k], 1);
+}
+
+// 4a. exclusive scan within blocks of BD_SCAN_B cells
+__global__ void __launch_bounds__(BD_SCAN_B) k_scan_blocks(BdDev d, BdConst c) {
+  if (failed(d.ctl) || !need(d.ctl)) return;
+  __shared__ int s[BD_SCAN_B];
+  const int nc2 = c.ncell * c.ncell;
+  int k = blockIdx.x * BD_SCAN_B + threadIdx.x;
+  int v = k < nc2 ? d.cell_count[k] : 0;
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int off = 1; off < BD_SCAN_B; off <<= 1) {
+    int t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+    __syncthreads();
+    s[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (k < nc2) d.cell_start[k] = s[threadIdx.x] - v;
+  if (threadIdx.x == BD_SCAN_B - 1) d.scan_sums[blockIdx.x] = s[threadIdx.x];
+}
+
+// 4b. exclusive scan of the block sums (one block, sequential chunks)
+__global__ void __launch_bounds__(BD_SCAN_B) k_scan_top(BdDev d, BdConst c, int nblocks) {
+  if (failed(d.ctl) || !need(d.ctl)) return;
+  __shared__ int s[BD_SCAN_B];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nblocks; base += BD_SCAN_B) {
+    int k = base + threadIdx.x;
+    int v = k < nblocks ? d.scan_sums[k] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < BD_SCAN_B; off <<= 1) {
+      int t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (k < nblocks) d.scan_sums[k] = carry + s[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == BD_SCAN_B - 1) carry += s[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// 4c. add block offsets; reset the scatter cursors
+__global__ void __launch_bounds__(BD_SCAN_B) k_scan_add(BdDev d, BdConst c) {
+  if (failed(d.ctl) || !need(d.ctl)) return;
+  const int nc2 = c.ncell * c.ncell;
+  int k = blockIdx.x * BD_SCAN_B + threadIdx.x;
+  if (k < nc2) {
+    int v = d.cell_start[k] + d.scan_sums[blockIdx.x];
+    d.cell_start[k] = v;
+    d.cell_cursor[k] = v;
+  }
+}
+
+// 5. scatter disk ids into cell order
+__global__ void k_vl_scatter(BdDev d, BdConst c) {
+  if (failed(d.ctl) || !need(d.ctl)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.np) return;
+  int k = d.cell_of[i];
+  if (k < 0) return;
+  int slot = atomicAdd(&d.cell_cursor[k], 1);
+  d.cell_idx[slot] = i;
+}
+
+// 6. per-disk neighbour lists (sorted), reference positions
+__global__ void k_vl_build(BdDev d, BdConst c) {
+  if (failed(d.ctl) || !need(d.ctl)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.np) return;
+  if (d.ext_id[i] < 0) {
+    d.vl_cnt[i] = 0;
+    return;
+  }
+  const double2 p = d.pos[i];
+  d.vl_ref[i] = p;
+  const int k = d.cell_of[i];
+  const int cx = k % c.ncell, cy = k / c.ncell;
+  int buf[BD_VL_MAX];
+  int m = 0;
+  bool over = false;
+  for (int gy = cy - 1; gy <= cy + 1; ++gy) {
+    if (gy < 0 || gy >= c.ncell) continue;
+    for (int gx = cx - 1; gx <= cx + 1; ++gx) {
+      if (gx < 0 || gx >= c.ncell) continue;
+      int cc = gy * c.ncell + gx;
+      int b = d.cell_start[cc], e = b + d.cell_count[cc];
+      for (int s = b; s < e; ++s) {
+        int j = d.cell_idx[s];
+        if (j == i) continue;
+        double2 q = d.pos[j];
+        double dx = __dsub_rn(p.x, q.x), dy = __dsub_rn(p.y, q.y);
+        double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+        if (r2 < c.rl2) {
+          if (m < BD_VL_MAX) {
+            // insertion in sorted position
+            int t = m++;
+            while (t > 0 && buf[t - 1] > j) {
+              buf[t] = buf[t - 1];
+              --t;
+            }
+            buf[t] = j;
+          } else {
+            over = true;
+          }
+        }
+      }
+    }
+  }
+  for (int t = 0; t < m; ++t) d.vl_idx[(size_t)t * c.np + i] = buf[t];
+  d.vl_cnt[i] = m;
+  if (over) atomicCAS(&d.ctl->status, 0, BD_ERR_UNSUPPORTED);
+}
+
+// 7. short-range force over the lists; clears the rebuild flag
+__global__ void k_force_verlet(BdDev d, BdConst c) {
+  if (failed(d.ctl)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    if (need(d.ctl)) {
+      d.ctl->vl_need = 0;
+      d.ctl->st_verlet_rebuilds += 1;
+    }
+  }
+  if (i >= c.np) return;
+  if (d.ext_id[i] < 0) return;
+  const float4 wi = d.work[i];
+  const int m = d.vl_cnt[i];
+  const float rc2 = (float)(c.r_cut * c.r_cut);
+  const float sg = (float)c.sigma, eps = (float)c.eps, kap = (float)c.kappa;
+  const float rwca2 = (float)(1.2599210498948732 * c.sigma * c.sigma);  // (2^(1/6) s)^2
+  float fx = 0.f, fy = 0.f;
+  for (int t = 0; t < m; ++t) {
+    int j = d.vl_idx[(size_t)t * c.np + i];
+    float4 wj = d.work[j];
+    // r_i - r_j from the (hi, lo) pairs: exact for near pairs
+    float dx = __fadd_rn(__fsub_rn(wi.x, wj.x), __fsub_rn(wi.z, wj.z));
+    float dy = __fadd_rn(__fsub_rn(wi.y, wj.y), __fsub_rn(wi.w, wj.w));
+    float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    if (fabsf(r2 - rc2) < 1e-5f * rc2) {
+      // at the cut-off the force jumps: decide as the FP64 reference does
+      double2 pi = d.pos[i], pj = d.pos[j];
+      double ex = __dsub_rn(pi.x, pj.x), ey = __dsub_rn(pi.y, pj.y);
+      if (!(sqrt(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey))) < c.r_cut)) continue;
+    } else if (r2 >= rc2) {
+      continue;
+    }
+    float r = sqrtf(r2);
+    float ir = 1.0f / r;
+    float mag = -eps * sg * expf(-kap * (r - sg)) * (ir * ir + kap * ir);
+    if (r2 < rwca2) {
+      float s2 = sg * sg / r2;
+      float s6 = s2 * s2 * s2;
+      mag += 24.0f * eps * ir * (2.0f * s6 * s6 - s6);
+    }
+    // -U'(r) along (r_i - r_j)/r
+    fx = fmaf(mag * ir, dx, fx);
+    fy = fmaf(mag * ir, dy, fy);
+  }
+  d.fpart[i] = make_double2((double)fx, (double)fy);
+}
+
+cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t s) {
+  const int b = 256;
+  const int gn = (c.np + b - 1) / b;
+  const int nc2 = c.ncell * c.ncell;
+  const int nsb = (nc2 + BD_SCAN_B - 1) / BD_SCAN_B;
+  k_vl_check<<<gn, b, 0, s>>>(d, c);
+  k_vl_clear<<<(nc2 + b - 1) / b, b, 0, s>>>(d, c);
+  k_vl_count<<<gn, b, 0, s>>>(d, c);
+  k_scan_blocks<<<nsb, BD_SCAN_B, 0, s>>>(d, c);
+  k_scan_top<<<1, BD_SCAN_B, 0, s>>>(d, c, nsb);
+  k_scan_add<<<nsb, BD_SCAN_B, 0, s>>>(d, c);
+  k_vl_scatter<<<gn, b, 0, s>>>(d, c);
+  k_vl_build<<<gn, 128, 0, s>>>(d, c);
+  k_force_verlet<<<gn, b, 0, s>>>(d, c);
+  return cudaGetLastError();
+}
+
+int bd_short_launches() { return 9; }

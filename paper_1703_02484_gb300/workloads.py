@@ -169,9 +169,9 @@ def _lattice(n: int, L: float, a: float, rng: np.random.Generator):
     jr = 0.45 * (s - 2.0 * a)
     rr = jr * np.sqrt(rng.uniform(0.0, 1.0, size=n))
     ph = rng.uniform(0.0, 2.0 * math.pi, size=n)
-    pts[:, 0] += rr * np.cos(ph)
-    pts[:, 1] += rr * np.sin(ph)
-    np.clip(pts, lo, hi, out=pts)
+    moved = pts + np.stack([rr * np.cos(ph), rr * np.sin(ph)], axis=1)
+    inside = np.all((moved >= lo) & (moved <= hi), axis=1)
+    pts[inside] = moved[inside]       # a site whose jitter leaves the box keeps its place
     return pts
 
 
@@ -208,13 +208,16 @@ def replica_table(R: int = 256, seed: int = 3, n_lo: int = 512, n_hi: int = 6553
 
 
 def near_contact_state(n: int, L: float, a: float, seed: int, gap: float = 0.02,
-                       frac: float = 0.3):
+                       frac: float = 0.3, rho: float | None = None):
     """RSA start in which a fraction of disks is moved next to a neighbour,
     leaving a surface gap in (0, gap]: a start with many near-contacts, so the
     first step already has overlaps to correct (a stand-in for a state taken
     later in a run)."""
     rng = np.random.default_rng(np.random.PCG64([seed, 0x4E454152]))
-    xy = _rsa(n, L, a, rng)
+    if rho is not None and rho > 0.35:
+        xy = _lattice(n, L, a, rng)
+    else:
+        xy = _rsa(n, L, a, rng)
     cs = 6.0 * a
     nc = max(1, int(L // cs))
     cs = L / nc

@@ -1,0 +1,109 @@
+"""GPU parity of the short-range path (Verlet lists + WCA/Yukawa force)."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1703_02484_gb300 as bd  # noqa: E402
+from paper_1703_02484_gb300 import workloads  # noqa: E402
+from oracle import forces as oforces  # noqa: E402
+from oracle import geometry, verlet  # noqa: E402
+from oracle import step as ostep  # noqa: E402
+from scipy.spatial import cKDTree  # noqa: E402
+
+CFG = workloads.CONFIGS["c3"]
+
+
+def stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def rel_err(F, ref):
+    scale = math.sqrt(float(np.mean(np.sum(ref ** 2, axis=1))))
+    return float(np.max(np.linalg.norm(F - ref, axis=1))) / scale
+
+
+def system(n, xy=None, skin=None, seed=2):
+    L = workloads.box_side(n, CFG.rho)
+    if xy is None:
+        xy = workloads.initial_positions(n, L, 1.0, CFG.rho, seed)
+    _, sp, th = workloads.initial_state(CFG, n=n)
+    p = bd.params_from_config(CFG, n=n)
+    if skin is not None:
+        p.skin = skin
+    return bd.System(p, xy, sp, th, stream=stream()), L, xy, sp, th
+
+
+@pytest.mark.parametrize("n", [3000, 20000])
+def test_verlet_lists_and_forces_match_oracle(n):
+    s, L, xy, sp, th = system(n)
+    F = s.forces()                          # first evaluation builds the lists
+    grid = s.state(want_tri=False)["xy"]
+    lists = s.neighbors()
+    ref_lists = verlet.build(grid, CFG.r_cut, CFG.skin)
+    for i in range(n):
+        assert np.array_equal(lists[i], ref_lists[i]), i
+    ref = oforces.short_range(grid, CFG.eps, CFG.kappa, 2.0, CFG.r_cut)
+    assert rel_err(F, ref) <= 1e-5
+
+
+def test_rebuild_trigger_and_lists_after_rebuild():
+    n = 4000
+    s, L, xy, sp, th = system(n, skin=0.04)
+    s.forces()
+    rebuilt = 0
+    for _ in range(20):
+        before = s.state(want_tri=False)["xy"]
+        st = s.step(1)
+        if st["verlet_rebuilds"]:
+            rebuilt += 1
+            lists = s.neighbors()
+            ref_lists = verlet.build(before, CFG.r_cut, 0.04)
+            for i in range(0, n, 3):
+                assert np.array_equal(lists[i], ref_lists[i])
+    assert rebuilt >= 2
+
+
+def test_short_one_step_parity():
+    n = 6000
+    L = workloads.box_side(n, CFG.rho)
+    xy = workloads.near_contact_state(n, L, 1.0, seed=5, rho=CFG.rho)
+    s, L, _, sp, th = system(n, xy=xy)
+    s.step(1)
+    out = s.state()
+    op = ostep.Params(L=L, a=1.0, law=CFG.law, eps=CFG.eps, kappa=CFG.kappa, r_cut=CFG.r_cut,
+                      D=CFG.D, Dr=CFG.Dr, v0=CFG.v0, dt=CFG.dt, seed=CFG.seed)
+    ref = ostep.step(xy, th, sp, 0, op)
+    assert ref["corr_iters"] >= 1
+    assert np.max(np.abs(out["xy"] - ref["xy"])) <= 1e-5
+    assert np.array_equal(geometry.edges(out["tri"]), geometry.edges(ref["tris"]))
+
+
+def test_full_size_c3_forces_sampled_and_steps():
+    n = CFG.n
+    s, L, xy, sp, th = system(n)
+    F = s.forces()
+    grid = s.state(want_tri=False)["xy"]
+    rng = np.random.default_rng(1)
+    idx = rng.choice(n, 2000, replace=False)
+    tree = cKDTree(grid)
+    pi, pj = [], []
+    for i in idx:
+        for j in tree.query_ball_point(grid[i], CFG.r_cut * (1 + 1e-9)):
+            if j != i:
+                pi.append(i)
+                pj.append(j)
+    ref = oforces.short_range_pairs(grid, np.array(pi), np.array(pj), CFG.eps, CFG.kappa, 2.0,
+                                    CFG.r_cut)[idx]
+    assert rel_err(F[idx], ref) <= 1e-5
+    st = s.step(20)
+    assert st["steps_done"] == 20
+    out = s.state()
+    assert len(cKDTree(out["xy"]).query_pairs(2.0 * (1 - 1e-12))) == 0
+    assert np.array_equal(geometry.edges(out["tri"]), geometry.edges(geometry.delaunay(out["xy"], L)))
