@@ -96,8 +96,13 @@ typedef struct bd_step_stats {
   int32_t max_corr_iters;   /* largest number of passes in one step */
   int32_t rejected;         /* 1 if the call stopped at a rejected step */
   int32_t verlet_rebuilds;  /* short range: neighbour-list rebuilds */
-  int32_t pad;
+  int32_t fail_phase;       /* why a step was undone: 0 none, 1 a pair passed through each other
+                               (Sec. 4.3), 2 an inverted triangle had no repair flip, 3 repair
+                               rounds exhausted, 4 flip rounds exhausted, 5 correction passes
+                               exhausted */
   double max_overlap;       /* deepest overlap sigma - r seen */
+  int32_t fail_item;        /* internal id of an offending triangle or edge (diagnostic) */
+  int32_t fail_count;       /* inverted triangles or reversed edges at the failure */
 } bd_step_stats;
 
 typedef struct bd_handle bd_handle;
@@ -141,10 +146,10 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats);
  *   xy       2n doubles, external disk order.
  *   theta    n floats.   species  n bytes.
  *   tri      3*n_tri ints: the current Delaunay triangulation of the disks
- *            plus four corner points (ids n..n+3 at (-C,-C), (2C,-C),
- *            (2C,2C), (-C,2C), C = ceil(L)), counter-clockwise; the buffer
- *            must hold 3*(2n+2) ints.
- *   n_tri    receives the number of triangles (2n+2).
+ *            plus the ghost points of bd_ghost_points (ids n, n+1, ...),
+ *            counter-clockwise; the buffer must hold 3*(2(n+G)-6) ints where
+ *            G is the ghost count (bd_ghost_points).
+ *   n_tri    receives the number of triangles, 2(n+G)-6.
  *   step     receives the index of the next step.
  * Errors: BD_ERR_ARG (h == NULL), BD_ERR_CUDA. */
 int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32_t *tri,
@@ -184,16 +189,32 @@ int bd_force_timing(bd_handle *h, int enable, int reset, double *total_ms, int64
 /* Number of kernel launches queued by the last bd_step call. */
 int64_t bd_last_launch_count(bd_handle *h);
 
+/* Host only: the fixed ghost points that close the triangulation of a box of
+ * side L for disks of radius a.  The paper's periodic box needs none; with
+ * walls they replace the torus and keep the triangles at the walls well
+ * shaped.  With C = ceil(L), W = S = ceil(2a) and
+ * off(k, s) = ((7919k + 104729s) mod 257)/1024, in this order:
+ *   four far corners (-F,-F), (G,-F), (G,G), (-F,G), F = C + 3W, G = 2C + 3W;
+ *   bottom row  (x, y) = (-W + kS + off(k,0), -W - off(k,4)),
+ *   top row     (-W + kS + off(k,1), C + W + off(k,5)), while -W + kS <= C + W;
+ *   left column (-W - off(k,6), -W + S/2 + kS + off(k,2)),
+ *   right column (C + W + off(k,7), -W + S/2 + kS + off(k,3)), while the
+ *   un-offset y < C + W.
+ *   xy     NULL to query the count, else 2*(*count) doubles to fill.
+ *   count  in: capacity (points) when xy != NULL; out: number of points.
+ * Errors: BD_ERR_ARG. */
+int bd_ghost_points(double L, double a, double *xy, int32_t *count);
+
 /* Host only (no GPU needed): the Delaunay triangulation bd_init builds
- * (Sec. 4.1), for n centres in a box of side L plus the four corner points
- * (ids n..n+3 at (-C,-C), (2C,-C), (2C,2C), (-C,2C), C = ceil(L)).
- *   xy         2n doubles; centres inside (-C, 2C)^2, no duplicates.
+ * (Sec. 4.1), for n centres in a box of side L (disk radius a) plus the
+ * ghost points of bd_ghost_points (ids n, n+1, ...).
+ *   xy         2n doubles; centres inside (0, L)^2, no duplicates.
  *   xy_grid    optional 2n doubles: the centres rounded to the position grid
  *              (the coordinates the triangulation is exact for).
- *   tri        3*(2n+2) ints, counter-clockwise triangles.
- *   n_tri      receives 2n+2.
- * Errors: BD_ERR_ARG, BD_ERR_TRIANGULATION (duplicate or outside point). */
-int bd_triangulate(int32_t n, const double *xy, double L, double *xy_grid, int32_t *tri,
+ *   tri        3*(2(n+G)-6) ints, counter-clockwise triangles.
+ *   n_tri      receives 2(n+G)-6.
+ * Errors: BD_ERR_ARG, BD_ERR_TRIANGULATION (duplicate point). */
+int bd_triangulate(int32_t n, const double *xy, double L, double a, double *xy_grid, int32_t *tri,
                    int32_t *n_tri);
 
 /* All-pairs long-range force for callers that cannot allocate device memory

@@ -4,12 +4,13 @@
   (`fractions.Fraction`, exact by construction), bulk work in the oracle's C
   expansion arithmetic (oracle/csrc).
 * The Delaunay triangulation (Sec. 4.1) of the disk centres together with
-  four fixed corner points far outside the box.  The paper's box is periodic
-  and its triangulation lives on a torus; with reflecting walls this build
-  closes the hull with the square of corners (-C,-C), (2C,-C), (2C,2C), (-C,2C)
-  with C = ceil(L).  Any pair of disks closer than sigma is a Delaunay edge
-  of this point set (its diametral circle is empty), so the overlap search
-  over triangulation edges still finds every overlap.
+  fixed ghost points outside the box.  The paper's box is periodic and its
+  triangulation lives on a torus; with reflecting walls this build closes the
+  hull with four far corners and a ring of points just outside the walls
+  (layout in `ghost_points`).  Any pair of disks closer than sigma is a
+  Delaunay edge of this point set (its diametral circle lies at y, x >= 0 and
+  holds no other point), so the overlap search over triangulation edges still
+  finds every overlap.
 * A brute-force Delaunay (every empty-circumcircle triangle, O(n^4)) for tiny
   inputs, which pins the builder.
 * The inverted-triangle flip predicate of Sec. 4.3, Eq. (predicate).
@@ -62,15 +63,42 @@ def incircle_exact_c(a, b, c, d):
     return _clib.lib().oracle_incircle_exact(*(float(v) for v in (*a, *b, *c, *d)))
 
 
-# ------------------------------------------------------------- corner points
+# ------------------------------------------------------------- ghost points
 
-def ghost_corners(L):
+def ghost_points(L, a=1.0):
+    """Fixed points closing the triangulation, in this order: the far corners
+    (-F,-F), (G,-F), (G,G), (-F,G) with F = C + 3W, G = 2C + 3W; then the
+    bottom row (side 0) at y = -W - off(k, 4) and the top row (side 1) at
+    y = C + W + off(k, 5), x = -W + k S + off(k, side); then the left column
+    (side 2) at x = -W - off(k, 6) and the right column (side 3) at
+    x = C + W + off(k, 7), y = -W + S/2 + k S + off(k, side); C = ceil(L),
+    W = S = ceil(2a), off(k, s) = ((7919 k + 104729 s) mod 257) / 1024."""
     C = float(math.ceil(L))
-    return np.array([[-C, -C], [2 * C, -C], [2 * C, 2 * C], [-C, 2 * C]], dtype=np.float64)
+    W = float(math.ceil(2.0 * a))
+    S = W
+    F, G = C + 3 * W, 2 * C + 3 * W
+    pts = [(-F, -F), (G, -F), (G, G), (-F, G)]
+
+    def off(k, s):
+        return ((7919 * k + 104729 * s) % 257) / 1024.0
+
+    for side in (0, 1):
+        k = 0
+        while -W + k * S <= C + W:
+            y = -W - off(k, 4 + side) if side == 0 else C + W + off(k, 4 + side)
+            pts.append((-W + k * S + off(k, side), y))
+            k += 1
+    for side in (2, 3):
+        k = 0
+        while -W + 0.5 * S + k * S < C + W:
+            x = -W - off(k, 4 + side) if side == 2 else C + W + off(k, 4 + side)
+            pts.append((x, -W + 0.5 * S + k * S + off(k, side)))
+            k += 1
+    return np.array(pts, dtype=np.float64)
 
 
-def with_ghosts(xy, L):
-    return np.concatenate([np.asarray(xy, dtype=np.float64), ghost_corners(L)], axis=0)
+def with_ghosts(xy, L, a=1.0):
+    return np.concatenate([np.asarray(xy, dtype=np.float64), ghost_points(L, a)], axis=0)
 
 
 def _insertion_order(xy):
@@ -88,21 +116,32 @@ def _insertion_order(xy):
     return np.lexsort((xkey, gy)).astype(np.int32)
 
 
-def delaunay(xy, L):
-    """Triangles (T, 3) of the Delaunay triangulation of xy plus the four
-    corner points, counter-clockwise; corner ids are n..n+3."""
+def delaunay(xy, L, a=1.0):
+    """Triangles (T, 3) of the Delaunay triangulation of the disks plus the
+    ghost points, counter-clockwise; ghost ids follow the disks (n + k for the
+    k-th point of ghost_points)."""
     xy = np.asarray(xy, dtype=np.float64)
     n = len(xy)
-    pts = with_ghosts(xy, L)
+    g = ghost_points(L, a)
+    ring = g[4:]
+    R = len(ring)
+    # the C builder wants the enclosing square last; it triangulates
+    # [disks, ring] inside it
+    pts = np.concatenate([xy, ring, g[:4]], axis=0)
     x = np.ascontiguousarray(pts[:, 0])
     y = np.ascontiguousarray(pts[:, 1])
-    order = np.ascontiguousarray(_insertion_order(xy))
-    out = np.zeros(3 * (2 * n + 8), dtype=np.int32)
-    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
-    nt = _clib.lib().oracle_delaunay(n, p(x), p(y), p(order), p(out))
+    order = np.ascontiguousarray(np.concatenate([np.arange(n, n + R, dtype=np.int32),
+                                                 _insertion_order(xy)]))
+    m = n + R
+    out = np.zeros(3 * (2 * m + 8), dtype=np.int32)
+    p = lambda arr: arr.ctypes.data_as(ctypes.c_void_p)
+    nt = _clib.lib().oracle_delaunay(m, p(x), p(y), p(order), p(out))
     if nt < 0:
         raise ValueError("oracle_delaunay failed with code %d" % nt)
-    return out[: 3 * nt].reshape(nt, 3).copy()
+    tris = out[: 3 * nt].reshape(nt, 3).copy()
+    # builder ids: disks 0..n-1, ring n..n+R-1, corners m..m+3 -> canonical
+    remap = np.concatenate([np.arange(n), n + 4 + np.arange(R), n + np.arange(4)]).astype(np.int32)
+    return remap[tris]
 
 
 def delaunay_generic(points, corner_square):

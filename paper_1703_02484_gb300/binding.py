@@ -40,12 +40,13 @@ class bd_step_stats(ctypes.Structure):
         ("overlap_pairs", ctypes.c_int64), ("flip_rounds", ctypes.c_int64),
         ("flips", ctypes.c_int64), ("repair_flips", ctypes.c_int64), ("inverted", ctypes.c_int64),
         ("max_corr_iters", ctypes.c_int32), ("rejected", ctypes.c_int32),
-        ("verlet_rebuilds", ctypes.c_int32), ("pad", ctypes.c_int32),
+        ("verlet_rebuilds", ctypes.c_int32), ("fail_phase", ctypes.c_int32),
         ("max_overlap", ctypes.c_double),
+        ("fail_item", ctypes.c_int32), ("fail_count", ctypes.c_int32),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 # entry points declared in include/bd.h: (name, restype, argtypes)
@@ -62,8 +63,10 @@ SIGNATURES = [
     ("bd_force_timing", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64)]),
     ("bd_last_launch_count", ctypes.c_int64, [_P]),
-    ("bd_triangulate", ctypes.c_int, [ctypes.c_int32, _P, ctypes.c_double, _P, _P,
+    ("bd_triangulate", ctypes.c_int, [ctypes.c_int32, _P, ctypes.c_double, ctypes.c_double, _P, _P,
                                       ctypes.POINTER(ctypes.c_int32)]),
+    ("bd_ghost_points", ctypes.c_int, [ctypes.c_double, ctypes.c_double, _P,
+                                       ctypes.POINTER(ctypes.c_int32)]),
     ("bd_forces_noalloc", ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_double),
                                          _P, _P]),
     ("bd_get_neighbors", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
@@ -155,6 +158,10 @@ class System:
                            st, ctypes.byref(h)), "bd_init")
         self.h = h
         self.params = params
+        q, L = self.geometry()
+        self.L = L
+        self.ghosts = ghost_points(L, params.a)
+        self.n_tri = 2 * (self.n + len(self.ghosts)) - 6
 
     def close(self):
         if self.h:
@@ -179,7 +186,7 @@ class System:
         xy = np.zeros((n, 2), dtype=np.float64)
         th = np.zeros(n, dtype=np.float32)
         sp = np.zeros(n, dtype=np.uint8)
-        tri = np.zeros((2 * n + 2, 3), dtype=np.int32) if want_tri else None
+        tri = np.zeros((self.n_tri, 3), dtype=np.int32) if want_tri else None
         nt = ctypes.c_int32()
         stp = ctypes.c_int64()
         _check(load().bd_get_state(self.h, _ptr(xy), _ptr(th), _ptr(sp), _ptr(tri),
@@ -219,16 +226,26 @@ class System:
         return int(load().bd_last_launch_count(self.h))
 
 
-def triangulate(xy, L):
+def ghost_points(L, a=1.0):
+    """The fixed ghost points closing the triangulation (bd_ghost_points)."""
+    cnt = ctypes.c_int32(0)
+    _check(load().bd_ghost_points(float(L), float(a), None, ctypes.byref(cnt)), "bd_ghost_points")
+    out = np.zeros((cnt.value, 2), dtype=np.float64)
+    _check(load().bd_ghost_points(float(L), float(a), _ptr(out), ctypes.byref(cnt)), "bd_ghost_points")
+    return out
+
+
+def triangulate(xy, L, a=1.0):
     """Host-side initial Delaunay triangulation (bd_triangulate): returns
-    (triangles (2n+2, 3), centres rounded to the position grid)."""
+    (triangles, centres rounded to the position grid)."""
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     n = len(xy)
-    tri = np.zeros((2 * n + 2, 3), dtype=np.int32)
+    G = len(ghost_points(L, a))
+    tri = np.zeros((2 * (n + G) - 6, 3), dtype=np.int32)
     grid = np.zeros_like(xy)
     nt = ctypes.c_int32()
-    _check(load().bd_triangulate(n, _ptr(xy), float(L), _ptr(grid), _ptr(tri), ctypes.byref(nt)),
-           "bd_triangulate")
+    _check(load().bd_triangulate(n, _ptr(xy), float(L), float(a), _ptr(grid), _ptr(tri),
+                                 ctypes.byref(nt)), "bd_triangulate")
     return tri[: nt.value], grid
 
 

@@ -17,8 +17,10 @@
 
 namespace bdhost {
 int build_delaunay(const double *X, const double *Y, const bdpred::Grid &grid,
-                   const std::vector<int> &order, const int g[4], std::vector<int> &V,
+                   const std::vector<int> &order, const std::vector<int> &g, std::vector<int> &V,
                    std::vector<int> &N);
+void make_ghosts(double L, double a, std::vector<double> &gx, std::vector<double> &gy);
+double ghost_extent(double L, double a);
 int rsa_place(int n, double lo, double hi, double dmin, uint64_t seed, std::vector<double> &xy);
 int any_overlap(int n, const double *xy, double lo, double hi, double dmin);
 uint64_t hilbert_index(uint32_t x, uint32_t y);
@@ -29,10 +31,10 @@ struct bd_handle {
   cudaStream_t stream = nullptr;
   BdDev d;
   BdConst c;
-  int n = 0, np = 0, np_i = 0, nt = 0;
+  int n = 0, np = 0, np_i = 0, nt = 0, ng = 0;
   std::vector<int> ext_of_int;  // np (-1 = empty slot)
   std::vector<int> int_of_ext;  // n
-  std::vector<double> host_pos; // (np + 4) * 2 mirror used for uploads (empty slots, corners)
+  std::vector<double> host_pos; // (np + ng) * 2 mirror used for uploads (empty slots, ghost points)
   int dt_grid = 0, dt_block = 0;
   int64_t step = 0;
   double2 *d_fsum = nullptr;
@@ -61,10 +63,10 @@ cudaError_t dalloc(bd_handle *h, T **ptr, size_t count) {
 
 size_t pad_to(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
-int grid_shift(double L) {
-  // coordinates lie in [-C, 2C] with C = ceil(L); need 2C * 2^s < 2^51
-  double C = ceil(L);
-  int e = (int)ceil(log2(2.0 * C + 1.0));
+int grid_shift(double L, double a) {
+  // every coordinate (disks and ghost points) is below E in magnitude; need E * 2^s < 2^51
+  double E = bdhost::ghost_extent(L, a);
+  int e = (int)ceil(log2(E + 1.0));
   return 51 - e;
 }
 
@@ -103,7 +105,7 @@ int pick_nchunk(const BdConst &c) {
   }
   // resident force blocks per SM from the occupancy calculator; choose the
   // number of j chunks so the (i block, j chunk) grid fills whole waves
-  int per_sm = bd_force_blocks_per_sm();
+  int per_sm = bd_force_blocks_per_sm(c.force_variant);
   if (per_sm < 1) per_sm = 1;
   const long slots = (long)sms * per_sm;
   const long ib = std::max(1, c.n_iblocks);
@@ -190,7 +192,7 @@ int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_i
   const int n = p.n;
   h->n = n;
   const double L = p.box_L > 0 ? p.box_L : sqrt((double)n * M_PI * p.a * p.a / p.area_fraction);
-  const int s = grid_shift(L);
+  const int s = grid_shift(L, p.a);
   const double q = ldexp(1.0, -s), inv_q = ldexp(1.0, s);
   const double wall_lo = ceil(p.a * inv_q) * q, wall_hi = floor((L - p.a) * inv_q) * q;
   if (!(wall_hi > wall_lo)) { delete h; return BD_ERR_ARG; }
@@ -279,28 +281,30 @@ int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_i
   std::vector<uint8_t> tile_sp(np / BD_TJ);
   for (size_t t = 0; t < tile_sp.size(); ++t) tile_sp[t] = (t * BD_TJ < seg0) ? 0 : 1;
 
-  // internal position mirror: np slots + 4 corner points
-  const double C = ceil(L);
-  h->host_pos.assign(2 * ((size_t)np + 4), 0.0);
+  // internal position mirror: np slots + ghost points
+  std::vector<double> ghx, ghy;
+  bdhost::make_ghosts(L, p.a, ghx, ghy);
+  const int ng = (int)ghx.size();
+  h->ng = ng;
+  h->host_pos.assign(2 * ((size_t)np + ng), 0.0);
   for (int i = 0; i < np; ++i) {
     int e = h->ext_of_int[i];
     if (e >= 0) {
       h->host_pos[2 * i] = xy[2 * e];
       h->host_pos[2 * i + 1] = xy[2 * e + 1];
     } else {
-      h->host_pos[2 * i] = 4.0 * C;  // never referenced by the triangulation
-      h->host_pos[2 * i + 1] = 4.0 * C;
+      h->host_pos[2 * i] = 0.5 * L;  // never referenced by the triangulation
+      h->host_pos[2 * i + 1] = 0.5 * L;
     }
   }
-  const double gx[4] = {-C, 2 * C, 2 * C, -C}, gy[4] = {-C, -C, 2 * C, 2 * C};
-  for (int k = 0; k < 4; ++k) {
-    h->host_pos[2 * ((size_t)np + k)] = gx[k];
-    h->host_pos[2 * ((size_t)np + k) + 1] = gy[k];
+  for (int k = 0; k < ng; ++k) {
+    h->host_pos[2 * ((size_t)np + k)] = ghx[k];
+    h->host_pos[2 * ((size_t)np + k) + 1] = ghy[k];
   }
 
   // ---- initial Delaunay triangulation on the host (Sec. 4.1) ----
-  std::vector<double> X(np + 4), Y(np + 4);
-  for (int i = 0; i < np + 4; ++i) {
+  std::vector<double> X(np + ng), Y(np + ng);
+  for (int i = 0; i < np + ng; ++i) {
     X[i] = h->host_pos[2 * i];
     Y[i] = h->host_pos[2 * i + 1];
   }
@@ -309,14 +313,15 @@ int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_i
   bdpred::Grid grid;
   grid.q = q;
   grid.inv_q = inv_q;
-  const int gids[4] = {np, np + 1, np + 2, np + 3};
+  std::vector<int> gids(ng);
+  for (int k = 0; k < ng; ++k) gids[k] = np + k;
   std::vector<int> V, N;
   if (bdhost::build_delaunay(X.data(), Y.data(), grid, order, gids, V, N) != 0) {
     delete h;
     return BD_ERR_TRIANGULATION;
   }
   const int nt = (int)(V.size() / 3);
-  if (nt != 2 * n + 2) {
+  if (nt != 2 * (n + ng) - 6) {
     delete h;
     return BD_ERR_TRIANGULATION;
   }
@@ -375,13 +380,17 @@ int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_i
   BdDev &d = h->d;
   memset(&d, 0, sizeof(d));
   cudaError_t e = cudaSuccess;
-  const size_t nv = (size_t)np + 4;
+  const size_t nv = (size_t)np + ng;
 #define BD_TRY(x)                         \
   do {                                    \
     e = (x);                              \
     if (e != cudaSuccess) goto cuda_error; \
   } while (0)
   {
+    {
+      const char *fv = getenv("BD_FORCE_VARIANT");
+      c.force_variant = fv ? atoi(fv) : 1;
+    }
     c.nchunk = p.law == BD_LAW_SHORT ? 1 : pick_nchunk(c);
     BD_TRY(dalloc(h, &d.pos, nv));
     BD_TRY(dalloc(h, &d.prev, nv));
@@ -551,6 +560,9 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
     stats->inverted = k.st_inverted;
     stats->max_corr_iters = k.st_max_corr_iters;
     stats->verlet_rebuilds = (int32_t)k.st_verlet_rebuilds;
+    stats->fail_phase = k.st_fail_phase;
+    stats->fail_item = k.st_fail_item;
+    stats->fail_count = k.st_fail_count;
     stats->rejected = k.status != 0;
     double mo;
     unsigned long long bits = k.st_max_overlap_bits;
@@ -734,18 +746,35 @@ int bd_force_timing(bd_handle *h, int enable, int reset, double *total_ms, int64
 
 int64_t bd_last_launch_count(bd_handle *h) { return h ? h->last_launches : -1; }
 
-int bd_triangulate(int32_t n, const double *xy, double L, double *xy_grid, int32_t *tri,
+int bd_ghost_points(double L, double a, double *xy, int32_t *count) {
+  if (!(L > 0) || !(a > 0) || !count) return BD_ERR_ARG;
+  std::vector<double> gx, gy;
+  bdhost::make_ghosts(L, a, gx, gy);
+  if (xy) {
+    if (*count < (int32_t)gx.size()) return BD_ERR_ARG;
+    for (size_t k = 0; k < gx.size(); ++k) {
+      xy[2 * k] = gx[k];
+      xy[2 * k + 1] = gy[k];
+    }
+  }
+  *count = (int32_t)gx.size();
+  return BD_OK;
+}
+
+int bd_triangulate(int32_t n, const double *xy, double L, double a, double *xy_grid, int32_t *tri,
                    int32_t *n_tri) {
-  if (n < 1 || !xy || !tri || !(L > 0)) return BD_ERR_ARG;
-  const int s = grid_shift(L);
+  if (n < 1 || !xy || !tri || !(L > 0) || !(a > 0)) return BD_ERR_ARG;
+  const int s = grid_shift(L, a);
   const double q = ldexp(1.0, -s), inv_q = ldexp(1.0, s);
-  const double C = ceil(L);
-  std::vector<double> X(n + 4), Y(n + 4);
+  std::vector<double> gx, gy;
+  bdhost::make_ghosts(L, a, gx, gy);
+  const int ng = (int)gx.size();
+  std::vector<double> X(n + ng), Y(n + ng);
   std::vector<uint64_t> hk(n);
   for (int i = 0; i < n; ++i) {
     X[i] = snap_host(xy[2 * i], q, inv_q);
     Y[i] = snap_host(xy[2 * i + 1], q, inv_q);
-    if (!(X[i] > -C && X[i] < 2 * C && Y[i] > -C && Y[i] < 2 * C)) return BD_ERR_ARG;
+    if (!(X[i] > 0 && X[i] < L && Y[i] > 0 && Y[i] < L)) return BD_ERR_ARG;
     if (xy_grid) {
       xy_grid[2 * i] = X[i];
       xy_grid[2 * i + 1] = Y[i];
@@ -754,22 +783,22 @@ int bd_triangulate(int32_t n, const double *xy, double L, double *xy_grid, int32
     uint32_t uy = (uint32_t)std::min(65535.0, std::max(0.0, Y[i] / L * 65536.0));
     hk[i] = bdhost::hilbert_index(ux, uy);
   }
-  const double gx[4] = {-C, 2 * C, 2 * C, -C}, gy[4] = {-C, -C, 2 * C, 2 * C};
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < ng; ++k) {
     X[n + k] = gx[k];
     Y[n + k] = gy[k];
   }
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
-  std::sort(order.begin(), order.end(), [&](int a, int b) { return hk[a] != hk[b] ? hk[a] < hk[b] : a < b; });
+  std::sort(order.begin(), order.end(), [&](int a_, int b_) { return hk[a_] != hk[b_] ? hk[a_] < hk[b_] : a_ < b_; });
   bdpred::Grid grid;
   grid.q = q;
   grid.inv_q = inv_q;
-  const int gids[4] = {n, n + 1, n + 2, n + 3};
+  std::vector<int> gids(ng);
+  for (int k = 0; k < ng; ++k) gids[k] = n + k;
   std::vector<int> V, N;
   if (bdhost::build_delaunay(X.data(), Y.data(), grid, order, gids, V, N) != 0) return BD_ERR_TRIANGULATION;
   const int nt = (int)(V.size() / 3);
-  if (nt != 2 * n + 2) return BD_ERR_TRIANGULATION;
+  if (nt != 2 * (n + ng) - 6) return BD_ERR_TRIANGULATION;
   memcpy(tri, V.data(), sizeof(int) * V.size());
   if (n_tri) *n_tri = nt;
   return BD_OK;

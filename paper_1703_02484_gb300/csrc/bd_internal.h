@@ -38,9 +38,11 @@ struct BdCtl {
   int st_max_corr_iters;
   int st_rejected;
   unsigned long long st_max_overlap_bits;   // double bits of the deepest overlap (monotone for >= 0)
-  int st_fail_phase;
+  int st_fail_phase;               // 1 reversal, 2 repair stuck, 3 repair rounds, 4 Lawson rounds, 5 overlap passes
   int vl_need;                     // Verlet rebuild requested for this step
   long long st_verlet_rebuilds;
+  int st_fail_item;                // an offending triangle (repair) or edge corner (reversal)
+  int st_fail_count;               // inverted triangles / reversed edges at the failure
 };
 
 // counter slots within BdCtl::cnt[phase % 4]
@@ -87,6 +89,7 @@ struct BdConst {
   uint64_t seed;
   uint32_t replica;
   int max_corr_iters, max_flip_rounds;
+  int force_variant;       // 0: scalar FP32 sweep, 1: packed f32x2 sweep
 };
 
 // launchers (kernels_*.cu)
@@ -94,7 +97,7 @@ cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t 
 cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, cudaStream_t s);
 cudaError_t bd_launch_dt(const BdDev &d, const BdConst &c, int mode, cudaStream_t s, int grid, int block);
 int bd_dt_grid(int *grid, int *block);
-int bd_force_blocks_per_sm();
+int bd_force_blocks_per_sm(int variant);
 cudaError_t bd_launch_work_copy(const BdDev &d, const BdConst &c, cudaStream_t s);
 cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t s);
 int bd_short_launches();

@@ -4,8 +4,8 @@
 // Sec. 4.1: "the Delaunay triangulation of the particle positions is built
 // only once from scratch on the host" and then maintained on the device.
 // The paper uses CGAL's periodic triangulation; this build uses reflecting
-// walls and closes the hull with four fixed corner points far outside the
-// box, and builds the triangulation by incremental insertion: each point
+// walls and closes the hull with fixed ghost points outside the box (see
+// make_ghosts), and builds the triangulation by incremental insertion: each point
 // splits the triangle (or edge) that contains it and Lawson flips restore
 // the empty-circle property around it.  Predicates are exact (predicates.cuh).
 //
@@ -170,6 +170,43 @@ struct Tri {
   }
 };
 
+// Points that close the triangulation around the box (ids after the disks).
+// The paper's box is periodic (a torus has no hull); with walls the hull is
+// closed here by four far corners plus a ring of fixed points just outside
+// the walls.  The ring keeps the triangles at the walls well shaped: with the
+// corners alone, disks along a wall form long slivers that a noise step
+// inverts.  Layout, with C = ceil(L), W = S = ceil(2a):
+//   [0..3] far corners (-F,-F), (G,-F), (G,G), (-F,G), F = C + 3W, G = 2C + 3W
+//   rows   y = -W - off(k, 4+side) (bottom, side 0), y = C + W + off(k, 4+side) (top, side 1),
+//          x = -W + k S + off(k, side)
+//   cols   x = -W - off(k, 4+side) (left, side 2),   x = C + W + off(k, 4+side) (right, side 3),
+//          y = -W + S/2 + k S + off(k, side)
+// off(k, s) = ((7919 k + 104729 s) mod 257) / 1024 in [0, 1/4] breaks the
+// symmetries that would make four ghost points cocircular.  All values are
+// dyadic, hence exact on the position grid.
+void make_ghosts(double L, double a, std::vector<double> &gx, std::vector<double> &gy) {
+  const double C = ceil(L), W = ceil(2.0 * a), S = W;
+  const double F = C + 3.0 * W, G = 2.0 * C + 3.0 * W;
+  gx.assign({-F, G, G, -F});
+  gy.assign({-F, -F, G, G});
+  auto off = [](long k, long side) { return (double)((7919L * k + 104729L * side) % 257L) / 1024.0; };
+  for (int side = 0; side < 2; ++side) {
+    for (long k = 0; -W + k * S <= C + W; ++k) {
+      gx.push_back(-W + k * S + off(k, side));
+      gy.push_back(side == 0 ? -W - off(k, 4 + side) : C + W + off(k, 4 + side));
+    }
+  }
+  for (int side = 2; side < 4; ++side) {
+    for (long k = 0; -W + 0.5 * S + k * S < C + W; ++k) {
+      gx.push_back(side == 2 ? -W - off(k, 4 + side) : C + W + off(k, 4 + side));
+      gy.push_back(-W + 0.5 * S + k * S + off(k, side));
+    }
+  }
+}
+
+// largest coordinate magnitude among disks and ghost points
+double ghost_extent(double L, double a) { return 2.0 * ceil(L) + 3.0 * ceil(2.0 * a); }
+
 // Hilbert-curve index of (x, y) on a 2^16 x 2^16 grid (locality order only)
 uint64_t hilbert_index(uint32_t x, uint32_t y) {
   const uint32_t n = 1u << 16;
@@ -191,12 +228,12 @@ uint64_t hilbert_index(uint32_t x, uint32_t y) {
   return d;
 }
 
-// Delaunay triangulation of points 0..nv-1 listed in `pts` (ids into X/Y)
-// plus the 4 corner points `g[4]` (counter-clockwise square enclosing all),
-// inserted in `order`.  Fills V/N (corner table).  Returns 0 or a negative
-// code (-2 duplicate point, -3 point outside the corner square).
+// Delaunay triangulation of the points listed in `order` (ids into X/Y)
+// plus the ghost points `g` (g[0..3] a counter-clockwise square enclosing
+// everything, the rest inserted first).  Fills V/N (corner table).  Returns 0
+// or a negative code (-2 duplicate point, -3 point outside the corner square).
 int build_delaunay(const double *X, const double *Y, const bdpred::Grid &grid,
-                   const std::vector<int> &order, const int g[4], std::vector<int> &V,
+                   const std::vector<int> &order, const std::vector<int> &g, std::vector<int> &V,
                    std::vector<int> &N) {
   Tri T;
   T.X = X;
@@ -210,6 +247,11 @@ int build_delaunay(const double *X, const double *Y, const bdpred::Grid &grid,
   T.link(3 * t0 + 1, 3 * t1 + 2);
   std::vector<int> stack;
   int last = t0;
+  for (size_t i = 4; i < g.size(); ++i) {
+    int r = T.insert(g[i], last, stack);
+    if (r < 0) return r;
+    last = r;
+  }
   for (size_t i = 0; i < order.size(); ++i) {
     int r = T.insert(order[i], last, stack);
     if (r < 0) return r;

@@ -277,7 +277,10 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
           if (!(d.moved[u] | d.moved[w])) continue;
           double2 a0 = d.prev[u], b0 = d.prev[w], a1 = d.pos[u], b1 = d.pos[w];
           double r0x = b0.x - a0.x, r0y = b0.y - a0.y, r1x = b1.x - a1.x, r1y = b1.y - a1.y;
-          if (r0x * r1x + r0y * r1y < 0.0) rej++;
+          if (r0x * r1x + r0y * r1y < 0.0) {
+            rej++;
+            atomicExch(&ctl->st_fail_item, cc);
+          }
         }
       }
       block_add(cnt(ctl, b.ph, C_INV), inv);
@@ -288,12 +291,20 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
     int n_inv = *(volatile int *)cnt(ctl, b.ph - 1, C_INV);
     int n_rej = *(volatile int *)cnt(ctl, b.ph - 1, C_REJECT);
     st_inv += n_inv;
-    if (n_rej) { status = BD_ERR_STEP_REJECTED; break; }
+    if (n_rej) {
+      status = BD_ERR_STEP_REJECTED;
+      if (lead) { ctl->st_fail_phase = 1; ctl->st_fail_count = n_rej; }
+      break;
+    }
 
     // ---------------- R: inversion repair ----------------
     int rounds = 0;
     while (n_inv > 0) {
-      if (rounds++ >= c.max_flip_rounds) { status = BD_ERR_STEP_REJECTED; break; }
+      if (rounds++ >= c.max_flip_rounds) {
+        status = BD_ERR_STEP_REJECTED;
+        if (lead) { ctl->st_fail_phase = 3; ctl->st_fail_count = n_inv; }
+        break;
+      }
       ++epoch;
       // RM: candidates
       phase_begin(ctl, b);
@@ -302,6 +313,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
         for (int t = tid; t < x.T; t += nth) {
           int4 v = d.tv[t];
           if (!(v.w & BD_TRI_INVERTED)) continue;
+          atomicExch(&ctl->st_fail_item, t);
           int4 nn = d.tn[t];
           for (int k = 0; k < 3; ++k) {
             int o = vk(nn, k);
@@ -322,7 +334,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
       }
       if (!grid_sync(ctl, b)) return;
       int n_cand = *(volatile int *)cnt(ctl, b.ph - 1, C_CAND);
-      if (n_cand == 0) { status = BD_ERR_STEP_REJECTED; break; }
+      if (n_cand == 0) {
+        status = BD_ERR_STEP_REJECTED;
+        if (lead) { ctl->st_fail_phase = 2; ctl->st_fail_count = n_inv; }
+        break;
+      }
       // RF: winners flip
       phase_begin(ctl, b);
       {
@@ -365,7 +381,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
     // ---------------- L: Lawson flips ----------------
     rounds = 0;
     for (;;) {
-      if (rounds++ >= c.max_flip_rounds) { status = BD_ERR_FLIP_NOT_CONVERGED; break; }
+      if (rounds++ >= c.max_flip_rounds) {
+        status = BD_ERR_FLIP_NOT_CONVERGED;
+        if (lead) ctl->st_fail_phase = 4;
+        break;
+      }
       ++epoch;
       phase_begin(ctl, b);
       for (int t = tid; t < x.T; t += nth) {
@@ -462,7 +482,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
     int n_ov = *(volatile int *)cnt(ctl, b.ph - 1, C_OVERLAP);
     if (n_ov == 0) break;
     st_overlap += n_ov;
-    if (corr_iter >= c.max_corr_iters) { status = BD_ERR_OVERLAP_NOT_CONVERGED; break; }
+    if (corr_iter >= c.max_corr_iters) {
+      status = BD_ERR_OVERLAP_NOT_CONVERGED;
+      if (lead) ctl->st_fail_phase = 5;
+      break;
+    }
     ++corr_iter;
     // ---------------- O: apply (capped at sigma/4) ----------------
     phase_begin(ctl, b);

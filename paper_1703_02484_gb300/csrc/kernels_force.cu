@@ -148,6 +148,142 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32(BdDev d, BdConst c) {
   }
 }
 
+// Packed variant: Blackwell's f32x2 instructions (add/sub/mul/fma on a pair
+// of FP32 values in one 64-bit register pair) process two i disks per
+// instruction, halving the issue slots of the FP32 work.  j disks are staged
+// as (x, x, y, y) so one 128-bit shared load yields both packed operands.
+namespace {
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk2(float a, float b) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void up2(u64 r, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+}  // namespace
+
+template <int IPT>
+__global__ void __launch_bounds__(BD_FT) k_force_long_f32x2(BdDev d, BdConst c) {
+  if (ctl_failed(d.ctl)) return;
+  constexpr int NP = IPT / 2;
+  constexpr int IB = BD_FT * IPT;
+  __shared__ ulonglong2 sj[2][BD_TJ];   // per j: ((x, x), (y, y)) re-centred
+  const int ib = blockIdx.x, jc = blockIdx.y, tid = threadIdx.x;
+  const float2 org = d.iorigin[ib];
+  u64 xi2[NP], yi2[NP], ax2[NP], ay2[NP];
+  float fxh[IPT], fxl[IPT], fyh[IPT], fyl[IPT], a0[IPT], a1[IPT];
+  int ii[IPT];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    float xs[2], ys[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = 2 * k + h;
+      int i = d.iperm[ib * IB + q * BD_FT + tid];
+      ii[q] = i;
+      if (i >= 0) {
+        float4 w = d.work[i];
+        xs[h] = __fadd_rn(__fsub_rn(w.x, org.x), w.z);
+        ys[h] = __fadd_rn(__fsub_rn(w.y, org.y), w.w);
+        int sp = d.species[i];
+        a0[q] = c.alpha[2 * sp + 0];
+        a1[q] = c.alpha[2 * sp + 1];
+      } else {
+        xs[h] = 1.0e18f;
+        ys[h] = 1.0e18f;
+        a0[q] = 0.f;
+        a1[q] = 0.f;
+      }
+      fxh[q] = fxl[q] = fyh[q] = fyl[q] = 0.f;
+    }
+    xi2[k] = pk2(xs[0], xs[1]);
+    yi2[k] = pk2(ys[0], ys[1]);
+    ax2[k] = ay2[k] = 0ull;
+  }
+  const int t_begin = (int)(((long long)c.ntiles * jc) / c.nchunk);
+  const int t_end = (int)(((long long)c.ntiles * (jc + 1)) / c.nchunk);
+  const float e0 = 1e-20f * (float)(c.a * c.a);
+  const u64 eps2 = pk2(e0, e0);
+  float2 st0, st1;
+  auto fetch = [&](int tile) {
+    int j0 = tile * BD_TJ + tid;
+    float4 w0 = d.work[j0], w1 = d.work[j0 + BD_FT];
+    st0 = make_float2(__fadd_rn(__fsub_rn(w0.x, org.x), w0.z), __fadd_rn(__fsub_rn(w0.y, org.y), w0.w));
+    st1 = make_float2(__fadd_rn(__fsub_rn(w1.x, org.x), w1.z), __fadd_rn(__fsub_rn(w1.y, org.y), w1.w));
+  };
+  auto store = [&](int b) {
+    sj[b][tid] = make_ulonglong2(pk2(st0.x, st0.x), pk2(st0.y, st0.y));
+    sj[b][tid + BD_FT] = make_ulonglong2(pk2(st1.x, st1.x), pk2(st1.y, st1.y));
+  };
+  int buf = 0;
+  if (t_begin < t_end) {
+    fetch(t_begin);
+    store(0);
+  }
+  __syncthreads();
+  for (int t = t_begin; t < t_end; ++t) {
+    if (t + 1 < t_end) fetch(t + 1);
+#pragma unroll 4
+    for (int jj = 0; jj < BD_TJ; ++jj) {
+      const ulonglong2 p = sj[buf][jj];
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        u64 dx = sub2(p.x, xi2[k]);
+        u64 dy = sub2(p.y, yi2[k]);
+        u64 r2 = fma2(dx, dx, eps2);
+        r2 = fma2(dy, dy, r2);
+        float ra, rb;
+        up2(r2, ra, rb);
+        u64 sv = pk2(rsqrt_apx(ra), rsqrt_apx(rb));
+        u64 s3 = mul2(mul2(sv, sv), sv);
+        ax2[k] = fma2(dx, s3, ax2[k]);
+        ay2[k] = fma2(dy, s3, ay2[k]);
+      }
+    }
+    const int sp = d.tile_species[t];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      float ax0, ax1, ay0, ay1;
+      up2(ax2[k], ax0, ax1);
+      up2(ay2[k], ay0, ay1);
+      const int q0 = 2 * k, q1 = 2 * k + 1;
+      const float al0 = sp ? a1[q0] : a0[q0], al1 = sp ? a1[q1] : a0[q1];
+      two_sum(fxh[q0], fxl[q0], -al0 * ax0);
+      two_sum(fyh[q0], fyl[q0], -al0 * ay0);
+      two_sum(fxh[q1], fxl[q1], -al1 * ax1);
+      two_sum(fyh[q1], fyl[q1], -al1 * ay1);
+      ax2[k] = ay2[k] = 0ull;
+    }
+    if (t + 1 < t_end) store(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) {
+    int i = ii[q];
+    if (i >= 0)
+      d.fpart[(size_t)jc * c.np + i] =
+          make_double2((double)fxh[q] + (double)fxl[q], (double)fyh[q] + (double)fyl[q]);
+  }
+}
+
 // FP64 variant (precision = 1): one disk per thread, FP64 master positions
 __global__ void __launch_bounds__(128) k_force_long_f64(BdDev d, BdConst c) {
   if (ctl_failed(d.ctl)) return;
@@ -285,16 +421,20 @@ __global__ void k_work_copy(BdDev d, BdConst c) {
   d.work[i] = split(d.pos[i]);
 }
 
-int bd_force_blocks_per_sm() {
+int bd_force_blocks_per_sm(int variant) {
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force_long_f32, BD_FT, 0) != cudaSuccess)
-    return 0;
-  return per;
+  cudaError_t e = variant == 1
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force_long_f32x2<BD_IPT>, BD_FT, 0)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force_long_f32, BD_FT, 0);
+  return e == cudaSuccess ? per : 0;
 }
 
 cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t s) {
   if (c.precision == 0) {
-    k_force_long_f32<<<dim3(c.n_iblocks, c.nchunk), BD_FT, 0, s>>>(d, c);
+    if (c.force_variant == 1)
+      k_force_long_f32x2<BD_IPT><<<dim3(c.n_iblocks, c.nchunk), BD_FT, 0, s>>>(d, c);
+    else
+      k_force_long_f32<<<dim3(c.n_iblocks, c.nchunk), BD_FT, 0, s>>>(d, c);
   } else {
     k_force_long_f64<<<dim3((c.np + 127) / 128, c.nchunk), 128, 0, s>>>(d, c);
   }

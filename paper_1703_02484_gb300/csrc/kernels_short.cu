@@ -5,6 +5,8 @@
 //   U = 4 eps[(s/r)^12 - (s/r)^6] + eps   (r < 2^(1/6) s),  s = 2a
 //     - eps (s/r) exp(-kappa (r - s)),
 //   F_i = sum_j -U'(r_ij) (r_i - r_j)/r_ij   for r_ij < r_cut.
+// The tail is evaluated in FP32; the WCA core, whose r^-13 force near contact
+// turns FP32 rounding into errors above 1e-5 of the net force, in FP64.
 //
 // Lists: every disk keeps the disks within r_cut + skin of it, decided in
 // FP64 as (x_i - x_j)^2 + (y_i - y_j)^2 < (r_cut + skin)^2 with two products
@@ -203,11 +205,14 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
   if (i >= c.np) return;
   if (d.ext_id[i] < 0) return;
   const float4 wi = d.work[i];
+  const double2 pi = d.pos[i];
   const int m = d.vl_cnt[i];
   const float rc2 = (float)(c.r_cut * c.r_cut);
   const float sg = (float)c.sigma, eps = (float)c.eps, kap = (float)c.kappa;
   const float rwca2 = (float)(1.2599210498948732 * c.sigma * c.sigma);  // (2^(1/6) s)^2
-  float fx = 0.f, fy = 0.f;
+  const double s2c = c.sigma * c.sigma, e24 = 24.0 * c.eps;
+  float fx = 0.f, fy = 0.f;      // Yukawa tail, FP32
+  double gx = 0.0, gy = 0.0;     // WCA core, FP64
   for (int t = 0; t < m; ++t) {
     int j = d.vl_idx[(size_t)t * c.np + i];
     float4 wj = d.work[j];
@@ -217,7 +222,7 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
     float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
     if (fabsf(r2 - rc2) < 1e-5f * rc2) {
       // at the cut-off the force jumps: decide as the FP64 reference does
-      double2 pi = d.pos[i], pj = d.pos[j];
+      double2 pj = d.pos[j];
       double ex = __dsub_rn(pi.x, pj.x), ey = __dsub_rn(pi.y, pj.y);
       if (!(sqrt(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey))) < c.r_cut)) continue;
     } else if (r2 >= rc2) {
@@ -225,17 +230,24 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
     }
     float r = sqrtf(r2);
     float ir = 1.0f / r;
-    float mag = -eps * sg * expf(-kap * (r - sg)) * (ir * ir + kap * ir);
+    // Yukawa tail: -U'(r) / r, smooth, in FP32
+    float my = -eps * sg * expf(-kap * (r - sg)) * (ir * ir + kap * ir) * ir;
+    fx = fmaf(my, dx, fx);
+    fy = fmaf(my, dy, fy);
     if (r2 < rwca2) {
-      float s2 = sg * sg / r2;
-      float s6 = s2 * s2 * s2;
-      mag += 24.0f * eps * ir * (2.0f * s6 * s6 - s6);
+      // WCA core near contact: -U'(r) ~ r^-13 amplifies rounding, so FP64
+      // from the master positions (no square root needed)
+      double2 pj = d.pos[j];
+      double ex = pi.x - pj.x, ey = pi.y - pj.y;
+      double q2 = ex * ex + ey * ey;
+      double s2 = s2c / q2;
+      double s6 = s2 * s2 * s2;
+      double cw = e24 * (2.0 * s6 * s6 - s6) / q2;
+      gx += cw * ex;
+      gy += cw * ey;
     }
-    // -U'(r) along (r_i - r_j)/r
-    fx = fmaf(mag * ir, dx, fx);
-    fy = fmaf(mag * ir, dy, fy);
   }
-  d.fpart[i] = make_double2((double)fx, (double)fy);
+  d.fpart[i] = make_double2((double)fx + gx, (double)fy + gy);
 }
 
 cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t s) {
@@ -250,7 +262,7 @@ cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t
   k_scan_top<<<1, BD_SCAN_B, 0, s>>>(d, c, nsb);
   k_scan_add<<<nsb, BD_SCAN_B, 0, s>>>(d, c);
   k_vl_scatter<<<gn, b, 0, s>>>(d, c);
-  k_vl_build<<<gn, 128, 0, s>>>(d, c);
+  k_vl_build<<<(c.np + 127) / 128, 128, 0, s>>>(d, c);
   k_force_verlet<<<gn, b, 0, s>>>(d, c);
   return cudaGetLastError();
 }

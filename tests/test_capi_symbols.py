@@ -60,13 +60,24 @@ def test_host_triangulation_equals_oracle_delaunay(n):
     L = workloads.box_side(max(n, 4), cfg.rho)
     xy = workloads.initial_positions(n, L, 1.0, cfg.rho, seed=n)
     tri, grid = binding.triangulate(xy, L)
-    assert len(tri) == 2 * n + 2
+    G = len(geometry.ghost_points(L))
+    assert len(tri) == 2 * (n + G) - 6
     assert np.max(np.abs(grid - xy)) <= 1e-11 * L
     ot = geometry.delaunay(grid, L)
     assert np.array_equal(geometry.edges(tri), geometry.edges(ot))
     P = geometry.with_ghosts(grid, L)
     for t in tri[: min(len(tri), 2000)]:
         assert geometry.orient(P[t[0]], P[t[1]], P[t[2]]) > 0
+
+
+def test_ghost_points_match_oracle_definition():
+    for L in (3.5, 12.9, 103.55, 1023.3, 2566.79):
+        assert np.array_equal(binding.ghost_points(L, 1.0), geometry.ghost_points(L, 1.0))
+    # ring points stay clear of the walls and inside the far corners
+    g = geometry.ghost_points(100.0, 1.0)
+    ring = g[4:]
+    assert np.all((ring[:, 0] <= -2) | (ring[:, 0] >= 102) | (ring[:, 1] <= -2) | (ring[:, 1] >= 102))
+    assert np.all(np.abs(ring) < np.abs(g[:4]).max())
 
 
 def test_host_triangulation_lattice_start():

@@ -178,7 +178,7 @@ def test_tiny_and_ragged_sizes(n):
     st = s.step(5)
     assert st["steps_done"] == 5
     out = s.state()
-    assert len(out["tri"]) == 2 * n + 2
+    assert len(out["tri"]) == 2 * (n + len(geometry.ghost_points(L))) - 6
     assert np.array_equal(geometry.edges(out["tri"]), geometry.edges(geometry.delaunay(out["xy"], L)))
     if n >= 2:
         assert len(cKDTree(out["xy"]).query_pairs(2.0 * (1 - 1e-12))) == 0

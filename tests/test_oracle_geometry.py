@@ -106,14 +106,25 @@ def test_exact_predicates_vs_rationals():
 
 def test_delaunay_vs_bruteforce_tiny():
     rng = np.random.default_rng(5)
+    sq = [[-60.0, -60.0], [80.0, -60.0], [80.0, 80.0], [-60.0, 80.0]]
     for trial in range(6):
         n = 14
-        L = 20.0
-        xy = rng.uniform(1, L - 1, size=(n, 2))
-        tris = geometry.delaunay(xy, L)
-        P = geometry.with_ghosts(xy, L)
+        xy = rng.uniform(1, 19, size=(n, 2))
+        tris = geometry.delaunay_generic(xy, sq)
+        P = np.concatenate([xy, sq])
         assert geometry.canonical_triangles(tris) == geometry.delaunay_bruteforce(P)
         assert len(tris) == 2 * n + 2
+
+
+def test_delaunay_with_ghost_ring_vs_bruteforce():
+    # a small box: disks plus its ghost points, brute-forced over all points
+    rng = np.random.default_rng(6)
+    L = 7.0
+    xy = rng.uniform(1, L - 1, size=(4, 2))
+    tris = geometry.delaunay(xy, L)
+    P = geometry.with_ghosts(xy, L)
+    assert geometry.canonical_triangles(tris) == geometry.delaunay_bruteforce(P)
+    assert len(tris) == 2 * len(P) - 6
 
 
 def test_delaunay_vs_qhull_and_properties():
@@ -126,8 +137,9 @@ def test_delaunay_vs_qhull_and_properties():
     assert np.array_equal(geometry.edges(tris), geometry.edges(Delaunay(P).simplices))
     assert geometry.general_position(P, tris)
     assert geometry.non_delaunay_edges(P, tris) == []
-    assert len(tris) == 2 * 3000 + 2
-    assert len(geometry.edges(tris)) == 3 * 3000 + 5
+    V = len(P)
+    assert len(tris) == 2 * V - 6
+    assert len(geometry.edges(tris)) == 3 * V - 7
 
 
 def test_box_side_formula():
