@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--workload", default="n1e5",
+                    help="configuration name (n1e5 is the headline; c1, c2, c3, c5 for tables)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -200,7 +202,7 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    cfg = workloads.CONFIGS["n1e5"]
+    cfg = workloads.CONFIGS[args.workload]
     xy, sp, th = workloads.initial_state(cfg)
     p = bd.params_from_config(cfg)
     p.replica = rank
@@ -250,6 +252,8 @@ def main():
     peak_tflops = sms * 128 * 2 * f_hz / 1e12
     avg_force_s = (force_ms / max(1, force_n)) / 1e3
     pairs = N * (N - 1)
+    if force_n == 0:
+        avg_force_s = float("nan")
     achieved = FLOPS_PER_PAIR * pairs / avg_force_s / 1e12
     pipe_frac = FP32_INST_PER_PAIR * pairs / avg_force_s / (sms * 128 * f_hz)
     traffic = None
@@ -287,6 +291,8 @@ def main():
                "h2d_bytes_per_step": N * (16 + 4), "d2h_bytes_per_step": N * (16 + 4 + 1)}
 
     if rank == 0:
+        if args.workload != "n1e5":
+            line_cfg = {"workload": "%s: N=%d, rho=%.2f, law=%d" % (cfg.name, N, cfg.rho, cfg.law), "N": N}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -304,6 +310,9 @@ def main():
                                       "12 flops/pair caps frac at 0.75" % (sms, f_hz / 1e6, pk_kind)},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
         }
+        if args.workload != "n1e5":
+            line["metric"] = "particle-steps/s (%s)" % cfg.name
+            line["config"].update(line_cfg)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(cfg, xy, sp, th)
         print(json.dumps(line), flush=True)

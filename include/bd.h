@@ -103,6 +103,7 @@ typedef struct bd_step_stats {
   double max_overlap;       /* deepest overlap sigma - r seen */
   int32_t fail_item;        /* internal id of an offending triangle or edge (diagnostic) */
   int32_t fail_count;       /* inverted triangles or reversed edges at the failure */
+  int64_t barriers;         /* grid-wide barriers of the device-side loops (all steps) */
 } bd_step_stats;
 
 typedef struct bd_handle bd_handle;

@@ -43,6 +43,7 @@ class bd_step_stats(ctypes.Structure):
         ("verlet_rebuilds", ctypes.c_int32), ("fail_phase", ctypes.c_int32),
         ("max_overlap", ctypes.c_double),
         ("fail_item", ctypes.c_int32), ("fail_count", ctypes.c_int32),
+        ("barriers", ctypes.c_int64),
     ]
 
     def as_dict(self):

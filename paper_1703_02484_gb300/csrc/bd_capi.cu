@@ -313,6 +313,7 @@ int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_i
   bdpred::Grid grid;
   grid.q = q;
   grid.inv_q = inv_q;
+  grid.s = s;
   std::vector<int> gids(ng);
   for (int k = 0; k < ng; ++k) gids[k] = np + k;
   std::vector<int> V, N;
@@ -346,6 +347,7 @@ int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_i
   c.wall_hi = wall_hi;
   c.q = q;
   c.inv_q = inv_q;
+  c.qshift = s;
   for (int k = 0; k < 4; ++k) {
     c.alpha[k] = (float)p.alpha[k];
     c.alpha_d[k] = p.alpha[k];
@@ -470,7 +472,7 @@ int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_i
     }
     BD_TRY(bd_launch_work_copy(d, c, st));
     BD_TRY(cudaStreamSynchronize(st));
-    if (bd_dt_grid(&h->dt_grid, &h->dt_block) != 0) {
+    if (bd_dt_grid_for(std::max(nt, np), &h->dt_grid, &h->dt_block) != 0) {
       bd_free(h);
       return BD_ERR_CUDA;
     }
@@ -563,6 +565,7 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
     stats->fail_phase = k.st_fail_phase;
     stats->fail_item = k.st_fail_item;
     stats->fail_count = k.st_fail_count;
+    stats->barriers = k.st_barriers;
     stats->rejected = k.status != 0;
     double mo;
     unsigned long long bits = k.st_max_overlap_bits;
@@ -570,7 +573,10 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
     stats->max_overlap = mo;
   }
   if (k.status) {
-    // clear the sticky status so the handle keeps working from the last good state
+    // clear the sticky status so the handle keeps working from the last good
+    // state; after a timed-out barrier also reset the barrier words
+    if (k.status == BD_ERR_DEVICE_TIMEOUT) cudaMemsetAsync(h->d.ctl, 0, offsetof(BdCtl, epoch), st);
+    cudaMemsetAsync(&h->d.ctl->cnt[0][0], 0, sizeof(h->d.ctl->cnt), st);
     cudaMemsetAsync(&h->d.ctl->status, 0, sizeof(int), st);
     cudaStreamSynchronize(st);
     return k.status;
@@ -793,6 +799,7 @@ int bd_triangulate(int32_t n, const double *xy, double L, double a, double *xy_g
   bdpred::Grid grid;
   grid.q = q;
   grid.inv_q = inv_q;
+  grid.s = s;
   std::vector<int> gids(ng);
   for (int k = 0; k < ng; ++k) gids[k] = n + k;
   std::vector<int> V, N;

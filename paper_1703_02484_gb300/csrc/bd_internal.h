@@ -24,7 +24,7 @@ struct BdCtl {
   unsigned int bar_count;
   unsigned int bar_gen;
   int status;
-  int pad0;
+  unsigned int exit_count;         // blocks that have left the triangulation kernel
   unsigned long long epoch;        // flip-round counter, grows across launches
   int cnt[4][8];                   // per-phase counters, rotated every barrier
   // statistics accumulated over a bd_step call
@@ -41,6 +41,7 @@ struct BdCtl {
   int st_fail_phase;               // 1 reversal, 2 repair stuck, 3 repair rounds, 4 Lawson rounds, 5 overlap passes
   int vl_need;                     // Verlet rebuild requested for this step
   long long st_verlet_rebuilds;
+  long long st_barriers;           // grid barriers passed by the triangulation kernel
   int st_fail_item;                // an offending triangle (repair) or edge corner (reversal)
   int st_fail_count;               // inverted triangles / reversed edges at the failure
 };
@@ -78,6 +79,7 @@ struct BdConst {
   int law, precision, n_species;
   double a, sigma, L, wall_lo, wall_hi;
   double q, inv_q;
+  int qshift;              // q = 2^-qshift
   float alpha[4];
   double alpha_d[4];
   double eps, kappa, r_cut, skin;
@@ -97,6 +99,7 @@ cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t 
 cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, cudaStream_t s);
 cudaError_t bd_launch_dt(const BdDev &d, const BdConst &c, int mode, cudaStream_t s, int grid, int block);
 int bd_dt_grid(int *grid, int *block);
+int bd_dt_grid_for(int work_items, int *grid, int *block);
 int bd_force_blocks_per_sm(int variant);
 cudaError_t bd_launch_work_copy(const BdDev &d, const BdConst &c, cudaStream_t s);
 cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t s);

@@ -82,15 +82,20 @@ __device__ bool grid_sync(BdCtl *ctl, Bar &b) {
         __threadfence();
         atomicExch(&ctl->bar_gen, target);
       } else {
-        unsigned long long t0 = gtimer();
+        // spin hot for a while (barriers are short), then back off; give up
+        // after BD_BARRIER_TIMEOUT_NS
+        unsigned long long t0 = 0;
         unsigned it = 0;
         while (ld_acquire(&ctl->bar_gen) != target) {
-          if ((++it & 63u) == 0 && gtimer() - t0 > BD_BARRIER_TIMEOUT_NS) {
+          ++it;
+          if (it < 4096u) continue;
+          if (t0 == 0) t0 = gtimer();
+          if ((it & 63u) == 0 && gtimer() - t0 > BD_BARRIER_TIMEOUT_NS) {
             atomicExch(&ctl->status, BD_ERR_DEVICE_TIMEOUT);
             ok = 0;
             break;
           }
-          __nanosleep(40);
+          __nanosleep(64);
         }
       }
       __threadfence();
@@ -104,6 +109,24 @@ __device__ bool grid_sync(BdCtl *ctl, Bar &b) {
 }
 
 __device__ __forceinline__ int *cnt(BdCtl *ctl, int ph, int slot) { return &ctl->cnt[ph & 3][slot]; }
+
+// every block calls this once on its way out; the last one resets the barrier
+// words and phase counters so the next launch starts clean without a memset
+__device__ void block_exit(BdCtl *ctl) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned k = atomicAdd(&ctl->exit_count, 1u);
+    if (k == gridDim.x - 1) {
+      ctl->bar_count = 0;
+      ctl->bar_gen = 0;
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 8; ++b) ctl->cnt[a][b] = 0;
+      __threadfence();
+      ctl->exit_count = 0;
+    }
+  }
+}
 
 // reset the counters two phases ahead (see the rotation argument in BdCtl)
 __device__ __forceinline__ void phase_begin(BdCtl *ctl, const Bar &b) {
@@ -154,18 +177,42 @@ __device__ __forceinline__ float4 split_pos(double2 p) {
   return make_float4(xh, yh, __double2float_rn(p.x - (double)xh), __double2float_rn(p.y - (double)yh));
 }
 
-// flip the edge facing corner c0 (corner table, in place); returns the two
-// triangle ids.  Outer-neighbour entries of the two triangles are copied from
-// their old slots; the re-link phase makes them consistent.
-__device__ void flip_edge(const Ctx &x, int c0, int o0, int &t0, int &t1) {
-  t0 = c0 / 3;
-  int k0 = c0 % 3;
-  t1 = o0 / 3;
-  int k1 = o0 % 3;
+// Claim the six triangles that flipping the edge facing corner cc touches:
+// the pair and the four triangles across its outer edges.  An edge that
+// holds all six claims owns them for the round, so its flip can rewrite the
+// neighbours' back-pointers directly.
+__device__ __forceinline__ void claim6(const Ctx &x, int t, int k, const int4 &nn, int o,
+                                       unsigned long long key) {
+  const int t1 = o / 3, k1 = o % 3;
+  const int4 nn1 = x.d.tn[t1];
+  atomicMax(&x.d.claim[t], key);
+  atomicMax(&x.d.claim[t1], key);
+  int e[4] = {vk(nn, (k + 1) % 3), vk(nn, (k + 2) % 3), vk(nn1, (k1 + 1) % 3), vk(nn1, (k1 + 2) % 3)};
+  for (int m = 0; m < 4; ++m)
+    if (e[m] >= 0) atomicMax(&x.d.claim[e[m] / 3], key);
+}
+
+__device__ __forceinline__ bool owns6(const Ctx &x, int t0, int k0, const int4 &N0, int o0,
+                                      unsigned long long key) {
+  const int t1 = o0 / 3, k1 = o0 % 3;
+  if (x.d.claim[t1] != key) return false;
+  const int4 N1 = x.d.tn[t1];
+  int e[4] = {vk(N0, (k0 + 1) % 3), vk(N0, (k0 + 2) % 3), vk(N1, (k1 + 1) % 3), vk(N1, (k1 + 2) % 3)};
+  for (int m = 0; m < 4; ++m)
+    if (e[m] >= 0 && x.d.claim[e[m] / 3] != key) return false;
+  return true;
+}
+
+// Flip the edge facing corner c0 in place (the two triangle slots are reused)
+// and point the four outer neighbours, owned by this flip, at the new corners.
+// Quad a-b-d-c with t0 = (a, b, c), t1 = (d, c, b) becomes t0 = (b, d, a),
+// t1 = (c, a, d): the edge bc is replaced by ad.
+__device__ void flip_owned(const Ctx &x, int c0, int o0) {
+  const int t0 = c0 / 3, k0 = c0 % 3, t1 = o0 / 3, k1 = o0 % 3;
   int4 V0 = x.d.tv[t0], V1 = x.d.tv[t1], N0 = x.d.tn[t0], N1 = x.d.tn[t1];
-  int a = vk(V0, k0), b = vk(V0, (k0 + 1) % 3), c = vk(V0, (k0 + 2) % 3), dd = vk(V1, k1);
-  int n_ca = vk(N0, (k0 + 1) % 3), n_ab = vk(N0, (k0 + 2) % 3);
-  int n_bd = vk(N1, (k1 + 1) % 3), n_dc = vk(N1, (k1 + 2) % 3);
+  const int a = vk(V0, k0), b = vk(V0, (k0 + 1) % 3), c = vk(V0, (k0 + 2) % 3), dd = vk(V1, k1);
+  const int n_ca = vk(N0, (k0 + 1) % 3), n_ab = vk(N0, (k0 + 2) % 3);
+  const int n_bd = vk(N1, (k1 + 1) % 3), n_dc = vk(N1, (k1 + 2) % 3);
   set_vk(V0, k0, b);
   set_vk(V0, (k0 + 1) % 3, dd);
   set_vk(V0, (k0 + 2) % 3, a);
@@ -184,55 +231,49 @@ __device__ void flip_edge(const Ctx &x, int c0, int o0, int &t0, int &t1) {
   x.d.tv[t1] = V1;
   x.d.tn[t0] = N0;
   x.d.tn[t1] = N1;
+  if (n_ab >= 0) ((int *)&x.d.tn[n_ab / 3])[n_ab % 3] = 3 * t0 + (k0 + 1) % 3;
+  if (n_bd >= 0) ((int *)&x.d.tn[n_bd / 3])[n_bd % 3] = 3 * t0 + (k0 + 2) % 3;
+  if (n_dc >= 0) ((int *)&x.d.tn[n_dc / 3])[n_dc % 3] = 3 * t1 + (k1 + 1) % 3;
+  if (n_ca >= 0) ((int *)&x.d.tn[n_ca / 3])[n_ca % 3] = 3 * t1 + (k1 + 2) % 3;
 }
 
-// re-link the outer neighbours of a triangle flipped in round `epoch`
-__device__ void relink(const Ctx &x, int t, unsigned long long epoch) {
-  int4 V = x.d.tv[t];
-  int4 N = x.d.tn[t];
-  int partner = (int)(x.d.partner[t] & 0xFFFFFFFFull);
-  bool changed = false;
-  for (int k = 0; k < 3; ++k) {
-    int o = vk(N, k);
-    if (o < 0) continue;
-    int tt = o / 3;
-    if (tt == partner) continue;  // the new diagonal, already consistent
-    int u = vk(V, (k + 1) % 3), w = vk(V, (k + 2) % 3);
-    unsigned long long pw = x.d.partner[tt];
-    if ((pw >> 32) != epoch) {
-      // neighbour unchanged: its corner index is still valid; point it back
-      int *slot = ((int *)&x.d.tn[tt]) + (o % 3);
-      *slot = 3 * t + k;
-    } else {
-      // neighbour flipped too: find the triangle and corner now facing edge (w, u)
-      int cand[2] = {tt, (int)(pw & 0xFFFFFFFFull)};
-      for (int s = 0; s < 2; ++s) {
-        int4 W = x.d.tv[cand[s]];
-        for (int j = 0; j < 3; ++j) {
-          if (vk(W, (j + 1) % 3) == w && vk(W, (j + 2) % 3) == u) {
-            set_vk(N, k, 3 * cand[s] + j);
-            changed = true;
-          }
-        }
-      }
-    }
-  }
-  if (changed) x.d.tn[t] = N;
+__device__ __forceinline__ unsigned long long claim_key(unsigned long long epoch, int corner) {
+  return (epoch << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)corner);
+}
+__device__ __forceinline__ int key_corner(unsigned long long key) {
+  return (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
 }
 
 }  // namespace
 
-// mode 0: full step after the integrator; mode 1: repair + Lawson only
+// One time step's triangulation work (mode 0), or the repair of the
+// triangulation after new positions are set (mode 1, no overlap correction).
+//
+// Phases, each ended by a grid barrier:
+//   P  one pass over the triangles: orientation of triangles with a moved
+//      corner (inverted => flag), the reversal test on edges with a moved end,
+//      Lawson marks on edges touching a dirty triangle, and the overlap scan
+//      of every disk-disk edge.  The scan is used only when the pass found no
+//      inverted triangle and no illegal edge, i.e. when the triangulation it
+//      scanned is the Delaunay triangulation of the current positions.
+//   R  inversion repair rounds (candidate marks, owned flips) when P found an
+//      inverted triangle; then P again.
+//   F  owned Lawson flips of the marked edges; then P again.
+//   A  apply the capped displacements (Algorithm 2) and reflect; then P again.
 __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdConst c, int mode) {
   Ctx x;
   x.d = d;
   x.c = c;
   x.g.q = c.q;
   x.g.inv_q = c.inv_q;
+  x.g.s = c.qshift;
   x.T = c.nt;
   x.np = c.np;
   BdCtl *ctl = d.ctl;
-  if (ld_status(&ctl->status) != 0) return;
+  if (ld_status(&ctl->status) != 0) {
+    block_exit(ctl);
+    return;
+  }
   Bar b;
   b.gen = 0;
   b.ph = 0;
@@ -241,278 +282,258 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
   const bool lead = (blockIdx.x == 0 && threadIdx.x == 0);
   unsigned long long epoch = ctl->epoch;   // written only at kernel end by the lead thread
   const double sigma = c.sigma;
+  const double sigma2_hi = sigma * sigma * (1.0 + 1e-9);   // pre-test; the decision is sqrt(r2) < sigma
   int status = 0;
   int corr_iter = 0;
   long long st_overlap = 0, st_flips = 0, st_rflips = 0, st_inv = 0, st_rounds = 0;
-  bool first = true;
+  bool first = true;       // take the rollback snapshot in the first pass
+  bool fresh = true;       // the moved flags describe the latest move
+  int lawson_rounds = 0;
 
   for (;;) {
-    // ---------------- A: validity ----------------
+    ++epoch;
+    // ---------------- P: check, mark, scan ----------------
     phase_begin(ctl, b);
     {
-      int inv = 0, rej = 0;
+      int inv = 0, rej = 0, cand = 0, nov = 0;
+      double mx = 0.0;
       for (int t = tid; t < x.T; t += nth) {
-        int4 v = d.tv[t];
-        int4 nn = d.tn[t];
+        const int4 v = d.tv[t];
+        const int4 nn = d.tn[t];
         if (first) {
           int4 vs = v;
           vs.w = 0;
           d.tv_snap[t] = vs;
           d.tn_snap[t] = nn;
         }
-        bool dirty = d.moved[v.x] | d.moved[v.y] | d.moved[v.z];
-        if (dirty) {
-          int o = orient_v(x, v.x, v.y, v.z);
-          int fl = BD_TRI_DIRTY | (o <= 0 ? BD_TRI_INVERTED : 0);
-          inv += (o <= 0);
+        int fl = v.w;
+        if (fresh && (d.moved[v.x] | d.moved[v.y] | d.moved[v.z])) {
+          const int o = orient_v(x, v.x, v.y, v.z);
+          fl = BD_TRI_DIRTY | (o <= 0 ? BD_TRI_INVERTED : 0);
           d.tv[t].w = fl;
         }
-        // Sec. 4.3 first criterion on edges with a moved end point
+        const bool inverted = (fl & BD_TRI_INVERTED) != 0;
+        inv += inverted ? 1 : 0;
         for (int k = 0; k < 3; ++k) {
-          int cc = 3 * t + k;
-          int o = vk(nn, k);
-          if (o <= cc) continue;
-          int u = vk(v, (k + 1) % 3), w = vk(v, (k + 2) % 3);
-          if (u >= x.np || w >= x.np) continue;
-          if (!(d.moved[u] | d.moved[w])) continue;
-          double2 a0 = d.prev[u], b0 = d.prev[w], a1 = d.pos[u], b1 = d.pos[w];
-          double r0x = b0.x - a0.x, r0y = b0.y - a0.y, r1x = b1.x - a1.x, r1y = b1.y - a1.y;
-          if (r0x * r1x + r0y * r1y < 0.0) {
-            rej++;
-            atomicExch(&ctl->st_fail_item, cc);
+          const int cc = 3 * t + k;
+          const int o = vk(nn, k);
+          if (o <= cc) continue;   // each interior edge once, from its smaller corner
+          const int u = vk(v, (k + 1) % 3), w = vk(v, (k + 2) % 3);
+          const bool disks = u < x.np && w < x.np;
+          const bool mv = fresh && (d.moved[u] | d.moved[w]);
+          if (disks && mv) {
+            // Sec. 4.3 first criterion: r0 . r1 < 0, exact on the grid
+            const double2 a0 = d.prev[u], b0 = d.prev[w], a1 = d.pos[u], b1 = d.pos[w];
+            if (bdpred::dot_sign(a0.x, a0.y, b0.x, b0.y, a1.x, a1.y, b1.x, b1.y, x.g) < 0) {
+              ++rej;
+              atomicExch(&ctl->st_fail_item, cc);
+            }
+          }
+          if (inverted) continue;   // marks and scan wait for the repair
+          const int4 v1 = d.tv[o / 3];
+          const bool d1 = (v1.w & BD_TRI_DIRTY) ||
+                          (fresh && (d.moved[v1.x] | d.moved[v1.y] | d.moved[v1.z]));
+          if ((fl & BD_TRI_DIRTY) || d1) {
+            const int q = vk(v1, o % 3);
+            if (incircle_v(x, v.x, v.y, v.z, q) > 0) {
+              claim6(x, t, k, nn, o, claim_key(epoch, cc));
+              ++cand;
+            }
+          }
+          if (mode == 0 && disks) {
+            const double2 pu = d.pos[u], pw = d.pos[w];
+            const double dx = __dsub_rn(pw.x, pu.x), dy = __dsub_rn(pw.y, pu.y);
+            const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+            if (r2 <= sigma2_hi) {
+              const double r = sqrt(r2);
+              if (r < sigma) {
+                const double del = sigma - r;
+                const double nx = dx / r, ny = dy / r;
+                atomicAdd(&d.disp[u].x, -del * nx);
+                atomicAdd(&d.disp[u].y, -del * ny);
+                atomicAdd(&d.disp[w].x, del * nx);
+                atomicAdd(&d.disp[w].y, del * ny);
+                ++nov;
+                mx = fmax(mx, del);
+              }
+            }
           }
         }
       }
       block_add(cnt(ctl, b.ph, C_INV), inv);
       block_add(cnt(ctl, b.ph, C_REJECT), rej);
+      block_add(cnt(ctl, b.ph, C_CAND), cand);
+      block_add(cnt(ctl, b.ph, C_OVERLAP), nov);
+      if (mx > 0.0) atomicMax(&ctl->st_max_overlap_bits, (unsigned long long)__double_as_longlong(mx));
     }
+    if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
     first = false;
-    if (!grid_sync(ctl, b)) return;
-    int n_inv = *(volatile int *)cnt(ctl, b.ph - 1, C_INV);
-    int n_rej = *(volatile int *)cnt(ctl, b.ph - 1, C_REJECT);
-    st_inv += n_inv;
+    const int n_inv = *(volatile int *)cnt(ctl, b.ph - 1, C_INV);
+    const int n_rej = *(volatile int *)cnt(ctl, b.ph - 1, C_REJECT);
+    const int n_cand = *(volatile int *)cnt(ctl, b.ph - 1, C_CAND);
+    const int n_ov = *(volatile int *)cnt(ctl, b.ph - 1, C_OVERLAP);
     if (n_rej) {
       status = BD_ERR_STEP_REJECTED;
       if (lead) { ctl->st_fail_phase = 1; ctl->st_fail_count = n_rej; }
       break;
     }
 
-    // ---------------- R: inversion repair ----------------
-    int rounds = 0;
-    while (n_inv > 0) {
-      if (rounds++ >= c.max_flip_rounds) {
-        status = BD_ERR_STEP_REJECTED;
-        if (lead) { ctl->st_fail_phase = 3; ctl->st_fail_count = n_inv; }
-        break;
-      }
-      ++epoch;
-      // RM: candidates
-      phase_begin(ctl, b);
-      {
-        int ncand = 0;
-        for (int t = tid; t < x.T; t += nth) {
-          int4 v = d.tv[t];
-          if (!(v.w & BD_TRI_INVERTED)) continue;
-          atomicExch(&ctl->st_fail_item, t);
-          int4 nn = d.tn[t];
-          for (int k = 0; k < 3; ++k) {
-            int o = vk(nn, k);
-            if (o < 0) continue;
-            int p = vk(v, k), u = vk(v, (k + 1) % 3), w = vk(v, (k + 2) % 3);
-            int4 v1 = d.tv[o / 3];
-            int q = vk(v1, o % 3);
-            if (orient_v(x, u, q, p) > 0 && orient_v(x, w, p, q) > 0) {
-              int cm = min(3 * t + k, o);
-              unsigned long long key = (epoch << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)cm);
-              atomicMax(&d.claim[t], key);
-              atomicMax(&d.claim[o / 3], key);
-              ++ncand;
+    if (n_inv > 0) {
+      // ---------------- R: inversion repair (this pass's marks and scan are void) ----------------
+      st_inv += n_inv;
+      int rounds = 0;
+      bool first_round = true;
+      for (;;) {
+        ++epoch;
+        phase_begin(ctl, b);
+        {
+          if (first_round) {
+            for (int i = tid; i < x.np; i += nth) {
+              d.disp[i] = make_double2(0.0, 0.0);
+              d.moved[i] = 0;
             }
           }
+          int inv = 0, ncand = 0;
+          for (int t = tid; t < x.T; t += nth) {
+            const int4 v = d.tv[t];
+            if (!(v.w & BD_TRI_INVERTED)) continue;
+            ++inv;
+            atomicExch(&ctl->st_fail_item, t);
+            const int4 nn = d.tn[t];
+            for (int k = 0; k < 3; ++k) {
+              const int o = vk(nn, k);
+              if (o < 0) continue;
+              const int p = vk(v, k), u = vk(v, (k + 1) % 3), w = vk(v, (k + 2) % 3);
+              const int q = vk(d.tv[o / 3], o % 3);
+              // orientation form of Eq. (predicate): both triangles of the
+              // other diagonal strictly counter-clockwise
+              if (orient_v(x, u, q, p) > 0 && orient_v(x, w, p, q) > 0) {
+                const int cm = min(3 * t + k, o);
+                const int tt = cm / 3, kk = cm % 3;
+                const int4 ncm = d.tn[tt];
+                claim6(x, tt, kk, ncm, vk(ncm, kk), claim_key(epoch, cm));
+                ++ncand;
+              }
+            }
+          }
+          block_add(cnt(ctl, b.ph, C_INV), inv);
+          block_add(cnt(ctl, b.ph, C_CAND), ncand);
         }
-        block_add(cnt(ctl, b.ph, C_CAND), ncand);
-      }
-      if (!grid_sync(ctl, b)) return;
-      int n_cand = *(volatile int *)cnt(ctl, b.ph - 1, C_CAND);
-      if (n_cand == 0) {
-        status = BD_ERR_STEP_REJECTED;
-        if (lead) { ctl->st_fail_phase = 2; ctl->st_fail_count = n_inv; }
-        break;
-      }
-      // RF: winners flip
-      phase_begin(ctl, b);
-      {
-        int nf = 0;
-        for (int t = tid; t < x.T; t += nth) {
-          unsigned long long key = d.claim[t];
-          if ((key >> 32) != epoch) continue;
-          int cm = (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
-          if (cm / 3 != t) continue;
-          int o = ((const int *)&d.tn[t])[cm % 3];
-          if (d.claim[o / 3] != key) continue;
-          int t0, t1;
-          flip_edge(x, cm, o, t0, t1);
-          d.partner[t0] = (epoch << 32) | (unsigned)t1;
-          d.partner[t1] = (epoch << 32) | (unsigned)t0;
-          int4 V0 = d.tv[t0], V1 = d.tv[t1];
-          if (orient_v(x, V0.x, V0.y, V0.z) <= 0) d.tv[t0].w = BD_TRI_DIRTY | BD_TRI_INVERTED;
-          if (orient_v(x, V1.x, V1.y, V1.z) <= 0) d.tv[t1].w = BD_TRI_DIRTY | BD_TRI_INVERTED;
-          ++nf;
+        if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+        first_round = false;
+        const int ni = *(volatile int *)cnt(ctl, b.ph - 1, C_INV);
+        const int nc = *(volatile int *)cnt(ctl, b.ph - 1, C_CAND);
+        if (ni == 0) break;
+        if (nc == 0 || rounds++ >= c.max_flip_rounds) {
+          status = BD_ERR_STEP_REJECTED;
+          if (lead) { ctl->st_fail_phase = nc == 0 ? 2 : 3; ctl->st_fail_count = ni; }
+          break;
         }
-        block_add(cnt(ctl, b.ph, C_FLIPS), nf);
-      }
-      if (!grid_sync(ctl, b)) return;
-      st_rflips += *(volatile int *)cnt(ctl, b.ph - 1, C_FLIPS);
-      // RX: re-link and recount
-      phase_begin(ctl, b);
-      {
-        int inv = 0;
-        for (int t = tid; t < x.T; t += nth) {
-          if ((d.partner[t] >> 32) == epoch) relink(x, t, epoch);
-          inv += (d.tv[t].w & BD_TRI_INVERTED) ? 1 : 0;
+        phase_begin(ctl, b);
+        {
+          int nf = 0;
+          for (int t = tid; t < x.T; t += nth) {
+            const unsigned long long key = d.claim[t];
+            if ((key >> 32) != epoch) continue;
+            const int cm = key_corner(key);
+            if (cm / 3 != t) continue;
+            const int4 N0 = d.tn[t];
+            const int o = vk(N0, cm % 3);
+            if (!owns6(x, t, cm % 3, N0, o, key)) continue;
+            flip_owned(x, cm, o);   // both new triangles are counter-clockwise by the rule
+            ++nf;
+          }
+          block_add(cnt(ctl, b.ph, C_FLIPS), nf);
         }
-        block_add(cnt(ctl, b.ph, C_INV), inv);
+        if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+        st_rflips += *(volatile int *)cnt(ctl, b.ph - 1, C_FLIPS);
       }
-      if (!grid_sync(ctl, b)) return;
-      n_inv = *(volatile int *)cnt(ctl, b.ph - 1, C_INV);
+      if (status) break;
+      fresh = false;
+      continue;
     }
-    if (status) break;
 
-    // ---------------- L: Lawson flips ----------------
-    rounds = 0;
-    for (;;) {
-      if (rounds++ >= c.max_flip_rounds) {
+    if (n_cand > 0) {
+      // ---------------- F: owned Lawson flips ----------------
+      if (lawson_rounds++ >= c.max_flip_rounds) {
         status = BD_ERR_FLIP_NOT_CONVERGED;
         if (lead) ctl->st_fail_phase = 4;
         break;
       }
-      ++epoch;
-      phase_begin(ctl, b);
-      for (int t = tid; t < x.T; t += nth) {
-        int4 v = d.tv[t];
-        int4 nn = d.tn[t];
-        for (int k = 0; k < 3; ++k) {
-          int cc = 3 * t + k;
-          int o = vk(nn, k);
-          if (o <= cc) continue;
-          int4 v1 = d.tv[o / 3];
-          if (!((v.w | v1.w) & BD_TRI_DIRTY)) continue;
-          int q = vk(v1, o % 3);
-          if (incircle_v(x, v.x, v.y, v.z, q) > 0) {
-            unsigned long long key = (epoch << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)cc);
-            atomicMax(&d.claim[t], key);
-            atomicMax(&d.claim[o / 3], key);
-          }
-        }
-      }
-      if (!grid_sync(ctl, b)) return;
       phase_begin(ctl, b);
       {
+        for (int i = tid; i < x.np; i += nth) {
+          d.disp[i] = make_double2(0.0, 0.0);   // this pass's scan is void
+          if (fresh) d.moved[i] = 0;
+        }
         int nf = 0;
         for (int t = tid; t < x.T; t += nth) {
-          unsigned long long key = d.claim[t];
+          const unsigned long long key = d.claim[t];
           if ((key >> 32) == epoch) {
-            // claimed this round: either this triangle's edge flips, or it
-            // stays dirty so a losing illegal edge is tested again next round
-            int cm = (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
+            const int cm = key_corner(key);
             if (cm / 3 == t) {
-              int o = ((const int *)&d.tn[t])[cm % 3];
-              if (d.claim[o / 3] == key) {
-                int t0, t1;
-                flip_edge(x, cm, o, t0, t1);
-                d.partner[t0] = (epoch << 32) | (unsigned)t1;
-                d.partner[t1] = (epoch << 32) | (unsigned)t0;
+              const int4 N0 = d.tn[t];
+              const int o = vk(N0, cm % 3);
+              if (owns6(x, t, cm % 3, N0, o, key)) {
+                flip_owned(x, cm, o);
                 ++nf;
               }
             }
+            // claimed but not flipped: stays dirty, its edges are tested again
           } else if (d.tv[t].w & BD_TRI_DIRTY) {
-            // every edge of this triangle was tested and found legal
-            d.tv[t].w = 0;
+            d.tv[t].w = 0;   // every edge of it was tested and found legal
           }
         }
         block_add(cnt(ctl, b.ph, C_FLIPS), nf);
       }
-      if (!grid_sync(ctl, b)) return;
-      int nf = *(volatile int *)cnt(ctl, b.ph - 1, C_FLIPS);
-      if (nf == 0) break;
-      st_flips += nf;
+      if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+      st_flips += *(volatile int *)cnt(ctl, b.ph - 1, C_FLIPS);
       st_rounds += 1;
-      phase_begin(ctl, b);
-      for (int t = tid; t < x.T; t += nth)
-        if ((d.partner[t] >> 32) == epoch) relink(x, t, epoch);
-      if (!grid_sync(ctl, b)) return;
+      fresh = false;
+      continue;
     }
-    if (status) break;
-    if (mode == 1) break;
 
-    // ---------------- O: overlap scan ----------------
-    phase_begin(ctl, b);
-    {
-      int nov = 0;
-      double mx = 0.0;
-      for (int i = tid; i < x.np; i += nth) d.moved[i] = 0;
-      for (int t = tid; t < x.T; t += nth) {
-        int4 v = d.tv[t];
-        int4 nn = d.tn[t];
-        for (int k = 0; k < 3; ++k) {
-          int cc = 3 * t + k;
-          int o = vk(nn, k);
-          if (o <= cc) continue;
-          int u = vk(v, (k + 1) % 3), w = vk(v, (k + 2) % 3);
-          if (u >= x.np || w >= x.np) continue;
-          double2 pu = d.pos[u], pw = d.pos[w];
-          double dx = __dsub_rn(pw.x, pu.x), dy = __dsub_rn(pw.y, pu.y);
-          double r = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-          if (r < sigma) {
-            double del = sigma - r;
-            double nx = dx / r, ny = dy / r;
-            atomicAdd(&d.disp[u].x, -del * nx);
-            atomicAdd(&d.disp[u].y, -del * ny);
-            atomicAdd(&d.disp[w].x, del * nx);
-            atomicAdd(&d.disp[w].y, del * ny);
-            ++nov;
-            mx = fmax(mx, del);
-          }
-        }
-      }
-      block_add(cnt(ctl, b.ph, C_OVERLAP), nov);
-      if (mx > 0.0) atomicMax(&ctl->st_max_overlap_bits, (unsigned long long)__double_as_longlong(mx));
-    }
-    if (!grid_sync(ctl, b)) return;
-    int n_ov = *(volatile int *)cnt(ctl, b.ph - 1, C_OVERLAP);
-    if (n_ov == 0) break;
-    st_overlap += n_ov;
+    // Delaunay triangulation of the current positions: the scan is valid
+    if (mode == 1 || n_ov == 0) break;
     if (corr_iter >= c.max_corr_iters) {
       status = BD_ERR_OVERLAP_NOT_CONVERGED;
       if (lead) ctl->st_fail_phase = 5;
       break;
     }
     ++corr_iter;
-    // ---------------- O: apply (capped at sigma/4) ----------------
+    st_overlap += n_ov;
+    lawson_rounds = 0;
+    // ---------------- A: apply (capped at sigma/4) ----------------
     phase_begin(ctl, b);
     {
       const double cap = 0.25 * sigma;
       for (int i = tid; i < x.np; i += nth) {
         if (d.ext_id[i] < 0) continue;
-        double2 p = d.pos[i];
+        const double2 p = d.pos[i];
         d.prev[i] = p;
-        double2 dd = d.disp[i];
-        if (dd.x == 0.0 && dd.y == 0.0) continue;
-        double mag = sqrt(__dadd_rn(__dmul_rn(dd.x, dd.x), __dmul_rn(dd.y, dd.y)));
-        double s = mag > cap ? cap / mag : 1.0;
-        double nxp = snap(p.x + dd.x * s, x.g), nyp = snap(p.y + dd.y * s, x.g);
+        const double2 dd = d.disp[i];
+        if (dd.x == 0.0 && dd.y == 0.0) {
+          d.moved[i] = 0;
+          continue;
+        }
+        const double mag = sqrt(__dadd_rn(__dmul_rn(dd.x, dd.x), __dmul_rn(dd.y, dd.y)));
+        const double sc = mag > cap ? cap / mag : 1.0;
+        double nxp = snap(p.x + dd.x * sc, x.g), nyp = snap(p.y + dd.y * sc, x.g);
         if (nxp < c.wall_lo) nxp = 2.0 * c.wall_lo - nxp;
         if (nxp > c.wall_hi) nxp = 2.0 * c.wall_hi - nxp;
         if (nyp < c.wall_lo) nyp = 2.0 * c.wall_lo - nyp;
         if (nyp > c.wall_hi) nyp = 2.0 * c.wall_hi - nyp;
-        double2 np2 = make_double2(nxp, nyp);
+        const double2 np2 = make_double2(nxp, nyp);
         d.pos[i] = np2;
         d.work[i] = split_pos(np2);
         d.disp[i] = make_double2(0.0, 0.0);
         d.moved[i] = 1;
       }
+      for (int t = tid; t < x.T; t += nth)
+        if (d.tv[t].w) d.tv[t].w = 0;
     }
-    if (!grid_sync(ctl, b)) return;
+    if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+    fresh = true;
   }
 
   if (status) {
@@ -520,7 +541,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
     phase_begin(ctl, b);
     for (int i = tid; i < x.np; i += nth) {
       if (d.ext_id[i] < 0) continue;
-      double2 p0 = d.pos0[i];
+      const double2 p0 = d.pos0[i];
       d.pos[i] = p0;
       d.prev[i] = p0;
       d.work[i] = split_pos(p0);
@@ -544,9 +565,24 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
     ctl->st_repair_flips += st_rflips;
     ctl->st_inverted += st_inv;
     ctl->st_flip_rounds += st_rounds;
+    ctl->st_barriers += b.gen;
     if (corr_iter > ctl->st_max_corr_iters) ctl->st_max_corr_iters = corr_iter;
     if (!status) ctl->st_steps += 1;
   }
+  block_exit(ctl);
+}
+
+int bd_dt_grid_for(int work_items, int *grid, int *block) {
+  // all co-resident blocks (the phases are latency-bound chains of dependent
+  // loads and integer predicates, so more threads in flight help), but no
+  // more than about one work item per thread
+  int g = 0, b = 0;
+  if (bd_dt_grid(&g, &b) != 0) return -1;
+  int want = (work_items + b - 1) / b;
+  if (want < 1) want = 1;
+  *grid = want < g ? want : g;
+  *block = b;
+  return 0;
 }
 
 int bd_dt_grid(int *grid, int *block) {
@@ -564,11 +600,8 @@ int bd_dt_grid(int *grid, int *block) {
 
 cudaError_t bd_launch_dt(const BdDev &d, const BdConst &c, int mode, cudaStream_t s, int grid,
                          int block) {
-  // fresh barrier state for this launch
-  cudaError_t e = cudaMemsetAsync(d.ctl, 0, 2 * sizeof(unsigned int), s);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(&d.ctl->cnt[0][0], 0, sizeof(d.ctl->cnt), s);
-  if (e != cudaSuccess) return e;
+  // the barrier words and phase counters were reset by the previous
+  // launch's last block (and zeroed at allocation)
   BdDev dd = d;
   BdConst cc = c;
   int m = mode;

@@ -12,11 +12,17 @@
 // whenever they are written).  Coordinates then convert exactly to int64 and
 //   orient2d  = bax*cay - bay*cax            |.| < 2^105  -> signed 128-bit
 //   incircle  = sum lift_k * minor_k         |.| < 2^213  -> signed 256-bit
-// are evaluated in fixed-width integer arithmetic.  A plain FP64 evaluation
-// with a conservative error bound decides the clear cases first; the integer
-// path runs only when the FP64 value is within the bound of zero.
+// are evaluated in fixed-width integer arithmetic.  On the host a plain FP64
+// evaluation with a conservative error bound decides the clear cases first and
+// the integer path runs only when the FP64 value is within the bound of zero.
+// On the GPU the integer path always runs: on this part FP64 issues at about
+// 1/64 of the FP32/INT32 rate, so the filter costs more than the exact
+// evaluation it would skip (BD_PRED_DEVICE_FILTER=1 restores it).  The grid
+// integer of a coordinate is read from its bit pattern (mantissa shifted by
+// exponent + s), with no floating-point operation.
 #pragma once
 #include <stdint.h>
+#include <string.h>
 
 #if defined(__CUDACC__)
 #define BD_HD __host__ __device__ __forceinline__
@@ -203,15 +209,23 @@ BD_HD int incircle_int(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t c
 struct Grid {
   double q;      // grid step 2^-s
   double inv_q;  // 2^s
+  int s;
 };
 
+// x / q for a grid value x (exact: x = m 2^(e-1075), so x / q = m 2^(e-1075+s))
 BD_HD int64_t to_int(double x, const Grid &g) {
+  uint64_t b;
 #if defined(__CUDA_ARCH__)
-  return __double2ll_rn(dmul(x, g.inv_q));
+  b = (uint64_t)__double_as_longlong(x);
 #else
-  double v = x * g.inv_q;
-  return (int64_t)(v < 0 ? v - 0.5 : v + 0.5);
+  memcpy(&b, &x, sizeof(b));
 #endif
+  const int e = (int)((b >> 52) & 0x7FFu);
+  if (e == 0) return 0;  // zero (the grid holds no subnormal values)
+  const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = e - 1075 + g.s;
+  const uint64_t v = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+  return (b >> 63) ? -(int64_t)v : (int64_t)v;
 }
 
 // --- filtered predicates on grid doubles ------------------------------------------
@@ -222,9 +236,17 @@ BD_HD int64_t to_int(double x, const Grid &g) {
 #ifndef BD_PRED_FILTER
 #define BD_PRED_FILTER 1
 #endif
+#ifndef BD_PRED_DEVICE_FILTER
+#define BD_PRED_DEVICE_FILTER 0
+#endif
+#if defined(__CUDA_ARCH__)
+#define BD_USE_FILTER (BD_PRED_FILTER && BD_PRED_DEVICE_FILTER)
+#else
+#define BD_USE_FILTER BD_PRED_FILTER
+#endif
 
 BD_HD int orient(double ax, double ay, double bx, double by, double cx, double cy, const Grid &g) {
-#if BD_PRED_FILTER
+#if BD_USE_FILTER
   double l = dmul(dsub(bx, ax), dsub(cy, ay));
   double r = dmul(dsub(by, ay), dsub(cx, ax));
   double det = dsub(l, r);
@@ -238,7 +260,7 @@ BD_HD int orient(double ax, double ay, double bx, double by, double cx, double c
 
 BD_HD int incircle(double ax, double ay, double bx, double by, double cx, double cy, double px,
                    double py, const Grid &g) {
-#if BD_PRED_FILTER
+#if BD_USE_FILTER
   double adx = dsub(ax, px), ady = dsub(ay, py);
   double bdx = dsub(bx, px), bdy = dsub(by, py);
   double cdx = dsub(cx, px), cdy = dsub(cy, py);
@@ -257,6 +279,14 @@ BD_HD int incircle(double ax, double ay, double bx, double by, double cx, double
 #endif
   return incircle_int(to_int(ax, g), to_int(ay, g), to_int(bx, g), to_int(by, g), to_int(cx, g),
                       to_int(cy, g), to_int(px, g), to_int(py, g));
+}
+
+// exact sign of the dot product (b0 - a0) . (b1 - a1) of two grid vectors
+BD_HD int dot_sign(double a0x, double a0y, double b0x, double b0y, double a1x, double a1y,
+                   double b1x, double b1y, const Grid &g) {
+  int64_t ux = to_int(b0x, g) - to_int(a0x, g), uy = to_int(b0y, g) - to_int(a0y, g);
+  int64_t vx = to_int(b1x, g) - to_int(a1x, g), vy = to_int(b1y, g) - to_int(a1y, g);
+  return sign128(add128(smul64(ux, vx), smul64(uy, vy)));
 }
 
 }  // namespace bdpred
