@@ -348,6 +348,18 @@ int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_i
   c.q = q;
   c.inv_q = inv_q;
   c.qshift = s;
+  {
+    // (sigma/q)^2 (1 + 1e-9), rounded up, as a 128-bit integer
+    long double sq = (long double)(2.0 * p.a) * (long double)inv_q;
+    long double v = sq * sq * (1.0L + 1e-9L);
+    long double two64 = 18446744073709551616.0L;
+    unsigned long long hi = (unsigned long long)(v / two64);
+    long double rem = v - (long double)hi * two64;
+    unsigned long long lo = (unsigned long long)rem;
+    if ((long double)lo < rem) ++lo;
+    c.sig2q_hi = hi;
+    c.sig2q_lo = lo;
+  }
   for (int k = 0; k < 4; ++k) {
     c.alpha[k] = (float)p.alpha[k];
     c.alpha_d[k] = p.alpha[k];

@@ -80,6 +80,7 @@ struct BdConst {
   double a, sigma, L, wall_lo, wall_hi;
   double q, inv_q;
   int qshift;              // q = 2^-qshift
+  unsigned long long sig2q_hi, sig2q_lo;  // ceil((sigma/q)^2 (1 + 1e-9)) as 128-bit
   float alpha[4];
   double alpha_d[4];
   double eps, kappa, r_cut, skin;

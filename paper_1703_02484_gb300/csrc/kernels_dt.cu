@@ -282,7 +282,6 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
   const bool lead = (blockIdx.x == 0 && threadIdx.x == 0);
   unsigned long long epoch = ctl->epoch;   // written only at kernel end by the lead thread
   const double sigma = c.sigma;
-  const double sigma2_hi = sigma * sigma * (1.0 + 1e-9);   // pre-test; the decision is sqrt(r2) < sigma
   int status = 0;
   int corr_iter = 0;
   long long st_overlap = 0, st_flips = 0, st_rflips = 0, st_inv = 0, st_rounds = 0;
@@ -342,9 +341,15 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
           }
           if (mode == 0 && disks) {
             const double2 pu = d.pos[u], pw = d.pos[w];
-            const double dx = __dsub_rn(pw.x, pu.x), dy = __dsub_rn(pw.y, pu.y);
-            const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-            if (r2 <= sigma2_hi) {
+            // exact pre-test in grid units: |r_w - r_u|^2 <= (sigma/q)^2 (1 + 1e-9)
+            const int64_t ix = bdpred::to_int(pw.x, x.g) - bdpred::to_int(pu.x, x.g);
+            const int64_t iy = bdpred::to_int(pw.y, x.g) - bdpred::to_int(pu.y, x.g);
+            const bdpred::i128 ir2 = bdpred::add128(bdpred::smul64(ix, ix), bdpred::smul64(iy, iy));
+            const bool near = ir2.hi < c.sig2q_hi || (ir2.hi == c.sig2q_hi && ir2.lo <= c.sig2q_lo);
+            if (near) {
+              // the decision itself as the FP64 reference makes it
+              const double dx = __dsub_rn(pw.x, pu.x), dy = __dsub_rn(pw.y, pu.y);
+              const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
               const double r = sqrt(r2);
               if (r < sigma) {
                 const double del = sigma - r;

@@ -6,7 +6,8 @@
 //     - eps (s/r) exp(-kappa (r - s)),
 //   F_i = sum_j -U'(r_ij) (r_i - r_j)/r_ij   for r_ij < r_cut.
 // The tail is evaluated in FP32; the WCA core, whose r^-13 force near contact
-// turns FP32 rounding into errors above 1e-5 of the net force, in FP64.
+// turns FP32 rounding into errors above 1e-5 of the net force, in float-float
+// FP32 arithmetic (FP64 issues at ~1/64 of the FP32 rate on this part).
 //
 // Lists: every disk keeps the disks within r_cut + skin of it, decided in
 // FP64 as (x_i - x_j)^2 + (y_i - y_j)^2 < (r_cut + skin)^2 with two products
@@ -27,6 +28,41 @@
 #define BD_SCAN_B 512
 
 namespace {
+
+// float-float arithmetic (value = hi + lo, |lo| <= ulp(hi)/2), about 48
+// significant bits from FP32 instructions only
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_make(float a, float b) {  // exact a + b, |a| >= |b| not required
+  float s = __fadd_rn(a, b);
+  float bp = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+  return {s, e};
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float s = __fadd_rn(p, e);
+  return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = ff_make(a.hi, b.hi);
+  float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  float h = __fadd_rn(s.hi, lo);
+  return {h, __fsub_rn(lo, __fsub_rn(h, s.hi))};
+}
+__device__ __forceinline__ ff ff_scale(ff a, float b) { return ff_mul(a, {b, 0.f}); }
+// a / b: FP32 quotient refined by one float-float residual step
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  ff r = ff_add(a, ff_scale(b, -q1));
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  float s = __fadd_rn(q1, q2);
+  return {s, __fsub_rn(q2, __fsub_rn(s, q1))};
+}
 
 __device__ __forceinline__ int failed(const BdCtl *ctl) { return *(volatile const int *)&ctl->status; }
 __device__ __forceinline__ int need(const BdCtl *ctl) { return *(volatile const int *)&ctl->vl_need; }
@@ -210,9 +246,8 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
   const float rc2 = (float)(c.r_cut * c.r_cut);
   const float sg = (float)c.sigma, eps = (float)c.eps, kap = (float)c.kappa;
   const float rwca2 = (float)(1.2599210498948732 * c.sigma * c.sigma);  // (2^(1/6) s)^2
-  const double s2c = c.sigma * c.sigma, e24 = 24.0 * c.eps;
   float fx = 0.f, fy = 0.f;      // Yukawa tail, FP32
-  double gx = 0.0, gy = 0.0;     // WCA core, FP64
+  ff gx = {0.f, 0.f}, gy = {0.f, 0.f};   // WCA core, float-float sums
   for (int t = 0; t < m; ++t) {
     int j = d.vl_idx[(size_t)t * c.np + i];
     float4 wj = d.work[j];
@@ -235,19 +270,23 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
     fx = fmaf(my, dx, fx);
     fy = fmaf(my, dy, fy);
     if (r2 < rwca2) {
-      // WCA core near contact: -U'(r) ~ r^-13 amplifies rounding, so FP64
-      // from the master positions (no square root needed)
-      double2 pj = d.pos[j];
-      double ex = pi.x - pj.x, ey = pi.y - pj.y;
-      double q2 = ex * ex + ey * ey;
-      double s2 = s2c / q2;
-      double s6 = s2 * s2 * s2;
-      double cw = e24 * (2.0 * s6 * s6 - s6) / q2;
-      gx += cw * ex;
-      gy += cw * ey;
+      // WCA core near contact: -U'(r) ~ r^-13 turns FP32 rounding into
+      // errors above 1e-5 of the net force, so the core is evaluated in
+      // float-float arithmetic (FP32 instructions, ~48-bit significands) from
+      // the exact coordinate differences
+      ff ex = ff_make(__fsub_rn(wi.x, wj.x), __fsub_rn(wi.z, wj.z));
+      ff ey = ff_make(__fsub_rn(wi.y, wj.y), __fsub_rn(wi.w, wj.w));
+      ff q2 = ff_add(ff_mul(ex, ex), ff_mul(ey, ey));
+      ff s2 = ff_div({sg * sg, 0.f}, q2);
+      ff s6 = ff_mul(ff_mul(s2, s2), s2);
+      ff t = ff_add(ff_scale(ff_mul(s6, s6), 2.0f), {-s6.hi, -s6.lo});
+      ff cw = ff_div(ff_scale(t, 24.0f * eps), q2);
+      gx = ff_add(gx, ff_mul(cw, ex));
+      gy = ff_add(gy, ff_mul(cw, ey));
     }
   }
-  d.fpart[i] = make_double2((double)fx + gx, (double)fy + gy);
+  d.fpart[i] = make_double2((double)fx + (double)gx.hi + (double)gx.lo,
+                            (double)fy + (double)gy.hi + (double)gy.lo);
 }
 
 cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t s) {
