@@ -142,6 +142,38 @@ int bd_init(const bd_params *p, const double *xy, const uint8_t *species, const 
  * BD_ERR_CUDA, BD_ERR_ARG (nsteps < 0). */
 int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats);
 
+/* Batched replicas (no counterpart in the paper; it serves ensembles of
+ * independent systems).  R systems of possibly different N, box, law and
+ * parameters advance together: every kernel launch of a step works on all of
+ * them (the all-pairs sweep over a work list of (replica, i block, j chunk)
+ * items whose chunk size and kernel variant an autotuner picks at init by
+ * timing), so a step costs one launch sequence however many replicas there
+ * are.  All replicas must share the disk radius a, precision and loop caps.
+ *   R        number of replicas (>= 1).
+ *   p        R parameter sets; replica r draws its noise from key (p[r].seed,
+ *            p[r].replica), so a replica evolves exactly as bd_init would
+ *            advance it alone.
+ *   xy, species, theta   concatenated per-replica arrays in replica order
+ *            (2*sum n, sum n, sum n) or NULL (each replica: RSA from its seed,
+ *            species 0, theta 0).
+ * bd_step, bd_get_state, bd_set_state and bd_compute_forces then act on the
+ * concatenation (external index = replica offset + index within replica);
+ * bd_get_replica returns one replica in its own ids.
+ * Errors: as bd_init. */
+int bd_batch_init(int32_t R, const bd_params *p, const double *xy, const uint8_t *species,
+                  const float *theta, void *stream, bd_handle **out);
+
+/* One replica of a handle in its own numbering: xy (2n), theta (n), tri
+ * (3*n_tri; disks 0..n-1, then its ghost points in bd_ghost_points order),
+ * its disk count n and box side L.  Any output may be NULL.
+ * Errors: BD_ERR_ARG (bad r), BD_ERR_CUDA. */
+int bd_get_replica(bd_handle *h, int32_t r, double *xy, float *theta, int32_t *tri, int32_t *n_tri,
+                   int32_t *n, double *L);
+
+/* The all-pairs sweep's tuning: j tiles (256 disks each) per work item, the
+ * kernel variant (0 scalar FP32, 1 packed f32x2) and the number of work items. */
+int bd_get_tuning(bd_handle *h, int32_t *tiles_per_item, int32_t *variant, int32_t *n_items);
+
 /* Copy the current state to host memory ("Ensure P updated to current
  * time", Algorithm 1).  Any pointer may be NULL to skip that output.
  *   xy       2n doubles, external disk order.

@@ -71,6 +71,12 @@ SIGNATURES = [
     ("bd_forces_noalloc", ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_double),
                                          _P, _P]),
     ("bd_get_neighbors", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    ("bd_batch_init", ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(bd_params), _P, _P, _P, _P,
+                                     ctypes.POINTER(_P)]),
+    ("bd_get_replica", ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
+    ("bd_get_tuning", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int32)]),
     ("bd_free", None, [_P]),
     ("bd_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -145,24 +151,38 @@ def params_from_config(cfg, n=None, seed=None):
 
 
 class System:
-    """One simulated system behind a bd_handle."""
+    """One simulated system (or a batch of replicas) behind a bd_handle."""
 
     def __init__(self, params, xy=None, species=None, theta=None, stream=None):
         lib = load()
-        self.n = params.n
+        batch = isinstance(params, (list, tuple))
+        plist = list(params) if batch else [params]
+        self.R = len(plist)
+        self.n = int(sum(p.n for p in plist))
         self._xy = None if xy is None else np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
         self._sp = None if species is None else np.ascontiguousarray(species, dtype=np.uint8)
         self._th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
         h = ctypes.c_void_p()
         st = None if stream is None else ctypes.c_void_p(int(stream))
-        _check(lib.bd_init(ctypes.byref(params), _ptr(self._xy), _ptr(self._sp), _ptr(self._th),
-                           st, ctypes.byref(h)), "bd_init")
+        if batch:
+            arr = (bd_params * self.R)(*plist)
+            self._plist = arr
+            _check(lib.bd_batch_init(self.R, arr, _ptr(self._xy), _ptr(self._sp), _ptr(self._th),
+                                     st, ctypes.byref(h)), "bd_batch_init")
+        else:
+            _check(lib.bd_init(ctypes.byref(params), _ptr(self._xy), _ptr(self._sp),
+                               _ptr(self._th), st, ctypes.byref(h)), "bd_init")
         self.h = h
         self.params = params
         q, L = self.geometry()
         self.L = L
-        self.ghosts = ghost_points(L, params.a)
-        self.n_tri = 2 * (self.n + len(self.ghosts)) - 6
+        self.n_tri = 0
+        for r in range(self.R):
+            nn, nt, LL = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+            _check(lib.bd_get_replica(self.h, r, None, None, None, ctypes.byref(nt), ctypes.byref(nn),
+                                      ctypes.byref(LL)), "bd_get_replica")
+            self.n_tri += nt.value
+        self.ghosts = ghost_points(L, plist[0].a)
 
     def close(self):
         if self.h:
@@ -214,6 +234,25 @@ class System:
         _check(load().bd_force_timing(self.h, int(enable), int(reset), ctypes.byref(ms),
                                       ctypes.byref(k)), "bd_force_timing")
         return ms.value, k.value
+
+    def replica(self, r):
+        """State of replica r in its own numbering: dict(xy, theta, tri, n, L)."""
+        lib = load()
+        nn, nt, LL = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(lib.bd_get_replica(self.h, int(r), None, None, None, ctypes.byref(nt),
+                                  ctypes.byref(nn), ctypes.byref(LL)), "bd_get_replica")
+        xy = np.zeros((nn.value, 2))
+        th = np.zeros(nn.value, dtype=np.float32)
+        tri = np.zeros((nt.value, 3), dtype=np.int32)
+        _check(lib.bd_get_replica(self.h, int(r), _ptr(xy), _ptr(th), _ptr(tri), ctypes.byref(nt),
+                                  ctypes.byref(nn), ctypes.byref(LL)), "bd_get_replica")
+        return dict(xy=xy, theta=th, tri=tri, n=nn.value, L=LL.value)
+
+    def tuning(self):
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().bd_get_tuning(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "bd_get_tuning")
+        return dict(tiles_per_item=a.value, variant=b.value, n_items=c.value)
 
     def neighbors(self, max_per=64):
         n = self.n

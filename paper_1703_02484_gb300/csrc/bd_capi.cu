@@ -1,6 +1,13 @@
 // C-ABI layer: handle lifetime, host-side set-up, the per-step launch
 // sequence and state transfer.  See include/bd.h for the contract of each
 // entry point.
+//
+// A handle advances R >= 1 independent replicas (a single system is R = 1).
+// Replicas are concatenated: each owns a contiguous range of internal disk
+// slots, its own ghost points (after all disks), its own triangles, j tiles,
+// force i blocks and Verlet cells; per-replica parameters live in a device
+// table (BdRep).  Every kernel works on the union, so one launch of each
+// kernel advances every replica.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -26,25 +33,45 @@ int any_overlap(int n, const double *xy, double lo, double hi, double dmin);
 uint64_t hilbert_index(uint32_t x, uint32_t y);
 }  // namespace bdhost
 
-struct bd_handle {
+namespace {
+
+struct RepHost {
   bd_params p;
+  double L = 0, wall_lo = 0, wall_hi = 0;
+  int n = 0;                   // disks
+  int ext_base = 0;            // first index in the concatenated external arrays
+  int slot_begin = 0, slot_end = 0;
+  int ghost_base = 0, ng = 0;  // ghost vertex ids ghost_base .. ghost_base + ng - 1
+  int tri_base = 0, nt = 0;
+  int iblock_base = 0, n_iblocks = 0;
+  int tile_begin = 0, tile_end = 0;
+};
+
+}  // namespace
+
+struct bd_handle {
   cudaStream_t stream = nullptr;
   BdDev d;
   BdConst c;
+  std::vector<RepHost> reps;
+  std::vector<BdRep> h_rep;
   int n = 0, np = 0, np_i = 0, nt = 0, ng = 0;
-  std::vector<int> ext_of_int;  // np (-1 = empty slot)
-  std::vector<int> int_of_ext;  // n
-  std::vector<double> host_pos; // (np + ng) * 2 mirror used for uploads (empty slots, ghost points)
+  std::vector<int> ext_of_int;    // internal slot -> concatenated external index (-1 = empty)
+  std::vector<int> int_of_ext;    // concatenated external index -> internal slot
+  std::vector<double> host_pos;   // (np + ng) * 2 mirror used for uploads
   int dt_grid = 0, dt_block = 0;
   int64_t step = 0;
   double2 *d_fsum = nullptr;
-  BdCtl *h_ctl = nullptr;       // pinned
+  BdCtl *h_ctl = nullptr;          // pinned
   std::vector<void *> dev_allocs;
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;   // pairs (start, end) per timed launch
   double force_ms = 0.0;
   int64_t force_launches = 0;
   int64_t last_launches = 0;
+  int tune_tiles = 0;              // j tiles per work item chosen for the sweep
+  int fpart_slots = 0;             // partial-force slots allocated
+  std::vector<int> fpart_cap;      // per replica: chunks that fit
 };
 
 namespace {
@@ -63,11 +90,16 @@ cudaError_t dalloc(bd_handle *h, T **ptr, size_t count) {
 
 size_t pad_to(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
-int grid_shift(double L, double a) {
-  // every coordinate (disks and ghost points) is below E in magnitude; need E * 2^s < 2^51
-  double E = bdhost::ghost_extent(L, a);
+int grid_shift_for(double E) {
+  // every coordinate is below E in magnitude; need E * 2^s < 2^51
   int e = (int)ceil(log2(E + 1.0));
   return 51 - e;
+}
+
+int grid_shift(double L, double a) { return grid_shift_for(bdhost::ghost_extent(L, a)); }
+
+double box_side(const bd_params &p) {
+  return p.box_L > 0 ? p.box_L : sqrt((double)p.n * M_PI * p.a * p.a / p.area_fraction);
 }
 
 int validate(const bd_params *p) {
@@ -92,40 +124,619 @@ int validate(const bd_params *p) {
 
 double snap_host(double v, double q, double inv_q) { return nearbyint(v * inv_q) * q; }
 
-int pick_nchunk(const BdConst &c) {
+// Build the long-range work items: every i block of a long-range replica
+// against chunks of at most `tiles` j tiles of the same replica.
+void make_items(bd_handle *h, int tiles, std::vector<int4> &items, int &max_chunk) {
+  items.clear();
+  max_chunk = 1;
+  for (size_t r = 0; r < h->reps.size(); ++r) {
+    RepHost &R = h->reps[r];
+    BdRep &B = h->h_rep[r];
+    if (R.p.law != BD_LAW_LONG) {
+      B.nchunk = 1;
+      continue;
+    }
+    const int nt_r = R.tile_end - R.tile_begin;
+    int nch = std::max(1, (nt_r + tiles - 1) / tiles);
+    if (!h->fpart_cap.empty()) nch = std::min(nch, h->fpart_cap[r]);
+    B.nchunk = nch;
+    max_chunk = std::max(max_chunk, nch);
+    for (int ib = 0; ib < R.n_iblocks; ++ib)
+      for (int ch = 0; ch < nch; ++ch) {
+        int t0 = R.tile_begin + (int)(((long long)nt_r * ch) / nch);
+        int t1 = R.tile_begin + (int)(((long long)nt_r * (ch + 1)) / nch);
+        if (t1 > t0) items.push_back(make_int4(R.iblock_base + ib, t0, t1, ch));
+      }
+  }
+}
+
+// j tiles per work item for a single system: fill whole waves of resident
+// force blocks (the occupancy calculator gives blocks per SM)
+int single_system_tiles(const bd_handle *h) {
   const char *env = getenv("BD_NCHUNK");
-  if (env && atoi(env) > 0) return std::min(atoi(env), c.ntiles);
+  const RepHost &R = h->reps[0];
+  const int ntiles = std::max(1, R.tile_end - R.tile_begin);
+  if (env && atoi(env) > 0) return std::max(1, (ntiles + atoi(env) - 1) / atoi(env));
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (c.precision == 1) {
-    int blocks = (c.np + 127) / 128;
+  if (h->c.precision == 1) {
+    int blocks = (h->np + 127) / 128;
     int want = std::max(1, (4 * sms) / std::max(1, blocks));
-    return std::max(1, std::min(want, c.ntiles));
+    want = std::max(1, std::min(want, ntiles));
+    return std::max(1, (ntiles + want - 1) / want);
   }
-  // resident force blocks per SM from the occupancy calculator; choose the
-  // number of j chunks so the (i block, j chunk) grid fills whole waves
-  int per_sm = bd_force_blocks_per_sm(c.force_variant);
+  int per_sm = bd_force_blocks_per_sm(h->c.force_variant);
   if (per_sm < 1) per_sm = 1;
   const long slots = (long)sms * per_sm;
-  const long ib = std::max(1, c.n_iblocks);
+  const long ib = std::max(1, R.n_iblocks);
   int best = 1;
   double best_eff = -1.0;
-  for (int ch = 1; ch <= std::min(c.ntiles, 64); ++ch) {
+  for (int ch = 1; ch <= std::min(ntiles, 64); ++ch) {
     long ctas = ib * ch;
     long waves = (ctas + slots - 1) / slots;
-    // useful fraction of the last wave, times the tile balance across chunks
     double fill = (double)ctas / (double)(waves * slots);
-    int tiles_max = (c.ntiles + ch - 1) / ch;
-    double bal = ((double)c.ntiles / ch) / tiles_max;
-    // prefer at least two waves of blocks per SM slot for latency hiding
+    int tiles_max = (ntiles + ch - 1) / ch;
+    double bal = ((double)ntiles / ch) / tiles_max;
     double eff = fill * bal * (waves >= 2 ? 1.0 : 0.9);
     if (eff > best_eff + 1e-9) {
       best_eff = eff;
       best = ch;
     }
   }
-  return best;
+  return std::max(1, (ntiles + best - 1) / best);
+}
+
+cudaError_t upload_items(bd_handle *h, const std::vector<int4> &items, int max_chunk) {
+  BdConst &c = h->c;
+  c.n_items = (int)items.size();
+  c.max_nchunk = max_chunk;
+  cudaError_t e = cudaSuccess;
+  if (h->d.items) {
+    void *old = (void *)h->d.items;
+    cudaFree(old);
+    h->dev_allocs.erase(std::find(h->dev_allocs.begin(), h->dev_allocs.end(), old));
+    h->d.items = nullptr;
+  }
+  e = dalloc(h, &h->d.items, std::max<size_t>(1, items.size()));
+  if (e != cudaSuccess) return e;
+  if (!items.empty())
+    e = cudaMemcpy(h->d.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy((void *)h->d.rep, h->h_rep.data(), h->h_rep.size() * sizeof(BdRep),
+                    cudaMemcpyHostToDevice);
+}
+
+// Autotuner of the batched sweep: time the force kernel for several chunk
+// sizes (j tiles per work item) and both kernel variants, keep the fastest.
+cudaError_t autotune(bd_handle *h) {
+  const int cand_tiles[] = {2, 4, 8, 16, 32, 64};
+  float best_ms = 1e30f;
+  int best_tiles = 16, best_var = h->c.force_variant;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaError_t e = cudaSuccess;
+  for (int var = 0; var < 2 && e == cudaSuccess; ++var) {
+    for (int tiles : cand_tiles) {
+      std::vector<int4> items;
+      int mc = 1;
+      make_items(h, tiles, items, mc);
+      e = upload_items(h, items, mc);
+      if (e != cudaSuccess) break;
+      float tot = 0.f;
+      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(a, h->stream);
+        e = bd_launch_force_long_variant(h->d, h->c, var, h->stream);
+        cudaEventRecord(b, h->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0) tot += ms;
+      }
+      if (e == cudaSuccess && tot < best_ms) {
+        best_ms = tot;
+        best_tiles = tiles;
+        best_var = var;
+      }
+    }
+  }
+  if (e == cudaSuccess) {
+    h->c.force_variant = best_var;
+    h->tune_tiles = best_tiles;
+    std::vector<int4> items;
+    int mc = 1;
+    make_items(h, best_tiles, items, mc);
+    e = upload_items(h, items, mc);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return e;
+}
+
+struct Spec {
+  bd_params p;
+  const double *xy;
+  const uint8_t *sp;
+  const float *th;
+};
+
+int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out);
+
+}  // namespace
+
+extern "C" void bd_free(bd_handle *h);
+
+namespace {
+
+int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) {
+  *out = nullptr;
+  const int R = (int)specs.size();
+  if (R < 1) return BD_ERR_ARG;
+  for (const Spec &s : specs) {
+    int rc = validate(&s.p);
+    if (rc) return rc;
+    if (s.p.a != specs[0].p.a || s.p.precision != specs[0].p.precision ||
+        s.p.max_corr_iters != specs[0].p.max_corr_iters ||
+        s.p.max_flip_rounds != specs[0].p.max_flip_rounds)
+      return BD_ERR_ARG;   // one disk radius, precision and loop caps per handle
+  }
+  bd_handle *h = new (std::nothrow) bd_handle();
+  if (!h) return BD_ERR_NOMEM;
+  memset(&h->d, 0, sizeof(h->d));
+  memset(&h->c, 0, sizeof(h->c));
+  h->stream = (cudaStream_t)stream;
+  const double a = specs[0].p.a;
+
+  // ---- position grid shared by all replicas ----
+  double E = 0.0;
+  for (const Spec &s : specs) E = std::max(E, bdhost::ghost_extent(box_side(s.p), a));
+  const int s_shift = grid_shift_for(E);
+  const double q = ldexp(1.0, -s_shift), inv_q = ldexp(1.0, s_shift);
+
+  h->reps.resize(R);
+  std::vector<std::vector<double>> xyr(R);
+  std::vector<std::vector<uint8_t>> spr(R);
+  std::vector<std::vector<float>> thr(R);
+  int ext = 0;
+  for (int r = 0; r < R; ++r) {
+    const bd_params &p = specs[r].p;
+    RepHost &RH = h->reps[r];
+    RH.p = p;
+    RH.n = p.n;
+    RH.ext_base = ext;
+    ext += p.n;
+    RH.L = box_side(p);
+    RH.wall_lo = ceil(p.a * inv_q) * q;
+    RH.wall_hi = floor((RH.L - p.a) * inv_q) * q;
+    if (!(RH.wall_hi > RH.wall_lo)) { delete h; return BD_ERR_ARG; }
+    std::vector<double> &xy = xyr[r];
+    xy.resize(2 * (size_t)p.n);
+    if (specs[r].xy) {
+      memcpy(xy.data(), specs[r].xy, sizeof(double) * 2 * (size_t)p.n);
+    } else if (bdhost::rsa_place(p.n, p.a, RH.L - p.a, 2.0 * p.a, p.seed, xy) != 0) {
+      delete h;
+      return BD_ERR_ARG;
+    }
+    for (size_t k = 0; k < xy.size(); ++k)
+      if (!isfinite(xy[k]) || xy[k] < p.a - 1e-9 * RH.L || xy[k] > RH.L - p.a + 1e-9 * RH.L) {
+        delete h;
+        return BD_ERR_INIT_OVERLAP;
+      }
+    if (bdhost::any_overlap(p.n, xy.data(), 0.0, RH.L, 2.0 * p.a * (1.0 - 1e-12))) {
+      delete h;
+      return BD_ERR_INIT_OVERLAP;
+    }
+    for (size_t k = 0; k < xy.size(); ++k)
+      xy[k] = std::min(RH.wall_hi, std::max(RH.wall_lo, snap_host(xy[k], q, inv_q)));
+    spr[r].assign(p.n, 0);
+    if (specs[r].sp)
+      for (int i = 0; i < p.n; ++i) {
+        if (specs[r].sp[i] >= p.n_species) { delete h; return BD_ERR_ARG; }
+        spr[r][i] = specs[r].sp[i];
+      }
+    thr[r].assign(p.n, 0.f);
+    if (specs[r].th) memcpy(thr[r].data(), specs[r].th, sizeof(float) * p.n);
+  }
+  h->n = ext;
+
+  // ---- internal order: per replica species-major, Hilbert-minor, tile-padded ----
+  std::vector<std::vector<int>> byhr(R);   // per replica: disk slots in Hilbert order
+  int slot = 0, iblock = 0;
+  std::vector<int> iperm;
+  std::vector<float2> iorg;
+  std::vector<uint8_t> tile_sp;
+  std::vector<int> slot_ext, slot_local, slot_rep;
+  for (int r = 0; r < R; ++r) {
+    RepHost &RH = h->reps[r];
+    const int n = RH.n;
+    const std::vector<double> &xy = xyr[r];
+    const std::vector<uint8_t> &sp = spr[r];
+    std::vector<uint64_t> hk(n);
+    for (int i = 0; i < n; ++i) {
+      uint32_t ux = (uint32_t)std::min(65535.0, std::max(0.0, xy[2 * i] / RH.L * 65536.0));
+      uint32_t uy = (uint32_t)std::min(65535.0, std::max(0.0, xy[2 * i + 1] / RH.L * 65536.0));
+      hk[i] = bdhost::hilbert_index(ux, uy);
+    }
+    std::vector<int> by_sp(n);
+    std::iota(by_sp.begin(), by_sp.end(), 0);
+    std::sort(by_sp.begin(), by_sp.end(), [&](int x, int y) {
+      if (sp[x] != sp[y]) return sp[x] < sp[y];
+      if (hk[x] != hk[y]) return hk[x] < hk[y];
+      return x < y;
+    });
+    int cnt_sp[2] = {0, 0};
+    for (int i = 0; i < n; ++i) cnt_sp[sp[i]]++;
+    const int seg0 = (int)pad_to(cnt_sp[0], BD_TJ), seg1 = (int)pad_to(cnt_sp[1], BD_TJ);
+    RH.slot_begin = slot;
+    RH.slot_end = slot + seg0 + seg1;
+    RH.tile_begin = slot / BD_TJ;
+    RH.tile_end = RH.slot_end / BD_TJ;
+    slot_ext.resize(RH.slot_end, -1);
+    slot_local.resize(RH.slot_end, -1);
+    slot_rep.resize(RH.slot_end, -1);
+    std::vector<int> local_slot(n);
+    {
+      int k0 = slot, k1 = slot + seg0;
+      for (int k = 0; k < n; ++k) {
+        int e = by_sp[k];
+        int sl = sp[e] == 0 ? k0++ : k1++;
+        slot_ext[sl] = RH.ext_base + e;
+        slot_local[sl] = e;
+        slot_rep[sl] = r;
+        local_slot[e] = sl;
+      }
+    }
+    for (int t = RH.tile_begin; t < RH.tile_end; ++t)
+      tile_sp.push_back((t * BD_TJ - RH.slot_begin) < seg0 ? 0 : 1);
+    slot = RH.slot_end;
+    // force i blocks: Hilbert order over the replica's disks
+    std::vector<int> by_h(n);
+    std::iota(by_h.begin(), by_h.end(), 0);
+    std::sort(by_h.begin(), by_h.end(), [&](int x, int y) { return hk[x] != hk[y] ? hk[x] < hk[y] : x < y; });
+    const int nib = (int)(pad_to(n, BD_IB) / BD_IB);
+    RH.iblock_base = iblock;
+    RH.n_iblocks = nib;
+    for (int b = 0; b < nib; ++b) {
+      double sx = 0, sy = 0;
+      int m = 0;
+      for (int k = b * BD_IB; k < (b + 1) * BD_IB; ++k) {
+        if (k < n) {
+          int e = by_h[k];
+          iperm.push_back(local_slot[e]);
+          sx += xy[2 * e];
+          sy += xy[2 * e + 1];
+          ++m;
+        } else {
+          iperm.push_back(-1);
+        }
+      }
+      iorg.push_back(m ? make_float2((float)nearbyint(sx / m), (float)nearbyint(sy / m)) : make_float2(0.f, 0.f));
+    }
+    iblock += nib;
+    byhr[r].resize(n);
+    for (int k = 0; k < n; ++k) byhr[r][k] = local_slot[by_h[k]];
+  }
+  const int np = slot;
+  h->np = np;
+  h->np_i = (int)iperm.size();
+  h->ext_of_int = slot_ext;
+  h->int_of_ext.assign(h->n, -1);
+  for (int i = 0; i < np; ++i)
+    if (slot_ext[i] >= 0) h->int_of_ext[slot_ext[i]] = i;
+
+  // ---- ghost points (after all disks) and the per-replica triangulations ----
+  int ng_total = 0;
+  std::vector<std::vector<double>> gxr(R), gyr(R);
+  for (int r = 0; r < R; ++r) {
+    bdhost::make_ghosts(h->reps[r].L, a, gxr[r], gyr[r]);
+    h->reps[r].ghost_base = np + ng_total;
+    h->reps[r].ng = (int)gxr[r].size();
+    ng_total += h->reps[r].ng;
+  }
+  h->ng = ng_total;
+  h->host_pos.assign(2 * ((size_t)np + ng_total), 0.0);
+  for (int i = 0; i < np; ++i) {
+    const int r = slot_rep[i];
+    if (r >= 0) {
+      int e = slot_local[i];
+      h->host_pos[2 * i] = xyr[r][2 * e];
+      h->host_pos[2 * i + 1] = xyr[r][2 * e + 1];
+    }
+  }
+  for (int r = 0; r < R; ++r)
+    for (int k = 0; k < h->reps[r].ng; ++k) {
+      h->host_pos[2 * ((size_t)h->reps[r].ghost_base + k)] = gxr[r][k];
+      h->host_pos[2 * ((size_t)h->reps[r].ghost_base + k) + 1] = gyr[r][k];
+    }
+  std::vector<double> X(np + ng_total), Y(np + ng_total);
+  for (int i = 0; i < np + ng_total; ++i) {
+    X[i] = h->host_pos[2 * i];
+    Y[i] = h->host_pos[2 * i + 1];
+  }
+  bdpred::Grid grid;
+  grid.q = q;
+  grid.inv_q = inv_q;
+  grid.s = s_shift;
+  std::vector<int4> tv_all, tn_all;
+  int tri_base = 0;
+  for (int r = 0; r < R; ++r) {
+    RepHost &RH = h->reps[r];
+    std::vector<int> gids(RH.ng);
+    for (int k = 0; k < RH.ng; ++k) gids[k] = RH.ghost_base + k;
+    std::vector<int> V, N;
+    if (bdhost::build_delaunay(X.data(), Y.data(), grid, byhr[r], gids, V, N) != 0) {
+      delete h;
+      return BD_ERR_TRIANGULATION;
+    }
+    const int nt_r = (int)(V.size() / 3);
+    if (nt_r != 2 * (RH.n + RH.ng) - 6) {
+      delete h;
+      return BD_ERR_TRIANGULATION;
+    }
+    RH.tri_base = tri_base;
+    RH.nt = nt_r;
+    for (int t = 0; t < nt_r; ++t) {
+      tv_all.push_back(make_int4(V[3 * t], V[3 * t + 1], V[3 * t + 2], 0));
+      auto sh = [&](int o) { return o < 0 ? -1 : o + 3 * tri_base; };
+      tn_all.push_back(make_int4(sh(N[3 * t]), sh(N[3 * t + 1]), sh(N[3 * t + 2]), 0));
+    }
+    tri_base += nt_r;
+  }
+  const int nt = tri_base;
+  h->nt = nt;
+
+  // ---- constants and the replica table ----
+  BdConst &c = h->c;
+  const bd_params &p0 = specs[0].p;
+  c.n = h->n;
+  c.np = np;
+  c.np_i = h->np_i;
+  c.nt = nt;
+  c.ntiles = np / BD_TJ;
+  c.n_iblocks = iblock;
+  c.R = R;
+  c.precision = p0.precision;
+  c.a = a;
+  c.sigma = 2.0 * a;
+  c.q = q;
+  c.inv_q = inv_q;
+  c.qshift = s_shift;
+  {
+    // (sigma/q)^2 (1 + 1e-9), rounded up, as a 128-bit integer
+    long double sq = (long double)(2.0 * a) * (long double)inv_q;
+    long double v = sq * sq * (1.0L + 1e-9L);
+    long double two64 = 18446744073709551616.0L;
+    unsigned long long hi = (unsigned long long)(v / two64);
+    long double rem = v - (long double)hi * two64;
+    unsigned long long lo = (unsigned long long)rem;
+    if ((long double)lo < rem) ++lo;
+    c.sig2q_hi = hi;
+    c.sig2q_lo = lo;
+  }
+  c.max_corr_iters = p0.max_corr_iters;
+  c.max_flip_rounds = p0.max_flip_rounds;
+  {
+    const char *fv = getenv("BD_FORCE_VARIANT");
+    c.force_variant = fv ? atoi(fv) : 1;
+  }
+  h->h_rep.resize(R);
+  int cell_base = 0;
+  for (int r = 0; r < R; ++r) {
+    const RepHost &RH = h->reps[r];
+    const bd_params &p = RH.p;
+    BdRep &B = h->h_rep[r];
+    memset(&B, 0, sizeof(B));
+    B.L = RH.L;
+    B.wall_lo = RH.wall_lo;
+    B.wall_hi = RH.wall_hi;
+    B.dt = p.dt;
+    B.amp = p.literal_noise ? sqrt(p.D * p.dt) : sqrt(2.0 * p.D * p.dt);
+    B.amp_r = sqrt(2.0 * p.Dr * p.dt);
+    B.v0 = p.v0;
+    B.eps = p.eps;
+    B.kappa = p.kappa;
+    B.r_cut = p.r_cut;
+    B.skin = p.skin;
+    B.rl2 = (p.r_cut + p.skin) * (p.r_cut + p.skin);
+    for (int k = 0; k < 4; ++k) {
+      B.alpha_d[k] = p.n_species == 1 ? p.alpha[0] : p.alpha[k];
+      B.alpha[k] = (float)B.alpha_d[k];
+    }
+    B.seed = p.seed;
+    B.replica = (unsigned)p.replica;
+    B.law = p.law;
+    B.slot_begin = RH.slot_begin;
+    B.slot_end = RH.slot_end;
+    B.n = RH.n;
+    B.nchunk = 1;
+    if (p.law == BD_LAW_SHORT) {
+      B.ncell = std::max(1, std::min(1 << 14, (int)floor(RH.L / (p.r_cut + p.skin))));
+      B.cell_size = RH.L / B.ncell;
+      B.cell_base = cell_base;
+      cell_base += B.ncell * B.ncell;
+      c.any_short = 1;
+    }
+    if (p.law == BD_LAW_LONG) c.any_long = 1;
+    c.n_species = std::max(c.n_species, p.n_species);
+  }
+  c.ncell_total = cell_base;
+  h->step = p0.step0;
+
+  // ---- device buffers ----
+  BdDev &d = h->d;
+  cudaError_t e = cudaSuccess;
+  const size_t nv = (size_t)np + ng_total;
+#define BD_TRY(x)                          \
+  do {                                     \
+    e = (x);                               \
+    if (e != cudaSuccess) goto cuda_error; \
+  } while (0)
+  {
+    BD_TRY(dalloc(h, &d.pos, nv));
+    BD_TRY(dalloc(h, &d.prev, nv));
+    BD_TRY(dalloc(h, &d.pos0, nv));
+    BD_TRY(dalloc(h, &d.work, (size_t)np));
+    BD_TRY(dalloc(h, &d.theta, (size_t)np));
+    BD_TRY(dalloc(h, &d.theta0, (size_t)np));
+    BD_TRY(dalloc(h, &d.species, (size_t)np));
+    BD_TRY(dalloc(h, &d.ext_id, (size_t)np));
+    BD_TRY(dalloc(h, &d.rep_of, (size_t)np));
+    BD_TRY(dalloc(h, &d.moved, nv));
+    BD_TRY(dalloc(h, &d.disp, (size_t)np));
+    {
+      BdRep *rp = nullptr;
+      BD_TRY(dalloc(h, &rp, (size_t)R));
+      d.rep = rp;
+    }
+    BD_TRY(dalloc(h, &d.tv, (size_t)nt));
+    BD_TRY(dalloc(h, &d.tn, (size_t)nt));
+    BD_TRY(dalloc(h, &d.tv_snap, (size_t)nt));
+    BD_TRY(dalloc(h, &d.tn_snap, (size_t)nt));
+    BD_TRY(dalloc(h, &d.claim, (size_t)nt));
+    BD_TRY(dalloc(h, &d.iperm, (size_t)std::max(1, h->np_i)));
+    BD_TRY(dalloc(h, &d.iorigin, (size_t)std::max(1, iblock)));
+    BD_TRY(dalloc(h, &d.tile_species, std::max<size_t>(1, tile_sp.size())));
+    BD_TRY(dalloc(h, &d.ctl, 1));
+    BD_TRY(dalloc(h, &h->d_fsum, (size_t)np));
+    BD_TRY(cudaMallocHost((void **)&h->h_ctl, sizeof(BdCtl)));
+    // partial-force slots: enough for the finest chunking tried (at most 64)
+    {
+      int slots = 1;
+      h->fpart_cap.assign(R, 1);
+      for (int r = 0; r < R; ++r) {
+        const int nt_r = h->reps[r].tile_end - h->reps[r].tile_begin;
+        const int cap = h->reps[r].p.law == BD_LAW_LONG ? std::min(64, std::max(1, nt_r)) : 1;
+        h->fpart_cap[r] = cap;
+        slots = std::max(slots, cap);
+      }
+      h->fpart_slots = slots;
+      BD_TRY(dalloc(h, &d.fpart, (size_t)slots * np));
+    }
+    if (c.any_short) {
+      const size_t nc2 = (size_t)std::max(1, c.ncell_total);
+      BD_TRY(dalloc(h, &d.vl_idx, (size_t)BD_VL_MAX * np));
+      BD_TRY(dalloc(h, &d.vl_cnt, (size_t)np));
+      BD_TRY(dalloc(h, &d.vl_ref, (size_t)np));
+      BD_TRY(dalloc(h, &d.cell_count, nc2));
+      BD_TRY(dalloc(h, &d.cell_start, nc2));
+      BD_TRY(dalloc(h, &d.cell_cursor, nc2));
+      BD_TRY(dalloc(h, &d.cell_idx, (size_t)np));
+      BD_TRY(dalloc(h, &d.cell_of, (size_t)np));
+      BD_TRY(dalloc(h, &d.scan_sums, (nc2 + 511) / 512 + 1));
+    }
+
+    cudaStream_t st = h->stream;
+    std::vector<float> th_i(np, 0.f);
+    std::vector<uint8_t> sp_i(np, 255);
+    for (int i = 0; i < np; ++i) {
+      const int r = slot_rep[i];
+      if (r >= 0) {
+        th_i[i] = thr[r][slot_local[i]];
+        sp_i[i] = spr[r][slot_local[i]];
+      }
+    }
+    BD_TRY(cudaMemcpyAsync(d.pos, h->host_pos.data(), nv * sizeof(double2), cudaMemcpyHostToDevice, st));
+    BD_TRY(cudaMemcpyAsync(d.prev, d.pos, nv * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    BD_TRY(cudaMemcpyAsync(d.pos0, d.pos, nv * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    BD_TRY(cudaMemcpyAsync(d.theta, th_i.data(), np * sizeof(float), cudaMemcpyHostToDevice, st));
+    BD_TRY(cudaMemcpyAsync(d.theta0, d.theta, np * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    BD_TRY(cudaMemcpyAsync(d.species, sp_i.data(), np, cudaMemcpyHostToDevice, st));
+    BD_TRY(cudaMemcpyAsync(d.ext_id, slot_local.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    BD_TRY(cudaMemcpyAsync(d.rep_of, slot_rep.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    BD_TRY(cudaMemsetAsync(d.moved, 0, nv, st));
+    BD_TRY(cudaMemsetAsync(d.disp, 0, np * sizeof(double2), st));
+    BD_TRY(cudaMemcpyAsync(d.tv, tv_all.data(), nt * sizeof(int4), cudaMemcpyHostToDevice, st));
+    BD_TRY(cudaMemcpyAsync(d.tn, tn_all.data(), nt * sizeof(int4), cudaMemcpyHostToDevice, st));
+    BD_TRY(cudaMemsetAsync(d.claim, 0, nt * sizeof(unsigned long long), st));
+    if (!iperm.empty())
+      BD_TRY(cudaMemcpyAsync(d.iperm, iperm.data(), iperm.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (!iorg.empty())
+      BD_TRY(cudaMemcpyAsync(d.iorigin, iorg.data(), iorg.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    if (!tile_sp.empty())
+      BD_TRY(cudaMemcpyAsync(d.tile_species, tile_sp.data(), tile_sp.size(), cudaMemcpyHostToDevice, st));
+    BD_TRY(cudaMemsetAsync(d.fpart, 0, (size_t)h->fpart_slots * np * sizeof(double2), st));
+    BD_TRY(cudaMemsetAsync(d.ctl, 0, sizeof(BdCtl), st));
+    if (c.any_short) {
+      // reference positions far away: the first force evaluation builds the lists
+      std::vector<double2> far(np, make_double2(1e30, 1e30));
+      BD_TRY(cudaMemcpyAsync(d.vl_ref, far.data(), np * sizeof(double2), cudaMemcpyHostToDevice, st));
+      BD_TRY(cudaMemsetAsync(d.vl_cnt, 0, np * sizeof(int), st));
+      BD_TRY(cudaStreamSynchronize(st));
+    }
+    BD_TRY(cudaStreamSynchronize(st));
+    // force work items: a single system fills whole waves; a batch is autotuned
+    {
+      std::vector<int4> items;
+      int mc = 1;
+      h->tune_tiles = R == 1 ? single_system_tiles(h) : 16;
+      make_items(h, h->tune_tiles, items, mc);
+      BD_TRY(upload_items(h, items, mc));
+      BD_TRY(bd_launch_work_copy(d, c, st));
+      BD_TRY(cudaStreamSynchronize(st));
+      if (R > 1 && c.any_long && c.precision == 0) BD_TRY(autotune(h));
+    }
+    if (bd_dt_grid_for(std::max(nt, np), &h->dt_grid, &h->dt_block) != 0) {
+      bd_free(h);
+      return BD_ERR_CUDA;
+    }
+  }
+#undef BD_TRY
+  *out = h;
+  return BD_OK;
+cuda_error:
+  bd_free(h);
+  return cuda_fail(e);
+}
+
+int read_ctl(bd_handle *h) {
+  cudaError_t e = cudaMemcpyAsync(h->h_ctl, h->d.ctl, sizeof(BdCtl), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return BD_OK;
+}
+
+cudaError_t reset_stats(bd_handle *h) {
+  // zero everything after the barrier words, the status and the epoch
+  char *base = (char *)h->d.ctl;
+  size_t off = offsetof(BdCtl, cnt);
+  cudaError_t e = cudaMemsetAsync(base + off, 0, sizeof(BdCtl) - off, h->stream);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(&h->d.ctl->status, 0, sizeof(int), h->stream);
+}
+
+int finish_status(bd_handle *h, int status) {
+  // clear the sticky status so the handle keeps working from the last good
+  // state; after a timed-out barrier also reset the barrier words
+  cudaStream_t st = h->stream;
+  if (status == BD_ERR_DEVICE_TIMEOUT) cudaMemsetAsync(h->d.ctl, 0, offsetof(BdCtl, epoch), st);
+  cudaMemsetAsync(&h->d.ctl->cnt[0][0], 0, sizeof(h->d.ctl->cnt), st);
+  cudaMemsetAsync(&h->d.ctl->status, 0, sizeof(int), st);
+  cudaStreamSynchronize(st);
+  return status;
+}
+
+// copy the disks' positions / directions / species (internal order)
+int fetch_disks(bd_handle *h, std::vector<double2> *pos, std::vector<float> *th,
+                std::vector<uint8_t> *sp) {
+  cudaStream_t st = h->stream;
+  const int np = h->np;
+  cudaError_t e = cudaSuccess;
+  if (pos) {
+    pos->resize(np);
+    e = cudaMemcpyAsync(pos->data(), h->d.pos, np * sizeof(double2), cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess && th) {
+    th->resize(np);
+    e = cudaMemcpyAsync(th->data(), h->d.theta, np * sizeof(float), cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess && sp) {
+    sp->resize(np);
+    e = cudaMemcpyAsync(sp->data(), h->d.species, np, cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? BD_OK : cuda_fail(e);
 }
 
 }  // namespace
@@ -178,340 +789,25 @@ void bd_free(bd_handle *h) {
   delete h;
 }
 
-int bd_init(const bd_params *p_in, const double *xy_in, const uint8_t *species_in,
-            const float *theta_in, void *stream, bd_handle **out) {
-  if (!out) return BD_ERR_ARG;
-  *out = nullptr;
-  int rc = validate(p_in);
-  if (rc) return rc;
-  bd_handle *h = new (std::nothrow) bd_handle();
-  if (!h) return BD_ERR_NOMEM;
-  h->p = *p_in;
-  h->stream = (cudaStream_t)stream;
-  const bd_params &p = h->p;
-  const int n = p.n;
-  h->n = n;
-  const double L = p.box_L > 0 ? p.box_L : sqrt((double)n * M_PI * p.a * p.a / p.area_fraction);
-  const int s = grid_shift(L, p.a);
-  const double q = ldexp(1.0, -s), inv_q = ldexp(1.0, s);
-  const double wall_lo = ceil(p.a * inv_q) * q, wall_hi = floor((L - p.a) * inv_q) * q;
-  if (!(wall_hi > wall_lo)) { delete h; return BD_ERR_ARG; }
-
-  // ---- positions, species, directions (external order) ----
-  std::vector<double> xy(2 * (size_t)n);
-  if (xy_in) {
-    memcpy(xy.data(), xy_in, sizeof(double) * 2 * (size_t)n);
-  } else if (bdhost::rsa_place(n, p.a, L - p.a, 2.0 * p.a, p.seed, xy) != 0) {
-    delete h;
-    return BD_ERR_ARG;
-  }
-  for (size_t k = 0; k < xy.size(); ++k) {
-    if (!isfinite(xy[k]) || xy[k] < p.a - 1e-9 * L || xy[k] > L - p.a + 1e-9 * L) {
-      delete h;
-      return BD_ERR_INIT_OVERLAP;
-    }
-  }
-  if (bdhost::any_overlap(n, xy.data(), 0.0, L, 2.0 * p.a * (1.0 - 1e-12))) {
-    delete h;
-    return BD_ERR_INIT_OVERLAP;
-  }
-  for (size_t k = 0; k < xy.size(); ++k)
-    xy[k] = std::min(wall_hi, std::max(wall_lo, snap_host(xy[k], q, inv_q)));
-  std::vector<uint8_t> sp(n, 0);
-  if (species_in) {
-    for (int i = 0; i < n; ++i) {
-      if (species_in[i] >= p.n_species) { delete h; return BD_ERR_ARG; }
-      sp[i] = species_in[i];
-    }
-  }
-  std::vector<float> th(n, 0.f);
-  if (theta_in) memcpy(th.data(), theta_in, sizeof(float) * n);
-
-  // ---- internal order: species-major, Hilbert-minor, tile-padded ----
-  std::vector<uint64_t> hk(n);
-  for (int i = 0; i < n; ++i) {
-    uint32_t ux = (uint32_t)std::min(65535.0, std::max(0.0, xy[2 * i] / L * 65536.0));
-    uint32_t uy = (uint32_t)std::min(65535.0, std::max(0.0, xy[2 * i + 1] / L * 65536.0));
-    hk[i] = bdhost::hilbert_index(ux, uy);
-  }
-  std::vector<int> by_sp(n);
-  std::iota(by_sp.begin(), by_sp.end(), 0);
-  std::sort(by_sp.begin(), by_sp.end(), [&](int a, int b) {
-    if (sp[a] != sp[b]) return sp[a] < sp[b];
-    if (hk[a] != hk[b]) return hk[a] < hk[b];
-    return a < b;
-  });
-  int cnt_sp[2] = {0, 0};
-  for (int i = 0; i < n; ++i) cnt_sp[sp[i]]++;
-  const size_t seg0 = pad_to(cnt_sp[0], BD_TJ), seg1 = pad_to(cnt_sp[1], BD_TJ);
-  const int np = (int)(seg0 + seg1);
-  h->np = np;
-  h->ext_of_int.assign(np, -1);
-  h->int_of_ext.assign(n, -1);
-  {
-    size_t k0 = 0, k1 = seg0;
-    for (int r = 0; r < n; ++r) {
-      int e = by_sp[r];
-      size_t slot = sp[e] == 0 ? k0++ : k1++;
-      h->ext_of_int[slot] = e;
-      h->int_of_ext[e] = (int)slot;
-    }
-  }
-  // i blocks of the force sweep: Hilbert order over all disks
-  std::vector<int> by_h(n);
-  std::iota(by_h.begin(), by_h.end(), 0);
-  std::sort(by_h.begin(), by_h.end(), [&](int a, int b) { return hk[a] != hk[b] ? hk[a] < hk[b] : a < b; });
-  const int np_i = (int)pad_to(n, BD_IB);
-  h->np_i = np_i;
-  std::vector<int> iperm(np_i, -1);
-  for (int r = 0; r < n; ++r) iperm[r] = h->int_of_ext[by_h[r]];
-  const int n_iblocks = np_i / BD_IB;
-  std::vector<float2> iorg(n_iblocks);
-  for (int b = 0; b < n_iblocks; ++b) {
-    double sx = 0, sy = 0;
-    int m = 0;
-    for (int k = b * BD_IB; k < std::min(n, (b + 1) * BD_IB); ++k) {
-      int e = by_h[k];
-      sx += xy[2 * e];
-      sy += xy[2 * e + 1];
-      ++m;
-    }
-    iorg[b] = m ? make_float2((float)nearbyint(sx / m), (float)nearbyint(sy / m)) : make_float2(0.f, 0.f);
-  }
-  std::vector<uint8_t> tile_sp(np / BD_TJ);
-  for (size_t t = 0; t < tile_sp.size(); ++t) tile_sp[t] = (t * BD_TJ < seg0) ? 0 : 1;
-
-  // internal position mirror: np slots + ghost points
-  std::vector<double> ghx, ghy;
-  bdhost::make_ghosts(L, p.a, ghx, ghy);
-  const int ng = (int)ghx.size();
-  h->ng = ng;
-  h->host_pos.assign(2 * ((size_t)np + ng), 0.0);
-  for (int i = 0; i < np; ++i) {
-    int e = h->ext_of_int[i];
-    if (e >= 0) {
-      h->host_pos[2 * i] = xy[2 * e];
-      h->host_pos[2 * i + 1] = xy[2 * e + 1];
-    } else {
-      h->host_pos[2 * i] = 0.5 * L;  // never referenced by the triangulation
-      h->host_pos[2 * i + 1] = 0.5 * L;
-    }
-  }
-  for (int k = 0; k < ng; ++k) {
-    h->host_pos[2 * ((size_t)np + k)] = ghx[k];
-    h->host_pos[2 * ((size_t)np + k) + 1] = ghy[k];
-  }
-
-  // ---- initial Delaunay triangulation on the host (Sec. 4.1) ----
-  std::vector<double> X(np + ng), Y(np + ng);
-  for (int i = 0; i < np + ng; ++i) {
-    X[i] = h->host_pos[2 * i];
-    Y[i] = h->host_pos[2 * i + 1];
-  }
-  std::vector<int> order(n);
-  for (int r = 0; r < n; ++r) order[r] = h->int_of_ext[by_h[r]];
-  bdpred::Grid grid;
-  grid.q = q;
-  grid.inv_q = inv_q;
-  grid.s = s;
-  std::vector<int> gids(ng);
-  for (int k = 0; k < ng; ++k) gids[k] = np + k;
-  std::vector<int> V, N;
-  if (bdhost::build_delaunay(X.data(), Y.data(), grid, order, gids, V, N) != 0) {
-    delete h;
-    return BD_ERR_TRIANGULATION;
-  }
-  const int nt = (int)(V.size() / 3);
-  if (nt != 2 * (n + ng) - 6) {
-    delete h;
-    return BD_ERR_TRIANGULATION;
-  }
-  h->nt = nt;
-
-  // ---- constants ----
-  BdConst &c = h->c;
-  memset(&c, 0, sizeof(c));
-  c.n = n;
-  c.np = np;
-  c.np_i = np_i;
-  c.nt = nt;
-  c.ntiles = np / BD_TJ;
-  c.n_iblocks = n_iblocks;
-  c.law = p.law;
-  c.precision = p.precision;
-  c.n_species = p.n_species;
-  c.a = p.a;
-  c.sigma = 2.0 * p.a;
-  c.L = L;
-  c.wall_lo = wall_lo;
-  c.wall_hi = wall_hi;
-  c.q = q;
-  c.inv_q = inv_q;
-  c.qshift = s;
-  {
-    // (sigma/q)^2 (1 + 1e-9), rounded up, as a 128-bit integer
-    long double sq = (long double)(2.0 * p.a) * (long double)inv_q;
-    long double v = sq * sq * (1.0L + 1e-9L);
-    long double two64 = 18446744073709551616.0L;
-    unsigned long long hi = (unsigned long long)(v / two64);
-    long double rem = v - (long double)hi * two64;
-    unsigned long long lo = (unsigned long long)rem;
-    if ((long double)lo < rem) ++lo;
-    c.sig2q_hi = hi;
-    c.sig2q_lo = lo;
-  }
-  for (int k = 0; k < 4; ++k) {
-    c.alpha[k] = (float)p.alpha[k];
-    c.alpha_d[k] = p.alpha[k];
-  }
-  if (p.n_species == 1) {
-    for (int k = 1; k < 4; ++k) {
-      c.alpha[k] = c.alpha[0];
-      c.alpha_d[k] = c.alpha_d[0];
-    }
-  }
-  c.eps = p.eps;
-  c.kappa = p.kappa;
-  c.r_cut = p.r_cut;
-  c.skin = p.skin;
-  c.rl2 = (p.r_cut + p.skin) * (p.r_cut + p.skin);
-  c.ncell = std::max(1, std::min(1 << 14, (int)floor(L / (p.r_cut + p.skin))));
-  c.cell_size = L / c.ncell;
-  c.D = p.D;
-  c.Dr = p.Dr;
-  c.v0 = p.v0;
-  c.dt = p.dt;
-  c.amp = p.literal_noise ? sqrt(p.D * p.dt) : sqrt(2.0 * p.D * p.dt);
-  c.amp_r = sqrt(2.0 * p.Dr * p.dt);
-  c.seed = p.seed;
-  c.replica = (uint32_t)p.replica;
-  c.max_corr_iters = p.max_corr_iters;
-  c.max_flip_rounds = p.max_flip_rounds;
-  c.nchunk = 1;
-  h->step = p.step0;
-
-  // ---- device buffers ----
-  BdDev &d = h->d;
-  memset(&d, 0, sizeof(d));
-  cudaError_t e = cudaSuccess;
-  const size_t nv = (size_t)np + ng;
-#define BD_TRY(x)                         \
-  do {                                    \
-    e = (x);                              \
-    if (e != cudaSuccess) goto cuda_error; \
-  } while (0)
-  {
-    {
-      const char *fv = getenv("BD_FORCE_VARIANT");
-      c.force_variant = fv ? atoi(fv) : 1;
-    }
-    c.nchunk = p.law == BD_LAW_SHORT ? 1 : pick_nchunk(c);
-    BD_TRY(dalloc(h, &d.pos, nv));
-    BD_TRY(dalloc(h, &d.prev, nv));
-    BD_TRY(dalloc(h, &d.pos0, nv));
-    BD_TRY(dalloc(h, &d.work, (size_t)np));
-    BD_TRY(dalloc(h, &d.theta, (size_t)np));
-    BD_TRY(dalloc(h, &d.theta0, (size_t)np));
-    BD_TRY(dalloc(h, &d.species, (size_t)np));
-    BD_TRY(dalloc(h, &d.ext_id, (size_t)np));
-    BD_TRY(dalloc(h, &d.moved, nv));
-    BD_TRY(dalloc(h, &d.disp, (size_t)np));
-    BD_TRY(dalloc(h, &d.tv, (size_t)nt));
-    BD_TRY(dalloc(h, &d.tn, (size_t)nt));
-    BD_TRY(dalloc(h, &d.tv_snap, (size_t)nt));
-    BD_TRY(dalloc(h, &d.tn_snap, (size_t)nt));
-    BD_TRY(dalloc(h, &d.claim, (size_t)nt));
-    BD_TRY(dalloc(h, &d.partner, (size_t)nt));
-    BD_TRY(dalloc(h, &d.iperm, (size_t)np_i));
-    BD_TRY(dalloc(h, &d.iorigin, (size_t)n_iblocks));
-    BD_TRY(dalloc(h, &d.tile_species, tile_sp.size()));
-    BD_TRY(dalloc(h, &d.fpart, (size_t)c.nchunk * np));
-    BD_TRY(dalloc(h, &d.ctl, 1));
-    if (p.law == BD_LAW_SHORT) {
-      const size_t nc2 = (size_t)c.ncell * c.ncell;
-      BD_TRY(dalloc(h, &d.vl_idx, (size_t)BD_VL_MAX * np));
-      BD_TRY(dalloc(h, &d.vl_cnt, (size_t)np));
-      BD_TRY(dalloc(h, &d.vl_ref, (size_t)np));
-      BD_TRY(dalloc(h, &d.cell_count, nc2));
-      BD_TRY(dalloc(h, &d.cell_start, nc2));
-      BD_TRY(dalloc(h, &d.cell_cursor, nc2));
-      BD_TRY(dalloc(h, &d.cell_idx, (size_t)np));
-      BD_TRY(dalloc(h, &d.cell_of, (size_t)np));
-      BD_TRY(dalloc(h, &d.scan_sums, (nc2 + 511) / 512 + 1));
-    }
-    BD_TRY(dalloc(h, &h->d_fsum, (size_t)np));
-    BD_TRY(cudaMallocHost((void **)&h->h_ctl, sizeof(BdCtl)));
-
-    cudaStream_t st = h->stream;
-    std::vector<float> th_i(np, 0.f);
-    std::vector<uint8_t> sp_i(np, 255);
-    for (int i = 0; i < np; ++i) {
-      int ex = h->ext_of_int[i];
-      if (ex >= 0) {
-        th_i[i] = th[ex];
-        sp_i[i] = sp[ex];
-      }
-    }
-    std::vector<int4> tv(nt), tn(nt);
-    for (int t = 0; t < nt; ++t) {
-      tv[t] = make_int4(V[3 * t], V[3 * t + 1], V[3 * t + 2], 0);
-      tn[t] = make_int4(N[3 * t], N[3 * t + 1], N[3 * t + 2], 0);
-    }
-    BD_TRY(cudaMemcpyAsync(d.pos, h->host_pos.data(), nv * sizeof(double2), cudaMemcpyHostToDevice, st));
-    BD_TRY(cudaMemcpyAsync(d.prev, d.pos, nv * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    BD_TRY(cudaMemcpyAsync(d.pos0, d.pos, nv * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    BD_TRY(cudaMemcpyAsync(d.theta, th_i.data(), np * sizeof(float), cudaMemcpyHostToDevice, st));
-    BD_TRY(cudaMemcpyAsync(d.theta0, d.theta, np * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    BD_TRY(cudaMemcpyAsync(d.species, sp_i.data(), np, cudaMemcpyHostToDevice, st));
-    BD_TRY(cudaMemcpyAsync(d.ext_id, h->ext_of_int.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
-    BD_TRY(cudaMemsetAsync(d.moved, 0, nv, st));
-    BD_TRY(cudaMemsetAsync(d.disp, 0, np * sizeof(double2), st));
-    BD_TRY(cudaMemcpyAsync(d.tv, tv.data(), nt * sizeof(int4), cudaMemcpyHostToDevice, st));
-    BD_TRY(cudaMemcpyAsync(d.tn, tn.data(), nt * sizeof(int4), cudaMemcpyHostToDevice, st));
-    BD_TRY(cudaMemsetAsync(d.claim, 0, nt * sizeof(unsigned long long), st));
-    BD_TRY(cudaMemsetAsync(d.partner, 0, nt * sizeof(unsigned long long), st));
-    BD_TRY(cudaMemcpyAsync(d.iperm, iperm.data(), np_i * sizeof(int), cudaMemcpyHostToDevice, st));
-    BD_TRY(cudaMemcpyAsync(d.iorigin, iorg.data(), n_iblocks * sizeof(float2), cudaMemcpyHostToDevice, st));
-    BD_TRY(cudaMemcpyAsync(d.tile_species, tile_sp.data(), tile_sp.size(), cudaMemcpyHostToDevice, st));
-    BD_TRY(cudaMemsetAsync(d.fpart, 0, (size_t)c.nchunk * np * sizeof(double2), st));
-    BD_TRY(cudaMemsetAsync(d.ctl, 0, sizeof(BdCtl), st));
-    if (p.law == BD_LAW_SHORT) {
-      // reference positions far away: the first force evaluation builds the lists
-      std::vector<double2> far(np, make_double2(1e30, 1e30));
-      BD_TRY(cudaMemcpyAsync(d.vl_ref, far.data(), np * sizeof(double2), cudaMemcpyHostToDevice, st));
-      BD_TRY(cudaMemsetAsync(d.vl_cnt, 0, np * sizeof(int), st));
-      BD_TRY(cudaStreamSynchronize(st));
-    }
-    BD_TRY(bd_launch_work_copy(d, c, st));
-    BD_TRY(cudaStreamSynchronize(st));
-    if (bd_dt_grid_for(std::max(nt, np), &h->dt_grid, &h->dt_block) != 0) {
-      bd_free(h);
-      return BD_ERR_CUDA;
-    }
-  }
-#undef BD_TRY
-  *out = h;
-  return BD_OK;
-cuda_error:
-  bd_free(h);
-  return cuda_fail(e);
+int bd_init(const bd_params *p, const double *xy, const uint8_t *species, const float *theta,
+            void *stream, bd_handle **out) {
+  if (!out || !p) return BD_ERR_ARG;
+  std::vector<Spec> specs(1);
+  specs[0] = {*p, xy, species, theta};
+  return build_handle(specs, stream, out);
 }
 
-static int read_ctl(bd_handle *h) {
-  cudaError_t e = cudaMemcpyAsync(h->h_ctl, h->d.ctl, sizeof(BdCtl), cudaMemcpyDeviceToHost, h->stream);
-  if (e != cudaSuccess) return cuda_fail(e);
-  e = cudaStreamSynchronize(h->stream);
-  if (e != cudaSuccess) return cuda_fail(e);
-  return BD_OK;
-}
-
-static cudaError_t reset_stats(bd_handle *h) {
-  // zero everything after the barrier words, the status and the epoch
-  char *base = (char *)h->d.ctl;
-  size_t off = offsetof(BdCtl, cnt);
-  cudaError_t e = cudaMemsetAsync(base + off, 0, sizeof(BdCtl) - off, h->stream);
-  if (e != cudaSuccess) return e;
-  return cudaMemsetAsync(&h->d.ctl->status, 0, sizeof(int), h->stream);
+int bd_batch_init(int32_t R, const bd_params *p, const double *xy, const uint8_t *species,
+                  const float *theta, void *stream, bd_handle **out) {
+  if (!out || !p || R < 1) return BD_ERR_ARG;
+  std::vector<Spec> specs(R);
+  size_t off = 0;
+  for (int r = 0; r < R; ++r) {
+    specs[r] = {p[r], xy ? xy + 2 * off : nullptr, species ? species + off : nullptr,
+                theta ? theta + off : nullptr};
+    off += (size_t)std::max(0, p[r].n);
+  }
+  return build_handle(specs, stream, out);
 }
 
 int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
@@ -522,7 +818,8 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
   if (e != cudaSuccess) return cuda_fail(e);
   int64_t launches = 0;
   int timed = 0;
-  if (h->timing && h->c.law == BD_LAW_LONG) {
+  const bool long_range = h->c.any_long;
+  if (h->timing && long_range) {
     while ((int)h->ev_pool.size() < 2 * nsteps) {
       cudaEvent_t ev;
       if (cudaEventCreate(&ev) != cudaSuccess) return BD_ERR_CUDA;
@@ -530,7 +827,7 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
     }
   }
   for (int s = 0; s < nsteps; ++s) {
-    if (h->c.law == BD_LAW_LONG) {
+    if (long_range) {
       bool tm = h->timing;
       if (tm) cudaEventRecord(h->ev_pool[2 * s], st);
       e = bd_launch_force_long(h->d, h->c, st);
@@ -541,7 +838,7 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
       }
       ++launches;
     }
-    if (h->c.law == BD_LAW_SHORT) {
+    if (h->c.any_short) {
       e = bd_launch_force_short(h->d, h->c, st);
       if (e != cudaSuccess) return cuda_fail(e);
       launches += bd_short_launches();
@@ -584,59 +881,38 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
     memcpy(&mo, &bits, sizeof(mo));
     stats->max_overlap = mo;
   }
-  if (k.status) {
-    // clear the sticky status so the handle keeps working from the last good
-    // state; after a timed-out barrier also reset the barrier words
-    if (k.status == BD_ERR_DEVICE_TIMEOUT) cudaMemsetAsync(h->d.ctl, 0, offsetof(BdCtl, epoch), st);
-    cudaMemsetAsync(&h->d.ctl->cnt[0][0], 0, sizeof(h->d.ctl->cnt), st);
-    cudaMemsetAsync(&h->d.ctl->status, 0, sizeof(int), st);
-    cudaStreamSynchronize(st);
-    return k.status;
-  }
+  if (k.status) return finish_status(h, k.status);
   return BD_OK;
 }
 
 int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32_t *tri,
                  int32_t *n_tri, int64_t *step) {
   if (!h) return BD_ERR_ARG;
-  cudaStream_t st = h->stream;
   const int np = h->np, n = h->n;
-  cudaError_t e;
-  if (xy) {
-    std::vector<double2> pos(np);
-    e = cudaMemcpyAsync(pos.data(), h->d.pos, np * sizeof(double2), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e);
-    for (int i = 0; i < n; ++i) {
-      double2 v = pos[h->int_of_ext[i]];
-      xy[2 * i] = v.x;
-      xy[2 * i + 1] = v.y;
+  std::vector<double2> pos;
+  std::vector<float> t;
+  std::vector<uint8_t> s;
+  int rc = fetch_disks(h, xy ? &pos : nullptr, theta ? &t : nullptr, species ? &s : nullptr);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    const int k = h->int_of_ext[i];
+    if (xy) {
+      xy[2 * i] = pos[k].x;
+      xy[2 * i + 1] = pos[k].y;
     }
-  }
-  if (theta) {
-    std::vector<float> t(np);
-    e = cudaMemcpyAsync(t.data(), h->d.theta, np * sizeof(float), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e);
-    for (int i = 0; i < n; ++i) theta[i] = t[h->int_of_ext[i]];
-  }
-  if (species) {
-    std::vector<uint8_t> s(np);
-    e = cudaMemcpyAsync(s.data(), h->d.species, np, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e);
-    for (int i = 0; i < n; ++i) species[i] = s[h->int_of_ext[i]];
+    if (theta) theta[i] = t[k];
+    if (species) species[i] = s[k];
   }
   if (tri) {
     std::vector<int4> tv(h->nt);
-    e = cudaMemcpyAsync(tv.data(), h->d.tv, h->nt * sizeof(int4), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaError_t e = cudaMemcpyAsync(tv.data(), h->d.tv, h->nt * sizeof(int4), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e);
     auto ext = [&](int v) { return v < np ? h->ext_of_int[v] : n + (v - np); };
-    for (int t = 0; t < h->nt; ++t) {
-      tri[3 * t] = ext(tv[t].x);
-      tri[3 * t + 1] = ext(tv[t].y);
-      tri[3 * t + 2] = ext(tv[t].z);
+    for (int k = 0; k < h->nt; ++k) {
+      tri[3 * k] = ext(tv[k].x);
+      tri[3 * k + 1] = ext(tv[k].y);
+      tri[3 * k + 2] = ext(tv[k].z);
     }
   }
   if (n_tri) *n_tri = h->nt;
@@ -644,18 +920,60 @@ int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32
   return BD_OK;
 }
 
+int bd_get_replica(bd_handle *h, int32_t r, double *xy, float *theta, int32_t *tri, int32_t *n_tri,
+                   int32_t *n, double *L) {
+  if (!h || r < 0 || r >= (int)h->reps.size()) return BD_ERR_ARG;
+  const RepHost &RH = h->reps[r];
+  if (n) *n = RH.n;
+  if (L) *L = RH.L;
+  if (n_tri) *n_tri = RH.nt;
+  if (!xy && !theta && !tri) return BD_OK;
+  std::vector<double2> pos;
+  std::vector<float> t;
+  int rc = fetch_disks(h, xy ? &pos : nullptr, theta ? &t : nullptr, nullptr);
+  if (rc) return rc;
+  for (int i = 0; i < RH.n; ++i) {
+    const int k = h->int_of_ext[RH.ext_base + i];
+    if (xy) {
+      xy[2 * i] = pos[k].x;
+      xy[2 * i + 1] = pos[k].y;
+    }
+    if (theta) theta[i] = t[k];
+  }
+  if (tri) {
+    std::vector<int4> tv(RH.nt);
+    cudaError_t e = cudaMemcpyAsync(tv.data(), h->d.tv + RH.tri_base, RH.nt * sizeof(int4),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    auto loc = [&](int v) { return v < h->np ? h->ext_of_int[v] - RH.ext_base : RH.n + (v - RH.ghost_base); };
+    for (int k = 0; k < RH.nt; ++k) {
+      tri[3 * k] = loc(tv[k].x);
+      tri[3 * k + 1] = loc(tv[k].y);
+      tri[3 * k + 2] = loc(tv[k].z);
+    }
+  }
+  return BD_OK;
+}
+
 int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
   if (!h || !xy) return BD_ERR_ARG;
-  const int n = h->n, np = h->np;
+  const int np = h->np;
   const BdConst &c = h->c;
-  for (int i = 0; i < 2 * n; ++i)
-    if (!isfinite(xy[i]) || xy[i] < c.a - 1e-9 * c.L || xy[i] > c.L - c.a + 1e-9 * c.L)
-      return BD_ERR_INIT_OVERLAP;
-  if (bdhost::any_overlap(n, xy, 0.0, c.L, c.sigma * (1.0 - 1e-12))) return BD_ERR_INIT_OVERLAP;
-  for (int i = 0; i < n; ++i) {
-    int k = h->int_of_ext[i];
-    h->host_pos[2 * k] = std::min(c.wall_hi, std::max(c.wall_lo, snap_host(xy[2 * i], c.q, c.inv_q)));
-    h->host_pos[2 * k + 1] = std::min(c.wall_hi, std::max(c.wall_lo, snap_host(xy[2 * i + 1], c.q, c.inv_q)));
+  for (const RepHost &RH : h->reps) {
+    const double *x = xy + 2 * (size_t)RH.ext_base;
+    for (int i = 0; i < 2 * RH.n; ++i)
+      if (!isfinite(x[i]) || x[i] < c.a - 1e-9 * RH.L || x[i] > RH.L - c.a + 1e-9 * RH.L)
+        return BD_ERR_INIT_OVERLAP;
+    if (bdhost::any_overlap(RH.n, x, 0.0, RH.L, c.sigma * (1.0 - 1e-12))) return BD_ERR_INIT_OVERLAP;
+  }
+  for (const RepHost &RH : h->reps) {
+    const double *x = xy + 2 * (size_t)RH.ext_base;
+    for (int i = 0; i < RH.n; ++i) {
+      const int k = h->int_of_ext[RH.ext_base + i];
+      h->host_pos[2 * k] = std::min(RH.wall_hi, std::max(RH.wall_lo, snap_host(x[2 * i], c.q, c.inv_q)));
+      h->host_pos[2 * k + 1] = std::min(RH.wall_hi, std::max(RH.wall_lo, snap_host(x[2 * i + 1], c.q, c.inv_q)));
+    }
   }
   cudaStream_t st = h->stream;
   const BdDev &d = h->d;
@@ -664,28 +982,20 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(d.prev, d.pos, (size_t)np * sizeof(double2), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d.theta0, d.theta, (size_t)np * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d.pos, h->host_pos.data(), (size_t)np * sizeof(double2), cudaMemcpyHostToDevice, st);
+  std::vector<float> th;
   if (e == cudaSuccess && theta) {
-    std::vector<float> th(np, 0.f);
-    // keep the old directions of untouched slots: gather on the host
-    e = cudaMemcpyAsync(th.data(), d.theta, (size_t)np * sizeof(float), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    for (int i = 0; i < n && e == cudaSuccess; ++i) th[h->int_of_ext[i]] = theta[i];
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d.theta, th.data(), (size_t)np * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    th.assign(np, 0.f);
+    for (int i = 0; i < h->n; ++i) th[h->int_of_ext[i]] = theta[i];
+    e = cudaMemcpyAsync(d.theta, th.data(), (size_t)np * sizeof(float), cudaMemcpyHostToDevice, st);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(d.moved, 1, (size_t)np, st);
   if (e == cudaSuccess) e = bd_launch_work_copy(d, c, st);
   if (e == cudaSuccess) e = reset_stats(h);
   if (e == cudaSuccess) e = bd_launch_dt(d, c, 1, st, h->dt_grid, h->dt_block);
   if (e != cudaSuccess) return cuda_fail(e);
-  int rc = read_ctl(h);
+  int rc = read_ctl(h);   // synchronises the stream (the staged theta stays alive until here)
   if (rc) return rc;
-  if (h->h_ctl->status) {
-    int s = h->h_ctl->status;
-    cudaMemsetAsync(&h->d.ctl->status, 0, sizeof(int), st);
-    cudaStreamSynchronize(st);
-    return s;
-  }
+  if (h->h_ctl->status) return finish_status(h, h->h_ctl->status);
   return BD_OK;
 }
 
@@ -693,12 +1003,9 @@ int bd_compute_forces(bd_handle *h, double *F) {
   if (!h || !F) return BD_ERR_ARG;
   cudaStream_t st = h->stream;
   const int n = h->n, np = h->np;
-  if (h->c.law == BD_LAW_NONE) {
-    memset(F, 0, sizeof(double) * 2 * (size_t)n);
-    return BD_OK;
-  }
-  cudaError_t e = h->c.law == BD_LAW_SHORT ? bd_launch_force_short(h->d, h->c, st)
-                                           : bd_launch_force_long(h->d, h->c, st);
+  cudaError_t e = cudaSuccess;
+  if (h->c.any_long) e = bd_launch_force_long(h->d, h->c, st);
+  if (e == cudaSuccess && h->c.any_short) e = bd_launch_force_short(h->d, h->c, st);
   if (e == cudaSuccess) e = bd_launch_force_sum(h->d, h->c, h->d_fsum, st);
   std::vector<double2> f(np);
   if (e == cudaSuccess) e = cudaMemcpyAsync(f.data(), h->d_fsum, np * sizeof(double2), cudaMemcpyDeviceToHost, st);
@@ -706,12 +1013,7 @@ int bd_compute_forces(bd_handle *h, double *F) {
   if (e != cudaSuccess) return cuda_fail(e);
   int rc = read_ctl(h);
   if (rc) return rc;
-  if (h->h_ctl->status) {
-    int s = h->h_ctl->status;
-    cudaMemsetAsync(&h->d.ctl->status, 0, sizeof(int), st);
-    cudaStreamSynchronize(st);
-    return s;
-  }
+  if (h->h_ctl->status) return finish_status(h, h->h_ctl->status);
   for (int i = 0; i < n; ++i) {
     double2 v = f[h->int_of_ext[i]];
     F[2 * i] = v.x;
@@ -722,7 +1024,7 @@ int bd_compute_forces(bd_handle *h, double *F) {
 
 int bd_get_neighbors(bd_handle *h, int32_t max_per, int32_t *counts, int32_t *idx) {
   if (!h || !counts || max_per < 0 || (max_per > 0 && !idx)) return BD_ERR_ARG;
-  if (h->c.law != BD_LAW_SHORT) return BD_ERR_UNSUPPORTED;
+  if (!h->c.any_short) return BD_ERR_UNSUPPORTED;
   const int np = h->np, n = h->n;
   std::vector<int> cnt(np), vi((size_t)BD_VL_MAX * np);
   cudaStream_t st = h->stream;
@@ -746,7 +1048,15 @@ int bd_get_neighbors(bd_handle *h, int32_t max_per, int32_t *counts, int32_t *id
 int bd_get_geometry(bd_handle *h, double *q, double *L) {
   if (!h) return BD_ERR_ARG;
   if (q) *q = h->c.q;
-  if (L) *L = h->c.L;
+  if (L) *L = h->reps[0].L;
+  return BD_OK;
+}
+
+int bd_get_tuning(bd_handle *h, int32_t *tiles_per_item, int32_t *variant, int32_t *n_items) {
+  if (!h) return BD_ERR_ARG;
+  if (tiles_per_item) *tiles_per_item = h->tune_tiles;
+  if (variant) *variant = h->c.force_variant;
+  if (n_items) *n_items = h->c.n_items;
   return BD_OK;
 }
 

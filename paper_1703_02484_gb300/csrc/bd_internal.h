@@ -49,25 +49,44 @@ struct BdCtl {
 // counter slots within BdCtl::cnt[phase % 4]
 enum { C_INV = 0, C_REJECT = 1, C_FLIPS = 2, C_OVERLAP = 3, C_CAND = 4 };
 
+// Per-replica parameters (a handle advances R >= 1 independent systems; a
+// single system is R = 1).  Device-resident table read by the kernels.
+struct BdRep {
+  double L, wall_lo, wall_hi;
+  double dt, amp, amp_r, v0;
+  double eps, kappa, r_cut, skin, rl2, cell_size;
+  double alpha_d[4];
+  float alpha[4];
+  unsigned long long seed;
+  unsigned int replica;
+  int law;
+  int ncell, cell_base;          // short range: cells per side, first cell
+  int nchunk;                    // long range: j chunks (partial-force slots)
+  int slot_begin, slot_end;      // internal disk slots of this replica
+  int n;                         // disks
+};
+
 struct BdDev {
-  // particles (internal order, np slots + 4 corner points at the end)
+  // disks (internal order, np slots), then the ghost points of every replica
   double2 *pos, *prev, *pos0;
   float4 *work;            // (x_hi, y_hi, x_lo, y_lo) FP32 pair of each coordinate
   float *theta, *theta0;
   uint8_t *species;        // 255 = empty slot
-  int *ext_id;             // external index (-1 = empty slot)
+  int *ext_id;             // index within its replica (-1 = empty slot): the Philox counter
+  int *rep_of;             // replica of each slot (-1 = empty slot)
   uint8_t *moved;
   double2 *disp;
-  // triangulation (corner table)
+  const BdRep *rep;        // [R]
+  // triangulation (corner table), all replicas
   int4 *tv, *tn, *tv_snap, *tn_snap;
   unsigned long long *claim;
-  unsigned long long *partner;
   // force sweep
-  int *iperm;              // spatial order of i (np_i slots, -1 = none)
+  int *iperm;              // spatial order of i per block (np_i slots, -1 = none)
   float2 *iorigin;         // per i-block origin (integers)
   uint8_t *tile_species;   // species of each j tile
-  double2 *fpart;          // [nchunk][np] partial forces
-  // short range: Verlet lists (column-major ELL) and the cell grid
+  int4 *items;             // work items (i block, first tile, end tile, partial slot)
+  double2 *fpart;          // [max_nchunk][np] partial forces
+  // short range: Verlet lists (column-major ELL) and the cell grids
   int *vl_idx, *vl_cnt;
   double2 *vl_ref;
   int *cell_count, *cell_start, *cell_cursor, *cell_idx, *cell_of, *scan_sums;
@@ -75,28 +94,24 @@ struct BdDev {
 };
 
 struct BdConst {
-  int n, np, np_i, nt, ntiles, nchunk, n_iblocks;
-  int law, precision, n_species;
-  double a, sigma, L, wall_lo, wall_hi;
+  int n, np, np_i, nt, ntiles, n_iblocks;
+  int R;                   // replicas
+  int n_items;             // force work items (long range)
+  int max_nchunk;          // partial-force slots
+  int ncell_total;         // short range: cells of all replicas
+  int any_long, any_short;
+  int precision, n_species;
+  double a, sigma;
   double q, inv_q;
   int qshift;              // q = 2^-qshift
   unsigned long long sig2q_hi, sig2q_lo;  // ceil((sigma/q)^2 (1 + 1e-9)) as 128-bit
-  float alpha[4];
-  double alpha_d[4];
-  double eps, kappa, r_cut, skin;
-  double rl2;              // (r_cut + skin)^2
-  double cell_size;
-  int ncell;               // cells per side
-  double D, Dr, v0, dt;
-  double amp, amp_r;       // translational / rotational noise amplitude
-  uint64_t seed;
-  uint32_t replica;
   int max_corr_iters, max_flip_rounds;
   int force_variant;       // 0: scalar FP32 sweep, 1: packed f32x2 sweep
 };
 
 // launchers (kernels_*.cu)
 cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t s);
+cudaError_t bd_launch_force_long_variant(const BdDev &d, const BdConst &c, int variant, cudaStream_t s);
 cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, cudaStream_t s);
 cudaError_t bd_launch_dt(const BdDev &d, const BdConst &c, int mode, cudaStream_t s, int grid, int block);
 int bd_dt_grid(int *grid, int *block);

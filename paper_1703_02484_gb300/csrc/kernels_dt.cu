@@ -524,10 +524,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
         const double mag = sqrt(__dadd_rn(__dmul_rn(dd.x, dd.x), __dmul_rn(dd.y, dd.y)));
         const double sc = mag > cap ? cap / mag : 1.0;
         double nxp = snap(p.x + dd.x * sc, x.g), nyp = snap(p.y + dd.y * sc, x.g);
-        if (nxp < c.wall_lo) nxp = 2.0 * c.wall_lo - nxp;
-        if (nxp > c.wall_hi) nxp = 2.0 * c.wall_hi - nxp;
-        if (nyp < c.wall_lo) nyp = 2.0 * c.wall_lo - nyp;
-        if (nyp > c.wall_hi) nyp = 2.0 * c.wall_hi - nyp;
+        const BdRep &R = d.rep[d.rep_of[i]];
+        if (nxp < R.wall_lo) nxp = 2.0 * R.wall_lo - nxp;
+        if (nxp > R.wall_hi) nxp = 2.0 * R.wall_hi - nxp;
+        if (nyp < R.wall_lo) nyp = 2.0 * R.wall_lo - nyp;
+        if (nyp > R.wall_hi) nyp = 2.0 * R.wall_hi - nyp;
         const double2 np2 = make_double2(nxp, nyp);
         d.pos[i] = np2;
         d.work[i] = split_pos(np2);

@@ -55,7 +55,8 @@ __device__ __forceinline__ int ctl_failed(const BdCtl *ctl) { return *(volatile 
 __global__ void __launch_bounds__(BD_FT) k_force_long_f32(BdDev d, BdConst c) {
   if (ctl_failed(d.ctl)) return;
   __shared__ float4 sj[2][BD_TJ / 2];   // (x_j, y_j, x_j+1, y_j+1) re-centred
-  const int ib = blockIdx.x, jc = blockIdx.y, tid = threadIdx.x;
+  const int4 item = d.items[blockIdx.x];  // (i block, first tile, end tile, partial slot)
+  const int ib = item.x, slot = item.w, tid = threadIdx.x;
   const float2 org = d.iorigin[ib];
   float xi[BD_IPT], yi[BD_IPT], ax[BD_IPT], ay[BD_IPT];
   float fxh[BD_IPT], fxl[BD_IPT], fyh[BD_IPT], fyl[BD_IPT], a0[BD_IPT], a1[BD_IPT];
@@ -69,8 +70,9 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32(BdDev d, BdConst c) {
       xi[q] = __fadd_rn(__fsub_rn(w.x, org.x), w.z);
       yi[q] = __fadd_rn(__fsub_rn(w.y, org.y), w.w);
       int s = d.species[i];
-      a0[q] = c.alpha[2 * s + 0];
-      a1[q] = c.alpha[2 * s + 1];
+      const BdRep &R = d.rep[d.rep_of[i]];
+      a0[q] = R.alpha[2 * s + 0];
+      a1[q] = R.alpha[2 * s + 1];
     } else {
       xi[q] = 1.0e18f;
       yi[q] = 1.0e18f;
@@ -80,8 +82,7 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32(BdDev d, BdConst c) {
     ax[q] = ay[q] = 0.f;
     fxh[q] = fxl[q] = fyh[q] = fyl[q] = 0.f;
   }
-  const int t_begin = (int)(((long long)c.ntiles * jc) / c.nchunk);
-  const int t_end = (int)(((long long)c.ntiles * (jc + 1)) / c.nchunk);
+  const int t_begin = item.y, t_end = item.z;
   const float eps0 = 1e-20f * (float)(c.a * c.a);
 
   // stage: each thread re-centres 2 disks of the tile (BD_TJ = 2 * BD_FT)
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32(BdDev d, BdConst c) {
   for (int q = 0; q < BD_IPT; ++q) {
     int i = ii[q];
     if (i >= 0)
-      d.fpart[(size_t)jc * c.np + i] =
+      d.fpart[(size_t)slot * c.np + i] =
           make_double2((double)fxh[q] + (double)fxl[q], (double)fyh[q] + (double)fyl[q]);
   }
 }
@@ -185,7 +186,8 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32x2(BdDev d, BdConst c) 
   constexpr int NP = IPT / 2;
   constexpr int IB = BD_FT * IPT;
   __shared__ ulonglong2 sj[2][BD_TJ];   // per j: ((x, x), (y, y)) re-centred
-  const int ib = blockIdx.x, jc = blockIdx.y, tid = threadIdx.x;
+  const int4 item = d.items[blockIdx.x];  // (i block, first tile, end tile, partial slot)
+  const int ib = item.x, slot = item.w, tid = threadIdx.x;
   const float2 org = d.iorigin[ib];
   u64 xi2[NP], yi2[NP], ax2[NP], ay2[NP];
   float fxh[IPT], fxl[IPT], fyh[IPT], fyl[IPT], a0[IPT], a1[IPT];
@@ -203,8 +205,9 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32x2(BdDev d, BdConst c) 
         xs[h] = __fadd_rn(__fsub_rn(w.x, org.x), w.z);
         ys[h] = __fadd_rn(__fsub_rn(w.y, org.y), w.w);
         int sp = d.species[i];
-        a0[q] = c.alpha[2 * sp + 0];
-        a1[q] = c.alpha[2 * sp + 1];
+        const BdRep &R = d.rep[d.rep_of[i]];
+        a0[q] = R.alpha[2 * sp + 0];
+        a1[q] = R.alpha[2 * sp + 1];
       } else {
         xs[h] = 1.0e18f;
         ys[h] = 1.0e18f;
@@ -217,8 +220,7 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32x2(BdDev d, BdConst c) 
     yi2[k] = pk2(ys[0], ys[1]);
     ax2[k] = ay2[k] = 0ull;
   }
-  const int t_begin = (int)(((long long)c.ntiles * jc) / c.nchunk);
-  const int t_end = (int)(((long long)c.ntiles * (jc + 1)) / c.nchunk);
+  const int t_begin = item.y, t_end = item.z;
   const float e0 = 1e-20f * (float)(c.a * c.a);
   const u64 eps2 = pk2(e0, e0);
   float2 st0, st1;
@@ -279,50 +281,77 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32x2(BdDev d, BdConst c) 
   for (int q = 0; q < IPT; ++q) {
     int i = ii[q];
     if (i >= 0)
-      d.fpart[(size_t)jc * c.np + i] =
+      d.fpart[(size_t)slot * c.np + i] =
           make_double2((double)fxh[q] + (double)fxl[q], (double)fyh[q] + (double)fyl[q]);
   }
 }
 
-// FP64 variant (precision = 1): one disk per thread, FP64 master positions
+// FP64 variant (precision = 1): one disk per thread, FP64 master positions;
+// grid (disk blocks, j chunks), chunk k of a replica covers a k-th of its slots
 __global__ void __launch_bounds__(128) k_force_long_f64(BdDev d, BdConst c) {
   if (ctl_failed(d.ctl)) return;
   __shared__ double2 sp[128];
   __shared__ int ss[128];
   const int i = blockIdx.x * 128 + threadIdx.x;
   const int jc = blockIdx.y;
-  const bool live = i < c.np && d.ext_id[i] >= 0;
+  // a block's disks may span two replicas: each thread keeps its own range
+  const int r = i < c.np ? d.rep_of[i] : -1;
+  const bool live = r >= 0;
+  const BdRep &R = d.rep[live ? r : 0];
   double2 pi = live ? d.pos[i] : make_double2(0.0, 0.0);
   int si = live ? d.species[i] : 0;
   double fx = 0.0, fy = 0.0;
-  const int per = (c.np + c.nchunk - 1) / c.nchunk;
-  const int j_begin = jc * per, j_end = min(c.np, j_begin + per);
-  for (int j0 = j_begin; j0 < j_end; j0 += 128) {
+  const int span = R.slot_end - R.slot_begin;
+  const int per = (span + R.nchunk - 1) / R.nchunk;
+  const int my_begin = R.slot_begin + jc * per, my_end = min(R.slot_end, my_begin + per);
+  // the block walks the union of its threads' ranges; a thread skips foreign j
+  __shared__ int s_lo, s_hi;
+  if (threadIdx.x == 0) {
+    s_lo = 0x7FFFFFFF;
+    s_hi = -1;
+  }
+  __syncthreads();
+  if (live && jc < R.nchunk && my_begin < my_end) {
+    atomicMin(&s_lo, my_begin);
+    atomicMax(&s_hi, my_end);
+  }
+  __syncthreads();
+  for (int j0 = s_lo; j0 < s_hi; j0 += 128) {
     int j = j0 + threadIdx.x;
-    bool ok = j < j_end && d.ext_id[j] >= 0;
+    bool ok = j < s_hi && d.ext_id[j] >= 0;
     sp[threadIdx.x] = ok ? d.pos[j] : make_double2(0.0, 0.0);
     ss[threadIdx.x] = ok ? (int)d.species[j] : -1;
     __syncthreads();
-    int m = min(128, j_end - j0);
-    for (int k = 0; k < m; ++k) {
-      int sk = ss[k];
-      if (sk < 0 || j0 + k == i) continue;
-      double rx = pi.x - sp[k].x, ry = pi.y - sp[k].y;
-      double r2 = rx * rx + ry * ry;
-      double cf = c.alpha_d[2 * si + sk] / (r2 * sqrt(r2));
-      fx += cf * rx;
-      fy += cf * ry;
+    int m = min(128, s_hi - j0);
+    if (live && jc < R.nchunk) {
+      for (int k = 0; k < m; ++k) {
+        const int jj = j0 + k;
+        int sk = ss[k];
+        if (sk < 0 || jj == i || jj < my_begin || jj >= my_end) continue;
+        double rx = pi.x - sp[k].x, ry = pi.y - sp[k].y;
+        double r2 = rx * rx + ry * ry;
+        double cf = R.alpha_d[2 * si + sk] / (r2 * sqrt(r2));
+        fx += cf * rx;
+        fy += cf * ry;
+      }
     }
     __syncthreads();
   }
-  if (live) d.fpart[(size_t)jc * c.np + i] = make_double2(fx, fy);
+  if (live && jc < R.nchunk) d.fpart[(size_t)jc * c.np + i] = make_double2(fx, fy);
 }
 
 __global__ void k_force_sum(BdDev d, BdConst c, double2 *out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= c.np) return;
+  const int r = d.rep_of[i];
+  if (r < 0) {
+    out[i] = make_double2(0.0, 0.0);
+    return;
+  }
+  const BdRep &R = d.rep[r];
+  const int ns = R.law == BD_LAW_LONG ? R.nchunk : (R.law == BD_LAW_SHORT ? 1 : 0);
   double fx = 0.0, fy = 0.0;
-  for (int k = 0; k < c.nchunk; ++k) {
+  for (int k = 0; k < ns; ++k) {
     double2 f = d.fpart[(size_t)k * c.np + i];
     fx += f.x;
     fy += f.y;
@@ -346,20 +375,20 @@ __global__ void k_integrate(BdDev d, BdConst c, long long step) {
   if (i >= c.np) return;
   const int e = d.ext_id[i];
   if (e < 0) return;
+  const BdRep &R = d.rep[d.rep_of[i]];
   double fx = 0.0, fy = 0.0;
-  if (c.law != BD_LAW_NONE) {
-    for (int k = 0; k < c.nchunk; ++k) {
-      double2 f = d.fpart[(size_t)k * c.np + i];
-      fx += f.x;
-      fy += f.y;
-    }
+  const int ns = R.law == BD_LAW_LONG ? R.nchunk : (R.law == BD_LAW_SHORT ? 1 : 0);
+  for (int k = 0; k < ns; ++k) {
+    double2 f = d.fpart[(size_t)k * c.np + i];
+    fx += f.x;
+    fy += f.y;
   }
   const double2 p = d.pos[i];
   d.pos0[i] = p;
   d.prev[i] = p;
   const float th = d.theta[i];
   d.theta0[i] = th;
-  bdrng::U4 r = bdrng::draw((uint32_t)e, (int64_t)step, c.seed, c.replica, bdrng::TAG_NOISE);
+  bdrng::U4 r = bdrng::draw((uint32_t)e, (int64_t)step, R.seed, R.replica, bdrng::TAG_NOISE);
   double nx, ny;
   float thn;
   if (c.precision == 0) {
@@ -375,12 +404,12 @@ __global__ void k_integrate(BdDev d, BdConst c, long long step) {
     float z2 = fminf(3.0f, fmaxf(-3.0f, rb * c2));
     float st, ct;
     sincosf(th, &st, &ct);
-    const float dt = (float)c.dt, v0 = (float)c.v0, amp = (float)c.amp;
+    const float dt = (float)R.dt, v0 = (float)R.v0, amp = (float)R.amp;
     float dxf = dt * ((float)fx + v0 * ct) + amp * z0;
     float dyf = dt * ((float)fy + v0 * st) + amp * z1;
     nx = p.x + (double)dxf;
     ny = p.y + (double)dyf;
-    thn = th + (float)c.amp_r * z2;
+    thn = th + (float)R.amp_r * z2;
   } else {
     const double sc = 2.3283064365386962890625e-10;
     double u0 = ((double)r.x + 0.5) * sc, u1 = ((double)r.y + 0.5) * sc;
@@ -394,16 +423,16 @@ __global__ void k_integrate(BdDev d, BdConst c, long long step) {
     double z2 = fmin(3.0, fmax(-3.0, rb * c2));
     double st, ct;
     sincos((double)th, &st, &ct);
-    nx = p.x + c.dt * (fx + c.v0 * ct) + c.amp * z0;
-    ny = p.y + c.dt * (fy + c.v0 * st) + c.amp * z1;
-    thn = (float)((double)th + c.amp_r * z2);
+    nx = p.x + R.dt * (fx + R.v0 * ct) + R.amp * z0;
+    ny = p.y + R.dt * (fy + R.v0 * st) + R.amp * z1;
+    thn = (float)((double)th + R.amp_r * z2);
   }
   nx = snapd(nx, c.q, c.inv_q);
   ny = snapd(ny, c.q, c.inv_q);
-  if (nx < c.wall_lo) nx = 2.0 * c.wall_lo - nx;
-  if (nx > c.wall_hi) nx = 2.0 * c.wall_hi - nx;
-  if (ny < c.wall_lo) ny = 2.0 * c.wall_lo - ny;
-  if (ny > c.wall_hi) ny = 2.0 * c.wall_hi - ny;
+  if (nx < R.wall_lo) nx = 2.0 * R.wall_lo - nx;
+  if (nx > R.wall_hi) nx = 2.0 * R.wall_hi - nx;
+  if (ny < R.wall_lo) ny = 2.0 * R.wall_lo - ny;
+  if (ny > R.wall_hi) ny = 2.0 * R.wall_hi - ny;
   const double2 pn = make_double2(nx, ny);
   d.pos[i] = pn;
   d.work[i] = split(pn);
@@ -429,16 +458,21 @@ int bd_force_blocks_per_sm(int variant) {
   return e == cudaSuccess ? per : 0;
 }
 
-cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t s) {
+cudaError_t bd_launch_force_long_variant(const BdDev &d, const BdConst &c, int variant, cudaStream_t s) {
   if (c.precision == 0) {
-    if (c.force_variant == 1)
-      k_force_long_f32x2<BD_IPT><<<dim3(c.n_iblocks, c.nchunk), BD_FT, 0, s>>>(d, c);
+    if (c.n_items == 0) return cudaSuccess;
+    if (variant == 1)
+      k_force_long_f32x2<BD_IPT><<<c.n_items, BD_FT, 0, s>>>(d, c);
     else
-      k_force_long_f32<<<dim3(c.n_iblocks, c.nchunk), BD_FT, 0, s>>>(d, c);
+      k_force_long_f32<<<c.n_items, BD_FT, 0, s>>>(d, c);
   } else {
-    k_force_long_f64<<<dim3((c.np + 127) / 128, c.nchunk), 128, 0, s>>>(d, c);
+    k_force_long_f64<<<dim3((c.np + 127) / 128, c.max_nchunk), 128, 0, s>>>(d, c);
   }
   return cudaGetLastError();
+}
+
+cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t s) {
+  return bd_launch_force_long_variant(d, c, c.force_variant, s);
 }
 
 cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, cudaStream_t s) {

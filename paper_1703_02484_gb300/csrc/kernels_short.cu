@@ -67,56 +67,75 @@ __device__ __forceinline__ ff ff_div(ff a, ff b) {
 __device__ __forceinline__ int failed(const BdCtl *ctl) { return *(volatile const int *)&ctl->status; }
 __device__ __forceinline__ int need(const BdCtl *ctl) { return *(volatile const int *)&ctl->vl_need; }
 
-__device__ __forceinline__ int cell_of(double2 p, const BdConst &c) {
-  int cx = (int)(p.x / c.cell_size);
-  int cy = (int)(p.y / c.cell_size);
-  cx = cx < 0 ? 0 : (cx >= c.ncell ? c.ncell - 1 : cx);
-  cy = cy < 0 ? 0 : (cy >= c.ncell ? c.ncell - 1 : cy);
-  return cy * c.ncell + cx;
+__device__ __forceinline__ int cell_of(double2 p, const BdRep &R) {
+  int cx = (int)(p.x / R.cell_size);
+  int cy = (int)(p.y / R.cell_size);
+  cx = cx < 0 ? 0 : (cx >= R.ncell ? R.ncell - 1 : cx);
+  cy = cy < 0 ? 0 : (cy >= R.ncell ? R.ncell - 1 : cy);
+  return R.cell_base + cy * R.ncell + cx;
+}
+
+// replica of slot i if it is a disk of a short-range replica, else null
+__device__ __forceinline__ const BdRep *short_rep(const BdDev &d, int i) {
+  const int r = d.rep_of[i];
+  if (r < 0) return nullptr;
+  const BdRep *R = &d.rep[r];
+  return R->law == BD_LAW_SHORT ? R : nullptr;
+}
+
+// block-uniform early exit: one thread reads the flags
+__device__ __forceinline__ bool skip_block(const BdCtl *ctl, bool need_rebuild) {
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = failed(ctl) || (need_rebuild && !need(ctl));
+  __syncthreads();
+  return s_skip != 0;
 }
 
 }  // namespace
 
 // 1. displacement trigger: some disk moved more than skin/2 since the build
 __global__ void k_vl_check(BdDev d, BdConst c) {
-  if (failed(d.ctl)) return;
+  if (skip_block(d.ctl, false)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool hit = false;
-  if (i < c.np && d.ext_id[i] >= 0) {
-    double2 p = d.pos[i], r = d.vl_ref[i];
-    double dx = p.x - r.x, dy = p.y - r.y;
-    hit = dx * dx + dy * dy > 0.25 * c.skin * c.skin;
+  if (i < c.np) {
+    const BdRep *R = short_rep(d, i);
+    if (R) {
+      double2 p = d.pos[i], r = d.vl_ref[i];
+      double dx = p.x - r.x, dy = p.y - r.y;
+      hit = dx * dx + dy * dy > 0.25 * R->skin * R->skin;
+    }
   }
   if (__any_sync(0xffffffffu, hit) && (threadIdx.x & 31) == 0) atomicExch(&d.ctl->vl_need, 1);
 }
 
-// 2. clear cell counts
+// 2. clear cell counts (grid-stride)
 __global__ void k_vl_clear(BdDev d, BdConst c) {
-  if (failed(d.ctl) || !need(d.ctl)) return;
-  const int nc2 = c.ncell * c.ncell;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nc2; k += gridDim.x * blockDim.x)
+  if (skip_block(d.ctl, true)) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < c.ncell_total; k += gridDim.x * blockDim.x)
     d.cell_count[k] = 0;
 }
 
-// 3. count disks per cell
+// 3. count disks per cell (grid-stride)
 __global__ void k_vl_count(BdDev d, BdConst c) {
-  if (failed(d.ctl) || !need(d.ctl)) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= c.np) return;
-  if (d.ext_id[i] < 0) {
-    d.cell_of[i] = -1;
-    return;
+  if (skip_block(d.ctl, true)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.np; i += gridDim.x * blockDim.x) {
+    const BdRep *R = short_rep(d, i);
+    if (!R || d.ext_id[i] < 0) {
+      d.cell_of[i] = -1;
+      continue;
+    }
+    int k = cell_of(d.pos[i], *R);
+    d.cell_of[i] = k;
+    atomicAdd(&d.cell_count[k], 1);
   }
-  int k = cell_of(d.pos[i], c);
-  d.cell_of[i] = k;
-  atomicAdd(&d.cell_count[k], 1);
 }
 
 // 4a. exclusive scan within blocks of BD_SCAN_B cells
 __global__ void __launch_bounds__(BD_SCAN_B) k_scan_blocks(BdDev d, BdConst c) {
-  if (failed(d.ctl) || !need(d.ctl)) return;
+  if (skip_block(d.ctl, true)) return;
   __shared__ int s[BD_SCAN_B];
-  const int nc2 = c.ncell * c.ncell;
+  const int nc2 = c.ncell_total;
   int k = blockIdx.x * BD_SCAN_B + threadIdx.x;
   int v = k < nc2 ? d.cell_count[k] : 0;
   s[threadIdx.x] = v;
@@ -133,7 +152,7 @@ __global__ void __launch_bounds__(BD_SCAN_B) k_scan_blocks(BdDev d, BdConst c) {
 
 // 4b. exclusive scan of the block sums (one block, sequential chunks)
 __global__ void __launch_bounds__(BD_SCAN_B) k_scan_top(BdDev d, BdConst c, int nblocks) {
-  if (failed(d.ctl) || !need(d.ctl)) return;
+  if (skip_block(d.ctl, true)) return;
   __shared__ int s[BD_SCAN_B];
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
@@ -158,8 +177,8 @@ __global__ void __launch_bounds__(BD_SCAN_B) k_scan_top(BdDev d, BdConst c, int 
 
 // 4c. add block offsets; reset the scatter cursors
 __global__ void __launch_bounds__(BD_SCAN_B) k_scan_add(BdDev d, BdConst c) {
-  if (failed(d.ctl) || !need(d.ctl)) return;
-  const int nc2 = c.ncell * c.ncell;
+  if (skip_block(d.ctl, true)) return;
+  const int nc2 = c.ncell_total;
   int k = blockIdx.x * BD_SCAN_B + threadIdx.x;
   if (k < nc2) {
     int v = d.cell_start[k] + d.scan_sums[blockIdx.x];
@@ -168,64 +187,66 @@ __global__ void __launch_bounds__(BD_SCAN_B) k_scan_add(BdDev d, BdConst c) {
   }
 }
 
-// 5. scatter disk ids into cell order
+// 5. scatter disk ids into cell order (grid-stride)
 __global__ void k_vl_scatter(BdDev d, BdConst c) {
-  if (failed(d.ctl) || !need(d.ctl)) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= c.np) return;
-  int k = d.cell_of[i];
-  if (k < 0) return;
-  int slot = atomicAdd(&d.cell_cursor[k], 1);
-  d.cell_idx[slot] = i;
+  if (skip_block(d.ctl, true)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.np; i += gridDim.x * blockDim.x) {
+    int k = d.cell_of[i];
+    if (k < 0) continue;
+    int slot = atomicAdd(&d.cell_cursor[k], 1);
+    d.cell_idx[slot] = i;
+  }
 }
 
-// 6. per-disk neighbour lists (sorted), reference positions
+// 6. per-disk neighbour lists (sorted), reference positions (grid-stride)
 __global__ void k_vl_build(BdDev d, BdConst c) {
-  if (failed(d.ctl) || !need(d.ctl)) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= c.np) return;
-  if (d.ext_id[i] < 0) {
-    d.vl_cnt[i] = 0;
-    return;
-  }
-  const double2 p = d.pos[i];
-  d.vl_ref[i] = p;
-  const int k = d.cell_of[i];
-  const int cx = k % c.ncell, cy = k / c.ncell;
-  int buf[BD_VL_MAX];
-  int m = 0;
-  bool over = false;
-  for (int gy = cy - 1; gy <= cy + 1; ++gy) {
-    if (gy < 0 || gy >= c.ncell) continue;
-    for (int gx = cx - 1; gx <= cx + 1; ++gx) {
-      if (gx < 0 || gx >= c.ncell) continue;
-      int cc = gy * c.ncell + gx;
-      int b = d.cell_start[cc], e = b + d.cell_count[cc];
-      for (int s = b; s < e; ++s) {
-        int j = d.cell_idx[s];
-        if (j == i) continue;
-        double2 q = d.pos[j];
-        double dx = __dsub_rn(p.x, q.x), dy = __dsub_rn(p.y, q.y);
-        double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-        if (r2 < c.rl2) {
-          if (m < BD_VL_MAX) {
-            // insertion in sorted position
-            int t = m++;
-            while (t > 0 && buf[t - 1] > j) {
-              buf[t] = buf[t - 1];
-              --t;
+  if (skip_block(d.ctl, true)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.np; i += gridDim.x * blockDim.x) {
+    const BdRep *Rp = short_rep(d, i);
+    if (!Rp || d.ext_id[i] < 0) {
+      d.vl_cnt[i] = 0;
+      continue;
+    }
+    const BdRep &R = *Rp;
+    const double2 p = d.pos[i];
+    d.vl_ref[i] = p;
+    const int k = d.cell_of[i] - R.cell_base;
+    const int cx = k % R.ncell, cy = k / R.ncell;
+    int buf[BD_VL_MAX];
+    int m = 0;
+    bool over = false;
+    for (int gy = cy - 1; gy <= cy + 1; ++gy) {
+      if (gy < 0 || gy >= R.ncell) continue;
+      for (int gx = cx - 1; gx <= cx + 1; ++gx) {
+        if (gx < 0 || gx >= R.ncell) continue;
+        int cc = R.cell_base + gy * R.ncell + gx;
+        int b = d.cell_start[cc], e = b + d.cell_count[cc];
+        for (int s = b; s < e; ++s) {
+          int j = d.cell_idx[s];
+          if (j == i) continue;
+          double2 q = d.pos[j];
+          double dx = __dsub_rn(p.x, q.x), dy = __dsub_rn(p.y, q.y);
+          double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+          if (r2 < R.rl2) {
+            if (m < BD_VL_MAX) {
+              // insertion in sorted position
+              int t = m++;
+              while (t > 0 && buf[t - 1] > j) {
+                buf[t] = buf[t - 1];
+                --t;
+              }
+              buf[t] = j;
+            } else {
+              over = true;
             }
-            buf[t] = j;
-          } else {
-            over = true;
           }
         }
       }
     }
+    for (int t = 0; t < m; ++t) d.vl_idx[(size_t)t * c.np + i] = buf[t];
+    d.vl_cnt[i] = m;
+    if (over) atomicCAS(&d.ctl->status, 0, BD_ERR_UNSUPPORTED);
   }
-  for (int t = 0; t < m; ++t) d.vl_idx[(size_t)t * c.np + i] = buf[t];
-  d.vl_cnt[i] = m;
-  if (over) atomicCAS(&d.ctl->status, 0, BD_ERR_UNSUPPORTED);
 }
 
 // 7. short-range force over the lists; clears the rebuild flag
@@ -239,12 +260,14 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
     }
   }
   if (i >= c.np) return;
-  if (d.ext_id[i] < 0) return;
+  const BdRep *Rp = short_rep(d, i);
+  if (!Rp || d.ext_id[i] < 0) return;
+  const BdRep &R = *Rp;
   const float4 wi = d.work[i];
   const double2 pi = d.pos[i];
   const int m = d.vl_cnt[i];
-  const float rc2 = (float)(c.r_cut * c.r_cut);
-  const float sg = (float)c.sigma, eps = (float)c.eps, kap = (float)c.kappa;
+  const float rc2 = (float)(R.r_cut * R.r_cut);
+  const float sg = (float)c.sigma, eps = (float)R.eps, kap = (float)R.kappa;
   const float rwca2 = (float)(1.2599210498948732 * c.sigma * c.sigma);  // (2^(1/6) s)^2
   float fx = 0.f, fy = 0.f;      // Yukawa tail, FP32
   ff gx = {0.f, 0.f}, gy = {0.f, 0.f};   // WCA core, float-float sums
@@ -259,7 +282,7 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
       // at the cut-off the force jumps: decide as the FP64 reference does
       double2 pj = d.pos[j];
       double ex = __dsub_rn(pi.x, pj.x), ey = __dsub_rn(pi.y, pj.y);
-      if (!(sqrt(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey))) < c.r_cut)) continue;
+      if (!(sqrt(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey))) < R.r_cut)) continue;
     } else if (r2 >= rc2) {
       continue;
     }
@@ -290,18 +313,22 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
 }
 
 cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t s) {
+  if (!c.any_short) return cudaSuccess;
   const int b = 256;
   const int gn = (c.np + b - 1) / b;
-  const int nc2 = c.ncell * c.ncell;
-  const int nsb = (nc2 + BD_SCAN_B - 1) / BD_SCAN_B;
+  const int nsb = (c.ncell_total + BD_SCAN_B - 1) / BD_SCAN_B;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int gs = 4 * sms;   // grid-stride launches: cheap when no rebuild is due
   k_vl_check<<<gn, b, 0, s>>>(d, c);
-  k_vl_clear<<<(nc2 + b - 1) / b, b, 0, s>>>(d, c);
-  k_vl_count<<<gn, b, 0, s>>>(d, c);
+  k_vl_clear<<<gs, b, 0, s>>>(d, c);
+  k_vl_count<<<gs, b, 0, s>>>(d, c);
   k_scan_blocks<<<nsb, BD_SCAN_B, 0, s>>>(d, c);
   k_scan_top<<<1, BD_SCAN_B, 0, s>>>(d, c, nsb);
   k_scan_add<<<nsb, BD_SCAN_B, 0, s>>>(d, c);
-  k_vl_scatter<<<gn, b, 0, s>>>(d, c);
-  k_vl_build<<<(c.np + 127) / 128, 128, 0, s>>>(d, c);
+  k_vl_scatter<<<gs, b, 0, s>>>(d, c);
+  k_vl_build<<<gs, 128, 0, s>>>(d, c);
   k_force_verlet<<<gn, b, 0, s>>>(d, c);
   return cudaGetLastError();
 }

@@ -257,3 +257,18 @@ def near_contact_state(n: int, L: float, a: float, seed: int, gap: float = 0.02,
         xy[i] = cand
         grid.setdefault(key(cand), set()).add(i)
     return xy
+
+
+def batch_configs(R: int = 256, seed: int = 3, n_lo: int = 512, n_hi: int = 65536):
+    """The batched workload: R replicas, N log-uniform in [n_lo, n_hi], area
+    fraction U[0.30, 0.50]; even replicas take c1's long-range law (alpha 0.1,
+    passive, dt 1e-4), odd replicas c3's short-range law (WCA + Yukawa, ABP
+    v0 0.5, D_r 0.2, dt 5e-5); all FP32.  Replica r draws its noise from key
+    (seed, r)."""
+    ns, rhos, laws = replica_table(R, seed, n_lo, n_hi)
+    out = []
+    for r in range(R):
+        base = CONFIGS["c1"] if laws[r] == LAW_LONG else CONFIGS["c3"]
+        out.append(replace(base, name="c4r%d" % r, n=int(ns[r]), rho=float(rhos[r]), seed=seed,
+                           precision=0, extra={"replica": r}))
+    return out
