@@ -177,6 +177,68 @@ def cpu_baseline(cfg, xy, sp, th):
                       "OpenMP over %d threads, Delaunay rebuilds and overlap correction): %.2f s" % (cores, t)}
 
 
+def run_batched(args):
+    """Batched workload: 256 replicas advanced together, against the same
+    replicas advanced one handle at a time (the plain single-system step)."""
+    import torch
+    import paper_1703_02484_gb300 as bd
+    from paper_1703_02484_gb300 import workloads
+    torch.cuda.set_device(0)
+    cfgs = workloads.batch_configs(256)
+    params = []
+    for r, cfg in enumerate(cfgs):
+        p = bd.params_from_config(cfg)
+        p.replica = r
+        p.seed = 3 + 1000 * r
+        params.append(p)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    b = bd.System(params, stream=stream.cuda_stream)
+    t_init = time.perf_counter() - t0
+    N = b.n
+    for _ in range(args.warmup):
+        b.step(1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        st = b.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    tune = b.tuning()
+    b.close()
+    # the same replicas one handle at a time (sampled: every 8th replica)
+    sample = list(range(0, 256, 8))
+    alone_ms = 0.0
+    n_sample = 0
+    for r in sample:
+        s1 = bd.System(params[r], stream=stream.cuda_stream)
+        for _ in range(2):
+            s1.step(1)
+        torch.cuda.synchronize()
+        a0 = time.perf_counter()
+        s1.step(args.steps)
+        torch.cuda.synchronize()
+        alone_ms += (time.perf_counter() - a0) * 1e3 / args.steps
+        n_sample += params[r].n
+        s1.close()
+    seq_ms = alone_ms * (256 / len(sample))
+    line = {"metric": "particle-steps/s (c4: 256 batched replicas)", "value": N / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "c4: 256 replicas, N log-uniform [512, 65536] (sum %d), rho U[0.3,0.5], "
+                                   "half c1 long-range law, half c3 short-range law" % N,
+                       "N": N, "init_s": t_init, "tuning": tune,
+                       "sequential_ms_per_step_estimate": seq_ms,
+                       "sequential_sample": "every 8th replica alone, scaled by 8",
+                       "batched_speedup": seq_ms / ms,
+                       "steps_done": st["steps_done"], "rejected": st["rejected"]},
+            "clocks": clk.summary(), "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,6 +254,9 @@ def main():
         run_reference(args)
         return
     args.warmup = max(3, args.warmup)
+    if args.workload == "c4":
+        run_batched(args)
+        return
 
     import torch
     import paper_1703_02484_gb300 as bd
