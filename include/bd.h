@@ -271,6 +271,66 @@ int bd_triangulate(int32_t n, const double *xy, double L, double a, double *xy_g
 int bd_forces_noalloc(int32_t n, const double *xy, const uint8_t *species, const double alpha[4],
                       double *F, void *stream);
 
+/* ---- Differentiated rollout (no counterpart in the paper) ----
+ * Gradients of a loss of a whole rollout with respect to the pair-force table
+ * A (bd_params.alpha, Sec. 2.2) and the self-propulsion speed v0 (Sec. 7), by
+ * a hand-written reverse-mode adjoint.  The differentiated map is the time
+ * step with its random and discrete choices frozen as the recorded run made
+ * them: the Philox noise, the wall reflections of every move, and for every
+ * correction pass (Algorithm 2) its overlapping pairs and which disks had
+ * their displacement capped at sigma/4.  Rounding to the position grid is
+ * taken as the identity.  Long-range law and single-system handles only.
+ * Pair terms of the adjoint are computed in FP32, every sum in FP64. */
+
+enum { BD_LOSS_MSD = 0 };
+
+/* Replace the force table (alpha: 4 doubles as bd_params.alpha, NULL = keep)
+ * and the self-propulsion speed (v0; NaN = keep) of every replica.  Discards
+ * a recorded rollout.  Errors: BD_ERR_ARG (non-finite alpha), BD_ERR_CUDA. */
+int bd_set_force_params(bd_handle *h, const double *alpha, double v0);
+
+/* Set the index of the next step (the Philox counter of its noise). */
+int bd_set_step(bd_handle *h, int64_t step);
+
+/* Advance nsteps steps exactly as bd_step does, recording the frozen choices
+ * and a checkpoint (positions, directions) every ckpt_every steps, then form
+ * the loss at the final positions x_T against the positions x_0 at the call:
+ *   BD_LOSS_MSD:  L = sum over species s of (MSD_s - target)^2,
+ *                 MSD_s = mean over disks of species s of |x_T - x_0|^2.
+ *   loss   receives L (may be NULL).   stats  as bd_step (may be NULL).
+ * Device memory: nsteps*N bytes of reflection flags, N bytes per correction
+ * pass, 8 bytes per overlapping pair, 20*N bytes per checkpoint.
+ * On a step failure the handle holds the state before the failed step, as
+ * bd_step leaves it, and no rollout is recorded.
+ * Errors: BD_ERR_ARG (nsteps < 1, ckpt_every < 1), BD_ERR_UNSUPPORTED
+ * (short-range law, batched handle, unknown loss_kind), the bd_step errors,
+ * BD_ERR_NOMEM, BD_ERR_CUDA. */
+int bd_rollout(bd_handle *h, int32_t nsteps, int32_t ckpt_every, int32_t loss_kind, double target,
+               double *loss, bd_step_stats *stats);
+
+/* Reverse pass of the last recorded rollout: grad receives 5 doubles,
+ * dL/dA00, dL/dA01, dL/dA10, dL/dA11, dL/dv0 (one species: dL/dalpha[0] in
+ * slot 0 and zeros in 1..3).  Segments are replayed from their checkpoints;
+ * the handle's state is not changed.  May be called more than once.
+ * Errors: BD_ERR_ARG (no recorded rollout), BD_ERR_NOMEM, BD_ERR_CUDA. */
+int bd_rollout_vjp(bd_handle *h, double *grad);
+
+/* The loss of the recorded rollout replayed with frozen choices from its
+ * start with another force table / speed (alpha NULL or v0 NaN = as
+ * recorded): the function bd_rollout_vjp differentiates, for finite
+ * differences.  The handle's state and recorded rollout are not changed.
+ * Errors: BD_ERR_ARG (no recorded rollout), BD_ERR_CUDA. */
+int bd_rollout_replay(bd_handle *h, const double *alpha, double v0, double *loss);
+
+/* Positions of the recorded rollout in external order (2n doubles): which = 0
+ * the start x_0, which = 1 where the last replay stopped: x_T after
+ * bd_rollout_replay (the reverse pass of bd_rollout_vjp ends its replays at
+ * the end of the first checkpoint segment).  Errors: BD_ERR_ARG. */
+int bd_rollout_positions(bd_handle *h, int32_t which, double *xy);
+
+/* Size of the recorded log: correction passes and overlapping pairs. */
+int bd_rollout_log_size(bd_handle *h, int32_t *n_pass, int32_t *n_pairs);
+
 /* Release the handle and its device memory (NULL is ignored). */
 void bd_free(bd_handle *h);
 

@@ -46,6 +46,11 @@ def lib():
             L.oracle_force_long.argtypes = [ctypes.c_int, p, p, p, p, ctypes.c_int, ctypes.c_int,
                                             p, p, ctypes.c_int]
             L.oracle_force_long.restype = None
+            L.oracle_force_long_jvp.argtypes = [ctypes.c_int, p, p, p, p, ctypes.c_int, p, p, p, p,
+                                                ctypes.c_int]
+            L.oracle_force_long_jvp.restype = None
+            L.oracle_force_long_dA.argtypes = [ctypes.c_int, p, p, p, p, ctypes.c_int]
+            L.oracle_force_long_dA.restype = None
             L.oracle_has_openmp.restype = ctypes.c_int
             _lib = L
         return _lib

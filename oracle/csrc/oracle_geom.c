@@ -448,6 +448,68 @@ void oracle_force_long(int n, const double *x, const double *y, const uint8_t *s
     (void)nthreads;
 }
 
+/* Derivatives of the long-range force F_i = sum_j A[s_i][s_j] r_ij/|r_ij|^3,
+ * r_ij = r_i - r_j (Sec. 2.2), for the differentiated rollout.
+ *
+ * oracle_force_long_jvp: K directions t (tx[k*n + i], ty[k*n + i]); out
+ * receives (dF/dx) t, i.e. for every i
+ *   sum_j A[s_i][s_j] M(r_ij) (t_i - t_j),   M(r) = I/|r|^3 - 3 r r^T/|r|^5,
+ * the derivative of r/|r|^3 with respect to r. */
+void oracle_force_long_jvp(int n, const double *x, const double *y, const uint8_t *s, const double *A,
+                           int K, const double *tx, const double *ty, double *ox, double *oy,
+                           int nthreads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int i = 0; i < n; i++) {
+        for (int k = 0; k < K; k++) {
+            double ax = 0.0, ay = 0.0;
+            const double *txk = tx + (size_t)k * n, *tyk = ty + (size_t)k * n;
+            for (int j = 0; j < n; j++) {
+                if (j == i) continue;
+                double rx = x[i] - x[j], ry = y[i] - y[j];
+                double r2 = rx * rx + ry * ry;
+                double r = sqrt(r2);
+                double r3 = r2 * r, r5 = r3 * r2;
+                double dx = txk[i] - txk[j], dy = tyk[i] - tyk[j];
+                double c = A[2 * s[i] + s[j]];
+                /* M (dx, dy) */
+                double mx = dx / r3 - 3.0 * rx * (rx * dx + ry * dy) / r5;
+                double my = dy / r3 - 3.0 * ry * (rx * dx + ry * dy) / r5;
+                ax += c * mx;
+                ay += c * my;
+            }
+            ox[(size_t)k * n + i] = ax;
+            oy[(size_t)k * n + i] = ay;
+        }
+    }
+    (void)nthreads;
+}
+
+/* oracle_force_long_dA: S[i][b] = sum over j != i with s_j = b of r_ij/|r_ij|^3,
+ * stored as S[4*i + 2*b + 0] (x) and S[4*i + 2*b + 1] (y); then
+ * dF_i/dA[a][b] = S[i][b] when s_i = a, else 0. */
+void oracle_force_long_dA(int n, const double *x, const double *y, const uint8_t *s, double *S,
+                          int nthreads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int i = 0; i < n; i++) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int j = 0; j < n; j++) {
+            if (j == i) continue;
+            double rx = x[i] - x[j], ry = y[i] - y[j];
+            double r2 = rx * rx + ry * ry;
+            double r = sqrt(r2);
+            int b = s[j] ? 1 : 0;
+            acc[2 * b] += rx / (r2 * r);
+            acc[2 * b + 1] += ry / (r2 * r);
+        }
+        for (int q = 0; q < 4; q++) S[4 * i + q] = acc[q];
+    }
+    (void)nthreads;
+}
+
 int oracle_has_openmp(void) {
 #ifdef _OPENMP
     return 1;

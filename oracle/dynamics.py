@@ -33,14 +33,19 @@ def reflect(xy, a, L):
     return xy
 
 
-def em_step(xy, theta, F, ids, step, seed, D, Dr, v0, dt, a, L, replica=0, literal_amp=False):
-    """One Euler-Maruyama + ABP step with reflection.  Returns (xy', theta')."""
+def em_move(xy, theta, F, ids, step, seed, D, Dr, v0, dt, replica=0, literal_amp=False):
+    """The Euler-Maruyama + ABP move before the walls.  Returns (xy', theta')."""
     xi_x, xi_y, n_th, _ = noise.normals(ids, step, seed, replica)
     amp = noise_amplitude(D, dt, literal_amp)
     th = np.asarray(theta, dtype=np.float64)
     dx = dt * (F[:, 0] + v0 * np.cos(th)) + amp * xi_x
     dy = dt * (F[:, 1] + v0 * np.sin(th)) + amp * xi_y
     new = np.stack([xy[:, 0] + dx, xy[:, 1] + dy], axis=1)
-    new = reflect(new, a, L)
     th_new = th + math.sqrt(2.0 * Dr * dt) * n_th
     return new, th_new
+
+
+def em_step(xy, theta, F, ids, step, seed, D, Dr, v0, dt, a, L, replica=0, literal_amp=False):
+    """One Euler-Maruyama + ABP step with reflection.  Returns (xy', theta')."""
+    new, th_new = em_move(xy, theta, F, ids, step, seed, D, Dr, v0, dt, replica, literal_amp)
+    return reflect(new, a, L), th_new

@@ -80,7 +80,7 @@ def correct(xy, L, a, max_iters=10000, tris=None, record=None):
         if len(pairs) == 0:
             return xy, tris, it, total, False
         if record is not None:
-            record.append({"pairs": pairs, "capped": capped, "disp": disp})
+            record.append({"pairs": pairs, "capped": capped, "disp": disp, "xy": xy})
         if len(reversed_edges(xy, new, E)):
             return xy, tris, it, total, True
         total += len(pairs)

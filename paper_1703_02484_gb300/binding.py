@@ -17,6 +17,7 @@ ERRORS = {
     -10: "BD_ERR_UNSUPPORTED",
 }
 LAW_NONE, LAW_LONG, LAW_SHORT = 0, 1, 2
+LOSS_MSD = 0
 
 
 class bd_params(ctypes.Structure):
@@ -77,6 +78,14 @@ SIGNATURES = [
                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
     ("bd_get_tuning", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32)]),
+    ("bd_set_force_params", ctypes.c_int, [_P, _P, ctypes.c_double]),
+    ("bd_set_step", ctypes.c_int, [_P, ctypes.c_int64]),
+    ("bd_rollout", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(bd_step_stats)]),
+    ("bd_rollout_vjp", ctypes.c_int, [_P, _P]),
+    ("bd_rollout_replay", ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    ("bd_rollout_positions", ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    ("bd_rollout_log_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     ("bd_free", None, [_P]),
     ("bd_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -264,6 +273,83 @@ class System:
 
     def last_launch_count(self):
         return int(load().bd_last_launch_count(self.h))
+
+    # ---- differentiated rollout ----
+    def set_force_params(self, alpha=None, v0=None):
+        A = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float64).reshape(4)
+        _check(load().bd_set_force_params(self.h, _ptr(A), float("nan") if v0 is None else float(v0)),
+               "bd_set_force_params")
+
+    def set_step(self, step):
+        _check(load().bd_set_step(self.h, int(step)), "bd_set_step")
+
+    def rollout(self, nsteps, ckpt_every=20, target=0.1, loss_kind=LOSS_MSD):
+        """Advance nsteps recording the frozen choices; returns (loss, stats)."""
+        loss = ctypes.c_double()
+        st = bd_step_stats()
+        _check(load().bd_rollout(self.h, int(nsteps), int(ckpt_every), int(loss_kind), float(target),
+                                 ctypes.byref(loss), ctypes.byref(st)), "bd_rollout")
+        return loss.value, st.as_dict()
+
+    def rollout_vjp(self):
+        """dL/d(A00, A01, A10, A11, v0) of the last recorded rollout."""
+        g = np.zeros(5, dtype=np.float64)
+        _check(load().bd_rollout_vjp(self.h, _ptr(g)), "bd_rollout_vjp")
+        return g
+
+    def rollout_replay(self, alpha=None, v0=None):
+        A = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float64).reshape(4)
+        loss = ctypes.c_double()
+        _check(load().bd_rollout_replay(self.h, _ptr(A), float("nan") if v0 is None else float(v0),
+                                        ctypes.byref(loss)), "bd_rollout_replay")
+        return loss.value
+
+    def rollout_positions(self, which=0):
+        xy = np.zeros((self.n, 2), dtype=np.float64)
+        _check(load().bd_rollout_positions(self.h, int(which), _ptr(xy)), "bd_rollout_positions")
+        return xy
+
+    def rollout_log_size(self):
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().bd_rollout_log_size(self.h, ctypes.byref(a), ctypes.byref(b)), "bd_rollout_log_size")
+        return a.value, b.value
+
+
+def rollout_loss(params, system, xy0, theta0, step0, nsteps, ckpt_every=20, target=0.1):
+    """Differentiable rollout loss: params is a torch tensor (5,) =
+    (A00, A01, A10, A11, v0); the system is reset to (xy0, theta0) at step
+    step0, advanced nsteps with bd_rollout, and the MSD loss returned as a
+    0-d float64 tensor whose backward runs bd_rollout_vjp."""
+    return _rollout_fn().apply(params, system, xy0, theta0, step0, nsteps, ckpt_every, target)
+
+
+_ROLLOUT_FN = None
+
+
+def _rollout_fn():
+    global _ROLLOUT_FN
+    if _ROLLOUT_FN is None:
+        import torch
+
+        class RolloutLoss(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, params, system, xy0, theta0, step0, nsteps, ckpt_every, target):
+                p = params.detach().to("cpu", torch.float64).numpy()
+                system.set_force_params(p[:4], p[4])
+                system.set_state(xy0, theta0)
+                system.set_step(step0)
+                loss, _ = system.rollout(nsteps, ckpt_every, target)
+                ctx.system = system
+                ctx.dev = params.device
+                return torch.tensor(loss, dtype=torch.float64, device=params.device)
+
+            @staticmethod
+            def backward(ctx, g):
+                grad = torch.from_numpy(ctx.system.rollout_vjp()).to(ctx.dev)
+                return g * grad, None, None, None, None, None, None, None
+
+        _ROLLOUT_FN = RolloutLoss
+    return _ROLLOUT_FN
 
 
 def ghost_points(L, a=1.0):

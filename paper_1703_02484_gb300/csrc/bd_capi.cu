@@ -19,6 +19,7 @@
 #include <numeric>
 #include <vector>
 
+#include "bd_handle.h"
 #include "bd_internal.h"
 #include "predicates.cuh"
 
@@ -33,50 +34,15 @@ int any_overlap(int n, const double *xy, double lo, double hi, double dmin);
 uint64_t hilbert_index(uint32_t x, uint32_t y);
 }  // namespace bdhost
 
-namespace {
-
-struct RepHost {
-  bd_params p;
-  double L = 0, wall_lo = 0, wall_hi = 0;
-  int n = 0;                   // disks
-  int ext_base = 0;            // first index in the concatenated external arrays
-  int slot_begin = 0, slot_end = 0;
-  int ghost_base = 0, ng = 0;  // ghost vertex ids ghost_base .. ghost_base + ng - 1
-  int tri_base = 0, nt = 0;
-  int iblock_base = 0, n_iblocks = 0;
-  int tile_begin = 0, tile_end = 0;
-};
-
-}  // namespace
-
-struct bd_handle {
-  cudaStream_t stream = nullptr;
-  BdDev d;
-  BdConst c;
-  std::vector<RepHost> reps;
-  std::vector<BdRep> h_rep;
-  int n = 0, np = 0, np_i = 0, nt = 0, ng = 0;
-  std::vector<int> ext_of_int;    // internal slot -> concatenated external index (-1 = empty)
-  std::vector<int> int_of_ext;    // concatenated external index -> internal slot
-  std::vector<double> host_pos;   // (np + ng) * 2 mirror used for uploads
-  int dt_grid = 0, dt_block = 0;
-  int64_t step = 0;
-  double2 *d_fsum = nullptr;
-  BdCtl *h_ctl = nullptr;          // pinned
-  std::vector<void *> dev_allocs;
-  bool timing = false;
-  std::vector<cudaEvent_t> ev_pool;   // pairs (start, end) per timed launch
-  double force_ms = 0.0;
-  int64_t force_launches = 0;
-  int64_t last_launches = 0;
-  int tune_tiles = 0;              // j tiles per work item chosen for the sweep
-  int fpart_slots = 0;             // partial-force slots allocated
-  std::vector<int> fpart_cap;      // per replica: chunks that fit
-};
-
-namespace {
+namespace bdcapi {
 
 int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? BD_ERR_NOMEM : BD_ERR_CUDA; }
+
+}  // namespace bdcapi
+
+using namespace bdcapi;
+
+namespace {
 
 template <class T>
 cudaError_t dalloc(bd_handle *h, T **ptr, size_t count) {
@@ -689,6 +655,10 @@ cuda_error:
   return cuda_fail(e);
 }
 
+}  // namespace
+
+namespace bdcapi {
+
 int read_ctl(bd_handle *h) {
   cudaError_t e = cudaMemcpyAsync(h->h_ctl, h->d.ctl, sizeof(BdCtl), cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -701,7 +671,7 @@ cudaError_t reset_stats(bd_handle *h) {
   // zero everything after the barrier words, the status and the epoch
   char *base = (char *)h->d.ctl;
   size_t off = offsetof(BdCtl, cnt);
-  cudaError_t e = cudaMemsetAsync(base + off, 0, sizeof(BdCtl) - off, h->stream);
+  cudaError_t e = cudaMemsetAsync(base + off, 0, offsetof(BdCtl, log_npass) - off, h->stream);
   if (e != cudaSuccess) return e;
   return cudaMemsetAsync(&h->d.ctl->status, 0, sizeof(int), h->stream);
 }
@@ -716,6 +686,10 @@ int finish_status(bd_handle *h, int status) {
   cudaStreamSynchronize(st);
   return status;
 }
+
+}  // namespace bdcapi
+
+namespace {
 
 // copy the disks' positions / directions / species (internal order)
 int fetch_disks(bd_handle *h, std::vector<double2> *pos, std::vector<float> *th,
@@ -783,6 +757,7 @@ void bd_free(bd_handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  bdcapi::rollout_release(h);
   for (void *p : h->dev_allocs) cudaFree(p);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
   for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
@@ -843,7 +818,7 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
       if (e != cudaSuccess) return cuda_fail(e);
       launches += bd_short_launches();
     }
-    e = bd_launch_integrate(h->d, h->c, h->step + s, st);
+    e = bd_launch_integrate(h->d, h->c, h->step + s, -1, st);
     if (e != cudaSuccess) return cuda_fail(e);
     e = bd_launch_dt(h->d, h->c, 0, st, h->dt_grid, h->dt_block);
     if (e != cudaSuccess) return cuda_fail(e);

@@ -15,6 +15,9 @@
 // neighbours within 5.6a even at close packing)
 #define BD_VL_MAX 64
 
+// threads (and i disks) per block of the all-pairs force adjoint
+#define BD_ADJ_T 128
+
 // triangle flag bits stored in tv[t].w
 #define BD_TRI_INVERTED 1
 #define BD_TRI_DIRTY 2
@@ -44,6 +47,11 @@ struct BdCtl {
   long long st_barriers;           // grid barriers passed by the triangulation kernel
   int st_fail_item;                // an offending triangle (repair) or edge corner (reversal)
   int st_fail_count;               // inverted triangles / reversed edges at the failure
+  // rollout log cursors (not reset per call)
+  int log_npass;                   // committed correction passes
+  int log_npairs;                  // logged pairs
+  int log_overflow;
+  int log_step;                    // rollout step being recorded (-1 = none)
 };
 
 // counter slots within BdCtl::cnt[phase % 4]
@@ -90,6 +98,12 @@ struct BdDev {
   int *vl_idx, *vl_cnt;
   double2 *vl_ref;
   int *cell_count, *cell_start, *cell_cursor, *cell_idx, *cell_of, *scan_sums;
+  // rollout log for the adjoint (null when not recording)
+  uint8_t *log_refl;       // [step][np] wall-reflection flags of the Euler-Maruyama move
+  uint8_t *log_pflags;     // [pass][np] bit 16: capped; bits 1,2,4,8: reflections of the pass
+  int2 *log_pairs;         // overlapping pairs of every committed correction pass
+  int *log_pass_begin;     // [pass + 1] first pair of each pass
+  int *log_step_pass;      // [step + 1] first pass of each step
   BdCtl *ctl;
 };
 
@@ -107,13 +121,16 @@ struct BdConst {
   unsigned long long sig2q_hi, sig2q_lo;  // ceil((sigma/q)^2 (1 + 1e-9)) as 128-bit
   int max_corr_iters, max_flip_rounds;
   int force_variant;       // 0: scalar FP32 sweep, 1: packed f32x2 sweep
+  int log_pairs_cap, log_pass_cap;   // rollout log capacities
 };
 
 // launchers (kernels_*.cu)
 cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t s);
 cudaError_t bd_launch_force_long_variant(const BdDev &d, const BdConst &c, int variant, cudaStream_t s);
-cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, cudaStream_t s);
-cudaError_t bd_launch_dt(const BdDev &d, const BdConst &c, int mode, cudaStream_t s, int grid, int block);
+cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, int log_step,
+                                cudaStream_t s);
+cudaError_t bd_launch_dt(const BdDev &d, const BdConst &c, int mode, cudaStream_t s, int grid, int block,
+                         int log_step = -1);
 int bd_dt_grid(int *grid, int *block);
 int bd_dt_grid_for(int work_items, int *grid, int *block);
 int bd_force_blocks_per_sm(int variant);

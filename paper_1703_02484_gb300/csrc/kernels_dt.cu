@@ -34,6 +34,7 @@
 #include <stdint.h>
 
 #include "bd_internal.h"
+#include "em.cuh"
 #include "predicates.cuh"
 
 #ifndef BD_BARRIER_TIMEOUT_NS
@@ -260,7 +261,8 @@ __device__ __forceinline__ int key_corner(unsigned long long key) {
 //      inverted triangle; then P again.
 //   F  owned Lawson flips of the marked edges; then P again.
 //   A  apply the capped displacements (Algorithm 2) and reflect; then P again.
-__global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdConst c, int mode) {
+__global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdConst c, int mode,
+                                                                 int log_step) {
   Ctx x;
   x.d = d;
   x.c = c;
@@ -288,6 +290,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
   bool first = true;       // take the rollback snapshot in the first pass
   bool fresh = true;       // the moved flags describe the latest move
   int lawson_rounds = 0;
+  // rollout log (adjoint): committed passes and their overlapping pairs
+  const bool logging = log_step >= 0 && d.log_pairs != nullptr;
+  int log_head = logging ? ctl->log_npairs : 0;
+  int log_npass = logging ? ctl->log_npass : 0;
+  int log_pidx = -1;
 
   for (;;) {
     ++epoch;
@@ -358,7 +365,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
                 atomicAdd(&d.disp[u].y, -del * ny);
                 atomicAdd(&d.disp[w].x, del * nx);
                 atomicAdd(&d.disp[w].y, del * ny);
-                ++nov;
+                const int k_ov = atomicAdd(cnt(ctl, b.ph, C_OVERLAP), 1);
+                if (logging) {
+                  if (log_head + k_ov < c.log_pairs_cap) d.log_pairs[log_head + k_ov] = make_int2(u, w);
+                  else atomicExch(&ctl->log_overflow, 1);
+                }
                 mx = fmax(mx, del);
               }
             }
@@ -368,7 +379,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
       block_add(cnt(ctl, b.ph, C_INV), inv);
       block_add(cnt(ctl, b.ph, C_REJECT), rej);
       block_add(cnt(ctl, b.ph, C_CAND), cand);
-      block_add(cnt(ctl, b.ph, C_OVERLAP), nov);
+      (void)nov;
       if (mx > 0.0) atomicMax(&ctl->st_max_overlap_bits, (unsigned long long)__double_as_longlong(mx));
     }
     if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
@@ -508,6 +519,20 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
     ++corr_iter;
     st_overlap += n_ov;
     lawson_rounds = 0;
+    if (logging) {
+      // commit this pass to the rollout log
+      log_pidx = log_npass < c.log_pass_cap ? log_npass : -1;
+      if (lead) {
+        if (log_pidx >= 0) {
+          d.log_pass_begin[log_pidx] = log_head;
+          d.log_pass_begin[log_pidx + 1] = log_head + n_ov;
+        } else {
+          atomicExch(&ctl->log_overflow, 1);
+        }
+      }
+      log_head += n_ov;
+      ++log_npass;
+    }
     // ---------------- A: apply (capped at sigma/4) ----------------
     phase_begin(ctl, b);
     {
@@ -519,17 +544,17 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
         const double2 dd = d.disp[i];
         if (dd.x == 0.0 && dd.y == 0.0) {
           d.moved[i] = 0;
+          if (log_pidx >= 0) d.log_pflags[(size_t)log_pidx * x.np + i] = 0;
           continue;
         }
         const double mag = sqrt(__dadd_rn(__dmul_rn(dd.x, dd.x), __dmul_rn(dd.y, dd.y)));
-        const double sc = mag > cap ? cap / mag : 1.0;
-        double nxp = snap(p.x + dd.x * sc, x.g), nyp = snap(p.y + dd.y * sc, x.g);
-        const BdRep &R = d.rep[d.rep_of[i]];
-        if (nxp < R.wall_lo) nxp = 2.0 * R.wall_lo - nxp;
-        if (nxp > R.wall_hi) nxp = 2.0 * R.wall_hi - nxp;
-        if (nyp < R.wall_lo) nyp = 2.0 * R.wall_lo - nyp;
-        if (nyp > R.wall_hi) nyp = 2.0 * R.wall_hi - nyp;
-        const double2 np2 = make_double2(nxp, nyp);
+        const bool capped = mag > cap;
+        const double sc = capped ? cap / mag : 1.0;
+        const double2 y = make_double2(snap(__dadd_rn(p.x, __dmul_rn(dd.x, sc)), x.g),
+                                       snap(__dadd_rn(p.y, __dmul_rn(dd.y, sc)), x.g));
+        int rfl = 0;
+        const double2 np2 = bdem::reflect(d.rep[d.rep_of[i]], y, &rfl);
+        if (log_pidx >= 0) d.log_pflags[(size_t)log_pidx * x.np + i] = (uint8_t)(rfl | (capped ? 16 : 0));
         d.pos[i] = np2;
         d.work[i] = split_pos(np2);
         d.disp[i] = make_double2(0.0, 0.0);
@@ -564,6 +589,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
     for (int i = tid; i < x.np; i += nth) d.moved[i] = 0;
   }
   if (lead) {
+    if (logging && !status) {
+      ctl->log_npairs = log_head;
+      ctl->log_npass = log_npass;
+      d.log_step_pass[log_step + 1] = log_npass;
+    }
     ctl->epoch = epoch + 1;
     ctl->st_corr_iters += corr_iter;
     ctl->st_overlap_pairs += st_overlap;
@@ -605,13 +635,13 @@ int bd_dt_grid(int *grid, int *block) {
 }
 
 cudaError_t bd_launch_dt(const BdDev &d, const BdConst &c, int mode, cudaStream_t s, int grid,
-                         int block) {
+                         int block, int log_step) {
   // the barrier words and phase counters were reset by the previous
   // launch's last block (and zeroed at allocation)
   BdDev dd = d;
   BdConst cc = c;
-  int m = mode;
-  void *args[] = {&dd, &cc, &m};
+  int m = mode, ls = log_step;
+  void *args[] = {&dd, &cc, &m, &ls};
   return cudaLaunchCooperativeKernel((const void *)k_triangulation, dim3(grid), dim3(block), args,
                                      0, s);
 }

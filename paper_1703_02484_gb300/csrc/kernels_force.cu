@@ -30,6 +30,7 @@
 #include <stdint.h>
 
 #include "bd_internal.h"
+#include "em.cuh"
 #include "philox.cuh"
 
 namespace {
@@ -359,85 +360,28 @@ __global__ void k_force_sum(BdDev d, BdConst c, double2 *out) {
   out[i] = make_double2(fx, fy);
 }
 
-namespace {
-__device__ __forceinline__ double snapd(double v, double q, double inv_q) {
-  return __dmul_rn(rint(__dmul_rn(v, inv_q)), q);
-}
-__device__ __forceinline__ float4 split(double2 p) {
-  float xh = __double2float_rn(p.x), yh = __double2float_rn(p.y);
-  return make_float4(xh, yh, __double2float_rn(p.x - (double)xh), __double2float_rn(p.y - (double)yh));
-}
-}  // namespace
-
-__global__ void k_integrate(BdDev d, BdConst c, long long step) {
+__global__ void k_integrate(BdDev d, BdConst c, long long step, int log_step) {
   if (ctl_failed(d.ctl)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= c.np) return;
   const int e = d.ext_id[i];
   if (e < 0) return;
   const BdRep &R = d.rep[d.rep_of[i]];
-  double fx = 0.0, fy = 0.0;
-  const int ns = R.law == BD_LAW_LONG ? R.nchunk : (R.law == BD_LAW_SHORT ? 1 : 0);
-  for (int k = 0; k < ns; ++k) {
-    double2 f = d.fpart[(size_t)k * c.np + i];
-    fx += f.x;
-    fy += f.y;
-  }
+  const double2 F = bdem::force_sum(d, c, R, i);
   const double2 p = d.pos[i];
   d.pos0[i] = p;
   d.prev[i] = p;
   const float th = d.theta[i];
   d.theta0[i] = th;
-  bdrng::U4 r = bdrng::draw((uint32_t)e, (int64_t)step, R.seed, R.replica, bdrng::TAG_NOISE);
-  double nx, ny;
   float thn;
-  if (c.precision == 0) {
-    const float sc = 2.3283064365386963e-10f;  // 2^-32
-    float u0 = __fmaf_rn((float)r.x, sc, 0.5f * sc), u1 = __fmaf_rn((float)r.y, sc, 0.5f * sc);
-    float u2 = __fmaf_rn((float)r.z, sc, 0.5f * sc), u3 = __fmaf_rn((float)r.w, sc, 0.5f * sc);
-    float ra = sqrtf(-2.0f * logf(u0)), rb = sqrtf(-2.0f * logf(u2));
-    float s1, c1, s2, c2;
-    sincospif(2.0f * u1, &s1, &c1);
-    sincospif(2.0f * u3, &s2, &c2);
-    float z0 = fminf(3.0f, fmaxf(-3.0f, ra * c1));
-    float z1 = fminf(3.0f, fmaxf(-3.0f, ra * s1));
-    float z2 = fminf(3.0f, fmaxf(-3.0f, rb * c2));
-    float st, ct;
-    sincosf(th, &st, &ct);
-    const float dt = (float)R.dt, v0 = (float)R.v0, amp = (float)R.amp;
-    float dxf = dt * ((float)fx + v0 * ct) + amp * z0;
-    float dyf = dt * ((float)fy + v0 * st) + amp * z1;
-    nx = p.x + (double)dxf;
-    ny = p.y + (double)dyf;
-    thn = th + (float)R.amp_r * z2;
-  } else {
-    const double sc = 2.3283064365386962890625e-10;
-    double u0 = ((double)r.x + 0.5) * sc, u1 = ((double)r.y + 0.5) * sc;
-    double u2 = ((double)r.z + 0.5) * sc, u3 = ((double)r.w + 0.5) * sc;
-    double ra = sqrt(-2.0 * log(u0)), rb = sqrt(-2.0 * log(u2));
-    double s1, c1, s2, c2;
-    sincospi(2.0 * u1, &s1, &c1);
-    sincospi(2.0 * u3, &s2, &c2);
-    double z0 = fmin(3.0, fmax(-3.0, ra * c1));
-    double z1 = fmin(3.0, fmax(-3.0, ra * s1));
-    double z2 = fmin(3.0, fmax(-3.0, rb * c2));
-    double st, ct;
-    sincos((double)th, &st, &ct);
-    nx = p.x + R.dt * (fx + R.v0 * ct) + R.amp * z0;
-    ny = p.y + R.dt * (fy + R.v0 * st) + R.amp * z1;
-    thn = (float)((double)th + R.amp_r * z2);
-  }
-  nx = snapd(nx, c.q, c.inv_q);
-  ny = snapd(ny, c.q, c.inv_q);
-  if (nx < R.wall_lo) nx = 2.0 * R.wall_lo - nx;
-  if (nx > R.wall_hi) nx = 2.0 * R.wall_hi - nx;
-  if (ny < R.wall_lo) ny = 2.0 * R.wall_lo - ny;
-  if (ny > R.wall_hi) ny = 2.0 * R.wall_hi - ny;
-  const double2 pn = make_double2(nx, ny);
+  const double2 y = bdem::em_move(c, R, (uint32_t)e, step, p, th, F, R.v0, &thn);
+  int flags = 0;
+  const double2 pn = bdem::reflect(R, y, &flags);
   d.pos[i] = pn;
-  d.work[i] = split(pn);
+  d.work[i] = bdem::split(pn);
   d.theta[i] = thn;
   d.moved[i] = 1;
+  if (log_step >= 0 && d.log_refl) d.log_refl[(size_t)log_step * c.np + i] = (uint8_t)flags;
 }
 
 __global__ void k_work_copy(BdDev d, BdConst c) {
@@ -447,7 +391,7 @@ __global__ void k_work_copy(BdDev d, BdConst c) {
     d.work[i] = make_float4(1.0e18f, 1.0e18f, 0.f, 0.f);
     return;
   }
-  d.work[i] = split(d.pos[i]);
+  d.work[i] = bdem::split(d.pos[i]);
 }
 
 int bd_force_blocks_per_sm(int variant) {
@@ -475,8 +419,9 @@ cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t 
   return bd_launch_force_long_variant(d, c, c.force_variant, s);
 }
 
-cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, cudaStream_t s) {
-  k_integrate<<<(c.np + 255) / 256, 256, 0, s>>>(d, c, (long long)step);
+cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, int log_step,
+                                cudaStream_t s) {
+  k_integrate<<<(c.np + 255) / 256, 256, 0, s>>>(d, c, (long long)step, log_step);
   return cudaGetLastError();
 }
 
