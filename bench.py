@@ -239,6 +239,61 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """Differentiated rollout (4096 disks, rho 0.35, two species, v0 = 1, 200
+    steps, checkpoints every 20): each timed unit is one recorded rollout
+    (bd_rollout) plus its reverse pass (bd_rollout_vjp), against the plain
+    steps (bd_step) over the same number of steps."""
+    import torch
+    import paper_1703_02484_gb300 as bd
+    from paper_1703_02484_gb300 import workloads
+    torch.cuda.set_device(0)
+    cfg = workloads.CONFIGS["c5"]
+    xy, sp, th = workloads.initial_state(cfg)
+    stream = torch.cuda.current_stream()
+    s = bd.System(bd.params_from_config(cfg), xy, sp, th, stream=stream.cuda_stream)
+    T = cfg.steps
+    for _ in range(args.warmup):
+        s.rollout(T, 20, 0.1)
+        s.rollout_vjp()
+        s.step(T)
+    K = max(1, min(args.steps, 20))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    launches = 0
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        for k in range(K):
+            ev[k][0].record(stream)
+            s.rollout(T, 20, 0.1)
+            launches += s.last_launch_count()
+            ev[k][1].record(stream)
+            g = s.rollout_vjp()
+            launches += s.last_launch_count()
+            ev[k][2].record(stream)
+            s.step(T)
+            ev[k][3].record(stream)
+        torch.cuda.synchronize()
+    fwd = sum(e[0].elapsed_time(e[1]) for e in ev) / K
+    bwd = sum(e[1].elapsed_time(e[2]) for e in ev) / K
+    plain = sum(e[2].elapsed_time(e[3]) for e in ev) / K
+    npass, npairs = s.rollout_log_size()
+    s.close()
+    line = {"metric": "particle-steps/s (c5: recorded rollout + reverse pass)",
+            "value": cfg.n * T / ((fwd + bwd) / 1e3), "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": (fwd + bwd) / T, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (adjoint sums f64)", "data": "synthetic",
+            "config": {"workload": "c5: N=4096, rho=0.35, two species, v0=1, 200 steps, checkpoints every 20, "
+                                   "MSD loss; gradient w.r.t. (A00, A01, A10, A11, v0)",
+                       "N": cfg.n, "rollout_steps": T,
+                       "forward_ms": fwd, "reverse_ms": bwd, "plain_steps_ms": plain,
+                       "gradient_evals_per_s": 1e3 / (fwd + bwd),
+                       "overhead_vs_plain": (fwd + bwd) / plain,
+                       "log_passes": npass, "log_pairs": npairs, "last_grad": list(map(float, g)),
+                       "l2": "working set (< 2 MB) stays in L2; not flushed"},
+            "gpu_launches": launches, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -248,7 +303,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--workload", default="n1e5",
-                    help="configuration name (n1e5 is the headline; c1, c2, c3, c5 for tables)")
+                    help="configuration name (n1e5 is the headline; c1, c2, c3, c5, c4 (batched), "
+                         "c5-grad (differentiated rollout) for tables)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -256,6 +312,9 @@ def main():
     args.warmup = max(3, args.warmup)
     if args.workload == "c4":
         run_batched(args)
+        return
+    if args.workload == "c5-grad":
+        run_adjoint(args)
         return
 
     import torch
@@ -321,12 +380,21 @@ def main():
         avg_force_s = float("nan")
     achieved = FLOPS_PER_PAIR * pairs / avg_force_s / 1e12
     pipe_frac = FP32_INST_PER_PAIR * pairs / avg_force_s / (sms * 128 * f_hz)
+    variant = system.tuning()["variant"]
+    kernel = "k_force_long_f32x2<4>" if variant == 1 else "k_force_long_f32"
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "force_long_f32_traffic.json")
-    if os.path.exists(prof):
+    # ncu DRAM bytes of one launch, used only while the kernel source is the
+    # one the counters were taken on
+    prof = os.path.join(ROOT, "profiles", "force_long_traffic_n1e5.json")
+    if os.path.exists(prof) and args.workload == "n1e5":
         try:
+            import hashlib
             with open(prof) as f:
-                traffic = json.load(f).get("traffic_bytes_per_launch")
+                rec = json.load(f)
+            with open(os.path.join(ROOT, "paper_1703_02484_gb300", "csrc", "kernels_force.cu"), "rb") as f:
+                h = hashlib.sha256(f.read()).hexdigest()[:16]
+            if rec.get("kernel") == kernel and rec.get("kernel_source_sha256_16") == h:
+                traffic = rec.get("traffic_bytes_per_launch")
         except Exception:
             traffic = None
 
@@ -366,7 +434,7 @@ def main():
                        "parallelism": "replicas%d" % ws,
                        "l2": "flushed between timed steps (256 MB write)",
                        "per_step_stats": {k: v / args.steps for k, v in stats_tot.items()}},
-            "roofline": {"bound": "alu", "kernel": "k_force_long_f32", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
                          "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                          "traffic": traffic, "fp32_pipe_frac": pipe_frac,
                          "pair_interactions_per_s": pairs / avg_force_s,
