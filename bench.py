@@ -31,6 +31,10 @@ UNIT = "particle-steps/s"
 WORKLOAD = "n1e5: N=100000 two-species ABP disks, rho=0.30, all-pairs 1/r^2 non-reciprocal, Delaunay overlap correction"
 FLOPS_PER_PAIR = 12      # 2 FADD + 2 FFMA(r^2) + 2 FMUL(s^3) + 2 FFMA(accumulate), FMA = 2 flops
 FP32_INST_PER_PAIR = 8   # the same work counted as FP32-pipe instructions (plus 1 MUFU rsqrt)
+# symmetric sweep: per unordered pair 2 FADD + 2 FFMA + 2 FMUL + 4 FFMA (both
+# sides) = 16 flops in 10 FP32 lane operations (+1 MUFU), i.e. per ordered pair:
+FLOPS_PER_PAIR_SYM = 8
+LANES_PER_PAIR_SYM = 5
 
 
 def peaks():
@@ -378,10 +382,16 @@ def main():
     pairs = N * (N - 1)
     if force_n == 0:
         avg_force_s = float("nan")
-    achieved = FLOPS_PER_PAIR * pairs / avg_force_s / 1e12
-    pipe_frac = FP32_INST_PER_PAIR * pairs / avg_force_s / (sms * 128 * f_hz)
-    variant = system.tuning()["variant"]
-    kernel = "k_force_long_f32x2<4>" if variant == 1 else "k_force_long_f32"
+    tune = system.tuning()
+    variant = tune["variant"]
+    # algorithmic FP32 work of the chosen sweep, per ordered pair interaction
+    flops_pp, lanes_pp = (FLOPS_PER_PAIR_SYM, LANES_PER_PAIR_SYM) if variant >= 2 else \
+        (FLOPS_PER_PAIR, FP32_INST_PER_PAIR)
+    achieved = flops_pp * pairs / avg_force_s / 1e12
+    pipe_frac = lanes_pp * pairs / avg_force_s / (sms * 128 * f_hz)
+    kernel = {0: "k_force_long_f32", 1: "k_force_long_f32x2<4>",
+              2: "k_force_long_sym<4,2> + k_force_sym_reduce",
+              3: "k_force_long_sym<2,4> + k_force_sym_reduce"}[variant]
     traffic = None
     # ncu DRAM bytes of one launch, used only while the kernel source is the
     # one the counters were taken on
@@ -433,6 +443,7 @@ def main():
             "config": {"workload": WORKLOAD, "N": N, "seed": cfg.seed,
                        "parallelism": "replicas%d" % ws,
                        "l2": "flushed between timed steps (256 MB write)",
+                       "force_tuning": tune,
                        "per_step_stats": {k: v / args.steps for k, v in stats_tot.items()}},
             "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
                          "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
@@ -440,7 +451,9 @@ def main():
                          "pair_interactions_per_s": pairs / avg_force_s,
                          "avg_launch_ms": avg_force_s * 1e3,
                          "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s max clock); "
-                                      "12 flops/pair caps frac at 0.75" % (sms, f_hz / 1e6, pk_kind)},
+                                      "flops counted per ordered pair: %d (%d FP32 lane ops), so frac "
+                                      "is capped at %.2f" % (sms, f_hz / 1e6, pk_kind, flops_pp, lanes_pp,
+                                                              flops_pp / (2.0 * lanes_pp))},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
         }
         if args.workload != "n1e5":

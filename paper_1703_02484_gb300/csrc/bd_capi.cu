@@ -116,6 +116,81 @@ void make_items(bd_handle *h, int tiles, std::vector<int4> &items, int &max_chun
   }
 }
 
+// Work items of the symmetric sweep: block P of a long-range replica against
+// its own two tiles (i side only) and every later tile of the replica, in
+// chunks of at most `tiles` tiles, plus the reduction lists (per block its
+// items, per tile its j-partial tiles, both in item order).
+struct SymPlan {
+  std::vector<int4> items;
+  std::vector<int> iptr, iidx, jptr, jidx;
+  int n_jtiles = 0;
+};
+
+void make_sym(const bd_handle *h, int tiles, SymPlan &S) {
+  const int nblocks = h->np / BD_SB, ntiles = h->np / BD_TJ;
+  std::vector<std::vector<int>> bl(nblocks), tl(ntiles);
+  S.items.clear();
+  S.n_jtiles = 0;
+  for (const RepHost &R : h->reps) {
+    if (R.p.law != BD_LAW_LONG) continue;
+    const int tb = R.tile_begin, te = R.tile_end;
+    for (int P = tb / 2; P < te / 2; ++P)
+      for (int c0 = 2 * P; c0 < te; c0 += tiles) {
+        const int c1 = std::min(te, c0 + tiles), jt0 = std::max(c0, 2 * P + 2);
+        const int it = (int)S.items.size();
+        S.items.push_back(make_int4(P, c0, c1, S.n_jtiles));
+        bl[P].push_back(it);
+        for (int t = jt0; t < c1; ++t) tl[t].push_back(S.n_jtiles + (t - jt0));
+        S.n_jtiles += std::max(0, c1 - jt0);
+      }
+  }
+  auto flatten = [](const std::vector<std::vector<int>> &v, std::vector<int> &ptr, std::vector<int> &idx) {
+    ptr.assign(v.size() + 1, 0);
+    idx.clear();
+    for (size_t k = 0; k < v.size(); ++k) {
+      idx.insert(idx.end(), v[k].begin(), v[k].end());
+      ptr[k + 1] = (int)idx.size();
+    }
+  };
+  flatten(bl, S.iptr, S.iidx);
+  flatten(tl, S.jptr, S.jidx);
+}
+
+// replace a device array owned by the handle
+template <class T>
+cudaError_t realloc_dev(bd_handle *h, T **ptr, size_t count) {
+  if (*ptr) {
+    void *old = (void *)*ptr;
+    cudaFree(old);
+    h->dev_allocs.erase(std::find(h->dev_allocs.begin(), h->dev_allocs.end(), old));
+    *ptr = nullptr;
+  }
+  return dalloc(h, ptr, std::max<size_t>(1, count));
+}
+
+template <class T>
+cudaError_t upload_vec(bd_handle *h, T **ptr, const std::vector<T> &v) {
+  cudaError_t e = realloc_dev(h, ptr, v.size());
+  if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+cudaError_t upload_sym(bd_handle *h, const SymPlan &S) {
+  BdDev &d = h->d;
+  cudaError_t e = upload_vec(h, &d.sitems, S.items);
+  if (e == cudaSuccess) e = upload_vec(h, &d.red_iptr, S.iptr);
+  if (e == cudaSuccess) e = upload_vec(h, &d.red_iidx, S.iidx);
+  if (e == cudaSuccess) e = upload_vec(h, &d.red_jptr, S.jptr);
+  if (e == cudaSuccess) e = upload_vec(h, &d.red_jidx, S.jidx);
+  if (e == cudaSuccess) e = realloc_dev(h, &d.ipart, S.items.size() * BD_SB);
+  if (e == cudaSuccess) e = realloc_dev(h, &d.jpart, (size_t)S.n_jtiles * BD_TJ);
+  if (e != cudaSuccess) return e;
+  h->c.n_sitems = (int)S.items.size();
+  h->c.max_nchunk = 1;
+  for (size_t r = 0; r < h->reps.size(); ++r) h->h_rep[r].nchunk = 1;
+  return cudaMemcpy((void *)h->d.rep, h->h_rep.data(), h->h_rep.size() * sizeof(BdRep), cudaMemcpyHostToDevice);
+}
+
 // j tiles per work item for a single system: fill whole waves of resident
 // force blocks (the occupancy calculator gives blocks per SM)
 int single_system_tiles(const bd_handle *h) {
@@ -173,48 +248,60 @@ cudaError_t upload_items(bd_handle *h, const std::vector<int4> &items, int max_c
                     cudaMemcpyHostToDevice);
 }
 
-// Autotuner of the batched sweep: time the force kernel for several chunk
-// sizes (j tiles per work item) and both kernel variants, keep the fastest.
+// set up the work list of a sweep variant with `tiles` j tiles per item
+cudaError_t use_variant(bd_handle *h, int variant, int tiles) {
+  h->c.force_variant = variant;
+  h->tune_tiles = tiles;
+  if (variant >= 2) {
+    SymPlan S;
+    make_sym(h, tiles, S);
+    return upload_sym(h, S);
+  }
+  std::vector<int4> items;
+  int mc = 1;
+  make_items(h, tiles, items, mc);
+  return upload_items(h, items, mc);
+}
+
+// Autotuner of the all-pairs sweep: time the force launch for each candidate
+// (kernel variant, j tiles per work item) and keep the fastest.  Candidates:
+// the one-sided sweeps (scalar, packed) and the symmetric sweep over several
+// chunk sizes; a single system also tries the wave-filling chunk size.
 cudaError_t autotune(bd_handle *h) {
-  const int cand_tiles[] = {2, 4, 8, 16, 32, 64};
+  std::vector<int2> cand;
+  if (h->reps.size() == 1) {
+    cand.push_back(make_int2(1, single_system_tiles(h)));
+  } else {
+    for (int t : {2, 4, 8, 16, 32, 64}) cand.push_back(make_int2(0, t));
+    for (int t : {2, 4, 8, 16, 32, 64}) cand.push_back(make_int2(1, t));
+  }
+  for (int v : {2, 3})
+    for (int t : {2, 4, 8, 16, 32}) cand.push_back(make_int2(v, t));
   float best_ms = 1e30f;
-  int best_tiles = 16, best_var = h->c.force_variant;
+  int2 best = cand[0];
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   cudaError_t e = cudaSuccess;
-  for (int var = 0; var < 2 && e == cudaSuccess; ++var) {
-    for (int tiles : cand_tiles) {
-      std::vector<int4> items;
-      int mc = 1;
-      make_items(h, tiles, items, mc);
-      e = upload_items(h, items, mc);
-      if (e != cudaSuccess) break;
-      float tot = 0.f;
-      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-        cudaEventRecord(a, h->stream);
-        e = bd_launch_force_long_variant(h->d, h->c, var, h->stream);
-        cudaEventRecord(b, h->stream);
-        cudaEventSynchronize(b);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        if (rep > 0) tot += ms;
-      }
-      if (e == cudaSuccess && tot < best_ms) {
-        best_ms = tot;
-        best_tiles = tiles;
-        best_var = var;
-      }
+  for (const int2 &cv : cand) {
+    e = use_variant(h, cv.x, cv.y);
+    if (e != cudaSuccess) break;
+    float tot = 0.f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+      cudaEventRecord(a, h->stream);
+      e = bd_launch_force_long_variant(h->d, h->c, cv.x, h->stream);
+      cudaEventRecord(b, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep > 0) tot += ms;
+    }
+    if (e == cudaSuccess && tot < best_ms) {
+      best_ms = tot;
+      best = cv;
     }
   }
-  if (e == cudaSuccess) {
-    h->c.force_variant = best_var;
-    h->tune_tiles = best_tiles;
-    std::vector<int4> items;
-    int mc = 1;
-    make_items(h, best_tiles, items, mc);
-    e = upload_items(h, items, mc);
-  }
+  if (e == cudaSuccess) e = use_variant(h, best.x, best.y);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   return e;
@@ -333,7 +420,7 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     });
     int cnt_sp[2] = {0, 0};
     for (int i = 0; i < n; ++i) cnt_sp[sp[i]]++;
-    const int seg0 = (int)pad_to(cnt_sp[0], BD_TJ), seg1 = (int)pad_to(cnt_sp[1], BD_TJ);
+    const int seg0 = (int)pad_to(cnt_sp[0], BD_SB), seg1 = (int)pad_to(cnt_sp[1], BD_SB);
     RH.slot_begin = slot;
     RH.slot_end = slot + seg0 + seg1;
     RH.tile_begin = slot / BD_TJ;
@@ -482,10 +569,7 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
   }
   c.max_corr_iters = p0.max_corr_iters;
   c.max_flip_rounds = p0.max_flip_rounds;
-  {
-    const char *fv = getenv("BD_FORCE_VARIANT");
-    c.force_variant = fv ? atoi(fv) : 1;
-  }
+  c.force_variant = 1;
   h->h_rep.resize(R);
   int cell_base = 0;
   for (int r = 0; r < R; ++r) {
@@ -602,6 +686,28 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
         sp_i[i] = spr[r][slot_local[i]];
       }
     }
+    {
+      // symmetric-sweep blocks: (replica, species) and an integer origin
+      const int nb = np / BD_SB;
+      std::vector<int2> sb(std::max(1, nb), make_int2(0, 0));
+      std::vector<float2> so(std::max(1, nb), make_float2(0.f, 0.f));
+      for (int P = 0; P < nb; ++P) {
+        double sx = 0.0, sy = 0.0;
+        int m = 0;
+        for (int i = P * BD_SB; i < (P + 1) * BD_SB; ++i) {
+          if (slot_rep[i] < 0) continue;
+          if (m == 0) sb[P] = make_int2(slot_rep[i], sp_i[i]);
+          sx += h->host_pos[2 * (size_t)i];
+          sy += h->host_pos[2 * (size_t)i + 1];
+          ++m;
+        }
+        if (m) so[P] = make_float2((float)nearbyint(sx / m), (float)nearbyint(sy / m));
+      }
+      BD_TRY(dalloc(h, &d.sblock, sb.size()));
+      BD_TRY(dalloc(h, &d.sorigin, so.size()));
+      BD_TRY(cudaMemcpy(d.sblock, sb.data(), sb.size() * sizeof(int2), cudaMemcpyHostToDevice));
+      BD_TRY(cudaMemcpy(d.sorigin, so.data(), so.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    }
     BD_TRY(cudaMemcpyAsync(d.pos, h->host_pos.data(), nv * sizeof(double2), cudaMemcpyHostToDevice, st));
     BD_TRY(cudaMemcpyAsync(d.prev, d.pos, nv * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     BD_TRY(cudaMemcpyAsync(d.pos0, d.pos, nv * sizeof(double2), cudaMemcpyDeviceToDevice, st));
@@ -631,16 +737,27 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
       BD_TRY(cudaStreamSynchronize(st));
     }
     BD_TRY(cudaStreamSynchronize(st));
-    // force work items: a single system fills whole waves; a batch is autotuned
+    // force work items: the FP64 sweep fills whole waves; the FP32 sweep is
+    // chosen by timing (or fixed by BD_FORCE_VARIANT / BD_FORCE_TILES)
     {
-      std::vector<int4> items;
-      int mc = 1;
-      h->tune_tiles = R == 1 ? single_system_tiles(h) : 16;
-      make_items(h, h->tune_tiles, items, mc);
-      BD_TRY(upload_items(h, items, mc));
       BD_TRY(bd_launch_work_copy(d, c, st));
       BD_TRY(cudaStreamSynchronize(st));
-      if (R > 1 && c.any_long && c.precision == 0) BD_TRY(autotune(h));
+      const char *fv = getenv("BD_FORCE_VARIANT"), *ft = getenv("BD_FORCE_TILES");
+      long long nmax = 0;
+      for (const RepHost &RH : h->reps)
+        if (RH.p.law == BD_LAW_LONG) nmax = std::max<long long>(nmax, RH.n);
+      if (c.precision == 1 || !c.any_long) {
+        BD_TRY(use_variant(h, c.precision == 1 ? 1 : c.force_variant, R == 1 ? single_system_tiles(h) : 16));
+      } else if (fv) {
+        const int v = std::min(3, std::max(0, atoi(fv)));
+        const int t = ft && atoi(ft) > 0 ? atoi(ft) : (v >= 2 ? 8 : (R == 1 ? single_system_tiles(h) : 16));
+        BD_TRY(use_variant(h, v, t));
+      } else if (nmax * nmax > 180000000000LL) {
+        // a launch takes more than ~50 ms: no timing at init
+        BD_TRY(use_variant(h, 2, 16));
+      } else {
+        BD_TRY(autotune(h));
+      }
     }
     if (bd_dt_grid_for(std::max(nt, np), &h->dt_grid, &h->dt_block) != 0) {
       bd_free(h);
@@ -811,7 +928,7 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
         cudaEventRecord(h->ev_pool[2 * s + 1], st);
         ++timed;
       }
-      ++launches;
+      launches += h->c.precision == 0 ? bd_force_launches(h->c.force_variant) : 1;
     }
     if (h->c.any_short) {
       e = bd_launch_force_short(h->d, h->c, st);
@@ -1031,7 +1148,7 @@ int bd_get_tuning(bd_handle *h, int32_t *tiles_per_item, int32_t *variant, int32
   if (!h) return BD_ERR_ARG;
   if (tiles_per_item) *tiles_per_item = h->tune_tiles;
   if (variant) *variant = h->c.force_variant;
-  if (n_items) *n_items = h->c.n_items;
+  if (n_items) *n_items = h->c.force_variant >= 2 ? h->c.n_sitems : h->c.n_items;
   return BD_OK;
 }
 

@@ -10,6 +10,9 @@
 #define BD_FT 128            // threads per force block
 #define BD_IPT 4             // i disks per thread
 #define BD_IB (BD_FT * BD_IPT)  // i disks per force block
+// symmetric sweep: blocks of BD_SB consecutive slots (two j tiles); species
+// segments are padded to whole blocks so a block holds one species
+#define BD_SB 512
 
 // Verlet list capacity per disk (hard disks of radius a have at most ~40
 // neighbours within 5.6a even at close packing)
@@ -94,6 +97,14 @@ struct BdDev {
   uint8_t *tile_species;   // species of each j tile
   int4 *items;             // work items (i block, first tile, end tile, partial slot)
   double2 *fpart;          // [max_nchunk][np] partial forces
+  // symmetric sweep (each unordered pair once, both disks updated)
+  int4 *sitems;            // (block, first tile, end tile, first j-partial tile)
+  int2 *sblock;            // per block: (replica, species)
+  float2 *sorigin;         // per block: integer origin for re-centring
+  double2 *ipart;          // [item][BD_SB] i-side partial forces
+  float2 *jpart;           // [j-partial tile][BD_TJ] j-side partial forces
+  int *red_iptr, *red_iidx;  // per block: the items whose i side it is
+  int *red_jptr, *red_jidx;  // per tile: the j-partial tiles that hold it
   // short range: Verlet lists (column-major ELL) and the cell grids
   int *vl_idx, *vl_cnt;
   double2 *vl_ref;
@@ -120,7 +131,8 @@ struct BdConst {
   int qshift;              // q = 2^-qshift
   unsigned long long sig2q_hi, sig2q_lo;  // ceil((sigma/q)^2 (1 + 1e-9)) as 128-bit
   int max_corr_iters, max_flip_rounds;
-  int force_variant;       // 0: scalar FP32 sweep, 1: packed f32x2 sweep
+  int force_variant;       // 0: scalar FP32 sweep, 1: packed f32x2 sweep, 2, 3: symmetric packed sweeps
+  int n_sitems;            // symmetric sweep work items
   int log_pairs_cap, log_pass_cap;   // rollout log capacities
 };
 
@@ -138,3 +150,5 @@ cudaError_t bd_launch_work_copy(const BdDev &d, const BdConst &c, cudaStream_t s
 cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t s);
 int bd_short_launches();
 cudaError_t bd_launch_force_sum(const BdDev &d, const BdConst &c, double2 *out, cudaStream_t s);
+cudaError_t bd_launch_force_sym(const BdDev &d, const BdConst &c, int variant, cudaStream_t s);
+int bd_force_launches(int variant);   // kernel launches of one long-range force evaluation

@@ -31,27 +31,10 @@
 
 #include "bd_internal.h"
 #include "em.cuh"
+#include "f32x2.cuh"
 #include "philox.cuh"
 
-namespace {
-
-__device__ __forceinline__ float rsqrt_apx(float x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ void two_sum(float &hi, float &lo, float t) {
-  float s = __fadd_rn(hi, t);
-  float bp = __fsub_rn(s, hi);
-  float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(t, bp));
-  hi = s;
-  lo = __fadd_rn(lo, err);
-}
-
-__device__ __forceinline__ int ctl_failed(const BdCtl *ctl) { return *(volatile const int *)&ctl->status; }
-
-}  // namespace
+using namespace bdf;
 
 __global__ void __launch_bounds__(BD_FT) k_force_long_f32(BdDev d, BdConst c) {
   if (ctl_failed(d.ctl)) return;
@@ -154,33 +137,6 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32(BdDev d, BdConst c) {
 // of FP32 values in one 64-bit register pair) process two i disks per
 // instruction, halving the issue slots of the FP32 work.  j disks are staged
 // as (x, x, y, y) so one 128-bit shared load yields both packed operands.
-namespace {
-typedef unsigned long long u64;
-__device__ __forceinline__ u64 pk2(float a, float b) {
-  u64 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void up2(u64 r, float &a, float &b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-  u64 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
-  u64 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
-  u64 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-}  // namespace
-
 template <int IPT>
 __global__ void __launch_bounds__(BD_FT) k_force_long_f32x2(BdDev d, BdConst c) {
   if (ctl_failed(d.ctl)) return;
@@ -404,6 +360,7 @@ int bd_force_blocks_per_sm(int variant) {
 
 cudaError_t bd_launch_force_long_variant(const BdDev &d, const BdConst &c, int variant, cudaStream_t s) {
   if (c.precision == 0) {
+    if (variant >= 2) return bd_launch_force_sym(d, c, variant, s);
     if (c.n_items == 0) return cudaSuccess;
     if (variant == 1)
       k_force_long_f32x2<BD_IPT><<<c.n_items, BD_FT, 0, s>>>(d, c);

@@ -1,0 +1,241 @@
+// Symmetric all-pairs sweep: the long-range force of Sec. 2.2,
+//   F_i = sum_{j != i} A[s_i][s_j] (r_i - r_j) / |r_i - r_j|^3,
+// with the geometric factor g_ij = (r_i - r_j)/|r_ij|^3 = -g_ji evaluated
+// once per unordered pair and added to both disks (A[s_i][s_j] g_ij to i,
+// -A[s_j][s_i] g_ij to j; the table need not be symmetric).
+//
+// Disks sit in blocks of BD_SB = 512 consecutive slots (two j tiles), each of
+// one species.  A work item pairs block P with a range of tiles:
+//  - tiles of P itself: the i side only, all ordered pairs inside P;
+//  - later tiles (index >= 2P + 2): every pair once, both sides.
+// Pairs with an earlier tile are done by that tile's block.
+//
+// Inside an item each warp holds a share of the disks i of P in registers
+// (four or eight per lane, as packed f32x2 pairs).  A tile of 256 disks j is staged
+// in shared memory; a warp takes 32 of them, one per lane, and passes them
+// round its lanes by shuffles, each j carrying its own accumulator, so after
+// 32 steps every j has met all of the warp's i and returned to its lane.  Per
+// unordered pair: 2 sub, 2 FMA (r^2), 1 MUFU rsqrt, 2 mul (r^-3), 2 FMA into
+// the i accumulators and 2 FMA into the j accumulator -- 10 FP32 lane
+// operations for two ordered pair interactions, against 8 per ordered pair in
+// the one-sided sweep.
+//
+// Partial forces are written, not added: the i side of each item to ipart,
+// the j side of each (item, tile) to jpart.  k_force_sym_reduce then sums, for
+// every disk, its block's i partials and its tile's j partials in a fixed
+// order, so the force is deterministic.  Coordinates are re-centred on the
+// block's integer origin from the (hi, lo) FP32 pair of each FP64 coordinate,
+// as in the one-sided sweep; per-tile FP32 sums are added in (hi, lo) pairs
+// on the i side and in FP64 by the reduction.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "bd_internal.h"
+#include "f32x2.cuh"
+
+using namespace bdf;
+
+namespace {
+
+__device__ __forceinline__ float2 recentre(float4 w, float2 org) {
+  return make_float2(__fadd_rn(__fsub_rn(w.x, org.x), w.z), __fadd_rn(__fsub_rn(w.y, org.y), w.w));
+}
+
+}  // namespace
+
+// NW warps per block, NP packed i pairs (2 NP disks) per lane:
+// NW * 32 * 2 * NP = BD_SB.  Shapes built: (4 warps, 4 disks per lane) and
+// (2 warps, 8 disks per lane); the second halves the ring's shuffles and
+// register moves per pair at half the warps per block.
+template <int NW, int NP>
+__global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) {
+  if (ctl_failed(d.ctl)) return;
+  constexpr int T = NW * 32;         // threads
+  constexpr int NQ = 2 * NP;         // disks i per thread
+  constexpr int NS = BD_TJ / T;      // j disks each thread stages per tile
+  static_assert(BD_SB == T * NQ, "a block is BD_SB disks");
+  __shared__ float2 sjp[2][BD_TJ];   // j positions, re-centred
+  __shared__ float2 shw[NW][BD_TJ];  // per-warp j-side sums of the current tile
+  const int4 item = d.sitems[blockIdx.x];
+  const int P = item.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int base = P * BD_SB;
+  const int tsym = 2 * P + 2;        // first tile met from both sides
+  const int2 binfo = d.sblock[P];
+  const BdRep &R = d.rep[binfo.x];
+  const int a = binfo.y;
+  const float2 org = d.sorigin[P];
+  u64 xi2[NP], yi2[NP], ax2[NP], ay2[NP];
+  float fxh[NQ], fxl[NQ], fyh[NQ], fyl[NQ];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    float2 p0 = recentre(d.work[base + (2 * k) * T + tid], org);
+    float2 p1 = recentre(d.work[base + (2 * k + 1) * T + tid], org);
+    xi2[k] = pk2(p0.x, p1.x);
+    yi2[k] = pk2(p0.y, p1.y);
+    ax2[k] = ay2[k] = 0ull;
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) fxh[q] = fxl[q] = fyh[q] = fyl[q] = 0.f;
+  const float e0 = 1e-20f * (float)(c.a * c.a);   // makes the self pair exactly 0
+  const u64 eps2 = pk2(e0, e0);
+  const int t_begin = item.y, t_end = item.z;
+  const int jt0 = max(t_begin, tsym);
+  float2 st[NS];
+  auto fetch = [&](int tile) {
+#pragma unroll
+    for (int m = 0; m < NS; ++m) st[m] = recentre(d.work[tile * BD_TJ + m * T + tid], org);
+  };
+  auto store = [&](int b) {
+#pragma unroll
+    for (int m = 0; m < NS; ++m) sjp[b][m * T + tid] = st[m];
+  };
+  int buf = 0;
+  if (t_begin < t_end) {
+    fetch(t_begin);
+    store(0);
+  }
+  __syncthreads();
+  for (int t = t_begin; t < t_end; ++t) {
+    if (t + 1 < t_end) fetch(t + 1);
+    const int b = d.tile_species[t];
+    if (t < tsym) {
+      // the block's own disks: i side only, j broadcast from shared memory
+#pragma unroll 4
+      for (int jj = 0; jj < BD_TJ; ++jj) {
+        const float2 p = sjp[buf][jj];
+        const u64 jx2 = pk2(p.x, p.x), jy2 = pk2(p.y, p.y);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          const u64 dx = sub2(jx2, xi2[k]);
+          const u64 dy = sub2(jy2, yi2[k]);
+          u64 r2 = fma2(dx, dx, eps2);
+          r2 = fma2(dy, dy, r2);
+          float ra, rb;
+          up2(r2, ra, rb);
+          const u64 sv = pk2(rsqrt_apx(ra), rsqrt_apx(rb));
+          const u64 s3 = mul2(mul2(sv, sv), sv);
+          ax2[k] = fma2(dx, s3, ax2[k]);
+          ay2[k] = fma2(dy, s3, ay2[k]);
+        }
+      }
+    } else {
+      // a later tile: every pair once, both sides
+      for (int g = 0; g < BD_TJ / 32; ++g) {
+        const float2 p = sjp[buf][g * 32 + lane];
+        float jx = p.x, jy = p.y;
+        u64 hx2 = 0ull, hy2 = 0ull;
+#pragma unroll 2
+        for (int rot = 0; rot < 32; ++rot) {
+          const u64 jx2 = pk2(jx, jx), jy2 = pk2(jy, jy);
+          // the next j position does not depend on this step's arithmetic
+          const int src = (lane + 1) & 31;
+          const float njx = __shfl_sync(0xffffffffu, jx, src);
+          const float njy = __shfl_sync(0xffffffffu, jy, src);
+#pragma unroll
+          for (int k = 0; k < NP; ++k) {
+            const u64 dx = sub2(jx2, xi2[k]);
+            const u64 dy = sub2(jy2, yi2[k]);
+            u64 r2 = fma2(dx, dx, eps2);
+            r2 = fma2(dy, dy, r2);
+            float ra, rb;
+            up2(r2, ra, rb);
+            const u64 sv = pk2(rsqrt_apx(ra), rsqrt_apx(rb));
+            const u64 s3 = mul2(mul2(sv, sv), sv);
+            ax2[k] = fma2(dx, s3, ax2[k]);
+            ay2[k] = fma2(dy, s3, ay2[k]);
+            hx2 = fma2(dx, s3, hx2);
+            hy2 = fma2(dy, s3, hy2);
+          }
+          // pass the j accumulator one lane down the ring, after its disk
+          float h0, h1, h2, h3;
+          up2(hx2, h0, h1);
+          up2(hy2, h2, h3);
+          h0 = __shfl_sync(0xffffffffu, h0, src);
+          h1 = __shfl_sync(0xffffffffu, h1, src);
+          h2 = __shfl_sync(0xffffffffu, h2, src);
+          h3 = __shfl_sync(0xffffffffu, h3, src);
+          hx2 = pk2(h0, h1);
+          hy2 = pk2(h2, h3);
+          jx = njx;
+          jy = njy;
+        }
+        // after 32 passes every j is back in its own lane
+        float h0, h1, h2, h3;
+        up2(hx2, h0, h1);
+        up2(hy2, h2, h3);
+        shw[warp][g * 32 + lane] = make_float2(__fadd_rn(h0, h1), __fadd_rn(h2, h3));
+      }
+      __syncthreads();
+      // j side of this tile: F_j += A[s_j][s_i] sum_i (r_j - r_i)/r^3
+      const float alj = R.alpha[2 * b + a];
+      float2 *out = d.jpart + (size_t)(item.w + (t - jt0)) * BD_TJ;
+      for (int jj = tid; jj < BD_TJ; jj += T) {
+        float hx = 0.f, hy = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          hx = __fadd_rn(hx, shw[w][jj].x);
+          hy = __fadd_rn(hy, shw[w][jj].y);
+        }
+        out[jj] = make_float2(alj * hx, alj * hy);
+      }
+    }
+    // i side of this tile: F_i -= A[s_i][s_j] sum_j (r_j - r_i)/r^3
+    const float ali = R.alpha[2 * a + b];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      float ax0, ax1, ay0, ay1;
+      up2(ax2[k], ax0, ax1);
+      up2(ay2[k], ay0, ay1);
+      two_sum(fxh[2 * k], fxl[2 * k], -ali * ax0);
+      two_sum(fyh[2 * k], fyl[2 * k], -ali * ay0);
+      two_sum(fxh[2 * k + 1], fxl[2 * k + 1], -ali * ax1);
+      two_sum(fyh[2 * k + 1], fyl[2 * k + 1], -ali * ay1);
+      ax2[k] = ay2[k] = 0ull;
+    }
+    if (t + 1 < t_end) store(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  double2 *ip = d.ipart + (size_t)blockIdx.x * BD_SB;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+    ip[q * T + tid] = make_double2((double)fxh[q] + (double)fxl[q], (double)fyh[q] + (double)fyl[q]);
+}
+
+// F_i = sum of its block's i partials + sum of its tile's j partials, in the
+// order the host listed them (item order), into partial-force slot 0
+__global__ void k_force_sym_reduce(BdDev d, BdConst c) {
+  if (ctl_failed(d.ctl)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.np) return;
+  const int r = d.rep_of[i];
+  if (r < 0 || d.rep[r].law != BD_LAW_LONG) return;
+  const int P = i / BD_SB, t = i / BD_TJ;
+  const int oi = i - P * BD_SB, oj = i - t * BD_TJ;
+  double fx = 0.0, fy = 0.0;
+  for (int k = d.red_iptr[P]; k < d.red_iptr[P + 1]; ++k) {
+    const double2 v = d.ipart[(size_t)d.red_iidx[k] * BD_SB + oi];
+    fx += v.x;
+    fy += v.y;
+  }
+  for (int k = d.red_jptr[t]; k < d.red_jptr[t + 1]; ++k) {
+    const float2 v = d.jpart[(size_t)d.red_jidx[k] * BD_TJ + oj];
+    fx += (double)v.x;
+    fy += (double)v.y;
+  }
+  d.fpart[i] = make_double2(fx, fy);
+}
+
+int bd_force_launches(int variant) { return variant >= 2 ? 2 : 1; }
+
+// variant 2: 4 warps x 4 disks per lane; variant 3: 2 warps x 8 disks per lane
+cudaError_t bd_launch_force_sym(const BdDev &d, const BdConst &c, int variant, cudaStream_t s) {
+  if (c.n_sitems == 0) return cudaSuccess;
+  if (variant == 3)
+    k_force_long_sym<2, 4><<<c.n_sitems, 64, 0, s>>>(d, c);
+  else
+    k_force_long_sym<4, 2><<<c.n_sitems, 128, 0, s>>>(d, c);
+  k_force_sym_reduce<<<(c.np + 255) / 256, 256, 0, s>>>(d, c);
+  return cudaGetLastError();
+}

@@ -408,7 +408,7 @@ int bd_rollout(bd_handle *h, int32_t nsteps, int32_t ckpt_every, int32_t loss_ki
         e = bd_launch_force_long(h->d, h->c, s);
         if (e == cudaSuccess) e = bd_launch_integrate(h->d, h->c, r->step0 + t, t, s);
         if (e == cudaSuccess) e = bd_launch_dt(h->d, h->c, 0, s, h->dt_grid, h->dt_block, t);
-        launches += 3;
+        launches += 2 + (h->c.precision == 0 ? bd_force_launches(h->c.force_variant) : 1);
       }
       if (e != cudaSuccess) break;
       int rc = bdcapi::read_ctl(h);

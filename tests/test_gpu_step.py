@@ -55,6 +55,26 @@ def test_forces_match_oracle(cfgname, n):
         assert err <= 1e-12
 
 
+@pytest.mark.parametrize("variant,tiles", [(0, 3), (1, 5), (2, 1), (2, 2), (2, 7), (3, 1), (3, 4)])
+@pytest.mark.parametrize("cfgname,n", [("c2", 3001), ("c2", 1300), ("c1", 1024)])
+def test_force_variants_match_oracle(monkeypatch, variant, tiles, cfgname, n):
+    # every FP32 sweep, chunk sizes that split rows unevenly, ragged species segments
+    monkeypatch.setenv("BD_FORCE_VARIANT", str(variant))
+    monkeypatch.setenv("BD_FORCE_TILES", str(tiles))
+    cfg = workloads.CONFIGS[cfgname]
+    xy, sp, th = workloads.initial_state(cfg, n=n)
+    p = bd.params_from_config(cfg, n=n)
+    p.precision = 0
+    s = bd.System(p, xy, sp, th, stream=stream())
+    assert s.tuning()["variant"] == variant and s.tuning()["tiles_per_item"] == tiles
+    F = s.forces()
+    grid = s.state(want_tri=False)["xy"]
+    A = cfg.alpha if cfg.n_species == 2 else (cfg.alpha[0],) * 4
+    assert force_error(F, oforces.long_range_numpy(grid, sp, A)) <= FORCE_TOL
+    # deterministic: a second evaluation gives the same bits
+    assert np.array_equal(s.forces(), F)
+
+
 def test_forces_full_size_sampled():
     cfg = workloads.CONFIGS["n1e5"]
     xy, sp, th = workloads.initial_state(cfg)
