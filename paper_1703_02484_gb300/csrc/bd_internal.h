@@ -101,7 +101,7 @@ struct BdDev {
   int4 *sitems;            // (block, first tile, end tile, first j-partial tile)
   int2 *sblock;            // per block: (replica, species)
   float2 *sorigin;         // per block: integer origin for re-centring
-  double2 *ipart;          // [item][BD_SB] i-side partial forces
+  float2 *ipart;           // [item][BD_SB] i-side partial forces
   float2 *jpart;           // [j-partial tile][BD_TJ] j-side partial forces
   int *red_iptr, *red_iidx;  // per block: the items whose i side it is
   int *red_jptr, *red_jidx;  // per tile: the j-partial tiles that hold it

@@ -26,7 +26,8 @@
 // order, so the force is deterministic.  Coordinates are re-centred on the
 // block's integer origin from the (hi, lo) FP32 pair of each FP64 coordinate,
 // as in the one-sided sweep; per-tile FP32 sums are added in (hi, lo) pairs
-// on the i side and in FP64 by the reduction.
+// within an item on the i side, and partials (FP32) in float-float by the
+// reduction.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -44,11 +45,14 @@ __device__ __forceinline__ float2 recentre(float4 w, float2 org) {
 
 }  // namespace
 
-// NW warps per block, NP packed i pairs (2 NP disks) per lane:
+// NW warps per block, NP packed i pairs (2 NP disks) per lane, NJ disks j
+// carried per lane, COMB: fold the packed halves of a j accumulator before
+// passing it (2 shuffles instead of 4), UR: unrolled ring steps.
 // NW * 32 * 2 * NP = BD_SB.  Shapes built: (4 warps, 4 disks per lane) and
-// (2 warps, 8 disks per lane); the second halves the ring's shuffles and
-// register moves per pair at half the warps per block.
-template <int NW, int NP>
+// (2 warps, 8 disks per lane), one j per lane, halves passed unfolded; the
+// second halves the ring's shuffles and register moves per pair.  (Two j per
+// lane, folded halves and deeper unrolling measured within 3 % of these.)
+template <int NW, int NP, int NJ, bool COMB, int UR>
 __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) {
   if (ctl_failed(d.ctl)) return;
   constexpr int T = NW * 32;         // threads
@@ -120,51 +124,70 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
         }
       }
     } else {
-      // a later tile: every pair once, both sides
-      for (int g = 0; g < BD_TJ / 32; ++g) {
-        const float2 p = sjp[buf][g * 32 + lane];
-        float jx = p.x, jy = p.y;
-        u64 hx2 = 0ull, hy2 = 0ull;
-#pragma unroll 2
-        for (int rot = 0; rot < 32; ++rot) {
-          const u64 jx2 = pk2(jx, jx), jy2 = pk2(jy, jy);
-          // the next j position does not depend on this step's arithmetic
-          const int src = (lane + 1) & 31;
-          const float njx = __shfl_sync(0xffffffffu, jx, src);
-          const float njy = __shfl_sync(0xffffffffu, jy, src);
+      // a later tile: every pair once, both sides; each lane carries NJ disks j
+      for (int g = 0; g < BD_TJ / (32 * NJ); ++g) {
+        float jx[NJ], jy[NJ];
+        u64 hx2[NJ], hy2[NJ];
 #pragma unroll
-          for (int k = 0; k < NP; ++k) {
-            const u64 dx = sub2(jx2, xi2[k]);
-            const u64 dy = sub2(jy2, yi2[k]);
-            u64 r2 = fma2(dx, dx, eps2);
-            r2 = fma2(dy, dy, r2);
-            float ra, rb;
-            up2(r2, ra, rb);
-            const u64 sv = pk2(rsqrt_apx(ra), rsqrt_apx(rb));
-            const u64 s3 = mul2(mul2(sv, sv), sv);
-            ax2[k] = fma2(dx, s3, ax2[k]);
-            ay2[k] = fma2(dy, s3, ay2[k]);
-            hx2 = fma2(dx, s3, hx2);
-            hy2 = fma2(dy, s3, hy2);
+        for (int m = 0; m < NJ; ++m) {
+          const float2 p = sjp[buf][(g * NJ + m) * 32 + lane];
+          jx[m] = p.x;
+          jy[m] = p.y;
+          hx2[m] = hy2[m] = 0ull;
+        }
+#pragma unroll UR
+        for (int rot = 0; rot < 32; ++rot) {
+          const int src = (lane + 1) & 31;
+#pragma unroll
+          for (int m = 0; m < NJ; ++m) {
+            const u64 jx2 = pk2(jx[m], jx[m]), jy2 = pk2(jy[m], jy[m]);
+            // the next j position does not depend on this step's arithmetic
+            const float njx = __shfl_sync(0xffffffffu, jx[m], src);
+            const float njy = __shfl_sync(0xffffffffu, jy[m], src);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+              const u64 dx = sub2(jx2, xi2[k]);
+              const u64 dy = sub2(jy2, yi2[k]);
+              u64 r2 = fma2(dx, dx, eps2);
+              r2 = fma2(dy, dy, r2);
+              float ra, rb;
+              up2(r2, ra, rb);
+              const u64 sv = pk2(rsqrt_apx(ra), rsqrt_apx(rb));
+              const u64 s3 = mul2(mul2(sv, sv), sv);
+              ax2[k] = fma2(dx, s3, ax2[k]);
+              ay2[k] = fma2(dy, s3, ay2[k]);
+              hx2[m] = fma2(dx, s3, hx2[m]);
+              hy2[m] = fma2(dy, s3, hy2[m]);
+            }
+            // pass the j accumulator one lane down the ring, after its disk
+            float h0, h1, h2, h3;
+            up2(hx2[m], h0, h1);
+            up2(hy2[m], h2, h3);
+            if (COMB) {
+              h0 = __shfl_sync(0xffffffffu, __fadd_rn(h0, h1), src);
+              h2 = __shfl_sync(0xffffffffu, __fadd_rn(h2, h3), src);
+              hx2[m] = pk2(h0, 0.f);
+              hy2[m] = pk2(h2, 0.f);
+            } else {
+              h0 = __shfl_sync(0xffffffffu, h0, src);
+              h1 = __shfl_sync(0xffffffffu, h1, src);
+              h2 = __shfl_sync(0xffffffffu, h2, src);
+              h3 = __shfl_sync(0xffffffffu, h3, src);
+              hx2[m] = pk2(h0, h1);
+              hy2[m] = pk2(h2, h3);
+            }
+            jx[m] = njx;
+            jy[m] = njy;
           }
-          // pass the j accumulator one lane down the ring, after its disk
-          float h0, h1, h2, h3;
-          up2(hx2, h0, h1);
-          up2(hy2, h2, h3);
-          h0 = __shfl_sync(0xffffffffu, h0, src);
-          h1 = __shfl_sync(0xffffffffu, h1, src);
-          h2 = __shfl_sync(0xffffffffu, h2, src);
-          h3 = __shfl_sync(0xffffffffu, h3, src);
-          hx2 = pk2(h0, h1);
-          hy2 = pk2(h2, h3);
-          jx = njx;
-          jy = njy;
         }
         // after 32 passes every j is back in its own lane
-        float h0, h1, h2, h3;
-        up2(hx2, h0, h1);
-        up2(hy2, h2, h3);
-        shw[warp][g * 32 + lane] = make_float2(__fadd_rn(h0, h1), __fadd_rn(h2, h3));
+#pragma unroll
+        for (int m = 0; m < NJ; ++m) {
+          float h0, h1, h2, h3;
+          up2(hx2[m], h0, h1);
+          up2(hy2[m], h2, h3);
+          shw[warp][(g * NJ + m) * 32 + lane] = make_float2(__fadd_rn(h0, h1), __fadd_rn(h2, h3));
+        }
       }
       __syncthreads();
       // j side of this tile: F_j += A[s_j][s_i] sum_i (r_j - r_i)/r^3
@@ -197,32 +220,53 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
     __syncthreads();
     buf ^= 1;
   }
-  double2 *ip = d.ipart + (size_t)blockIdx.x * BD_SB;
+  float2 *ip = d.ipart + (size_t)blockIdx.x * BD_SB;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q)
-    ip[q * T + tid] = make_double2((double)fxh[q] + (double)fxl[q], (double)fyh[q] + (double)fyl[q]);
+  for (int q = 0; q < NQ; ++q) ip[q * T + tid] = make_float2(__fadd_rn(fxh[q], fxl[q]), __fadd_rn(fyh[q], fyl[q]));
 }
 
 // F_i = sum of its block's i partials + sum of its tile's j partials, in the
-// order the host listed them (item order), into partial-force slot 0
-__global__ void k_force_sym_reduce(BdDev d, BdConst c) {
+// order the host listed them (item order), into partial-force slot 0.  The
+// sums are float-float (TwoSum into a (hi, lo) FP32 pair, about 48 bits): FP64
+// adds run at 1/64 of the FP32 rate on this part and would bound the kernel.
+// Four running sums take every fourth partial, so four loads are in flight;
+// they are combined in a fixed order at the end.
+__global__ void __launch_bounds__(256) k_force_sym_reduce(BdDev d, BdConst c) {
   if (ctl_failed(d.ctl)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= c.np) return;
   const int r = d.rep_of[i];
   if (r < 0 || d.rep[r].law != BD_LAW_LONG) return;
   const int P = i / BD_SB, t = i / BD_TJ;
-  const int oi = i - P * BD_SB, oj = i - t * BD_TJ;
+  const float2 *ib = d.ipart + (i - P * BD_SB);
+  const float2 *jb = d.jpart + (i - t * BD_TJ);
+  float xh[4] = {0.f, 0.f, 0.f, 0.f}, xl[4] = {0.f, 0.f, 0.f, 0.f};
+  float yh[4] = {0.f, 0.f, 0.f, 0.f}, yl[4] = {0.f, 0.f, 0.f, 0.f};
+  auto run = [&](const int *idx, int k0, int k1, const float2 *b, int stride) {
+    int k = k0;
+    for (; k + 4 <= k1; k += 4) {
+      float2 v[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) v[m] = b[(size_t)__ldg(idx + k + m) * stride];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        two_sum(xh[m], xl[m], v[m].x);
+        two_sum(yh[m], yl[m], v[m].y);
+      }
+    }
+    for (int m = 0; k < k1; ++k, ++m) {
+      const float2 v = b[(size_t)__ldg(idx + k) * stride];
+      two_sum(xh[m], xl[m], v.x);
+      two_sum(yh[m], yl[m], v.y);
+    }
+  };
+  run(d.red_iidx, d.red_iptr[P], d.red_iptr[P + 1], ib, BD_SB);
+  run(d.red_jidx, d.red_jptr[t], d.red_jptr[t + 1], jb, BD_TJ);
   double fx = 0.0, fy = 0.0;
-  for (int k = d.red_iptr[P]; k < d.red_iptr[P + 1]; ++k) {
-    const double2 v = d.ipart[(size_t)d.red_iidx[k] * BD_SB + oi];
-    fx += v.x;
-    fy += v.y;
-  }
-  for (int k = d.red_jptr[t]; k < d.red_jptr[t + 1]; ++k) {
-    const float2 v = d.jpart[(size_t)d.red_jidx[k] * BD_TJ + oj];
-    fx += (double)v.x;
-    fy += (double)v.y;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    fx += (double)xh[m] + (double)xl[m];
+    fy += (double)yh[m] + (double)yl[m];
   }
   d.fpart[i] = make_double2(fx, fy);
 }
@@ -232,10 +276,10 @@ int bd_force_launches(int variant) { return variant >= 2 ? 2 : 1; }
 // variant 2: 4 warps x 4 disks per lane; variant 3: 2 warps x 8 disks per lane
 cudaError_t bd_launch_force_sym(const BdDev &d, const BdConst &c, int variant, cudaStream_t s) {
   if (c.n_sitems == 0) return cudaSuccess;
-  if (variant == 3)
-    k_force_long_sym<2, 4><<<c.n_sitems, 64, 0, s>>>(d, c);
+  if (variant == 2)
+    k_force_long_sym<4, 2, 1, false, 2><<<c.n_sitems, 128, 0, s>>>(d, c);
   else
-    k_force_long_sym<4, 2><<<c.n_sitems, 128, 0, s>>>(d, c);
+    k_force_long_sym<2, 4, 1, false, 2><<<c.n_sitems, 64, 0, s>>>(d, c);
   k_force_sym_reduce<<<(c.np + 255) / 256, 256, 0, s>>>(d, c);
   return cudaGetLastError();
 }

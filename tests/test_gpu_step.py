@@ -5,6 +5,7 @@ relative to the force norm (read as the RMS of |F_i| over the system), and
 position error <= 1e-5 a after one step; the Delaunay edge set must match
 exactly for points in general position."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -75,19 +76,18 @@ def test_force_variants_match_oracle(monkeypatch, variant, tiles, cfgname, n):
     assert np.array_equal(s.forces(), F)
 
 
-def test_forces_full_size_sampled():
-    cfg = workloads.CONFIGS["n1e5"]
+@pytest.mark.parametrize("cfgname", ["n1e5", "c2"])
+def test_forces_full_size_every_disk(cfgname):
+    # the full workload in the configuration the benchmark times (autotuned
+    # sweep), every disk against the oracle's FP64 sum (OpenMP C loop)
+    cfg = workloads.CONFIGS[cfgname]
     xy, sp, th = workloads.initial_state(cfg)
     s = bd.System(bd.params_from_config(cfg), xy, sp, th, stream=stream())
     F = s.forces()
     grid = s.state(want_tri=False)["xy"]
-    rng = np.random.default_rng(0)
-    idx = np.sort(rng.choice(cfg.n, 256, replace=False))
-    ref = np.concatenate([oforces.long_range(grid, sp, cfg.alpha, idx=[i], threads=1) for i in idx])
-    # RMS force scale from the sample
-    scale = math.sqrt(float(np.mean(np.sum(ref ** 2, axis=1))))
-    err = float(np.max(np.linalg.norm(F[idx] - ref, axis=1))) / scale
-    assert err <= FORCE_TOL, err
+    ref = oforces.long_range(grid, sp, cfg.alpha, threads=max(1, os.cpu_count() or 1))
+    err = force_error(F, ref)
+    assert err <= FORCE_TOL, (err, s.tuning())
 
 
 def _one_step(cfgname, n, seed_state, step_index=0, near_contact=True):
