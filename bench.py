@@ -401,7 +401,8 @@ def main():
             import hashlib
             with open(prof) as f:
                 rec = json.load(f)
-            with open(os.path.join(ROOT, "paper_1703_02484_gb300", "csrc", "kernels_force.cu"), "rb") as f:
+            src = "kernels_sym.cu" if variant >= 2 else "kernels_force.cu"
+            with open(os.path.join(ROOT, "paper_1703_02484_gb300", "csrc", src), "rb") as f:
                 h = hashlib.sha256(f.read()).hexdigest()[:16]
             if rec.get("kernel") == kernel and rec.get("kernel_source_sha256_16") == h:
                 traffic = rec.get("traffic_bytes_per_launch")

@@ -226,47 +226,54 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
 }
 
 // F_i = sum of its block's i partials + sum of its tile's j partials, in the
-// order the host listed them (item order), into partial-force slot 0.  The
-// sums are float-float (TwoSum into a (hi, lo) FP32 pair, about 48 bits): FP64
-// adds run at 1/64 of the FP32 rate on this part and would bound the kernel.
-// Four running sums take every fourth partial, so four loads are in flight;
-// they are combined in a fixed order at the end.
-__global__ void __launch_bounds__(256) k_force_sym_reduce(BdDev d, BdConst c) {
+// order the host listed them (item order), into partial-force slot 0.
+// A block of 256 threads serves 64 consecutive disks: thread group g (of 4)
+// takes every fourth partial (entries g, g + 4, ...) of the 64 disks, so the
+// loads stay coalesced and four times as many warps hide their latency; the
+// four group sums are added in a fixed order.  Sums are float-float (TwoSum
+// into a (hi, lo) FP32 pair, about 48 bits): FP64 adds run at 1/64 of the FP32
+// rate on this part and would bound the kernel.
+#define BD_RED_D 64   // disks per reduction block
+__global__ void __launch_bounds__(4 * BD_RED_D) k_force_sym_reduce(BdDev d, BdConst c) {
+  __shared__ float4 part[4][BD_RED_D];
   if (ctl_failed(d.ctl)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= c.np) return;
-  const int r = d.rep_of[i];
-  if (r < 0 || d.rep[r].law != BD_LAW_LONG) return;
-  const int P = i / BD_SB, t = i / BD_TJ;
+  const int g = threadIdx.x / BD_RED_D, dl = threadIdx.x % BD_RED_D;
+  const int i = blockIdx.x * BD_RED_D + dl;        // np is a multiple of 512: i < np
+  const int P = i / BD_SB, t = i / BD_TJ;           // the same for the whole block
   const float2 *ib = d.ipart + (i - P * BD_SB);
   const float2 *jb = d.jpart + (i - t * BD_TJ);
-  float xh[4] = {0.f, 0.f, 0.f, 0.f}, xl[4] = {0.f, 0.f, 0.f, 0.f};
-  float yh[4] = {0.f, 0.f, 0.f, 0.f}, yl[4] = {0.f, 0.f, 0.f, 0.f};
+  float xh[2] = {0.f, 0.f}, xl[2] = {0.f, 0.f}, yh[2] = {0.f, 0.f}, yl[2] = {0.f, 0.f};
   auto run = [&](const int *idx, int k0, int k1, const float2 *b, int stride) {
-    int k = k0;
-    for (; k + 4 <= k1; k += 4) {
-      float2 v[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) v[m] = b[(size_t)__ldg(idx + k + m) * stride];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        two_sum(xh[m], xl[m], v[m].x);
-        two_sum(yh[m], yl[m], v[m].y);
-      }
+    int k = k0 + g;
+    for (; k + 4 < k1; k += 8) {
+      const float2 v0 = b[(size_t)__ldg(idx + k) * stride];
+      const float2 v1 = b[(size_t)__ldg(idx + k + 4) * stride];
+      two_sum(xh[0], xl[0], v0.x);
+      two_sum(yh[0], yl[0], v0.y);
+      two_sum(xh[1], xl[1], v1.x);
+      two_sum(yh[1], yl[1], v1.y);
     }
-    for (int m = 0; k < k1; ++k, ++m) {
-      const float2 v = b[(size_t)__ldg(idx + k) * stride];
-      two_sum(xh[m], xl[m], v.x);
-      two_sum(yh[m], yl[m], v.y);
+    if (k < k1) {
+      const float2 v0 = b[(size_t)__ldg(idx + k) * stride];
+      two_sum(xh[0], xl[0], v0.x);
+      two_sum(yh[0], yl[0], v0.y);
     }
   };
   run(d.red_iidx, d.red_iptr[P], d.red_iptr[P + 1], ib, BD_SB);
   run(d.red_jidx, d.red_jptr[t], d.red_jptr[t + 1], jb, BD_TJ);
+  two_sum(xh[0], xl[0], xh[1]);
+  two_sum(yh[0], yl[0], yh[1]);
+  part[g][dl] = make_float4(xh[0], __fadd_rn(xl[0], xl[1]), yh[0], __fadd_rn(yl[0], yl[1]));
+  __syncthreads();
+  if (g != 0) return;
+  const int r = d.rep_of[i];
+  if (r < 0 || d.rep[r].law != BD_LAW_LONG) return;
   double fx = 0.0, fy = 0.0;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    fx += (double)xh[m] + (double)xl[m];
-    fy += (double)yh[m] + (double)yl[m];
+    const float4 q = part[m][dl];
+    fx += (double)q.x + (double)q.y;
+    fy += (double)q.z + (double)q.w;
   }
   d.fpart[i] = make_double2(fx, fy);
 }
@@ -280,6 +287,6 @@ cudaError_t bd_launch_force_sym(const BdDev &d, const BdConst &c, int variant, c
     k_force_long_sym<4, 2, 1, false, 2><<<c.n_sitems, 128, 0, s>>>(d, c);
   else
     k_force_long_sym<2, 4, 1, false, 2><<<c.n_sitems, 64, 0, s>>>(d, c);
-  k_force_sym_reduce<<<(c.np + 255) / 256, 256, 0, s>>>(d, c);
+  k_force_sym_reduce<<<c.np / BD_RED_D, 4 * BD_RED_D, 0, s>>>(d, c);
   return cudaGetLastError();
 }
