@@ -86,6 +86,7 @@ SIGNATURES = [
     ("bd_rollout_replay", ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     ("bd_rollout_positions", ctypes.c_int, [_P, ctypes.c_int32, _P]),
     ("bd_rollout_log_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    ("bd_stage_times", ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     ("bd_free", None, [_P]),
     ("bd_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -273,6 +274,14 @@ class System:
 
     def last_launch_count(self):
         return int(load().bd_last_launch_count(self.h))
+
+    def stage_times(self, reset=False):
+        """Triangulation-kernel stage times (ms) and pass counts since the last
+        reset: dict check/repair/flip/apply -> (ms, passes)."""
+        ms = np.zeros(4, dtype=np.float64)
+        n = np.zeros(4, dtype=np.int64)
+        _check(load().bd_stage_times(self.h, int(reset), _ptr(ms), _ptr(n)), "bd_stage_times")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(("check", "repair", "flip", "apply"))}
 
     # ---- differentiated rollout ----
     def set_force_params(self, alpha=None, v0=None):

@@ -793,6 +793,13 @@ cudaError_t reset_stats(bd_handle *h) {
   return cudaMemsetAsync(&h->d.ctl->status, 0, sizeof(int), h->stream);
 }
 
+void add_stage_times(bd_handle *h) {
+  for (int k = 0; k < 4; ++k) {
+    h->stage_ns[k] += (double)h->h_ctl->st_stage_ns[k];
+    h->stage_cnt[k] += h->h_ctl->st_stage_cnt[k];
+  }
+}
+
 int finish_status(bd_handle *h, int status) {
   // clear the sticky status so the handle keeps working from the last good
   // state; after a timed-out barrier also reset the barrier words
@@ -952,6 +959,7 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
     }
   }
   const BdCtl &k = *h->h_ctl;
+  add_stage_times(h);
   h->step += k.st_steps;
   if (stats) {
     stats->steps_done = k.st_steps;
@@ -1165,6 +1173,20 @@ int bd_force_timing(bd_handle *h, int enable, int reset, double *total_ms, int64
 }
 
 int64_t bd_last_launch_count(bd_handle *h) { return h ? h->last_launches : -1; }
+
+int bd_stage_times(bd_handle *h, int reset, double *ms, int64_t *phases) {
+  if (!h) return BD_ERR_ARG;
+  for (int k = 0; k < 4; ++k) {
+    if (ms) ms[k] = h->stage_ns[k] * 1e-6;
+    if (phases) phases[k] = h->stage_cnt[k];
+  }
+  if (reset)
+    for (int k = 0; k < 4; ++k) {
+      h->stage_ns[k] = 0.0;
+      h->stage_cnt[k] = 0;
+    }
+  return BD_OK;
+}
 
 int bd_ghost_points(double L, double a, double *xy, int32_t *count) {
   if (!(L > 0) || !(a > 0) || !count) return BD_ERR_ARG;

@@ -46,6 +46,8 @@ struct bd_handle {
   int fpart_slots = 0;             // partial-force slots allocated
   std::vector<int> fpart_cap;      // per replica: chunks that fit
   BdRollout *ro = nullptr;         // differentiated rollout state (lazily created)
+  double stage_ns[4] = {0, 0, 0, 0};   // triangulation-kernel stage times since the last reset
+  int64_t stage_cnt[4] = {0, 0, 0, 0};
 };
 
 namespace bdcapi {
@@ -54,6 +56,7 @@ int read_ctl(bd_handle *h);                // copy the control block to h_ctl (s
 cudaError_t reset_stats(bd_handle *h);     // zero the per-call statistics
 int finish_status(bd_handle *h, int status);
 void rollout_release(bd_handle *h);        // free the rollout buffers
+void add_stage_times(bd_handle *h);        // accumulate the stage times of the last read_ctl
 }  // namespace bdcapi
 
 // adjoint kernels (adjoint.cu)

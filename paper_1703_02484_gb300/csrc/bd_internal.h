@@ -50,6 +50,11 @@ struct BdCtl {
   long long st_barriers;           // grid barriers passed by the triangulation kernel
   int st_fail_item;                // an offending triangle (repair) or edge corner (reversal)
   int st_fail_count;               // inverted triangles / reversed edges at the failure
+  // wall time of the triangulation kernel's stages as its lead thread sees
+  // them (each stage's work plus its closing grid barrier): P check/mark/scan,
+  // R inversion repair, F Lawson flips, A apply corrections
+  unsigned long long st_stage_ns[4];
+  long long st_stage_cnt[4];
   // rollout log cursors (not reset per call)
   int log_npass;                   // committed correction passes
   int log_npairs;                  // logged pairs

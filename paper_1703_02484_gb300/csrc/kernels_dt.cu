@@ -111,6 +111,16 @@ __device__ bool grid_sync(BdCtl *ctl, Bar &b) {
 
 __device__ __forceinline__ int *cnt(BdCtl *ctl, int ph, int slot) { return &ctl->cnt[ph & 3][slot]; }
 
+enum { STAGE_P = 0, STAGE_R = 1, STAGE_F = 2, STAGE_A = 3 };
+
+// lead thread only: charge the time since the last mark to a stage
+__device__ __forceinline__ void stage_tick(BdCtl *ctl, int stage, unsigned long long &mark) {
+  const unsigned long long now = gtimer();
+  ctl->st_stage_ns[stage] += now - mark;
+  ctl->st_stage_cnt[stage] += 1;
+  mark = now;
+}
+
 // every block calls this once on its way out; the last one resets the barrier
 // words and phase counters so the next launch starts clean without a memset
 __device__ void block_exit(BdCtl *ctl) {
@@ -157,14 +167,60 @@ struct Ctx {
   bdpred::Grid g;
   int T;
   int np;
+  float sig2f;   // sigma^2 (1 + 1e-5): FP32 screen of the overlap scan
 };
 
+// FP32 filters in front of the exact integer predicates.  Every disk's
+// position is also held as an FP32 pair (x_hi, x_lo) with x_hi + x_lo equal to
+// the FP64 position to ~1e-11 a (the sweeps' copy), so a coordinate
+// difference (b_hi - a_hi) + (b_lo - a_lo) carries one FP32 rounding of
+// itself (relative 2^-24).  The determinant is then evaluated in FP32 with
+// explicit rounding and compared with a bound on its error relative to the
+// permanent (the same expression with absolute values): Shewchuk's bounds for
+// exact inputs (3e-16 / 1.1e-15 relative in FP64, i.e. about 4 and 11 units
+// of the working precision) plus one unit per input factor, times a safety
+// factor of about four.  Outside the bound the FP32 sign is the exact sign;
+// inside it, or for ghost points (no FP32 copy), the integer path decides.
+__device__ __forceinline__ float fdiff(float bh, float bl, float ah, float al) {
+  return __fadd_rn(__fsub_rn(bh, ah), __fsub_rn(bl, al));
+}
+
 __device__ __forceinline__ int orient_v(const Ctx &x, int a, int b, int c) {
+  if (a < x.np && b < x.np && c < x.np) {
+    const float4 wa = x.d.work[a], wb = x.d.work[b], wc = x.d.work[c];
+    const float bax = fdiff(wb.x, wb.z, wa.x, wa.z), bay = fdiff(wb.y, wb.w, wa.y, wa.w);
+    const float cax = fdiff(wc.x, wc.z, wa.x, wa.z), cay = fdiff(wc.y, wc.w, wa.y, wa.w);
+    const float l = __fmul_rn(bax, cay), r = __fmul_rn(bay, cax);
+    const float det = __fsub_rn(l, r);
+    const float bound = 1.5e-6f * __fadd_rn(fabsf(l), fabsf(r));
+    if (det > bound) return 1;
+    if (-det > bound) return -1;
+  }
   double2 pa = x.d.pos[a], pb = x.d.pos[b], pc = x.d.pos[c];
   return bdpred::orient(pa.x, pa.y, pb.x, pb.y, pc.x, pc.y, x.g);
 }
 
 __device__ __forceinline__ int incircle_v(const Ctx &x, int a, int b, int c, int p) {
+  if (a < x.np && b < x.np && c < x.np && p < x.np) {
+    const float4 wa = x.d.work[a], wb = x.d.work[b], wc = x.d.work[c], wp = x.d.work[p];
+    const float adx = fdiff(wa.x, wa.z, wp.x, wp.z), ady = fdiff(wa.y, wa.w, wp.y, wp.w);
+    const float bdx = fdiff(wb.x, wb.z, wp.x, wp.z), bdy = fdiff(wb.y, wb.w, wp.y, wp.w);
+    const float cdx = fdiff(wc.x, wc.z, wp.x, wp.z), cdy = fdiff(wc.y, wc.w, wp.y, wp.w);
+    const float bcl = __fmul_rn(bdx, cdy), bcr = __fmul_rn(bdy, cdx);
+    const float cal = __fmul_rn(cdx, ady), car = __fmul_rn(cdy, adx);
+    const float abl = __fmul_rn(adx, bdy), abr = __fmul_rn(ady, bdx);
+    const float al = __fadd_rn(__fmul_rn(adx, adx), __fmul_rn(ady, ady));
+    const float bl = __fadd_rn(__fmul_rn(bdx, bdx), __fmul_rn(bdy, bdy));
+    const float cl = __fadd_rn(__fmul_rn(cdx, cdx), __fmul_rn(cdy, cdy));
+    const float det = __fadd_rn(__fadd_rn(__fmul_rn(al, __fsub_rn(bcl, bcr)), __fmul_rn(bl, __fsub_rn(cal, car))),
+                                __fmul_rn(cl, __fsub_rn(abl, abr)));
+    const float perm =
+        __fadd_rn(__fadd_rn(__fmul_rn(al, __fadd_rn(fabsf(bcl), fabsf(bcr))), __fmul_rn(bl, __fadd_rn(fabsf(cal), fabsf(car)))),
+                  __fmul_rn(cl, __fadd_rn(fabsf(abl), fabsf(abr))));
+    const float bound = 4e-6f * perm;
+    if (det > bound) return 1;
+    if (-det > bound) return -1;
+  }
   double2 pa = x.d.pos[a], pb = x.d.pos[b], pc = x.d.pos[c], pp = x.d.pos[p];
   return bdpred::incircle(pa.x, pa.y, pb.x, pb.y, pc.x, pc.y, pp.x, pp.y, x.g);
 }
@@ -271,6 +327,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
   x.g.s = c.qshift;
   x.T = c.nt;
   x.np = c.np;
+  x.sig2f = (float)(c.sigma * c.sigma * (1.0 + 1e-5));
   BdCtl *ctl = d.ctl;
   if (ld_status(&ctl->status) != 0) {
     block_exit(ctl);
@@ -279,6 +336,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
   Bar b;
   b.gen = 0;
   b.ph = 0;
+  unsigned long long t_mark = gtimer();   // stage timing (lead thread)
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
   const bool lead = (blockIdx.x == 0 && threadIdx.x == 0);
@@ -347,6 +405,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
             }
           }
           if (mode == 0 && disks) {
+            // FP32 screen: a pair whose FP32 squared distance exceeds
+            // sigma^2 (1 + 1e-5) is farther than sigma (FP32 error ~3e-7)
+            const float4 wu = d.work[u], ww = d.work[w];
+            const float fdx = fdiff(ww.x, ww.z, wu.x, wu.z), fdy = fdiff(ww.y, ww.w, wu.y, wu.w);
+            if (__fadd_rn(__fmul_rn(fdx, fdx), __fmul_rn(fdy, fdy)) > x.sig2f) continue;
             const double2 pu = d.pos[u], pw = d.pos[w];
             // exact pre-test in grid units: |r_w - r_u|^2 <= (sigma/q)^2 (1 + 1e-9)
             const int64_t ix = bdpred::to_int(pw.x, x.g) - bdpred::to_int(pu.x, x.g);
@@ -383,6 +446,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
       if (mx > 0.0) atomicMax(&ctl->st_max_overlap_bits, (unsigned long long)__double_as_longlong(mx));
     }
     if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+    if (lead) stage_tick(ctl, STAGE_P, t_mark);
     first = false;
     const int n_inv = *(volatile int *)cnt(ctl, b.ph - 1, C_INV);
     const int n_rej = *(volatile int *)cnt(ctl, b.ph - 1, C_REJECT);
@@ -436,6 +500,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
           block_add(cnt(ctl, b.ph, C_CAND), ncand);
         }
         if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+        if (lead) stage_tick(ctl, STAGE_R, t_mark);
         first_round = false;
         const int ni = *(volatile int *)cnt(ctl, b.ph - 1, C_INV);
         const int nc = *(volatile int *)cnt(ctl, b.ph - 1, C_CAND);
@@ -462,6 +527,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
           block_add(cnt(ctl, b.ph, C_FLIPS), nf);
         }
         if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+        if (lead) stage_tick(ctl, STAGE_R, t_mark);
         st_rflips += *(volatile int *)cnt(ctl, b.ph - 1, C_FLIPS);
       }
       if (status) break;
@@ -503,6 +569,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
         block_add(cnt(ctl, b.ph, C_FLIPS), nf);
       }
       if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+      if (lead) stage_tick(ctl, STAGE_F, t_mark);
       st_flips += *(volatile int *)cnt(ctl, b.ph - 1, C_FLIPS);
       st_rounds += 1;
       fresh = false;
@@ -564,6 +631,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS) k_triangulation(BdDev d, BdCons
         if (d.tv[t].w) d.tv[t].w = 0;
     }
     if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+    if (lead) stage_tick(ctl, STAGE_A, t_mark);
     fresh = true;
   }
 

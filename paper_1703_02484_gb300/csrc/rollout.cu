@@ -427,6 +427,7 @@ int bd_rollout(bd_handle *h, int32_t nsteps, int32_t ckpt_every, int32_t loss_ki
       }
       if (!kc.log_overflow) {
         add_stats(&acc_stats, kc);
+        bdcapi::add_stage_times(h);
         const int seg_pass = kc.log_npass - used_pass, seg_pairs = kc.log_npairs - used_pairs;
         pass_per_step = std::max<int64_t>(pass_per_step, (seg_pass + k - 1) / k);
         pairs_per_step = std::max<int64_t>(pairs_per_step, (seg_pairs + k - 1) / k);
