@@ -346,6 +346,7 @@ def main():
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     system.force_timing(True, reset=True)
+    system.stage_times(reset=True)
     launches = 0
     stats_tot = {}
     if ws > 1:
@@ -366,6 +367,7 @@ def main():
     ms_steps = [a.elapsed_time(b) for a, b in ev]
     t_ms = float(sum(ms_steps))
     force_ms, force_n = system.force_timing(False)
+    stage_ms = {k: v[0] / args.steps for k, v in system.stage_times(reset=True).items()}
     if ws > 1:
         tt = torch.tensor([t_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -460,6 +462,19 @@ def main():
         if args.workload != "n1e5":
             line["metric"] = "particle-steps/s (%s)" % cfg.name
             line["config"].update(line_cfg)
+        line["config"]["triangulation_stage_ms_per_step"] = stage_ms
+        if not (avg_force_s > 0):
+            # no all-pairs launch in this workload (short-range law)
+            line["roofline"] = None
+        elif cfg.precision == 1:
+            # FP64 sweep (one disk per thread, 12 FP64 flops per ordered pair);
+            # FP64 issues at 1/64 of the FP32 rate on this part
+            p64 = peak_tflops / 64.0
+            a64 = FLOPS_PER_PAIR * pairs / avg_force_s / 1e12
+            line["roofline"] = {"bound": "fp64", "kernel": "k_force_long_f64", "achieved": a64, "peak": p64,
+                                "unit": "TFLOP/s", "frac": a64 / p64, "traffic": None,
+                                "avg_launch_ms": avg_force_s * 1e3,
+                                "peak_note": "FP32 peak / 64 (the part's FP64 issue rate)"}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(cfg, xy, sp, th)
         print(json.dumps(line), flush=True)
