@@ -128,7 +128,10 @@ int bd_default_params(bd_params *p);
 int bd_init(const bd_params *p, const double *xy, const uint8_t *species, const float *theta,
             void *stream, bd_handle **out);
 
-/* Algorithm 1 lines 3-8: advance nsteps time steps.  Each step computes the
+/* Algorithm 1 lines 3-8: advance nsteps time steps.  Each step is one replay
+ * of a CUDA graph holding its launch sequence (captured on first use and
+ * again whenever the handle's kernel tables change; the environment variable
+ * BD_NO_GRAPH, or a failed capture, selects plain launches instead).  Each step computes the
  * forces (Sec. 2.2), applies Eq. (integration) with truncated Philox noise
  * (Sec. 2.4) and self-propulsion (Sec. 7), reflects at the walls, checks
  * r0.r1 < 0 on every triangulation edge and repairs inverted triangles

@@ -612,6 +612,7 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
   }
   c.ncell_total = cell_base;
   h->step = p0.step0;
+  h->graph_off = getenv("BD_NO_GRAPH") != nullptr;
 
   // ---- device buffers ----
   BdDev &d = h->d;
@@ -729,6 +730,11 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
       BD_TRY(cudaMemcpyAsync(d.tile_species, tile_sp.data(), tile_sp.size(), cudaMemcpyHostToDevice, st));
     BD_TRY(cudaMemsetAsync(d.fpart, 0, (size_t)h->fpart_slots * np * sizeof(double2), st));
     BD_TRY(cudaMemsetAsync(d.ctl, 0, sizeof(BdCtl), st));
+    {
+      const long long s0 = h->step;
+      BD_TRY(cudaMemcpyAsync(&d.ctl->step_dev, &s0, sizeof(s0), cudaMemcpyHostToDevice, st));
+      BD_TRY(cudaStreamSynchronize(st));
+    }
     if (c.any_short) {
       // reference positions far away: the first force evaluation builds the lists
       std::vector<double2> far(np, make_double2(1e30, 1e30));
@@ -837,6 +843,73 @@ int fetch_disks(bd_handle *h, std::vector<double2> *pos, std::vector<float> *th,
   return e == cudaSuccess ? BD_OK : cuda_fail(e);
 }
 
+// Capture one step (force, integration, triangulation) as a graph on the
+// handle's private stream.  The integration reads the step index from the
+// device counter, so every replay is the next step.
+cudaError_t capture_step_graph(bd_handle *h) {
+  cudaError_t e = cudaSuccess;
+  if (!h->cap_stream) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+    if (!h->graph_ev[k]) e = cudaEventCreate(&h->graph_ev[k]);
+  if (e != cudaSuccess) return e;
+  if (h->step_graph) {
+    cudaGraphExecDestroy(h->step_graph);
+    h->step_graph = nullptr;
+  }
+  cudaStream_t cs = h->cap_stream;
+  const bool tm = h->timing && h->c.any_long;
+  int launches = 0;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t el = cudaSuccess;
+  if (h->c.any_long) {
+    if (tm) el = cudaEventRecordWithFlags(h->graph_ev[0], cs, cudaEventRecordExternal);
+    if (el == cudaSuccess) el = bd_launch_force_long(h->d, h->c, cs);
+    if (el == cudaSuccess && tm) el = cudaEventRecordWithFlags(h->graph_ev[1], cs, cudaEventRecordExternal);
+    launches += h->c.precision == 0 ? bd_force_launches(h->c.force_variant) : 1;
+  }
+  if (el == cudaSuccess && h->c.any_short) {
+    el = bd_launch_force_short(h->d, h->c, cs);
+    launches += bd_short_launches();
+  }
+  if (el == cudaSuccess) el = bd_launch_integrate(h->d, h->c, -1, -1, cs);
+  if (el == cudaSuccess) el = bd_launch_dt(h->d, h->c, 0, cs, h->dt_grid, h->dt_block);
+  launches += 2;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cs, &g);
+  if (el != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();   // clear a launch error of the failed capture
+    return el != cudaSuccess ? el : e;
+  }
+  e = cudaGraphInstantiate(&h->step_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->step_graph = nullptr;
+    cudaGetLastError();
+    return e;
+  }
+  h->graph_d = h->d;
+  h->graph_c = h->c;
+  h->graph_timed = tm;
+  h->graph_launches = launches;
+  return cudaSuccess;
+}
+
+// the captured graph is usable for the current tables and timing mode
+bool step_graph_ready(bd_handle *h) {
+  if (h->graph_off) return false;
+  const bool tm = h->timing && h->c.any_long;
+  if (h->step_graph && tm == h->graph_timed && memcmp(&h->graph_d, &h->d, sizeof(BdDev)) == 0 &&
+      memcmp(&h->graph_c, &h->c, sizeof(BdConst)) == 0)
+    return true;
+  if (capture_step_graph(h) != cudaSuccess) {
+    h->graph_off = true;   // fall back to plain launches from now on
+    return false;
+  }
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -882,6 +955,10 @@ void bd_free(bd_handle *h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   bdcapi::rollout_release(h);
+  if (h->step_graph) cudaGraphExecDestroy(h->step_graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (int k = 0; k < 2; ++k)
+    if (h->graph_ev[k]) cudaEventDestroy(h->graph_ev[k]);
   for (void *p : h->dev_allocs) cudaFree(p);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
   for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
@@ -925,7 +1002,17 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
       h->ev_pool.push_back(ev);
     }
   }
-  for (int s = 0; s < nsteps; ++s) {
+  // one graph replay per step, unless timing wants a launch per step in a
+  // multi-step call (the graph holds one pair of timing events)
+  const bool use_graph = nsteps > 0 && !(h->timing && long_range && nsteps > 1) && step_graph_ready(h);
+  if (use_graph) {
+    for (int s = 0; s < nsteps; ++s) {
+      e = cudaGraphLaunch(h->step_graph, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+    launches = (int64_t)nsteps * h->graph_launches;
+  }
+  for (int s = 0; s < (use_graph ? 0 : nsteps); ++s) {
     if (long_range) {
       bool tm = h->timing;
       if (tm) cudaEventRecord(h->ev_pool[2 * s], st);
@@ -951,6 +1038,13 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
   h->last_launches = launches;
   int rc = read_ctl(h);
   if (rc) return rc;
+  if (use_graph && h->graph_timed) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->graph_ev[0], h->graph_ev[1]) == cudaSuccess) {
+      h->force_ms += ms;
+      h->force_launches += 1;
+    }
+  }
   for (int s = 0; s < timed; ++s) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, h->ev_pool[2 * s], h->ev_pool[2 * s + 1]) == cudaSuccess) {

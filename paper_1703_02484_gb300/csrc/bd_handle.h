@@ -46,6 +46,16 @@ struct bd_handle {
   int fpart_slots = 0;             // partial-force slots allocated
   std::vector<int> fpart_cap;      // per replica: chunks that fit
   BdRollout *ro = nullptr;         // differentiated rollout state (lazily created)
+  // one step as a CUDA graph, replayed by bd_step (captured on a private
+  // stream; valid while the kernel-argument tables equal the captured ones)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_graph = nullptr;
+  cudaEvent_t graph_ev[2] = {nullptr, nullptr};   // force timing inside the graph
+  BdDev graph_d;
+  BdConst graph_c;
+  bool graph_timed = false;
+  bool graph_off = false;          // capture failed or disabled (BD_NO_GRAPH)
+  int graph_launches = 0;          // kernels in one replay
   double stage_ns[4] = {0, 0, 0, 0};   // triangulation-kernel stage times since the last reset
   int64_t stage_cnt[4] = {0, 0, 0, 0};
 };

@@ -60,6 +60,7 @@ struct BdCtl {
   int log_npairs;                  // logged pairs
   int log_overflow;
   int log_step;                    // rollout step being recorded (-1 = none)
+  long long step_dev;              // index of the next step (advanced by the triangulation kernel)
 };
 
 // counter slots within BdCtl::cnt[phase % 4]

@@ -681,6 +681,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
     ctl->st_barriers += b.gen;
     if (corr_iter > ctl->st_max_corr_iters) ctl->st_max_corr_iters = corr_iter;
     if (!status) ctl->st_steps += 1;
+    if (!status && mode == 0) ctl->step_dev += 1;
   }
   block_exit(ctl);
 }

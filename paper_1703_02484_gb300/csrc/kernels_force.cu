@@ -316,10 +316,12 @@ __global__ void k_force_sum(BdDev d, BdConst c, double2 *out) {
   out[i] = make_double2(fx, fy);
 }
 
+// step < 0: the index of the step is the device counter (graph replays)
 __global__ void k_integrate(BdDev d, BdConst c, long long step, int log_step) {
   if (ctl_failed(d.ctl)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= c.np) return;
+  if (step < 0) step = *(volatile const long long *)&d.ctl->step_dev;
   const int e = d.ext_id[i];
   if (e < 0) return;
   const BdRep &R = d.rep[d.rep_of[i]];

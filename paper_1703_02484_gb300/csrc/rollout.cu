@@ -309,7 +309,10 @@ extern "C" {
 int bd_set_step(bd_handle *h, int64_t step) {
   if (!h || step < 0) return BD_ERR_ARG;
   h->step = step;
-  return BD_OK;
+  const long long v = step;
+  cudaError_t e = cudaMemcpyAsync(&h->d.ctl->step_dev, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? BD_OK : cuda_fail(e);
 }
 
 int bd_set_force_params(bd_handle *h, const double *alpha, double v0) {
@@ -451,6 +454,12 @@ int bd_rollout(bd_handle *h, int32_t nsteps, int32_t ckpt_every, int32_t loss_ki
         e = cudaMemcpyAsync(h->d.tn, r->tn_seg, (size_t)h->nt * sizeof(int4), cudaMemcpyDeviceToDevice, s);
       if (e == cudaSuccess) e = bd_launch_work_copy(h->d, h->c, s);
       if (e == cudaSuccess) e = set_log_cursors(h, used_pass, used_pairs);
+      if (e == cudaSuccess) {
+        // the undone steps had advanced the device step counter
+        const long long s0 = r->step0 + t0;
+        e = cudaMemcpyAsync(&h->d.ctl->step_dev, &s0, sizeof(s0), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      }
       if (e != cudaSuccess) break;
     }
     if (e != cudaSuccess) break;

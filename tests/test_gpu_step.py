@@ -209,3 +209,24 @@ def test_init_rejects_overlap():
     with pytest.raises(bd.BDError) as e:
         bd.System(p, np.array([[5.0, 5.0], [6.0, 5.0]]))
     assert e.value.code == -3
+
+
+@pytest.mark.parametrize("cfgname,n", [("c5", 4096), ("c3", 30000)])
+def test_graph_replay_equals_plain_launches(monkeypatch, cfgname, n):
+    # bd_step replays one captured graph per step; with graphs disabled the
+    # same kernels are launched one by one: identical trajectories
+    cfg = workloads.CONFIGS[cfgname]
+    xy, sp, th = workloads.initial_state(cfg, n=n)
+    out = []
+    for off in (False, True):
+        if off:
+            monkeypatch.setenv("BD_NO_GRAPH", "1")
+        else:
+            monkeypatch.delenv("BD_NO_GRAPH", raising=False)
+        s = bd.System(bd.params_from_config(cfg, n=n), xy, sp, th, stream=stream())
+        s.step(7)
+        s.step(1)
+        out.append(s.state())
+    assert out[0]["step"] == out[1]["step"] == 8
+    assert np.array_equal(out[0]["xy"], out[1]["xy"])
+    assert np.array_equal(out[0]["tri"], out[1]["tri"])
