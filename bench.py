@@ -308,7 +308,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--workload", default="n1e5",
                     help="configuration name (n1e5 is the headline; c1, c2, c3, c5, c4 (batched), "
-                         "c5-grad (differentiated rollout) for tables)")
+                         "c5-grad (differentiated rollout), c3-verlet (overlap correction over the "
+                         "Verlet lists) for tables)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -330,9 +331,12 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    cfg = workloads.CONFIGS[args.workload]
+    verlet_mode = args.workload.endswith("-verlet")
+    cfg = workloads.CONFIGS[args.workload[:-len("-verlet")] if verlet_mode else args.workload]
     xy, sp, th = workloads.initial_state(cfg)
     p = bd.params_from_config(cfg)
+    if verlet_mode:
+        p.overlap_mode = bd.OVERLAP_VERLET   # Algorithm 2 over the Verlet lists, no triangulation
     p.replica = rank
     stream = torch.cuda.current_stream()
     system = bd.System(p, xy, sp, th, stream=stream.cuda_stream)
@@ -460,8 +464,10 @@ def main():
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
         }
         if args.workload != "n1e5":
-            line["metric"] = "particle-steps/s (%s)" % cfg.name
+            line["metric"] = "particle-steps/s (%s)" % args.workload
             line["config"].update(line_cfg)
+            if verlet_mode:
+                line["config"]["overlap_pairs_from"] = "Verlet lists (no triangulation)"
         line["config"]["triangulation_stage_ms_per_step"] = stage_ms
         if not (avg_force_s > 0):
             # no all-pairs launch in this workload (short-range law)

@@ -82,7 +82,15 @@ typedef struct bd_params {
   int32_t literal_noise;   /* 1: noise amplitude sqrt(D dt) as printed in Eq. (integration);
                               0 (default): sqrt(2 D dt) per component */
   int64_t step0;         /* index of the first step (Philox counter), for resumed runs */
+  int32_t overlap_mode;  /* which pairs Algorithm 2 tests (Sec. 4.4):
+                            BD_OVERLAP_DELAUNAY (default): the edges of the Delaunay
+                              triangulation maintained every step (Sec. 4.1, 4.3);
+                            BD_OVERLAP_VERLET: the Verlet lists of the short-range force
+                              (the paper's short-range path, Sec. 5 and Fig. "overlaps"):
+                              no triangulation is kept; short-range law only */
 } bd_params;
+
+enum { BD_OVERLAP_DELAUNAY = 0, BD_OVERLAP_VERLET = 1 };
 
 /* Counters of one bd_step call (the paper's per-step metrics, Sec. 6). */
 typedef struct bd_step_stats {
@@ -181,7 +189,8 @@ int bd_get_replica(bd_handle *h, int32_t r, double *xy, float *theta, int32_t *t
 int bd_get_tuning(bd_handle *h, int32_t *tiles_per_item, int32_t *variant, int32_t *n_items);
 
 /* Copy the current state to host memory ("Ensure P updated to current
- * time", Algorithm 1).  Any pointer may be NULL to skip that output.
+ * time", Algorithm 1).  Any pointer may be NULL to skip that output.  With
+ * BD_OVERLAP_VERLET no triangulation is kept: *n_tri is 0 and tri untouched.
  *   xy       2n doubles, external disk order.
  *   theta    n floats.   species  n bytes.
  *   tri      3*n_tri ints: the current Delaunay triangulation of the disks

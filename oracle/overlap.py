@@ -89,3 +89,46 @@ def correct(xy, L, a, max_iters=10000, tris=None, record=None):
         tris = None
         if it >= max_iters:
             return xy, geometry.delaunay(xy, L), it, total, True
+
+
+def close_pairs(xy, sigma, chunk=512):
+    """Every pair i < j with |r_j - r_i| < sigma, by brute force (chunked)."""
+    xy = np.asarray(xy, dtype=np.float64)
+    n = len(xy)
+    out = []
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        d = xy[None, :, :] - xy[c0:c1, None, :]          # r_j - r_i
+        r = np.sqrt(d[:, :, 0] * d[:, :, 0] + d[:, :, 1] * d[:, :, 1])
+        ii, jj = np.nonzero(r < sigma)
+        ii = ii + c0
+        keep = jj > ii
+        if keep.any():
+            out.append(np.stack([ii[keep], jj[keep]], axis=1))
+    return np.concatenate(out) if out else np.zeros((0, 2), dtype=np.int64)
+
+
+def correct_allpairs(xy, L, a, max_iters=10000, record=None):
+    """Algorithm 2 over every pair of disks (the short-range path of Sec. 5,
+    where the neighbour lists, not a triangulation, supply the pairs): each
+    pass takes every pair closer than sigma, sums the displacements Jacobi
+    style, caps each at sigma/4 and reflects, until no pair is closer than
+    sigma.  Returns (xy, passes that moved disks, overlapping pairs seen,
+    rejected flag)."""
+    sigma = 2.0 * a
+    xy = np.asarray(xy, dtype=np.float64)
+    it = 0
+    total = 0
+    while True:
+        E = close_pairs(xy, sigma)
+        if len(E) == 0:
+            return xy, it, total, False
+        new, pairs, capped, disp = correction_pass(xy, E, sigma, a, L)
+        if record is not None:
+            record.append({"pairs": pairs, "capped": capped, "disp": disp, "xy": xy})
+        total += len(pairs)
+        it += 1
+        xy = new
+        if it >= max_iters:
+            return xy, it, total, True
+

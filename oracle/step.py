@@ -53,8 +53,12 @@ def compute_forces(xy, species, p: Params, threads=1):
 
 
 def step(xy, theta, species, step_index, p: Params, ids=None, tris=None, F=None,
-         threads=1, record=None):
-    """Returns dict(xy, theta, tris, corr_iters, overlap_pairs, rejected, F)."""
+         threads=1, record=None, pairs_from="delaunay"):
+    """Returns dict(xy, theta, tris, corr_iters, overlap_pairs, rejected, F).
+
+    pairs_from="allpairs": the short-range path of Sec. 5, whose neighbour lists
+    supply the pairs of Algorithm 2: every pair closer than sigma is corrected,
+    no triangulation is involved (tris is None, no reversal test)."""
     xy = np.asarray(xy, dtype=np.float64)
     n = len(xy)
     ids = np.arange(n) if ids is None else np.asarray(ids)
@@ -62,6 +66,11 @@ def step(xy, theta, species, step_index, p: Params, ids=None, tris=None, F=None,
         F = compute_forces(xy, species, p, threads)
     new, th = dynamics.em_step(xy, theta, F, ids, step_index, p.seed, p.D, p.Dr, p.v0, p.dt,
                                p.a, p.L, p.replica, p.literal_amp)
+    if pairs_from == "allpairs":
+        out, iters, pairs, rej = overlap.correct_allpairs(new, p.L, p.a, p.max_corr_iters,
+                                                              record=record)
+        return dict(xy=out, theta=th, tris=None, corr_iters=iters, overlap_pairs=pairs,
+                    rejected=rej, F=F, xy_em=new)
     if tris is None:
         tris = geometry.delaunay(xy, p.L)
     E0 = overlap.real_edges(tris, n)

@@ -18,6 +18,7 @@ ERRORS = {
 }
 LAW_NONE, LAW_LONG, LAW_SHORT = 0, 1, 2
 LOSS_MSD = 0
+OVERLAP_DELAUNAY, OVERLAP_VERLET = 0, 1
 
 
 class bd_params(ctypes.Structure):
@@ -32,6 +33,7 @@ class bd_params(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("replica", ctypes.c_int32),
         ("max_corr_iters", ctypes.c_int32), ("max_flip_rounds", ctypes.c_int32),
         ("literal_noise", ctypes.c_int32), ("step0", ctypes.c_int64),
+        ("overlap_mode", ctypes.c_int32),
     ]
 
 

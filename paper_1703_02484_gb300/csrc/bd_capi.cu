@@ -85,6 +85,8 @@ int validate(const bd_params *p) {
     if (!(p->r_cut > 2.0 * p->a) || !(p->skin > 0) || !(p->eps >= 0) || !(p->kappa >= 0)) return BD_ERR_ARG;
     if (p->precision != 0) return BD_ERR_UNSUPPORTED;
   }
+  if (p->overlap_mode < BD_OVERLAP_DELAUNAY || p->overlap_mode > BD_OVERLAP_VERLET) return BD_ERR_ARG;
+  if (p->overlap_mode == BD_OVERLAP_VERLET && p->law != BD_LAW_SHORT) return BD_ERR_UNSUPPORTED;
   return BD_OK;
 }
 
@@ -331,8 +333,8 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     if (rc) return rc;
     if (s.p.a != specs[0].p.a || s.p.precision != specs[0].p.precision ||
         s.p.max_corr_iters != specs[0].p.max_corr_iters ||
-        s.p.max_flip_rounds != specs[0].p.max_flip_rounds)
-      return BD_ERR_ARG;   // one disk radius, precision and loop caps per handle
+        s.p.max_flip_rounds != specs[0].p.max_flip_rounds || s.p.overlap_mode != specs[0].p.overlap_mode)
+      return BD_ERR_ARG;   // one disk radius, precision, loop caps and overlap mode per handle
   }
   bd_handle *h = new (std::nothrow) bd_handle();
   if (!h) return BD_ERR_NOMEM;
@@ -568,6 +570,14 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     c.sig2q_lo = lo;
   }
   c.max_corr_iters = p0.max_corr_iters;
+  c.overlap_verlet = p0.overlap_mode == BD_OVERLAP_VERLET ? 1 : 0;
+  {
+    // the lists hold every pair within r_cut + skin of the build positions, so
+    // every pair closer than sigma while no disk has moved (r_cut + skin - sigma)/2
+    double reach = 1e300;
+    for (const Spec &sp : specs) reach = std::min(reach, 0.5 * (sp.p.r_cut + sp.p.skin - 2.0 * sp.p.a));
+    c.vl_reach2 = c.overlap_verlet ? reach * reach * (1.0 - 1e-9) : 0.0;
+  }
   c.max_flip_rounds = p0.max_flip_rounds;
   c.force_variant = 1;
   h->h_rep.resize(R);
@@ -676,6 +686,10 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
       BD_TRY(dalloc(h, &d.cell_of, (size_t)np));
       BD_TRY(dalloc(h, &d.scan_sums, (nc2 + 511) / 512 + 1));
     }
+    if (c.overlap_verlet) {
+      BD_TRY(dalloc(h, &d.vc_hit, (size_t)np));
+      BD_TRY(cudaMemsetAsync(d.vc_hit, 0, (size_t)np, h->stream));
+    }
 
     cudaStream_t st = h->stream;
     std::vector<float> th_i(np, 0.f);
@@ -765,7 +779,8 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
         BD_TRY(autotune(h));
       }
     }
-    if (bd_dt_grid_for(std::max(nt, np), &h->dt_grid, &h->dt_block) != 0) {
+    if (bd_dt_grid_for(std::max(nt, np), &h->dt_grid, &h->dt_block) != 0 ||
+        (c.overlap_verlet && bd_vcorr_grid_for(np, &h->vc_grid, &h->vc_block) != 0)) {
       bd_free(h);
       return BD_ERR_CUDA;
     }
@@ -843,6 +858,13 @@ int fetch_disks(bd_handle *h, std::vector<double2> *pos, std::vector<float> *th,
   return e == cudaSuccess ? BD_OK : cuda_fail(e);
 }
 
+// the per-step correction stage: triangulation maintenance + Algorithm 2 over
+// its edges, or Algorithm 2 over the Verlet lists
+cudaError_t launch_correction(bd_handle *h, cudaStream_t s) {
+  if (h->c.overlap_verlet) return bd_launch_overlap_verlet(h->d, h->c, s, h->vc_grid, h->vc_block);
+  return bd_launch_dt(h->d, h->c, 0, s, h->dt_grid, h->dt_block);
+}
+
 // Capture one step (force, integration, triangulation) as a graph on the
 // handle's private stream.  The integration reads the step index from the
 // device counter, so every replay is the next step.
@@ -873,7 +895,7 @@ cudaError_t capture_step_graph(bd_handle *h) {
     launches += bd_short_launches();
   }
   if (el == cudaSuccess) el = bd_launch_integrate(h->d, h->c, -1, -1, cs);
-  if (el == cudaSuccess) el = bd_launch_dt(h->d, h->c, 0, cs, h->dt_grid, h->dt_block);
+  if (el == cudaSuccess) el = launch_correction(h, cs);
   launches += 2;
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(cs, &g);
@@ -1031,7 +1053,7 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
     }
     e = bd_launch_integrate(h->d, h->c, h->step + s, -1, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    e = bd_launch_dt(h->d, h->c, 0, st, h->dt_grid, h->dt_block);
+    e = launch_correction(h, st);
     if (e != cudaSuccess) return cuda_fail(e);
     launches += 2;
   }
@@ -1097,7 +1119,7 @@ int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32
     if (theta) theta[i] = t[k];
     if (species) species[i] = s[k];
   }
-  if (tri) {
+  if (tri && !h->c.overlap_verlet) {
     std::vector<int4> tv(h->nt);
     cudaError_t e = cudaMemcpyAsync(tv.data(), h->d.tv, h->nt * sizeof(int4), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1109,7 +1131,7 @@ int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32
       tri[3 * k + 2] = ext(tv[k].z);
     }
   }
-  if (n_tri) *n_tri = h->nt;
+  if (n_tri) *n_tri = h->c.overlap_verlet ? 0 : h->nt;
   if (step) *step = h->step;
   return BD_OK;
 }
@@ -1120,7 +1142,8 @@ int bd_get_replica(bd_handle *h, int32_t r, double *xy, float *theta, int32_t *t
   const RepHost &RH = h->reps[r];
   if (n) *n = RH.n;
   if (L) *L = RH.L;
-  if (n_tri) *n_tri = RH.nt;
+  if (n_tri) *n_tri = h->c.overlap_verlet ? 0 : RH.nt;
+  if (h->c.overlap_verlet) tri = nullptr;
   if (!xy && !theta && !tri) return BD_OK;
   std::vector<double2> pos;
   std::vector<float> t;
@@ -1185,7 +1208,7 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
   if (e == cudaSuccess) e = cudaMemsetAsync(d.moved, 1, (size_t)np, st);
   if (e == cudaSuccess) e = bd_launch_work_copy(d, c, st);
   if (e == cudaSuccess) e = reset_stats(h);
-  if (e == cudaSuccess) e = bd_launch_dt(d, c, 1, st, h->dt_grid, h->dt_block);
+  if (e == cudaSuccess && !c.overlap_verlet) e = bd_launch_dt(d, c, 1, st, h->dt_grid, h->dt_block);
   if (e != cudaSuccess) return cuda_fail(e);
   int rc = read_ctl(h);   // synchronises the stream (the staged theta stays alive until here)
   if (rc) return rc;

@@ -33,6 +33,7 @@ struct bd_handle {
   std::vector<int> int_of_ext;    // concatenated external index -> internal slot
   std::vector<double> host_pos;   // (np + ng) * 2 mirror used for uploads
   int dt_grid = 0, dt_block = 0;
+  int vc_grid = 0, vc_block = 0;   // Verlet-list overlap correction launch
   int64_t step = 0;
   double2 *d_fsum = nullptr;
   BdCtl *h_ctl = nullptr;          // pinned

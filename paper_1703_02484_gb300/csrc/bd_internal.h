@@ -115,6 +115,7 @@ struct BdDev {
   int *vl_idx, *vl_cnt;
   double2 *vl_ref;
   int *cell_count, *cell_start, *cell_cursor, *cell_idx, *cell_of, *scan_sums;
+  uint8_t *vc_hit;         // Verlet-list overlap correction: the disk overlapped in the last pass
   // rollout log for the adjoint (null when not recording)
   uint8_t *log_refl;       // [step][np] wall-reflection flags of the Euler-Maruyama move
   uint8_t *log_pflags;     // [pass][np] bit 16: capped; bits 1,2,4,8: reflections of the pass
@@ -139,6 +140,9 @@ struct BdConst {
   int max_corr_iters, max_flip_rounds;
   int force_variant;       // 0: scalar FP32 sweep, 1: packed f32x2 sweep, 2, 3: symmetric packed sweeps
   int n_sitems;            // symmetric sweep work items
+  int overlap_verlet;      // 1: Algorithm 2 over the Verlet lists, no triangulation kept
+  double vl_reach2;        // squared displacement since the list build below which the lists
+                           // still hold every pair closer than sigma
   int log_pairs_cap, log_pass_cap;   // rollout log capacities
 };
 
@@ -157,4 +161,6 @@ cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t
 int bd_short_launches();
 cudaError_t bd_launch_force_sum(const BdDev &d, const BdConst &c, double2 *out, cudaStream_t s);
 cudaError_t bd_launch_force_sym(const BdDev &d, const BdConst &c, int variant, cudaStream_t s);
+cudaError_t bd_launch_overlap_verlet(const BdDev &d, const BdConst &c, cudaStream_t s, int grid, int block);
+int bd_vcorr_grid_for(int work_items, int *grid, int *block);
 int bd_force_launches(int variant);   // kernel launches of one long-range force evaluation

@@ -40,81 +40,14 @@
 
 #include "bd_internal.h"
 #include "em.cuh"
+#include "gridsync.cuh"
 #include "predicates.cuh"
-
-#ifndef BD_BARRIER_TIMEOUT_NS
-#define BD_BARRIER_TIMEOUT_NS 2000000000ull
-#endif
 
 #define BD_DT_THREADS 256
 
+using namespace bdgs;
+
 namespace {
-
-struct Bar {
-  unsigned gen;
-  int ph;
-};
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ int ld_status(const int *p) {
-  return *(volatile const int *)p;
-}
-
-// bounded grid barrier; returns false if the grid must stop
-__device__ bool grid_sync(BdCtl *ctl, Bar &b) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    if (ld_status(&ctl->status) == BD_ERR_DEVICE_TIMEOUT) {
-      ok = 0;
-    } else {
-      unsigned target = b.gen + 1;
-      __threadfence();
-      unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-      if (arrived == gridDim.x - 1) {
-        atomicExch(&ctl->bar_count, 0u);
-        __threadfence();
-        atomicExch(&ctl->bar_gen, target);
-      } else {
-        // spin hot for a while (barriers are short), then back off; give up
-        // after BD_BARRIER_TIMEOUT_NS
-        unsigned long long t0 = 0;
-        unsigned it = 0;
-        while (ld_acquire(&ctl->bar_gen) != target) {
-          ++it;
-          if (it < 4096u) continue;
-          if (t0 == 0) t0 = gtimer();
-          if ((it & 63u) == 0 && gtimer() - t0 > BD_BARRIER_TIMEOUT_NS) {
-            atomicExch(&ctl->status, BD_ERR_DEVICE_TIMEOUT);
-            ok = 0;
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
-      __threadfence();
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  b.gen++;
-  b.ph++;
-  return s_ok != 0;
-}
-
-__device__ __forceinline__ int *cnt(BdCtl *ctl, int ph, int slot) { return &ctl->cnt[ph & 3][slot]; }
 
 enum { STAGE_P = 0, STAGE_R = 1, STAGE_F = 2, STAGE_A = 3 };
 
@@ -124,41 +57,6 @@ __device__ __forceinline__ void stage_tick(BdCtl *ctl, int stage, unsigned long 
   ctl->st_stage_ns[stage] += now - mark;
   ctl->st_stage_cnt[stage] += 1;
   mark = now;
-}
-
-// every block calls this once on its way out; the last one resets the barrier
-// words and phase counters so the next launch starts clean without a memset
-__device__ void block_exit(BdCtl *ctl) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned k = atomicAdd(&ctl->exit_count, 1u);
-    if (k == gridDim.x - 1) {
-      ctl->bar_count = 0;
-      ctl->bar_gen = 0;
-      for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 8; ++b) ctl->cnt[a][b] = 0;
-      __threadfence();
-      ctl->exit_count = 0;
-    }
-  }
-}
-
-// reset the counters two phases ahead (see the rotation argument in BdCtl)
-__device__ __forceinline__ void phase_begin(BdCtl *ctl, const Bar &b) {
-  if (blockIdx.x == 0 && threadIdx.x < 8) ctl->cnt[(b.ph + 2) & 3][threadIdx.x] = 0;
-}
-
-// block-aggregated atomic add
-__device__ __forceinline__ void block_add(int *dst, int v) {
-  __shared__ int s_acc;
-  if (threadIdx.x == 0) s_acc = 0;
-  __syncthreads();
-  // warp reduce
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_acc, v);
-  __syncthreads();
-  if (threadIdx.x == 0 && s_acc) atomicAdd(dst, s_acc);
 }
 
 __device__ __forceinline__ int vk(const int4 &v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }

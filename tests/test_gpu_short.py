@@ -107,3 +107,67 @@ def test_full_size_c3_forces_sampled_and_steps():
     out = s.state()
     assert len(cKDTree(out["xy"]).query_pairs(2.0 * (1 - 1e-12))) == 0
     assert np.array_equal(geometry.edges(out["tri"]), geometry.edges(geometry.delaunay(out["xy"], L)))
+
+
+# ---- Algorithm 2 over the Verlet lists (the paper's short-range path) ----
+
+def verlet_system(n, xy=None, seed=None):
+    L = workloads.box_side(n, CFG.rho)
+    if xy is None:
+        xy, sp, th = workloads.initial_state(CFG, n=n)
+    else:
+        _, sp, th = workloads.initial_state(CFG, n=n)
+    p = bd.params_from_config(CFG, n=n)
+    p.overlap_mode = bd.OVERLAP_VERLET
+    return bd.System(p, xy, sp, th, stream=stream()), L, xy, sp, th
+
+
+@pytest.mark.parametrize("n,seed", [(3000, 7), (12000, 8)])
+def test_verlet_correction_one_step_parity(n, seed):
+    L = workloads.box_side(n, CFG.rho)
+    xy = workloads.near_contact_state(n, L, 1.0, seed=seed, rho=CFG.rho)
+    s, L, _, sp, th = verlet_system(n, xy=xy)
+    st = s.step(1)
+    out = s.state()
+    assert out["n_tri"] == 0
+    op = ostep.Params(L=L, a=1.0, law=CFG.law, eps=CFG.eps, kappa=CFG.kappa, r_cut=CFG.r_cut,
+                      D=CFG.D, Dr=CFG.Dr, v0=CFG.v0, dt=CFG.dt, seed=CFG.seed)
+    ref = ostep.step(xy, th, sp, 0, op, pairs_from="allpairs")
+    assert ref["corr_iters"] >= 1 and not ref["rejected"]
+    assert st["corr_iters"] == ref["corr_iters"]
+    assert st["overlap_pairs"] == ref["overlap_pairs"]
+    assert np.max(np.abs(out["xy"] - ref["xy"])) <= 1e-5
+    assert len(cKDTree(out["xy"]).query_pairs(2.0 * (1 - 1e-12))) == 0
+
+
+def test_verlet_correction_trajectory_state_parity():
+    # a state reached on the GPU fed back as a new start: one more step on both sides
+    n = 5000
+    s, L, xy, sp, th = verlet_system(n)
+    s.step(15)
+    mid = s.state(want_tri=False)
+    op = ostep.Params(L=L, a=1.0, law=CFG.law, eps=CFG.eps, kappa=CFG.kappa, r_cut=CFG.r_cut,
+                      D=CFG.D, Dr=CFG.Dr, v0=CFG.v0, dt=CFG.dt, seed=CFG.seed)
+    ref = ostep.step(mid["xy"], mid["theta"], mid["species"], mid["step"], op, pairs_from="allpairs")
+    s.step(1)
+    out = s.state(want_tri=False)
+    assert np.max(np.abs(out["xy"] - ref["xy"])) <= 1e-5
+
+
+def test_verlet_correction_full_size_steps():
+    s, L, xy, sp, th = verlet_system(CFG.n)
+    st = s.step(30)
+    assert st["steps_done"] == 30 and st["rejected"] == 0
+    out = s.state(want_tri=False)
+    assert len(cKDTree(out["xy"]).query_pairs(2.0 * (1 - 1e-12))) == 0
+    assert np.all(out["xy"] >= 1.0) and np.all(out["xy"] <= L - 1.0)
+
+
+def test_verlet_mode_requires_short_range():
+    cfg = workloads.CONFIGS["c2"]
+    p = bd.params_from_config(cfg, n=500)
+    p.overlap_mode = bd.OVERLAP_VERLET
+    xy, sp, th = workloads.initial_state(cfg, n=500)
+    with pytest.raises(bd.BDError) as e:
+        bd.System(p, xy, sp, th, stream=stream())
+    assert e.value.code == -10

@@ -59,3 +59,36 @@ def test_full_step_leaves_no_overlap_and_a_delaunay_triangulation():
     P = geometry.with_ghosts(r["xy"], L)
     assert geometry.non_delaunay_edges(P, r["tris"]) == []
     assert np.all(r["xy"] >= 1.0) and np.all(r["xy"] <= L - 1.0)
+
+
+def test_close_pairs_is_brute_force():
+    rng = np.random.default_rng(11)
+    xy = rng.uniform(0, 12, (300, 2))
+    E = overlap.close_pairs(xy, 2.0)
+    ref = {(i, j) for i in range(300) for j in range(i + 1, 300)
+           if (xy[j, 0] - xy[i, 0]) ** 2 + (xy[j, 1] - xy[i, 1]) ** 2 < 4.0}
+    assert {tuple(e) for e in E.tolist()} == ref
+
+
+def test_allpairs_two_disk_bounce():
+    # one overlapping pair: each disk moves by the full depth (final separation 2 sigma - r)
+    xy = np.array([[10.0, 10.0], [11.5, 10.0]])
+    out, it, tot, rej = overlap.correct_allpairs(xy, 40.0, 1.0)
+    assert not rej and it == 1 and tot == 1
+    assert np.allclose(out, [[9.5, 10.0], [12.0, 10.0]], atol=1e-15)
+
+
+def test_allpairs_equals_delaunay_correction_when_overlaps_are_edges():
+    # mild overlaps: every overlapping pair is a Delaunay edge (Gabriel), so
+    # both neighbour sources give the same passes and the same result
+    from paper_1703_02484_gb300 import workloads
+    L = workloads.box_side(400, 0.3)
+    xy = workloads.near_contact_state(400, L, 1.0, seed=5)
+    rng = np.random.default_rng(6)
+    xy = np.clip(xy + rng.normal(scale=0.01, size=xy.shape), 1.0, L - 1.0)
+    a, it_a, tot_a, rej_a = overlap.correct_allpairs(xy, L, 1.0)
+    b, _, it_b, tot_b, rej_b = overlap.correct(xy, L, 1.0)
+    assert not rej_a and not rej_b and it_a >= 1
+    assert it_a == it_b and tot_a == tot_b
+    assert np.max(np.abs(a - b)) <= 1e-12
+    assert len(overlap.close_pairs(a, 2.0 * (1 - 1e-12))) == 0
