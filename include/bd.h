@@ -88,6 +88,17 @@ typedef struct bd_params {
                             BD_OVERLAP_VERLET: the Verlet lists of the short-range force
                               (the paper's short-range path, Sec. 5 and Fig. "overlaps"):
                               no triangulation is kept; short-range law only */
+  int32_t max_dt_halvings; /* Sec. 4.3: a move rejected because a pair passed through each
+                              other (or an inverted triangle could not be repaired, or a disk
+                              outran its Verlet list) is "repeated with a lower dt".  0
+                              (default): the step is rejected.  H in 1..20: the rejected move
+                              is replaced by two moves of half its length, each with forces at
+                              its own start and fresh noise (Philox counter word 3 =
+                              256 * piece, pieces numbered as a binary heap from the whole
+                              step, piece 1, whose noise is unchanged); a rejected half is
+                              halved again, down to dt / 2^H.  Single-system handles only
+                              (bd_batch_init returns BD_ERR_UNSUPPORTED for H > 0); recorded
+                              rollouts (bd_rollout) do not halve. */
 } bd_params;
 
 enum { BD_OVERLAP_DELAUNAY = 0, BD_OVERLAP_VERLET = 1 };
@@ -112,6 +123,8 @@ typedef struct bd_step_stats {
   int32_t fail_item;        /* internal id of an offending triangle or edge (diagnostic) */
   int32_t fail_count;       /* inverted triangles or reversed edges at the failure */
   int64_t barriers;         /* grid-wide barriers of the device-side loops (all steps) */
+  int64_t substeps;         /* moves shorter than dt that completed (max_dt_halvings > 0) */
+  int64_t halvings;         /* rejected moves that were replaced by their two halves */
 } bd_step_stats;
 
 typedef struct bd_handle bd_handle;
@@ -145,7 +158,9 @@ int bd_init(const bd_params *p, const double *xy, const uint8_t *species, const 
  * r0.r1 < 0 on every triangulation edge and repairs inverted triangles
  * (Sec. 4.3), restores the Delaunay property by edge flips, and iterates
  * Algorithm 2 (Sec. 4.4) until no triangulation edge is shorter than sigma,
- * re-checking and flipping after every correction pass.
+ * re-checking and flipping after every correction pass.  With
+ * bd_params.max_dt_halvings > 0 a rejected step is redone as halves (plain
+ * launches, one synchronisation per piece) before the call gives up on it.
  *   stats  optional (NULL allowed): counters of this call.
  * Returns BD_OK, or BD_ERR_STEP_REJECTED / BD_ERR_OVERLAP_NOT_CONVERGED /
  * BD_ERR_FLIP_NOT_CONVERGED (the failing step is undone and the call stops;
@@ -356,6 +371,11 @@ int bd_rollout_positions(bd_handle *h, int32_t which, double *xy);
 
 /* Size of the recorded log: correction passes and overlapping pairs. */
 int bd_rollout_log_size(bd_handle *h, int32_t *n_pass, int32_t *n_pairs);
+
+/* sizeof(bd_params) and sizeof(bd_step_stats) as this library was built,
+ * for bindings that lay the structures out themselves.  Either pointer may be
+ * NULL.  Always BD_OK. */
+int bd_struct_sizes(int32_t *params_bytes, int32_t *stats_bytes);
 
 /* Release the handle and its device memory (NULL is ignored). */
 void bd_free(bd_handle *h);

@@ -18,7 +18,7 @@ import math
 
 import numpy as np
 
-from . import noise
+from . import noise, philox
 
 
 def noise_amplitude(D, dt, literal_amp=False):
@@ -33,9 +33,12 @@ def reflect(xy, a, L):
     return xy
 
 
-def em_move(xy, theta, F, ids, step, seed, D, Dr, v0, dt, replica=0, literal_amp=False):
-    """The Euler-Maruyama + ABP move before the walls.  Returns (xy', theta')."""
-    xi_x, xi_y, n_th, _ = noise.normals(ids, step, seed, replica)
+def em_move(xy, theta, F, ids, step, seed, D, Dr, v0, dt, replica=0, literal_amp=False,
+            tag=philox.TAG_NOISE):
+    """The Euler-Maruyama + ABP move before the walls.  Returns (xy', theta').
+    dt is the length of this move (a piece of a redone step uses its own, with
+    the noise of counter word `tag`)."""
+    xi_x, xi_y, n_th, _ = noise.normals(ids, step, seed, replica, tag)
     amp = noise_amplitude(D, dt, literal_amp)
     th = np.asarray(theta, dtype=np.float64)
     dx = dt * (F[:, 0] + v0 * np.cos(th)) + amp * xi_x
@@ -45,7 +48,8 @@ def em_move(xy, theta, F, ids, step, seed, D, Dr, v0, dt, replica=0, literal_amp
     return new, th_new
 
 
-def em_step(xy, theta, F, ids, step, seed, D, Dr, v0, dt, a, L, replica=0, literal_amp=False):
+def em_step(xy, theta, F, ids, step, seed, D, Dr, v0, dt, a, L, replica=0, literal_amp=False,
+            tag=philox.TAG_NOISE):
     """One Euler-Maruyama + ABP step with reflection.  Returns (xy', theta')."""
-    new, th_new = em_move(xy, theta, F, ids, step, seed, D, Dr, v0, dt, replica, literal_amp)
+    new, th_new = em_move(xy, theta, F, ids, step, seed, D, Dr, v0, dt, replica, literal_amp, tag)
     return reflect(new, a, L), th_new

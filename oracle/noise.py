@@ -30,9 +30,10 @@ def clamp(z):
     return np.clip(z, -CLAMP, CLAMP)
 
 
-def normals(ids, step, seed, replica=0):
-    """(xi_x, xi_y, n_theta, spare) for the given particle ids at `step`."""
-    u = uniforms(philox.draw(ids, step, seed, replica))
+def normals(ids, step, seed, replica=0, tag=philox.TAG_NOISE):
+    """(xi_x, xi_y, n_theta, spare) for the given particle ids at `step`
+    (tag: the fourth counter word, see oracle.philox.substep_tag)."""
+    u = uniforms(philox.draw(ids, step, seed, replica, tag))
     z0, z1 = box_muller(u[0], u[1])
     z2, z3 = box_muller(u[2], u[3])
     return clamp(z0), clamp(z1), clamp(z2), clamp(z3)

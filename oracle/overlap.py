@@ -25,6 +25,11 @@ import numpy as np
 from . import dynamics, geometry
 
 
+# why a step was rejected (0 = it was not): a pair passed through each other
+# (Sec. 4.3), or Algorithm 2 ran out of passes
+REJ_NONE, REJ_REVERSAL, REJ_NOT_CONVERGED = 0, 1, 2
+
+
 def real_edges(tris, n):
     e = geometry.edges(tris)
     return e[(e[:, 0] < n) & (e[:, 1] < n)]
@@ -66,7 +71,7 @@ def reversed_edges(xy0, xy1, E):
 def correct(xy, L, a, max_iters=10000, tris=None, record=None):
     """Iterate Algorithm 2 until no Delaunay edge is shorter than sigma = 2a.
     Returns (xy, tris of final positions, iterations that moved disks,
-    total overlapping edges seen, rejected flag)."""
+    total overlapping edges seen, rejection reason REJ_*: false when none)."""
     sigma = 2.0 * a
     n = len(xy)
     xy = np.asarray(xy, dtype=np.float64)
@@ -78,17 +83,17 @@ def correct(xy, L, a, max_iters=10000, tris=None, record=None):
         E = real_edges(tris, n)
         new, pairs, capped, disp = correction_pass(xy, E, sigma, a, L)
         if len(pairs) == 0:
-            return xy, tris, it, total, False
+            return xy, tris, it, total, REJ_NONE
         if record is not None:
             record.append({"pairs": pairs, "capped": capped, "disp": disp, "xy": xy})
         if len(reversed_edges(xy, new, E)):
-            return xy, tris, it, total, True
+            return xy, tris, it, total, REJ_REVERSAL
         total += len(pairs)
         it += 1
         xy = new
         tris = None
         if it >= max_iters:
-            return xy, geometry.delaunay(xy, L), it, total, True
+            return xy, geometry.delaunay(xy, L), it, total, REJ_NOT_CONVERGED
 
 
 def close_pairs(xy, sigma, chunk=512):
@@ -122,7 +127,7 @@ def correct_allpairs(xy, L, a, max_iters=10000, record=None):
     while True:
         E = close_pairs(xy, sigma)
         if len(E) == 0:
-            return xy, it, total, False
+            return xy, it, total, REJ_NONE
         new, pairs, capped, disp = correction_pass(xy, E, sigma, a, L)
         if record is not None:
             record.append({"pairs": pairs, "capped": capped, "disp": disp, "xy": xy})
@@ -130,5 +135,5 @@ def correct_allpairs(xy, L, a, max_iters=10000, record=None):
         it += 1
         xy = new
         if it >= max_iters:
-            return xy, it, total, True
+            return xy, it, total, REJ_NOT_CONVERGED
 

@@ -25,6 +25,15 @@ MASK = np.uint64(0xFFFFFFFF)
 TAG_NOISE = 0
 
 
+def substep_tag(node: int) -> int:
+    """Counter word 3 of the noise of one piece of a step that was redone with
+    a lower dt (Sec. 4.3).  Pieces are numbered as a binary heap: node 1 is
+    the whole step, nodes 2k and 2k+1 the two halves of node k.  The whole
+    step keeps TAG_NOISE; node k >= 2 uses TAG_NOISE + 256 k."""
+    node = int(node)
+    return TAG_NOISE if node <= 1 else (TAG_NOISE + 256 * node) & 0xFFFFFFFF
+
+
 def philox4x32_10(c0, c1, c2, c3, k0, k1):
     """Vectorised Philox4x32-10.  Inputs are uint32-valued arrays or scalars
     (broadcast together); returns four uint32 arrays."""

@@ -13,12 +13,21 @@ Steps 3-4 need the Delaunay triangulation, which the oracle builds from
 scratch; inverted-triangle repair and edge flips (Sec. 4.3) are how the GPU
 *maintains* that triangulation, so they have no counterpart here beyond the
 final triangulation itself.
+
+Rejected moves (Sec. 4.3): when a pair passes through each other "the last
+positions are discarded and integration is repeated with a lower dt".  With
+Params.max_halvings = H > 0 a rejected move is replaced by two moves of half
+its length, each with forces at its own start and fresh noise (counter word
+oracle.philox.substep_tag(node), pieces numbered as a binary heap from the
+whole step, node 1); a half that is rejected in turn is halved again, down to
+dt / 2^H.  If a piece of length dt / 2^H is rejected the whole step is
+rejected and the state is left as it was.
 """
 from dataclasses import dataclass
 
 import numpy as np
 
-from . import dynamics, forces, geometry, overlap
+from . import dynamics, forces, geometry, overlap, philox
 
 LAW_NONE, LAW_LONG, LAW_SHORT = 0, 1, 2
 
@@ -40,6 +49,7 @@ class Params:
     replica: int = 0
     max_corr_iters: int = 10000
     literal_amp: bool = False
+    max_halvings: int = 0
 
 
 def compute_forces(xy, species, p: Params, threads=1):
@@ -52,20 +62,17 @@ def compute_forces(xy, species, p: Params, threads=1):
     return np.zeros_like(np.asarray(xy, dtype=np.float64))
 
 
-def step(xy, theta, species, step_index, p: Params, ids=None, tris=None, F=None,
-         threads=1, record=None, pairs_from="delaunay"):
-    """Returns dict(xy, theta, tris, corr_iters, overlap_pairs, rejected, F).
-
-    pairs_from="allpairs": the short-range path of Sec. 5, whose neighbour lists
-    supply the pairs of Algorithm 2: every pair closer than sigma is corrected,
-    no triangulation is involved (tris is None, no reversal test)."""
-    xy = np.asarray(xy, dtype=np.float64)
+def _piece(xy, theta, species, step_index, p: Params, ids, tris, F, threads, record, pairs_from,
+           node):
+    """One move of length dt / 2^level (level = depth of `node` in the heap
+    numbering) from xy with the noise of that node, then the validity test and
+    the overlap correction."""
     n = len(xy)
-    ids = np.arange(n) if ids is None else np.asarray(ids)
     if F is None:
         F = compute_forces(xy, species, p, threads)
-    new, th = dynamics.em_step(xy, theta, F, ids, step_index, p.seed, p.D, p.Dr, p.v0, p.dt,
-                               p.a, p.L, p.replica, p.literal_amp)
+    dt = p.dt / float(2 ** (int(node).bit_length() - 1))
+    new, th = dynamics.em_step(xy, theta, F, ids, step_index, p.seed, p.D, p.Dr, p.v0, dt,
+                               p.a, p.L, p.replica, p.literal_amp, philox.substep_tag(node))
     if pairs_from == "allpairs":
         out, iters, pairs, rej = overlap.correct_allpairs(new, p.L, p.a, p.max_corr_iters,
                                                               record=record)
@@ -76,8 +83,54 @@ def step(xy, theta, species, step_index, p: Params, ids=None, tris=None, F=None,
     E0 = overlap.real_edges(tris, n)
     if len(overlap.reversed_edges(xy, new, E0)):
         return dict(xy=xy, theta=np.asarray(theta, np.float64), tris=tris, corr_iters=0,
-                    overlap_pairs=0, rejected=True, F=F)
+                    overlap_pairs=0, rejected=overlap.REJ_REVERSAL, F=F)
     out, tris1, iters, pairs, rej = overlap.correct(new, p.L, p.a, p.max_corr_iters,
                                                     record=record)
     return dict(xy=out, theta=th, tris=tris1, corr_iters=iters, overlap_pairs=pairs,
                 rejected=rej, F=F, xy_em=new)
+
+
+def step(xy, theta, species, step_index, p: Params, ids=None, tris=None, F=None,
+         threads=1, record=None, pairs_from="delaunay"):
+    """Returns dict(xy, theta, tris, corr_iters, overlap_pairs, rejected, F,
+    substeps, halvings).
+
+    pairs_from="allpairs": the short-range path of Sec. 5, whose neighbour lists
+    supply the pairs of Algorithm 2: every pair closer than sigma is corrected,
+    no triangulation is involved (tris is None, no reversal test).
+
+    substeps: pieces shorter than dt that completed (0 when the whole step was
+    accepted); halvings: rejected pieces that were replaced by their halves."""
+    xy = np.asarray(xy, dtype=np.float64)
+    ids = np.arange(len(xy)) if ids is None else np.asarray(ids)
+    r = _piece(xy, theta, species, step_index, p, ids, tris, F, threads, record, pairs_from, 1)
+    r["substeps"], r["halvings"] = 0, 0
+    if r["rejected"] != overlap.REJ_REVERSAL or p.max_halvings <= 0:
+        return r
+    # Sec. 4.3: discard the move, integrate again with half the time step
+    count = {"substeps": 0, "halvings": 0, "corr_iters": 0, "overlap_pairs": 0}
+
+    def halves(x, th, tr, node, depth_left):
+        count["halvings"] += 1
+        for child in (2 * node, 2 * node + 1):
+            q = _piece(x, th, species, step_index, p, ids, tr, None, threads, None, pairs_from, child)
+            if q["rejected"] == overlap.REJ_REVERSAL and depth_left > 1:
+                ok, x, th, tr = halves(x, th, tr, child, depth_left - 1)
+                if not ok:
+                    return False, x, th, tr
+                continue
+            if q["rejected"]:
+                return False, x, th, tr
+            count["substeps"] += 1
+            count["corr_iters"] += q["corr_iters"]
+            count["overlap_pairs"] += q["overlap_pairs"]
+            x, th, tr = q["xy"], q["theta"], q["tris"]
+        return True, x, th, tr
+
+    ok, x, th, tr = halves(xy, np.asarray(theta, np.float64), tris, 1, p.max_halvings)
+    if not ok:
+        r.update(count)
+        return r
+    return dict(xy=x, theta=th, tris=tr, corr_iters=count["corr_iters"],
+                overlap_pairs=count["overlap_pairs"], rejected=overlap.REJ_NONE, F=r["F"],
+                substeps=count["substeps"], halvings=count["halvings"])

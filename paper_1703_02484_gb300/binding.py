@@ -33,7 +33,7 @@ class bd_params(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("replica", ctypes.c_int32),
         ("max_corr_iters", ctypes.c_int32), ("max_flip_rounds", ctypes.c_int32),
         ("literal_noise", ctypes.c_int32), ("step0", ctypes.c_int64),
-        ("overlap_mode", ctypes.c_int32),
+        ("overlap_mode", ctypes.c_int32), ("max_dt_halvings", ctypes.c_int32),
     ]
 
 
@@ -47,6 +47,7 @@ class bd_step_stats(ctypes.Structure):
         ("max_overlap", ctypes.c_double),
         ("fail_item", ctypes.c_int32), ("fail_count", ctypes.c_int32),
         ("barriers", ctypes.c_int64),
+        ("substeps", ctypes.c_int64), ("halvings", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -89,6 +90,7 @@ SIGNATURES = [
     ("bd_rollout_positions", ctypes.c_int, [_P, ctypes.c_int32, _P]),
     ("bd_rollout_log_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     ("bd_stage_times", ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    ("bd_struct_sizes", ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     ("bd_free", None, [_P]),
     ("bd_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -115,6 +117,11 @@ def load(build_if_missing: bool = True):
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
+    ps, ss = ctypes.c_int32(), ctypes.c_int32()
+    lib.bd_struct_sizes(ctypes.byref(ps), ctypes.byref(ss))
+    if (ps.value, ss.value) != (ctypes.sizeof(bd_params), ctypes.sizeof(bd_step_stats)):
+        raise RuntimeError("libbd_gb300.so structure sizes (%d, %d) differ from the binding's (%d, %d)"
+                           % (ps.value, ss.value, ctypes.sizeof(bd_params), ctypes.sizeof(bd_step_stats)))
     _lib = lib
     return lib
 
@@ -138,7 +145,7 @@ def _ptr(a):
 def make_params(n, L=None, rho=None, a=1.0, law=LAW_NONE, alpha=(0, 0, 0, 0), n_species=1,
                 eps=1.0, kappa=1.0, r_cut=5.0, skin=0.6, D=1.0, Dr=0.0, v0=0.0, dt=1e-4,
                 seed=0, replica=0, precision=0, max_corr_iters=1000, max_flip_rounds=4096,
-                literal_noise=0, step0=0):
+                literal_noise=0, step0=0, max_dt_halvings=0):
     p = bd_params()
     _check(load().bd_default_params(ctypes.byref(p)), "bd_default_params")
     p.n, p.n_species, p.a = int(n), int(n_species), float(a)
@@ -152,6 +159,7 @@ def make_params(n, L=None, rho=None, a=1.0, law=LAW_NONE, alpha=(0, 0, 0, 0), n_
     p.seed, p.replica = int(seed), int(replica)
     p.max_corr_iters, p.max_flip_rounds = int(max_corr_iters), int(max_flip_rounds)
     p.literal_noise, p.step0 = int(literal_noise), int(step0)
+    p.max_dt_halvings = int(max_dt_halvings)
     return p
 
 

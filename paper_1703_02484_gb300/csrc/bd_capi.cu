@@ -87,6 +87,7 @@ int validate(const bd_params *p) {
   }
   if (p->overlap_mode < BD_OVERLAP_DELAUNAY || p->overlap_mode > BD_OVERLAP_VERLET) return BD_ERR_ARG;
   if (p->overlap_mode == BD_OVERLAP_VERLET && p->law != BD_LAW_SHORT) return BD_ERR_UNSUPPORTED;
+  if (p->max_dt_halvings < 0 || p->max_dt_halvings > 20) return BD_ERR_ARG;
   return BD_OK;
 }
 
@@ -335,6 +336,7 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
         s.p.max_corr_iters != specs[0].p.max_corr_iters ||
         s.p.max_flip_rounds != specs[0].p.max_flip_rounds || s.p.overlap_mode != specs[0].p.overlap_mode)
       return BD_ERR_ARG;   // one disk radius, precision, loop caps and overlap mode per handle
+    if (R > 1 && s.p.max_dt_halvings > 0) return BD_ERR_UNSUPPORTED;   // halving: one system per handle
   }
   bd_handle *h = new (std::nothrow) bd_handle();
   if (!h) return BD_ERR_NOMEM;
@@ -690,6 +692,15 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
       BD_TRY(dalloc(h, &d.vc_hit, (size_t)np));
       BD_TRY(cudaMemsetAsync(d.vc_hit, 0, (size_t)np, h->stream));
     }
+    h->max_halvings = specs[0].p.max_dt_halvings;
+    if (h->max_halvings > 0) {
+      // the state at the start of a step that is being redone in pieces
+      BD_TRY(dalloc(h, &h->hs_pos, (size_t)np));
+      BD_TRY(dalloc(h, &h->hs_work, (size_t)np));
+      BD_TRY(dalloc(h, &h->hs_theta, (size_t)np));
+      BD_TRY(dalloc(h, &h->hs_tv, (size_t)nt));
+      BD_TRY(dalloc(h, &h->hs_tn, (size_t)nt));
+    }
 
     cudaStream_t st = h->stream;
     std::vector<float> th_i(np, 0.f);
@@ -932,6 +943,152 @@ bool step_graph_ready(bd_handle *h) {
   return true;
 }
 
+// Queue nsteps whole steps (one graph replay each, or plain launches when
+// every force launch is timed), wait for them, read the control block and fold
+// the force timings in.  A failed step makes the later ones no-ops.
+int queue_steps(bd_handle *h, int32_t nsteps, int64_t *launches_out) {
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  int64_t launches = 0;
+  int timed = 0;
+  const bool long_range = h->c.any_long;
+  if (h->timing && long_range) {
+    while ((int)h->ev_pool.size() < 2 * nsteps) {
+      cudaEvent_t ev;
+      if (cudaEventCreate(&ev) != cudaSuccess) return BD_ERR_CUDA;
+      h->ev_pool.push_back(ev);
+    }
+  }
+  // one graph replay per step, unless timing wants a launch per step in a
+  // multi-step call (the graph holds one pair of timing events)
+  const bool use_graph = nsteps > 0 && !(h->timing && long_range && nsteps > 1) && step_graph_ready(h);
+  if (use_graph) {
+    for (int s = 0; s < nsteps; ++s) {
+      e = cudaGraphLaunch(h->step_graph, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+    launches = (int64_t)nsteps * h->graph_launches;
+  }
+  for (int s = 0; s < (use_graph ? 0 : nsteps); ++s) {
+    if (long_range) {
+      bool tm = h->timing;
+      if (tm) cudaEventRecord(h->ev_pool[2 * s], st);
+      e = bd_launch_force_long(h->d, h->c, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+      if (tm) {
+        cudaEventRecord(h->ev_pool[2 * s + 1], st);
+        ++timed;
+      }
+      launches += h->c.precision == 0 ? bd_force_launches(h->c.force_variant) : 1;
+    }
+    if (h->c.any_short) {
+      e = bd_launch_force_short(h->d, h->c, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+      launches += bd_short_launches();
+    }
+    e = bd_launch_integrate(h->d, h->c, h->step + s, -1, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = launch_correction(h, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    launches += 2;
+  }
+  *launches_out += launches;
+  int rc = read_ctl(h);
+  if (rc) return rc;
+  if (use_graph && h->graph_timed) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->graph_ev[0], h->graph_ev[1]) == cudaSuccess) {
+      h->force_ms += ms;
+      h->force_launches += 1;
+    }
+  }
+  for (int s = 0; s < timed; ++s) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[2 * s], h->ev_pool[2 * s + 1]) == cudaSuccess) {
+      h->force_ms += ms;
+      h->force_launches += 1;
+    }
+  }
+  return BD_OK;
+}
+
+// ---- Sec. 4.3: a rejected move is repeated with a lower dt ----
+
+// copy the step-start state to (save) or from (restore) the halving snapshot
+cudaError_t halving_snapshot(bd_handle *h, bool save) {
+  cudaStream_t st = h->stream;
+  const size_t np = (size_t)h->np, nt = (size_t)h->nt;
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  cudaError_t e = cudaMemcpyAsync(save ? h->hs_pos : h->d.pos, save ? h->d.pos : h->hs_pos,
+                                  np * sizeof(double2), k, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(save ? h->hs_work : h->d.work, save ? h->d.work : h->hs_work, np * sizeof(float4), k, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(save ? h->hs_theta : h->d.theta, save ? h->d.theta : h->hs_theta, np * sizeof(float), k,
+                        st);
+  if (e == cudaSuccess && !h->c.overlap_verlet) {
+    e = cudaMemcpyAsync(save ? h->hs_tv : h->d.tv, save ? h->d.tv : h->hs_tv, nt * sizeof(int4), k, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(save ? h->hs_tn : h->d.tn, save ? h->d.tn : h->hs_tn, nt * sizeof(int4), k, st);
+  }
+  if (e == cudaSuccess && !save) {
+    e = cudaMemcpyAsync(h->d.prev, h->d.pos, np * sizeof(double2), k, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d.moved, 0, np, st);
+  }
+  return e;
+}
+
+// one piece of the step h->step with plain launches: forces at the piece's
+// start, the move of length dt / 2^depth(node), the correction stage (which
+// undoes the piece itself when it fails)
+cudaError_t launch_piece(bd_handle *h, int node, int64_t *launches) {
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  if (h->c.any_long) {
+    e = bd_launch_force_long(h->d, h->c, st);
+    *launches += h->c.precision == 0 ? bd_force_launches(h->c.force_variant) : 1;
+  }
+  if (e == cudaSuccess && h->c.any_short) {
+    e = bd_launch_force_short(h->d, h->c, st);
+    *launches += bd_short_launches();
+  }
+  if (e == cudaSuccess) e = bd_launch_integrate(h->d, h->c, h->step, -1, st, node);
+  if (e == cudaSuccess)
+    e = h->c.overlap_verlet ? bd_launch_overlap_verlet(h->d, h->c, st, h->vc_grid, h->vc_block, 0)
+                            : bd_launch_dt(h->d, h->c, 2, st, h->dt_grid, h->dt_block);
+  *launches += 2;
+  return e;
+}
+
+// a rejection that a shorter move can avoid: a pair passed through each
+// other, an inverted triangle without repair, or a disk beyond its list's reach
+bool halvable(const BdCtl &k) {
+  return k.status == BD_ERR_STEP_REJECTED &&
+         (k.st_fail_phase == 1 || k.st_fail_phase == 2 || k.st_fail_phase == 3 || k.st_fail_phase == 6);
+}
+
+// piece `node` was rejected and undone: run its two halves in order, halving
+// again a half that is rejected, down to depth max_halvings.  Returns BD_OK
+// or the status of the piece that could not be completed (undone by its
+// kernel; the caller restores the step's start).
+int run_halves(bd_handle *h, int node, int depth, int64_t *launches, int64_t *halvings) {
+  *halvings += 1;
+  for (int child = 2 * node; child <= 2 * node + 1; ++child) {
+    cudaError_t e = launch_piece(h, child, launches);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int rc = read_ctl(h);
+    if (rc) return rc;
+    const int status = h->h_ctl->status;
+    if (status == BD_OK) continue;
+    const bool again = halvable(*h->h_ctl) && depth + 1 < h->max_halvings;
+    finish_status(h, status);
+    if (!again) return status;
+    rc = run_halves(h, child, depth + 1, launches, halvings);
+    if (rc) return rc;
+  }
+  return BD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -951,6 +1108,12 @@ const char *bd_strerror(int code) {
     case BD_ERR_UNSUPPORTED: return "unsupported parameter combination";
     default: return "unknown status";
   }
+}
+
+int bd_struct_sizes(int32_t *params_bytes, int32_t *stats_bytes) {
+  if (params_bytes) *params_bytes = (int32_t)sizeof(bd_params);
+  if (stats_bytes) *stats_bytes = (int32_t)sizeof(bd_step_stats);
+  return BD_OK;
 }
 
 int bd_default_params(bd_params *p) {
@@ -1011,72 +1174,46 @@ int bd_batch_init(int32_t R, const bd_params *p, const double *xy, const uint8_t
 int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
   if (!h || nsteps < 0) return BD_ERR_ARG;
   if (stats) memset(stats, 0, sizeof(*stats));
-  cudaStream_t st = h->stream;
   cudaError_t e = reset_stats(h);
   if (e != cudaSuccess) return cuda_fail(e);
-  int64_t launches = 0;
-  int timed = 0;
-  const bool long_range = h->c.any_long;
-  if (h->timing && long_range) {
-    while ((int)h->ev_pool.size() < 2 * nsteps) {
-      cudaEvent_t ev;
-      if (cudaEventCreate(&ev) != cudaSuccess) return BD_ERR_CUDA;
-      h->ev_pool.push_back(ev);
+  const int64_t step_base = h->step;
+  int64_t launches = 0, halvings = 0;
+  int status = BD_OK;
+  int32_t todo = nsteps;
+  for (;;) {
+    int rc = queue_steps(h, todo, &launches);
+    if (rc) return rc;
+    const BdCtl &k = *h->h_ctl;
+    h->step = step_base + k.st_steps;
+    if (k.status == BD_OK) break;
+    if (!(h->max_halvings > 0 && halvable(k))) {
+      status = k.status;
+      break;
     }
-  }
-  // one graph replay per step, unless timing wants a launch per step in a
-  // multi-step call (the graph holds one pair of timing events)
-  const bool use_graph = nsteps > 0 && !(h->timing && long_range && nsteps > 1) && step_graph_ready(h);
-  if (use_graph) {
-    for (int s = 0; s < nsteps; ++s) {
-      e = cudaGraphLaunch(h->step_graph, st);
-      if (e != cudaSuccess) return cuda_fail(e);
-    }
-    launches = (int64_t)nsteps * h->graph_launches;
-  }
-  for (int s = 0; s < (use_graph ? 0 : nsteps); ++s) {
-    if (long_range) {
-      bool tm = h->timing;
-      if (tm) cudaEventRecord(h->ev_pool[2 * s], st);
-      e = bd_launch_force_long(h->d, h->c, st);
-      if (e != cudaSuccess) return cuda_fail(e);
-      if (tm) {
-        cudaEventRecord(h->ev_pool[2 * s + 1], st);
-        ++timed;
-      }
-      launches += h->c.precision == 0 ? bd_force_launches(h->c.force_variant) : 1;
-    }
-    if (h->c.any_short) {
-      e = bd_launch_force_short(h->d, h->c, st);
-      if (e != cudaSuccess) return cuda_fail(e);
-      launches += bd_short_launches();
-    }
-    e = bd_launch_integrate(h->d, h->c, h->step + s, -1, st);
+    // Sec. 4.3: the rejected step was undone by its kernel; keep its start and
+    // repeat it as two halves (each halved again when rejected)
+    const int64_t done = k.st_steps;
+    finish_status(h, BD_ERR_STEP_REJECTED);
+    e = halving_snapshot(h, true);
     if (e != cudaSuccess) return cuda_fail(e);
-    e = launch_correction(h, st);
+    rc = run_halves(h, 1, 0, &launches, &halvings);
+    if (rc == BD_ERR_CUDA || rc == BD_ERR_NOMEM) return rc;
+    if (rc != BD_OK) {
+      e = halving_snapshot(h, false);
+      if (e != cudaSuccess) return cuda_fail(e);
+      status = rc;
+      rc = read_ctl(h);
+      if (rc) return rc;
+      break;
+    }
+    e = bd_launch_advance_step(h->d, h->stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    launches += 2;
+    todo = nsteps - (int32_t)(done + 1);
   }
   h->last_launches = launches;
-  int rc = read_ctl(h);
-  if (rc) return rc;
-  if (use_graph && h->graph_timed) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, h->graph_ev[0], h->graph_ev[1]) == cudaSuccess) {
-      h->force_ms += ms;
-      h->force_launches += 1;
-    }
-  }
-  for (int s = 0; s < timed; ++s) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, h->ev_pool[2 * s], h->ev_pool[2 * s + 1]) == cudaSuccess) {
-      h->force_ms += ms;
-      h->force_launches += 1;
-    }
-  }
   const BdCtl &k = *h->h_ctl;
   add_stage_times(h);
-  h->step += k.st_steps;
+  h->step = step_base + k.st_steps;
   if (stats) {
     stats->steps_done = k.st_steps;
     stats->corr_iters = k.st_corr_iters;
@@ -1087,18 +1224,20 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
     stats->inverted = k.st_inverted;
     stats->max_corr_iters = k.st_max_corr_iters;
     stats->verlet_rebuilds = (int32_t)k.st_verlet_rebuilds;
-    stats->fail_phase = k.st_fail_phase;
+    stats->fail_phase = status ? k.st_fail_phase : 0;
     stats->fail_item = k.st_fail_item;
     stats->fail_count = k.st_fail_count;
     stats->barriers = k.st_barriers;
-    stats->rejected = k.status != 0;
+    stats->rejected = status != 0;
+    stats->substeps = k.st_substeps;
+    stats->halvings = halvings;
     double mo;
     unsigned long long bits = k.st_max_overlap_bits;
     memcpy(&mo, &bits, sizeof(mo));
     stats->max_overlap = mo;
   }
   if (k.status) return finish_status(h, k.status);
-  return BD_OK;
+  return status;
 }
 
 int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32_t *tri,

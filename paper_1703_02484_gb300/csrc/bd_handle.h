@@ -57,6 +57,12 @@ struct bd_handle {
   bool graph_timed = false;
   bool graph_off = false;          // capture failed or disabled (BD_NO_GRAPH)
   int graph_launches = 0;          // kernels in one replay
+  // Sec. 4.3 halving of rejected moves: depth limit and the step-start state
+  int max_halvings = 0;
+  double2 *hs_pos = nullptr;
+  float4 *hs_work = nullptr;
+  float *hs_theta = nullptr;
+  int4 *hs_tv = nullptr, *hs_tn = nullptr;
   double stage_ns[4] = {0, 0, 0, 0};   // triangulation-kernel stage times since the last reset
   int64_t stage_cnt[4] = {0, 0, 0, 0};
 };

@@ -47,6 +47,7 @@ struct BdCtl {
   int st_fail_phase;               // 1 reversal, 2 repair stuck, 3 repair rounds, 4 Lawson rounds, 5 overlap passes
   int vl_need;                     // Verlet rebuild requested for this step
   long long st_verlet_rebuilds;
+  long long st_substeps;           // pieces of halved steps that completed
   long long st_barriers;           // grid barriers passed by the triangulation kernel
   int st_fail_item;                // an offending triangle (repair) or edge corner (reversal)
   int st_fail_count;               // inverted triangles / reversed edges at the failure
@@ -149,8 +150,11 @@ struct BdConst {
 // launchers (kernels_*.cu)
 cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t s);
 cudaError_t bd_launch_force_long_variant(const BdDev &d, const BdConst &c, int variant, cudaStream_t s);
+// node: piece of the step in the heap numbering of halved steps (1 = the whole step)
 cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, int log_step,
-                                cudaStream_t s);
+                                cudaStream_t s, int node = 1);
+// mode 0: a whole time step; 1: repair after new positions (no correction);
+// 2: a piece of a halved step (as 0, but the step counter does not advance)
 cudaError_t bd_launch_dt(const BdDev &d, const BdConst &c, int mode, cudaStream_t s, int grid, int block,
                          int log_step = -1);
 int bd_dt_grid(int *grid, int *block);
@@ -161,6 +165,10 @@ cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t
 int bd_short_launches();
 cudaError_t bd_launch_force_sum(const BdDev &d, const BdConst &c, double2 *out, cudaStream_t s);
 cudaError_t bd_launch_force_sym(const BdDev &d, const BdConst &c, int variant, cudaStream_t s);
-cudaError_t bd_launch_overlap_verlet(const BdDev &d, const BdConst &c, cudaStream_t s, int grid, int block);
+// advance = 0: a piece of a halved step (the step counter does not advance)
+cudaError_t bd_launch_overlap_verlet(const BdDev &d, const BdConst &c, cudaStream_t s, int grid, int block,
+                                     int advance = 1);
+// a halved step completed: advance the device step counter and the step count
+cudaError_t bd_launch_advance_step(const BdDev &d, cudaStream_t s);
 int bd_vcorr_grid_for(int work_items, int *grid, int *block);
 int bd_force_launches(int variant);   // kernel launches of one long-range force evaluation

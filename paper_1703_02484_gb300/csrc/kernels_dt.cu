@@ -206,8 +206,10 @@ __device__ __forceinline__ int key_corner(unsigned long long key) {
 
 }  // namespace
 
-// One time step's triangulation work (mode 0), or the repair of the
-// triangulation after new positions are set (mode 1, no overlap correction).
+// One time step's triangulation work (mode 0), the repair of the
+// triangulation after new positions are set (mode 1, no overlap correction),
+// or one piece of a halved step (mode 2: as mode 0, but the step counter does
+// not advance).
 //
 // Phases, each ended by a grid barrier:
 //   P  one pass over the triangles: orientation of triangles with a moved
@@ -311,7 +313,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
               ++cand;
             }
           }
-          if (mode == 0 && disks) {
+          if (mode != 1 && disks) {
             // FP32 screen: a pair whose FP32 squared distance exceeds
             // sigma^2 (1 + 1e-5) is farther than sigma (FP32 error ~3e-7)
             const float4 wu = d.work[u], ww = d.work[w];
@@ -578,7 +580,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
     ctl->st_flip_rounds += st_rounds;
     ctl->st_barriers += b.gen;
     if (corr_iter > ctl->st_max_corr_iters) ctl->st_max_corr_iters = corr_iter;
-    if (!status) ctl->st_steps += 1;
+    if (!status && mode == 2) ctl->st_substeps += 1;
+    else if (!status) ctl->st_steps += 1;
     if (!status && mode == 0) ctl->step_dev += 1;
   }
   block_exit(ctl);

@@ -317,7 +317,7 @@ __global__ void k_force_sum(BdDev d, BdConst c, double2 *out) {
 }
 
 // step < 0: the index of the step is the device counter (graph replays)
-__global__ void k_integrate(BdDev d, BdConst c, long long step, int log_step) {
+__global__ void k_integrate(BdDev d, BdConst c, long long step, int log_step, int node) {
   if (ctl_failed(d.ctl)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= c.np) return;
@@ -332,14 +332,32 @@ __global__ void k_integrate(BdDev d, BdConst c, long long step, int log_step) {
   const float th = d.theta[i];
   d.theta0[i] = th;
   float thn;
-  const double2 y = bdem::em_move(c, R, (uint32_t)e, step, p, th, F, R.v0, &thn);
   int flags = 0;
-  const double2 pn = bdem::reflect(R, y, &flags);
-  d.pos[i] = pn;
-  d.work[i] = bdem::split(pn);
+  if (c.precision == 0) {
+    // move, reflection and FP32 copy in grid units (no FP64 arithmetic)
+    long long X, Y;
+    bdem::em_move_grid(c, R, (uint32_t)e, step, p, th, F, R.v0, &thn, (uint32_t)node, &X, &Y);
+    const bdpred::Grid g{c.q, c.inv_q, c.qshift};
+    flags = bdem::reflect_grid(bdpred::to_int(R.wall_lo, g), bdpred::to_int(R.wall_hi, g), X, Y);
+    d.pos[i] = make_double2(bdem::grid_to_double(X, c.qshift), bdem::grid_to_double(Y, c.qshift));
+    const float2 sx = bdem::grid_split(X, c.qshift), sy = bdem::grid_split(Y, c.qshift);
+    d.work[i] = make_float4(sx.x, sy.x, sx.y, sy.y);
+  } else {
+    const double2 y = bdem::em_move(c, R, (uint32_t)e, step, p, th, F, R.v0, &thn, (uint32_t)node);
+    const double2 pn = bdem::reflect(R, y, &flags);
+    d.pos[i] = pn;
+    d.work[i] = bdem::split(pn);
+  }
   d.theta[i] = thn;
   d.moved[i] = 1;
   if (log_step >= 0 && d.log_refl) d.log_refl[(size_t)log_step * c.np + i] = (uint8_t)flags;
+}
+
+// all pieces of a halved step completed: the step counts as one time step
+__global__ void k_advance_step(BdCtl *ctl) {
+  if (*(volatile int *)&ctl->status) return;
+  ctl->step_dev += 1;
+  ctl->st_steps += 1;
 }
 
 __global__ void k_work_copy(BdDev d, BdConst c) {
@@ -379,8 +397,13 @@ cudaError_t bd_launch_force_long(const BdDev &d, const BdConst &c, cudaStream_t 
 }
 
 cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, int log_step,
-                                cudaStream_t s) {
-  k_integrate<<<(c.np + 255) / 256, 256, 0, s>>>(d, c, (long long)step, log_step);
+                                cudaStream_t s, int node) {
+  k_integrate<<<(c.np + 255) / 256, 256, 0, s>>>(d, c, (long long)step, log_step, node);
+  return cudaGetLastError();
+}
+
+cudaError_t bd_launch_advance_step(const BdDev &d, cudaStream_t s) {
+  k_advance_step<<<1, 1, 0, s>>>(d.ctl);
   return cudaGetLastError();
 }
 

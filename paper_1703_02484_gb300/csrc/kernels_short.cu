@@ -24,6 +24,7 @@
 #include <stdint.h>
 
 #include "bd_internal.h"
+#include "em.cuh"
 
 #define BD_SCAN_B 512
 
@@ -101,9 +102,20 @@ __global__ void k_vl_check(BdDev d, BdConst c) {
   if (i < c.np) {
     const BdRep *R = short_rep(d, i);
     if (R) {
-      double2 p = d.pos[i], r = d.vl_ref[i];
-      double dx = p.x - r.x, dy = p.y - r.y;
-      hit = dx * dx + dy * dy > 0.25 * R->skin * R->skin;
+      // displacement since the build in grid units (exact), screened in FP32;
+      // only a displacement within 1e-5 of skin/2 is decided in FP64
+      const double2 p = d.pos[i], r = d.vl_ref[i];
+      const bdpred::Grid g{c.q, c.inv_q, c.qshift};
+      const float fx = bdem::grid_to_float(bdpred::to_int(p.x, g) - bdpred::to_int(r.x, g), c.qshift);
+      const float fy = bdem::grid_to_float(bdpred::to_int(p.y, g) - bdpred::to_int(r.y, g), c.qshift);
+      const float d2 = __fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy));
+      const float thr = (float)(0.25 * R->skin * R->skin);
+      if (d2 > thr * 1.00001f) {
+        hit = true;
+      } else if (d2 >= thr * 0.99999f) {
+        double dx = p.x - r.x, dy = p.y - r.y;
+        hit = dx * dx + dy * dy > 0.25 * R->skin * R->skin;
+      }
     }
   }
   if (__any_sync(0xffffffffu, hit) && (threadIdx.x & 31) == 0) atomicExch(&d.ctl->vl_need, 1);
@@ -271,45 +283,61 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
   const float rwca2 = (float)(1.2599210498948732 * c.sigma * c.sigma);  // (2^(1/6) s)^2
   float fx = 0.f, fy = 0.f;      // Yukawa tail, FP32
   ff gx = {0.f, 0.f}, gy = {0.f, 0.f};   // WCA core, float-float sums
-  for (int t = 0; t < m; ++t) {
-    int j = d.vl_idx[(size_t)t * c.np + i];
-    float4 wj = d.work[j];
-    // r_i - r_j from the (hi, lo) pairs: exact for near pairs
-    float dx = __fadd_rn(__fsub_rn(wi.x, wj.x), __fsub_rn(wi.z, wj.z));
-    float dy = __fadd_rn(__fsub_rn(wi.y, wj.y), __fsub_rn(wi.w, wj.w));
-    float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-    if (fabsf(r2 - rc2) < 1e-5f * rc2) {
-      // at the cut-off the force jumps: decide as the FP64 reference does
-      double2 pj = d.pos[j];
-      double ex = __dsub_rn(pi.x, pj.x), ey = __dsub_rn(pi.y, pj.y);
-      if (!(sqrt(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey))) < R.r_cut)) continue;
-    } else if (r2 >= rc2) {
-      continue;
-    }
-    float r = sqrtf(r2);
-    float ir = 1.0f / r;
-    // Yukawa tail: -U'(r) / r, smooth, in FP32
-    float my = -eps * sg * expf(-kap * (r - sg)) * (ir * ir + kap * ir) * ir;
-    fx = fmaf(my, dx, fx);
-    fy = fmaf(my, dy, fy);
-    if (r2 < rwca2) {
-      // WCA core near contact: -U'(r) ~ r^-13 turns FP32 rounding into
-      // errors above 1e-5 of the net force, so the core is evaluated in
-      // float-float arithmetic (FP32 instructions, ~48-bit significands) from
-      // the exact coordinate differences
-      ff ex = ff_make(__fsub_rn(wi.x, wj.x), __fsub_rn(wi.z, wj.z));
-      ff ey = ff_make(__fsub_rn(wi.y, wj.y), __fsub_rn(wi.w, wj.w));
-      ff q2 = ff_add(ff_mul(ex, ex), ff_mul(ey, ey));
-      ff s2 = ff_div({sg * sg, 0.f}, q2);
-      ff s6 = ff_mul(ff_mul(s2, s2), s2);
-      ff t = ff_add(ff_scale(ff_mul(s6, s6), 2.0f), {-s6.hi, -s6.lo});
-      ff cw = ff_div(ff_scale(t, 24.0f * eps), q2);
-      gx = ff_add(gx, ff_mul(cw, ex));
-      gy = ff_add(gy, ff_mul(cw, ey));
+  // four list entries at a time: their index loads, then their position
+  // gathers, are issued before any of them is used (the loop is bound by the
+  // latency of these dependent loads, not by arithmetic)
+  for (int t0 = 0; t0 < m; t0 += 4) {
+    int jj[4];
+    float4 wv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) jj[u] = t0 + u < m ? d.vl_idx[(size_t)(t0 + u) * c.np + i] : i;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) wv[u] = d.work[jj[u]];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (t0 + u >= m) break;
+      const int j = jj[u];
+      const float4 wj = wv[u];
+      // r_i - r_j from the (hi, lo) pairs: exact for near pairs
+      const float dx = __fadd_rn(__fsub_rn(wi.x, wj.x), __fsub_rn(wi.z, wj.z));
+      const float dy = __fadd_rn(__fsub_rn(wi.y, wj.y), __fsub_rn(wi.w, wj.w));
+      const float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+      if (fabsf(r2 - rc2) < 1e-5f * rc2) {
+        // at the cut-off the force jumps: decide as the FP64 reference does
+        const double2 pj = d.pos[j];
+        const double ex = __dsub_rn(pi.x, pj.x), ey = __dsub_rn(pi.y, pj.y);
+        if (!(sqrt(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey))) < R.r_cut)) continue;
+      } else if (r2 >= rc2) {
+        continue;
+      }
+      // Yukawa tail: -U'(r) / r, smooth, in FP32 (approximate reciprocal
+      // square root and exponential: relative error ~1e-7)
+      const float ir = rsqrtf(r2);
+      const float r = r2 * ir;
+      const float my = -eps * sg * __expf(-kap * (r - sg)) * (ir * ir + kap * ir) * ir;
+      fx = fmaf(my, dx, fx);
+      fy = fmaf(my, dy, fy);
+      if (r2 < rwca2) {
+        // WCA core near contact: -U'(r) ~ r^-13 turns FP32 rounding into
+        // errors above 1e-5 of the net force, so the core is evaluated in
+        // float-float arithmetic (FP32 instructions, ~48-bit significands) from
+        // the exact coordinate differences
+        ff ex = ff_make(__fsub_rn(wi.x, wj.x), __fsub_rn(wi.z, wj.z));
+        ff ey = ff_make(__fsub_rn(wi.y, wj.y), __fsub_rn(wi.w, wj.w));
+        ff q2 = ff_add(ff_mul(ex, ex), ff_mul(ey, ey));
+        ff s2 = ff_div({sg * sg, 0.f}, q2);
+        ff s6 = ff_mul(ff_mul(s2, s2), s2);
+        ff t = ff_add(ff_scale(ff_mul(s6, s6), 2.0f), {-s6.hi, -s6.lo});
+        ff cw = ff_div(ff_scale(t, 24.0f * eps), q2);
+        gx = ff_add(gx, ff_mul(cw, ex));
+        gy = ff_add(gy, ff_mul(cw, ey));
+      }
     }
   }
-  d.fpart[i] = make_double2((double)fx + (double)gx.hi + (double)gx.lo,
-                            (double)fy + (double)gy.hi + (double)gy.lo);
+  // the float-float total, rounded once to FP32 (the move reads the force in
+  // FP32), stored as a double without FP64 arithmetic
+  const ff tx = ff_add(gx, {fx, 0.f}), ty = ff_add(gy, {fy, 0.f});
+  d.fpart[i] = make_double2((double)tx.hi, (double)ty.hi);
 }
 
 cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t s) {

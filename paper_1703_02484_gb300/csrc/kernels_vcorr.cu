@@ -51,7 +51,7 @@ __device__ __forceinline__ void stage_tick(BdCtl *ctl, int stage, unsigned long 
 
 }  // namespace
 
-__global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdConst c) {
+__global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdConst c, int advance) {
   BdCtl *ctl = d.ctl;
   if (ld_status(&ctl->status) != 0) {
     block_exit(ctl);
@@ -179,9 +179,11 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
     ctl->st_overlap_pairs += st_overlap;
     ctl->st_barriers += b.gen;
     if (corr_iter > ctl->st_max_corr_iters) ctl->st_max_corr_iters = corr_iter;
-    if (!status) {
+    if (!status && advance) {
       ctl->st_steps += 1;
       ctl->step_dev += 1;
+    } else if (!status) {
+      ctl->st_substeps += 1;
     }
   }
   block_exit(ctl);
@@ -201,9 +203,11 @@ int bd_vcorr_grid_for(int work_items, int *grid, int *block) {
   return 0;
 }
 
-cudaError_t bd_launch_overlap_verlet(const BdDev &d, const BdConst &c, cudaStream_t s, int grid, int block) {
+cudaError_t bd_launch_overlap_verlet(const BdDev &d, const BdConst &c, cudaStream_t s, int grid, int block,
+                                     int advance) {
   BdDev dd = d;
   BdConst cc = c;
-  void *args[] = {&dd, &cc};
+  int adv = advance;
+  void *args[] = {&dd, &cc, &adv};
   return cudaLaunchCooperativeKernel((const void *)k_overlap_verlet, dim3(grid), dim3(block), args, 0, s);
 }

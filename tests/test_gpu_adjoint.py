@@ -145,7 +145,7 @@ def test_autograd_function():
     assert np.allclose(params.grad.numpy(), g, rtol=1e-10, atol=0)
     # same parameters and start: same loss
     loss2 = bd.rollout_loss(params.detach(), s, x0, th0, 0, 20, 5, TARGET)
-    assert float(loss2) == float(loss)
+    assert float(loss2) == float(loss.detach())
 
 
 def test_rollout_argument_errors():
