@@ -166,6 +166,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind):
+    """HBM roofline of the per-step correction kernel of the short-range path.
+
+    Duration: the kernel's own device-clock stage timers (bd_stage_times),
+    summed over its stages, per launch (one launch per step).  Algorithmic
+    bytes per launch, from the pass counts of the same timers:
+      k_triangulation: every check pass reads the corner table (32 B per
+        triangle) and each disk's moved flag and FP32 position (17 B); the
+        first pass also writes the rollback snapshot (32 B per triangle); a
+        flip round reads the claims and flags (24 B per triangle); an apply
+        pass reads and writes positions, displacements and flags (100 B per
+        disk) and clears triangle flags (16 B per triangle).
+      k_overlap_verlet: a scan pass reads each disk's count, flag, both
+        position copies and its list with the neighbours' flags (38 + 5 m B
+        per disk, m the mean list length) and writes its displacement and hit
+        flag (17 B); an apply pass 100 B per disk."""
+    ms = sum(v[0] for v in stage_raw.values()) / steps
+    if not ms > 0:
+        return None
+    if verlet_mode:
+        cnt = system.neighbors()
+        m = float(np.mean([len(c) for c in cnt]))
+        scans, applies = stage_raw["check"][1] / steps, stage_raw["apply"][1] / steps
+        per = scans * N * (38 + 5 * m + 17) + applies * N * 100
+        kernel = "k_overlap_verlet"
+        note = "%.2f scan passes (mean list %.1f) and %.2f apply passes per launch" % (scans, m, applies)
+    else:
+        T = system.n_tri
+        P, F, A = (stage_raw[k][1] / steps for k in ("check", "flip", "apply"))
+        per = P * (32 * T + 17 * N) + 32 * T + F * 24 * T + A * (100 * N + 16 * T)
+        kernel = "k_triangulation"
+        note = ("%.2f check passes, %.2f flip rounds, %.2f apply passes per launch over %d triangles"
+                % (P, F, A, T))
+    gbs = per / (ms / 1e3) / 1e9
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    return {"bound": "hbm", "kernel": kernel, "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": gbs / peak, "traffic": None, "algorithmic_bytes_per_launch": per,
+            "avg_launch_ms": ms,
+            "peak_note": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs); duration from the kernel's "
+                         "device-clock stage timers; %s" % (pk_kind, note)}
+
+
 def cpu_baseline(cfg, xy, sp, th):
     """One full oracle step of the workload (exact all-pairs forces on all host
     cores), the oracle as it stands."""
@@ -371,7 +413,8 @@ def main():
     ms_steps = [a.elapsed_time(b) for a, b in ev]
     t_ms = float(sum(ms_steps))
     force_ms, force_n = system.force_timing(False)
-    stage_ms = {k: v[0] / args.steps for k, v in system.stage_times(reset=True).items()}
+    stage_raw = system.stage_times(reset=True)
+    stage_ms = {k: v[0] / args.steps for k, v in stage_raw.items()}
     if ws > 1:
         tt = torch.tensor([t_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -442,7 +485,7 @@ def main():
 
     if rank == 0:
         if args.workload != "n1e5":
-            line_cfg = {"workload": "%s: N=%d, rho=%.2f, law=%d" % (cfg.name, N, cfg.rho, cfg.law), "N": N}
+            line_cfg = {"workload": "%s: N=%d, rho=%.2f, law=%d" % (args.workload, N, cfg.rho, cfg.law), "N": N}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -470,8 +513,10 @@ def main():
                 line["config"]["overlap_pairs_from"] = "Verlet lists (no triangulation)"
         line["config"]["triangulation_stage_ms_per_step"] = stage_ms
         if not (avg_force_s > 0):
-            # no all-pairs launch in this workload (short-range law)
-            line["roofline"] = None
+            # no all-pairs launch (short-range law): the dominant kernel is the
+            # persistent correction kernel, bound by memory (gathers), so its
+            # line is HBM bytes against the measured copy bandwidth
+            line["roofline"] = correction_roofline(system, stage_raw, args.steps, N, verlet_mode, pk, pk_kind)
         elif cfg.precision == 1:
             # FP64 sweep (one disk per thread, 12 FP64 flops per ordered pair);
             # FP64 issues at 1/64 of the FP32 rate on this part

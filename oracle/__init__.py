@@ -14,4 +14,4 @@ bench.py may import it.  It shares no code with the CUDA library and never
 reads anything the CUDA library produced except the state it is asked to step
 from.  Every function cites the passage it follows.
 """
-from . import philox, noise, forces, dynamics, geometry, overlap, step, verlet  # noqa: F401
+from . import philox, noise, forces, dynamics, geometry, periodic, overlap, step, verlet  # noqa: F401

@@ -448,6 +448,34 @@ void oracle_force_long(int n, const double *x, const double *y, const uint8_t *s
     (void)nthreads;
 }
 
+/* The same sum in a periodic box of side L with the minimum-image
+ * convention (Sec. 2.1): r_ij is replaced by its image nearest the origin,
+ * r_ij - L round(r_ij / L) per component. */
+void oracle_force_long_periodic(int n, const double *x, const double *y, const uint8_t *s,
+                                const double *A, double L, int i0, int i1, double *fx, double *fy,
+                                int nthreads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int i = i0; i < i1; i++) {
+        double ax = 0.0, ay = 0.0;
+        for (int j = 0; j < n; j++) {
+            if (j == i) continue;
+            double rx = x[i] - x[j], ry = y[i] - y[j];
+            rx -= L * nearbyint(rx / L);
+            ry -= L * nearbyint(ry / L);
+            double r2 = rx * rx + ry * ry;
+            double r = sqrt(r2);
+            double c = A[2 * s[i] + s[j]] / (r2 * r);
+            ax += c * rx;
+            ay += c * ry;
+        }
+        fx[i - i0] = ax;
+        fy[i - i0] = ay;
+    }
+    (void)nthreads;
+}
+
 /* Derivatives of the long-range force F_i = sum_j A[s_i][s_j] r_ij/|r_ij|^3,
  * r_ij = r_i - r_j (Sec. 2.2), for the differentiated rollout.
  *

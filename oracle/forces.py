@@ -5,8 +5,9 @@ k of mu_i alpha_k f(r_i - r_k) with f(r) = r / |r|^3.  The charges enter only
 through the product for the ordered species pair, so the oracle stores that
 product as a 2x2 table A[s_i][s_k] ("force ON species s_i FROM species s_k");
 a positive entry pushes i away from k.  The table need not factor as
-mu_i alpha_k, nor be symmetric (non-reciprocal interactions).  No images:
-the box has reflecting walls.
+mu_i alpha_k, nor be symmetric (non-reciprocal interactions).  With
+reflecting walls there are no images; in a periodic box (Sec. 2.1) every
+pair vector takes its minimum image.
 
 Short range: the paper's r/r^7 law is replaced by a WCA core plus a Yukawa
 tail, both truncated (not shifted) at r_cut as in Eq. (displacement) /
@@ -22,8 +23,9 @@ import numpy as np
 from . import _clib
 
 
-def long_range_numpy(xy, species, A, idx=None):
-    """Direct O(N^2) sum, numpy, for moderate N.  Returns (n_idx, 2)."""
+def long_range_numpy(xy, species, A, idx=None, L=None):
+    """Direct O(N^2) sum, numpy, for moderate N.  Returns (n_idx, 2).
+    L: periodic box side (minimum-image pair vectors, Sec. 2.1); None = walls."""
     xy = np.asarray(xy, dtype=np.float64)
     s = np.asarray(species, dtype=np.int64)
     A = np.asarray(A, dtype=np.float64).reshape(2, 2)
@@ -33,6 +35,8 @@ def long_range_numpy(xy, species, A, idx=None):
     for c0 in range(0, len(idx), 512):
         ii = idx[c0:c0 + 512]
         d = xy[ii, None, :] - xy[None, :, :]          # r_i - r_k
+        if L is not None:
+            d = d - L * np.round(d / L)
         r2 = np.einsum("ijk,ijk->ij", d, d)
         self_ = ii[:, None] == np.arange(n)[None, :]
         r2[self_] = 1.0
@@ -42,9 +46,9 @@ def long_range_numpy(xy, species, A, idx=None):
     return out
 
 
-def long_range(xy, species, A, idx=None, threads=1):
+def long_range(xy, species, A, idx=None, threads=1, L=None):
     """Same sum in the oracle's plain C loop (OpenMP over i when threads > 1).
-    idx must be a contiguous range (or None for all)."""
+    idx must be a contiguous range (or None for all); L as long_range_numpy."""
     xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64))
     n = len(xy)
     x = np.ascontiguousarray(xy[:, 0])
@@ -60,7 +64,11 @@ def long_range(xy, species, A, idx=None, threads=1):
     fx = np.zeros(i1 - i0)
     fy = np.zeros(i1 - i0)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
-    _clib.lib().oracle_force_long(n, p(x), p(y), p(s), p(A), i0, i1, p(fx), p(fy), int(threads))
+    if L is None:
+        _clib.lib().oracle_force_long(n, p(x), p(y), p(s), p(A), i0, i1, p(fx), p(fy), int(threads))
+    else:
+        _clib.lib().oracle_force_long_periodic(n, p(x), p(y), p(s), p(A), float(L), i0, i1, p(fx),
+                                               p(fy), int(threads))
     return np.stack([fx, fy], axis=1)
 
 
@@ -81,11 +89,14 @@ def short_range_potential(r, eps, kappa, sigma_c):
     return wca + yuk
 
 
-def short_range_pairs(xy, pairs_i, pairs_j, eps, kappa, sigma_c, r_cut):
+def short_range_pairs(xy, pairs_i, pairs_j, eps, kappa, sigma_c, r_cut, L=None):
     """Force on each i from its listed partners j (one row per listed pair):
-    returns (n, 2) accumulated over the given ordered pairs (i <- j)."""
+    returns (n, 2) accumulated over the given ordered pairs (i <- j).
+    L: periodic box side (minimum image); None = walls."""
     xy = np.asarray(xy, dtype=np.float64)
     d = xy[pairs_i] - xy[pairs_j]
+    if L is not None:
+        d = d - L * np.round(d / L)
     r = np.sqrt(np.einsum("ij,ij->i", d, d))
     mag = np.where(r < r_cut, short_range_magnitude(r, eps, kappa, sigma_c), 0.0)
     f = d * (mag / r)[:, None]
@@ -94,12 +105,14 @@ def short_range_pairs(xy, pairs_i, pairs_j, eps, kappa, sigma_c, r_cut):
     return out
 
 
-def short_range(xy, eps, kappa, sigma_c, r_cut):
-    """Brute-force all-pairs evaluation of the truncated short-range force."""
+def short_range(xy, eps, kappa, sigma_c, r_cut, L=None):
+    """All-pairs evaluation of the truncated short-range force (candidate
+    pairs from a k-d tree, periodic when L is given; the law is above)."""
     xy = np.asarray(xy, dtype=np.float64)
     n = len(xy)
     from scipy.spatial import cKDTree  # neighbour search only; the force is below
-    pairs = np.array(sorted(cKDTree(xy).query_pairs(r_cut * (1 + 1e-9))), dtype=np.int64).reshape(-1, 2)
+    tree = cKDTree(xy) if L is None else cKDTree(np.mod(xy, L), boxsize=L)
+    pairs = np.array(sorted(tree.query_pairs(r_cut * (1 + 1e-9))), dtype=np.int64).reshape(-1, 2)
     pi = np.concatenate([pairs[:, 0], pairs[:, 1]])
     pj = np.concatenate([pairs[:, 1], pairs[:, 0]])
-    return short_range_pairs(xy, pi, pj, eps, kappa, sigma_c, r_cut)
+    return short_range_pairs(xy, pi, pj, eps, kappa, sigma_c, r_cut, L)

@@ -22,7 +22,7 @@ the triangulation from scratch before every pass.
 """
 import numpy as np
 
-from . import dynamics, geometry
+from . import dynamics, geometry, periodic
 
 
 # why a step was rejected (0 = it was not): a pair passed through each other
@@ -137,3 +137,86 @@ def correct_allpairs(xy, L, a, max_iters=10000, record=None):
         if it >= max_iters:
             return xy, it, total, REJ_NOT_CONVERGED
 
+
+
+# ------------------------------------------------------ periodic box (Sec. 2.1)
+# Pairs are torus edges keyed (u, w, sx, sy) (oracle.periodic): the pair
+# vector is r_w + L s - r_u.  A disk that leaves the box re-enters at the
+# other side (Algorithm 2's apply step "applying the periodic boundary
+# conditions").
+
+
+def correction_pass_periodic(xy, K, sigma, L):
+    """One pass of Algorithm 2 over torus edges K.  Returns (new positions
+    before wrapping, overlapping keys, capped mask, raw displacement)."""
+    xy = np.asarray(xy, dtype=np.float64)
+    d = periodic.edge_vectors(xy, K, L)
+    r = np.sqrt(d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1])
+    hit = r < sigma
+    pairs = K[hit]
+    disp = np.zeros_like(xy)
+    if hit.any():
+        nhat = d[hit] / r[hit][:, None]
+        delta = (sigma - r[hit])[:, None]
+        np.add.at(disp, pairs[:, 0], -delta * nhat)
+        np.add.at(disp, pairs[:, 1], delta * nhat)
+    mag = np.sqrt(disp[:, 0] ** 2 + disp[:, 1] ** 2)
+    cap = sigma / 4.0
+    capped = mag > cap
+    scale = np.where(capped, cap / np.where(mag > 0, mag, 1.0), 1.0)
+    return xy + disp * scale[:, None], pairs, capped, disp
+
+
+def reversed_keys(xy0, xy1, K, L):
+    """Sec. 4.3 reversal test on torus edges: xy1 are the positions after the
+    move *before* wrapping, so r1 = r0 + (move of w) - (move of u)."""
+    r0 = periodic.edge_vectors(xy0, K, L)
+    r1 = periodic.edge_vectors(xy1, K, L)
+    dot = r0[:, 0] * r1[:, 0] + r0[:, 1] * r1[:, 1]
+    return K[dot < 0]
+
+
+def correct_periodic(xy, L, a, max_iters=10000, record=None):
+    """Algorithm 2 over the edges of the torus Delaunay triangulation of the
+    current positions until none is shorter than sigma (as correct()).
+    Returns (xy, (tri, shift) of the final positions, passes, overlapping
+    edges seen, rejection reason)."""
+    sigma = 2.0 * a
+    xy = np.asarray(xy, dtype=np.float64)
+    it = 0
+    total = 0
+    while True:
+        tri, sh = periodic.delaunay_torus(xy, L)
+        K = periodic.edge_keys(tri, sh)
+        new, pairs, capped, disp = correction_pass_periodic(xy, K, sigma, L)
+        if len(pairs) == 0:
+            return xy, (tri, sh), it, total, REJ_NONE
+        if record is not None:
+            record.append({"pairs": pairs, "capped": capped, "disp": disp, "xy": xy})
+        if len(reversed_keys(xy, new, K, L)):
+            return xy, (tri, sh), it, total, REJ_REVERSAL
+        total += len(pairs)
+        it += 1
+        xy = periodic.wrap(new, L)
+        if it >= max_iters:
+            return xy, periodic.delaunay_torus(xy, L), it, total, REJ_NOT_CONVERGED
+
+
+def correct_allpairs_periodic(xy, L, a, max_iters=10000, record=None):
+    """correct_allpairs() in a periodic box (minimum-image pairs)."""
+    sigma = 2.0 * a
+    xy = np.asarray(xy, dtype=np.float64)
+    it = 0
+    total = 0
+    while True:
+        K = periodic.close_pairs(xy, sigma, L)
+        if len(K) == 0:
+            return xy, it, total, REJ_NONE
+        new, pairs, capped, disp = correction_pass_periodic(xy, K, sigma, L)
+        if record is not None:
+            record.append({"pairs": pairs, "capped": capped, "disp": disp, "xy": xy})
+        total += len(pairs)
+        it += 1
+        xy = periodic.wrap(new, L)
+        if it >= max_iters:
+            return xy, it, total, REJ_NOT_CONVERGED

@@ -14,6 +14,9 @@ scratch; inverted-triangle repair and edge flips (Sec. 4.3) are how the GPU
 *maintains* that triangulation, so they have no counterpart here beyond the
 final triangulation itself.
 
+Periodic box (Params.periodic, Sec. 2.1): minimum-image forces, moves that
+wrap, and the torus triangulation of oracle.periodic.
+
 Rejected moves (Sec. 4.3): when a pair passes through each other "the last
 positions are discarded and integration is repeated with a lower dt".  With
 Params.max_halvings = H > 0 a rejected move is replaced by two moves of half
@@ -27,7 +30,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import dynamics, forces, geometry, overlap, philox
+from . import dynamics, forces, geometry, overlap, periodic, philox
 
 LAW_NONE, LAW_LONG, LAW_SHORT = 0, 1, 2
 
@@ -50,15 +53,17 @@ class Params:
     max_corr_iters: int = 10000
     literal_amp: bool = False
     max_halvings: int = 0
+    periodic: bool = False
 
 
 def compute_forces(xy, species, p: Params, threads=1):
+    Lp = p.L if p.periodic else None
     if p.law == LAW_LONG:
         if len(xy) <= 4096:
-            return forces.long_range_numpy(xy, species, p.alpha)
-        return forces.long_range(xy, species, p.alpha, threads=threads)
+            return forces.long_range_numpy(xy, species, p.alpha, L=Lp)
+        return forces.long_range(xy, species, p.alpha, threads=threads, L=Lp)
     if p.law == LAW_SHORT:
-        return forces.short_range(xy, p.eps, p.kappa, 2.0 * p.a, p.r_cut)
+        return forces.short_range(xy, p.eps, p.kappa, 2.0 * p.a, p.r_cut, L=Lp)
     return np.zeros_like(np.asarray(xy, dtype=np.float64))
 
 
@@ -71,6 +76,8 @@ def _piece(xy, theta, species, step_index, p: Params, ids, tris, F, threads, rec
     if F is None:
         F = compute_forces(xy, species, p, threads)
     dt = p.dt / float(2 ** (int(node).bit_length() - 1))
+    if p.periodic:
+        return _piece_periodic(xy, theta, F, step_index, p, ids, tris, record, pairs_from, node, dt)
     new, th = dynamics.em_step(xy, theta, F, ids, step_index, p.seed, p.D, p.Dr, p.v0, dt,
                                p.a, p.L, p.replica, p.literal_amp, philox.substep_tag(node))
     if pairs_from == "allpairs":
@@ -86,6 +93,30 @@ def _piece(xy, theta, species, step_index, p: Params, ids, tris, F, threads, rec
                     overlap_pairs=0, rejected=overlap.REJ_REVERSAL, F=F)
     out, tris1, iters, pairs, rej = overlap.correct(new, p.L, p.a, p.max_corr_iters,
                                                     record=record)
+    return dict(xy=out, theta=th, tris=tris1, corr_iters=iters, overlap_pairs=pairs,
+                rejected=rej, F=F, xy_em=new)
+
+
+def _piece_periodic(xy, theta, F, step_index, p, ids, tris, record, pairs_from, node, dt):
+    """_piece() in a periodic box (Sec. 2.1): the move wraps instead of
+    reflecting, pair vectors take their minimum image, and the triangulation
+    is the torus one (tris = (tri, shift), oracle.periodic)."""
+    moved, th = dynamics.em_move(xy, theta, F, ids, step_index, p.seed, p.D, p.Dr, p.v0, dt,
+                                 p.replica, p.literal_amp, philox.substep_tag(node))
+    new = periodic.wrap(moved, p.L)
+    if pairs_from == "allpairs":
+        out, iters, pairs, rej = overlap.correct_allpairs_periodic(new, p.L, p.a, p.max_corr_iters,
+                                                                   record=record)
+        return dict(xy=out, theta=th, tris=None, corr_iters=iters, overlap_pairs=pairs,
+                    rejected=rej, F=F, xy_em=new)
+    if tris is None:
+        tris = periodic.delaunay_torus(xy, p.L)
+    K0 = periodic.edge_keys(*tris)
+    if len(overlap.reversed_keys(xy, moved, K0, p.L)):
+        return dict(xy=xy, theta=np.asarray(theta, np.float64), tris=tris, corr_iters=0,
+                    overlap_pairs=0, rejected=overlap.REJ_REVERSAL, F=F)
+    out, tris1, iters, pairs, rej = overlap.correct_periodic(new, p.L, p.a, p.max_corr_iters,
+                                                             record=record)
     return dict(xy=out, theta=th, tris=tris1, corr_iters=iters, overlap_pairs=pairs,
                 rejected=rej, F=F, xy_em=new)
 

@@ -11,8 +11,9 @@ products and one sum, each rounded once.
 import numpy as np
 
 
-def build(xy, r_cut, skin):
-    """List of sorted neighbour index arrays, one per disk (brute force)."""
+def build(xy, r_cut, skin, L=None):
+    """List of sorted neighbour index arrays, one per disk (brute force).
+    L: periodic box side (minimum-image differences); None = walls."""
     xy = np.asarray(xy, dtype=np.float64)
     n = len(xy)
     rl2 = (r_cut + skin) * (r_cut + skin)
@@ -20,6 +21,9 @@ def build(xy, r_cut, skin):
     for c0 in range(0, n, 1024):
         dx = xy[c0:c0 + 1024, None, 0] - xy[None, :, 0]
         dy = xy[c0:c0 + 1024, None, 1] - xy[None, :, 1]
+        if L is not None:
+            dx = dx - L * np.round(dx / L)
+            dy = dy - L * np.round(dy / L)
         d2 = dx * dx + dy * dy
         for r in range(d2.shape[0]):
             i = c0 + r
