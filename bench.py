@@ -35,6 +35,11 @@ FP32_INST_PER_PAIR = 8   # the same work counted as FP32-pipe instructions (plus
 # sides) = 16 flops in 10 FP32 lane operations (+1 MUFU), i.e. per ordered pair:
 FLOPS_PER_PAIR_SYM = 8
 LANES_PER_PAIR_SYM = 5
+# periodic sweep: per ordered pair 2 hi + 2 lo differences and 2 adds (exact
+# near-pair vectors), 2 FFMA (r^2), 2 FMUL, 2 FFMA (accumulate) = 12 lane
+# operations (16 flops), plus the minimum-image tests (not counted)
+FLOPS_PER_PAIR_PER = 16
+LANES_PER_PAIR_PER = 12
 
 
 def peaks():
@@ -208,13 +213,14 @@ def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind):
                          "device-clock stage timers; %s" % (pk_kind, note)}
 
 
-def cpu_baseline(cfg, xy, sp, th):
+def cpu_baseline(cfg, xy, sp, th, periodic=False):
     """One full oracle step of the workload (exact all-pairs forces on all host
     cores), the oracle as it stands."""
     from oracle import step as ostep
     cores = os.cpu_count() or 1
-    op = ostep.Params(L=cfg.L, a=cfg.a, law=cfg.law, alpha=cfg.alpha, D=cfg.D, Dr=cfg.Dr,
-                      v0=cfg.v0, dt=cfg.dt, seed=cfg.seed)
+    L = float(np.float32(cfg.L)) if periodic else cfg.L
+    op = ostep.Params(L=L, a=cfg.a, law=cfg.law, alpha=cfg.alpha, D=cfg.D, Dr=cfg.Dr,
+                      v0=cfg.v0, dt=cfg.dt, seed=cfg.seed, periodic=periodic)
     t0 = time.perf_counter()
     ostep.step(xy, th, sp, 0, op, threads=cores)
     t = time.perf_counter() - t0
@@ -350,8 +356,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--workload", default="n1e5",
                     help="configuration name (n1e5 is the headline; c1, c2, c3, c5, c4 (batched), "
-                         "c5-grad (differentiated rollout), c3-verlet (overlap correction over the "
-                         "Verlet lists) for tables)")
+                         "c5-grad (differentiated rollout); suffixes -verlet (overlap correction over "
+                         "the Verlet lists) and -periodic (periodic box), e.g. c3-verlet, n1e5-periodic)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -373,12 +379,16 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    verlet_mode = args.workload.endswith("-verlet")
-    cfg = workloads.CONFIGS[args.workload[:-len("-verlet")] if verlet_mode else args.workload]
+    base, *modes = args.workload.split("-")
+    verlet_mode = "verlet" in modes
+    periodic_mode = "periodic" in modes
+    cfg = workloads.CONFIGS[base]
     xy, sp, th = workloads.initial_state(cfg)
     p = bd.params_from_config(cfg)
     if verlet_mode:
         p.overlap_mode = bd.OVERLAP_VERLET   # Algorithm 2 over the Verlet lists, no triangulation
+    if periodic_mode:
+        p.boundary = bd.BOUNDARY_PERIODIC    # the paper's periodic box (minimum image, torus triangulation)
     p.replica = rank
     stream = torch.cuda.current_stream()
     system = bd.System(p, xy, sp, th, stream=stream.cuda_stream)
@@ -436,11 +446,15 @@ def main():
     # algorithmic FP32 work of the chosen sweep, per ordered pair interaction
     flops_pp, lanes_pp = (FLOPS_PER_PAIR_SYM, LANES_PER_PAIR_SYM) if variant >= 2 else \
         (FLOPS_PER_PAIR, FP32_INST_PER_PAIR)
+    if periodic_mode:
+        flops_pp, lanes_pp = FLOPS_PER_PAIR_PER, LANES_PER_PAIR_PER
     achieved = flops_pp * pairs / avg_force_s / 1e12
     pipe_frac = lanes_pp * pairs / avg_force_s / (sms * 128 * f_hz)
     kernel = {0: "k_force_long_f32", 1: "k_force_long_f32x2<4>",
               2: "k_force_long_sym<4,2> + k_force_sym_reduce",
               3: "k_force_long_sym<2,4> + k_force_sym_reduce"}[variant]
+    if periodic_mode:
+        kernel = "k_force_long_per"
     traffic = None
     # ncu DRAM bytes of one launch, used only while the kernel source is the
     # one the counters were taken on
@@ -511,6 +525,8 @@ def main():
             line["config"].update(line_cfg)
             if verlet_mode:
                 line["config"]["overlap_pairs_from"] = "Verlet lists (no triangulation)"
+            if periodic_mode:
+                line["config"]["boundary"] = "periodic (minimum image, torus triangulation)"
         line["config"]["triangulation_stage_ms_per_step"] = stage_ms
         if not (avg_force_s > 0):
             # no all-pairs launch (short-range law): the dominant kernel is the
@@ -527,7 +543,7 @@ def main():
                                 "avg_launch_ms": avg_force_s * 1e3,
                                 "peak_note": "FP32 peak / 64 (the part's FP64 issue rate)"}
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(cfg, xy, sp, th)
+            line["cpu_baseline"] = cpu_baseline(cfg, xy, sp, th, periodic_mode)
         print(json.dumps(line), flush=True)
     system.close()
     if ws > 1:

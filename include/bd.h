@@ -2,7 +2,8 @@
  * bd.h -- C ABI of the GB300 Brownian hard-disk time stepper.
  *
  * The library advances N hard disks of radius a (diameter sigma = 2a) in a
- * square box [0, L]^2 with reflecting walls, following the per-step method
+ * square box [0, L]^2 with reflecting walls or periodic boundaries (Sec. 2.1,
+ * bd_params.boundary), following the per-step method
  * of Carter, Hitschfeld, Navarro & Soto, "GPU parallel simulation algorithm
  * of Brownian particles with excluded volume using Delaunay triangulations"
  * (arXiv:1703.02484), Algorithm 1 (Sec. 4.1): forces, Euler-Maruyama update
@@ -99,9 +100,21 @@ typedef struct bd_params {
                               halved again, down to dt / 2^H.  Single-system handles only
                               (bd_batch_init returns BD_ERR_UNSUPPORTED for H > 0); recorded
                               rollouts (bd_rollout) do not halve. */
+  int32_t boundary;        /* BD_BOUNDARY_WALLS (default): reflecting walls, centres in
+                              [a, L - a], the triangulation closed by fixed ghost points;
+                              BD_BOUNDARY_PERIODIC: the paper's periodic box (Sec. 2.1):
+                              centres in [0, L), pair vectors take their minimum image, a disk
+                              leaving one side re-enters at the other, and the triangulation
+                              is the Delaunay triangulation of the flat torus (Sec. 4.1), kept
+                              without ghost points (2n triangles, corners carry image shifts,
+                              bd_get_tri_shifts).  L is rounded to the nearest FP32 value.
+                              Periodic handles need n >= 16 and L >= 8 sigma; the all-pairs
+                              sweep uses its one-sided forms there; recorded rollouts
+                              (bd_rollout) are walls-only. */
 } bd_params;
 
 enum { BD_OVERLAP_DELAUNAY = 0, BD_OVERLAP_VERLET = 1 };
+enum { BD_BOUNDARY_WALLS = 0, BD_BOUNDARY_PERIODIC = 1 };
 
 /* Counters of one bd_step call (the paper's per-step metrics, Sec. 6). */
 typedef struct bd_step_stats {
@@ -211,8 +224,10 @@ int bd_get_tuning(bd_handle *h, int32_t *tiles_per_item, int32_t *variant, int32
  *   tri      3*n_tri ints: the current Delaunay triangulation of the disks
  *            plus the ghost points of bd_ghost_points (ids n, n+1, ...),
  *            counter-clockwise; the buffer must hold 3*(2(n+G)-6) ints where
- *            G is the ghost count (bd_ghost_points).
- *   n_tri    receives the number of triangles, 2(n+G)-6.
+ *            G is the ghost count (bd_ghost_points).  Periodic box: the
+ *            triangulation of the torus, 2n triangles of disk ids, whose
+ *            corner shifts bd_get_tri_shifts gives.
+ *   n_tri    receives the number of triangles, 2(n+G)-6 (periodic: 2n).
  *   step     receives the index of the next step.
  * Errors: BD_ERR_ARG (h == NULL), BD_ERR_CUDA. */
 int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32_t *tri,
@@ -240,6 +255,14 @@ int bd_compute_forces(bd_handle *h, double *F);
  * first force evaluation (bd_compute_forces or the first step).
  * Errors: BD_ERR_ARG, BD_ERR_UNSUPPORTED (long-range handle), BD_ERR_CUDA. */
 int bd_get_neighbors(bd_handle *h, int32_t max_per, int32_t *counts, int32_t *idx);
+
+/* Periodic box: the image shifts of the triangle corners returned by
+ * bd_get_state (or bd_get_replica for replica r; r < 0 = the whole handle).
+ * shifts receives 6 bytes per triangle, (sx, sy) for corners 0, 1, 2: corner
+ * k of triangle t lies at xy[tri[3t + k]] + L (sx, sy), each in {-1, 0, 1},
+ * and corner 0 at shift (0, 0).  With walls every shift is 0.
+ * Errors: BD_ERR_ARG, BD_ERR_CUDA. */
+int bd_get_tri_shifts(bd_handle *h, int32_t r, int8_t *shifts);
 
 /* Position-grid step q (coordinates are multiples of q) and box side L. */
 int bd_get_geometry(bd_handle *h, double *q, double *L);
@@ -290,6 +313,22 @@ int bd_ghost_points(double L, double a, double *xy, int32_t *count);
  * Errors: BD_ERR_ARG, BD_ERR_TRIANGULATION (duplicate point). */
 int bd_triangulate(int32_t n, const double *xy, double L, double a, double *xy_grid, int32_t *tri,
                    int32_t *n_tri);
+
+/* Host only (no GPU needed): the Delaunay triangulation of the flat torus
+ * (periodic box, Sec. 2.1 and 4.1) that bd_init builds for
+ * boundary = BD_BOUNDARY_PERIODIC, for n >= 3 centres in a box of side L
+ * (rounded to FP32 as bd_params.box_L is).
+ *   xy         2n doubles, any real coordinates (taken modulo L).
+ *   xy_grid    optional 2n doubles: the centres brought into [0, L) on the
+ *              position grid (the coordinates the triangulation is exact for).
+ *   tri        3*(2n) ints, counter-clockwise triangles of disk ids.
+ *   shifts     6*(2n) bytes: (sx, sy) of each corner, corner k of triangle t
+ *              at xy_grid[tri[3t + k]] + L (sx, sy); corner 0 at (0, 0).
+ *   n_tri      receives 2n.
+ * Errors: BD_ERR_ARG, BD_ERR_TRIANGULATION (duplicate point, or a point set
+ * whose torus triangulation is not a simplicial complex, e.g. too few points). */
+int bd_triangulate_periodic(int32_t n, const double *xy, double L, double *xy_grid, int32_t *tri,
+                            int8_t *shifts, int32_t *n_tri);
 
 /* All-pairs long-range force for callers that cannot allocate device memory
  * (no counterpart in the paper; it exists for users whose device memory is

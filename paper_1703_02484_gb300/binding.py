@@ -17,6 +17,7 @@ ERRORS = {
     -10: "BD_ERR_UNSUPPORTED",
 }
 LAW_NONE, LAW_LONG, LAW_SHORT = 0, 1, 2
+BOUNDARY_WALLS, BOUNDARY_PERIODIC = 0, 1
 LOSS_MSD = 0
 OVERLAP_DELAUNAY, OVERLAP_VERLET = 0, 1
 
@@ -34,6 +35,7 @@ class bd_params(ctypes.Structure):
         ("max_corr_iters", ctypes.c_int32), ("max_flip_rounds", ctypes.c_int32),
         ("literal_noise", ctypes.c_int32), ("step0", ctypes.c_int64),
         ("overlap_mode", ctypes.c_int32), ("max_dt_halvings", ctypes.c_int32),
+        ("boundary", ctypes.c_int32),
     ]
 
 
@@ -90,6 +92,9 @@ SIGNATURES = [
     ("bd_rollout_positions", ctypes.c_int, [_P, ctypes.c_int32, _P]),
     ("bd_rollout_log_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     ("bd_stage_times", ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    ("bd_get_tri_shifts", ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    ("bd_triangulate_periodic", ctypes.c_int, [ctypes.c_int32, _P, ctypes.c_double, _P, _P, _P,
+                                               ctypes.POINTER(ctypes.c_int32)]),
     ("bd_struct_sizes", ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     ("bd_free", None, [_P]),
     ("bd_strerror", ctypes.c_char_p, [ctypes.c_int]),
@@ -145,7 +150,7 @@ def _ptr(a):
 def make_params(n, L=None, rho=None, a=1.0, law=LAW_NONE, alpha=(0, 0, 0, 0), n_species=1,
                 eps=1.0, kappa=1.0, r_cut=5.0, skin=0.6, D=1.0, Dr=0.0, v0=0.0, dt=1e-4,
                 seed=0, replica=0, precision=0, max_corr_iters=1000, max_flip_rounds=4096,
-                literal_noise=0, step0=0, max_dt_halvings=0):
+                literal_noise=0, step0=0, max_dt_halvings=0, boundary=BOUNDARY_WALLS):
     p = bd_params()
     _check(load().bd_default_params(ctypes.byref(p)), "bd_default_params")
     p.n, p.n_species, p.a = int(n), int(n_species), float(a)
@@ -160,6 +165,7 @@ def make_params(n, L=None, rho=None, a=1.0, law=LAW_NONE, alpha=(0, 0, 0, 0), n_
     p.max_corr_iters, p.max_flip_rounds = int(max_corr_iters), int(max_flip_rounds)
     p.literal_noise, p.step0 = int(literal_noise), int(step0)
     p.max_dt_halvings = int(max_dt_halvings)
+    p.boundary = int(boundary)
     return p
 
 
@@ -233,6 +239,22 @@ class System:
         _check(load().bd_get_state(self.h, _ptr(xy), _ptr(th), _ptr(sp), _ptr(tri),
                                    ctypes.byref(nt), ctypes.byref(stp)), "bd_get_state")
         return dict(xy=xy, theta=th, species=sp, tri=tri, n_tri=nt.value, step=stp.value)
+
+    def tri_shifts(self, replica=-1):
+        """Corner image shifts (n_tri, 3, 2) of the triangulation (periodic box)."""
+        nt = self.n_tri if replica < 0 else self.replica_sizes()[replica][1]
+        sh = np.zeros((nt, 3, 2), dtype=np.int8)
+        _check(load().bd_get_tri_shifts(self.h, int(replica), _ptr(sh)), "bd_get_tri_shifts")
+        return sh.astype(np.int64)
+
+    def replica_sizes(self):
+        out = []
+        for r in range(self.R):
+            nn, nt, LL = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+            _check(load().bd_get_replica(self.h, r, None, None, None, ctypes.byref(nt), ctypes.byref(nn),
+                                         ctypes.byref(LL)), "bd_get_replica")
+            out.append((nn.value, nt.value, LL.value))
+        return out
 
     def set_state(self, xy, theta=None):
         xy = np.ascontiguousarray(xy, dtype=np.float64)
@@ -392,6 +414,20 @@ def triangulate(xy, L, a=1.0):
     _check(load().bd_triangulate(n, _ptr(xy), float(L), float(a), _ptr(grid), _ptr(tri),
                                  ctypes.byref(nt)), "bd_triangulate")
     return tri[: nt.value], grid
+
+
+def triangulate_periodic(xy, L):
+    """Host-side torus triangulation (bd_triangulate_periodic): returns
+    (triangles (2n, 3), corner shifts (2n, 3, 2), centres on the grid in [0, L))."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    n = len(xy)
+    tri = np.zeros((2 * n, 3), dtype=np.int32)
+    sh = np.zeros((2 * n, 3, 2), dtype=np.int8)
+    grid = np.zeros_like(xy)
+    nt = ctypes.c_int32()
+    _check(load().bd_triangulate_periodic(n, _ptr(xy), float(L), _ptr(grid), _ptr(tri), _ptr(sh),
+                                          ctypes.byref(nt)), "bd_triangulate_periodic")
+    return tri[: nt.value], sh[: nt.value].astype(np.int64), grid
 
 
 def forces_noalloc(n, xy_dev_ptr, species_dev_ptr, alpha, F_dev_ptr, stream=None):

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <new>
 #include <numeric>
+#include <limits>
 #include <vector>
 
 #include "bd_handle.h"
@@ -31,6 +32,10 @@ void make_ghosts(double L, double a, std::vector<double> &gx, std::vector<double
 double ghost_extent(double L, double a);
 int rsa_place(int n, double lo, double hi, double dmin, uint64_t seed, std::vector<double> &xy);
 int any_overlap(int n, const double *xy, double lo, double hi, double dmin);
+int any_overlap_periodic(int n, const double *xy, double L, double dmin);
+int build_torus_delaunay(const double *X, const double *Y, const std::vector<int> &ids, double L,
+                         const bdpred::Grid &grid, std::vector<int> &V, std::vector<int> &S,
+                         std::vector<int> &N);
 uint64_t hilbert_index(uint32_t x, uint32_t y);
 }  // namespace bdhost
 
@@ -65,7 +70,17 @@ int grid_shift_for(double E) {
 int grid_shift(double L, double a) { return grid_shift_for(bdhost::ghost_extent(L, a)); }
 
 double box_side(const bd_params &p) {
-  return p.box_L > 0 ? p.box_L : sqrt((double)p.n * M_PI * p.a * p.a / p.area_fraction);
+  const double L = p.box_L > 0 ? p.box_L : sqrt((double)p.n * M_PI * p.a * p.a / p.area_fraction);
+  // periodic box: a side exactly representable in FP32, so that the sweeps'
+  // minimum-image subtractions of L are exact
+  return p.boundary == BD_BOUNDARY_PERIODIC ? (double)(float)L : L;
+}
+
+// largest coordinate magnitude the predicates see: ghost points (walls) or
+// corners lifted by one box side (periodic)
+double coord_extent(const bd_params &p) {
+  const double L = box_side(p);
+  return p.boundary == BD_BOUNDARY_PERIODIC ? 4.0 * ceil(L) + 8.0 : bdhost::ghost_extent(L, p.a);
 }
 
 int validate(const bd_params *p) {
@@ -88,10 +103,25 @@ int validate(const bd_params *p) {
   if (p->overlap_mode < BD_OVERLAP_DELAUNAY || p->overlap_mode > BD_OVERLAP_VERLET) return BD_ERR_ARG;
   if (p->overlap_mode == BD_OVERLAP_VERLET && p->law != BD_LAW_SHORT) return BD_ERR_UNSUPPORTED;
   if (p->max_dt_halvings < 0 || p->max_dt_halvings > 20) return BD_ERR_ARG;
+  if (p->boundary < BD_BOUNDARY_WALLS || p->boundary > BD_BOUNDARY_PERIODIC) return BD_ERR_ARG;
+  if (p->boundary == BD_BOUNDARY_PERIODIC) {
+    if (p->n < 16) return BD_ERR_UNSUPPORTED;
+    const double L = box_side(*p);
+    if (!(L >= 16.0 * p->a) || !(L < 1e7)) return BD_ERR_UNSUPPORTED;
+    if (p->law == BD_LAW_SHORT && L < 3.0 * (p->r_cut + p->skin)) return BD_ERR_UNSUPPORTED;
+  }
   return BD_OK;
 }
 
 double snap_host(double v, double q, double inv_q) { return nearbyint(v * inv_q) * q; }
+
+// a periodic coordinate in [0, L) on the grid (L is a multiple of q)
+double periodic_coord(double v, double L, double q, double inv_q) {
+  double y = snap_host(v - L * floor(v / L), q, inv_q);
+  if (y >= L) y -= L;
+  if (y < 0.0) y += L;
+  return y;
+}
 
 // Build the long-range work items: every i block of a long-range replica
 // against chunks of at most `tiles` j tiles of the same replica.
@@ -272,14 +302,19 @@ cudaError_t use_variant(bd_handle *h, int variant, int tiles) {
 // chunk sizes; a single system also tries the wave-filling chunk size.
 cudaError_t autotune(bd_handle *h) {
   std::vector<int2> cand;
-  if (h->reps.size() == 1) {
+  if (h->c.any_periodic) {
+    // periodic boxes: the scalar one-sided sweep (minimum images), chunk sizes only
+    for (int t : {2, 4, 8, 16, 32, 64}) cand.push_back(make_int2(0, t));
+    if (h->reps.size() == 1) cand.push_back(make_int2(0, single_system_tiles(h)));
+  } else if (h->reps.size() == 1) {
     cand.push_back(make_int2(1, single_system_tiles(h)));
   } else {
     for (int t : {2, 4, 8, 16, 32, 64}) cand.push_back(make_int2(0, t));
     for (int t : {2, 4, 8, 16, 32, 64}) cand.push_back(make_int2(1, t));
   }
-  for (int v : {2, 3})
-    for (int t : {2, 4, 8, 16, 32}) cand.push_back(make_int2(v, t));
+  if (!h->c.any_periodic)
+    for (int v : {2, 3})
+      for (int t : {2, 4, 8, 16, 32}) cand.push_back(make_int2(v, t));
   float best_ms = 1e30f;
   int2 best = cand[0];
   cudaEvent_t a, b;
@@ -347,7 +382,7 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
 
   // ---- position grid shared by all replicas ----
   double E = 0.0;
-  for (const Spec &s : specs) E = std::max(E, bdhost::ghost_extent(box_side(s.p), a));
+  for (const Spec &s : specs) E = std::max(E, coord_extent(s.p));
   const int s_shift = grid_shift_for(E);
   const double q = ldexp(1.0, -s_shift), inv_q = ldexp(1.0, s_shift);
 
@@ -364,8 +399,9 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     RH.ext_base = ext;
     ext += p.n;
     RH.L = box_side(p);
-    RH.wall_lo = ceil(p.a * inv_q) * q;
-    RH.wall_hi = floor((RH.L - p.a) * inv_q) * q;
+    RH.periodic = p.boundary == BD_BOUNDARY_PERIODIC;
+    RH.wall_lo = RH.periodic ? 0.0 : ceil(p.a * inv_q) * q;
+    RH.wall_hi = RH.periodic ? RH.L : floor((RH.L - p.a) * inv_q) * q;
     if (!(RH.wall_hi > RH.wall_lo)) { delete h; return BD_ERR_ARG; }
     std::vector<double> &xy = xyr[r];
     xy.resize(2 * (size_t)p.n);
@@ -375,17 +411,29 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
       delete h;
       return BD_ERR_ARG;
     }
-    for (size_t k = 0; k < xy.size(); ++k)
-      if (!isfinite(xy[k]) || xy[k] < p.a - 1e-9 * RH.L || xy[k] > RH.L - p.a + 1e-9 * RH.L) {
+    if (RH.periodic) {
+      // any real coordinate: brought into [0, L) on the grid
+      for (size_t k = 0; k < xy.size(); ++k) {
+        if (!isfinite(xy[k])) { delete h; return BD_ERR_INIT_OVERLAP; }
+        xy[k] = periodic_coord(xy[k], RH.L, q, inv_q);
+      }
+      if (bdhost::any_overlap_periodic(p.n, xy.data(), RH.L, 2.0 * p.a * (1.0 - 1e-12))) {
         delete h;
         return BD_ERR_INIT_OVERLAP;
       }
-    if (bdhost::any_overlap(p.n, xy.data(), 0.0, RH.L, 2.0 * p.a * (1.0 - 1e-12))) {
-      delete h;
-      return BD_ERR_INIT_OVERLAP;
+    } else {
+      for (size_t k = 0; k < xy.size(); ++k)
+        if (!isfinite(xy[k]) || xy[k] < p.a - 1e-9 * RH.L || xy[k] > RH.L - p.a + 1e-9 * RH.L) {
+          delete h;
+          return BD_ERR_INIT_OVERLAP;
+        }
+      if (bdhost::any_overlap(p.n, xy.data(), 0.0, RH.L, 2.0 * p.a * (1.0 - 1e-12))) {
+        delete h;
+        return BD_ERR_INIT_OVERLAP;
+      }
+      for (size_t k = 0; k < xy.size(); ++k)
+        xy[k] = std::min(RH.wall_hi, std::max(RH.wall_lo, snap_host(xy[k], q, inv_q)));
     }
-    for (size_t k = 0; k < xy.size(); ++k)
-      xy[k] = std::min(RH.wall_hi, std::max(RH.wall_lo, snap_host(xy[k], q, inv_q)));
     spr[r].assign(p.n, 0);
     if (specs[r].sp)
       for (int i = 0; i < p.n; ++i) {
@@ -468,7 +516,22 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
           iperm.push_back(-1);
         }
       }
-      iorg.push_back(m ? make_float2((float)nearbyint(sx / m), (float)nearbyint(sy / m)) : make_float2(0.f, 0.f));
+      if (RH.periodic && m) {
+        // periodic box: a block may straddle an edge; its origin is the mean
+        // of its disks' minimum images about its first disk (the patch
+        // centre), which the sweeps re-centre on with minimum images
+        const int e0 = by_h[b * BD_IB];
+        double mx = 0.0, my = 0.0;
+        for (int k = b * BD_IB; k < std::min(n, (b + 1) * BD_IB); ++k) {
+          const int e = by_h[k];
+          double dx = xy[2 * e] - xy[2 * e0], dy = xy[2 * e + 1] - xy[2 * e0 + 1];
+          mx += dx - RH.L * nearbyint(dx / RH.L);
+          my += dy - RH.L * nearbyint(dy / RH.L);
+        }
+        iorg.push_back(make_float2((float)nearbyint(xy[2 * e0] + mx / m), (float)nearbyint(xy[2 * e0 + 1] + my / m)));
+      } else {
+        iorg.push_back(m ? make_float2((float)nearbyint(sx / m), (float)nearbyint(sy / m)) : make_float2(0.f, 0.f));
+      }
     }
     iblock += nib;
     byhr[r].resize(n);
@@ -486,7 +549,7 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
   int ng_total = 0;
   std::vector<std::vector<double>> gxr(R), gyr(R);
   for (int r = 0; r < R; ++r) {
-    bdhost::make_ghosts(h->reps[r].L, a, gxr[r], gyr[r]);
+    if (!h->reps[r].periodic) bdhost::make_ghosts(h->reps[r].L, a, gxr[r], gyr[r]);   // a torus needs none
     h->reps[r].ghost_base = np + ng_total;
     h->reps[r].ng = (int)gxr[r].size();
     ng_total += h->reps[r].ng;
@@ -521,20 +584,29 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     RepHost &RH = h->reps[r];
     std::vector<int> gids(RH.ng);
     for (int k = 0; k < RH.ng; ++k) gids[k] = RH.ghost_base + k;
-    std::vector<int> V, N;
-    if (bdhost::build_delaunay(X.data(), Y.data(), grid, byhr[r], gids, V, N) != 0) {
+    std::vector<int> V, N, S;
+    if (RH.periodic) {
+      if (bdhost::build_torus_delaunay(X.data(), Y.data(), byhr[r], RH.L, grid, V, S, N) != 0) {
+        delete h;
+        return BD_ERR_TRIANGULATION;
+      }
+    } else if (bdhost::build_delaunay(X.data(), Y.data(), grid, byhr[r], gids, V, N) != 0) {
       delete h;
       return BD_ERR_TRIANGULATION;
     }
     const int nt_r = (int)(V.size() / 3);
-    if (nt_r != 2 * (RH.n + RH.ng) - 6) {
+    if (nt_r != (RH.periodic ? 2 * RH.n : 2 * (RH.n + RH.ng) - 6)) {
       delete h;
       return BD_ERR_TRIANGULATION;
     }
     RH.tri_base = tri_base;
     RH.nt = nt_r;
     for (int t = 0; t < nt_r; ++t) {
-      tv_all.push_back(make_int4(V[3 * t], V[3 * t + 1], V[3 * t + 2], 0));
+      int w = 0;
+      if (RH.periodic)
+        for (int k = 0; k < 3; ++k)
+          w |= ((S[6 * t + 2 * k] & 3) << (8 + 4 * k)) | ((S[6 * t + 2 * k + 1] & 3) << (10 + 4 * k));
+      tv_all.push_back(make_int4(V[3 * t], V[3 * t + 1], V[3 * t + 2], w));
       auto sh = [&](int o) { return o < 0 ? -1 : o + 3 * tri_base; };
       tn_all.push_back(make_int4(sh(N[3 * t]), sh(N[3 * t + 1]), sh(N[3 * t + 2]), 0));
     }
@@ -592,6 +664,12 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     B.L = RH.L;
     B.wall_lo = RH.wall_lo;
     B.wall_hi = RH.wall_hi;
+    B.periodic = RH.periodic ? 1 : 0;
+    B.Lf = (float)RH.L;
+    B.hLf = RH.periodic ? 0.5f * (float)RH.L : std::numeric_limits<float>::infinity();
+    B.invLf = RH.periodic ? (float)(1.0 / RH.L) : 0.f;
+    B.LQ = (long long)nearbyint(RH.L * inv_q);
+    if (RH.periodic) c.any_periodic = 1;
     B.dt = p.dt;
     B.amp = p.literal_noise ? sqrt(p.D * p.dt) : sqrt(2.0 * p.D * p.dt);
     B.amp_r = sqrt(2.0 * p.Dr * p.dt);
@@ -614,6 +692,8 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     B.nchunk = 1;
     if (p.law == BD_LAW_SHORT) {
       B.ncell = std::max(1, std::min(1 << 14, (int)floor(RH.L / (p.r_cut + p.skin))));
+      // periodic cells wrap around: at least three per side keep the 3 x 3
+      // neighbourhoods free of repeated cells (validate() checks L)
       B.cell_size = RH.L / B.ncell;
       B.cell_base = cell_base;
       cell_base += B.ncell * B.ncell;
@@ -646,6 +726,10 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     BD_TRY(dalloc(h, &d.ext_id, (size_t)np));
     BD_TRY(dalloc(h, &d.rep_of, (size_t)np));
     BD_TRY(dalloc(h, &d.moved, nv));
+    if (c.any_periodic) {
+      BD_TRY(dalloc(h, &d.wrap, (size_t)np));
+      BD_TRY(cudaMemsetAsync(d.wrap, 0, (size_t)np, h->stream));
+    }
     BD_TRY(dalloc(h, &d.disp, (size_t)np));
     {
       BdRep *rp = nullptr;
@@ -780,12 +864,12 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
       if (c.precision == 1 || !c.any_long) {
         BD_TRY(use_variant(h, c.precision == 1 ? 1 : c.force_variant, R == 1 ? single_system_tiles(h) : 16));
       } else if (fv) {
-        const int v = std::min(3, std::max(0, atoi(fv)));
+        const int v = c.any_periodic ? 0 : std::min(3, std::max(0, atoi(fv)));
         const int t = ft && atoi(ft) > 0 ? atoi(ft) : (v >= 2 ? 8 : (R == 1 ? single_system_tiles(h) : 16));
         BD_TRY(use_variant(h, v, t));
       } else if (nmax * nmax > 180000000000LL) {
         // a launch takes more than ~50 ms: no timing at init
-        BD_TRY(use_variant(h, 2, 16));
+        BD_TRY(use_variant(h, c.any_periodic ? 0 : 2, c.any_periodic ? 64 : 16));
       } else {
         BD_TRY(autotune(h));
       }
@@ -1275,6 +1359,23 @@ int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32
   return BD_OK;
 }
 
+int bd_get_tri_shifts(bd_handle *h, int32_t r, int8_t *shifts) {
+  if (!h || !shifts || r >= (int)h->reps.size()) return BD_ERR_ARG;
+  if (h->c.overlap_verlet) return BD_OK;
+  const int base = r < 0 ? 0 : h->reps[r].tri_base, nt = r < 0 ? h->nt : h->reps[r].nt;
+  std::vector<int4> tv(nt);
+  cudaError_t e = cudaMemcpyAsync(tv.data(), h->d.tv + base, nt * sizeof(int4), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  auto f = [](int w, int bit) { return (int8_t)((((w >> bit) & 3) ^ 2) - 2); };
+  for (int t = 0; t < nt; ++t)
+    for (int k = 0; k < 3; ++k) {
+      shifts[6 * t + 2 * k] = f(tv[t].w, 8 + 4 * k);
+      shifts[6 * t + 2 * k + 1] = f(tv[t].w, 10 + 4 * k);
+    }
+  return BD_OK;
+}
+
 int bd_get_replica(bd_handle *h, int32_t r, double *xy, float *theta, int32_t *tri, int32_t *n_tri,
                    int32_t *n, double *L) {
   if (!h || r < 0 || r >= (int)h->reps.size()) return BD_ERR_ARG;
@@ -1316,8 +1417,19 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
   if (!h || !xy) return BD_ERR_ARG;
   const int np = h->np;
   const BdConst &c = h->c;
+  std::vector<double> wrapped;
   for (const RepHost &RH : h->reps) {
     const double *x = xy + 2 * (size_t)RH.ext_base;
+    if (RH.periodic) {
+      wrapped.resize(2 * (size_t)RH.n);
+      for (int i = 0; i < 2 * RH.n; ++i) {
+        if (!isfinite(x[i])) return BD_ERR_INIT_OVERLAP;
+        wrapped[i] = periodic_coord(x[i], RH.L, c.q, c.inv_q);
+      }
+      if (bdhost::any_overlap_periodic(RH.n, wrapped.data(), RH.L, c.sigma * (1.0 - 1e-12)))
+        return BD_ERR_INIT_OVERLAP;
+      continue;
+    }
     for (int i = 0; i < 2 * RH.n; ++i)
       if (!isfinite(x[i]) || x[i] < c.a - 1e-9 * RH.L || x[i] > RH.L - c.a + 1e-9 * RH.L)
         return BD_ERR_INIT_OVERLAP;
@@ -1327,8 +1439,13 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
     const double *x = xy + 2 * (size_t)RH.ext_base;
     for (int i = 0; i < RH.n; ++i) {
       const int k = h->int_of_ext[RH.ext_base + i];
-      h->host_pos[2 * k] = std::min(RH.wall_hi, std::max(RH.wall_lo, snap_host(x[2 * i], c.q, c.inv_q)));
-      h->host_pos[2 * k + 1] = std::min(RH.wall_hi, std::max(RH.wall_lo, snap_host(x[2 * i + 1], c.q, c.inv_q)));
+      if (RH.periodic) {
+        h->host_pos[2 * k] = periodic_coord(x[2 * i], RH.L, c.q, c.inv_q);
+        h->host_pos[2 * k + 1] = periodic_coord(x[2 * i + 1], RH.L, c.q, c.inv_q);
+      } else {
+        h->host_pos[2 * k] = std::min(RH.wall_hi, std::max(RH.wall_lo, snap_host(x[2 * i], c.q, c.inv_q)));
+        h->host_pos[2 * k + 1] = std::min(RH.wall_hi, std::max(RH.wall_lo, snap_host(x[2 * i + 1], c.q, c.inv_q)));
+      }
     }
   }
   cudaStream_t st = h->stream;
@@ -1345,6 +1462,8 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
     e = cudaMemcpyAsync(d.theta, th.data(), (size_t)np * sizeof(float), cudaMemcpyHostToDevice, st);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(d.moved, 1, (size_t)np, st);
+  // periodic box: a new coordinate across an edge from the old one re-entered
+  if (e == cudaSuccess && c.any_periodic) e = bd_launch_periodic_wraps(d, c, st);
   if (e == cudaSuccess) e = bd_launch_work_copy(d, c, st);
   if (e == cudaSuccess) e = reset_stats(h);
   if (e == cudaSuccess && !c.overlap_verlet) e = bd_launch_dt(d, c, 1, st, h->dt_grid, h->dt_block);
@@ -1500,6 +1619,41 @@ int bd_triangulate(int32_t n, const double *xy, double L, double a, double *xy_g
   if (nt != 2 * (n + ng) - 6) return BD_ERR_TRIANGULATION;
   memcpy(tri, V.data(), sizeof(int) * V.size());
   if (n_tri) *n_tri = nt;
+  return BD_OK;
+}
+
+int bd_triangulate_periodic(int32_t n, const double *xy, double L, double *xy_grid, int32_t *tri,
+                            int8_t *shifts, int32_t *n_tri) {
+  if (n < 3 || !xy || !tri || !shifts || !(L > 0) || !(L < 1e7)) return BD_ERR_ARG;
+  bd_params p;
+  bd_default_params(&p);
+  p.boundary = BD_BOUNDARY_PERIODIC;
+  p.box_L = L;
+  p.n = n;
+  const double Lp = box_side(p);
+  const int s = grid_shift_for(coord_extent(p));
+  const double q = ldexp(1.0, -s), inv_q = ldexp(1.0, s);
+  std::vector<double> X(n), Y(n);
+  for (int i = 0; i < n; ++i) {
+    if (!isfinite(xy[2 * i]) || !isfinite(xy[2 * i + 1])) return BD_ERR_ARG;
+    X[i] = periodic_coord(xy[2 * i], Lp, q, inv_q);
+    Y[i] = periodic_coord(xy[2 * i + 1], Lp, q, inv_q);
+    if (xy_grid) {
+      xy_grid[2 * i] = X[i];
+      xy_grid[2 * i + 1] = Y[i];
+    }
+  }
+  std::vector<int> ids(n);
+  std::iota(ids.begin(), ids.end(), 0);
+  bdpred::Grid grid;
+  grid.q = q;
+  grid.inv_q = inv_q;
+  grid.s = s;
+  std::vector<int> V, S, N;
+  if (bdhost::build_torus_delaunay(X.data(), Y.data(), ids, Lp, grid, V, S, N) != 0) return BD_ERR_TRIANGULATION;
+  memcpy(tri, V.data(), sizeof(int) * V.size());
+  for (size_t k = 0; k < S.size(); ++k) shifts[k] = (int8_t)S[k];
+  if (n_tri) *n_tri = (int32_t)(V.size() / 3);
   return BD_OK;
 }
 

@@ -11,6 +11,7 @@
 struct RepHost {
   bd_params p;
   double L = 0, wall_lo = 0, wall_hi = 0;
+  bool periodic = false;       // periodic box (no ghost points, torus triangulation)
   int n = 0;                   // disks
   int ext_base = 0;            // first index in the concatenated external arrays
   int slot_begin = 0, slot_end = 0;

@@ -24,6 +24,11 @@
 // triangle flag bits stored in tv[t].w
 #define BD_TRI_INVERTED 1
 #define BD_TRI_DIRTY 2
+#define BD_TRI_FLAGS 3
+// periodic box: corner k of a triangle sits at pos[v_k] + L (sx_k, sy_k);
+// each component is a 2-bit two's-complement field of tv[t].w (0, 1 = +1,
+// 3 = -1): sx_k at bit 8 + 4k, sy_k at bit 10 + 4k.  Zero for walls.
+#define BD_TRI_SHIFT_BITS 0xFFF00
 
 // device control block of the triangulation kernel
 struct BdCtl {
@@ -62,6 +67,8 @@ struct BdCtl {
   int log_overflow;
   int log_step;                    // rollout step being recorded (-1 = none)
   long long step_dev;              // index of the next step (advanced by the triangulation kernel)
+  int n_wrapped;                   // periodic box: disks that re-entered in the last move (consumed
+                                   // by the triangulation kernel's shift pass; not a statistic)
 };
 
 // counter slots within BdCtl::cnt[phase % 4]
@@ -71,6 +78,11 @@ enum { C_INV = 0, C_REJECT = 1, C_FLIPS = 2, C_OVERLAP = 3, C_CAND = 4 };
 // single system is R = 1).  Device-resident table read by the kernels.
 struct BdRep {
   double L, wall_lo, wall_hi;
+  // periodic box (Sec. 2.1): the side is a multiple of the position grid and
+  // exactly representable in FP32 (Lf), LQ = L / q
+  int periodic;
+  float Lf, hLf, invLf;
+  long long LQ;
   double dt, amp, amp_r, v0;
   double eps, kappa, r_cut, skin, rl2, cell_size;
   double alpha_d[4];
@@ -93,6 +105,7 @@ struct BdDev {
   int *ext_id;             // index within its replica (-1 = empty slot): the Philox counter
   int *rep_of;             // replica of each slot (-1 = empty slot)
   uint8_t *moved;
+  uint8_t *wrap;           // periodic box: re-entries of the last move (bits 0-1 x, 2-3 y; 1 = -L, 3 = +L)
   double2 *disp;
   const BdRep *rep;        // [R]
   // triangulation (corner table), all replicas
@@ -133,6 +146,7 @@ struct BdConst {
   int max_nchunk;          // partial-force slots
   int ncell_total;         // short range: cells of all replicas
   int any_long, any_short;
+  int any_periodic;        // some replica has a periodic box
   int precision, n_species;
   double a, sigma;
   double q, inv_q;
@@ -161,6 +175,9 @@ int bd_dt_grid(int *grid, int *block);
 int bd_dt_grid_for(int work_items, int *grid, int *block);
 int bd_force_blocks_per_sm(int variant);
 cudaError_t bd_launch_work_copy(const BdDev &d, const BdConst &c, cudaStream_t s);
+// periodic box, after new positions were set (pos0 = old): the re-entry of
+// each disk (wrap bytes, n_wrapped) for the triangulation's corner shifts
+cudaError_t bd_launch_periodic_wraps(const BdDev &d, const BdConst &c, cudaStream_t s);
 cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t s);
 int bd_short_launches();
 cudaError_t bd_launch_force_sum(const BdDev &d, const BdConst &c, double2 *out, cudaStream_t s);

@@ -66,6 +66,16 @@ __device__ __forceinline__ float2 grid_split(long long X, int s) {
   return make_float2(X == 0 ? 0.f : __int_as_float(__float_as_int(h) - (s << 23)), grid_to_float(r, s));
 }
 
+// periodic re-entry in grid units (Sec. 2.1): X, Y brought into [0, LQ).
+// Returns the wrap code: bits 0-1 (x) and 2-3 (y) hold k in 2-bit two's
+// complement, where the stored coordinate is the geometric one less L k.
+__device__ __forceinline__ int wrap_grid(long long LQ, long long &X, long long &Y) {
+  int f = 0;
+  if (X < 0) { X += LQ; f |= 3; } else if (X >= LQ) { X -= LQ; f |= 1; }
+  if (Y < 0) { Y += LQ; f |= 12; } else if (Y >= LQ) { Y -= LQ; f |= 4; }
+  return f;
+}
+
 // mirror reflection at the walls in grid units (flag bits as reflect())
 __device__ __forceinline__ int reflect_grid(long long lo, long long hi, long long &X, long long &Y) {
   int f = 0;

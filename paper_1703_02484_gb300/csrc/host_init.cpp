@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <unordered_map>
 #include <vector>
 
 #include "philox.cuh"
@@ -259,6 +260,195 @@ int build_delaunay(const double *X, const double *Y, const bdpred::Grid &grid,
   }
   V.swap(T.V);
   N.swap(T.N);
+  return 0;
+}
+
+// ---- periodic box (Sec. 2.1; the triangulation lives on a flat torus, Sec. 4.1) ----
+//
+// The torus triangulation is read off the planar Delaunay triangulation of
+// the points plus their images within a band of width w around the box
+// (shifted by L in x, y or both), closed by four far corners.  A torus
+// triangle is kept once, as the lifted triangle whose smallest point id sits
+// in the box itself (shift 0).  Corners carry integer image shifts: corner k
+// lies at (X, Y)[id] + L shift_k; each triangle is stored with corner 0 at
+// shift 0.  The result is accepted only if it is a closed torus triangulation
+// (2n triangles, every edge shared by exactly two, matched by vertex pair
+// and relative shift), every triangle is counter-clockwise and every edge is
+// locally Delaunay (exact predicates on the lifted grid coordinates); a band
+// too narrow for that is doubled and the build repeated.
+
+namespace {
+
+struct TorusPt {
+  int id, sx, sy;
+};
+
+inline uint64_t edge_key(int u, int w, int sx, int sy) {
+  return ((uint64_t)(uint32_t)u << 34) | ((uint64_t)(uint32_t)w << 6) | ((uint64_t)(sx + 2) << 3) |
+         (uint64_t)(sy + 2);
+}
+
+}  // namespace
+
+int build_torus_delaunay(const double *X, const double *Y, const std::vector<int> &ids, double L,
+                         const bdpred::Grid &grid, std::vector<int> &V, std::vector<int> &S,
+                         std::vector<int> &N) {
+  const int n = (int)ids.size();
+  if (n < 3) return -4;
+  const int64_t LQ = bdpred::to_int(L, grid);
+  double w = std::min(L, 8.0 * L / sqrt((double)n) + 1.0);
+  for (int attempt = 0; attempt < 6; ++attempt, w = std::min(L, 2.0 * w)) {
+    // points: the box's own, then images within the band, then 4 far corners
+    std::vector<TorusPt> pts;
+    std::vector<double> px, py;
+    pts.reserve(n + n / 2);
+    for (int k = 0; k < n; ++k) {
+      const int i = ids[k];
+      for (int sy = -1; sy <= 1; ++sy)
+        for (int sx = -1; sx <= 1; ++sx) {
+          const double x = X[i] + sx * L, y = Y[i] + sy * L;
+          if (x < -w || x >= L + w || y < -w || y >= L + w) continue;
+          if (sx == 0 && sy == 0) continue;
+          pts.push_back({i, sx, sy});
+          px.push_back(x);
+          py.push_back(y);
+        }
+    }
+    std::vector<TorusPt> all;
+    std::vector<double> ax, ay;
+    all.reserve(n + pts.size() + 4);
+    for (int k = 0; k < n; ++k) {
+      all.push_back({ids[k], 0, 0});
+      ax.push_back(X[ids[k]]);
+      ay.push_back(Y[ids[k]]);
+    }
+    for (size_t k = 0; k < pts.size(); ++k) {
+      all.push_back(pts[k]);
+      ax.push_back(px[k]);
+      ay.push_back(py[k]);
+    }
+    const int m = (int)all.size();
+    const double F = 3.0 * L + 3.0 * w;
+    const double cx[4] = {-F, L + F, L + F, -F}, cy[4] = {-F, -F, L + F, L + F};
+    for (int k = 0; k < 4; ++k) {
+      all.push_back({-1, 0, 0});
+      ax.push_back(cx[k]);
+      ay.push_back(cy[k]);
+    }
+    std::vector<int> order(m), gids(4);
+    for (int k = 0; k < m; ++k) order[k] = k;
+    // insertion in a locality order keeps the point-location walks short
+    std::vector<uint64_t> hk(m);
+    for (int k = 0; k < m; ++k) {
+      uint32_t ux = (uint32_t)std::min(65535.0, std::max(0.0, (ax[k] + w) / (L + 2 * w) * 65536.0));
+      uint32_t uy = (uint32_t)std::min(65535.0, std::max(0.0, (ay[k] + w) / (L + 2 * w) * 65536.0));
+      hk[k] = hilbert_index(ux, uy);
+    }
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return hk[a] != hk[b] ? hk[a] < hk[b] : a < b; });
+    for (int k = 0; k < 4; ++k) gids[k] = m + k;
+    std::vector<int> PV, PN;
+    if (build_delaunay(ax.data(), ay.data(), grid, order, gids, PV, PN) != 0) return -2;
+    // keep one lift per torus triangle
+    V.clear();
+    S.clear();
+    const int ntp = (int)(PV.size() / 3);
+    for (int t = 0; t < ntp; ++t) {
+      const int a = PV[3 * t], b = PV[3 * t + 1], c = PV[3 * t + 2];
+      if (a >= m || b >= m || c >= m) continue;
+      const TorusPt *q[3] = {&all[a], &all[b], &all[c]};
+      int k0 = 0;
+      for (int k = 1; k < 3; ++k)
+        if (q[k]->id < q[k0]->id) k0 = k;
+      if (q[k0]->sx != 0 || q[k0]->sy != 0) continue;
+      // rotate so that corner 0 is the one at shift 0 with the smallest id
+      for (int k = 0; k < 3; ++k) {
+        const TorusPt *r = q[(k0 + k) % 3];
+        V.push_back(r->id);
+        S.push_back(r->sx);
+        S.push_back(r->sy);
+      }
+    }
+    const int T = (int)(V.size() / 3);
+    if (T != 2 * n) continue;
+    // neighbours: the edge opposite corner k runs from corner k+1 to k+2 with
+    // relative shift s; its twin in the neighbour runs back with shift -s
+    std::unordered_map<uint64_t, int> dir;
+    dir.reserve(3 * (size_t)T * 2);
+    bool ok = true;
+    for (int t = 0; t < T && ok; ++t)
+      for (int k = 0; k < 3; ++k) {
+        const int c1 = 3 * t + (k + 1) % 3, c2 = 3 * t + (k + 2) % 3;
+        const uint64_t key = edge_key(V[c1], V[c2], S[2 * c2] - S[2 * c1], S[2 * c2 + 1] - S[2 * c1 + 1]);
+        if (!dir.emplace(key, 3 * t + k).second) { ok = false; break; }
+      }
+    if (!ok) continue;
+    N.assign(3 * (size_t)T, -1);
+    for (int t = 0; t < T && ok; ++t)
+      for (int k = 0; k < 3; ++k) {
+        const int c1 = 3 * t + (k + 1) % 3, c2 = 3 * t + (k + 2) % 3;
+        auto it = dir.find(edge_key(V[c2], V[c1], S[2 * c1] - S[2 * c2], S[2 * c1 + 1] - S[2 * c2 + 1]));
+        if (it == dir.end()) { ok = false; break; }
+        N[3 * t + k] = it->second;
+      }
+    if (!ok) continue;
+    // exact checks on lifted grid coordinates
+    auto lx = [&](int c) { return bdpred::to_int(X[V[c]], grid) + (int64_t)S[2 * c] * LQ; };
+    auto ly = [&](int c) { return bdpred::to_int(Y[V[c]], grid) + (int64_t)S[2 * c + 1] * LQ; };
+    for (int t = 0; t < T && ok; ++t) {
+      const int c0 = 3 * t;
+      if (bdpred::orient_int(lx(c0), ly(c0), lx(c0 + 1), ly(c0 + 1), lx(c0 + 2), ly(c0 + 2)) <= 0) ok = false;
+      for (int k = 0; k < 3 && ok; ++k) {
+        const int o = N[3 * t + k], t1 = o / 3, k1 = o % 3;
+        // the neighbour's frame: its corner k1+2 is this triangle's corner k+1
+        const int cu = 3 * t + (k + 1) % 3, cu1 = 3 * t1 + (k1 + 2) % 3;
+        const int64_t ox = (int64_t)(S[2 * cu] - S[2 * cu1]) * LQ, oy = (int64_t)(S[2 * cu + 1] - S[2 * cu1 + 1]) * LQ;
+        if (bdpred::incircle_int(lx(c0), ly(c0), lx(c0 + 1), ly(c0 + 1), lx(c0 + 2), ly(c0 + 2), lx(o) + ox,
+                                 ly(o) + oy) > 0)
+          ok = false;
+      }
+    }
+    if (ok) return 0;
+    if (w >= L) break;
+  }
+  return -5;
+}
+
+// periodic minimum-image overlap check (centres in [0, L)): 1 if some pair
+// is closer than dmin
+int any_overlap_periodic(int n, const double *xy, double L, double dmin) {
+  int nc = std::max(1, std::min(4096, (int)floor(L / dmin)));
+  if (nc < 3) {
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < i; ++j) {
+        double dx = xy[2 * j] - xy[2 * i], dy = xy[2 * j + 1] - xy[2 * i + 1];
+        dx -= L * nearbyint(dx / L);
+        dy -= L * nearbyint(dy / L);
+        if (dx * dx + dy * dy < dmin * dmin) return 1;
+      }
+    return 0;
+  }
+  const double cs = L / nc;
+  std::vector<std::vector<int>> cells((size_t)nc * nc);
+  for (int i = 0; i < n; ++i) {
+    int cx = std::min(nc - 1, std::max(0, (int)(xy[2 * i] / cs)));
+    int cy = std::min(nc - 1, std::max(0, (int)(xy[2 * i + 1] / cs)));
+    cells[(size_t)cx * nc + cy].push_back(i);
+  }
+  for (int i = 0; i < n; ++i) {
+    int cx = std::min(nc - 1, std::max(0, (int)(xy[2 * i] / cs)));
+    int cy = std::min(nc - 1, std::max(0, (int)(xy[2 * i + 1] / cs)));
+    for (int gx = cx - 1; gx <= cx + 1; ++gx)
+      for (int gy = cy - 1; gy <= cy + 1; ++gy) {
+        const int ux = (gx + nc) % nc, uy = (gy + nc) % nc;
+        for (int j : cells[(size_t)ux * nc + uy]) {
+          if (j >= i) continue;
+          double dx = xy[2 * j] - xy[2 * i], dy = xy[2 * j + 1] - xy[2 * i + 1];
+          dx -= L * nearbyint(dx / L);
+          dy -= L * nearbyint(dy / L);
+          if (dx * dx + dy * dy < dmin * dmin) return 1;
+        }
+      }
+  }
   return 0;
 }
 

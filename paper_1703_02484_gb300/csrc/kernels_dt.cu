@@ -128,6 +128,60 @@ __device__ __forceinline__ int incircle_v(const Ctx &x, int a, int b, int c, int
   return bdpred::incircle(pa.x, pa.y, pb.x, pb.y, pc.x, pc.y, pp.x, pp.y, x.g);
 }
 
+// ---- periodic box: image shifts of triangle corners (Sec. 2.1, 4.1) ----
+// Corner k of a triangle lies at pos[v_k] + L (sx_k, sy_k); the shifts are
+// 2-bit two's-complement fields of tv.w (BD_TRI_SHIFT_BITS), all zero with
+// walls, and corner 0 is kept at shift 0.  Straddling triangles are decided
+// by the exact integer predicates on lifted grid coordinates.
+__device__ __forceinline__ int sh2(int w, int bit) { return (((w >> bit) & 3) ^ 2) - 2; }
+__device__ __forceinline__ int shx(int w, int k) { return sh2(w, 8 + 4 * k); }
+__device__ __forceinline__ int shy(int w, int k) { return sh2(w, 10 + 4 * k); }
+__device__ __forceinline__ int put_shift(int k, int sx, int sy) {
+  return ((sx & 3) << (8 + 4 * k)) | ((sy & 3) << (10 + 4 * k));
+}
+// the wrap of the last move of disk v: stored = geometric - L k
+__device__ __forceinline__ int wrapx(uint8_t w) { return ((w & 3) ^ 2) - 2; }
+__device__ __forceinline__ int wrapy(uint8_t w) { return (((w >> 2) & 3) ^ 2) - 2; }
+
+struct Lift {
+  long long x, y;
+};
+
+__device__ __forceinline__ Lift lift(const Ctx &x, int v, int sx, int sy, long long LQ) {
+  const double2 p = x.d.pos[v];
+  return {bdpred::to_int(p.x, x.g) + sx * LQ, bdpred::to_int(p.y, x.g) + sy * LQ};
+}
+
+__device__ __forceinline__ long long rep_LQ(const Ctx &x, int v) { return x.d.rep[x.d.rep_of[v]].LQ; }
+
+// orientation of corners (a, b, c) with shifts (sa, sb, sc)
+__device__ __forceinline__ int orient_s(const Ctx &x, int a, int sax, int say, int b, int sbx, int sby, int c,
+                                        int scx, int scy) {
+  if ((sax | say | sbx | sby | scx | scy) == 0) return orient_v(x, a, b, c);
+  const long long LQ = rep_LQ(x, a);
+  const Lift A = lift(x, a, sax, say, LQ), B = lift(x, b, sbx, sby, LQ), C = lift(x, c, scx, scy, LQ);
+  return bdpred::orient_int(A.x, A.y, B.x, B.y, C.x, C.y);
+}
+
+// in-circle test of p (shift sp) against triangle t's corners (shifts in w)
+__device__ __forceinline__ int incircle_s(const Ctx &x, const int4 &v, int p, int spx, int spy) {
+  const int w = v.w;
+  if (((w & BD_TRI_SHIFT_BITS) | spx | spy) == 0) return incircle_v(x, v.x, v.y, v.z, p);
+  const long long LQ = rep_LQ(x, v.x);
+  const Lift A = lift(x, v.x, shx(w, 0), shy(w, 0), LQ), B = lift(x, v.y, shx(w, 1), shy(w, 1), LQ);
+  const Lift C = lift(x, v.z, shx(w, 2), shy(w, 2), LQ), P = lift(x, p, spx, spy, LQ);
+  return bdpred::incircle_int(A.x, A.y, B.x, B.y, C.x, C.y, P.x, P.y);
+}
+
+// shift, in the frame of triangle t (corner tab w), of the vertex opposite
+// the edge facing corner k, read from the neighbour (tab w1, corner k1):
+// t's corner k+1 is the neighbour's corner k1+2
+__device__ __forceinline__ void opp_shift(int w, int k, int w1, int k1, int &sx, int &sy) {
+  const int ku = (k + 1) % 3, ku1 = (k1 + 2) % 3;
+  sx = shx(w1, k1) + shx(w, ku) - shx(w1, ku1);
+  sy = shy(w1, k1) + shy(w, ku) - shy(w1, ku1);
+}
+
 __device__ __forceinline__ double snap(double v, const bdpred::Grid &g) {
   return __dmul_rn(rint(__dmul_rn(v, g.inv_q)), g.q);
 }
@@ -185,8 +239,30 @@ __device__ void flip_owned(const Ctx &x, int c0, int o0) {
   set_vk(N1, k1, 3 * t0 + k0);
   set_vk(N1, (k1 + 1) % 3, n_dc);
   set_vk(N1, (k1 + 2) % 3, n_ca);
-  V0.w = BD_TRI_DIRTY;
-  V1.w = BD_TRI_DIRTY;
+  // image shifts (periodic box): the new corners in t0's frame; d comes from
+  // t1's frame, offset by b's shift difference between the two frames
+  const int w0 = V0.w, w1 = V1.w;
+  int nw0 = BD_TRI_DIRTY, nw1 = BD_TRI_DIRTY;
+  if ((w0 | w1) & BD_TRI_SHIFT_BITS) {
+    const int Ax = shx(w0, k0), Ay = shy(w0, k0);
+    const int Bx = shx(w0, (k0 + 1) % 3), By = shy(w0, (k0 + 1) % 3);
+    const int Cx = shx(w0, (k0 + 2) % 3), Cy = shy(w0, (k0 + 2) % 3);
+    const int Dx = shx(w1, k1) + Bx - shx(w1, (k1 + 2) % 3), Dy = shy(w1, k1) + By - shy(w1, (k1 + 2) % 3);
+    // t0 = (b, d, a) at (k0, k0+1, k0+2); t1 = (c, a, d) at (k1, k1+1, k1+2)
+    int sx0[3], sy0[3], sx1[3], sy1[3];
+    sx0[k0] = Bx; sy0[k0] = By;
+    sx0[(k0 + 1) % 3] = Dx; sy0[(k0 + 1) % 3] = Dy;
+    sx0[(k0 + 2) % 3] = Ax; sy0[(k0 + 2) % 3] = Ay;
+    sx1[k1] = Cx; sy1[k1] = Cy;
+    sx1[(k1 + 1) % 3] = Ax; sy1[(k1 + 1) % 3] = Ay;
+    sx1[(k1 + 2) % 3] = Dx; sy1[(k1 + 2) % 3] = Dy;
+    for (int k = 0; k < 3; ++k) {
+      nw0 |= put_shift(k, sx0[k] - sx0[0], sy0[k] - sy0[0]);
+      nw1 |= put_shift(k, sx1[k] - sx1[0], sy1[k] - sy1[0]);
+    }
+  }
+  V0.w = nw0;
+  V1.w = nw1;
   x.d.tv[t0] = V0;
   x.d.tv[t1] = V1;
   x.d.tn[t0] = N0;
@@ -265,6 +341,34 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
 
   for (;;) {
     ++epoch;
+    // ---------------- W: shifts of triangles whose corners re-entered (periodic box) ----------------
+    if (fresh && c.any_periodic && *(volatile int *)&ctl->n_wrapped != 0) {
+      phase_begin(ctl, b);
+      for (int t = tid; t < x.T; t += nth) {
+        const int4 v = d.tv[t];
+        if (first) {
+          int4 vs = v;
+          vs.w = v.w & ~BD_TRI_FLAGS;
+          d.tv_snap[t] = vs;
+          d.tn_snap[t] = d.tn[t];
+        }
+        const uint8_t w0 = d.wrap[v.x], w1 = d.wrap[v.y], w2 = d.wrap[v.z];
+        if ((w0 | w1 | w2) == 0) continue;
+        // a corner stored L k lower than where it geometrically is: shift += k
+        const int kx[3] = {wrapx(w0), wrapx(w1), wrapx(w2)}, ky[3] = {wrapy(w0), wrapy(w1), wrapy(w2)};
+        int sx[3], sy[3];
+        for (int k = 0; k < 3; ++k) {
+          sx[k] = shx(v.w, k) + kx[k];
+          sy[k] = shy(v.w, k) + ky[k];
+        }
+        int nw = v.w & BD_TRI_FLAGS;
+        for (int k = 0; k < 3; ++k) nw |= put_shift(k, sx[k] - sx[0], sy[k] - sy[0]);
+        d.tv[t].w = nw;
+      }
+      if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+      if (lead) ctl->n_wrapped = 0;
+      first = false;
+    }
     // ---------------- P: check, mark, scan ----------------
     phase_begin(ctl, b);
     {
@@ -275,15 +379,16 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         const int4 nn = d.tn[t];
         if (first) {
           int4 vs = v;
-          vs.w = 0;
+          vs.w = v.w & ~BD_TRI_FLAGS;
           d.tv_snap[t] = vs;
           d.tn_snap[t] = nn;
         }
-        int fl = v.w;
+        int fl = v.w & BD_TRI_FLAGS;
         if (fresh && (d.moved[v.x] | d.moved[v.y] | d.moved[v.z])) {
-          const int o = orient_v(x, v.x, v.y, v.z);
+          const int o = orient_s(x, v.x, shx(v.w, 0), shy(v.w, 0), v.y, shx(v.w, 1), shy(v.w, 1), v.z,
+                                 shx(v.w, 2), shy(v.w, 2));
           fl = BD_TRI_DIRTY | (o <= 0 ? BD_TRI_INVERTED : 0);
-          d.tv[t].w = fl;
+          d.tv[t].w = (v.w & ~BD_TRI_FLAGS) | fl;
         }
         const bool inverted = (fl & BD_TRI_INVERTED) != 0;
         inv += inverted ? 1 : 0;
@@ -294,10 +399,28 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           const int u = vk(v, (k + 1) % 3), w = vk(v, (k + 2) % 3);
           const bool disks = u < x.np && w < x.np;
           const bool mv = fresh && (d.moved[u] | d.moved[w]);
+          // image shift of w relative to u in this triangle (periodic box; 0 with walls)
+          const int rsx = shx(v.w, (k + 2) % 3) - shx(v.w, (k + 1) % 3);
+          const int rsy = shy(v.w, (k + 2) % 3) - shy(v.w, (k + 1) % 3);
+          long long LQ = 0;
+          if (rsx | rsy) LQ = rep_LQ(x, u);
           if (disks && mv) {
-            // Sec. 4.3 first criterion: r0 . r1 < 0, exact on the grid
+            // Sec. 4.3 first criterion: r0 . r1 < 0, exact on the grid (in a
+            // periodic box the edge's shift before the move is the present one
+            // less the re-entries of its end points)
             const double2 a0 = d.prev[u], b0 = d.prev[w], a1 = d.pos[u], b1 = d.pos[w];
-            if (bdpred::dot_sign(a0.x, a0.y, b0.x, b0.y, a1.x, a1.y, b1.x, b1.y, x.g) < 0) {
+            int ox = rsx, oy = rsy;
+            if (c.any_periodic) {
+              const uint8_t wu = d.wrap[u], ww = d.wrap[w];
+              ox -= wrapx(ww) - wrapx(wu);
+              oy -= wrapy(ww) - wrapy(wu);
+              if ((ox | oy) && LQ == 0) LQ = rep_LQ(x, u);
+            }
+            const int64_t ux = bdpred::to_int(b0.x, x.g) - bdpred::to_int(a0.x, x.g) + ox * LQ;
+            const int64_t uy = bdpred::to_int(b0.y, x.g) - bdpred::to_int(a0.y, x.g) + oy * LQ;
+            const int64_t vx = bdpred::to_int(b1.x, x.g) - bdpred::to_int(a1.x, x.g) + rsx * LQ;
+            const int64_t vy = bdpred::to_int(b1.y, x.g) - bdpred::to_int(a1.y, x.g) + rsy * LQ;
+            if (bdpred::sign128(bdpred::add128(bdpred::smul64(ux, vx), bdpred::smul64(uy, vy))) < 0) {
               ++rej;
               atomicExch(&ctl->st_fail_item, cc);
             }
@@ -308,26 +431,32 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
                           (fresh && (d.moved[v1.x] | d.moved[v1.y] | d.moved[v1.z]));
           if ((fl & BD_TRI_DIRTY) || d1) {
             const int q = vk(v1, o % 3);
-            if (incircle_v(x, v.x, v.y, v.z, q) > 0) {
+            int sqx, sqy;
+            opp_shift(v.w, k, v1.w, o % 3, sqx, sqy);
+            if (incircle_s(x, v, q, sqx, sqy) > 0) {
               claim6(x, t, k, nn, o, claim_key(epoch, cc));
               ++cand;
             }
           }
           if (mode != 1 && disks) {
             // FP32 screen: a pair whose FP32 squared distance exceeds
-            // sigma^2 (1 + 1e-5) is farther than sigma (FP32 error ~3e-7)
-            const float4 wu = d.work[u], ww = d.work[w];
-            const float fdx = fdiff(ww.x, ww.z, wu.x, wu.z), fdy = fdiff(ww.y, ww.w, wu.y, wu.w);
-            if (__fadd_rn(__fmul_rn(fdx, fdx), __fmul_rn(fdy, fdy)) > x.sig2f) continue;
+            // sigma^2 (1 + 1e-5) is farther than sigma (FP32 error ~3e-7);
+            // edges across a periodic box edge skip it
+            if ((rsx | rsy) == 0) {
+              const float4 wu = d.work[u], ww = d.work[w];
+              const float fdx = fdiff(ww.x, ww.z, wu.x, wu.z), fdy = fdiff(ww.y, ww.w, wu.y, wu.w);
+              if (__fadd_rn(__fmul_rn(fdx, fdx), __fmul_rn(fdy, fdy)) > x.sig2f) continue;
+            }
             const double2 pu = d.pos[u], pw = d.pos[w];
             // exact pre-test in grid units: |r_w - r_u|^2 <= (sigma/q)^2 (1 + 1e-9)
-            const int64_t ix = bdpred::to_int(pw.x, x.g) - bdpred::to_int(pu.x, x.g);
-            const int64_t iy = bdpred::to_int(pw.y, x.g) - bdpred::to_int(pu.y, x.g);
+            const int64_t ix = bdpred::to_int(pw.x, x.g) - bdpred::to_int(pu.x, x.g) + rsx * LQ;
+            const int64_t iy = bdpred::to_int(pw.y, x.g) - bdpred::to_int(pu.y, x.g) + rsy * LQ;
             const bdpred::i128 ir2 = bdpred::add128(bdpred::smul64(ix, ix), bdpred::smul64(iy, iy));
             const bool near = ir2.hi < c.sig2q_hi || (ir2.hi == c.sig2q_hi && ir2.lo <= c.sig2q_lo);
             if (near) {
-              // the decision itself as the FP64 reference makes it
-              const double dx = __dsub_rn(pw.x, pu.x), dy = __dsub_rn(pw.y, pu.y);
+              // the decision itself as the FP64 reference makes it (the
+              // difference of two grid values is exact in FP64)
+              const double dx = bdem::grid_to_double(ix, x.g.s), dy = bdem::grid_to_double(iy, x.g.s);
               const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
               const double r = sqrt(r2);
               if (r < sigma) {
@@ -393,10 +522,17 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
               const int o = vk(nn, k);
               if (o < 0) continue;
               const int p = vk(v, k), u = vk(v, (k + 1) % 3), w = vk(v, (k + 2) % 3);
-              const int q = vk(d.tv[o / 3], o % 3);
+              const int4 v1 = d.tv[o / 3];
+              const int q = vk(v1, o % 3);
+              int sqx, sqy;
+              opp_shift(v.w, k, v1.w, o % 3, sqx, sqy);
+              const int spx = shx(v.w, k), spy = shy(v.w, k);
+              const int sux = shx(v.w, (k + 1) % 3), suy = shy(v.w, (k + 1) % 3);
+              const int swx = shx(v.w, (k + 2) % 3), swy = shy(v.w, (k + 2) % 3);
               // orientation form of Eq. (predicate): both triangles of the
               // other diagonal strictly counter-clockwise
-              if (orient_v(x, u, q, p) > 0 && orient_v(x, w, p, q) > 0) {
+              if (orient_s(x, u, sux, suy, q, sqx, sqy, p, spx, spy) > 0 &&
+                  orient_s(x, w, swx, swy, p, spx, spy, q, sqx, sqy) > 0) {
                 const int cm = min(3 * t + k, o);
                 const int tt = cm / 3, kk = cm % 3;
                 const int4 ncm = d.tn[tt];
@@ -471,8 +607,9 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
               }
             }
             // claimed but not flipped: stays dirty, its edges are tested again
-          } else if (d.tv[t].w & BD_TRI_DIRTY) {
-            d.tv[t].w = 0;   // every edge of it was tested and found legal
+          } else {
+            const int tw = d.tv[t].w;
+            if (tw & BD_TRI_DIRTY) d.tv[t].w = tw & ~BD_TRI_FLAGS;   // every edge tested and legal
           }
         }
         block_add(cnt(ctl, b.ph, C_FLIPS), nf);
@@ -513,11 +650,13 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
     phase_begin(ctl, b);
     {
       const double cap = 0.25 * sigma;
+      int nwrap = 0;
       for (int i = tid; i < x.np; i += nth) {
         if (d.ext_id[i] < 0) continue;
         const double2 p = d.pos[i];
         d.prev[i] = p;
         const double2 dd = d.disp[i];
+        if (c.any_periodic) d.wrap[i] = 0;
         if (dd.x == 0.0 && dd.y == 0.0) {
           d.moved[i] = 0;
           if (log_pidx >= 0) d.log_pflags[(size_t)log_pidx * x.np + i] = 0;
@@ -529,15 +668,29 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         const double2 y = make_double2(snap(__dadd_rn(p.x, __dmul_rn(dd.x, sc)), x.g),
                                        snap(__dadd_rn(p.y, __dmul_rn(dd.y, sc)), x.g));
         int rfl = 0;
-        const double2 np2 = bdem::reflect(d.rep[d.rep_of[i]], y, &rfl);
+        const BdRep &R = d.rep[d.rep_of[i]];
+        double2 np2;
+        if (R.periodic) {
+          // Algorithm 2 "applying the periodic boundary conditions": re-entry
+          long long X = bdpred::to_int(y.x, x.g), Y = bdpred::to_int(y.y, x.g);
+          const int wr = bdem::wrap_grid(R.LQ, X, Y);
+          d.wrap[i] = (uint8_t)wr;
+          if (wr) ++nwrap;
+          np2 = make_double2(bdem::grid_to_double(X, x.g.s), bdem::grid_to_double(Y, x.g.s));
+        } else {
+          np2 = bdem::reflect(R, y, &rfl);
+        }
         if (log_pidx >= 0) d.log_pflags[(size_t)log_pidx * x.np + i] = (uint8_t)(rfl | (capped ? 16 : 0));
         d.pos[i] = np2;
         d.work[i] = split_pos(np2);
         d.disp[i] = make_double2(0.0, 0.0);
         d.moved[i] = 1;
       }
-      for (int t = tid; t < x.T; t += nth)
-        if (d.tv[t].w) d.tv[t].w = 0;
+      if (c.any_periodic) block_add(&ctl->n_wrapped, nwrap);
+      for (int t = tid; t < x.T; t += nth) {
+        const int tw = d.tv[t].w;
+        if (tw & BD_TRI_FLAGS) d.tv[t].w = tw & ~BD_TRI_FLAGS;
+      }
     }
     if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
     if (lead) stage_tick(ctl, STAGE_A, t_mark);

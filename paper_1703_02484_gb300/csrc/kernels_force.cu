@@ -133,6 +133,137 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32(BdDev d, BdConst c) {
   }
 }
 
+// Periodic box (Sec. 2.1): the one-sided sweep with minimum images.  Each
+// coordinate is re-centred on the block's origin as its minimum image, formed
+// exactly in grid units from the FP64 master and kept as an FP32 (hi, lo)
+// pair, so a pair vector is (hi_j - hi_i) + (lo_j - lo_i): the hi difference
+// is exact for near pairs (and takes its minimum image, one exact addition or
+// subtraction of L, when beyond L/2), the sum is rounded once.  This keeps
+// near pairs at FP32 resolution of their separation wherever they sit in the
+// block.  Inert padding slots are staged far away and never wrapped.
+// Replicas with walls in the same batch run here too (no wrap, hL = +inf).
+// Per ordered pair: 12 FP32 lane operations + 1 MUFU + the wrap test.
+__device__ __forceinline__ float4 stage_q(const BdDev &d, const BdConst &c, int j, long long ox, long long oy,
+                                          long long LQ) {
+  if (d.ext_id[j] < 0) return make_float4(1.0e18f, 1.0e18f, 0.f, 0.f);
+  const bdpred::Grid g{c.q, c.inv_q, c.qshift};
+  const double2 p = d.pos[j];
+  long long X = bdpred::to_int(p.x, g) - ox, Y = bdpred::to_int(p.y, g) - oy;
+  if (LQ > 0) {
+    const long long h = LQ / 2;
+    X = X > h ? X - LQ : (X < -h ? X + LQ : X);
+    Y = Y > h ? Y - LQ : (Y < -h ? Y + LQ : Y);
+  }
+  const float2 sx = bdem::grid_split(X, c.qshift), sy = bdem::grid_split(Y, c.qshift);
+  return make_float4(sx.x, sy.x, sx.y, sy.y);
+}
+
+__device__ __forceinline__ float min_image(float dx, float Lf, float hLf) {
+  dx = dx > hLf ? __fsub_rn(dx, Lf) : dx;
+  return dx < -hLf ? __fadd_rn(dx, Lf) : dx;
+}
+
+__global__ void __launch_bounds__(BD_FT) k_force_long_per(BdDev d, BdConst c) {
+  if (ctl_failed(d.ctl)) return;
+  __shared__ float4 sj[2][BD_TJ];   // per j: (x_hi, y_hi, x_lo, y_lo) re-centred
+  const int4 item = d.items[blockIdx.x];  // (i block, first tile, end tile, partial slot)
+  const int ib = item.x, slot = item.w, tid = threadIdx.x;
+  const float2 org = d.iorigin[ib];
+  float Lf = 0.f, hLf = __int_as_float(0x7f800000);
+  long long LQ = 0;
+  {
+    const int i0 = d.iperm[ib * BD_IB];
+    const BdRep &R0 = d.rep[i0 >= 0 ? d.rep_of[i0] : 0];
+    if (R0.periodic) {
+      Lf = R0.Lf;
+      hLf = R0.hLf;
+      LQ = R0.LQ;
+    }
+  }
+  const long long ox = (long long)org.x * (1ll << c.qshift);   // integer origins: exact in grid units
+  const long long oy = (long long)org.y * (1ll << c.qshift);
+  float xh[BD_IPT], yh[BD_IPT], xl[BD_IPT], yl[BD_IPT], ax[BD_IPT], ay[BD_IPT];
+  float fxh[BD_IPT], fxl[BD_IPT], fyh[BD_IPT], fyl[BD_IPT], a0[BD_IPT], a1[BD_IPT];
+  int ii[BD_IPT];
+#pragma unroll
+  for (int q = 0; q < BD_IPT; ++q) {
+    int i = d.iperm[ib * BD_IB + q * BD_FT + tid];
+    ii[q] = i;
+    if (i >= 0) {
+      const float4 u = stage_q(d, c, i, ox, oy, LQ);
+      xh[q] = u.x;
+      yh[q] = u.y;
+      xl[q] = u.z;
+      yl[q] = u.w;
+      int s = d.species[i];
+      const BdRep &R = d.rep[d.rep_of[i]];
+      a0[q] = R.alpha[2 * s + 0];
+      a1[q] = R.alpha[2 * s + 1];
+    } else {
+      xh[q] = yh[q] = 1.0e18f;
+      xl[q] = yl[q] = 0.f;
+      a0[q] = a1[q] = 0.f;
+    }
+    ax[q] = ay[q] = 0.f;
+    fxh[q] = fxl[q] = fyh[q] = fyl[q] = 0.f;
+  }
+  const int t_begin = item.y, t_end = item.z;
+  const float eps0 = 1e-20f * (float)(c.a * c.a);
+  float4 st0, st1;
+  auto fetch = [&](int tile) {
+    const int j0 = tile * BD_TJ + tid;
+    st0 = stage_q(d, c, j0, ox, oy, LQ);
+    st1 = stage_q(d, c, j0 + BD_FT, ox, oy, LQ);
+  };
+  int buf = 0;
+  if (t_begin < t_end) {
+    fetch(t_begin);
+    sj[0][tid] = st0;
+    sj[0][tid + BD_FT] = st1;
+  }
+  __syncthreads();
+  for (int t = t_begin; t < t_end; ++t) {
+    if (t + 1 < t_end) fetch(t + 1);
+#pragma unroll 4
+    for (int jj = 0; jj < BD_TJ; ++jj) {
+      const float4 p = sj[buf][jj];
+#pragma unroll
+      for (int q = 0; q < BD_IPT; ++q) {
+        const float dx = __fadd_rn(min_image(__fsub_rn(p.x, xh[q]), Lf, hLf), __fsub_rn(p.z, xl[q]));
+        const float dy = __fadd_rn(min_image(__fsub_rn(p.y, yh[q]), Lf, hLf), __fsub_rn(p.w, yl[q]));
+        float r2 = __fmaf_rn(dx, dx, eps0);
+        r2 = __fmaf_rn(dy, dy, r2);
+        const float sv = rsqrt_apx(r2);
+        const float s3 = __fmul_rn(__fmul_rn(sv, sv), sv);
+        ax[q] = __fmaf_rn(dx, s3, ax[q]);
+        ay[q] = __fmaf_rn(dy, s3, ay[q]);
+      }
+    }
+    // (r_j - r_i) was summed: the force on i is -A[s_i][s_tile] times it
+    const int sp = d.tile_species[t];
+#pragma unroll
+    for (int q = 0; q < BD_IPT; ++q) {
+      const float al = sp ? a1[q] : a0[q];
+      two_sum(fxh[q], fxl[q], -al * ax[q]);
+      two_sum(fyh[q], fyl[q], -al * ay[q]);
+      ax[q] = ay[q] = 0.f;
+    }
+    if (t + 1 < t_end) {
+      sj[buf ^ 1][tid] = st0;
+      sj[buf ^ 1][tid + BD_FT] = st1;
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int q = 0; q < BD_IPT; ++q) {
+    const int i = ii[q];
+    if (i >= 0)
+      d.fpart[(size_t)slot * c.np + i] =
+          make_double2((double)fxh[q] + (double)fxl[q], (double)fyh[q] + (double)fyl[q]);
+  }
+}
+
 // Packed variant: Blackwell's f32x2 instructions (add/sub/mul/fma on a pair
 // of FP32 values in one 64-bit register pair) process two i disks per
 // instruction, halving the issue slots of the FP32 work.  j disks are staged
@@ -286,6 +417,11 @@ __global__ void __launch_bounds__(128) k_force_long_f64(BdDev d, BdConst c) {
         int sk = ss[k];
         if (sk < 0 || jj == i || jj < my_begin || jj >= my_end) continue;
         double rx = pi.x - sp[k].x, ry = pi.y - sp[k].y;
+        if (R.periodic) {
+          // minimum image (Sec. 2.1)
+          rx -= R.L * rint(rx / R.L);
+          ry -= R.L * rint(ry / R.L);
+        }
         double r2 = rx * rx + ry * ry;
         double cf = R.alpha_d[2 * si + sk] / (r2 * sqrt(r2));
         fx += cf * rx;
@@ -333,21 +469,28 @@ __global__ void k_integrate(BdDev d, BdConst c, long long step, int log_step, in
   d.theta0[i] = th;
   float thn;
   int flags = 0;
+  const bdpred::Grid g{c.q, c.inv_q, c.qshift};
+  long long X, Y;
   if (c.precision == 0) {
     // move, reflection and FP32 copy in grid units (no FP64 arithmetic)
-    long long X, Y;
     bdem::em_move_grid(c, R, (uint32_t)e, step, p, th, F, R.v0, &thn, (uint32_t)node, &X, &Y);
-    const bdpred::Grid g{c.q, c.inv_q, c.qshift};
-    flags = bdem::reflect_grid(bdpred::to_int(R.wall_lo, g), bdpred::to_int(R.wall_hi, g), X, Y);
-    d.pos[i] = make_double2(bdem::grid_to_double(X, c.qshift), bdem::grid_to_double(Y, c.qshift));
-    const float2 sx = bdem::grid_split(X, c.qshift), sy = bdem::grid_split(Y, c.qshift);
-    d.work[i] = make_float4(sx.x, sy.x, sx.y, sy.y);
   } else {
     const double2 y = bdem::em_move(c, R, (uint32_t)e, step, p, th, F, R.v0, &thn, (uint32_t)node);
-    const double2 pn = bdem::reflect(R, y, &flags);
-    d.pos[i] = pn;
-    d.work[i] = bdem::split(pn);
+    X = bdpred::to_int(y.x, g);
+    Y = bdpred::to_int(y.y, g);
   }
+  if (R.periodic) {
+    // re-entry at the opposite side (Sec. 2.1); the triangulation kernel
+    // shifts the corners of the disks that re-entered
+    const int wr = bdem::wrap_grid(R.LQ, X, Y);
+    d.wrap[i] = (uint8_t)wr;
+    if (wr && !c.overlap_verlet) atomicAdd(&d.ctl->n_wrapped, 1);
+  } else {
+    flags = bdem::reflect_grid(bdpred::to_int(R.wall_lo, g), bdpred::to_int(R.wall_hi, g), X, Y);
+  }
+  d.pos[i] = make_double2(bdem::grid_to_double(X, c.qshift), bdem::grid_to_double(Y, c.qshift));
+  const float2 sx = bdem::grid_split(X, c.qshift), sy = bdem::grid_split(Y, c.qshift);
+  d.work[i] = make_float4(sx.x, sy.x, sx.y, sy.y);
   d.theta[i] = thn;
   d.moved[i] = 1;
   if (log_step >= 0 && d.log_refl) d.log_refl[(size_t)log_step * c.np + i] = (uint8_t)flags;
@@ -382,7 +525,9 @@ cudaError_t bd_launch_force_long_variant(const BdDev &d, const BdConst &c, int v
   if (c.precision == 0) {
     if (variant >= 2) return bd_launch_force_sym(d, c, variant, s);
     if (c.n_items == 0) return cudaSuccess;
-    if (variant == 1)
+    if (c.any_periodic)
+      k_force_long_per<<<c.n_items, BD_FT, 0, s>>>(d, c);   // the one form with minimum images
+    else if (variant == 1)
       k_force_long_f32x2<BD_IPT><<<c.n_items, BD_FT, 0, s>>>(d, c);
     else
       k_force_long_f32<<<c.n_items, BD_FT, 0, s>>>(d, c);
@@ -404,6 +549,30 @@ cudaError_t bd_launch_integrate(const BdDev &d, const BdConst &c, int64_t step, 
 
 cudaError_t bd_launch_advance_step(const BdDev &d, cudaStream_t s) {
   k_advance_step<<<1, 1, 0, s>>>(d.ctl);
+  return cudaGetLastError();
+}
+
+// periodic box: a coordinate that moved by more than L/2 crossed an edge
+// (stored = geometric - L k, k = round((old - new) / L))
+__global__ void k_periodic_wraps(BdDev d, BdConst c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.np) return;
+  const int r = d.rep_of[i];
+  if (r < 0 || !d.rep[r].periodic) return;
+  const long long LQ = d.rep[r].LQ;
+  const bdpred::Grid g{c.q, c.inv_q, c.qshift};
+  const double2 o = d.pos0[i], p = d.pos[i];
+  const long long dx = bdpred::to_int(o.x, g) - bdpred::to_int(p.x, g);
+  const long long dy = bdpred::to_int(o.y, g) - bdpred::to_int(p.y, g);
+  const int kx = dx > LQ / 2 ? 1 : (dx < -LQ / 2 ? -1 : 0);
+  const int ky = dy > LQ / 2 ? 1 : (dy < -LQ / 2 ? -1 : 0);
+  const int wr = (kx & 3) | ((ky & 3) << 2);
+  d.wrap[i] = (uint8_t)wr;
+  if (wr) atomicAdd(&d.ctl->n_wrapped, 1);
+}
+
+cudaError_t bd_launch_periodic_wraps(const BdDev &d, const BdConst &c, cudaStream_t s) {
+  k_periodic_wraps<<<(c.np + 255) / 256, 256, 0, s>>>(d, c);
   return cudaGetLastError();
 }
 

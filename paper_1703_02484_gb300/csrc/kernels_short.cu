@@ -76,6 +76,14 @@ __device__ __forceinline__ int cell_of(double2 p, const BdRep &R) {
   return R.cell_base + cy * R.ncell + cx;
 }
 
+// periodic box (Sec. 2.1): minimum image of an exact FP64 coordinate difference
+__device__ __forceinline__ double dmin_image(double d, const BdRep &R) {
+  if (!R.periodic) return d;
+  if (d > 0.5 * R.L) return __dsub_rn(d, R.L);
+  if (d < -0.5 * R.L) return __dadd_rn(d, R.L);
+  return d;
+}
+
 // replica of slot i if it is a disk of a short-range replica, else null
 __device__ __forceinline__ const BdRep *short_rep(const BdDev &d, int i) {
   const int r = d.rep_of[i];
@@ -106,15 +114,27 @@ __global__ void k_vl_check(BdDev d, BdConst c) {
       // only a displacement within 1e-5 of skin/2 is decided in FP64
       const double2 p = d.pos[i], r = d.vl_ref[i];
       const bdpred::Grid g{c.q, c.inv_q, c.qshift};
-      const float fx = bdem::grid_to_float(bdpred::to_int(p.x, g) - bdpred::to_int(r.x, g), c.qshift);
-      const float fy = bdem::grid_to_float(bdpred::to_int(p.y, g) - bdpred::to_int(r.y, g), c.qshift);
-      const float d2 = __fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy));
-      const float thr = (float)(0.25 * R->skin * R->skin);
-      if (d2 > thr * 1.00001f) {
-        hit = true;
-      } else if (d2 >= thr * 0.99999f) {
-        double dx = p.x - r.x, dy = p.y - r.y;
-        hit = dx * dx + dy * dy > 0.25 * R->skin * R->skin;
+      if (r.x > 1e29) {
+        hit = true;   // never built (reference parked far away)
+      } else {
+        long long ex = bdpred::to_int(p.x, g) - bdpred::to_int(r.x, g);
+        long long ey = bdpred::to_int(p.y, g) - bdpred::to_int(r.y, g);
+        if (R->periodic) {
+          // displacement across an edge: its minimum image
+          const long long h = R->LQ / 2;
+          ex = ex > h ? ex - R->LQ : (ex < -h ? ex + R->LQ : ex);
+          ey = ey > h ? ey - R->LQ : (ey < -h ? ey + R->LQ : ey);
+        }
+        const float fx = bdem::grid_to_float(ex, c.qshift);
+        const float fy = bdem::grid_to_float(ey, c.qshift);
+        const float d2 = __fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy));
+        const float thr = (float)(0.25 * R->skin * R->skin);
+        if (d2 > thr * 1.00001f) {
+          hit = true;
+        } else if (d2 >= thr * 0.99999f) {
+          double dx = dmin_image(p.x - r.x, *R), dy = dmin_image(p.y - r.y, *R);
+          hit = dx * dx + dy * dy > 0.25 * R->skin * R->skin;
+        }
       }
     }
   }
@@ -227,9 +247,12 @@ __global__ void k_vl_build(BdDev d, BdConst c) {
     int buf[BD_VL_MAX];
     int m = 0;
     bool over = false;
-    for (int gy = cy - 1; gy <= cy + 1; ++gy) {
+    for (int gy0 = cy - 1; gy0 <= cy + 1; ++gy0) {
+      // periodic box: the cells wrap around (at least three per side)
+      const int gy = R.periodic ? (gy0 + R.ncell) % R.ncell : gy0;
       if (gy < 0 || gy >= R.ncell) continue;
-      for (int gx = cx - 1; gx <= cx + 1; ++gx) {
+      for (int gx0 = cx - 1; gx0 <= cx + 1; ++gx0) {
+        const int gx = R.periodic ? (gx0 + R.ncell) % R.ncell : gx0;
         if (gx < 0 || gx >= R.ncell) continue;
         int cc = R.cell_base + gy * R.ncell + gx;
         int b = d.cell_start[cc], e = b + d.cell_count[cc];
@@ -237,7 +260,7 @@ __global__ void k_vl_build(BdDev d, BdConst c) {
           int j = d.cell_idx[s];
           if (j == i) continue;
           double2 q = d.pos[j];
-          double dx = __dsub_rn(p.x, q.x), dy = __dsub_rn(p.y, q.y);
+          double dx = dmin_image(__dsub_rn(p.x, q.x), R), dy = dmin_image(__dsub_rn(p.y, q.y), R);
           double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
           if (r2 < R.rl2) {
             if (m < BD_VL_MAX) {
@@ -298,14 +321,30 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
       if (t0 + u >= m) break;
       const int j = jj[u];
       const float4 wj = wv[u];
-      // r_i - r_j from the (hi, lo) pairs: exact for near pairs
-      const float dx = __fadd_rn(__fsub_rn(wi.x, wj.x), __fsub_rn(wi.z, wj.z));
-      const float dy = __fadd_rn(__fsub_rn(wi.y, wj.y), __fsub_rn(wi.w, wj.w));
+      // r_i - r_j as an FP32 (hi, lo) pair: from the disks' own pairs, exact
+      // for near pairs; a pair across a periodic box edge is formed exactly in
+      // grid units from the FP64 masters instead (its hi parts differ by ~L)
+      float hx = __fsub_rn(wi.x, wj.x), hy = __fsub_rn(wi.y, wj.y);
+      float lx = __fsub_rn(wi.z, wj.z), ly = __fsub_rn(wi.w, wj.w);
+      if (R.periodic && (fabsf(hx) > R.hLf || fabsf(hy) > R.hLf)) {
+        const bdpred::Grid g{c.q, c.inv_q, c.qshift};
+        const double2 pj = d.pos[j];
+        long long X = bdpred::to_int(pi.x, g) - bdpred::to_int(pj.x, g);
+        long long Y = bdpred::to_int(pi.y, g) - bdpred::to_int(pj.y, g);
+        const long long h = R.LQ / 2;
+        X = X > h ? X - R.LQ : (X < -h ? X + R.LQ : X);
+        Y = Y > h ? Y - R.LQ : (Y < -h ? Y + R.LQ : Y);
+        const float2 sx = bdem::grid_split(X, c.qshift), sy = bdem::grid_split(Y, c.qshift);
+        hx = sx.x; lx = sx.y;
+        hy = sy.x; ly = sy.y;
+      }
+      const float dx = __fadd_rn(hx, lx);
+      const float dy = __fadd_rn(hy, ly);
       const float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
       if (fabsf(r2 - rc2) < 1e-5f * rc2) {
         // at the cut-off the force jumps: decide as the FP64 reference does
         const double2 pj = d.pos[j];
-        const double ex = __dsub_rn(pi.x, pj.x), ey = __dsub_rn(pi.y, pj.y);
+        const double ex = dmin_image(__dsub_rn(pi.x, pj.x), R), ey = dmin_image(__dsub_rn(pi.y, pj.y), R);
         if (!(sqrt(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey))) < R.r_cut)) continue;
       } else if (r2 >= rc2) {
         continue;
@@ -322,8 +361,8 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
         // errors above 1e-5 of the net force, so the core is evaluated in
         // float-float arithmetic (FP32 instructions, ~48-bit significands) from
         // the exact coordinate differences
-        ff ex = ff_make(__fsub_rn(wi.x, wj.x), __fsub_rn(wi.z, wj.z));
-        ff ey = ff_make(__fsub_rn(wi.y, wj.y), __fsub_rn(wi.w, wj.w));
+        ff ex = ff_make(hx, lx);
+        ff ey = ff_make(hy, ly);
         ff q2 = ff_add(ff_mul(ex, ex), ff_mul(ey, ey));
         ff s2 = ff_div({sg * sg, 0.f}, q2);
         ff s6 = ff_mul(ff_mul(s2, s2), s2);

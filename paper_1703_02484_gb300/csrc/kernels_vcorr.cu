@@ -41,6 +41,19 @@ __device__ __forceinline__ float fdiff(float bh, float bl, float ah, float al) {
   return __fadd_rn(__fsub_rn(bh, ah), __fsub_rn(bl, al));
 }
 
+// the FP32 screen's coordinate difference; a pair across a periodic box edge
+// (hi parts ~L apart, not exact in FP32) reports 0 and is decided exactly
+__device__ __forceinline__ float fdiff_p(float bh, float bl, float ah, float al, const BdRep &R) {
+  const float h = __fsub_rn(bh, ah);
+  if (R.periodic && fabsf(h) > R.hLf) return 0.f;
+  return __fadd_rn(h, __fsub_rn(bl, al));
+}
+__device__ __forceinline__ long long imin_image(long long d, const BdRep &R) {
+  if (!R.periodic) return d;
+  const long long h = R.LQ / 2;
+  return d > h ? d - R.LQ : (d < -h ? d + R.LQ : d);
+}
+
 // lead thread only: charge the time since the last mark to a stage
 __device__ __forceinline__ void stage_tick(BdCtl *ctl, int stage, unsigned long long &mark) {
   const unsigned long long now = gtimer();
@@ -79,9 +92,12 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
         if (d.ext_id[i] < 0) continue;
         const bool mi = d.moved[i] != 0;
         const double2 pi = d.pos[i];
+        const BdRep &R = d.rep[d.rep_of[i]];
+        const bdpred::Grid g{c.q, c.inv_q, c.qshift};
         if (mi) {
           const double2 r0 = d.vl_ref[i];
-          const double ex = __dsub_rn(pi.x, r0.x), ey = __dsub_rn(pi.y, r0.y);
+          const double ex = bdem::grid_to_double(imin_image(bdpred::to_int(pi.x, g) - bdpred::to_int(r0.x, g), R), c.qshift);
+          const double ey = bdem::grid_to_double(imin_image(bdpred::to_int(pi.y, g) - bdpred::to_int(r0.y, g), R), c.qshift);
           if (__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) > c.vl_reach2) {
             ++stale;
             atomicExch(&ctl->st_fail_item, i);
@@ -95,10 +111,12 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
           const int j = d.vl_idx[(size_t)t * c.np + i];
           if (!mi && !d.moved[j]) continue;   // neither end moved since the last pass
           const float4 wj = d.work[j];
-          const float fx = fdiff(wj.x, wj.z, wi.x, wi.z), fy = fdiff(wj.y, wj.w, wi.y, wi.w);
+          const float fx = fdiff_p(wj.x, wj.z, wi.x, wi.z, R), fy = fdiff_p(wj.y, wj.w, wi.y, wi.w, R);
           if (__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)) > sig2f) continue;
           const double2 pj = d.pos[j];
-          const double dx = __dsub_rn(pj.x, pi.x), dy = __dsub_rn(pj.y, pi.y);
+          // the exact difference (grid units), its minimum image in a periodic box
+          const double dx = bdem::grid_to_double(imin_image(bdpred::to_int(pj.x, g) - bdpred::to_int(pi.x, g), R), c.qshift);
+          const double dy = bdem::grid_to_double(imin_image(bdpred::to_int(pj.y, g) - bdpred::to_int(pi.y, g), R), c.qshift);
           const double r = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
           if (r < sigma) {
             const double del = sigma - r;
@@ -149,7 +167,16 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
         const double2 y = make_double2(bdem::snapd(__dadd_rn(p.x, __dmul_rn(dd.x, sc)), c.q, c.inv_q),
                                        bdem::snapd(__dadd_rn(p.y, __dmul_rn(dd.y, sc)), c.q, c.inv_q));
         int rfl = 0;
-        const double2 pn = bdem::reflect(d.rep[d.rep_of[i]], y, &rfl);
+        const BdRep &R = d.rep[d.rep_of[i]];
+        double2 pn;
+        if (R.periodic) {
+          const bdpred::Grid g{c.q, c.inv_q, c.qshift};
+          long long X = bdpred::to_int(y.x, g), Y = bdpred::to_int(y.y, g);
+          bdem::wrap_grid(R.LQ, X, Y);
+          pn = make_double2(bdem::grid_to_double(X, c.qshift), bdem::grid_to_double(Y, c.qshift));
+        } else {
+          pn = bdem::reflect(R, y, &rfl);
+        }
         d.pos[i] = pn;
         d.work[i] = bdem::split(pn);
         d.moved[i] = 1;

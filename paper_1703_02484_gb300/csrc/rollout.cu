@@ -345,7 +345,7 @@ int bd_rollout(bd_handle *h, int32_t nsteps, int32_t ckpt_every, int32_t loss_ki
   if (!h || nsteps < 1 || ckpt_every < 1 || !isfinite(target)) return BD_ERR_ARG;
   if (stats) memset(stats, 0, sizeof(*stats));
   if (loss_kind != BD_LOSS_MSD) return BD_ERR_UNSUPPORTED;
-  if (h->reps.size() != 1 || h->reps[0].p.law != BD_LAW_LONG) return BD_ERR_UNSUPPORTED;
+  if (h->reps.size() != 1 || h->reps[0].p.law != BD_LAW_LONG || h->reps[0].periodic) return BD_ERR_UNSUPPORTED;
   if (!h->ro) {
     h->ro = new (std::nothrow) BdRollout;
     if (!h->ro) return BD_ERR_NOMEM;

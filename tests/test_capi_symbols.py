@@ -89,3 +89,25 @@ def test_host_triangulation_lattice_start():
     tri, grid = binding.triangulate(xy, L)
     ot = geometry.delaunay(grid, L)
     assert np.array_equal(geometry.edges(tri), geometry.edges(ot))
+
+
+@pytest.mark.parametrize("n,rho,seed", [(16, 0.1, 1), (50, 0.3, 2), (777, 0.3, 3), (5000, 0.5, 4)])
+def test_host_torus_triangulation_equals_oracle(n, rho, seed):
+    # the periodic box's initial triangulation (built on the host, Sec. 4.1)
+    # against the oracle's torus Delaunay triangulation of the 3 x 3 tiling
+    from oracle import periodic
+    L = workloads.box_side(n, rho)
+    Lf = float(np.float32(L))
+    xy = workloads.initial_positions(n, Lf, 1.0, rho, seed=seed)
+    xy = xy + np.random.default_rng(seed).uniform(0, Lf, 2)       # straddle the box edges
+    tri, sh, grid = binding.triangulate_periodic(xy, L)
+    assert len(tri) == 2 * n
+    assert np.all((grid >= 0) & (grid < Lf))
+    assert np.max(np.abs(periodic.min_image(grid - xy, Lf))) <= 1e-11 * Lf
+    assert np.all(sh[:, 0, :] == 0)
+    assert periodic.is_torus_triangulation(tri, sh)
+    ref = periodic.edge_keys(*periodic.delaunay_torus(grid, Lf))
+    assert np.array_equal(periodic.edge_keys(tri, sh), ref)
+    corners = periodic.lifted(grid, tri, sh, Lf)
+    for a, b, c in corners[: min(len(corners), 3000)]:
+        assert geometry.orient(a, b, c) > 0
