@@ -138,6 +138,9 @@ typedef struct bd_step_stats {
   int64_t barriers;         /* grid-wide barriers of the device-side loops (all steps) */
   int64_t substeps;         /* moves shorter than dt that completed (max_dt_halvings > 0) */
   int64_t halvings;         /* rejected moves that were replaced by their two halves */
+  int64_t tri_visits;       /* triangles examined by the check passes (a pass after the
+                               first of a move visits only the triangles near moved
+                               disks, flips and overlaps) */
 } bd_step_stats;
 
 typedef struct bd_handle bd_handle;

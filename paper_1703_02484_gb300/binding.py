@@ -50,6 +50,7 @@ class bd_step_stats(ctypes.Structure):
         ("fail_item", ctypes.c_int32), ("fail_count", ctypes.c_int32),
         ("barriers", ctypes.c_int64),
         ("substeps", ctypes.c_int64), ("halvings", ctypes.c_int64),
+        ("tri_visits", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -646,6 +646,10 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
   c.max_corr_iters = p0.max_corr_iters;
   c.overlap_verlet = p0.overlap_mode == BD_OVERLAP_VERLET ? 1 : 0;
   {
+    const char *tl = getenv("BD_TRI_LISTS");
+    c.tri_lists = tl ? std::min(2, std::max(0, atoi(tl))) : 0;
+  }
+  {
     // the lists hold every pair within r_cut + skin of the build positions, so
     // every pair closer than sigma while no disk has moved (r_cut + skin - sigma)/2
     double reach = 1e300;
@@ -741,6 +745,10 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     BD_TRY(dalloc(h, &d.tv_snap, (size_t)nt));
     BD_TRY(dalloc(h, &d.tn_snap, (size_t)nt));
     BD_TRY(dalloc(h, &d.claim, (size_t)nt));
+    BD_TRY(dalloc(h, &d.vt, nv));
+    BD_TRY(dalloc(h, &d.act, 3 * (size_t)nt));
+    BD_TRY(dalloc(h, &d.act_mark, 3 * (size_t)nt));
+    BD_TRY(cudaMemsetAsync(d.act_mark, 0, 3 * (size_t)nt * sizeof(unsigned), h->stream));
     BD_TRY(dalloc(h, &d.iperm, (size_t)std::max(1, h->np_i)));
     BD_TRY(dalloc(h, &d.iorigin, (size_t)std::max(1, iblock)));
     BD_TRY(dalloc(h, &d.tile_species, std::max<size_t>(1, tile_sp.size())));
@@ -784,6 +792,7 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
       BD_TRY(dalloc(h, &h->hs_theta, (size_t)np));
       BD_TRY(dalloc(h, &h->hs_tv, (size_t)nt));
       BD_TRY(dalloc(h, &h->hs_tn, (size_t)nt));
+      BD_TRY(dalloc(h, &h->hs_vt, nv));
     }
 
     cudaStream_t st = h->stream;
@@ -830,6 +839,16 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     BD_TRY(cudaMemsetAsync(d.disp, 0, np * sizeof(double2), st));
     BD_TRY(cudaMemcpyAsync(d.tv, tv_all.data(), nt * sizeof(int4), cudaMemcpyHostToDevice, st));
     BD_TRY(cudaMemcpyAsync(d.tn, tn_all.data(), nt * sizeof(int4), cudaMemcpyHostToDevice, st));
+    {
+      // one corner per vertex (the star walks of the triangulation kernel start there)
+      std::vector<int> vt(nv, -1);
+      for (int t = 0; t < nt; ++t) {
+        vt[tv_all[t].x] = 3 * t;
+        vt[tv_all[t].y] = 3 * t + 1;
+        vt[tv_all[t].z] = 3 * t + 2;
+      }
+      BD_TRY(cudaMemcpy(d.vt, vt.data(), nv * sizeof(int), cudaMemcpyHostToDevice));
+    }
     BD_TRY(cudaMemsetAsync(d.claim, 0, nt * sizeof(unsigned long long), st));
     if (!iperm.empty())
       BD_TRY(cudaMemcpyAsync(d.iperm, iperm.data(), iperm.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1114,6 +1133,9 @@ cudaError_t halving_snapshot(bd_handle *h, bool save) {
     e = cudaMemcpyAsync(save ? h->hs_tv : h->d.tv, save ? h->d.tv : h->hs_tv, nt * sizeof(int4), k, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(save ? h->hs_tn : h->d.tn, save ? h->d.tn : h->hs_tn, nt * sizeof(int4), k, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(save ? h->hs_vt : h->d.vt, save ? h->d.vt : h->hs_vt,
+                          ((size_t)h->np + h->ng) * sizeof(int), k, st);
   }
   if (e == cudaSuccess && !save) {
     e = cudaMemcpyAsync(h->d.prev, h->d.pos, np * sizeof(double2), k, st);
@@ -1314,6 +1336,7 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
     stats->barriers = k.st_barriers;
     stats->rejected = status != 0;
     stats->substeps = k.st_substeps;
+    stats->tri_visits = k.st_tri_visits;
     stats->halvings = halvings;
     double mo;
     unsigned long long bits = k.st_max_overlap_bits;

@@ -64,6 +64,7 @@ struct bd_handle {
   float4 *hs_work = nullptr;
   float *hs_theta = nullptr;
   int4 *hs_tv = nullptr, *hs_tn = nullptr;
+  int *hs_vt = nullptr;
   double stage_ns[4] = {0, 0, 0, 0};   // triangulation-kernel stage times since the last reset
   int64_t stage_cnt[4] = {0, 0, 0, 0};
 };

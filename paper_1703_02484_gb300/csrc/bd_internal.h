@@ -53,6 +53,7 @@ struct BdCtl {
   int vl_need;                     // Verlet rebuild requested for this step
   long long st_verlet_rebuilds;
   long long st_substeps;           // pieces of halved steps that completed
+  long long st_tri_visits;         // triangles examined by the check passes
   long long st_barriers;           // grid barriers passed by the triangulation kernel
   int st_fail_item;                // an offending triangle (repair) or edge corner (reversal)
   int st_fail_count;               // inverted triangles / reversed edges at the failure
@@ -69,6 +70,8 @@ struct BdCtl {
   long long step_dev;              // index of the next step (advanced by the triangulation kernel)
   int n_wrapped;                   // periodic box: disks that re-entered in the last move (consumed
                                    // by the triangulation kernel's shift pass; not a statistic)
+  int act_n[3];                    // lengths of the rotating triangle lists (zeroed at kernel exit)
+  unsigned act_gen;                // next list generation (grows across launches)
 };
 
 // counter slots within BdCtl::cnt[phase % 4]
@@ -111,6 +114,9 @@ struct BdDev {
   // triangulation (corner table), all replicas
   int4 *tv, *tn, *tv_snap, *tn_snap;
   unsigned long long *claim;
+  int *vt;                 // per vertex: one corner holding it (kept by the flips)
+  int *act;                // 3 x nt: rotating lists of the triangles a check pass visits
+  unsigned *act_mark;      // 3 x nt: generation at which a triangle joined each list
   // force sweep
   int *iperm;              // spatial order of i per block (np_i slots, -1 = none)
   float2 *iorigin;         // per i-block origin (integers)
@@ -156,6 +162,9 @@ struct BdConst {
   int force_variant;       // 0: scalar FP32 sweep, 1: packed f32x2 sweep, 2, 3: symmetric packed sweeps
   int n_sitems;            // symmetric sweep work items
   int overlap_verlet;      // 1: Algorithm 2 over the Verlet lists, no triangulation kept
+  int tri_lists;           // check passes after the first of a move: 0 lists when a full pass
+                           // is throughput-bound (many triangles per thread), 1 always lists,
+                           // 2 always full (environment variable BD_TRI_LISTS at init)
   double vl_reach2;        // squared displacement since the list build below which the lists
                            // still hold every pair closer than sigma
   int log_pairs_cap, log_pass_cap;   // rollout log capacities

@@ -92,6 +92,7 @@ static __device__ void block_exit(BdCtl *ctl) {
     if (k == gridDim.x - 1) {
       ctl->bar_count = 0;
       ctl->bar_gen = 0;
+      for (int l = 0; l < 3; ++l) ctl->act_n[l] = 0;
       for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 8; ++b) ctl->cnt[a][b] = 0;
       __threadfence();

@@ -267,10 +267,31 @@ __device__ void flip_owned(const Ctx &x, int c0, int o0) {
   x.d.tv[t1] = V1;
   x.d.tn[t0] = N0;
   x.d.tn[t1] = N1;
+  // the four vertices' corners moved: t0 = (b, d, a), t1 = (c, a, d)
+  x.d.vt[b] = 3 * t0 + k0;
+  x.d.vt[dd] = 3 * t0 + (k0 + 1) % 3;
+  x.d.vt[a] = 3 * t0 + (k0 + 2) % 3;
+  x.d.vt[c] = 3 * t1 + k1;
   if (n_ab >= 0) ((int *)&x.d.tn[n_ab / 3])[n_ab % 3] = 3 * t0 + (k0 + 1) % 3;
   if (n_bd >= 0) ((int *)&x.d.tn[n_bd / 3])[n_bd % 3] = 3 * t0 + (k0 + 2) % 3;
   if (n_dc >= 0) ((int *)&x.d.tn[n_dc / 3])[n_dc % 3] = 3 * t1 + (k1 + 1) % 3;
   if (n_ca >= 0) ((int *)&x.d.tn[n_ca / 3])[n_ca % 3] = 3 * t1 + (k1 + 2) % 3;
+}
+
+// Append triangle t to a list once per generation (a list is visited by one
+// check pass; its generation tags the members).  The lanes of a warp that
+// append together reserve their slots with one atomic on the list length.
+__device__ __forceinline__ void push_tri(int *list, unsigned *mark, int *n, unsigned gen, int t) {
+  const bool add = atomicExch(&mark[t], gen) != gen;
+  const unsigned act = __activemask();
+  const unsigned want = __ballot_sync(act, add);
+  if (!want) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(want) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(n, __popc(want));
+  base = __shfl_sync(act, base, leader);
+  if (add) list[base + __popc(want & ((1u << lane) - 1u))] = t;
 }
 
 __device__ __forceinline__ unsigned long long claim_key(unsigned long long epoch, int corner) {
@@ -338,9 +359,35 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
   int log_head = logging ? ctl->log_npairs : 0;
   int log_npass = logging ? ctl->log_npass : 0;
   int log_pidx = -1;
+  // Check-pass domains.  The first pass of a move (and the pass after an
+  // inversion repair) visits every triangle; a later pass visits only a list:
+  // the triangles a flip touched or left dirty, those with an overlapping
+  // edge, and after a correction move the stars of the moved disks.  Every
+  // other edge kept its end points and its place in the triangulation since it
+  // was last checked, so its earlier verdicts (legal, not overlapping) stand.
+  // Lists rotate over three slots: pass kp visits slot kp % 3 (generation
+  // g0 + kp) and fills slot (kp + 1) % 3; the lead empties slot (kp + 2) % 3.
+  const unsigned g0 = *(volatile unsigned *)&ctl->act_gen;
+  int kp = 0;
+  bool full = true;
+  // Lists pay off when a full pass is bound by the number of triangles per
+  // thread; with a few triangles per thread a full pass is as short as one
+  // thread's chain of dependent loads, which a list pass (an extra
+  // indirection and membership reads) only lengthens (measured: 2^20 disks,
+  // 18 triangles per thread, check stage 0.37 -> 0.30 ms per step; 10^5
+  // disks, 1.8 per thread, 0.13 -> 0.17 ms).
+  const bool use_lists = c.tri_lists == 1 || (c.tri_lists == 0 && x.T > 4 * nth);
+  long long tri_visits = 0;
 
   for (;;) {
     ++epoch;
+    const int slot = kp % 3, nslot = (kp + 1) % 3;
+    const unsigned gen = g0 + (unsigned)kp, ngen = gen + 1u;
+    const int *dom = d.act + (size_t)slot * x.T;
+    const unsigned *cmark = d.act_mark + (size_t)slot * x.T;
+    int *nlist = d.act + (size_t)nslot * x.T;
+    unsigned *nmark = d.act_mark + (size_t)nslot * x.T;
+    int *ncount = &ctl->act_n[nslot];
     // ---------------- W: shifts of triangles whose corners re-entered (periodic box) ----------------
     if (fresh && c.any_periodic && *(volatile int *)&ctl->n_wrapped != 0) {
       phase_begin(ctl, b);
@@ -370,11 +417,14 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       first = false;
     }
     // ---------------- P: check, mark, scan ----------------
+    const int dom_n = full ? x.T : *(volatile int *)&ctl->act_n[slot];
+    if (lead) tri_visits += dom_n;
     phase_begin(ctl, b);
     {
       int inv = 0, rej = 0, cand = 0, nov = 0;
       double mx = 0.0;
-      for (int t = tid; t < x.T; t += nth) {
+      for (int it = tid; it < dom_n; it += nth) {
+        const int t = full ? it : dom[it];
         const int4 v = d.tv[t];
         const int4 nn = d.tn[t];
         if (first) {
@@ -395,7 +445,9 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         for (int k = 0; k < 3; ++k) {
           const int cc = 3 * t + k;
           const int o = vk(nn, k);
-          if (o <= cc) continue;   // each interior edge once, from its smaller corner
+          // each interior edge once: from its smaller corner, or from this side
+          // when the neighbour is not visited by this pass
+          if (o < 0 || (o <= cc && (full || cmark[o / 3] == gen))) continue;
           const int u = vk(v, (k + 1) % 3), w = vk(v, (k + 2) % 3);
           const bool disks = u < x.np && w < x.np;
           const bool mv = fresh && (d.moved[u] | d.moved[w]);
@@ -466,6 +518,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
                 atomicAdd(&d.disp[u].y, -del * ny);
                 atomicAdd(&d.disp[w].x, del * nx);
                 atomicAdd(&d.disp[w].y, del * ny);
+                if (use_lists) push_tri(nlist, nmark, ncount, ngen, t);   // checked again in the next pass
                 const int k_ov = atomicAdd(cnt(ctl, b.ph, C_OVERLAP), 1);
                 if (logging) {
                   if (log_head + k_ov < c.log_pairs_cap) d.log_pairs[log_head + k_ov] = make_int2(u, w);
@@ -484,7 +537,10 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       if (mx > 0.0) atomicMax(&ctl->st_max_overlap_bits, (unsigned long long)__double_as_longlong(mx));
     }
     if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
-    if (lead) stage_tick(ctl, STAGE_P, t_mark);
+    if (lead) {
+      stage_tick(ctl, STAGE_P, t_mark);
+      ctl->act_n[(kp + 2) % 3] = 0;   // filled by the next pass
+    }
     first = false;
     const int n_inv = *(volatile int *)cnt(ctl, b.ph - 1, C_INV);
     const int n_rej = *(volatile int *)cnt(ctl, b.ph - 1, C_REJECT);
@@ -577,6 +633,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       }
       if (status) break;
       fresh = false;
+      full = true;   // the repaired region's marks and scan were skipped: check everything
+      ++kp;
       continue;
     }
 
@@ -589,24 +647,35 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       }
       phase_begin(ctl, b);
       {
-        for (int i = tid; i < x.np; i += nth) {
-          d.disp[i] = make_double2(0.0, 0.0);   // this pass's scan is void
-          if (fresh) d.moved[i] = 0;
-        }
+        if (n_ov || fresh)
+          for (int i = tid; i < x.np; i += nth) {
+            if (n_ov) d.disp[i] = make_double2(0.0, 0.0);   // this pass's scan is void
+            if (fresh) d.moved[i] = 0;
+          }
         int nf = 0;
-        for (int t = tid; t < x.T; t += nth) {
+        // the same triangles as the pass that marked the edges: each candidate
+        // is owned by the triangle that tested it
+        for (int it = tid; it < dom_n; it += nth) {
+          const int t = full ? it : dom[it];
           const unsigned long long key = d.claim[t];
           if ((key >> 32) == epoch) {
             const int cm = key_corner(key);
+            bool flipped = false;
             if (cm / 3 == t) {
               const int4 N0 = d.tn[t];
               const int o = vk(N0, cm % 3);
               if (owns6(x, t, cm % 3, N0, o, key)) {
                 flip_owned(x, cm, o);
+                if (use_lists) {
+                  push_tri(nlist, nmark, ncount, ngen, t);
+                  push_tri(nlist, nmark, ncount, ngen, o / 3);
+                }
+                flipped = true;
                 ++nf;
               }
             }
             // claimed but not flipped: stays dirty, its edges are tested again
+            if (use_lists && !flipped && (d.tv[t].w & BD_TRI_DIRTY)) push_tri(nlist, nmark, ncount, ngen, t);
           } else {
             const int tw = d.tv[t].w;
             if (tw & BD_TRI_DIRTY) d.tv[t].w = tw & ~BD_TRI_FLAGS;   // every edge tested and legal
@@ -619,6 +688,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       st_flips += *(volatile int *)cnt(ctl, b.ph - 1, C_FLIPS);
       st_rounds += 1;
       fresh = false;
+      full = !use_lists;
+      ++kp;
       continue;
     }
 
@@ -685,9 +756,23 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         d.work[i] = split_pos(np2);
         d.disp[i] = make_double2(0.0, 0.0);
         d.moved[i] = 1;
+        // the next pass visits the star of the moved disk (walked across the
+        // edges (i, p) of its triangles, from the corner vt[i])
+        const int c0 = d.vt[i];
+        int cw = c0;
+        for (int guard = 0; use_lists && guard < 256; ++guard) {
+          const int tw = cw / 3;
+          push_tri(nlist, nmark, ncount, ngen, tw);
+          const int o = ((const int *)&d.tn[tw])[(cw % 3 + 2) % 3];
+          if (o < 0) break;
+          cw = 3 * (o / 3) + (o % 3 + 2) % 3;
+          if (cw == c0) break;
+        }
       }
       if (c.any_periodic) block_add(&ctl->n_wrapped, nwrap);
-      for (int t = tid; t < x.T; t += nth) {
+      // flags left by the last check pass sit on the triangles it visited
+      for (int it = tid; it < dom_n; it += nth) {
+        const int t = full ? it : dom[it];
         const int tw = d.tv[t].w;
         if (tw & BD_TRI_FLAGS) d.tv[t].w = tw & ~BD_TRI_FLAGS;
       }
@@ -695,6 +780,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
     if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
     if (lead) stage_tick(ctl, STAGE_A, t_mark);
     fresh = true;
+    full = !use_lists;
+    ++kp;
   }
 
   if (status) {
@@ -711,8 +798,13 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       d.moved[i] = 0;
     }
     for (int t = tid; t < x.T; t += nth) {
-      d.tv[t] = d.tv_snap[t];
+      const int4 vs = d.tv_snap[t];
+      d.tv[t] = vs;
       d.tn[t] = d.tn_snap[t];
+      // a corner per vertex of the restored triangulation (any one will do)
+      d.vt[vs.x] = 3 * t;
+      d.vt[vs.y] = 3 * t + 1;
+      d.vt[vs.z] = 3 * t + 2;
     }
     if (lead) atomicCAS(&ctl->status, 0, status);
   } else {
@@ -725,6 +817,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       d.log_step_pass[log_step + 1] = log_npass;
     }
     ctl->epoch = epoch + 1;
+    ctl->act_gen = g0 + (unsigned)kp + 3u;
+    ctl->st_tri_visits += tri_visits;
     ctl->st_corr_iters += corr_iter;
     ctl->st_overlap_pairs += st_overlap;
     ctl->st_flips += st_flips;

@@ -142,7 +142,11 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32(BdDev d, BdConst c) {
 // near pairs at FP32 resolution of their separation wherever they sit in the
 // block.  Inert padding slots are staged far away and never wrapped.
 // Replicas with walls in the same batch run here too (no wrap, hL = +inf).
-// Per ordered pair: 12 FP32 lane operations + 1 MUFU + the wrap test.
+// Per (block, tile) the bounding boxes of the two decide the form used for
+// all its pairs: no pair beyond L/2 in a component and no pair closer than
+// 6 (box gap) -> the hi parts alone (8 FP32 lane operations + 1 MUFU per
+// pair, as the walls sweep); close boxes -> the exact (hi, lo) vector (12);
+// boxes straddling L/2 -> (hi, lo) with the per-pair minimum image.
 __device__ __forceinline__ float4 stage_q(const BdDev &d, const BdConst &c, int j, long long ox, long long oy,
                                           long long LQ) {
   if (d.ext_id[j] < 0) return make_float4(1.0e18f, 1.0e18f, 0.f, 0.f);
@@ -163,9 +167,34 @@ __device__ __forceinline__ float min_image(float dx, float Lf, float hLf) {
   return dx < -hLf ? __fadd_rn(dx, Lf) : dx;
 }
 
+// bounding box (x_min, x_max, y_min, y_max) of staged coordinates, inert
+// slots (1e18) left out; block-wide through per-warp partials in shared memory
+__device__ __forceinline__ void box_add(float4 &bx, float x, float y) {
+  if (x > 1.0e17f) return;
+  bx.x = fminf(bx.x, x);
+  bx.y = fmaxf(bx.y, x);
+  bx.z = fminf(bx.z, y);
+  bx.w = fmaxf(bx.w, y);
+}
+__device__ __forceinline__ float4 warp_box(float4 bx) {
+  for (int o = 16; o > 0; o >>= 1) {
+    bx.x = fminf(bx.x, __shfl_xor_sync(0xffffffffu, bx.x, o));
+    bx.y = fmaxf(bx.y, __shfl_xor_sync(0xffffffffu, bx.y, o));
+    bx.z = fminf(bx.z, __shfl_xor_sync(0xffffffffu, bx.z, o));
+    bx.w = fmaxf(bx.w, __shfl_xor_sync(0xffffffffu, bx.w, o));
+  }
+  return bx;
+}
+__device__ __forceinline__ float4 empty_box() { return make_float4(3e38f, -3e38f, 3e38f, -3e38f); }
+__device__ __forceinline__ float4 merge_box(float4 a, float4 b) {
+  return make_float4(fminf(a.x, b.x), fmaxf(a.y, b.y), fminf(a.z, b.z), fmaxf(a.w, b.w));
+}
+
 __global__ void __launch_bounds__(BD_FT) k_force_long_per(BdDev d, BdConst c) {
   if (ctl_failed(d.ctl)) return;
   __shared__ float4 sj[2][BD_TJ];   // per j: (x_hi, y_hi, x_lo, y_lo) re-centred
+  __shared__ float4 sbox[2][BD_FT / 32];   // per-warp boxes of the staged tile
+  __shared__ float4 sibox[BD_FT / 32];     // per-warp boxes of the block's disks i
   const int4 item = d.items[blockIdx.x];  // (i block, first tile, end tile, partial slot)
   const int ib = item.x, slot = item.w, tid = threadIdx.x;
   const float2 org = d.iorigin[ib];
@@ -209,34 +238,95 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_per(BdDev d, BdConst c) {
   }
   const int t_begin = item.y, t_end = item.z;
   const float eps0 = 1e-20f * (float)(c.a * c.a);
+  const int warp = tid >> 5, lane = tid & 31;
+  {
+    float4 bx = empty_box();
+#pragma unroll
+    for (int q = 0; q < BD_IPT; ++q) box_add(bx, xh[q], yh[q]);
+    bx = warp_box(bx);
+    if (lane == 0) sibox[warp] = bx;
+  }
   float4 st0, st1;
   auto fetch = [&](int tile) {
     const int j0 = tile * BD_TJ + tid;
     st0 = stage_q(d, c, j0, ox, oy, LQ);
     st1 = stage_q(d, c, j0 + BD_FT, ox, oy, LQ);
   };
+  auto store = [&](int b) {
+    sj[b][tid] = st0;
+    sj[b][tid + BD_FT] = st1;
+    float4 bx = empty_box();
+    box_add(bx, st0.x, st0.y);
+    box_add(bx, st1.x, st1.y);
+    bx = warp_box(bx);
+    if (lane == 0) sbox[b][warp] = bx;
+  };
   int buf = 0;
   if (t_begin < t_end) {
     fetch(t_begin);
-    sj[0][tid] = st0;
-    sj[0][tid + BD_FT] = st1;
+    store(0);
   }
   __syncthreads();
+  float4 ibx = empty_box();
+#pragma unroll
+  for (int w = 0; w < BD_FT / 32; ++w) ibx = merge_box(ibx, sibox[w]);
   for (int t = t_begin; t < t_end; ++t) {
     if (t + 1 < t_end) fetch(t + 1);
-#pragma unroll 4
-    for (int jj = 0; jj < BD_TJ; ++jj) {
-      const float4 p = sj[buf][jj];
+    float4 jb = empty_box();
 #pragma unroll
-      for (int q = 0; q < BD_IPT; ++q) {
-        const float dx = __fadd_rn(min_image(__fsub_rn(p.x, xh[q]), Lf, hLf), __fsub_rn(p.z, xl[q]));
-        const float dy = __fadd_rn(min_image(__fsub_rn(p.y, yh[q]), Lf, hLf), __fsub_rn(p.w, yl[q]));
-        float r2 = __fmaf_rn(dx, dx, eps0);
-        r2 = __fmaf_rn(dy, dy, r2);
-        const float sv = rsqrt_apx(r2);
-        const float s3 = __fmul_rn(__fmul_rn(sv, sv), sv);
-        ax[q] = __fmaf_rn(dx, s3, ax[q]);
-        ay[q] = __fmaf_rn(dy, s3, ay[q]);
+    for (int w = 0; w < BD_FT / 32; ++w) jb = merge_box(jb, sbox[buf][w]);
+    // pair components range over [jmin - imax, jmax - imin]
+    const bool wrap = jb.y - ibx.x > hLf || jb.x - ibx.y < -hLf || jb.w - ibx.z > hLf || jb.z - ibx.w < -hLf;
+    const float gx = fmaxf(0.f, fmaxf(jb.x - ibx.y, ibx.x - jb.y));
+    const float gy = fmaxf(0.f, fmaxf(jb.z - ibx.w, ibx.z - jb.w));
+    const bool near = gx * gx + gy * gy < 36.f;
+    if (wrap) {
+#pragma unroll 4
+      for (int jj = 0; jj < BD_TJ; ++jj) {
+        const float4 p = sj[buf][jj];
+#pragma unroll
+        for (int q = 0; q < BD_IPT; ++q) {
+          const float dx = __fadd_rn(min_image(__fsub_rn(p.x, xh[q]), Lf, hLf), __fsub_rn(p.z, xl[q]));
+          const float dy = __fadd_rn(min_image(__fsub_rn(p.y, yh[q]), Lf, hLf), __fsub_rn(p.w, yl[q]));
+          float r2 = __fmaf_rn(dx, dx, eps0);
+          r2 = __fmaf_rn(dy, dy, r2);
+          const float sv = rsqrt_apx(r2);
+          const float s3 = __fmul_rn(__fmul_rn(sv, sv), sv);
+          ax[q] = __fmaf_rn(dx, s3, ax[q]);
+          ay[q] = __fmaf_rn(dy, s3, ay[q]);
+        }
+      }
+    } else if (near) {
+#pragma unroll 4
+      for (int jj = 0; jj < BD_TJ; ++jj) {
+        const float4 p = sj[buf][jj];
+#pragma unroll
+        for (int q = 0; q < BD_IPT; ++q) {
+          const float dx = __fadd_rn(__fsub_rn(p.x, xh[q]), __fsub_rn(p.z, xl[q]));
+          const float dy = __fadd_rn(__fsub_rn(p.y, yh[q]), __fsub_rn(p.w, yl[q]));
+          float r2 = __fmaf_rn(dx, dx, eps0);
+          r2 = __fmaf_rn(dy, dy, r2);
+          const float sv = rsqrt_apx(r2);
+          const float s3 = __fmul_rn(__fmul_rn(sv, sv), sv);
+          ax[q] = __fmaf_rn(dx, s3, ax[q]);
+          ay[q] = __fmaf_rn(dy, s3, ay[q]);
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int jj = 0; jj < BD_TJ; ++jj) {
+        const float4 p = sj[buf][jj];
+#pragma unroll
+        for (int q = 0; q < BD_IPT; ++q) {
+          const float dx = __fsub_rn(p.x, xh[q]);
+          const float dy = __fsub_rn(p.y, yh[q]);
+          float r2 = __fmaf_rn(dx, dx, eps0);
+          r2 = __fmaf_rn(dy, dy, r2);
+          const float sv = rsqrt_apx(r2);
+          const float s3 = __fmul_rn(__fmul_rn(sv, sv), sv);
+          ax[q] = __fmaf_rn(dx, s3, ax[q]);
+          ay[q] = __fmaf_rn(dy, s3, ay[q]);
+        }
       }
     }
     // (r_j - r_i) was summed: the force on i is -A[s_i][s_tile] times it
@@ -248,10 +338,7 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_per(BdDev d, BdConst c) {
       two_sum(fyh[q], fyl[q], -al * ay[q]);
       ax[q] = ay[q] = 0.f;
     }
-    if (t + 1 < t_end) {
-      sj[buf ^ 1][tid] = st0;
-      sj[buf ^ 1][tid + BD_FT] = st1;
-    }
+    if (t + 1 < t_end) store(buf ^ 1);
     __syncthreads();
     buf ^= 1;
   }

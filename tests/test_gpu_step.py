@@ -230,3 +230,44 @@ def test_graph_replay_equals_plain_launches(monkeypatch, cfgname, n):
     assert out[0]["step"] == out[1]["step"] == 8
     assert np.array_equal(out[0]["xy"], out[1]["xy"])
     assert np.array_equal(out[0]["tri"], out[1]["tri"])
+
+
+@pytest.mark.parametrize("cfgname,n,seed,k", [("c2", 4000, 1, 0), ("c5", 4096, 4, 99)])
+def test_one_step_parity_with_check_lists(monkeypatch, cfgname, n, seed, k):
+    # the check passes after the first of a move visit only listed triangles
+    # (used by default when a full pass has many triangles per thread, i.e. at
+    # 2^20 disks); BD_TRI_LISTS=1 forces them at sizes the oracle steps fully
+    monkeypatch.setenv("BD_TRI_LISTS", "1")
+    cfg, L, s, st, out, ref = _one_step(cfgname, n, seed, k)
+    assert not ref["rejected"] and ref["corr_iters"] >= 1
+    assert float(np.max(np.abs(out["xy"] - ref["xy"]))) <= POS_TOL * cfg.a
+    assert st["corr_iters"] == ref["corr_iters"]
+    assert np.array_equal(geometry.edges(out["tri"]), geometry.edges(ref["tris"]))
+    assert len(cKDTree(out["xy"]).query_pairs(2 * cfg.a * (1 - 1e-12))) == 0
+    # the later passes visited far fewer triangles than full passes would
+    passes = s.stage_times()["check"][1]
+    assert passes >= 2 and st["tri_visits"] < s.n_tri * (1 + 0.5 * (passes - 1))
+
+
+def test_multi_step_with_check_lists_matches_full_passes(monkeypatch):
+    # 60 steps with lists and with full passes: the same trajectory (up to the
+    # order of FP64 atomic additions in Algorithm 2) and the same
+    # triangulation, Delaunay every 20 steps
+    cfg = workloads.CONFIGS["c5"]
+    n = 4096
+    xy, sp, th = workloads.initial_state(cfg, n=n)
+    L = workloads.box_side(n, cfg.rho)
+    monkeypatch.setenv("BD_TRI_LISTS", "1")
+    a = bd.System(bd.params_from_config(cfg, n=n), xy, sp, th, stream=stream())
+    monkeypatch.setenv("BD_TRI_LISTS", "2")
+    b = bd.System(bd.params_from_config(cfg, n=n), xy, sp, th, stream=stream())
+    for _ in range(3):
+        sa, sb = a.step(20), b.step(20)
+        assert sa["steps_done"] == sb["steps_done"] == 20
+        assert sa["tri_visits"] < sb["tri_visits"]
+        oa, ob = a.state(), b.state()
+        assert float(np.max(np.abs(oa["xy"] - ob["xy"]))) <= 1e-9
+        assert np.array_equal(geometry.edges(oa["tri"]), geometry.edges(ob["tri"]))
+        assert np.array_equal(geometry.edges(oa["tri"]), geometry.edges(geometry.delaunay(oa["xy"], L)))
+    a.close()
+    b.close()
