@@ -171,18 +171,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind):
+def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind, visits=None):
     """HBM roofline of the per-step correction kernel of the short-range path.
 
     Duration: the kernel's own device-clock stage timers (bd_stage_times),
     summed over its stages, per launch (one launch per step).  Algorithmic
-    bytes per launch, from the pass counts of the same timers:
-      k_triangulation: every check pass reads the corner table (32 B per
-        triangle) and each disk's moved flag and FP32 position (17 B); the
-        first pass also writes the rollback snapshot (32 B per triangle); a
-        flip round reads the claims and flags (24 B per triangle); an apply
-        pass reads and writes positions, displacements and flags (100 B per
-        disk) and clears triangle flags (16 B per triangle).
+    bytes per launch, from the pass counts of the same timers and the
+    triangles the check passes visited (bd_step_stats.tri_visits, V):
+      k_triangulation: a check pass reads the corner table of each triangle
+        it visits (32 B) and, in the first pass of the step, each disk's moved
+        flag and FP32 position (17 B); the first pass also writes the rollback
+        snapshot (32 B per triangle); a flip round reads the claims and flags
+        of the triangles its pass visited (24 B each); an apply pass reads and
+        writes positions, displacements and flags (100 B per disk).
       k_overlap_verlet: a scan pass reads each disk's count, flag, both
         position copies and its list with the neighbours' flags (38 + 5 m B
         per disk, m the mean list length) and writes its displacement and hit
@@ -200,10 +201,11 @@ def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind):
     else:
         T = system.n_tri
         P, F, A = (stage_raw[k][1] / steps for k in ("check", "flip", "apply"))
-        per = P * (32 * T + 17 * N) + 32 * T + F * 24 * T + A * (100 * N + 16 * T)
+        V = visits if visits else P * T
+        per = 32 * V + 17 * N + 32 * T + 24 * V * (F / max(P, 1.0)) + A * 100 * N
         kernel = "k_triangulation"
-        note = ("%.2f check passes, %.2f flip rounds, %.2f apply passes per launch over %d triangles"
-                % (P, F, A, T))
+        note = ("%.2f check passes visiting %.0f triangles, %.2f flip rounds, %.2f apply passes per "
+                "launch; %d triangles" % (P, V, F, A, T))
     gbs = per / (ms / 1e3) / 1e9
     peak = float(pk.get("hbm_gbs", 6800.0))
     return {"bound": "hbm", "kernel": kernel, "achieved": gbs, "peak": peak, "unit": "GB/s",
@@ -415,7 +417,7 @@ def main():
             st = system.step(1)
             ev[k][1].record(stream)
             launches += system.last_launch_count()
-            for key in ("corr_iters", "flips", "repair_flips", "overlap_pairs", "inverted"):
+            for key in ("corr_iters", "flips", "repair_flips", "overlap_pairs", "inverted", "tri_visits"):
                 stats_tot[key] = stats_tot.get(key, 0) + st[key]
         torch.cuda.synchronize()
     if ws > 1:
@@ -532,7 +534,8 @@ def main():
             # no all-pairs launch (short-range law): the dominant kernel is the
             # persistent correction kernel, bound by memory (gathers), so its
             # line is HBM bytes against the measured copy bandwidth
-            line["roofline"] = correction_roofline(system, stage_raw, args.steps, N, verlet_mode, pk, pk_kind)
+            line["roofline"] = correction_roofline(system, stage_raw, args.steps, N, verlet_mode, pk, pk_kind,
+                                                   stats_tot.get("tri_visits", 0) / args.steps)
         elif cfg.precision == 1:
             # FP64 sweep (one disk per thread, 12 FP64 flops per ordered pair);
             # FP64 issues at 1/64 of the FP32 rate on this part
