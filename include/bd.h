@@ -60,16 +60,18 @@ enum { BD_LAW_NONE = 0, BD_LAW_LONG = 1, BD_LAW_SHORT = 2 };
  * memory; the pair-force charges are those of Sec. 2.2. */
 typedef struct bd_params {
   int32_t n;             /* number of disks, >= 1 */
-  int32_t n_species;     /* 1 or 2 */
+  int32_t n_species;     /* 1 to 4 */
   double a;              /* disk radius (> 0); sigma = 2a */
   double box_L;          /* box side; <= 0 => sqrt(n pi a^2 / area_fraction) (Sec. 6) */
   double area_fraction;  /* used only when box_L <= 0 */
   int32_t law;           /* BD_LAW_NONE, BD_LAW_LONG (Sec. 2.2, f = r/r^3, all pairs),
                             BD_LAW_SHORT (WCA core + Yukawa tail, cut at r_cut, Verlet lists) */
   int32_t precision;     /* 0: forces and increments in FP32; 1: in FP64 */
-  double alpha[4];       /* long range: A[s_i][s_j] row-major, coefficient of the force ON
-                            species s_i FROM species s_j, F_i = sum_j A (r_i - r_j)/|r_ij|^3
-                            (= mu_i alpha_j of Sec. 2.2); A > 0 repels */
+  double alpha[16];      /* long range: the n_species x n_species table A, row-major
+                            (A[s_i][s_j] at alpha[s_i * n_species + s_j]; one species: alpha[0]),
+                            coefficient of the force ON species s_i FROM species s_j,
+                            F_i = sum_j A (r_i - r_j)/|r_ij|^3 (= mu_i alpha_j of Sec. 2.2, which
+                            allows any number of species); A > 0 repels */
   double eps, kappa;     /* short range: energy scale and Yukawa inverse length */
   double r_cut, skin;    /* short range: cut-off radius and Verlet skin */
   double D;              /* translational diffusion coefficient */
@@ -362,14 +364,17 @@ int bd_forces_noalloc(int32_t n, const double *xy, const uint8_t *species, const
  * them: the Philox noise, the wall reflections of every move, and for every
  * correction pass (Algorithm 2) its overlapping pairs and which disks had
  * their displacement capped at sigma/4.  Rounding to the position grid is
- * taken as the identity.  Long-range law and single-system handles only.
+ * taken as the identity.  Long-range law, walls, one or two species and
+ * single-system handles only.
  * Pair terms of the adjoint are computed in FP32, every sum in FP64. */
 
 enum { BD_LOSS_MSD = 0 };
 
-/* Replace the force table (alpha: 4 doubles as bd_params.alpha, NULL = keep)
- * and the self-propulsion speed (v0; NaN = keep) of every replica.  Discards
- * a recorded rollout.  Errors: BD_ERR_ARG (non-finite alpha), BD_ERR_CUDA. */
+/* Replace the force table (alpha: 4 doubles, the table of one or two species
+ * as bd_params.alpha, NULL = keep) and the self-propulsion speed (v0; NaN =
+ * keep) of every replica.  Discards a recorded rollout.  Errors: BD_ERR_ARG
+ * (non-finite alpha), BD_ERR_UNSUPPORTED (alpha given and a replica has more
+ * than two species), BD_ERR_CUDA. */
 int bd_set_force_params(bd_handle *h, const double *alpha, double v0);
 
 /* Set the index of the next step (the Philox counter of its noise). */

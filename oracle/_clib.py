@@ -44,10 +44,11 @@ def lib():
             L.oracle_delaunay.argtypes = [ctypes.c_int, p, p, p, p]
             L.oracle_delaunay.restype = ctypes.c_int
             L.oracle_force_long.argtypes = [ctypes.c_int, p, p, p, p, ctypes.c_int, ctypes.c_int,
-                                            p, p, ctypes.c_int]
+                                            ctypes.c_int, p, p, ctypes.c_int]
             L.oracle_force_long.restype = None
-            L.oracle_force_long_periodic.argtypes = [ctypes.c_int, p, p, p, p, ctypes.c_double,
-                                                     ctypes.c_int, ctypes.c_int, p, p, ctypes.c_int]
+            L.oracle_force_long_periodic.argtypes = [ctypes.c_int, p, p, p, p, ctypes.c_int,
+                                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, p, p,
+                                                     ctypes.c_int]
             L.oracle_force_long_periodic.restype = None
             L.oracle_force_long_jvp.argtypes = [ctypes.c_int, p, p, p, p, ctypes.c_int, p, p, p, p,
                                                 ctypes.c_int]

@@ -427,7 +427,7 @@ int oracle_delaunay(int n, const double *x, const double *y, const int *order, i
 
 /* F_i = sum_{j != i} A[s_i][s_j] (r_i - r_j) / |r_i - r_j|^3 for i in [i0, i1) */
 void oracle_force_long(int n, const double *x, const double *y, const uint8_t *s, const double *A,
-                       int i0, int i1, double *fx, double *fy, int nthreads) {
+                       int ns, int i0, int i1, double *fx, double *fy, int nthreads) {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
 #endif
@@ -438,7 +438,7 @@ void oracle_force_long(int n, const double *x, const double *y, const uint8_t *s
             double rx = x[i] - x[j], ry = y[i] - y[j];
             double r2 = rx * rx + ry * ry;
             double r = sqrt(r2);
-            double c = A[2 * s[i] + s[j]] / (r2 * r);
+            double c = A[ns * s[i] + s[j]] / (r2 * r);
             ax += c * rx;
             ay += c * ry;
         }
@@ -452,8 +452,8 @@ void oracle_force_long(int n, const double *x, const double *y, const uint8_t *s
  * convention (Sec. 2.1): r_ij is replaced by its image nearest the origin,
  * r_ij - L round(r_ij / L) per component. */
 void oracle_force_long_periodic(int n, const double *x, const double *y, const uint8_t *s,
-                                const double *A, double L, int i0, int i1, double *fx, double *fy,
-                                int nthreads) {
+                                const double *A, int ns, double L, int i0, int i1, double *fx,
+                                double *fy, int nthreads) {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
 #endif
@@ -466,7 +466,7 @@ void oracle_force_long_periodic(int n, const double *x, const double *y, const u
             ry -= L * nearbyint(ry / L);
             double r2 = rx * rx + ry * ry;
             double r = sqrt(r2);
-            double c = A[2 * s[i] + s[j]] / (r2 * r);
+            double c = A[ns * s[i] + s[j]] / (r2 * r);
             ax += c * rx;
             ay += c * ry;
         }

@@ -3,7 +3,7 @@
 Long range (Sec. 2.2): the force on disk i is the sum over every other disk
 k of mu_i alpha_k f(r_i - r_k) with f(r) = r / |r|^3.  The charges enter only
 through the product for the ordered species pair, so the oracle stores that
-product as a 2x2 table A[s_i][s_k] ("force ON species s_i FROM species s_k");
+product as an n x n table A[s_i][s_k] (n species) ("force ON species s_i FROM species s_k");
 a positive entry pushes i away from k.  The table need not factor as
 mu_i alpha_k, nor be symmetric (non-reciprocal interactions).  With
 reflecting walls there are no images; in a periodic box (Sec. 2.1) every
@@ -23,12 +23,22 @@ import numpy as np
 from . import _clib
 
 
+def species_table(A):
+    """The n x n table A[s_i][s_k] from its row-major entries (n^2 of them,
+    n = 1 .. 4)."""
+    A = np.asarray(A, dtype=np.float64).reshape(-1)
+    n = int(round(len(A) ** 0.5))
+    if n * n != len(A):
+        raise ValueError("a square table is needed, got %d entries" % len(A))
+    return A.reshape(n, n)
+
+
 def long_range_numpy(xy, species, A, idx=None, L=None):
     """Direct O(N^2) sum, numpy, for moderate N.  Returns (n_idx, 2).
     L: periodic box side (minimum-image pair vectors, Sec. 2.1); None = walls."""
     xy = np.asarray(xy, dtype=np.float64)
     s = np.asarray(species, dtype=np.int64)
-    A = np.asarray(A, dtype=np.float64).reshape(2, 2)
+    A = species_table(A)
     n = len(xy)
     idx = np.arange(n) if idx is None else np.asarray(idx)
     out = np.zeros((len(idx), 2))
@@ -54,7 +64,9 @@ def long_range(xy, species, A, idx=None, threads=1, L=None):
     x = np.ascontiguousarray(xy[:, 0])
     y = np.ascontiguousarray(xy[:, 1])
     s = np.ascontiguousarray(np.asarray(species, dtype=np.uint8))
-    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(4))
+    T = species_table(A)
+    ns = len(T)
+    A = np.ascontiguousarray(T.reshape(-1))
     if idx is None:
         i0, i1 = 0, n
     else:
@@ -65,9 +77,9 @@ def long_range(xy, species, A, idx=None, threads=1, L=None):
     fy = np.zeros(i1 - i0)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     if L is None:
-        _clib.lib().oracle_force_long(n, p(x), p(y), p(s), p(A), i0, i1, p(fx), p(fy), int(threads))
+        _clib.lib().oracle_force_long(n, p(x), p(y), p(s), p(A), ns, i0, i1, p(fx), p(fy), int(threads))
     else:
-        _clib.lib().oracle_force_long_periodic(n, p(x), p(y), p(s), p(A), float(L), i0, i1, p(fx),
+        _clib.lib().oracle_force_long_periodic(n, p(x), p(y), p(s), p(A), ns, float(L), i0, i1, p(fx),
                                                p(fy), int(threads))
     return np.stack([fx, fy], axis=1)
 

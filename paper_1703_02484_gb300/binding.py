@@ -27,7 +27,7 @@ class bd_params(ctypes.Structure):
         ("n", ctypes.c_int32), ("n_species", ctypes.c_int32),
         ("a", ctypes.c_double), ("box_L", ctypes.c_double), ("area_fraction", ctypes.c_double),
         ("law", ctypes.c_int32), ("precision", ctypes.c_int32),
-        ("alpha", ctypes.c_double * 4),
+        ("alpha", ctypes.c_double * 16),
         ("eps", ctypes.c_double), ("kappa", ctypes.c_double),
         ("r_cut", ctypes.c_double), ("skin", ctypes.c_double),
         ("D", ctypes.c_double), ("Dr", ctypes.c_double), ("v0", ctypes.c_double), ("dt", ctypes.c_double),
@@ -158,7 +158,9 @@ def make_params(n, L=None, rho=None, a=1.0, law=LAW_NONE, alpha=(0, 0, 0, 0), n_
     p.box_L = float(L) if L is not None else 0.0
     p.area_fraction = float(rho) if rho is not None else 0.0
     p.law, p.precision = int(law), int(precision)
-    for k in range(4):
+    if len(alpha) > 16:
+        raise ValueError("alpha: at most a 4 x 4 table")
+    for k in range(len(alpha)):
         p.alpha[k] = float(alpha[k])
     p.eps, p.kappa, p.r_cut, p.skin = float(eps), float(kappa), float(r_cut), float(skin)
     p.D, p.Dr, p.v0, p.dt = float(D), float(Dr), float(v0), float(dt)

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(BD_ADJ_T) k_vjp_force(BdDev d, BdConst c, cons
   const double2 mui_d = live ? mu[i] : make_double2(0.0, 0.0);
   const float2 mui = make_float2((float)mui_d.x, (float)mui_d.y);
   const int si = live ? (d.species[i] ? 1 : 0) : 0;
-  const float ai0 = R.alpha[2 * si], ai1 = R.alpha[2 * si + 1];
+  const float ai0 = R.alpha[BD_MAX_SPECIES * si], ai1 = R.alpha[BD_MAX_SPECIES * si + 1];
   double jx = 0.0, jy = 0.0, s0x = 0.0, s0y = 0.0, s1x = 0.0, s1y = 0.0;
   const int jb = blockIdx.y * jchunk, je = min(c.np, jb + jchunk);
   for (int j0 = jb; j0 < je; j0 += BD_ADJ_T) {
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(BD_ADJ_T) k_vjp_force(BdDev d, BdConst c, cons
       const float q3 = (rx == 0.f && ry == 0.f) ? 0.f : ir2 * ir;
       const int sj = ssp[k];
       const float aij = sj ? ai1 : ai0;
-      const float aji = R.alpha[2 * sj + si];
+      const float aji = R.alpha[BD_MAX_SPECIES * sj + si];
       // w = A_ij mu_i - A_ji mu_j;  M w = (w - 3 r (r . w)/r^2) / r^3
       const float wx = aij * mui.x - aji * smu[k].x, wy = aij * mui.y - aji * smu[k].y;
       const float rw = (rx * wx + ry * wy) * ir2;

@@ -43,6 +43,16 @@ namespace bdcapi {
 
 int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? BD_ERR_NOMEM : BD_ERR_CUDA; }
 
+void rep_set_alpha(BdRep &B, const double *alpha, int n_species) {
+  for (int i = 0; i < BD_MAX_SPECIES; ++i)
+    for (int j = 0; j < BD_MAX_SPECIES; ++j) {
+      double v = 0.0;
+      if (i < n_species && j < n_species) v = n_species == 1 ? alpha[0] : alpha[i * n_species + j];
+      B.alpha_d[BD_MAX_SPECIES * i + j] = v;
+      B.alpha[BD_MAX_SPECIES * i + j] = (float)v;
+    }
+}
+
 }  // namespace bdcapi
 
 using namespace bdcapi;
@@ -86,14 +96,14 @@ double coord_extent(const bd_params &p) {
 int validate(const bd_params *p) {
   if (!p) return BD_ERR_ARG;
   if (p->n < 1 || p->n > (1 << 28)) return BD_ERR_ARG;
-  if (p->n_species < 1 || p->n_species > 2) return BD_ERR_ARG;
+  if (p->n_species < 1 || p->n_species > BD_MAX_SPECIES) return BD_ERR_ARG;
   if (!(p->a > 0) || !isfinite(p->a)) return BD_ERR_ARG;
   if (!(p->box_L > 0) && !(p->area_fraction > 0 && p->area_fraction < 0.9)) return BD_ERR_ARG;
   if (p->law < BD_LAW_NONE || p->law > BD_LAW_SHORT) return BD_ERR_ARG;
   if (p->precision < 0 || p->precision > 1) return BD_ERR_ARG;
   if (!(p->dt > 0) || !isfinite(p->dt)) return BD_ERR_ARG;
   if (!(p->D >= 0) || !(p->Dr >= 0) || !isfinite(p->v0)) return BD_ERR_ARG;
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < p->n_species * p->n_species; ++k)
     if (!isfinite(p->alpha[k])) return BD_ERR_ARG;
   if (p->max_corr_iters < 1 || p->max_flip_rounds < 1) return BD_ERR_ARG;
   if (p->law == BD_LAW_SHORT) {
@@ -470,11 +480,16 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
       if (hk[x] != hk[y]) return hk[x] < hk[y];
       return x < y;
     });
-    int cnt_sp[2] = {0, 0};
+    // one segment per species, each a whole number of 512-disk blocks
+    int cnt_sp[BD_MAX_SPECIES] = {0, 0, 0, 0}, seg[BD_MAX_SPECIES], seg_begin[BD_MAX_SPECIES + 1];
     for (int i = 0; i < n; ++i) cnt_sp[sp[i]]++;
-    const int seg0 = (int)pad_to(cnt_sp[0], BD_SB), seg1 = (int)pad_to(cnt_sp[1], BD_SB);
+    seg_begin[0] = slot;
+    for (int k = 0; k < BD_MAX_SPECIES; ++k) {
+      seg[k] = (int)pad_to(cnt_sp[k], BD_SB);
+      seg_begin[k + 1] = seg_begin[k] + seg[k];
+    }
     RH.slot_begin = slot;
-    RH.slot_end = slot + seg0 + seg1;
+    RH.slot_end = seg_begin[BD_MAX_SPECIES];
     RH.tile_begin = slot / BD_TJ;
     RH.tile_end = RH.slot_end / BD_TJ;
     slot_ext.resize(RH.slot_end, -1);
@@ -482,10 +497,11 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     slot_rep.resize(RH.slot_end, -1);
     std::vector<int> local_slot(n);
     {
-      int k0 = slot, k1 = slot + seg0;
+      int next[BD_MAX_SPECIES];
+      for (int k = 0; k < BD_MAX_SPECIES; ++k) next[k] = seg_begin[k];
       for (int k = 0; k < n; ++k) {
         int e = by_sp[k];
-        int sl = sp[e] == 0 ? k0++ : k1++;
+        int sl = next[sp[e]]++;
         slot_ext[sl] = RH.ext_base + e;
         slot_local[sl] = e;
         slot_rep[sl] = r;
@@ -493,7 +509,11 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
       }
     }
     for (int t = RH.tile_begin; t < RH.tile_end; ++t)
-      tile_sp.push_back((t * BD_TJ - RH.slot_begin) < seg0 ? 0 : 1);
+    {
+      int k = 0;
+      while (k + 1 < BD_MAX_SPECIES && t * BD_TJ >= seg_begin[k + 1]) ++k;
+      tile_sp.push_back((uint8_t)k);
+    }
     slot = RH.slot_end;
     // force i blocks: Hilbert order over the replica's disks
     std::vector<int> by_h(n);
@@ -683,10 +703,7 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     B.r_cut = p.r_cut;
     B.skin = p.skin;
     B.rl2 = (p.r_cut + p.skin) * (p.r_cut + p.skin);
-    for (int k = 0; k < 4; ++k) {
-      B.alpha_d[k] = p.n_species == 1 ? p.alpha[0] : p.alpha[k];
-      B.alpha[k] = (float)B.alpha_d[k];
-    }
+    rep_set_alpha(B, p.alpha, p.n_species);
     B.seed = p.seed;
     B.replica = (unsigned)p.replica;
     B.law = p.law;

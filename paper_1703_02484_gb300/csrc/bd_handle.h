@@ -70,6 +70,9 @@ struct bd_handle {
 };
 
 namespace bdcapi {
+// the user's n_species x n_species table (row-major; one species: alpha[0])
+// into the replica's BD_MAX_SPECIES-wide FP64 and FP32 tables
+void rep_set_alpha(BdRep &B, const double *alpha, int n_species);
 int cuda_fail(cudaError_t e);
 int read_ctl(bd_handle *h);                // copy the control block to h_ctl (synchronises)
 cudaError_t reset_stats(bd_handle *h);     // zero the per-call statistics

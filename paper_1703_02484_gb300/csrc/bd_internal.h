@@ -14,6 +14,9 @@
 // segments are padded to whole blocks so a block holds one species
 #define BD_SB 512
 
+// species per system (the long-range table is stored BD_MAX_SPECIES wide)
+#define BD_MAX_SPECIES 4
+
 // Verlet list capacity per disk (hard disks of radius a have at most ~40
 // neighbours within 5.6a even at close packing)
 #define BD_VL_MAX 64
@@ -88,8 +91,8 @@ struct BdRep {
   long long LQ;
   double dt, amp, amp_r, v0;
   double eps, kappa, r_cut, skin, rl2, cell_size;
-  double alpha_d[4];
-  float alpha[4];
+  double alpha_d[BD_MAX_SPECIES * BD_MAX_SPECIES];   // A[s_i][s_j] at [BD_MAX_SPECIES s_i + s_j]
+  float alpha[BD_MAX_SPECIES * BD_MAX_SPECIES];
   unsigned long long seed;
   unsigned int replica;
   int law;

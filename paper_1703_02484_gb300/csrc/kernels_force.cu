@@ -43,25 +43,22 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32(BdDev d, BdConst c) {
   const int ib = item.x, slot = item.w, tid = threadIdx.x;
   const float2 org = d.iorigin[ib];
   float xi[BD_IPT], yi[BD_IPT], ax[BD_IPT], ay[BD_IPT];
-  float fxh[BD_IPT], fxl[BD_IPT], fyh[BD_IPT], fyl[BD_IPT], a0[BD_IPT], a1[BD_IPT];
+  float fxh[BD_IPT], fxl[BD_IPT], fyh[BD_IPT], fyl[BD_IPT];
+  const float *arow[BD_IPT];   // row A[s_i][.] of the table (the block is one replica's)
   int ii[BD_IPT];
 #pragma unroll
   for (int q = 0; q < BD_IPT; ++q) {
     int i = d.iperm[ib * BD_IB + q * BD_FT + tid];
     ii[q] = i;
+    arow[q] = d.rep[0].alpha;
     if (i >= 0) {
       float4 w = d.work[i];
       xi[q] = __fadd_rn(__fsub_rn(w.x, org.x), w.z);
       yi[q] = __fadd_rn(__fsub_rn(w.y, org.y), w.w);
-      int s = d.species[i];
-      const BdRep &R = d.rep[d.rep_of[i]];
-      a0[q] = R.alpha[2 * s + 0];
-      a1[q] = R.alpha[2 * s + 1];
+      arow[q] = d.rep[d.rep_of[i]].alpha + BD_MAX_SPECIES * d.species[i];
     } else {
       xi[q] = 1.0e18f;
       yi[q] = 1.0e18f;
-      a0[q] = 0.f;
-      a1[q] = 0.f;
     }
     ax[q] = ay[q] = 0.f;
     fxh[q] = fxl[q] = fyh[q] = fyl[q] = 0.f;
@@ -115,7 +112,7 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32(BdDev d, BdConst c) {
     const int sp = d.tile_species[t];
 #pragma unroll
     for (int q = 0; q < BD_IPT; ++q) {
-      float al = sp ? a1[q] : a0[q];
+      const float al = arow[q][sp];
       two_sum(fxh[q], fxl[q], -al * ax[q]);
       two_sum(fyh[q], fyl[q], -al * ay[q]);
       ax[q] = ay[q] = 0.f;
@@ -212,26 +209,24 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_per(BdDev d, BdConst c) {
   const long long ox = (long long)org.x * (1ll << c.qshift);   // integer origins: exact in grid units
   const long long oy = (long long)org.y * (1ll << c.qshift);
   float xh[BD_IPT], yh[BD_IPT], xl[BD_IPT], yl[BD_IPT], ax[BD_IPT], ay[BD_IPT];
-  float fxh[BD_IPT], fxl[BD_IPT], fyh[BD_IPT], fyl[BD_IPT], a0[BD_IPT], a1[BD_IPT];
+  float fxh[BD_IPT], fxl[BD_IPT], fyh[BD_IPT], fyl[BD_IPT];
+  const float *arow[BD_IPT];   // row A[s_i][.] of the table
   int ii[BD_IPT];
 #pragma unroll
   for (int q = 0; q < BD_IPT; ++q) {
     int i = d.iperm[ib * BD_IB + q * BD_FT + tid];
     ii[q] = i;
+    arow[q] = d.rep[0].alpha;
     if (i >= 0) {
       const float4 u = stage_q(d, c, i, ox, oy, LQ);
       xh[q] = u.x;
       yh[q] = u.y;
       xl[q] = u.z;
       yl[q] = u.w;
-      int s = d.species[i];
-      const BdRep &R = d.rep[d.rep_of[i]];
-      a0[q] = R.alpha[2 * s + 0];
-      a1[q] = R.alpha[2 * s + 1];
+      arow[q] = d.rep[d.rep_of[i]].alpha + BD_MAX_SPECIES * d.species[i];
     } else {
       xh[q] = yh[q] = 1.0e18f;
       xl[q] = yl[q] = 0.f;
-      a0[q] = a1[q] = 0.f;
     }
     ax[q] = ay[q] = 0.f;
     fxh[q] = fxl[q] = fyh[q] = fyl[q] = 0.f;
@@ -333,7 +328,7 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_per(BdDev d, BdConst c) {
     const int sp = d.tile_species[t];
 #pragma unroll
     for (int q = 0; q < BD_IPT; ++q) {
-      const float al = sp ? a1[q] : a0[q];
+      const float al = arow[q][sp];
       two_sum(fxh[q], fxl[q], -al * ax[q]);
       two_sum(fyh[q], fyl[q], -al * ay[q]);
       ax[q] = ay[q] = 0.f;
@@ -365,7 +360,8 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32x2(BdDev d, BdConst c) 
   const int ib = item.x, slot = item.w, tid = threadIdx.x;
   const float2 org = d.iorigin[ib];
   u64 xi2[NP], yi2[NP], ax2[NP], ay2[NP];
-  float fxh[IPT], fxl[IPT], fyh[IPT], fyl[IPT], a0[IPT], a1[IPT];
+  float fxh[IPT], fxl[IPT], fyh[IPT], fyl[IPT];
+  const float *arow[IPT];   // row A[s_i][.] of the table
   int ii[IPT];
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
@@ -375,19 +371,15 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32x2(BdDev d, BdConst c) 
       const int q = 2 * k + h;
       int i = d.iperm[ib * IB + q * BD_FT + tid];
       ii[q] = i;
+      arow[q] = d.rep[0].alpha;
       if (i >= 0) {
         float4 w = d.work[i];
         xs[h] = __fadd_rn(__fsub_rn(w.x, org.x), w.z);
         ys[h] = __fadd_rn(__fsub_rn(w.y, org.y), w.w);
-        int sp = d.species[i];
-        const BdRep &R = d.rep[d.rep_of[i]];
-        a0[q] = R.alpha[2 * sp + 0];
-        a1[q] = R.alpha[2 * sp + 1];
+        arow[q] = d.rep[d.rep_of[i]].alpha + BD_MAX_SPECIES * d.species[i];
       } else {
         xs[h] = 1.0e18f;
         ys[h] = 1.0e18f;
-        a0[q] = 0.f;
-        a1[q] = 0.f;
       }
       fxh[q] = fxl[q] = fyh[q] = fyl[q] = 0.f;
     }
@@ -441,7 +433,7 @@ __global__ void __launch_bounds__(BD_FT) k_force_long_f32x2(BdDev d, BdConst c) 
       up2(ax2[k], ax0, ax1);
       up2(ay2[k], ay0, ay1);
       const int q0 = 2 * k, q1 = 2 * k + 1;
-      const float al0 = sp ? a1[q0] : a0[q0], al1 = sp ? a1[q1] : a0[q1];
+      const float al0 = arow[q0][sp], al1 = arow[q1][sp];
       two_sum(fxh[q0], fxl[q0], -al0 * ax0);
       two_sum(fyh[q0], fyl[q0], -al0 * ay0);
       two_sum(fxh[q1], fxl[q1], -al1 * ax1);
@@ -510,7 +502,7 @@ __global__ void __launch_bounds__(128) k_force_long_f64(BdDev d, BdConst c) {
           ry -= R.L * rint(ry / R.L);
         }
         double r2 = rx * rx + ry * ry;
-        double cf = R.alpha_d[2 * si + sk] / (r2 * sqrt(r2));
+        double cf = R.alpha_d[BD_MAX_SPECIES * si + sk] / (r2 * sqrt(r2));
         fx += cf * rx;
         fy += cf * ry;
       }

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
       }
       __syncthreads();
       // j side of this tile: F_j += A[s_j][s_i] sum_i (r_j - r_i)/r^3
-      const float alj = R.alpha[2 * b + a];
+      const float alj = R.alpha[BD_MAX_SPECIES * b + a];
       float2 *out = d.jpart + (size_t)(item.w + (t - jt0)) * BD_TJ;
       for (int jj = tid; jj < BD_TJ; jj += T) {
         float hx = 0.f, hy = 0.f;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
       }
     }
     // i side of this tile: F_i -= A[s_i][s_j] sum_j (r_j - r_i)/r^3
-    const float ali = R.alpha[2 * a + b];
+    const float ali = R.alpha[BD_MAX_SPECIES * a + b];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       float ax0, ax1, ay0, ay1;

@@ -317,18 +317,18 @@ int bd_set_step(bd_handle *h, int64_t step) {
 
 int bd_set_force_params(bd_handle *h, const double *alpha, double v0) {
   if (!h) return BD_ERR_ARG;
-  if (alpha)
+  if (alpha) {
     for (int k = 0; k < 4; ++k)
       if (!isfinite(alpha[k])) return BD_ERR_ARG;
+    for (const RepHost &RH : h->reps)
+      if (RH.p.n_species > 2) return BD_ERR_UNSUPPORTED;   // the 4-entry table is 2 x 2
+  }
   for (size_t r = 0; r < h->reps.size(); ++r) {
     bd_params &p = h->reps[r].p;
     BdRep &B = h->h_rep[r];
     if (alpha) {
-      for (int k = 0; k < 4; ++k) {
-        p.alpha[k] = alpha[k];
-        B.alpha_d[k] = p.n_species == 1 ? alpha[0] : alpha[k];
-        B.alpha[k] = (float)B.alpha_d[k];
-      }
+      for (int k = 0; k < 4; ++k) p.alpha[k] = alpha[k];
+      bdcapi::rep_set_alpha(B, p.alpha, p.n_species);
     }
     if (isfinite(v0)) {
       p.v0 = v0;
@@ -345,7 +345,9 @@ int bd_rollout(bd_handle *h, int32_t nsteps, int32_t ckpt_every, int32_t loss_ki
   if (!h || nsteps < 1 || ckpt_every < 1 || !isfinite(target)) return BD_ERR_ARG;
   if (stats) memset(stats, 0, sizeof(*stats));
   if (loss_kind != BD_LOSS_MSD) return BD_ERR_UNSUPPORTED;
-  if (h->reps.size() != 1 || h->reps[0].p.law != BD_LAW_LONG || h->reps[0].periodic) return BD_ERR_UNSUPPORTED;
+  if (h->reps.size() != 1 || h->reps[0].p.law != BD_LAW_LONG || h->reps[0].periodic ||
+      h->reps[0].p.n_species > 2)
+    return BD_ERR_UNSUPPORTED;
   if (!h->ro) {
     h->ro = new (std::nothrow) BdRollout;
     if (!h->ro) return BD_ERR_NOMEM;
@@ -546,11 +548,7 @@ int bd_rollout_replay(bd_handle *h, const double *alpha, double v0, double *loss
   if (e != cudaSuccess) return cuda_fail(e);
   const BdRep saved = h->h_rep[0];
   BdRep &B = h->h_rep[0];
-  if (alpha)
-    for (int k = 0; k < 4; ++k) {
-      B.alpha_d[k] = h->reps[0].p.n_species == 1 ? alpha[0] : alpha[k];
-      B.alpha[k] = (float)B.alpha_d[k];
-    }
+  if (alpha) bdcapi::rep_set_alpha(B, alpha, h->reps[0].p.n_species);
   if (isfinite(v0)) B.v0 = v0;
   e = upload_rep(h);
   const BdDev dr = replay_dev(h, r);

@@ -50,7 +50,10 @@ def test_init_argument_errors_without_gpu():
     h = ctypes.c_void_p()
     assert lib.bd_init(ctypes.byref(p), None, None, None, None, ctypes.byref(h)) == -1
     p = binding.make_params(10, rho=0.3, law=binding.LAW_LONG)
+    p.n_species = 5                      # at most four species
+    assert lib.bd_init(ctypes.byref(p), None, None, None, None, ctypes.byref(h)) == -1
     p.n_species = 3
+    p.alpha[4] = float("nan")            # the 3 x 3 table is checked entry by entry
     assert lib.bd_init(ctypes.byref(p), None, None, None, None, ctypes.byref(h)) == -1
 
 

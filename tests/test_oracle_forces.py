@@ -78,3 +78,48 @@ def test_short_range_cutoff_and_newton3():
     f = forces.short_range(two, 1.0, 1.0, 2.0, 5.0)
     # Yukawa tail attracts: force on 0 points toward +x
     assert f[0, 0] > 0 and f[1, 0] < 0
+
+
+def test_more_species_two_body_and_relabelling():
+    # Sec. 2.2's force mu_i alpha_k f(r_i - r_k) allows any number of species;
+    # the oracle takes an n x n table A[s_i][s_k]
+    rng = np.random.default_rng(4)
+    A3 = rng.normal(size=(3, 3))
+    xy = np.array([[1.0, 2.0], [4.0, 6.0]])          # 5 apart
+    F = forces.long_range_numpy(xy, np.array([0, 2], np.uint8), A3.reshape(-1))
+    d = xy[0] - xy[1]
+    assert np.allclose(F[0], A3[0, 2] * d / 125.0, rtol=1e-14)
+    assert np.allclose(F[1], -A3[2, 0] * d / 125.0, rtol=1e-14)
+    # a third species that copies species 0's rows and columns changes nothing
+    A2 = rng.normal(size=(2, 2))
+    A3 = np.zeros((3, 3))
+    A3[:2, :2] = A2
+    A3[2, :2] = A2[0]
+    A3[:2, 2] = A2[:, 0]
+    A3[2, 2] = A2[0, 0]
+    n = 300
+    xy = rng.uniform(0, 60, (n, 2))
+    s2 = rng.integers(0, 2, n).astype(np.uint8)
+    s3 = s2.copy()
+    s3[(s2 == 0) & (rng.random(n) < 0.5)] = 2
+    F2 = forces.long_range_numpy(xy, s2, A2.reshape(-1))
+    F3 = forces.long_range_numpy(xy, s3, A3.reshape(-1))
+    assert np.max(np.abs(F2 - F3)) <= 1e-12 * np.max(np.abs(F2))
+    # the C loop takes the same table
+    F3c = forces.long_range(xy, s3, A3.reshape(-1))
+    assert np.max(np.abs(F3c - F3)) <= 1e-12 * np.max(np.abs(F3))
+
+
+def test_factorised_table_matches_charges():
+    # A[s_i][s_k] = mu_{s_i} alpha_{s_k} (Sec. 2.2): F_i = mu_i sum_k alpha_k r_ik / r^3
+    rng = np.random.default_rng(5)
+    mu, al = rng.normal(size=4), rng.normal(size=4)
+    n = 200
+    xy = rng.uniform(0, 50, (n, 2))
+    s = rng.integers(0, 4, n).astype(np.uint8)
+    F = forces.long_range_numpy(xy, s, np.outer(mu, al).reshape(-1))
+    d = xy[:, None, :] - xy[None, :, :]
+    r = np.linalg.norm(d, axis=2)
+    np.fill_diagonal(r, np.inf)
+    ref = mu[s][:, None] * np.einsum("k,ikc->ic", al[s], d / r[:, :, None] ** 3)
+    assert np.allclose(F, ref, rtol=1e-11, atol=1e-14)
