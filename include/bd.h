@@ -133,7 +133,8 @@ typedef struct bd_step_stats {
   int32_t fail_phase;       /* why a step was undone: 0 none, 1 a pair passed through each other
                                (Sec. 4.3), 2 an inverted triangle had no repair flip, 3 repair
                                rounds exhausted, 4 flip rounds exhausted, 5 correction passes
-                               exhausted */
+                               exhausted, 6 a disk outran its Verlet list, 7 positions set by
+                               bd_set_state overlap */
   double max_overlap;       /* deepest overlap sigma - r seen */
   int32_t fail_item;        /* internal id of an offending triangle or edge (diagnostic) */
   int32_t fail_count;       /* inverted triangles or reversed edges at the failure */
@@ -239,11 +240,14 @@ int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32
                  int32_t *n_tri, int64_t *step);
 
 /* Replace positions (and, if theta != NULL, directions) with host values in
- * external order, e.g. to resume from a checkpoint.  The disks must not
- * overlap; the triangulation is carried over and repaired on the device
- * (inverted-triangle repair and edge flips, Sec. 4.3), so moves should be
- * small compared with the disk spacing.
- * Errors: BD_ERR_ARG, BD_ERR_INIT_OVERLAP, BD_ERR_STEP_REJECTED (repair
+ * external order, e.g. to resume from a checkpoint.  The triangulation is
+ * carried over and repaired on the device (inverted-triangle repair and edge
+ * flips, Sec. 4.3), so moves should be small compared with the disk spacing.
+ * No two disks may be closer than sigma: the device scans the repaired
+ * Delaunay triangulation's edges, which hold the closest pair (Verlet-list
+ * handles check on the host).
+ * Errors: BD_ERR_ARG, BD_ERR_INIT_OVERLAP (a centre outside the box, or a
+ * pair closer than sigma; state unchanged), BD_ERR_STEP_REJECTED (repair
  * failed; state unchanged), BD_ERR_CUDA. */
 int bd_set_state(bd_handle *h, const double *xy, const float *theta);
 

@@ -1462,19 +1462,29 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
     const double *x = xy + 2 * (size_t)RH.ext_base;
     if (RH.periodic) {
       wrapped.resize(2 * (size_t)RH.n);
-      for (int i = 0; i < 2 * RH.n; ++i) {
+      for (int i = 0; i < 2 * RH.n; ++i)
         if (!isfinite(x[i])) return BD_ERR_INIT_OVERLAP;
-        wrapped[i] = periodic_coord(x[i], RH.L, c.q, c.inv_q);
-      }
-      if (bdhost::any_overlap_periodic(RH.n, wrapped.data(), RH.L, c.sigma * (1.0 - 1e-12)))
-        return BD_ERR_INIT_OVERLAP;
       continue;
     }
     for (int i = 0; i < 2 * RH.n; ++i)
       if (!isfinite(x[i]) || x[i] < c.a - 1e-9 * RH.L || x[i] > RH.L - c.a + 1e-9 * RH.L)
         return BD_ERR_INIT_OVERLAP;
-    if (bdhost::any_overlap(RH.n, x, 0.0, RH.L, c.sigma * (1.0 - 1e-12))) return BD_ERR_INIT_OVERLAP;
   }
+  // pairs closer than sigma are found on the device: the repaired Delaunay
+  // triangulation's edges hold the closest pair (Verlet-list handles, which
+  // keep no triangulation, check on the host)
+  if (c.overlap_verlet)
+    for (const RepHost &RH : h->reps) {
+      const double *x = xy + 2 * (size_t)RH.ext_base;
+      if (RH.periodic) {
+        wrapped.resize(2 * (size_t)RH.n);
+        for (int i = 0; i < 2 * RH.n; ++i) wrapped[i] = periodic_coord(x[i], RH.L, c.q, c.inv_q);
+        if (bdhost::any_overlap_periodic(RH.n, wrapped.data(), RH.L, c.sigma * (1.0 - 1e-12)))
+          return BD_ERR_INIT_OVERLAP;
+      } else if (bdhost::any_overlap(RH.n, x, 0.0, RH.L, c.sigma * (1.0 - 1e-12))) {
+        return BD_ERR_INIT_OVERLAP;
+      }
+    }
   for (const RepHost &RH : h->reps) {
     const double *x = xy + 2 * (size_t)RH.ext_base;
     for (int i = 0; i < RH.n; ++i) {

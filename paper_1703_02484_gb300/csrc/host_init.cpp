@@ -413,6 +413,24 @@ int build_torus_delaunay(const double *X, const double *Y, const std::vector<int
   return -5;
 }
 
+// Cell list as a counting sort (flat arrays): cell of each centre, start of
+// each cell's run in `order`.  Cells of side >= dmin, nc per side.
+static void cell_sort(int n, const double *xy, double lo, double cs, int nc, std::vector<int> &cell,
+                      std::vector<int> &start, std::vector<int> &order) {
+  cell.resize(n);
+  start.assign((size_t)nc * nc + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const int cx = std::min(nc - 1, std::max(0, (int)((xy[2 * i] - lo) / cs)));
+    const int cy = std::min(nc - 1, std::max(0, (int)((xy[2 * i + 1] - lo) / cs)));
+    cell[i] = cy * nc + cx;
+    ++start[cell[i] + 1];
+  }
+  for (size_t k = 0; k + 1 < start.size(); ++k) start[k + 1] += start[k];
+  order.resize(n);
+  std::vector<int> fill(start.begin(), start.end() - 1);
+  for (int i = 0; i < n; ++i) order[fill[cell[i]]++] = i;
+}
+
 // periodic minimum-image overlap check (centres in [0, L)): 1 if some pair
 // is closer than dmin
 int any_overlap_periodic(int n, const double *xy, double L, double dmin) {
@@ -428,19 +446,15 @@ int any_overlap_periodic(int n, const double *xy, double L, double dmin) {
     return 0;
   }
   const double cs = L / nc;
-  std::vector<std::vector<int>> cells((size_t)nc * nc);
+  std::vector<int> cell, start, order;
+  cell_sort(n, xy, 0.0, cs, nc, cell, start, order);
   for (int i = 0; i < n; ++i) {
-    int cx = std::min(nc - 1, std::max(0, (int)(xy[2 * i] / cs)));
-    int cy = std::min(nc - 1, std::max(0, (int)(xy[2 * i + 1] / cs)));
-    cells[(size_t)cx * nc + cy].push_back(i);
-  }
-  for (int i = 0; i < n; ++i) {
-    int cx = std::min(nc - 1, std::max(0, (int)(xy[2 * i] / cs)));
-    int cy = std::min(nc - 1, std::max(0, (int)(xy[2 * i + 1] / cs)));
-    for (int gx = cx - 1; gx <= cx + 1; ++gx)
-      for (int gy = cy - 1; gy <= cy + 1; ++gy) {
-        const int ux = (gx + nc) % nc, uy = (gy + nc) % nc;
-        for (int j : cells[(size_t)ux * nc + uy]) {
+    const int cx = cell[i] % nc, cy = cell[i] / nc;
+    for (int gy = cy - 1; gy <= cy + 1; ++gy)
+      for (int gx = cx - 1; gx <= cx + 1; ++gx) {
+        const int c = ((gy + nc) % nc) * nc + (gx + nc) % nc;
+        for (int k = start[c]; k < start[c + 1]; ++k) {
+          const int j = order[k];
           if (j >= i) continue;
           double dx = xy[2 * j] - xy[2 * i], dy = xy[2 * j + 1] - xy[2 * i + 1];
           dx -= L * nearbyint(dx / L);
@@ -497,19 +511,20 @@ int any_overlap(int n, const double *xy, double lo, double hi, double dmin) {
   double W = hi - lo;
   int nc = std::max(1, std::min(4096, (int)floor(W / dmin)));
   double cs = W / nc;
-  std::vector<std::vector<int>> cells((size_t)nc * nc);
+  std::vector<int> cell, start, order;
+  cell_sort(n, xy, lo, cs, nc, cell, start, order);
   for (int i = 0; i < n; ++i) {
-    int cx = std::min(nc - 1, std::max(0, (int)((xy[2 * i] - lo) / cs)));
-    int cy = std::min(nc - 1, std::max(0, (int)((xy[2 * i + 1] - lo) / cs)));
-    for (int gx = cx - 1; gx <= cx + 1; ++gx)
-      for (int gy = cy - 1; gy <= cy + 1; ++gy) {
-        if (gx < 0 || gy < 0 || gx >= nc || gy >= nc) continue;
-        for (int j : cells[(size_t)gx * nc + gy]) {
-          double dx = xy[2 * j] - xy[2 * i], dy = xy[2 * j + 1] - xy[2 * i + 1];
+    const int cx = cell[i] % nc, cy = cell[i] / nc;
+    for (int gy = std::max(0, cy - 1); gy <= std::min(nc - 1, cy + 1); ++gy)
+      for (int gx = std::max(0, cx - 1); gx <= std::min(nc - 1, cx + 1); ++gx) {
+        const int c = gy * nc + gx;
+        for (int k = start[c]; k < start[c + 1]; ++k) {
+          const int j = order[k];
+          if (j >= i) continue;
+          const double dx = xy[2 * j] - xy[2 * i], dy = xy[2 * j + 1] - xy[2 * i + 1];
           if (dx * dx + dy * dy < dmin * dmin) return 1;
         }
       }
-    cells[(size_t)cx * nc + cy].push_back(i);
   }
   return 0;
 }

@@ -304,7 +304,8 @@ __device__ __forceinline__ int key_corner(unsigned long long key) {
 }  // namespace
 
 // One time step's triangulation work (mode 0), the repair of the
-// triangulation after new positions are set (mode 1, no overlap correction),
+// triangulation after new positions are set (mode 1: no overlap correction; an
+// overlapping pair rejects the positions with BD_ERR_INIT_OVERLAP),
 // or one piece of a halved step (mode 2: as mode 0, but the step counter does
 // not advance).
 //
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
               ++cand;
             }
           }
-          if (mode != 1 && disks) {
+          if (disks) {
             // FP32 screen: a pair whose FP32 squared distance exceeds
             // sigma^2 (1 + 1e-5) is farther than sigma (FP32 error ~3e-7);
             // edges across a periodic box edge skip it
@@ -694,7 +695,16 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
     }
 
     // Delaunay triangulation of the current positions: the scan is valid
-    if (mode == 1 || n_ov == 0) break;
+    if (mode == 1) {
+      // new positions set from outside: they must not overlap (the scan of
+      // this Delaunay triangulation finds the closest pair)
+      if (n_ov) {
+        status = BD_ERR_INIT_OVERLAP;
+        if (lead) { ctl->st_fail_phase = 7; ctl->st_fail_count = n_ov; }
+      }
+      break;
+    }
+    if (n_ov == 0) break;
     if (corr_iter >= c.max_corr_iters) {
       status = BD_ERR_OVERLAP_NOT_CONVERGED;
       if (lead) ctl->st_fail_phase = 5;

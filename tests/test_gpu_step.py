@@ -271,3 +271,32 @@ def test_multi_step_with_check_lists_matches_full_passes(monkeypatch):
         assert np.array_equal(geometry.edges(oa["tri"]), geometry.edges(geometry.delaunay(oa["xy"], L)))
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_set_state_rejects_overlapping_positions(boundary):
+    # the device finds the overlap on the repaired Delaunay triangulation's
+    # edges; the handle keeps its state
+    cfg = workloads.CONFIGS["c5"]
+    n = 2000
+    xy, sp, th = workloads.initial_state(cfg, n=n)
+    L = workloads.box_side(n, cfg.rho)
+    p = bd.params_from_config(cfg, n=n)
+    if boundary:
+        L = float(np.float32(L))
+        p.box_L = L
+        p.boundary = bd.BOUNDARY_PERIODIC
+    s = bd.System(p, xy, sp, th, stream=stream())
+    before = s.state()
+    dist, nb = cKDTree(xy).query(xy, k=2)
+    i = int(np.argmin(dist[:, 1]))          # a disk and its nearest neighbour
+    j = int(nb[i, 1])
+    bad = xy.copy()
+    bad[j] = xy[i] + 1.9 * (xy[j] - xy[i]) / np.linalg.norm(xy[j] - xy[i])   # 1.9 < sigma apart
+    with pytest.raises(bd.BDError) as e:
+        s.set_state(bad)
+    assert e.value.code == -3
+    after = s.state()
+    assert np.array_equal(after["xy"], before["xy"]) and np.array_equal(after["tri"], before["tri"])
+    s.step(3)                       # still usable
+    s.close()
