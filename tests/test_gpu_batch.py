@@ -94,3 +94,38 @@ def test_full_batched_workload_runs_clean():
         assert len(cKDTree(rep["xy"]).query_pairs(2.0 * (1 - 1e-12))) == 0
         assert np.array_equal(geometry.edges(rep["tri"]),
                               geometry.edges(geometry.delaunay(rep["xy"], rep["L"])))
+
+
+def test_batch_mixes_walls_and_periodic_replicas():
+    # replicas with walls and with a periodic box in one handle: each advances
+    # as it does alone (the periodic sweep serves both kinds in a batch)
+    from oracle import periodic
+    cfgs, params, xys, sps, ths = small_batch(R=4, seed=21)
+    for r in (1, 3):
+        L = float(np.float32(workloads.box_side(params[r].n, cfgs[r].rho)))
+        params[r].box_L = L
+        params[r].boundary = bd.BOUNDARY_PERIODIC
+        xys[r] = periodic.wrap(xys[r] + np.array([0.3 * L, 0.7 * L]), L)
+    b = bd.System(params, np.concatenate(xys), np.concatenate(sps), np.concatenate(ths), stream=stream())
+    st = b.step(8)
+    assert st["steps_done"] == 8
+    shifts = b.tri_shifts()
+    off = 0
+    for r in range(4):
+        rep = b.replica(r)
+        alone = bd.System(params[r], xys[r], sps[r], ths[r], stream=stream())
+        alone.step(8)
+        a = alone.state()
+        L = rep["L"]
+        d = rep["xy"] - a["xy"]
+        if params[r].boundary:
+            d = periodic.min_image(d, L)
+            sh = shifts[off:off + len(rep["tri"])]
+            assert np.array_equal(periodic.edge_keys(rep["tri"].astype(np.int64), sh),
+                                  periodic.edge_keys(*periodic.delaunay_torus(rep["xy"], L)))
+        else:
+            assert np.array_equal(geometry.edges(rep["tri"]), geometry.edges(a["tri"]))
+        assert float(np.max(np.abs(d))) <= 1e-8
+        off += len(rep["tri"])
+        alone.close()
+    b.close()
