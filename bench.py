@@ -188,7 +188,7 @@ def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind, v
         position copies and its list with the neighbours' flags (38 + 5 m B
         per disk, m the mean list length) and writes its displacement and hit
         flag (17 B); an apply pass 100 B per disk."""
-    ms = sum(v[0] for v in stage_raw.values()) / steps
+    ms = sum(v[0] for k, v in stage_raw.items() if k != "check_lists") / steps   # check_lists is part of check
     if not ms > 0:
         return None
     if verlet_mode:

@@ -288,11 +288,13 @@ int64_t bd_last_launch_count(bd_handle *h);
  * bd_rollout since the last reset, as the paper splits a step's time into
  * its stages (Sec. 6): ms[0] the validity check / Lawson marks / overlap scan
  * passes (Sec. 4.3-4.4), ms[1] inversion repair (Sec. 4.3), ms[2] Lawson flip
- * rounds, ms[3] applying the capped corrections (Algorithm 2); each stage's
- * work plus its closing grid barrier, measured on the device clock.
- * phases[k] counts the stage's passes.  Either output may be NULL; reset = 1
- * clears the totals after reading.  The force and integration kernels are
- * separate launches (bd_force_timing covers the force). */
+ * rounds, ms[3] applying the capped corrections (Algorithm 2), ms[4] the part
+ * of ms[0] spent in check passes that visit only a list of triangles; each
+ * stage's work plus its closing grid barrier, measured on the device clock.
+ * phases[k] counts the stage's passes.  ms and phases hold 5 entries; either
+ * may be NULL; reset = 1 clears the totals after reading.  The force and
+ * integration kernels are separate launches (bd_force_timing covers the
+ * force). */
 int bd_stage_times(bd_handle *h, int reset, double *ms, int64_t *phases);
 
 /* Host only: the fixed ghost points that close the triangulation of a box of

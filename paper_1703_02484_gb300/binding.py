@@ -313,10 +313,11 @@ class System:
     def stage_times(self, reset=False):
         """Triangulation-kernel stage times (ms) and pass counts since the last
         reset: dict check/repair/flip/apply -> (ms, passes)."""
-        ms = np.zeros(4, dtype=np.float64)
-        n = np.zeros(4, dtype=np.int64)
+        ms = np.zeros(5, dtype=np.float64)
+        n = np.zeros(5, dtype=np.int64)
         _check(load().bd_stage_times(self.h, int(reset), _ptr(ms), _ptr(n)), "bd_stage_times")
-        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(("check", "repair", "flip", "apply"))}
+        return {k: (float(ms[i]), int(n[i]))
+                for i, k in enumerate(("check", "repair", "flip", "apply", "check_lists"))}
 
     # ---- differentiated rollout ----
     def set_force_params(self, alpha=None, v0=None):

@@ -946,7 +946,7 @@ cudaError_t reset_stats(bd_handle *h) {
 }
 
 void add_stage_times(bd_handle *h) {
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     h->stage_ns[k] += (double)h->h_ctl->st_stage_ns[k];
     h->stage_cnt[k] += h->h_ctl->st_stage_cnt[k];
   }
@@ -1601,12 +1601,12 @@ int64_t bd_last_launch_count(bd_handle *h) { return h ? h->last_launches : -1; }
 
 int bd_stage_times(bd_handle *h, int reset, double *ms, int64_t *phases) {
   if (!h) return BD_ERR_ARG;
-  for (int k = 0; k < 4; ++k) {
-    if (ms) ms[k] = h->stage_ns[k] * 1e-6;
-    if (phases) phases[k] = h->stage_cnt[k];
+  for (int k = 0; k < 5; ++k) {
+    if (ms) ms[k] = (k == 0 ? h->stage_ns[0] + h->stage_ns[4] : h->stage_ns[k]) * 1e-6;
+    if (phases) phases[k] = k == 0 ? h->stage_cnt[0] + h->stage_cnt[4] : h->stage_cnt[k];
   }
   if (reset)
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
       h->stage_ns[k] = 0.0;
       h->stage_cnt[k] = 0;
     }

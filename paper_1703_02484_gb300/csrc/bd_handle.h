@@ -65,8 +65,8 @@ struct bd_handle {
   float *hs_theta = nullptr;
   int4 *hs_tv = nullptr, *hs_tn = nullptr;
   int *hs_vt = nullptr;
-  double stage_ns[4] = {0, 0, 0, 0};   // triangulation-kernel stage times since the last reset
-  int64_t stage_cnt[4] = {0, 0, 0, 0};
+  double stage_ns[5] = {0, 0, 0, 0, 0};   // triangulation-kernel stage times since the last reset
+  int64_t stage_cnt[5] = {0, 0, 0, 0, 0};
 };
 
 namespace bdcapi {

@@ -63,8 +63,8 @@ struct BdCtl {
   // wall time of the triangulation kernel's stages as its lead thread sees
   // them (each stage's work plus its closing grid barrier): P check/mark/scan,
   // R inversion repair, F Lawson flips, A apply corrections
-  unsigned long long st_stage_ns[4];
-  long long st_stage_cnt[4];
+  unsigned long long st_stage_ns[5];   // [4]: check passes that visit a list
+  long long st_stage_cnt[5];
   // rollout log cursors (not reset per call)
   int log_npass;                   // committed correction passes
   int log_npairs;                  // logged pairs

@@ -49,7 +49,7 @@ using namespace bdgs;
 
 namespace {
 
-enum { STAGE_P = 0, STAGE_R = 1, STAGE_F = 2, STAGE_A = 3 };
+enum { STAGE_P = 0, STAGE_R = 1, STAGE_F = 2, STAGE_A = 3, STAGE_PL = 4 };
 
 // lead thread only: charge the time since the last mark to a stage
 __device__ __forceinline__ void stage_tick(BdCtl *ctl, int stage, unsigned long long &mark) {
@@ -136,6 +136,12 @@ __device__ __forceinline__ int incircle_v(const Ctx &x, int a, int b, int c, int
 __device__ __forceinline__ int sh2(int w, int bit) { return (((w >> bit) & 3) ^ 2) - 2; }
 __device__ __forceinline__ int shx(int w, int k) { return sh2(w, 8 + 4 * k); }
 __device__ __forceinline__ int shy(int w, int k) { return sh2(w, 10 + 4 * k); }
+// the kernel is compiled twice: with walls (PER = false) every shift is the
+// constant 0 and the shift arithmetic disappears
+template <bool PER>
+__device__ __forceinline__ int tshx(int w, int k) { return PER ? shx(w, k) : 0; }
+template <bool PER>
+__device__ __forceinline__ int tshy(int w, int k) { return PER ? shy(w, k) : 0; }
 __device__ __forceinline__ int put_shift(int k, int sx, int sy) {
   return ((sx & 3) << (8 + 4 * k)) | ((sy & 3) << (10 + 4 * k));
 }
@@ -164,9 +170,10 @@ __device__ __forceinline__ int orient_s(const Ctx &x, int a, int sax, int say, i
 }
 
 // in-circle test of p (shift sp) against triangle t's corners (shifts in w)
+template <bool PER>
 __device__ __forceinline__ int incircle_s(const Ctx &x, const int4 &v, int p, int spx, int spy) {
   const int w = v.w;
-  if (((w & BD_TRI_SHIFT_BITS) | spx | spy) == 0) return incircle_v(x, v.x, v.y, v.z, p);
+  if (!PER || ((w & BD_TRI_SHIFT_BITS) | spx | spy) == 0) return incircle_v(x, v.x, v.y, v.z, p);
   const long long LQ = rep_LQ(x, v.x);
   const Lift A = lift(x, v.x, shx(w, 0), shy(w, 0), LQ), B = lift(x, v.y, shx(w, 1), shy(w, 1), LQ);
   const Lift C = lift(x, v.z, shx(w, 2), shy(w, 2), LQ), P = lift(x, p, spx, spy, LQ);
@@ -176,7 +183,12 @@ __device__ __forceinline__ int incircle_s(const Ctx &x, const int4 &v, int p, in
 // shift, in the frame of triangle t (corner tab w), of the vertex opposite
 // the edge facing corner k, read from the neighbour (tab w1, corner k1):
 // t's corner k+1 is the neighbour's corner k1+2
+template <bool PER>
 __device__ __forceinline__ void opp_shift(int w, int k, int w1, int k1, int &sx, int &sy) {
+  if (!PER) {
+    sx = sy = 0;
+    return;
+  }
   const int ku = (k + 1) % 3, ku1 = (k1 + 2) % 3;
   sx = shx(w1, k1) + shx(w, ku) - shx(w1, ku1);
   sy = shy(w1, k1) + shy(w, ku) - shy(w1, ku1);
@@ -221,6 +233,7 @@ __device__ __forceinline__ bool owns6(const Ctx &x, int t0, int k0, const int4 &
 // and point the four outer neighbours, owned by this flip, at the new corners.
 // Quad a-b-d-c with t0 = (a, b, c), t1 = (d, c, b) becomes t0 = (b, d, a),
 // t1 = (c, a, d): the edge bc is replaced by ad.
+template <bool PER>
 __device__ void flip_owned(const Ctx &x, int c0, int o0) {
   const int t0 = c0 / 3, k0 = c0 % 3, t1 = o0 / 3, k1 = o0 % 3;
   int4 V0 = x.d.tv[t0], V1 = x.d.tv[t1], N0 = x.d.tn[t0], N1 = x.d.tn[t1];
@@ -243,7 +256,7 @@ __device__ void flip_owned(const Ctx &x, int c0, int o0) {
   // t1's frame, offset by b's shift difference between the two frames
   const int w0 = V0.w, w1 = V1.w;
   int nw0 = BD_TRI_DIRTY, nw1 = BD_TRI_DIRTY;
-  if ((w0 | w1) & BD_TRI_SHIFT_BITS) {
+  if (PER && ((w0 | w1) & BD_TRI_SHIFT_BITS)) {
     const int Ax = shx(w0, k0), Ay = shy(w0, k0);
     const int Bx = shx(w0, (k0 + 1) % 3), By = shy(w0, (k0 + 1) % 3);
     const int Cx = shx(w0, (k0 + 2) % 3), Cy = shy(w0, (k0 + 2) % 3);
@@ -324,6 +337,7 @@ __device__ __forceinline__ int key_corner(unsigned long long key) {
 // latency-bound chains of dependent loads, and the spills this costs sit in
 // the exact-predicate fallbacks (measured: 3 blocks 20 % faster than 2 on
 // 2^20 disks; 4 blocks slower at 1e5).
+template <bool PER>
 __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdConst c, int mode,
                                                                  int log_step) {
   Ctx x;
@@ -390,7 +404,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
     unsigned *nmark = d.act_mark + (size_t)nslot * x.T;
     int *ncount = &ctl->act_n[nslot];
     // ---------------- W: shifts of triangles whose corners re-entered (periodic box) ----------------
-    if (fresh && c.any_periodic && *(volatile int *)&ctl->n_wrapped != 0) {
+    if (PER && fresh && *(volatile int *)&ctl->n_wrapped != 0) {
       phase_begin(ctl, b);
       for (int t = tid; t < x.T; t += nth) {
         const int4 v = d.tv[t];
@@ -406,8 +420,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         const int kx[3] = {wrapx(w0), wrapx(w1), wrapx(w2)}, ky[3] = {wrapy(w0), wrapy(w1), wrapy(w2)};
         int sx[3], sy[3];
         for (int k = 0; k < 3; ++k) {
-          sx[k] = shx(v.w, k) + kx[k];
-          sy[k] = shy(v.w, k) + ky[k];
+          sx[k] = tshx<PER>(v.w, k) + kx[k];
+          sy[k] = tshy<PER>(v.w, k) + ky[k];
         }
         int nw = v.w & BD_TRI_FLAGS;
         for (int k = 0; k < 3; ++k) nw |= put_shift(k, sx[k] - sx[0], sy[k] - sy[0]);
@@ -436,8 +450,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         }
         int fl = v.w & BD_TRI_FLAGS;
         if (fresh && (d.moved[v.x] | d.moved[v.y] | d.moved[v.z])) {
-          const int o = orient_s(x, v.x, shx(v.w, 0), shy(v.w, 0), v.y, shx(v.w, 1), shy(v.w, 1), v.z,
-                                 shx(v.w, 2), shy(v.w, 2));
+          const int o = orient_s(x, v.x, tshx<PER>(v.w, 0), tshy<PER>(v.w, 0), v.y, tshx<PER>(v.w, 1), tshy<PER>(v.w, 1), v.z,
+                                 tshx<PER>(v.w, 2), tshy<PER>(v.w, 2));
           fl = BD_TRI_DIRTY | (o <= 0 ? BD_TRI_INVERTED : 0);
           d.tv[t].w = (v.w & ~BD_TRI_FLAGS) | fl;
         }
@@ -453,8 +467,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           const bool disks = u < x.np && w < x.np;
           const bool mv = fresh && (d.moved[u] | d.moved[w]);
           // image shift of w relative to u in this triangle (periodic box; 0 with walls)
-          const int rsx = shx(v.w, (k + 2) % 3) - shx(v.w, (k + 1) % 3);
-          const int rsy = shy(v.w, (k + 2) % 3) - shy(v.w, (k + 1) % 3);
+          const int rsx = tshx<PER>(v.w, (k + 2) % 3) - tshx<PER>(v.w, (k + 1) % 3);
+          const int rsy = tshy<PER>(v.w, (k + 2) % 3) - tshy<PER>(v.w, (k + 1) % 3);
           long long LQ = 0;
           if (rsx | rsy) LQ = rep_LQ(x, u);
           if (disks && mv) {
@@ -463,7 +477,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
             // less the re-entries of its end points)
             const double2 a0 = d.prev[u], b0 = d.prev[w], a1 = d.pos[u], b1 = d.pos[w];
             int ox = rsx, oy = rsy;
-            if (c.any_periodic) {
+            if (PER) {
               const uint8_t wu = d.wrap[u], ww = d.wrap[w];
               ox -= wrapx(ww) - wrapx(wu);
               oy -= wrapy(ww) - wrapy(wu);
@@ -485,8 +499,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           if ((fl & BD_TRI_DIRTY) || d1) {
             const int q = vk(v1, o % 3);
             int sqx, sqy;
-            opp_shift(v.w, k, v1.w, o % 3, sqx, sqy);
-            if (incircle_s(x, v, q, sqx, sqy) > 0) {
+            opp_shift<PER>(v.w, k, v1.w, o % 3, sqx, sqy);
+            if (incircle_s<PER>(x, v, q, sqx, sqy) > 0) {
               claim6(x, t, k, nn, o, claim_key(epoch, cc));
               ++cand;
             }
@@ -539,7 +553,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
     }
     if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
     if (lead) {
-      stage_tick(ctl, STAGE_P, t_mark);
+      stage_tick(ctl, full ? STAGE_P : STAGE_PL, t_mark);
       ctl->act_n[(kp + 2) % 3] = 0;   // filled by the next pass
     }
     first = false;
@@ -582,10 +596,10 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
               const int4 v1 = d.tv[o / 3];
               const int q = vk(v1, o % 3);
               int sqx, sqy;
-              opp_shift(v.w, k, v1.w, o % 3, sqx, sqy);
-              const int spx = shx(v.w, k), spy = shy(v.w, k);
-              const int sux = shx(v.w, (k + 1) % 3), suy = shy(v.w, (k + 1) % 3);
-              const int swx = shx(v.w, (k + 2) % 3), swy = shy(v.w, (k + 2) % 3);
+              opp_shift<PER>(v.w, k, v1.w, o % 3, sqx, sqy);
+              const int spx = tshx<PER>(v.w, k), spy = tshy<PER>(v.w, k);
+              const int sux = tshx<PER>(v.w, (k + 1) % 3), suy = tshy<PER>(v.w, (k + 1) % 3);
+              const int swx = tshx<PER>(v.w, (k + 2) % 3), swy = tshy<PER>(v.w, (k + 2) % 3);
               // orientation form of Eq. (predicate): both triangles of the
               // other diagonal strictly counter-clockwise
               if (orient_s(x, u, sux, suy, q, sqx, sqy, p, spx, spy) > 0 &&
@@ -623,7 +637,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
             const int4 N0 = d.tn[t];
             const int o = vk(N0, cm % 3);
             if (!owns6(x, t, cm % 3, N0, o, key)) continue;
-            flip_owned(x, cm, o);   // both new triangles are counter-clockwise by the rule
+            flip_owned<PER>(x, cm, o);   // both new triangles are counter-clockwise by the rule
             ++nf;
           }
           block_add(cnt(ctl, b.ph, C_FLIPS), nf);
@@ -666,7 +680,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
               const int4 N0 = d.tn[t];
               const int o = vk(N0, cm % 3);
               if (owns6(x, t, cm % 3, N0, o, key)) {
-                flip_owned(x, cm, o);
+                flip_owned<PER>(x, cm, o);
                 if (use_lists) {
                   push_tri(nlist, nmark, ncount, ngen, t);
                   push_tri(nlist, nmark, ncount, ngen, o / 3);
@@ -737,7 +751,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         const double2 p = d.pos[i];
         d.prev[i] = p;
         const double2 dd = d.disp[i];
-        if (c.any_periodic) d.wrap[i] = 0;
+        if (PER) d.wrap[i] = 0;
         if (dd.x == 0.0 && dd.y == 0.0) {
           d.moved[i] = 0;
           if (log_pidx >= 0) d.log_pflags[(size_t)log_pidx * x.np + i] = 0;
@@ -751,7 +765,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         int rfl = 0;
         const BdRep &R = d.rep[d.rep_of[i]];
         double2 np2;
-        if (R.periodic) {
+        if (PER && R.periodic) {
           // Algorithm 2 "applying the periodic boundary conditions": re-entry
           long long X = bdpred::to_int(y.x, x.g), Y = bdpred::to_int(y.y, x.g);
           const int wr = bdem::wrap_grid(R.LQ, X, Y);
@@ -779,7 +793,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           if (cw == c0) break;
         }
       }
-      if (c.any_periodic) block_add(&ctl->n_wrapped, nwrap);
+      if (PER) block_add(&ctl->n_wrapped, nwrap);
       // flags left by the last check pass sit on the triangles it visited
       for (int it = tid; it < dom_n; it += nth) {
         const int t = full ? it : dom[it];
@@ -861,7 +875,7 @@ int bd_dt_grid(int *grid, int *block) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_triangulation, BD_DT_THREADS, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_triangulation<false>, BD_DT_THREADS, 0) !=
       cudaSuccess)
     return -1;
   if (per < 1) return -1;
@@ -878,6 +892,6 @@ cudaError_t bd_launch_dt(const BdDev &d, const BdConst &c, int mode, cudaStream_
   BdConst cc = c;
   int m = mode, ls = log_step;
   void *args[] = {&dd, &cc, &m, &ls};
-  return cudaLaunchCooperativeKernel((const void *)k_triangulation, dim3(grid), dim3(block), args,
-                                     0, s);
+  const void *fn = c.any_periodic ? (const void *)k_triangulation<true> : (const void *)k_triangulation<false>;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, s);
 }
