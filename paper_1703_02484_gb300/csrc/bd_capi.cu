@@ -747,6 +747,7 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     BD_TRY(dalloc(h, &d.ext_id, (size_t)np));
     BD_TRY(dalloc(h, &d.rep_of, (size_t)np));
     BD_TRY(dalloc(h, &d.moved, nv));
+    BD_TRY(dalloc(h, &d.dmove, (size_t)np));
     if (c.any_periodic) {
       BD_TRY(dalloc(h, &d.wrap, (size_t)np));
       BD_TRY(cudaMemsetAsync(d.wrap, 0, (size_t)np, h->stream));

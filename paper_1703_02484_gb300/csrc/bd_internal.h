@@ -111,6 +111,7 @@ struct BdDev {
   int *ext_id;             // index within its replica (-1 = empty slot): the Philox counter
   int *rep_of;             // replica of each slot (-1 = empty slot)
   uint8_t *moved;
+  float2 *dmove;           // position less prev, FP32 (disks with the moved flag; the reversal filter)
   uint8_t *wrap;           // periodic box: re-entries of the last move (bits 0-1 x, 2-3 y; 1 = -L, 3 = +L)
   double2 *disp;
   const BdRep *rep;        // [R]

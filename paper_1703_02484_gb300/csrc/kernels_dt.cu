@@ -88,9 +88,11 @@ __device__ __forceinline__ float fdiff(float bh, float bl, float ah, float al) {
   return __fadd_rn(__fsub_rn(bh, ah), __fsub_rn(bl, al));
 }
 
-__device__ __forceinline__ int orient_v(const Ctx &x, int a, int b, int c) {
-  if (a < x.np && b < x.np && c < x.np) {
-    const float4 wa = x.d.work[a], wb = x.d.work[b], wc = x.d.work[c];
+// the filters on preloaded FP32 pairs (filt: all corners are disks, whose
+// pairs are loaded; ghost points have none)
+__device__ __forceinline__ int orient_pre(const Ctx &x, bool filt, const float4 &wa, const float4 &wb,
+                                          const float4 &wc, int a, int b, int c) {
+  if (filt) {
     const float bax = fdiff(wb.x, wb.z, wa.x, wa.z), bay = fdiff(wb.y, wb.w, wa.y, wa.w);
     const float cax = fdiff(wc.x, wc.z, wa.x, wa.z), cay = fdiff(wc.y, wc.w, wa.y, wa.w);
     const float l = __fmul_rn(bax, cay), r = __fmul_rn(bay, cax);
@@ -103,9 +105,9 @@ __device__ __forceinline__ int orient_v(const Ctx &x, int a, int b, int c) {
   return bdpred::orient(pa.x, pa.y, pb.x, pb.y, pc.x, pc.y, x.g);
 }
 
-__device__ __forceinline__ int incircle_v(const Ctx &x, int a, int b, int c, int p) {
-  if (a < x.np && b < x.np && c < x.np && p < x.np) {
-    const float4 wa = x.d.work[a], wb = x.d.work[b], wc = x.d.work[c], wp = x.d.work[p];
+__device__ __forceinline__ int incircle_pre(const Ctx &x, bool filt, const float4 &wa, const float4 &wb,
+                                            const float4 &wc, const float4 &wp, int a, int b, int c, int p) {
+  if (filt) {
     const float adx = fdiff(wa.x, wa.z, wp.x, wp.z), ady = fdiff(wa.y, wa.w, wp.y, wp.w);
     const float bdx = fdiff(wb.x, wb.z, wp.x, wp.z), bdy = fdiff(wb.y, wb.w, wp.y, wp.w);
     const float cdx = fdiff(wc.x, wc.z, wp.x, wp.z), cdy = fdiff(wc.y, wc.w, wp.y, wp.w);
@@ -126,6 +128,33 @@ __device__ __forceinline__ int incircle_v(const Ctx &x, int a, int b, int c, int
   }
   double2 pa = x.d.pos[a], pb = x.d.pos[b], pc = x.d.pos[c], pp = x.d.pos[p];
   return bdpred::incircle(pa.x, pa.y, pb.x, pb.y, pc.x, pc.y, pp.x, pp.y, x.g);
+}
+
+__device__ __forceinline__ float4 work_of(const Ctx &x, int v) {
+  return v < x.np ? x.d.work[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ int orient_v(const Ctx &x, int a, int b, int c) {
+  const bool filt = a < x.np && b < x.np && c < x.np;
+  return orient_pre(x, filt, work_of(x, a), work_of(x, b), work_of(x, c), a, b, c);
+}
+
+__device__ __forceinline__ int incircle_v(const Ctx &x, int a, int b, int c, int p) {
+  const bool filt = a < x.np && b < x.np && c < x.np && p < x.np;
+  return incircle_pre(x, filt, work_of(x, a), work_of(x, b), work_of(x, c), work_of(x, p), a, b, c, p);
+}
+
+// Sec. 4.3 reversal test r0 . r1 < 0 of the edge u -> w, exact on the grid:
+// r1 from the present positions, r0 from those before the move (ox, oy: the
+// edge's image shift before the move, in units of LQ)
+__device__ __forceinline__ bool reversed_exact(const Ctx &x, int u, int w, int ox, int oy, int rsx, int rsy,
+                                               long long LQ) {
+  const double2 a0 = x.d.prev[u], b0 = x.d.prev[w], a1 = x.d.pos[u], b1 = x.d.pos[w];
+  const int64_t ux = bdpred::to_int(b0.x, x.g) - bdpred::to_int(a0.x, x.g) + ox * LQ;
+  const int64_t uy = bdpred::to_int(b0.y, x.g) - bdpred::to_int(a0.y, x.g) + oy * LQ;
+  const int64_t vx = bdpred::to_int(b1.x, x.g) - bdpred::to_int(a1.x, x.g) + rsx * LQ;
+  const int64_t vy = bdpred::to_int(b1.y, x.g) - bdpred::to_int(a1.y, x.g) + rsy * LQ;
+  return bdpred::sign128(bdpred::add128(bdpred::smul64(ux, vx), bdpred::smul64(uy, vy))) < 0;
 }
 
 // ---- periodic box: image shifts of triangle corners (Sec. 2.1, 4.1) ----
@@ -438,6 +467,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
     {
       int inv = 0, rej = 0, cand = 0, nov = 0;
       double mx = 0.0;
+      if constexpr (PER)
       for (int it = tid; it < dom_n; it += nth) {
         const int t = full ? it : dom[it];
         const int4 v = d.tv[t];
@@ -475,19 +505,14 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
             // Sec. 4.3 first criterion: r0 . r1 < 0, exact on the grid (in a
             // periodic box the edge's shift before the move is the present one
             // less the re-entries of its end points)
-            const double2 a0 = d.prev[u], b0 = d.prev[w], a1 = d.pos[u], b1 = d.pos[w];
             int ox = rsx, oy = rsy;
-            if (PER) {
+            {
               const uint8_t wu = d.wrap[u], ww = d.wrap[w];
               ox -= wrapx(ww) - wrapx(wu);
               oy -= wrapy(ww) - wrapy(wu);
               if ((ox | oy) && LQ == 0) LQ = rep_LQ(x, u);
             }
-            const int64_t ux = bdpred::to_int(b0.x, x.g) - bdpred::to_int(a0.x, x.g) + ox * LQ;
-            const int64_t uy = bdpred::to_int(b0.y, x.g) - bdpred::to_int(a0.y, x.g) + oy * LQ;
-            const int64_t vx = bdpred::to_int(b1.x, x.g) - bdpred::to_int(a1.x, x.g) + rsx * LQ;
-            const int64_t vy = bdpred::to_int(b1.y, x.g) - bdpred::to_int(a1.y, x.g) + rsy * LQ;
-            if (bdpred::sign128(bdpred::add128(bdpred::smul64(ux, vx), bdpred::smul64(uy, vy))) < 0) {
+            if (reversed_exact(x, u, w, ox, oy, rsx, rsy, LQ)) {
               ++rej;
               atomicExch(&ctl->st_fail_item, cc);
             }
@@ -523,6 +548,121 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
             if (near) {
               // the decision itself as the FP64 reference makes it (the
               // difference of two grid values is exact in FP64)
+              const double dx = bdem::grid_to_double(ix, x.g.s), dy = bdem::grid_to_double(iy, x.g.s);
+              const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+              const double r = sqrt(r2);
+              if (r < sigma) {
+                const double del = sigma - r;
+                const double nx = dx / r, ny = dy / r;
+                atomicAdd(&d.disp[u].x, -del * nx);
+                atomicAdd(&d.disp[u].y, -del * ny);
+                atomicAdd(&d.disp[w].x, del * nx);
+                atomicAdd(&d.disp[w].y, del * ny);
+                if (use_lists) push_tri(nlist, nmark, ncount, ngen, t);   // checked again in the next pass
+                const int k_ov = atomicAdd(cnt(ctl, b.ph, C_OVERLAP), 1);
+                if (logging) {
+                  if (log_head + k_ov < c.log_pairs_cap) d.log_pairs[log_head + k_ov] = make_int2(u, w);
+                  else atomicExch(&ctl->log_overflow, 1);
+                }
+                mx = fmax(mx, del);
+              }
+            }
+          }
+        }
+      }
+      else
+      for (int it = tid; it < dom_n; it += nth) {
+        // walls: the three corners' FP32 pairs and moved flags are loaded once
+        // and serve the orientation, the reversal and in-circle filters and the
+        // overlap screen of all three edges
+        const int t = full ? it : dom[it];
+        const int4 v = d.tv[t];
+        const int4 nn = d.tn[t];
+        if (first) {
+          int4 vs = v;
+          vs.w = v.w & ~BD_TRI_FLAGS;
+          d.tv_snap[t] = vs;
+          d.tn_snap[t] = nn;
+        }
+        const int vv[3] = {v.x, v.y, v.z};
+        const bool isd[3] = {v.x < x.np, v.y < x.np, v.z < x.np};
+        float4 W[3];
+        uint8_t mvd[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          W[k] = work_of(x, vv[k]);
+          mvd[k] = fresh ? d.moved[vv[k]] : (uint8_t)0;
+        }
+        int fl = v.w & BD_TRI_FLAGS;
+        if (mvd[0] | mvd[1] | mvd[2]) {
+          const int o = orient_pre(x, isd[0] && isd[1] && isd[2], W[0], W[1], W[2], v.x, v.y, v.z);
+          fl = BD_TRI_DIRTY | (o <= 0 ? BD_TRI_INVERTED : 0);
+          d.tv[t].w = (v.w & ~BD_TRI_FLAGS) | fl;
+        }
+        const bool inverted = (fl & BD_TRI_INVERTED) != 0;
+        inv += inverted ? 1 : 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int cc = 3 * t + k;
+          const int o = vk(nn, k);
+          // each interior edge once: from its smaller corner, or from this side
+          // when the neighbour is not visited by this pass
+          if (o < 0 || (o <= cc && (full || cmark[o / 3] == gen))) continue;
+          const int ku = (k + 1) % 3, kw = (k + 2) % 3;
+          const int u = vv[ku], w = vv[kw];
+          const bool disks = isd[ku] && isd[kw];
+          // r1 = r_w - r_u from the FP32 pairs (one rounding)
+          const float r1x = fdiff(W[kw].x, W[kw].z, W[ku].x, W[ku].z);
+          const float r1y = fdiff(W[kw].y, W[kw].w, W[ku].y, W[ku].w);
+          if (disks && (mvd[ku] | mvd[kw])) {
+            // Sec. 4.3 first criterion r0 . r1 < 0; r0 = r1 - (move of w - move
+            // of u), screened in FP32, exact on the grid near zero
+            bool rev;
+            if (mode != 1) {
+              const float2 mu = mvd[ku] ? d.dmove[u] : make_float2(0.f, 0.f);
+              const float2 mw = mvd[kw] ? d.dmove[w] : make_float2(0.f, 0.f);
+              const float r0x = __fsub_rn(r1x, __fsub_rn(mw.x, mu.x)), r0y = __fsub_rn(r1y, __fsub_rn(mw.y, mu.y));
+              // every rounding above is relative (one FP32 rounding of a grid
+              // value or of a sum): the computed dot is within ~8 2^-24 S of
+              // the exact one, S = |r0|^2 + |r1|^2 + |m_u|^2 + |m_w|^2
+              const float dot = __fadd_rn(__fmul_rn(r0x, r1x), __fmul_rn(r0y, r1y));
+              const float S = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r0x, r0x), __fmul_rn(r0y, r0y)),
+                                                  __fadd_rn(__fmul_rn(r1x, r1x), __fmul_rn(r1y, r1y))),
+                                        __fadd_rn(__fadd_rn(__fmul_rn(mu.x, mu.x), __fmul_rn(mu.y, mu.y)),
+                                                  __fadd_rn(__fmul_rn(mw.x, mw.x), __fmul_rn(mw.y, mw.y))));
+              const float bound = 4e-6f * S;
+              rev = dot > bound ? false : (-dot > bound ? true : reversed_exact(x, u, w, 0, 0, 0, 0, 0));
+            } else {
+              rev = reversed_exact(x, u, w, 0, 0, 0, 0, 0);
+            }
+            if (rev) {
+              ++rej;
+              atomicExch(&ctl->st_fail_item, cc);
+            }
+          }
+          if (inverted) continue;   // marks and scan wait for the repair
+          const int4 v1 = d.tv[o / 3];
+          const int q = vk(v1, o % 3);
+          const bool d1 = (v1.w & BD_TRI_DIRTY) || (mvd[ku] | mvd[kw]) || (fresh && d.moved[q]);
+          if ((fl & BD_TRI_DIRTY) || d1) {
+            const bool filt = isd[0] && isd[1] && isd[2] && q < x.np;
+            if (incircle_pre(x, filt, W[0], W[1], W[2], work_of(x, q), v.x, v.y, v.z, q) > 0) {
+              claim6(x, t, k, nn, o, claim_key(epoch, cc));
+              ++cand;
+            }
+          }
+          if (disks) {
+            // FP32 screen: a pair whose FP32 squared distance exceeds
+            // sigma^2 (1 + 1e-5) is farther than sigma (FP32 error ~3e-7)
+            if (__fadd_rn(__fmul_rn(r1x, r1x), __fmul_rn(r1y, r1y)) > x.sig2f) continue;
+            const double2 pu = d.pos[u], pw = d.pos[w];
+            // exact pre-test in grid units: |r_w - r_u|^2 <= (sigma/q)^2 (1 + 1e-9)
+            const int64_t ix = bdpred::to_int(pw.x, x.g) - bdpred::to_int(pu.x, x.g);
+            const int64_t iy = bdpred::to_int(pw.y, x.g) - bdpred::to_int(pu.y, x.g);
+            const bdpred::i128 ir2 = bdpred::add128(bdpred::smul64(ix, ix), bdpred::smul64(iy, iy));
+            const bool near = ir2.hi < c.sig2q_hi || (ir2.hi == c.sig2q_hi && ir2.lo <= c.sig2q_lo);
+            if (near) {
+              // the decision itself as the FP64 reference makes it
               const double dx = bdem::grid_to_double(ix, x.g.s), dy = bdem::grid_to_double(iy, x.g.s);
               const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
               const double r = sqrt(r2);
@@ -778,6 +918,10 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         if (log_pidx >= 0) d.log_pflags[(size_t)log_pidx * x.np + i] = (uint8_t)(rfl | (capped ? 16 : 0));
         d.pos[i] = np2;
         d.work[i] = split_pos(np2);
+        if (!PER) {
+          d.dmove[i] = make_float2(bdem::grid_to_float(bdpred::to_int(np2.x, x.g) - bdpred::to_int(p.x, x.g), x.g.s),
+                                   bdem::grid_to_float(bdpred::to_int(np2.y, x.g) - bdpred::to_int(p.y, x.g), x.g.s));
+        }
         d.disp[i] = make_double2(0.0, 0.0);
         d.moved[i] = 1;
         // the next pass visits the star of the moved disk (walked across the

@@ -568,6 +568,8 @@ __global__ void k_integrate(BdDev d, BdConst c, long long step, int log_step, in
     flags = bdem::reflect_grid(bdpred::to_int(R.wall_lo, g), bdpred::to_int(R.wall_hi, g), X, Y);
   }
   d.pos[i] = make_double2(bdem::grid_to_double(X, c.qshift), bdem::grid_to_double(Y, c.qshift));
+  d.dmove[i] = make_float2(bdem::grid_to_float(X - bdpred::to_int(p.x, g), c.qshift),
+                           bdem::grid_to_float(Y - bdpred::to_int(p.y, g), c.qshift));
   const float2 sx = bdem::grid_split(X, c.qshift), sy = bdem::grid_split(Y, c.qshift);
   d.work[i] = make_float4(sx.x, sy.x, sx.y, sy.y);
   d.theta[i] = thn;
