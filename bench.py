@@ -487,9 +487,7 @@ def main():
         for _ in range(args.e2e_steps):
             system.set_state(hxy, hth)          # host -> device (positions, directions)
             system.step(1)
-            o = system.state(want_tri=False)    # device -> host
-            hxy[:] = o["xy"]
-            hth[:] = o["theta"]
+            system.read_state(hxy, hth)         # device -> host
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         if ws > 1:
@@ -497,7 +495,7 @@ def main():
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             te = float(tt.item())
         e2e = {"value": ws * N * args.e2e_steps / te, "unit": UNIT,
-               "h2d_bytes_per_step": N * (16 + 4), "d2h_bytes_per_step": N * (16 + 4 + 1)}
+               "h2d_bytes_per_step": N * (16 + 4), "d2h_bytes_per_step": N * (16 + 4)}
 
     if rank == 0:
         if args.workload != "n1e5":

@@ -235,6 +235,10 @@ int bd_get_tuning(bd_handle *h, int32_t *tiles_per_item, int32_t *variant, int32
  *            corner shifts bd_get_tri_shifts gives.
  *   n_tri    receives the number of triangles, 2(n+G)-6 (periodic: 2n).
  *   step     receives the index of the next step.
+ * Positions, directions and species are permuted to external order on the
+ * device and copied straight into the caller's arrays (one copy each; page-
+ * locked arrays make it a direct transfer).  The call returns when the
+ * copies are complete.
  * Errors: BD_ERR_ARG (h == NULL), BD_ERR_CUDA. */
 int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32_t *tri,
                  int32_t *n_tri, int64_t *step);
@@ -245,7 +249,11 @@ int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32
  * flips, Sec. 4.3), so moves should be small compared with the disk spacing.
  * No two disks may be closer than sigma: the device scans the repaired
  * Delaunay triangulation's edges, which hold the closest pair (Verlet-list
- * handles check on the host).
+ * handles check on the host).  The arrays are copied to the device as they
+ * are (page-locked arrays make it a direct transfer); the range checks (finite;
+ * with walls a centre in [a, L-a] up to 1e-9 L), the rounding to the position
+ * grid and the permutation to the internal order run there.  The call
+ * returns when the new state is in place and checked.
  * Errors: BD_ERR_ARG, BD_ERR_INIT_OVERLAP (a centre outside the box, or a
  * pair closer than sigma; state unchanged), BD_ERR_STEP_REJECTED (repair
  * failed; state unchanged), BD_ERR_CUDA. */

@@ -243,6 +243,16 @@ class System:
                                    ctypes.byref(nt), ctypes.byref(stp)), "bd_get_state")
         return dict(xy=xy, theta=th, species=sp, tri=tri, n_tri=nt.value, step=stp.value)
 
+    def read_state(self, xy, theta=None, species=None):
+        """Fill caller-owned arrays (C-contiguous; float64 (n, 2), float32 (n,), uint8 (n,))
+        with the current positions, directions and species, without allocating."""
+        n = self.n
+        for a, dt, shape in ((xy, np.float64, (n, 2)), (theta, np.float32, (n,)), (species, np.uint8, (n,))):
+            if a is not None and (a.dtype != dt or a.shape != shape or not a.flags.c_contiguous):
+                raise ValueError("read_state: expected a C-contiguous %s array of shape %s" % (np.dtype(dt), shape))
+        _check(load().bd_get_state(self.h, _ptr(xy), _ptr(theta), _ptr(species), None, None, None),
+               "bd_get_state")
+
     def tri_shifts(self, replica=-1):
         """Corner image shifts (n_tri, 3, 2) of the triangulation (periodic box)."""
         nt = self.n_tri if replica < 0 else self.replica_sizes()[replica][1]

@@ -14,7 +14,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libbd_gb300.so")
 SOURCES = ["bd_capi.cu", "kernels_force.cu", "kernels_dt.cu", "host_init.cpp", "noalloc.cu", "kernels_short.cu",
            "adjoint.cu", "rollout.cu", "kernels_sym.cu",
-           "kernels_vcorr.cu"]
+           "kernels_vcorr.cu", "kernels_io.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I", os.path.join(HERE, "..", "include")]

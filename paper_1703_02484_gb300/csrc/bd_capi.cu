@@ -746,6 +746,10 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     BD_TRY(dalloc(h, &d.species, (size_t)np));
     BD_TRY(dalloc(h, &d.ext_id, (size_t)np));
     BD_TRY(dalloc(h, &d.rep_of, (size_t)np));
+    BD_TRY(dalloc(h, &d.ext_glob, (size_t)np));
+    BD_TRY(dalloc(h, &d.xfer_xy, (size_t)std::max(1, h->n)));
+    BD_TRY(dalloc(h, &d.xfer_th, (size_t)std::max(1, h->n)));
+    BD_TRY(dalloc(h, &d.xfer_sp, (size_t)std::max(1, h->n)));
     BD_TRY(dalloc(h, &d.moved, nv));
     BD_TRY(dalloc(h, &d.dmove, (size_t)np));
     if (c.any_periodic) {
@@ -853,6 +857,7 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     BD_TRY(cudaMemcpyAsync(d.species, sp_i.data(), np, cudaMemcpyHostToDevice, st));
     BD_TRY(cudaMemcpyAsync(d.ext_id, slot_local.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
     BD_TRY(cudaMemcpyAsync(d.rep_of, slot_rep.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    BD_TRY(cudaMemcpyAsync(d.ext_glob, h->ext_of_int.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
     BD_TRY(cudaMemsetAsync(d.moved, 0, nv, st));
     BD_TRY(cudaMemsetAsync(d.disp, 0, np * sizeof(double2), st));
     BD_TRY(cudaMemcpyAsync(d.tv, tv_all.data(), nt * sizeof(int4), cudaMemcpyHostToDevice, st));
@@ -1369,19 +1374,15 @@ int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32
                  int32_t *n_tri, int64_t *step) {
   if (!h) return BD_ERR_ARG;
   const int np = h->np, n = h->n;
-  std::vector<double2> pos;
-  std::vector<float> t;
-  std::vector<uint8_t> s;
-  int rc = fetch_disks(h, xy ? &pos : nullptr, theta ? &t : nullptr, species ? &s : nullptr);
-  if (rc) return rc;
-  for (int i = 0; i < n; ++i) {
-    const int k = h->int_of_ext[i];
-    if (xy) {
-      xy[2 * i] = pos[k].x;
-      xy[2 * i + 1] = pos[k].y;
-    }
-    if (theta) theta[i] = t[k];
-    if (species) species[i] = s[k];
+  if (xy || theta || species) {
+    // permuted to the caller's order on the device, then one copy per array
+    cudaStream_t st = h->stream;
+    cudaError_t e = bd_launch_state_out(h->d, h->c, st);
+    if (e == cudaSuccess && xy) e = cudaMemcpyAsync(xy, h->d.xfer_xy, (size_t)n * sizeof(double2), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && theta) e = cudaMemcpyAsync(theta, h->d.xfer_th, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && species) e = cudaMemcpyAsync(species, h->d.xfer_sp, (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
   }
   if (tri && !h->c.overlap_verlet) {
     std::vector<int4> tv(h->nt);
@@ -1458,25 +1459,16 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
   if (!h || !xy) return BD_ERR_ARG;
   const int np = h->np;
   const BdConst &c = h->c;
-  std::vector<double> wrapped;
-  for (const RepHost &RH : h->reps) {
-    const double *x = xy + 2 * (size_t)RH.ext_base;
-    if (RH.periodic) {
-      wrapped.resize(2 * (size_t)RH.n);
-      for (int i = 0; i < 2 * RH.n; ++i)
-        if (!isfinite(x[i])) return BD_ERR_INIT_OVERLAP;
-      continue;
-    }
-    for (int i = 0; i < 2 * RH.n; ++i)
-      if (!isfinite(x[i]) || x[i] < c.a - 1e-9 * RH.L || x[i] > RH.L - c.a + 1e-9 * RH.L)
-        return BD_ERR_INIT_OVERLAP;
-  }
-  // pairs closer than sigma are found on the device: the repaired Delaunay
-  // triangulation's edges hold the closest pair (Verlet-list handles, which
-  // keep no triangulation, check on the host)
-  if (c.overlap_verlet)
+  if (c.overlap_verlet) {
+    // Verlet-list handles keep no triangulation: the range checks and the
+    // search for pairs closer than sigma run on the host
+    std::vector<double> wrapped;
     for (const RepHost &RH : h->reps) {
       const double *x = xy + 2 * (size_t)RH.ext_base;
+      for (int i = 0; i < 2 * RH.n; ++i)
+        if (!isfinite(x[i]) ||
+            (!RH.periodic && (x[i] < c.a - 1e-9 * RH.L || x[i] > RH.L - c.a + 1e-9 * RH.L)))
+          return BD_ERR_INIT_OVERLAP;
       if (RH.periodic) {
         wrapped.resize(2 * (size_t)RH.n);
         for (int i = 0; i < 2 * RH.n; ++i) wrapped[i] = periodic_coord(x[i], RH.L, c.q, c.inv_q);
@@ -1486,40 +1478,28 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
         return BD_ERR_INIT_OVERLAP;
       }
     }
-  for (const RepHost &RH : h->reps) {
-    const double *x = xy + 2 * (size_t)RH.ext_base;
-    for (int i = 0; i < RH.n; ++i) {
-      const int k = h->int_of_ext[RH.ext_base + i];
-      if (RH.periodic) {
-        h->host_pos[2 * k] = periodic_coord(x[2 * i], RH.L, c.q, c.inv_q);
-        h->host_pos[2 * k + 1] = periodic_coord(x[2 * i + 1], RH.L, c.q, c.inv_q);
-      } else {
-        h->host_pos[2 * k] = std::min(RH.wall_hi, std::max(RH.wall_lo, snap_host(x[2 * i], c.q, c.inv_q)));
-        h->host_pos[2 * k + 1] = std::min(RH.wall_hi, std::max(RH.wall_lo, snap_host(x[2 * i + 1], c.q, c.inv_q)));
-      }
-    }
   }
+  // The caller's arrays are copied as they are; the range checks, the
+  // rounding to the grid and the permutation to slot order run on the device
+  // (k_state_check, k_state_in), and pairs closer than sigma are found by the
+  // repaired Delaunay triangulation's overlap scan (its edges hold the closest
+  // pair).  Any failure leaves the previous state in place.
   cudaStream_t st = h->stream;
   const BdDev &d = h->d;
-  cudaError_t e;
-  e = cudaMemcpyAsync(d.pos0, d.pos, (size_t)np * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+  cudaError_t e = reset_stats(h);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d.pos0, d.pos, (size_t)np * sizeof(double2), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d.prev, d.pos, (size_t)np * sizeof(double2), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d.theta0, d.theta, (size_t)np * sizeof(float), cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d.pos, h->host_pos.data(), (size_t)np * sizeof(double2), cudaMemcpyHostToDevice, st);
-  std::vector<float> th;
-  if (e == cudaSuccess && theta) {
-    th.assign(np, 0.f);
-    for (int i = 0; i < h->n; ++i) th[h->int_of_ext[i]] = theta[i];
-    e = cudaMemcpyAsync(d.theta, th.data(), (size_t)np * sizeof(float), cudaMemcpyHostToDevice, st);
-  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d.xfer_xy, xy, (size_t)h->n * sizeof(double2), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && theta) e = cudaMemcpyAsync(d.xfer_th, theta, (size_t)h->n * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = bd_launch_state_in(d, c, theta ? 1 : 0, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.moved, 1, (size_t)np, st);
   // periodic box: a new coordinate across an edge from the old one re-entered
   if (e == cudaSuccess && c.any_periodic) e = bd_launch_periodic_wraps(d, c, st);
   if (e == cudaSuccess) e = bd_launch_work_copy(d, c, st);
-  if (e == cudaSuccess) e = reset_stats(h);
   if (e == cudaSuccess && !c.overlap_verlet) e = bd_launch_dt(d, c, 1, st, h->dt_grid, h->dt_block);
   if (e != cudaSuccess) return cuda_fail(e);
-  int rc = read_ctl(h);   // synchronises the stream (the staged theta stays alive until here)
+  int rc = read_ctl(h);   // synchronises the stream
   if (rc) return rc;
   if (h->h_ctl->status) return finish_status(h, h->h_ctl->status);
   return BD_OK;

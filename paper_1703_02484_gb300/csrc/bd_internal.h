@@ -110,6 +110,10 @@ struct BdDev {
   uint8_t *species;        // 255 = empty slot
   int *ext_id;             // index within its replica (-1 = empty slot): the Philox counter
   int *rep_of;             // replica of each slot (-1 = empty slot)
+  int *ext_glob;           // each slot's index in the caller's order over all replicas (-1 = empty)
+  double2 *xfer_xy;        // [n] state transfers in the caller's order: positions,
+  float *xfer_th;          //   directions,
+  uint8_t *xfer_sp;        //   species
   uint8_t *moved;
   float2 *dmove;           // position less prev, FP32 (disks with the moved flag; the reversal filter)
   uint8_t *wrap;           // periodic box: re-entries of the last move (bits 0-1 x, 2-3 y; 1 = -L, 3 = +L)
@@ -188,6 +192,11 @@ int bd_dt_grid(int *grid, int *block);
 int bd_dt_grid_for(int work_items, int *grid, int *block);
 int bd_force_blocks_per_sm(int variant);
 cudaError_t bd_launch_work_copy(const BdDev &d, const BdConst &c, cudaStream_t s);
+// caller-order positions (and directions) in xfer_* -> checked, grid-rounded slots; a
+// disk outside the box sets status BD_ERR_INIT_OVERLAP and nothing is stored
+cudaError_t bd_launch_state_in(const BdDev &d, const BdConst &c, int with_theta, cudaStream_t s);
+// slots -> caller-order positions, directions and species in xfer_*
+cudaError_t bd_launch_state_out(const BdDev &d, const BdConst &c, cudaStream_t s);
 // periodic box, after new positions were set (pos0 = old): the re-entry of
 // each disk (wrap bytes, n_wrapped) for the triangulation's corner shifts
 cudaError_t bd_launch_periodic_wraps(const BdDev &d, const BdConst &c, cudaStream_t s);

@@ -1,0 +1,90 @@
+// State transfers between the caller's order and the internal slot order.
+//
+// The caller's positions and directions are copied to the device as they are
+// (disk e of the concatenated replicas at index e) and permuted there: one
+// thread per internal slot gathers its disk, checks it, rounds it to the
+// position grid and stores it.  bd_get_state runs the inverse scatter and one
+// copy per array to the caller.  The checks and roundings are the same
+// operations, in the same order and precision, as the host's at bd_init, so a
+// position set here is the one bd_init would have stored.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "bd_internal.h"
+
+namespace {
+
+__device__ __forceinline__ double snap_grid(double v, const BdConst &c) {
+  return __dmul_rn(rint(__dmul_rn(v, c.inv_q)), c.q);
+}
+
+// a periodic coordinate in [0, L) on the grid (L is a multiple of q)
+__device__ __forceinline__ double periodic_grid(double v, double L, const BdConst &c) {
+  double y = snap_grid(__dsub_rn(v, __dmul_rn(L, floor(__ddiv_rn(v, L)))), c);
+  if (y >= L) y = __dsub_rn(y, L);
+  if (y < 0.0) y = __dadd_rn(y, L);
+  return y;
+}
+
+// a centre must be finite and, with walls, lie in [a, L - a] up to 1e-9 L
+__global__ void k_state_check(BdDev d, BdConst c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.np) return;
+  const int e = d.ext_glob[i];
+  if (e < 0) return;
+  const BdRep &R = d.rep[d.rep_of[i]];
+  const double2 p = d.xfer_xy[e];
+  bool bad = !isfinite(p.x) || !isfinite(p.y);
+  if (!R.periodic) {
+    const double tol = __dmul_rn(1e-9, R.L);
+    const double lo = __dsub_rn(c.a, tol), hi = __dadd_rn(__dsub_rn(R.L, c.a), tol);
+    bad = bad || p.x < lo || p.x > hi || p.y < lo || p.y > hi;
+  }
+  if (bad) atomicCAS(&d.ctl->status, 0, BD_ERR_INIT_OVERLAP);
+}
+
+// store the checked positions (and directions) in slot order; nothing is
+// written when any disk failed the check
+__global__ void k_state_in(BdDev d, BdConst c, int with_theta) {
+  if (*(volatile const int *)&d.ctl->status) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.np) return;
+  const int e = d.ext_glob[i];
+  if (e < 0) return;
+  const BdRep &R = d.rep[d.rep_of[i]];
+  const double2 p = d.xfer_xy[e];
+  double2 y;
+  if (R.periodic) {
+    y = make_double2(periodic_grid(p.x, R.L, c), periodic_grid(p.y, R.L, c));
+  } else {
+    y = make_double2(fmin(R.wall_hi, fmax(R.wall_lo, snap_grid(p.x, c))),
+                     fmin(R.wall_hi, fmax(R.wall_lo, snap_grid(p.y, c))));
+  }
+  d.pos[i] = y;
+  if (with_theta) d.theta[i] = d.xfer_th[e];
+}
+
+__global__ void k_state_out(BdDev d, BdConst c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.np) return;
+  const int e = d.ext_glob[i];
+  if (e < 0) return;
+  d.xfer_xy[e] = d.pos[i];
+  d.xfer_th[e] = d.theta[i];
+  d.xfer_sp[e] = d.species[i];
+}
+
+}  // namespace
+
+cudaError_t bd_launch_state_in(const BdDev &d, const BdConst &c, int with_theta, cudaStream_t s) {
+  const int nb = (c.np + 255) / 256;
+  k_state_check<<<nb, 256, 0, s>>>(d, c);
+  k_state_in<<<nb, 256, 0, s>>>(d, c, with_theta);
+  return cudaGetLastError();
+}
+
+cudaError_t bd_launch_state_out(const BdDev &d, const BdConst &c, cudaStream_t s) {
+  k_state_out<<<(c.np + 255) / 256, 256, 0, s>>>(d, c);
+  return cudaGetLastError();
+}
