@@ -180,7 +180,7 @@ def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind, v
     triangles the check passes visited (bd_step_stats.tri_visits, V):
       k_triangulation: a check pass reads the corner table of each triangle
         it visits (32 B) and, in the first pass of the step, each disk's moved
-        flag and FP32 position (17 B); the first pass also writes the rollback
+        flag, FP32 position and FP32 move (25 B); the first pass also writes the rollback
         snapshot (32 B per triangle); a flip round reads the claims and flags
         of the triangles its pass visited (24 B each); an apply pass reads and
         writes positions, displacements and flags (100 B per disk).
@@ -202,7 +202,7 @@ def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind, v
         T = system.n_tri
         P, F, A = (stage_raw[k][1] / steps for k in ("check", "flip", "apply"))
         V = visits if visits else P * T
-        per = 32 * V + 17 * N + 32 * T + 24 * V * (F / max(P, 1.0)) + A * 100 * N
+        per = 32 * V + 25 * N + 32 * T + 24 * V * (F / max(P, 1.0)) + A * 100 * N
         kernel = "k_triangulation"
         note = ("%.2f check passes visiting %.0f triangles, %.2f flip rounds, %.2f apply passes per "
                 "launch; %d triangles" % (P, V, F, A, T))
