@@ -16,8 +16,14 @@ the parameters p = (A00, A01, A10, A11, v0):
   d_j(z)_u = -sum (sigma - r) n,  d_j(z)_w = +sum (sigma - r) n  over the pass's
             pairs (u, w), n = (z_w - z_u)/r, r = |z_w - z_u|;
   cap(d) = d, or (sigma/4) d/|d| for a capped disk.
-The loss is L = sum_s (MSD_s - target)^2 with MSD_s the mean of
-|x_T - x_0|^2 over species s.
+Two losses of the final positions x_T:
+  MSD:  L = sum_s (MSD_s - target)^2 with MSD_s the mean of |x_T - x_0|^2
+        over species s;
+  HIST: L = sum_b (h_b(x_T) - h_b(x_0))^2, the pair-distance histogram of
+        the final positions against that of the start, with 32 Gaussian
+        bins of width a/4 centred over [2a, 10a]:
+        h_b(x) = (1/n) sum_{i<j} exp(-(r_ij - c_b)^2 / (2 s^2)),
+        c_b = 2a + (b + 1/2) a/4, s = a/4 (walls: no images).
 
 The gradient, (a) by forward-mode tangents: T = dx/dp (n, 2, 5) carried
 through every move and pass with the chain rule, and (b) by central finite
@@ -223,6 +229,69 @@ def msd_loss_grad(xT, x0, species, target):
     return g
 
 
+HIST_BINS = 32
+
+
+def hist_centres(a):
+    """c_b = 2a + (b + 1/2) a/4, b = 0..31: 32 bins of width a/4 covering [2a, 10a]."""
+    return 2.0 * a + (np.arange(HIST_BINS) + 0.5) * (0.25 * a)
+
+
+def pair_histogram(x, a):
+    """h_b = (1/n) sum over pairs i < j of exp(-(r_ij - c_b)^2 / (2 s^2)), s = a/4."""
+    x = np.asarray(x, dtype=np.float64)
+    n = len(x)
+    c = hist_centres(a)
+    s2 = (0.25 * a) ** 2
+    h = np.zeros(HIST_BINS)
+    for i in range(n - 1):
+        d = x[i + 1:] - x[i]
+        r = np.sqrt(d[:, 0] ** 2 + d[:, 1] ** 2)
+        u = r[:, None] - c[None, :]
+        h += np.exp(-u * u / (2.0 * s2)).sum(axis=0)
+    return h / n
+
+
+def hist_loss(xT, x0, a):
+    return float(np.sum((pair_histogram(xT, a) - pair_histogram(x0, a)) ** 2))
+
+
+def hist_loss_grad(xT, x0, a):
+    """dL/dx_T, (n, 2): dL/dr_ij = sum_b 2 (h_b - h0_b)/n * dK/du(r_ij - c_b),
+    K(u) = exp(-u^2 / (2 s^2)), dK/du = -(u / s^2) K(u), and dr_ij/dx_i = (x_i - x_j)/r_ij."""
+    xT = np.asarray(xT, dtype=np.float64)
+    n = len(xT)
+    c = hist_centres(a)
+    s2 = (0.25 * a) ** 2
+    wb = 2.0 * (pair_histogram(xT, a) - pair_histogram(x0, a)) / n
+    g = np.zeros_like(xT)
+    for i in range(n - 1):
+        d = xT[i] - xT[i + 1:]
+        r = np.sqrt(d[:, 0] ** 2 + d[:, 1] ** 2)
+        u = r[:, None] - c[None, :]
+        dLdr = (wb[None, :] * (-u / s2) * np.exp(-u * u / (2.0 * s2))).sum(axis=1)
+        v = (dLdr / r)[:, None] * d
+        g[i] += v.sum(axis=0)
+        g[i + 1:] -= v
+    return g
+
+
+def loss_value(xT, x0, species, target, a, loss="msd"):
+    if loss == "msd":
+        return msd_loss(xT, x0, species, target)
+    if loss == "hist":
+        return hist_loss(xT, x0, a)
+    raise ValueError(loss)
+
+
+def loss_grad(xT, x0, species, target, a, loss="msd"):
+    if loss == "msd":
+        return msd_loss_grad(xT, x0, species, target)
+    if loss == "hist":
+        return hist_loss_grad(xT, x0, a)
+    raise ValueError(loss)
+
+
 # ---------------------------------------------------------------- gradients
 
 def _pair_G(v, sigma):
@@ -234,7 +303,7 @@ def _pair_G(v, sigma):
     return (sigma / r)[:, None, None] * P - I
 
 
-def tangent_gradient(rec, species, p, target, threads=1):
+def tangent_gradient(rec, species, p, target, threads=1, loss="msd"):
     """dL/dp, p = (A00, A01, A10, A11, v0), by forward-mode tangents along the
     frozen map.  Returns (grad (5,), final positions)."""
     sigma = 2.0 * p.a
@@ -277,11 +346,11 @@ def tangent_gradient(rec, species, p, target, threads=1):
                 Td[c] = np.einsum("mab,mbk->mak", ((sigma / 4.0) / m)[:, None, None] * P, Td[c])
             x = apply_flags(x + capped_move(d, c, sigma), ps["flags"], p.a, p.L)
             Tm = (Tm + Td) * flag_signs(ps["flags"])[:, :, None]
-    g = msd_loss_grad(x, rec["x0"], sp, target)
+    g = loss_grad(x, rec["x0"], sp, target, p.a, loss)
     return np.einsum("ia,iak->k", g, Tm), x
 
 
-def fd_gradient(rec, species, p, target, h=1e-4, threads=1):
+def fd_gradient(rec, species, p, target, h=1e-4, threads=1, loss="msd"):
     """dL/dp by central differences of the frozen replay, step h."""
     base = np.array(list(p.alpha) + [p.v0], dtype=np.float64)
     out = np.zeros(NPARAM)
@@ -291,6 +360,6 @@ def fd_gradient(rec, species, p, target, h=1e-4, threads=1):
             q = base.copy()
             q[k] += sgn * h
             xT = replay(rec, species, p, alpha=tuple(q[:4]), v0=q[4], threads=threads)
-            vals.append(msd_loss(xT, rec["x0"], species, target))
+            vals.append(loss_value(xT, rec["x0"], species, target, p.a, loss))
         out[k] = (vals[0] - vals[1]) / (2.0 * h)
     return out

@@ -158,3 +158,71 @@ def test_reflection_flags_reproduce_walls():
     s = adjoint.flag_signs(f)
     assert np.all(s[(y[:, 0] < 1.0) | (y[:, 0] > 9.0), 0] == -1.0)
     assert np.all(s[(y[:, 0] >= 1.0) & (y[:, 0] <= 9.0), 0] == 1.0)
+
+
+# ---- pair-distance histogram loss ----
+
+def test_hist_single_pair_peaks_at_its_bin():
+    # one pair at the centre of bin 5: K(0) = 1 gives h_5 = 1/n, and the bins
+    # either side are equal (the centres are evenly spaced about it)
+    a = 1.0
+    c = adjoint.hist_centres(a)
+    assert c[0] == 2.125 and c[-1] == 9.875 and np.allclose(np.diff(c), 0.25)
+    x = np.array([[10.0, 10.0], [10.0 + c[5], 10.0]])
+    h = adjoint.pair_histogram(x, a)
+    assert int(np.argmax(h)) == 5 and h[5] == 0.5
+    assert abs(h[4] - h[6]) <= 1e-15 and abs(h[2] - h[8]) <= 1e-15
+    assert h[4] < h[5] and h[3] < h[4]
+
+
+@pytest.mark.parametrize("side", [6.0, 5.3, 7.11])
+def test_hist_bins_sum_to_the_gaussian_integral(side):
+    # bins spaced one kernel width s apart: for a distance r well inside
+    # [2a, 10a] the sum over bins of exp(-(r - c_b)^2 / 2 s^2) is, by Poisson
+    # summation, sqrt(2 pi) (1 + 2 exp(-2 pi^2) cos(2 pi (r - c_0) / s)) (the
+    # next term is exp(-8 pi^2) ~ 1e-34; the 32-bin truncation cuts tails
+    # beyond 11 s)
+    a = 1.0
+    s = 0.25 * a
+    tri = side * np.array([[0.0, 0.0], [1.0, 0.0], [0.5, np.sqrt(3.0) / 2.0]])
+    h = adjoint.pair_histogram(tri + 20.0, a)
+    c0 = adjoint.hist_centres(a)[0]
+    want = np.sqrt(2.0 * np.pi) * (1.0 + 2.0 * np.exp(-2.0 * np.pi ** 2) * np.cos(2.0 * np.pi * (side - c0) / s))
+    assert abs(h.sum() - want) <= 1e-13     # 3 pairs at distance side, n = 3
+
+
+def test_hist_is_rigid_motion_invariant():
+    rng = np.random.default_rng(8)
+    x = rng.uniform(0.0, 14.0, (40, 2))
+    phi = 0.7
+    R = np.array([[np.cos(phi), -np.sin(phi)], [np.sin(phi), np.cos(phi)]])
+    y = x @ R.T + np.array([3.0, -5.0])
+    assert np.max(np.abs(adjoint.pair_histogram(x, 1.0) - adjoint.pair_histogram(y, 1.0))) <= 1e-13
+    assert adjoint.hist_loss(y, x, 1.0) <= 1e-26
+
+
+def test_hist_loss_gradient_matches_differences():
+    rng = np.random.default_rng(9)
+    n = 30
+    x0 = rng.uniform(0.0, 12.0, (n, 2))
+    xT = x0 + rng.normal(scale=0.4, size=(n, 2))
+    g = adjoint.hist_loss_grad(xT, x0, 1.0)
+    eps = 1e-6
+    for i in (0, 11, 29):
+        for c in (0, 1):
+            a, b = xT.copy(), xT.copy()
+            a[i, c] += eps
+            b[i, c] -= eps
+            fd = (adjoint.hist_loss(a, x0, 1.0) - adjoint.hist_loss(b, x0, 1.0)) / (2 * eps)
+            assert abs(fd - g[i, c]) <= 1e-6 * max(1e-6, np.max(np.abs(g)))
+    # a rigid translation of x_T changes nothing: the gradient sums to zero
+    assert np.max(np.abs(g.sum(axis=0))) <= 1e-12 * np.max(np.abs(g))
+
+
+def test_tangent_gradient_hist_loss_matches_central_differences(fast_rollout):
+    rec, sp, p = fast_rollout
+    g, _ = adjoint.tangent_gradient(rec, sp, p, target=0.1, loss="hist")
+    fd = adjoint.fd_gradient(rec, sp, p, target=0.1, h=1e-4, loss="hist")
+    scale = np.max(np.abs(fd))
+    assert scale > 0
+    assert np.max(np.abs(g - fd)) <= 1e-6 * scale, (g, fd)
