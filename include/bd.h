@@ -382,7 +382,7 @@ int bd_forces_noalloc(int32_t n, const double *xy, const uint8_t *species, const
  * single-system handles only.
  * Pair terms of the adjoint are computed in FP32, every sum in FP64. */
 
-enum { BD_LOSS_MSD = 0 };
+enum { BD_LOSS_MSD = 0, BD_LOSS_HIST = 1 };
 
 /* Replace the force table (alpha: 4 doubles, the table of one or two species
  * as bd_params.alpha, NULL = keep) and the self-propulsion speed (v0; NaN =
@@ -399,6 +399,13 @@ int bd_set_step(bd_handle *h, int64_t step);
  * the loss at the final positions x_T against the positions x_0 at the call:
  *   BD_LOSS_MSD:  L = sum over species s of (MSD_s - target)^2,
  *                 MSD_s = mean over disks of species s of |x_T - x_0|^2.
+ *   BD_LOSS_HIST: L = sum over bins b of (h_b(x_T) - h_b(x_0))^2, the
+ *                 pair-distance histogram of x_T against that of the start:
+ *                 h_b(x) = (1/n) sum over pairs i < j of
+ *                 exp(-(r_ij - c_b)^2 / (2 s^2)), 32 bins of width a/4 over
+ *                 [2a, 10a] (c_b = 2a + (b + 1/2) a/4), s = a/4; pairs
+ *                 farther than 12.5a (weight < 1e-24) are skipped; target is
+ *                 not used.  Sums in FP64, in a fixed order.
  *   loss   receives L (may be NULL).   stats  as bd_step (may be NULL).
  * Device memory: nsteps*N bytes of reflection flags, N bytes per correction
  * pass, 8 bytes per overlapping pair, 20*N bytes per checkpoint.

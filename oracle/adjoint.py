@@ -306,6 +306,14 @@ def _pair_G(v, sigma):
 def tangent_gradient(rec, species, p, target, threads=1, loss="msd"):
     """dL/dp, p = (A00, A01, A10, A11, v0), by forward-mode tangents along the
     frozen map.  Returns (grad (5,), final positions)."""
+    Tm, x = tangent_map(rec, species, p, threads)
+    g = loss_grad(x, rec["x0"], species, target, p.a, loss)
+    return np.einsum("ia,iak->k", g, Tm), x
+
+
+def tangent_map(rec, species, p, threads=1):
+    """dx_T/dp, (n, 2, 5), carried forward through every move and pass of the
+    frozen map; returns (dx_T/dp, x_T)."""
     sigma = 2.0 * p.a
     sp = np.asarray(species)
     x = rec["x0"].copy()
@@ -346,8 +354,7 @@ def tangent_gradient(rec, species, p, target, threads=1, loss="msd"):
                 Td[c] = np.einsum("mab,mbk->mak", ((sigma / 4.0) / m)[:, None, None] * P, Td[c])
             x = apply_flags(x + capped_move(d, c, sigma), ps["flags"], p.a, p.L)
             Tm = (Tm + Td) * flag_signs(ps["flags"])[:, :, None]
-    g = loss_grad(x, rec["x0"], sp, target, p.a, loss)
-    return np.einsum("ia,iak->k", g, Tm), x
+    return Tm, x
 
 
 def fd_gradient(rec, species, p, target, h=1e-4, threads=1, loss="msd"):

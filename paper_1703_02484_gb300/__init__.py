@@ -3,6 +3,6 @@
 The compute path is libbd_gb300.so (CUDA kernels for sm_103a behind the C ABI
 of include/bd.h); this package only marshals arguments to it."""
 from . import workloads  # noqa: F401
-from .binding import (BOUNDARY_PERIODIC, BOUNDARY_WALLS, LAW_LONG, LAW_NONE, LAW_SHORT, LOSS_MSD,  # noqa: F401
+from .binding import (BOUNDARY_PERIODIC, BOUNDARY_WALLS, LAW_LONG, LAW_NONE, LAW_SHORT, LOSS_HIST, LOSS_MSD,  # noqa: F401
                       OVERLAP_DELAUNAY, OVERLAP_VERLET, BDError, System, load, make_params,
                       params_from_config, rollout_loss)

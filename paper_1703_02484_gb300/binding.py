@@ -19,6 +19,7 @@ ERRORS = {
 LAW_NONE, LAW_LONG, LAW_SHORT = 0, 1, 2
 BOUNDARY_WALLS, BOUNDARY_PERIODIC = 0, 1
 LOSS_MSD = 0
+LOSS_HIST = 1
 OVERLAP_DELAUNAY, OVERLAP_VERLET = 0, 1
 
 
@@ -370,12 +371,13 @@ class System:
         return a.value, b.value
 
 
-def rollout_loss(params, system, xy0, theta0, step0, nsteps, ckpt_every=20, target=0.1):
+def rollout_loss(params, system, xy0, theta0, step0, nsteps, ckpt_every=20, target=0.1, loss_kind=LOSS_MSD):
     """Differentiable rollout loss: params is a torch tensor (5,) =
     (A00, A01, A10, A11, v0); the system is reset to (xy0, theta0) at step
-    step0, advanced nsteps with bd_rollout, and the MSD loss returned as a
-    0-d float64 tensor whose backward runs bd_rollout_vjp."""
-    return _rollout_fn().apply(params, system, xy0, theta0, step0, nsteps, ckpt_every, target)
+    step0, advanced nsteps with bd_rollout, and the loss (LOSS_MSD or
+    LOSS_HIST) returned as a 0-d float64 tensor whose backward runs
+    bd_rollout_vjp."""
+    return _rollout_fn().apply(params, system, xy0, theta0, step0, nsteps, ckpt_every, target, loss_kind)
 
 
 _ROLLOUT_FN = None
@@ -388,12 +390,12 @@ def _rollout_fn():
 
         class RolloutLoss(torch.autograd.Function):
             @staticmethod
-            def forward(ctx, params, system, xy0, theta0, step0, nsteps, ckpt_every, target):
+            def forward(ctx, params, system, xy0, theta0, step0, nsteps, ckpt_every, target, loss_kind):
                 p = params.detach().to("cpu", torch.float64).numpy()
                 system.set_force_params(p[:4], p[4])
                 system.set_state(xy0, theta0)
                 system.set_step(step0)
-                loss, _ = system.rollout(nsteps, ckpt_every, target)
+                loss, _ = system.rollout(nsteps, ckpt_every, target, loss_kind)
                 ctx.system = system
                 ctx.dev = params.device
                 return torch.tensor(loss, dtype=torch.float64, device=params.device)
@@ -401,7 +403,7 @@ def _rollout_fn():
             @staticmethod
             def backward(ctx, g):
                 grad = torch.from_numpy(ctx.system.rollout_vjp()).to(ctx.dev)
-                return g * grad, None, None, None, None, None, None, None
+                return g * grad, None, None, None, None, None, None, None, None
 
         _ROLLOUT_FN = RolloutLoss
     return _ROLLOUT_FN

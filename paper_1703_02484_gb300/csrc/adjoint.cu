@@ -300,7 +300,135 @@ __global__ void k_msd_loss_grad(BdDev d, BdConst c, const double2 *x0, const dou
   lam[i] = make_double2(f * (p.x - q.x), f * (p.y - q.y));
 }
 
+// ---------------------------------------------------------------- pair-distance histogram loss
+// h_b(x) = (1/n) sum over pairs i < j of K(r_ij - c_b), K(u) = exp(-u^2 / (2 s^2)),
+// c_b = 2a + (b + 1/2) a/4 (b = 0..31), s = a/4; L = sum_b (h_b(x_T) - h_b(x_0))^2.
+// Pairs farther than 12.5a are skipped: their kernel weight at the last
+// centre (9.875a) is exp(-55) ~ 1e-24.  One warp per disk i; its lanes take
+// the disks j in a fixed stride, and the warp's sums are combined by a
+// shuffle tree, so every sum is in a fixed order (deterministic).
+
+#define BD_HIST_BINS 32
+
+__device__ __forceinline__ double hist_centre(double a, int b) {
+  return __dadd_rn(__dmul_rn(2.0, a), __dmul_rn((double)b + 0.5, __dmul_rn(0.25, a)));
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// per-disk partial histograms: hpart[i][b] = sum over j > i of K(r_ij - c_b)
+__global__ void k_hist_pairs(BdDev d, BdConst c, const double2 *x, double *hpart) {
+  const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= c.np) return;
+  double acc[BD_HIST_BINS];
+#pragma unroll
+  for (int b = 0; b < BD_HIST_BINS; ++b) acc[b] = 0.0;
+  if (d.ext_id[i] >= 0) {
+    const double a = c.a, s = 0.25 * a, inv2s2 = 1.0 / (2.0 * s * s), rc = 12.5 * a;
+    const double2 p = x[i];
+    for (int j = i + 1 + lane; j < c.np; j += 32) {
+      if (d.ext_id[j] < 0) continue;
+      const double2 q = x[j];
+      const double dx = __dsub_rn(q.x, p.x), dy = __dsub_rn(q.y, p.y);
+      const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+      if (r2 > rc * rc) continue;
+      const double r = sqrt(r2);
+#pragma unroll
+      for (int b = 0; b < BD_HIST_BINS; ++b) {
+        const double u = __dsub_rn(r, hist_centre(a, b));
+        acc[b] += exp(-__dmul_rn(__dmul_rn(u, u), inv2s2));
+      }
+    }
+  }
+  double mine = 0.0;
+#pragma unroll
+  for (int b = 0; b < BD_HIST_BINS; ++b) {
+    const double t = warp_sum_d(acc[b]);
+    if (lane == b) mine = t;
+  }
+  hpart[(size_t)i * BD_HIST_BINS + lane] = mine;
+}
+
+// h = sum over disks of hpart / n in a fixed order (8 row groups per bin,
+// combined in order); with h0: w_b = 2 (h_b - h0_b) / n and the loss
+__global__ void __launch_bounds__(256) k_hist_reduce(BdConst c, const double *hpart, double inv_n,
+                                                     const double *h0, double *h, double *w, double *loss) {
+  __shared__ double part[8][BD_HIST_BINS];
+  __shared__ double sq[BD_HIST_BINS];
+  const int b = threadIdx.x & 31, g = threadIdx.x >> 5;
+  double t = 0.0;
+  for (int i = g; i < c.np; i += 8) t += hpart[(size_t)i * BD_HIST_BINS + b];
+  part[g][b] = t;
+  __syncthreads();
+  if (g != 0) return;
+  double hb = 0.0;
+  for (int k = 0; k < 8; ++k) hb += part[k][b];
+  hb *= inv_n;
+  h[b] = hb;
+  if (!h0) return;
+  const double df = hb - h0[b];
+  w[b] = 2.0 * df * inv_n;
+  sq[b] = df * df;
+  __syncwarp();
+  if (b == 0 && loss) {
+    double L = 0.0;
+    for (int k = 0; k < BD_HIST_BINS; ++k) L += sq[k];
+    *loss = L;
+  }
+}
+
+// lam_i = dscale dL/dx_i = dscale sum_{j != i} g(r_ij) (x_i - x_j) / r_ij,
+// g(r) = sum_b w_b dK/du(r - c_b), dK/du = -(u / s^2) K(u)
+__global__ void k_hist_grad(BdDev d, BdConst c, const double2 *x, const double *w, double dscale,
+                            double2 *lam) {
+  const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= c.np) return;
+  double gx = 0.0, gy = 0.0;
+  if (d.ext_id[i] >= 0) {
+    const double a = c.a, s = 0.25 * a, inv_s2 = 1.0 / (s * s), inv2s2 = 0.5 * inv_s2, rc = 12.5 * a;
+    double wb[BD_HIST_BINS];
+#pragma unroll
+    for (int b = 0; b < BD_HIST_BINS; ++b) wb[b] = w[b];
+    const double2 p = x[i];
+    for (int j = lane; j < c.np; j += 32) {
+      if (j == i || d.ext_id[j] < 0) continue;
+      const double2 q = x[j];
+      const double dx = __dsub_rn(p.x, q.x), dy = __dsub_rn(p.y, q.y);
+      const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+      if (r2 > rc * rc) continue;
+      const double r = sqrt(r2);
+      double g = 0.0;
+#pragma unroll
+      for (int b = 0; b < BD_HIST_BINS; ++b) {
+        const double u = __dsub_rn(r, hist_centre(a, b));
+        g += wb[b] * (-u * inv_s2) * exp(-__dmul_rn(__dmul_rn(u, u), inv2s2));
+      }
+      gx += g / r * dx;
+      gy += g / r * dy;
+    }
+  }
+  gx = warp_sum_d(gx);
+  gy = warp_sum_d(gy);
+  if (lane == 0) lam[i] = make_double2(dscale * gx, dscale * gy);
+}
+
 // ---------------------------------------------------------------- launchers
+
+cudaError_t bd_adj_hist(const BdDev &d, const BdConst &c, int n, const double2 *x, double *hpart, double *h,
+                        const double *h0, double *w, double *loss, double2 *lam, double dscale, cudaStream_t s) {
+  if (n <= 0) return cudaErrorInvalidValue;
+  const int blocks = (int)(((size_t)c.np * 32 + 255) / 256);
+  k_hist_pairs<<<blocks, 256, 0, s>>>(d, c, x, hpart);
+  k_hist_reduce<<<1, 256, 0, s>>>(c, hpart, 1.0 / (double)n, h0, h, w, loss);
+  if (h0 && lam) k_hist_grad<<<blocks, 256, 0, s>>>(d, c, x, w, dscale, lam);
+  return cudaGetLastError();
+}
 
 cudaError_t bd_adj_rp_em(const BdDev &d, const BdConst &c, long long step, int k_local, cudaStream_t s) {
   k_rp_em<<<(c.np + 255) / 256, 256, 0, s>>>(d, c, step, k_local);

@@ -91,3 +91,8 @@ cudaError_t bd_adj_vjp_em(const BdDev &d, const BdConst &c, int k_local, const d
                           double2 *lam, double2 *jpart, double *gpart, double *grad, cudaStream_t s);
 cudaError_t bd_adj_msd(const BdDev &d, const BdConst &c, const double2 *x0, double *acc, double target,
                        double dscale, double2 *lam, double *loss, cudaStream_t s);
+// pair-distance histogram of the disk slots' positions x (n disks) into h[32]
+// (hpart: np x 32 doubles of scratch); with h0 also w = dL/dh, the loss
+// sum_b (h_b - h0_b)^2 (loss may be NULL) and, with lam, dscale dL/dx
+cudaError_t bd_adj_hist(const BdDev &d, const BdConst &c, int n, const double2 *x, double *hpart, double *h,
+                        const double *h0, double *w, double *loss, double2 *lam, double dscale, cudaStream_t s);

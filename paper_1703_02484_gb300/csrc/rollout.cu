@@ -51,6 +51,9 @@ struct BdRollout {
   int4 *tv_seg = nullptr, *tn_seg = nullptr;
   double2 *lam_T = nullptr;      // dL/dx at the final positions
   double *acc = nullptr;         // [0..3] MSD sums, [4] loss, [5] replay loss, [8..12] gradient
+  int loss_kind = BD_LOSS_MSD;
+  double *hist = nullptr;        // histogram loss: [0, 32) h(x_0), [32, 64) h, [64, 96) dL/dh
+  double *hpart = nullptr;       // [np][32] per-disk partial histograms
   // reverse-pass scratch
   double2 *seg_x = nullptr;
   float *seg_th = nullptr;
@@ -286,6 +289,8 @@ void rollout_release(bd_handle *h) {
   release(&r->tn_seg);
   release(&r->lam_T);
   release(&r->acc);
+  release(&r->hist);
+  release(&r->hpart);
   release(&r->seg_x);
   release(&r->seg_th);
   release(&r->seg_z);
@@ -344,7 +349,7 @@ int bd_rollout(bd_handle *h, int32_t nsteps, int32_t ckpt_every, int32_t loss_ki
                double *loss, bd_step_stats *stats) {
   if (!h || nsteps < 1 || ckpt_every < 1 || !isfinite(target)) return BD_ERR_ARG;
   if (stats) memset(stats, 0, sizeof(*stats));
-  if (loss_kind != BD_LOSS_MSD) return BD_ERR_UNSUPPORTED;
+  if (loss_kind != BD_LOSS_MSD && loss_kind != BD_LOSS_HIST) return BD_ERR_UNSUPPORTED;
   if (h->reps.size() != 1 || h->reps[0].p.law != BD_LAW_LONG || h->reps[0].periodic ||
       h->reps[0].p.n_species > 2)
     return BD_ERR_UNSUPPORTED;
@@ -360,6 +365,7 @@ int bd_rollout(bd_handle *h, int32_t nsteps, int32_t ckpt_every, int32_t loss_ki
   r->every = std::min(ckpt_every, nsteps);
   r->nseg = (nsteps + r->every - 1) / r->every;
   r->target = target;
+  r->loss_kind = loss_kind;
   r->step0 = h->step;
   cudaError_t e = cudaSuccess;
   if ((size_t)nsteps * np > r->refl_cap) {
@@ -383,6 +389,11 @@ int bd_rollout(bd_handle *h, int32_t nsteps, int32_t ckpt_every, int32_t loss_ki
     if (e == cudaSuccess) e = regrow(&r->tn_seg, 0, (size_t)h->nt, s);
     if (e == cudaSuccess) e = regrow(&r->lam_T, 0, np, s);
     if (e == cudaSuccess) e = regrow(&r->acc, 0, 16, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (loss_kind == BD_LOSS_HIST && !r->hist) {
+    e = regrow(&r->hist, 0, 96, s);
+    if (e == cudaSuccess) e = regrow(&r->hpart, 0, 32 * np, s);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   // log capacity guesses, raised as the rollout shows what it needs
@@ -472,7 +483,15 @@ int bd_rollout(bd_handle *h, int32_t nsteps, int32_t ckpt_every, int32_t loss_ki
   if (stats) *stats = acc_stats;
   if (e != cudaSuccess) return cuda_fail(e);
   // loss and dL/dx_T
-  e = bd_adj_msd(h->d, h->c, r->ck_pos, r->acc, target, 1.0, r->lam_T, r->acc + 4, s);
+  if (loss_kind == BD_LOSS_HIST) {
+    // the histogram of the start (the first checkpoint), then of x_T against it
+    e = bd_adj_hist(h->d, h->c, h->n, r->ck_pos, r->hpart, r->hist, nullptr, nullptr, nullptr, nullptr, 1.0, s);
+    if (e == cudaSuccess)
+      e = bd_adj_hist(h->d, h->c, h->n, h->d.pos, r->hpart, r->hist + 32, r->hist, r->hist + 64, r->acc + 4,
+                      r->lam_T, 1.0, s);
+  } else {
+    e = bd_adj_msd(h->d, h->c, r->ck_pos, r->acc, target, 1.0, r->lam_T, r->acc + 4, s);
+  }
   double lv = 0.0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&lv, r->acc + 4, sizeof(double), cudaMemcpyDeviceToHost, s);
   r->step_pass.assign(nsteps + 1, 0);
@@ -554,7 +573,13 @@ int bd_rollout_replay(bd_handle *h, const double *alpha, double v0, double *loss
   const BdDev dr = replay_dev(h, r);
   if (e == cudaSuccess) e = load_checkpoint(h, r, dr, 0);
   if (e == cudaSuccess) e = replay(h, r, dr, 0, r->nsteps, false);
-  if (e == cudaSuccess) e = bd_adj_msd(dr, h->c, r->ck_pos, r->acc, r->target, 1.0, nullptr, r->acc + 5, s);
+  if (e == cudaSuccess) {
+    if (r->loss_kind == BD_LOSS_HIST)
+      e = bd_adj_hist(dr, h->c, h->n, dr.pos, r->hpart, r->hist + 32, r->hist, r->hist + 64, r->acc + 5, nullptr,
+                      1.0, s);
+    else
+      e = bd_adj_msd(dr, h->c, r->ck_pos, r->acc, r->target, 1.0, nullptr, r->acc + 5, s);
+  }
   double lv = 0.0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&lv, r->acc + 5, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

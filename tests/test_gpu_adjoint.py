@@ -107,7 +107,8 @@ def test_fp32_rollout_gradient_matches_oracle():
 
 
 def test_full_size_rollout_gradient_matches_oracle():
-    # 4096 disks, area fraction 0.35, two species, v0 = 1, 200 steps, checkpoints every 20
+    # 4096 disks, area fraction 0.35, two species, v0 = 1, 200 steps, checkpoints
+    # every 20; both losses, from the same start and noise
     cfg = workloads.CONFIGS["c5"]
     xy, sp, th = workloads.initial_state(cfg)
     s = bd.System(bd.params_from_config(cfg), xy, sp, th, stream=stream())
@@ -115,15 +116,59 @@ def test_full_size_rollout_gradient_matches_oracle():
     loss, stats = s.rollout(cfg.steps, ckpt_every=20, target=TARGET)
     assert stats["steps_done"] == cfg.steps
     g = s.rollout_vjp()
+    s.set_state(st["xy"], st["theta"])
+    s.set_step(0)
+    loss_h, _ = s.rollout(cfg.steps, ckpt_every=20, loss_kind=bd.LOSS_HIST)
+    g_h = s.rollout_vjp()
     L = workloads.box_side(cfg.n, cfg.rho)
     P = ostep.Params(L=L, a=cfg.a, law=cfg.law, alpha=cfg.alpha, D=cfg.D, Dr=cfg.Dr, v0=cfg.v0, dt=cfg.dt,
                      seed=cfg.seed)
     rec = adjoint.record(st["xy"], st["theta"].astype(np.float64), sp, P, cfg.steps, threads=THREADS)
     assert s.rollout_log_size() == _log_size(rec)
     assert abs(loss - adjoint.msd_loss(rec["xT"], rec["x0"], sp, TARGET)) <= 1e-6 * loss
-    gref, _ = adjoint.tangent_gradient(rec, sp, P, TARGET, threads=THREADS)
+    assert abs(loss_h - adjoint.hist_loss(rec["xT"], rec["x0"], cfg.a)) <= 1e-4 * loss_h
+    Tm, xT = adjoint.tangent_map(rec, sp, P, threads=THREADS)
     # every component to 1e-3 of its own size
+    gref = np.einsum("ia,iak->k", adjoint.msd_loss_grad(xT, rec["x0"], sp, TARGET), Tm)
     assert np.all(np.abs(g - gref) <= 1e-3 * np.abs(gref)), (g, gref)
+    gref_h = np.einsum("ia,iak->k", adjoint.hist_loss_grad(xT, rec["x0"], cfg.a), Tm)
+    # each component to 1e-3 of its own size, or to 1e-4 of the largest for a
+    # component that nearly cancels
+    tol = np.maximum(1e-3 * np.abs(gref_h), 1e-4 * np.max(np.abs(gref_h)))
+    assert np.all(np.abs(g_h - gref_h) <= tol), (g_h, gref_h)
+
+
+def test_fp64_hist_loss_gradient_matches_oracle():
+    s, x0, th0, sp, P = _setup(500, 1, seed=27)
+    loss, stats = s.rollout(30, ckpt_every=7, loss_kind=bd.LOSS_HIST)
+    assert stats["steps_done"] == 30 and stats["corr_iters"] > 0
+    g = s.rollout_vjp()
+    rec = adjoint.record(x0, th0, sp, P, 30, threads=THREADS)
+    assert s.rollout_log_size() == _log_size(rec)
+    ref_loss = adjoint.hist_loss(rec["xT"], rec["x0"], P.a)
+    assert ref_loss > 0 and abs(loss - ref_loss) <= 1e-8 * ref_loss
+    gref, _ = adjoint.tangent_gradient(rec, sp, P, TARGET, threads=THREADS, loss="hist")
+    assert _rel(g, gref) <= 1e-5, (g, gref)
+    assert abs(s.rollout_replay() - loss) <= 1e-12 * loss
+    # the GPU's own frozen replay, differenced centrally
+    base = np.array(list(P.alpha) + [P.v0])
+    h = 1e-4
+    fd = np.zeros(5)
+    for k in range(5):
+        up, dn = base.copy(), base.copy()
+        up[k] += h
+        dn[k] -= h
+        fd[k] = (s.rollout_replay(up[:4], up[4]) - s.rollout_replay(dn[:4], dn[4])) / (2 * h)
+    assert _rel(g, fd) <= 1e-5, (g, fd)
+
+
+def test_fp32_hist_loss_gradient_matches_oracle():
+    s, x0, th0, sp, P = _setup(1024, 0, seed=28)
+    s.rollout(40, ckpt_every=20, loss_kind=bd.LOSS_HIST)
+    g = s.rollout_vjp()
+    rec = adjoint.record(x0, th0, sp, P, 40, threads=THREADS)
+    gref, _ = adjoint.tangent_gradient(rec, sp, P, TARGET, threads=THREADS, loss="hist")
+    assert _rel(g, gref) <= 1e-3, (g, gref)
 
 
 def test_rollout_forward_is_the_step():
@@ -146,6 +191,11 @@ def test_autograd_function():
     # same parameters and start: same loss
     loss2 = bd.rollout_loss(params.detach(), s, x0, th0, 0, 20, 5, TARGET)
     assert float(loss2) == float(loss.detach())
+    # the histogram loss through the same function
+    p2 = params.detach().clone().requires_grad_(True)
+    lh = bd.rollout_loss(p2, s, x0, th0, 0, 20, 5, TARGET, bd.LOSS_HIST)
+    lh.backward()
+    assert np.allclose(p2.grad.numpy(), s.rollout_vjp(), rtol=1e-10, atol=0)
 
 
 def test_rollout_argument_errors():
