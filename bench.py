@@ -303,12 +303,14 @@ def run_adjoint(args):
     from paper_1703_02484_gb300 import workloads
     torch.cuda.set_device(0)
     cfg = workloads.CONFIGS["c5"]
+    hist = args.workload.endswith("-hist")
+    kind = bd.LOSS_HIST if hist else bd.LOSS_MSD
     xy, sp, th = workloads.initial_state(cfg)
     stream = torch.cuda.current_stream()
     s = bd.System(bd.params_from_config(cfg), xy, sp, th, stream=stream.cuda_stream)
     T = cfg.steps
     for _ in range(args.warmup):
-        s.rollout(T, 20, 0.1)
+        s.rollout(T, 20, 0.1, kind)
         s.rollout_vjp()
         s.step(T)
     K = max(1, min(args.steps, 20))
@@ -318,7 +320,7 @@ def run_adjoint(args):
     with ClockSampler(0) as clk:
         for k in range(K):
             ev[k][0].record(stream)
-            s.rollout(T, 20, 0.1)
+            s.rollout(T, 20, 0.1, kind)
             launches += s.last_launch_count()
             ev[k][1].record(stream)
             g = s.rollout_vjp()
@@ -337,7 +339,8 @@ def run_adjoint(args):
             "warmup": args.warmup, "ms_per_step": (fwd + bwd) / T, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (adjoint sums f64)", "data": "synthetic",
             "config": {"workload": "c5: N=4096, rho=0.35, two species, v0=1, 200 steps, checkpoints every 20, "
-                                   "MSD loss; gradient w.r.t. (A00, A01, A10, A11, v0)",
+                                   "%s loss; gradient w.r.t. (A00, A01, A10, A11, v0)"
+                                   % ("pair-distance histogram" if hist else "MSD"),
                        "N": cfg.n, "rollout_steps": T,
                        "forward_ms": fwd, "reverse_ms": bwd, "plain_steps_ms": plain,
                        "gradient_evals_per_s": 1e3 / (fwd + bwd),
@@ -358,7 +361,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--workload", default="n1e5",
                     help="configuration name (n1e5 is the headline; c1, c2, c3, c5, c4 (batched), "
-                         "c5-grad (differentiated rollout); suffixes -verlet (overlap correction over "
+                         "c5-grad (differentiated rollout, MSD loss; c5-grad-hist: histogram loss); suffixes -verlet (overlap correction over "
                          "the Verlet lists) and -periodic (periodic box), e.g. c3-verlet, n1e5-periodic)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -368,7 +371,7 @@ def main():
     if args.workload == "c4":
         run_batched(args)
         return
-    if args.workload == "c5-grad":
+    if args.workload in ("c5-grad", "c5-grad-hist"):
         run_adjoint(args)
         return
 
