@@ -36,9 +36,11 @@
 // device control block of the triangulation kernel
 struct BdCtl {
   unsigned int bar_count;
-  unsigned int bar_gen;
   int status;
   unsigned int exit_count;         // blocks that have left the triangulation kernel
+  unsigned int pad0[29];
+  unsigned int bar_gen;            // on a 128-byte line of its own: the blocks waiting at a
+  unsigned int pad1[31];           // barrier poll it, and only it
   unsigned long long epoch;        // flip-round counter, grows across launches
   int cnt[4][8];                   // per-phase counters, rotated every barrier
   // statistics accumulated over a bd_step call

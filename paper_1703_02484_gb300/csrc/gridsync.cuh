@@ -36,8 +36,15 @@ __device__ __forceinline__ int ld_status(const int *p) {
   return *(volatile const int *)p;
 }
 
-// bounded grid barrier; returns false if the grid must stop
-static __device__ bool grid_sync(BdCtl *ctl, Bar &b) {
+// Words every thread needs after a barrier, read once per block by thread 0
+// and handed to the block through shared memory (116k threads reading one
+// global line would queue ~18k requests on one L2 slice per barrier).
+enum { BC_CNT = 0, BC_ACT = 8, BC_N = 11 };
+
+// bounded grid barrier; returns false if the grid must stop.  With bc (block
+// shared, BC_N ints): bc[BC_CNT + k] = the counters of the phase that just
+// ended, bc[BC_ACT + l] = the lengths of the triangle lists.
+static __device__ bool grid_sync(BdCtl *ctl, Bar &b, int *bc = nullptr) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -70,6 +77,11 @@ static __device__ bool grid_sync(BdCtl *ctl, Bar &b) {
         }
       }
       __threadfence();
+    }
+    if (ok && bc) {
+      const volatile int *row = ctl->cnt[b.ph & 3];
+      for (int k = 0; k < 8; ++k) bc[BC_CNT + k] = row[k];
+      for (int l = 0; l < 3; ++l) bc[BC_ACT + l] = ((const volatile int *)ctl->act_n)[l];
     }
     s_ok = ok;
   }

@@ -88,6 +88,32 @@ __device__ __forceinline__ float fdiff(float bh, float bl, float ah, float al) {
   return __fadd_rn(__fsub_rn(bh, ah), __fsub_rn(bl, al));
 }
 
+// The exact integer paths are rare (the filters decide almost every case) and
+// long; they are kept out of line, one copy each, so that a thread that needs
+// one fetches a single shared instruction stream rather than a cold inlined
+// copy at every call site (a miss in the instruction cache costs about an L2
+// round trip per line, and the slowest thread of a pass sets its length).
+__device__ __noinline__ int orient_exact(const double2 *__restrict__ pos, bdpred::Grid g, int a, int b, int c) {
+  const double2 pa = pos[a], pb = pos[b], pc = pos[c];
+  return bdpred::orient(pa.x, pa.y, pb.x, pb.y, pc.x, pc.y, g);
+}
+
+__device__ __noinline__ int incircle_exact(const double2 *__restrict__ pos, bdpred::Grid g, int a, int b, int c,
+                                           int p) {
+  const double2 pa = pos[a], pb = pos[b], pc = pos[c], pp = pos[p];
+  return bdpred::incircle(pa.x, pa.y, pb.x, pb.y, pc.x, pc.y, pp.x, pp.y, g);
+}
+
+__device__ __noinline__ int orient_lifted(long long ax, long long ay, long long bx, long long by, long long cx,
+                                          long long cy) {
+  return bdpred::orient_int(ax, ay, bx, by, cx, cy);
+}
+
+__device__ __noinline__ int incircle_lifted(long long ax, long long ay, long long bx, long long by, long long cx,
+                                            long long cy, long long px, long long py) {
+  return bdpred::incircle_int(ax, ay, bx, by, cx, cy, px, py);
+}
+
 // the filters on preloaded FP32 pairs (filt: all corners are disks, whose
 // pairs are loaded; ghost points have none)
 __device__ __forceinline__ int orient_pre(const Ctx &x, bool filt, const float4 &wa, const float4 &wb,
@@ -101,8 +127,7 @@ __device__ __forceinline__ int orient_pre(const Ctx &x, bool filt, const float4 
     if (det > bound) return 1;
     if (-det > bound) return -1;
   }
-  double2 pa = x.d.pos[a], pb = x.d.pos[b], pc = x.d.pos[c];
-  return bdpred::orient(pa.x, pa.y, pb.x, pb.y, pc.x, pc.y, x.g);
+  return orient_exact(x.d.pos, x.g, a, b, c);
 }
 
 __device__ __forceinline__ int incircle_pre(const Ctx &x, bool filt, const float4 &wa, const float4 &wb,
@@ -126,8 +151,7 @@ __device__ __forceinline__ int incircle_pre(const Ctx &x, bool filt, const float
     if (det > bound) return 1;
     if (-det > bound) return -1;
   }
-  double2 pa = x.d.pos[a], pb = x.d.pos[b], pc = x.d.pos[c], pp = x.d.pos[p];
-  return bdpred::incircle(pa.x, pa.y, pb.x, pb.y, pc.x, pc.y, pp.x, pp.y, x.g);
+  return incircle_exact(x.d.pos, x.g, a, b, c, p);
 }
 
 __device__ __forceinline__ float4 work_of(const Ctx &x, int v) {
@@ -147,14 +171,20 @@ __device__ __forceinline__ int incircle_v(const Ctx &x, int a, int b, int c, int
 // Sec. 4.3 reversal test r0 . r1 < 0 of the edge u -> w, exact on the grid:
 // r1 from the present positions, r0 from those before the move (ox, oy: the
 // edge's image shift before the move, in units of LQ)
+__device__ __noinline__ bool reversed_grid(const double2 *__restrict__ prev, const double2 *__restrict__ pos,
+                                           bdpred::Grid g, int u, int w, int ox, int oy, int rsx, int rsy,
+                                           long long LQ) {
+  const double2 a0 = prev[u], b0 = prev[w], a1 = pos[u], b1 = pos[w];
+  const int64_t ux = bdpred::to_int(b0.x, g) - bdpred::to_int(a0.x, g) + ox * LQ;
+  const int64_t uy = bdpred::to_int(b0.y, g) - bdpred::to_int(a0.y, g) + oy * LQ;
+  const int64_t vx = bdpred::to_int(b1.x, g) - bdpred::to_int(a1.x, g) + rsx * LQ;
+  const int64_t vy = bdpred::to_int(b1.y, g) - bdpred::to_int(a1.y, g) + rsy * LQ;
+  return bdpred::sign128(bdpred::add128(bdpred::smul64(ux, vx), bdpred::smul64(uy, vy))) < 0;
+}
+
 __device__ __forceinline__ bool reversed_exact(const Ctx &x, int u, int w, int ox, int oy, int rsx, int rsy,
                                                long long LQ) {
-  const double2 a0 = x.d.prev[u], b0 = x.d.prev[w], a1 = x.d.pos[u], b1 = x.d.pos[w];
-  const int64_t ux = bdpred::to_int(b0.x, x.g) - bdpred::to_int(a0.x, x.g) + ox * LQ;
-  const int64_t uy = bdpred::to_int(b0.y, x.g) - bdpred::to_int(a0.y, x.g) + oy * LQ;
-  const int64_t vx = bdpred::to_int(b1.x, x.g) - bdpred::to_int(a1.x, x.g) + rsx * LQ;
-  const int64_t vy = bdpred::to_int(b1.y, x.g) - bdpred::to_int(a1.y, x.g) + rsy * LQ;
-  return bdpred::sign128(bdpred::add128(bdpred::smul64(ux, vx), bdpred::smul64(uy, vy))) < 0;
+  return reversed_grid(x.d.prev, x.d.pos, x.g, u, w, ox, oy, rsx, rsy, LQ);
 }
 
 // ---- periodic box: image shifts of triangle corners (Sec. 2.1, 4.1) ----
@@ -195,7 +225,7 @@ __device__ __forceinline__ int orient_s(const Ctx &x, int a, int sax, int say, i
   if ((sax | say | sbx | sby | scx | scy) == 0) return orient_v(x, a, b, c);
   const long long LQ = rep_LQ(x, a);
   const Lift A = lift(x, a, sax, say, LQ), B = lift(x, b, sbx, sby, LQ), C = lift(x, c, scx, scy, LQ);
-  return bdpred::orient_int(A.x, A.y, B.x, B.y, C.x, C.y);
+  return orient_lifted(A.x, A.y, B.x, B.y, C.x, C.y);
 }
 
 // in-circle test of p (shift sp) against triangle t's corners (shifts in w)
@@ -206,7 +236,7 @@ __device__ __forceinline__ int incircle_s(const Ctx &x, const int4 &v, int p, in
   const long long LQ = rep_LQ(x, v.x);
   const Lift A = lift(x, v.x, shx(w, 0), shy(w, 0), LQ), B = lift(x, v.y, shx(w, 1), shy(w, 1), LQ);
   const Lift C = lift(x, v.z, shx(w, 2), shy(w, 2), LQ), P = lift(x, p, spx, spy, LQ);
-  return bdpred::incircle_int(A.x, A.y, B.x, B.y, C.x, C.y, P.x, P.y);
+  return incircle_lifted(A.x, A.y, B.x, B.y, C.x, C.y, P.x, P.y);
 }
 
 // shift, in the frame of triangle t (corner tab w), of the vertex opposite
@@ -386,6 +416,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
   Bar b;
   b.gen = 0;
   b.ph = 0;
+  __shared__ int bc[BC_N];                // phase counters and list lengths, per barrier
   unsigned long long t_mark = gtimer();   // stage timing (lead thread)
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
@@ -456,12 +487,12 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         for (int k = 0; k < 3; ++k) nw |= put_shift(k, sx[k] - sx[0], sy[k] - sy[0]);
         d.tv[t].w = nw;
       }
-      if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+      if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
       if (lead) ctl->n_wrapped = 0;
       first = false;
     }
     // ---------------- P: check, mark, scan ----------------
-    const int dom_n = full ? x.T : *(volatile int *)&ctl->act_n[slot];
+    const int dom_n = full ? x.T : bc[BC_ACT + slot];
     if (lead) tri_visits += dom_n;
     phase_begin(ctl, b);
     {
@@ -691,16 +722,16 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       (void)nov;
       if (mx > 0.0) atomicMax(&ctl->st_max_overlap_bits, (unsigned long long)__double_as_longlong(mx));
     }
-    if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+    if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
     if (lead) {
       stage_tick(ctl, full ? STAGE_P : STAGE_PL, t_mark);
       ctl->act_n[(kp + 2) % 3] = 0;   // filled by the next pass
     }
     first = false;
-    const int n_inv = *(volatile int *)cnt(ctl, b.ph - 1, C_INV);
-    const int n_rej = *(volatile int *)cnt(ctl, b.ph - 1, C_REJECT);
-    const int n_cand = *(volatile int *)cnt(ctl, b.ph - 1, C_CAND);
-    const int n_ov = *(volatile int *)cnt(ctl, b.ph - 1, C_OVERLAP);
+    const int n_inv = bc[BC_CNT + C_INV];
+    const int n_rej = bc[BC_CNT + C_REJECT];
+    const int n_cand = bc[BC_CNT + C_CAND];
+    const int n_ov = bc[BC_CNT + C_OVERLAP];
     if (n_rej) {
       status = BD_ERR_STEP_REJECTED;
       if (lead) { ctl->st_fail_phase = 1; ctl->st_fail_count = n_rej; }
@@ -755,11 +786,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           block_add(cnt(ctl, b.ph, C_INV), inv);
           block_add(cnt(ctl, b.ph, C_CAND), ncand);
         }
-        if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+        if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
         if (lead) stage_tick(ctl, STAGE_R, t_mark);
         first_round = false;
-        const int ni = *(volatile int *)cnt(ctl, b.ph - 1, C_INV);
-        const int nc = *(volatile int *)cnt(ctl, b.ph - 1, C_CAND);
+        const int ni = bc[BC_CNT + C_INV];
+        const int nc = bc[BC_CNT + C_CAND];
         if (ni == 0) break;
         if (nc == 0 || rounds++ >= c.max_flip_rounds) {
           status = BD_ERR_STEP_REJECTED;
@@ -782,9 +813,9 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           }
           block_add(cnt(ctl, b.ph, C_FLIPS), nf);
         }
-        if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+        if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
         if (lead) stage_tick(ctl, STAGE_R, t_mark);
-        st_rflips += *(volatile int *)cnt(ctl, b.ph - 1, C_FLIPS);
+        st_rflips += bc[BC_CNT + C_FLIPS];
       }
       if (status) break;
       fresh = false;
@@ -838,9 +869,9 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         }
         block_add(cnt(ctl, b.ph, C_FLIPS), nf);
       }
-      if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+      if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
       if (lead) stage_tick(ctl, STAGE_F, t_mark);
-      st_flips += *(volatile int *)cnt(ctl, b.ph - 1, C_FLIPS);
+      st_flips += bc[BC_CNT + C_FLIPS];
       st_rounds += 1;
       fresh = false;
       full = !use_lists;
@@ -945,7 +976,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         if (tw & BD_TRI_FLAGS) d.tv[t].w = tw & ~BD_TRI_FLAGS;
       }
     }
-    if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+    if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
     if (lead) stage_tick(ctl, STAGE_A, t_mark);
     fresh = true;
     full = !use_lists;

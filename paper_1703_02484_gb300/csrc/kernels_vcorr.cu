@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
   Bar b;
   b.gen = 0;
   b.ph = 0;
+  __shared__ int bc[BC_N];   // phase counters, per barrier
   unsigned long long t_mark = gtimer();
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
@@ -134,10 +135,10 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
       block_add(cnt(ctl, b.ph, C_REJECT), stale);
       if (mx > 0.0) atomicMax(&ctl->st_max_overlap_bits, (unsigned long long)__double_as_longlong(mx));
     }
-    if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+    if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
     if (lead) stage_tick(ctl, 0, t_mark);
-    const int n_rej = *(volatile int *)cnt(ctl, b.ph - 1, C_REJECT);
-    const int n_ov = *(volatile int *)cnt(ctl, b.ph - 1, C_OVERLAP);
+    const int n_rej = bc[BC_CNT + C_REJECT];
+    const int n_ov = bc[BC_CNT + C_OVERLAP];
     if (n_rej) {
       status = BD_ERR_STEP_REJECTED;
       if (lead) { ctl->st_fail_phase = 6; ctl->st_fail_count = n_rej; }
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
         d.moved[i] = 1;
       }
     }
-    if (!grid_sync(ctl, b)) { block_exit(ctl); return; }
+    if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
     if (lead) stage_tick(ctl, 3, t_mark);
   }
 
