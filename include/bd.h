@@ -249,7 +249,8 @@ int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32
  * flips, Sec. 4.3), so moves should be small compared with the disk spacing.
  * No two disks may be closer than sigma: the device scans the repaired
  * Delaunay triangulation's edges, which hold the closest pair (Verlet-list
- * handles check on the host).  The arrays are copied to the device as they
+ * handles scan their neighbour lists, rebuilt first when a disk moved more
+ * than skin/2 from where they were built).  The arrays are copied to the device as they
  * are (page-locked arrays make it a direct transfer); the range checks (finite;
  * with walls a centre in [a, L-a] up to 1e-9 L), the rounding to the position
  * grid and the permutation to the internal order run there.  The call

@@ -264,14 +264,29 @@ __global__ void k_vjp_grad_sum(BdDev d, int nblocks, const double *gpart, double
 // ---------------------------------------------------------------- loss
 
 // per-species sums of |x_T - x_0|^2 and counts (acc[0..1] sums, acc[2..3] counts)
-__global__ void k_msd_sums(BdDev d, BdConst c, const double2 *x0, double *acc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= c.np || d.ext_id[i] < 0) return;
-  const double2 p = d.pos[i], q = x0[i];
-  const double dx = p.x - q.x, dy = p.y - q.y;
-  const int s = d.species[i] ? 1 : 0;
-  atomicAdd(&acc[s], dx * dx + dy * dy);
-  atomicAdd(&acc[2 + s], 1.0);
+// per-species sums of |x_T - x_0|^2 and counts, in a fixed order (one block:
+// thread t takes disks t, t + 1024, ...; then a fixed tree), so that the loss
+// is the same number on every run
+__global__ void __launch_bounds__(1024) k_msd_sums(BdDev d, BdConst c, const double2 *x0, double *acc) {
+  __shared__ double sh[4][1024];
+  const int t = threadIdx.x;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = t; i < c.np; i += 1024) {
+    if (d.ext_id[i] < 0) continue;
+    const double2 p = d.pos[i], q = x0[i];
+    const double dx = p.x - q.x, dy = p.y - q.y;
+    const int s = d.species[i] ? 1 : 0;
+    v[s] += dx * dx + dy * dy;
+    v[2 + s] += 1.0;
+  }
+  for (int k = 0; k < 4; ++k) sh[k][t] = v[k];
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if (t < w)
+      for (int k = 0; k < 4; ++k) sh[k][t] += sh[k][t + w];
+    __syncthreads();
+  }
+  if (t < 4) acc[t] = sh[t][0];
 }
 
 // loss = sum_s (MSD_s - target)^2 and its gradient lambda_i = dscale dL/dx_i
@@ -480,9 +495,7 @@ cudaError_t bd_adj_vjp_em(const BdDev &d, const BdConst &c, int k_local, const d
 
 cudaError_t bd_adj_msd(const BdDev &d, const BdConst &c, const double2 *x0, double *acc, double target,
                        double dscale, double2 *lam, double *loss, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(acc, 0, 4 * sizeof(double), s);
-  if (e != cudaSuccess) return e;
-  k_msd_sums<<<(c.np + 255) / 256, 256, 0, s>>>(d, c, x0, acc);
+  k_msd_sums<<<1, 1024, 0, s>>>(d, c, x0, acc);
   k_msd_loss_grad<<<(c.np + 255) / 256, 256, 0, s>>>(d, c, x0, acc, target, dscale, lam, loss);
   return cudaGetLastError();
 }

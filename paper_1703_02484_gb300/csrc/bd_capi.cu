@@ -1459,31 +1459,14 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
   if (!h || !xy) return BD_ERR_ARG;
   const int np = h->np;
   const BdConst &c = h->c;
-  if (c.overlap_verlet) {
-    // Verlet-list handles keep no triangulation: the range checks and the
-    // search for pairs closer than sigma run on the host
-    std::vector<double> wrapped;
-    for (const RepHost &RH : h->reps) {
-      const double *x = xy + 2 * (size_t)RH.ext_base;
-      for (int i = 0; i < 2 * RH.n; ++i)
-        if (!isfinite(x[i]) ||
-            (!RH.periodic && (x[i] < c.a - 1e-9 * RH.L || x[i] > RH.L - c.a + 1e-9 * RH.L)))
-          return BD_ERR_INIT_OVERLAP;
-      if (RH.periodic) {
-        wrapped.resize(2 * (size_t)RH.n);
-        for (int i = 0; i < 2 * RH.n; ++i) wrapped[i] = periodic_coord(x[i], RH.L, c.q, c.inv_q);
-        if (bdhost::any_overlap_periodic(RH.n, wrapped.data(), RH.L, c.sigma * (1.0 - 1e-12)))
-          return BD_ERR_INIT_OVERLAP;
-      } else if (bdhost::any_overlap(RH.n, x, 0.0, RH.L, c.sigma * (1.0 - 1e-12))) {
-        return BD_ERR_INIT_OVERLAP;
-      }
-    }
-  }
   // The caller's arrays are copied as they are; the range checks, the
   // rounding to the grid and the permutation to slot order run on the device
-  // (k_state_check, k_state_in), and pairs closer than sigma are found by the
+  // (k_state_check, k_state_in).  Pairs closer than sigma are found by the
   // repaired Delaunay triangulation's overlap scan (its edges hold the closest
-  // pair).  Any failure leaves the previous state in place.
+  // pair), or with Verlet lists by a scan of the lists, rebuilt first if a
+  // disk moved more than skin/2 from where they were built (they then hold
+  // every pair within r_cut >= sigma).  Any failure leaves the previous state
+  // in place.
   cudaStream_t st = h->stream;
   const BdDev &d = h->d;
   cudaError_t e = reset_stats(h);
@@ -1498,6 +1481,10 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
   if (e == cudaSuccess && c.any_periodic) e = bd_launch_periodic_wraps(d, c, st);
   if (e == cudaSuccess) e = bd_launch_work_copy(d, c, st);
   if (e == cudaSuccess && !c.overlap_verlet) e = bd_launch_dt(d, c, 1, st, h->dt_grid, h->dt_block);
+  if (e == cudaSuccess && c.overlap_verlet) {
+    e = bd_launch_force_short(d, c, st);
+    if (e == cudaSuccess) e = bd_launch_overlap_verlet(d, c, st, h->vc_grid, h->vc_block, -1);
+  }
   if (e != cudaSuccess) return cuda_fail(e);
   int rc = read_ctl(h);   // synchronises the stream
   if (rc) return rc;

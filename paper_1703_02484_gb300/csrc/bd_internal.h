@@ -206,7 +206,9 @@ cudaError_t bd_launch_force_short(const BdDev &d, const BdConst &c, cudaStream_t
 int bd_short_launches();
 cudaError_t bd_launch_force_sum(const BdDev &d, const BdConst &c, double2 *out, cudaStream_t s);
 cudaError_t bd_launch_force_sym(const BdDev &d, const BdConst &c, int variant, cudaStream_t s);
-// advance = 0: a piece of a halved step (the step counter does not advance)
+// advance = 0: a piece of a halved step (the step counter does not advance);
+// advance = -1: positions set from outside, a pair closer than sigma rejects them
+// (BD_ERR_INIT_OVERLAP, restored from pos0) and nothing is corrected
 cudaError_t bd_launch_overlap_verlet(const BdDev &d, const BdConst &c, cudaStream_t s, int grid, int block,
                                      int advance = 1);
 // a halved step completed: advance the device step counter and the step count

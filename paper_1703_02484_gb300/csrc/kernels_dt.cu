@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
             // Sec. 4.3 first criterion r0 . r1 < 0; r0 = r1 - (move of w - move
             // of u), screened in FP32, exact on the grid near zero
             bool rev;
-            if (mode != 1) {
+            {
               const float2 mu = mvd[ku] ? d.dmove[u] : make_float2(0.f, 0.f);
               const float2 mw = mvd[kw] ? d.dmove[w] : make_float2(0.f, 0.f);
               const float r0x = __fsub_rn(r1x, __fsub_rn(mw.x, mu.x)), r0y = __fsub_rn(r1y, __fsub_rn(mw.y, mu.y));
@@ -663,8 +663,6 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
                                                   __fadd_rn(__fmul_rn(mw.x, mw.x), __fmul_rn(mw.y, mw.y))));
               const float bound = 4e-6f * S;
               rev = dot > bound ? false : (-dot > bound ? true : reversed_exact(x, u, w, 0, 0, 0, 0, 0));
-            } else {
-              rev = reversed_exact(x, u, w, 0, 0, 0, 0, 0);
             }
             if (rev) {
               ++rej;

@@ -12,6 +12,8 @@
 #include <stdint.h>
 
 #include "bd_internal.h"
+#include "em.cuh"
+#include "predicates.cuh"
 
 namespace {
 
@@ -60,6 +62,14 @@ __global__ void k_state_in(BdDev d, BdConst c, int with_theta) {
   } else {
     y = make_double2(fmin(R.wall_hi, fmax(R.wall_lo, snap_grid(p.x, c))),
                      fmin(R.wall_hi, fmax(R.wall_lo, snap_grid(p.y, c))));
+  }
+  if (!R.periodic) {
+    // the move from the previous positions, for the triangulation's FP32
+    // reversal screen (exact grid difference, one rounding to FP32)
+    const double2 o = d.pos[i];
+    const bdpred::Grid g{c.q, c.inv_q, c.qshift};
+    d.dmove[i] = make_float2(bdem::grid_to_float(bdpred::to_int(y.x, g) - bdpred::to_int(o.x, g), c.qshift),
+                             bdem::grid_to_float(bdpred::to_int(y.y, g) - bdpred::to_int(o.y, g), c.qshift));
   }
   d.pos[i] = y;
   if (with_theta) d.theta[i] = d.xfer_th[e];

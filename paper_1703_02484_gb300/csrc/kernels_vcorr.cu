@@ -144,6 +144,14 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
       if (lead) { ctl->st_fail_phase = 6; ctl->st_fail_count = n_rej; }
       break;
     }
+    if (advance < 0) {
+      // positions set from outside: any pair closer than sigma rejects them
+      if (n_ov) {
+        status = BD_ERR_INIT_OVERLAP;
+        if (lead) { ctl->st_fail_phase = 7; ctl->st_fail_count = n_ov; }
+      }
+      break;
+    }
     if (n_ov == 0) break;
     if (corr_iter >= c.max_corr_iters) {
       status = BD_ERR_OVERLAP_NOT_CONVERGED;
@@ -207,10 +215,10 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
     ctl->st_overlap_pairs += st_overlap;
     ctl->st_barriers += b.gen;
     if (corr_iter > ctl->st_max_corr_iters) ctl->st_max_corr_iters = corr_iter;
-    if (!status && advance) {
+    if (!status && advance > 0) {
       ctl->st_steps += 1;
       ctl->step_dev += 1;
-    } else if (!status) {
+    } else if (!status && advance == 0) {
       ctl->st_substeps += 1;
     }
   }

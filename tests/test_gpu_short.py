@@ -171,3 +171,50 @@ def test_verlet_mode_requires_short_range():
     with pytest.raises(bd.BDError) as e:
         bd.System(p, xy, sp, th, stream=stream())
     assert e.value.code == -10
+
+
+@pytest.mark.parametrize("far", [False, True])
+def test_verlet_set_state_checks_overlaps_on_the_device(far):
+    # bd_set_state on a Verlet-list handle: the lists (rebuilt when a disk moved
+    # more than skin/2 from where they were built) are scanned for pairs closer
+    # than sigma; a good state is taken, an overlapping one rejected with the
+    # previous state kept
+    n = 4000
+    s, L, xy, sp, th = verlet_system(n)
+    s.step(3)
+    before = s.state(want_tri=False)
+    good = before["xy"].copy()
+    if far:
+        # one disk moved by more than skin/2 (0.3): the lists must be rebuilt
+        dist, _ = cKDTree(good).query(good, k=2)
+        for k in np.argsort(-dist[:, 1])[:20]:
+            for step in ((0.45, 0.0), (-0.45, 0.0), (0.0, 0.45), (0.0, -0.45)):
+                trial = good.copy()
+                trial[k] += step
+                if np.all(trial[k] >= 1.0) and np.all(trial[k] <= L - 1.0) and \
+                        len(cKDTree(trial).query_pairs(2.0)) == 0:
+                    good = trial
+                    break
+            else:
+                continue
+            break
+        assert not np.array_equal(good, before["xy"])
+    s.set_state(good)
+    q, _ = s.geometry()
+    got = s.state(want_tri=False)["xy"]
+    assert np.max(np.abs(got - good)) <= q      # rounded to the position grid
+    good = got
+    dist, nb = cKDTree(good).query(good, k=2)
+    i = int(np.argmin(dist[:, 1]))
+    j = int(nb[i, 1])
+    bad = good.copy()
+    bad[j] = good[i] + 1.9 * (good[j] - good[i]) / np.linalg.norm(good[j] - good[i])
+    with pytest.raises(bd.BDError) as e:
+        s.set_state(bad)
+    assert e.value.code == -3
+    assert np.array_equal(s.state(want_tri=False)["xy"], good)
+    st = s.step(5)
+    assert st["steps_done"] == 5
+    out = s.state(want_tri=False)
+    assert len(cKDTree(out["xy"]).query_pairs(2.0 * (1 - 1e-12))) == 0
+    s.close()
