@@ -300,3 +300,39 @@ def test_set_state_rejects_overlapping_positions(boundary):
     assert np.array_equal(after["xy"], before["xy"]) and np.array_equal(after["tri"], before["tri"])
     s.step(3)                       # still usable
     s.close()
+
+
+@pytest.mark.parametrize("eps", [1e-3, 2e-9])
+@pytest.mark.parametrize("turn", [-1, 1])
+def test_reversal_test_near_perpendicular_moves(eps, turn):
+    # Sec. 4.3's criterion r0 . r1 < 0 on one edge, through bd_set_state (its
+    # repair pass tests every edge of the move): w turned about u by 90 deg
+    # - turn * eps gives r0 . r1 = |r|^2 sin(turn * eps).  At eps = 1e-3 the
+    # FP32 screen decides; at 2e-9 the product lies inside its bound and the
+    # exact grid test decides.  Either way the outcome follows the exact sign.
+    # Small disks (a = 0.01, |r| = 0.03): the turn moves w by 0.04, far less
+    # than its distance to any other point, so no triangle inverts.
+    L, r = 60.0, 0.03
+    xy = np.array([[30.0, 30.0], [30.0 + r, 30.0], [12.0, 45.0], [48.0, 14.0]])
+    p = bd.make_params(n=4, L=L, a=0.01, D=0.0, dt=1e-4, seed=3)
+    s = bd.System(p, xy, np.zeros(4, np.uint8), np.zeros(4, np.float32), stream=stream())
+    q, _ = s.geometry()
+    before = s.state()
+    u, w = before["xy"][0], before["xy"][1]
+    th = np.pi / 2 - turn * eps
+    new = before["xy"].copy()
+    new[1] = u + r * np.array([np.cos(th), np.sin(th)])
+    gi = lambda v: [int(round(c / q)) for c in v]     # noqa: E731  (grid integers)
+    U0, W0, W1 = gi(u), gi(w), gi(np.rint(new[1] / q) * q)
+    dot = (W0[0] - U0[0]) * (W1[0] - U0[0]) + (W0[1] - U0[1]) * (W1[1] - U0[1])
+    assert dot != 0 and (dot > 0) == (turn > 0)
+    if dot > 0:
+        s.set_state(new)
+        assert np.max(np.abs(s.state()["xy"][1] - new[1])) <= q
+    else:
+        with pytest.raises(bd.BDError) as e:
+            s.set_state(new)
+        assert e.value.code == -4
+        after = s.state()
+        assert np.array_equal(after["xy"], before["xy"]) and np.array_equal(after["tri"], before["tri"])
+    s.close()
