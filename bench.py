@@ -111,6 +111,30 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device):
+    """The largest x over the ranks (the job's time is its slowest rank's);
+    the only collective of the replicas path, outside the timed region."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_params(bd, cfg, rank, modes=()):
+    """Rank r advances its own replica of the workload: the same start and
+    parameters, its own Philox stream (key word 1 = seed_hi xor r)."""
+    p = bd.params_from_config(cfg)
+    if "verlet" in modes:
+        p.overlap_mode = bd.OVERLAP_VERLET   # Algorithm 2 over the Verlet lists, no triangulation
+    if "periodic" in modes:
+        p.boundary = bd.BOUNDARY_PERIODIC    # the paper's periodic box (minimum image, torus triangulation)
+    p.replica = rank
+    return p
+
+
 def run_reference(args):
     """The oracle (plain FP64 CPU restatement) on the same workload, host cores.
 
@@ -389,12 +413,7 @@ def main():
     periodic_mode = "periodic" in modes
     cfg = workloads.CONFIGS[base]
     xy, sp, th = workloads.initial_state(cfg)
-    p = bd.params_from_config(cfg)
-    if verlet_mode:
-        p.overlap_mode = bd.OVERLAP_VERLET   # Algorithm 2 over the Verlet lists, no triangulation
-    if periodic_mode:
-        p.boundary = bd.BOUNDARY_PERIODIC    # the paper's periodic box (minimum image, torus triangulation)
-    p.replica = rank
+    p = rank_params(bd, cfg, rank, modes)
     stream = torch.cuda.current_stream()
     system = bd.System(p, xy, sp, th, stream=stream.cuda_stream)
     N = cfg.n
@@ -430,10 +449,7 @@ def main():
     force_ms, force_n = system.force_timing(False)
     stage_raw = system.stage_times(reset=True)
     stage_ms = {k: v[0] / args.steps for k, v in stage_raw.items()}
-    if ws > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(t_ms, ws, "cuda")
     ms_per_step = t_ms / args.steps
     value = ws * N * args.steps / (t_ms / 1e3)
 
@@ -493,10 +509,7 @@ def main():
             system.read_state(hxy, hth)         # device -> host
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        if ws > 1:
-            tt = torch.tensor([te], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(te, ws, "cuda")
         e2e = {"value": ws * N * args.e2e_steps / te, "unit": UNIT,
                "h2d_bytes_per_step": N * (16 + 4), "d2h_bytes_per_step": N * (16 + 4)}
 
