@@ -35,9 +35,11 @@ FP32_INST_PER_PAIR = 8   # the same work counted as FP32-pipe instructions (plus
 # sides) = 16 flops in 10 FP32 lane operations (+1 MUFU), i.e. per ordered pair:
 FLOPS_PER_PAIR_SYM = 8
 LANES_PER_PAIR_SYM = 5
-# periodic sweep: per ordered pair 2 hi + 2 lo differences and 2 adds (exact
-# near-pair vectors), 2 FFMA (r^2), 2 FMUL, 2 FFMA (accumulate) = 12 lane
-# operations (16 flops), plus the minimum-image tests (not counted)
+# one-sided periodic sweep: per ordered pair 2 hi + 2 lo differences and 2 adds
+# (exact near-pair vectors), 2 FFMA (r^2), 2 FMUL, 2 FFMA (accumulate) = 12 lane
+# operations (16 flops), plus the minimum-image tests (not counted).  The
+# symmetric sweep's periodic form counts as the symmetric sweep (its per-pair
+# minimum images, in the tiles near the antipode, are not counted)
 FLOPS_PER_PAIR_PER = 16
 LANES_PER_PAIR_PER = 12
 
@@ -467,7 +469,7 @@ def main():
     # algorithmic FP32 work of the chosen sweep, per ordered pair interaction
     flops_pp, lanes_pp = (FLOPS_PER_PAIR_SYM, LANES_PER_PAIR_SYM) if variant >= 2 else \
         (FLOPS_PER_PAIR, FP32_INST_PER_PAIR)
-    if periodic_mode:
+    if periodic_mode and variant < 2:
         flops_pp, lanes_pp = FLOPS_PER_PAIR_PER, LANES_PER_PAIR_PER
     achieved = flops_pp * pairs / avg_force_s / 1e12
     pipe_frac = lanes_pp * pairs / avg_force_s / (sms * 128 * f_hz)
@@ -475,7 +477,7 @@ def main():
               2: "k_force_long_sym<4,2> + k_force_sym_reduce",
               3: "k_force_long_sym<2,4> + k_force_sym_reduce"}[variant]
     if periodic_mode:
-        kernel = "k_force_long_per"
+        kernel = "k_force_long_per" if variant < 2 else kernel.replace("> +", ", periodic> +")
     traffic = None
     # ncu DRAM bytes of one launch, used only while the kernel source is the
     # one the counters were taken on

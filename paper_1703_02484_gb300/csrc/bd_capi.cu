@@ -313,7 +313,8 @@ cudaError_t use_variant(bd_handle *h, int variant, int tiles) {
 cudaError_t autotune(bd_handle *h) {
   std::vector<int2> cand;
   if (h->c.any_periodic) {
-    // periodic boxes: the scalar one-sided sweep (minimum images), chunk sizes only
+    // periodic boxes: the scalar one-sided sweep and the symmetric sweep, both
+    // with minimum images
     for (int t : {2, 4, 8, 16, 32, 64}) cand.push_back(make_int2(0, t));
     if (h->reps.size() == 1) cand.push_back(make_int2(0, single_system_tiles(h)));
   } else if (h->reps.size() == 1) {
@@ -322,9 +323,8 @@ cudaError_t autotune(bd_handle *h) {
     for (int t : {2, 4, 8, 16, 32, 64}) cand.push_back(make_int2(0, t));
     for (int t : {2, 4, 8, 16, 32, 64}) cand.push_back(make_int2(1, t));
   }
-  if (!h->c.any_periodic)
-    for (int v : {2, 3})
-      for (int t : {2, 4, 8, 16, 32}) cand.push_back(make_int2(v, t));
+  for (int v : {2, 3})
+    for (int t : {2, 4, 8, 16, 32}) cand.push_back(make_int2(v, t));
   float best_ms = 1e30f;
   int2 best = cand[0];
   cudaEvent_t a, b;
@@ -842,7 +842,27 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
           sy += h->host_pos[2 * (size_t)i + 1];
           ++m;
         }
-        if (m) so[P] = make_float2((float)nearbyint(sx / m), (float)nearbyint(sy / m));
+        if (m && h->reps[sb[P].x].periodic) {
+          // periodic box: the mean of the block's minimum images about its
+          // first disk (the symmetric sweep re-centres on it with minimum images)
+          const double L = h->reps[sb[P].x].L;
+          double x0 = 0.0, y0 = 0.0, mx = 0.0, my = 0.0;
+          bool have = false;
+          for (int i = P * BD_SB; i < (P + 1) * BD_SB; ++i) {
+            if (slot_rep[i] < 0) continue;
+            const double x = h->host_pos[2 * (size_t)i], y = h->host_pos[2 * (size_t)i + 1];
+            if (!have) {
+              x0 = x;
+              y0 = y;
+              have = true;
+            }
+            mx += (x - x0) - L * nearbyint((x - x0) / L);
+            my += (y - y0) - L * nearbyint((y - y0) / L);
+          }
+          so[P] = make_float2((float)nearbyint(x0 + mx / m), (float)nearbyint(y0 + my / m));
+        } else if (m) {
+          so[P] = make_float2((float)nearbyint(sx / m), (float)nearbyint(sy / m));
+        }
       }
       BD_TRY(dalloc(h, &d.sblock, sb.size()));
       BD_TRY(dalloc(h, &d.sorigin, so.size()));
@@ -906,12 +926,13 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
       if (c.precision == 1 || !c.any_long) {
         BD_TRY(use_variant(h, c.precision == 1 ? 1 : c.force_variant, R == 1 ? single_system_tiles(h) : 16));
       } else if (fv) {
-        const int v = c.any_periodic ? 0 : std::min(3, std::max(0, atoi(fv)));
+        int v = std::min(3, std::max(0, atoi(fv)));
+        if (c.any_periodic && v == 1) v = 0;   // the packed one-sided sweep has no periodic form
         const int t = ft && atoi(ft) > 0 ? atoi(ft) : (v >= 2 ? 8 : (R == 1 ? single_system_tiles(h) : 16));
         BD_TRY(use_variant(h, v, t));
       } else if (nmax * nmax > 180000000000LL) {
         // a launch takes more than ~50 ms: no timing at init
-        BD_TRY(use_variant(h, c.any_periodic ? 0 : 2, c.any_periodic ? 64 : 16));
+        BD_TRY(use_variant(h, 2, 16));
       } else {
         BD_TRY(autotune(h));
       }

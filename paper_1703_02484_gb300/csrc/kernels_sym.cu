@@ -32,8 +32,12 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "bd_internal.h"
+#include "em.cuh"
 #include "f32x2.cuh"
+#include "predicates.cuh"
 
 using namespace bdf;
 
@@ -41,6 +45,61 @@ namespace {
 
 __device__ __forceinline__ float2 recentre(float4 w, float2 org) {
   return make_float2(__fadd_rn(__fsub_rn(w.x, org.x), w.z), __fadd_rn(__fsub_rn(w.y, org.y), w.w));
+}
+
+// periodic box: disk j about the block origin (ox, oy) as its minimum image,
+// formed exactly in grid units and kept as an FP32 (hi, lo) pair (LQ = 0:
+// walls, no wrap); inert slots far away
+__device__ __forceinline__ float4 rel_grid(const BdDev &d, const BdConst &c, int j, long long ox, long long oy,
+                                           long long LQ) {
+  if (d.ext_id[j] < 0) return make_float4(1.0e18f, 1.0e18f, 0.f, 0.f);
+  const bdpred::Grid g{c.q, c.inv_q, c.qshift};
+  const double2 p = d.pos[j];
+  long long X = bdpred::to_int(p.x, g) - ox, Y = bdpred::to_int(p.y, g) - oy;
+  if (LQ > 0) {
+    const long long h = LQ / 2;
+    X = X > h ? X - LQ : (X < -h ? X + LQ : X);
+    Y = Y > h ? Y - LQ : (Y < -h ? Y + LQ : Y);
+  }
+  const float2 sx = bdem::grid_split(X, c.qshift), sy = bdem::grid_split(Y, c.qshift);
+  return make_float4(sx.x, sy.x, sx.y, sy.y);
+}
+
+// bounding box (x_min, x_max, y_min, y_max), inert slots (1e18) left out
+__device__ __forceinline__ void sbox_add(float4 &bx, float x, float y) {
+  if (x > 1.0e17f) return;
+  bx.x = fminf(bx.x, x);
+  bx.y = fmaxf(bx.y, x);
+  bx.z = fminf(bx.z, y);
+  bx.w = fmaxf(bx.w, y);
+}
+__device__ __forceinline__ float4 swarp_box(float4 bx) {
+  for (int o = 16; o > 0; o >>= 1) {
+    bx.x = fminf(bx.x, __shfl_xor_sync(0xffffffffu, bx.x, o));
+    bx.y = fmaxf(bx.y, __shfl_xor_sync(0xffffffffu, bx.y, o));
+    bx.z = fminf(bx.z, __shfl_xor_sync(0xffffffffu, bx.z, o));
+    bx.w = fmaxf(bx.w, __shfl_xor_sync(0xffffffffu, bx.w, o));
+  }
+  return bx;
+}
+__device__ __forceinline__ float4 sempty_box() { return make_float4(3e38f, -3e38f, 3e38f, -3e38f); }
+__device__ __forceinline__ float4 smerge_box(float4 a, float4 b) {
+  return make_float4(fminf(a.x, b.x), fmaxf(a.y, b.y), fminf(a.z, b.z), fmaxf(a.w, b.w));
+}
+
+// minimum image of a packed pair of coordinate differences in (-3L/2, 3L/2):
+// t = rint(dx / L) by the 1.5 2^23 rounding constant, dx - t L exact (Sterbenz)
+__device__ __forceinline__ u64 min_image2(u64 dx, u64 invL2, u64 nL2, u64 M2) {
+  const u64 t = sub2(fma2(dx, invL2, M2), M2);
+  return fma2(t, nL2, dx);
+}
+// the same by compares, which leaves the far-away inert slots far away
+__device__ __forceinline__ u64 min_image2_cmp(u64 dx, float Lf, float hLf) {
+  float a, b;
+  up2(dx, a, b);
+  a = a > hLf ? __fsub_rn(a, Lf) : (a < -hLf ? __fadd_rn(a, Lf) : a);
+  b = b > hLf ? __fsub_rn(b, Lf) : (b < -hLf ? __fadd_rn(b, Lf) : b);
+  return pk2(a, b);
 }
 
 }  // namespace
@@ -52,14 +111,22 @@ __device__ __forceinline__ float2 recentre(float4 w, float2 org) {
 // (2 warps, 8 disks per lane), one j per lane, halves passed unfolded; the
 // second halves the ring's shuffles and register moves per pair.  (Two j per
 // lane, folded halves and deeper unrolling measured within 3 % of these.)
-template <int NW, int NP, int NJ, bool COMB, int UR>
+//
+// PER (periodic boxes, Sec. 2.1): every coordinate is re-centred on the block
+// origin as its minimum image, exactly in grid units (near pairs, across an
+// edge too, are then plain differences); per (block, tile) the bounding boxes
+// tell whether any pair component can exceed L/2, and only such tiles (those
+// near the block's antipode) take the per-pair minimum image: 3 packed
+// operations per coordinate, or compares when the tile holds inert slots.
+template <int NW, int NP, int NJ, bool COMB, int UR, bool PER>
 __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) {
   if (ctl_failed(d.ctl)) return;
   constexpr int T = NW * 32;         // threads
   constexpr int NQ = 2 * NP;         // disks i per thread
   constexpr int NS = BD_TJ / T;      // j disks each thread stages per tile
   static_assert(BD_SB == T * NQ, "a block is BD_SB disks");
-  __shared__ float2 sjp[2][BD_TJ];   // j positions, re-centred
+  __shared__ float2 sjp[2][BD_TJ];   // j positions, re-centred (PER: the hi parts)
+  __shared__ float2 sjl[2][BD_TJ];   // PER: the lo parts
   __shared__ float2 shw[NW][BD_TJ];  // per-warp j-side sums of the current tile
   const int4 item = d.sitems[blockIdx.x];
   const int P = item.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -69,30 +136,88 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
   const BdRep &R = d.rep[binfo.x];
   const int a = binfo.y;
   const float2 org = d.sorigin[P];
+  long long LQ = 0, ox = 0, oy = 0;
+  float Lf = 0.f, hLf = __int_as_float(0x7f800000);
+  if (PER) {
+    if (R.periodic) {
+      LQ = R.LQ;
+      Lf = R.Lf;
+      hLf = R.hLf;
+    }
+    ox = (long long)org.x * (1ll << c.qshift);   // integer origins: exact in grid units
+    oy = (long long)org.y * (1ll << c.qshift);
+  }
+  auto rel = [&](int j) -> float4 {
+    if (PER) return rel_grid(d, c, j, ox, oy, LQ);
+    const float2 v = recentre(d.work[j], org);
+    return make_float4(v.x, v.y, 0.f, 0.f);
+  };
+  __shared__ float4 sbox[2][NW];     // PER: per-warp boxes of the staged tile
+  __shared__ int spad[2][NW];        //      and whether it holds inert slots
+  __shared__ float4 sibox[NW];       //      per-warp boxes of the block's disks i
+  __shared__ int sipad[NW];          //      and whether they include inert slots
   u64 xi2[NP], yi2[NP], ax2[NP], ay2[NP];
+  u64 xl2[NP], yl2[NP];              // PER: lo parts of the disks i
   float fxh[NQ], fxl[NQ], fyh[NQ], fyl[NQ];
+  float4 ibox = sempty_box();
+  bool ipad = false;
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
-    float2 p0 = recentre(d.work[base + (2 * k) * T + tid], org);
-    float2 p1 = recentre(d.work[base + (2 * k + 1) * T + tid], org);
+    const float4 p0 = rel(base + (2 * k) * T + tid);
+    const float4 p1 = rel(base + (2 * k + 1) * T + tid);
     xi2[k] = pk2(p0.x, p1.x);
     yi2[k] = pk2(p0.y, p1.y);
+    xl2[k] = pk2(p0.z, p1.z);
+    yl2[k] = pk2(p0.w, p1.w);
     ax2[k] = ay2[k] = 0ull;
+    if (PER) {
+      sbox_add(ibox, p0.x, p0.y);
+      sbox_add(ibox, p1.x, p1.y);
+      ipad = ipad || p0.x > 1.0e17f || p1.x > 1.0e17f;
+    }
   }
+  if (PER) {
+    ibox = swarp_box(ibox);
+    ipad = __any_sync(0xffffffffu, ipad);
+    if (lane == 0) {
+      sibox[warp] = ibox;
+      sipad[warp] = ipad ? 1 : 0;
+    }
+  }
+  const u64 invL2 = pk2(Lf > 0.f ? 1.0f / Lf : 0.f, Lf > 0.f ? 1.0f / Lf : 0.f);
+  const u64 nL2 = pk2(-Lf, -Lf), M2 = pk2(12582912.0f, 12582912.0f);
 #pragma unroll
   for (int q = 0; q < NQ; ++q) fxh[q] = fxl[q] = fyh[q] = fyl[q] = 0.f;
   const float e0 = 1e-20f * (float)(c.a * c.a);   // makes the self pair exactly 0
   const u64 eps2 = pk2(e0, e0);
   const int t_begin = item.y, t_end = item.z;
   const int jt0 = max(t_begin, tsym);
-  float2 st[NS];
+  float4 st[NS];
   auto fetch = [&](int tile) {
 #pragma unroll
-    for (int m = 0; m < NS; ++m) st[m] = recentre(d.work[tile * BD_TJ + m * T + tid], org);
+    for (int m = 0; m < NS; ++m) st[m] = rel(tile * BD_TJ + m * T + tid);
   };
   auto store = [&](int b) {
 #pragma unroll
-    for (int m = 0; m < NS; ++m) sjp[b][m * T + tid] = st[m];
+    for (int m = 0; m < NS; ++m) {
+      sjp[b][m * T + tid] = make_float2(st[m].x, st[m].y);
+      if (PER) sjl[b][m * T + tid] = make_float2(st[m].z, st[m].w);
+    }
+    if (PER) {
+      float4 bx = sempty_box();
+      bool pad = false;
+#pragma unroll
+      for (int m = 0; m < NS; ++m) {
+        sbox_add(bx, st[m].x, st[m].y);
+        pad = pad || st[m].x > 1.0e17f;
+      }
+      bx = swarp_box(bx);
+      pad = __any_sync(0xffffffffu, pad);
+      if (lane == 0) {
+        sbox[b][warp] = bx;
+        spad[b][warp] = pad ? 1 : 0;
+      }
+    }
   };
   int buf = 0;
   if (t_begin < t_end) {
@@ -100,94 +225,193 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
     store(0);
   }
   __syncthreads();
-  for (int t = t_begin; t < t_end; ++t) {
-    if (t + 1 < t_end) fetch(t + 1);
-    const int b = d.tile_species[t];
-    if (t < tsym) {
-      // the block's own disks: i side only, j broadcast from shared memory
+  // pair differences: MODE 0 plain, 1 packed minimum image, 2 minimum image by compares
+  // pair differences (r_j - r_i): MODE 0 the hi parts alone; 1 the exact
+  // near-pair vector (hi_j - hi_i) + (lo_j - lo_i); 2 the same with the packed
+  // minimum image of the hi difference; 3 with the minimum image by compares;
+  // 4 near pairs across the antipode (a block spanning the box): the hi
+  // difference, about L there, is formed exactly as s + e (TwoDiff), s takes
+  // the minimum image (exact: |s| in [L/2, 3L/2]), then e and the lo
+  // difference are added
+  auto diff = [&](auto MODE, u64 jh2, u64 ih2, u64 jl2, u64 il2) -> u64 {
+    constexpr int mode = decltype(MODE)::value;
+    u64 dd = sub2(jh2, ih2);
+    if constexpr (mode == 4) {
+      const u64 v = sub2(dd, jh2);
+      const u64 e = sub2(sub2(jh2, sub2(dd, v)), add2(ih2, v));
+      return add2(min_image2_cmp(dd, Lf, hLf), add2(e, sub2(jl2, il2)));
+    }
+    if constexpr (mode == 2) dd = min_image2(dd, invL2, nL2, M2);
+    if constexpr (mode == 3) dd = min_image2_cmp(dd, Lf, hLf);
+    if constexpr (mode >= 1) dd = add2(dd, sub2(jl2, il2));
+    return dd;
+  };
+  auto own_tile = [&](auto MODE) {
+    // the block's own disks: i side only, j broadcast from shared memory
 #pragma unroll 4
-      for (int jj = 0; jj < BD_TJ; ++jj) {
-        const float2 p = sjp[buf][jj];
-        const u64 jx2 = pk2(p.x, p.x), jy2 = pk2(p.y, p.y);
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-          const u64 dx = sub2(jx2, xi2[k]);
-          const u64 dy = sub2(jy2, yi2[k]);
-          u64 r2 = fma2(dx, dx, eps2);
-          r2 = fma2(dy, dy, r2);
-          float ra, rb;
-          up2(r2, ra, rb);
-          const u64 sv = pk2(rsqrt_apx(ra), rsqrt_apx(rb));
-          const u64 s3 = mul2(mul2(sv, sv), sv);
-          ax2[k] = fma2(dx, s3, ax2[k]);
-          ay2[k] = fma2(dy, s3, ay2[k]);
-        }
+    for (int jj = 0; jj < BD_TJ; ++jj) {
+      const float2 p = sjp[buf][jj];
+      const u64 jx2 = pk2(p.x, p.x), jy2 = pk2(p.y, p.y);
+      u64 jxl2 = 0ull, jyl2 = 0ull;
+      if constexpr (decltype(MODE)::value >= 1) {
+        const float2 pl = sjl[buf][jj];
+        jxl2 = pk2(pl.x, pl.x);
+        jyl2 = pk2(pl.y, pl.y);
       }
-    } else {
-      // a later tile: every pair once, both sides; each lane carries NJ disks j
-      for (int g = 0; g < BD_TJ / (32 * NJ); ++g) {
-        float jx[NJ], jy[NJ];
-        u64 hx2[NJ], hy2[NJ];
 #pragma unroll
-        for (int m = 0; m < NJ; ++m) {
-          const float2 p = sjp[buf][(g * NJ + m) * 32 + lane];
-          jx[m] = p.x;
-          jy[m] = p.y;
-          hx2[m] = hy2[m] = 0ull;
+      for (int k = 0; k < NP; ++k) {
+        const u64 dx = diff(MODE, jx2, xi2[k], jxl2, xl2[k]);
+        const u64 dy = diff(MODE, jy2, yi2[k], jyl2, yl2[k]);
+        u64 r2 = fma2(dx, dx, eps2);
+        r2 = fma2(dy, dy, r2);
+        float ra, rb;
+        up2(r2, ra, rb);
+        const u64 sv = pk2(rsqrt_apx(ra), rsqrt_apx(rb));
+        const u64 s3 = mul2(mul2(sv, sv), sv);
+        ax2[k] = fma2(dx, s3, ax2[k]);
+        ay2[k] = fma2(dy, s3, ay2[k]);
+      }
+    }
+  };
+  auto ring_tile = [&](auto MODE) {
+    // a later tile: every pair once, both sides; each lane carries NJ disks j
+    for (int g = 0; g < BD_TJ / (32 * NJ); ++g) {
+      constexpr bool LO = decltype(MODE)::value >= 1;
+      float jx[NJ], jy[NJ], jxl[NJ], jyl[NJ];
+      u64 hx2[NJ], hy2[NJ];
+#pragma unroll
+      for (int m = 0; m < NJ; ++m) {
+        const float2 p = sjp[buf][(g * NJ + m) * 32 + lane];
+        jx[m] = p.x;
+        jy[m] = p.y;
+        jxl[m] = jyl[m] = 0.f;
+        if constexpr (LO) {
+          const float2 pl = sjl[buf][(g * NJ + m) * 32 + lane];
+          jxl[m] = pl.x;
+          jyl[m] = pl.y;
         }
+        hx2[m] = hy2[m] = 0ull;
+      }
 #pragma unroll UR
-        for (int rot = 0; rot < 32; ++rot) {
-          const int src = (lane + 1) & 31;
-#pragma unroll
-          for (int m = 0; m < NJ; ++m) {
-            const u64 jx2 = pk2(jx[m], jx[m]), jy2 = pk2(jy[m], jy[m]);
-            // the next j position does not depend on this step's arithmetic
-            const float njx = __shfl_sync(0xffffffffu, jx[m], src);
-            const float njy = __shfl_sync(0xffffffffu, jy[m], src);
-#pragma unroll
-            for (int k = 0; k < NP; ++k) {
-              const u64 dx = sub2(jx2, xi2[k]);
-              const u64 dy = sub2(jy2, yi2[k]);
-              u64 r2 = fma2(dx, dx, eps2);
-              r2 = fma2(dy, dy, r2);
-              float ra, rb;
-              up2(r2, ra, rb);
-              const u64 sv = pk2(rsqrt_apx(ra), rsqrt_apx(rb));
-              const u64 s3 = mul2(mul2(sv, sv), sv);
-              ax2[k] = fma2(dx, s3, ax2[k]);
-              ay2[k] = fma2(dy, s3, ay2[k]);
-              hx2[m] = fma2(dx, s3, hx2[m]);
-              hy2[m] = fma2(dy, s3, hy2[m]);
-            }
-            // pass the j accumulator one lane down the ring, after its disk
-            float h0, h1, h2, h3;
-            up2(hx2[m], h0, h1);
-            up2(hy2[m], h2, h3);
-            if (COMB) {
-              h0 = __shfl_sync(0xffffffffu, __fadd_rn(h0, h1), src);
-              h2 = __shfl_sync(0xffffffffu, __fadd_rn(h2, h3), src);
-              hx2[m] = pk2(h0, 0.f);
-              hy2[m] = pk2(h2, 0.f);
-            } else {
-              h0 = __shfl_sync(0xffffffffu, h0, src);
-              h1 = __shfl_sync(0xffffffffu, h1, src);
-              h2 = __shfl_sync(0xffffffffu, h2, src);
-              h3 = __shfl_sync(0xffffffffu, h3, src);
-              hx2[m] = pk2(h0, h1);
-              hy2[m] = pk2(h2, h3);
-            }
-            jx[m] = njx;
-            jy[m] = njy;
-          }
-        }
-        // after 32 passes every j is back in its own lane
+      for (int rot = 0; rot < 32; ++rot) {
+        const int src = (lane + 1) & 31;
 #pragma unroll
         for (int m = 0; m < NJ; ++m) {
+          const u64 jx2 = pk2(jx[m], jx[m]), jy2 = pk2(jy[m], jy[m]);
+          const u64 jxl2 = LO ? pk2(jxl[m], jxl[m]) : 0ull, jyl2 = LO ? pk2(jyl[m], jyl[m]) : 0ull;
+          // the next j position does not depend on this step's arithmetic
+          const float njx = __shfl_sync(0xffffffffu, jx[m], src);
+          const float njy = __shfl_sync(0xffffffffu, jy[m], src);
+          float njxl = 0.f, njyl = 0.f;
+          if constexpr (LO) {
+            njxl = __shfl_sync(0xffffffffu, jxl[m], src);
+            njyl = __shfl_sync(0xffffffffu, jyl[m], src);
+          }
+#pragma unroll
+          for (int k = 0; k < NP; ++k) {
+            const u64 dx = diff(MODE, jx2, xi2[k], jxl2, xl2[k]);
+            const u64 dy = diff(MODE, jy2, yi2[k], jyl2, yl2[k]);
+            u64 r2 = fma2(dx, dx, eps2);
+            r2 = fma2(dy, dy, r2);
+            float ra, rb;
+            up2(r2, ra, rb);
+            const u64 sv = pk2(rsqrt_apx(ra), rsqrt_apx(rb));
+            const u64 s3 = mul2(mul2(sv, sv), sv);
+            ax2[k] = fma2(dx, s3, ax2[k]);
+            ay2[k] = fma2(dy, s3, ay2[k]);
+            hx2[m] = fma2(dx, s3, hx2[m]);
+            hy2[m] = fma2(dy, s3, hy2[m]);
+          }
+          // pass the j accumulator one lane down the ring, after its disk
           float h0, h1, h2, h3;
           up2(hx2[m], h0, h1);
           up2(hy2[m], h2, h3);
-          shw[warp][(g * NJ + m) * 32 + lane] = make_float2(__fadd_rn(h0, h1), __fadd_rn(h2, h3));
+          if (COMB) {
+            h0 = __shfl_sync(0xffffffffu, __fadd_rn(h0, h1), src);
+            h2 = __shfl_sync(0xffffffffu, __fadd_rn(h2, h3), src);
+            hx2[m] = pk2(h0, 0.f);
+            hy2[m] = pk2(h2, 0.f);
+          } else {
+            h0 = __shfl_sync(0xffffffffu, h0, src);
+            h1 = __shfl_sync(0xffffffffu, h1, src);
+            h2 = __shfl_sync(0xffffffffu, h2, src);
+            h3 = __shfl_sync(0xffffffffu, h3, src);
+            hx2[m] = pk2(h0, h1);
+            hy2[m] = pk2(h2, h3);
+          }
+          jx[m] = njx;
+          jy[m] = njy;
+          jxl[m] = njxl;
+          jyl[m] = njyl;
         }
+      }
+      // after 32 passes every j is back in its own lane
+#pragma unroll
+      for (int m = 0; m < NJ; ++m) {
+        float h0, h1, h2, h3;
+        up2(hx2[m], h0, h1);
+        up2(hy2[m], h2, h3);
+        shw[warp][(g * NJ + m) * 32 + lane] = make_float2(__fadd_rn(h0, h1), __fadd_rn(h2, h3));
+      }
+    }
+  };
+  float4 ibx = sempty_box();
+  int ipd = 0;   // inert slots among the disks i: the packed minimum image would
+                 // bring them near, so their tiles take the compares
+  if (PER) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      ibx = smerge_box(ibx, sibox[w]);
+      ipd |= sipad[w];
+    }
+  }
+  for (int t = t_begin; t < t_end; ++t) {
+    if (t + 1 < t_end) fetch(t + 1);
+    const int b = d.tile_species[t];
+    int mode = 0;
+    if constexpr (PER) {
+      float4 jb = sempty_box();
+      int pad = ipd;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        jb = smerge_box(jb, sbox[buf][w]);
+        pad |= spad[buf][w];
+      }
+      // pair components range over [j_min - i_max, j_max - i_min]
+      const bool wrap = LQ > 0 && (jb.y - ibx.x > hLf || jb.x - ibx.y < -hLf || jb.w - ibx.z > hLf ||
+                                   jb.z - ibx.w < -hLf);
+      // boxes closer than 20: the exact vector keeps their pairs at FP32
+      // resolution of their separation (a 512-disk block puts coordinates up
+      // to L/2 from its origin, where one rounding costs ulp(L/2) / 2)
+      const float gx = fmaxf(0.f, fmaxf(jb.x - ibx.y, ibx.x - jb.y));
+      const float gy = fmaxf(0.f, fmaxf(jb.z - ibx.w, ibx.z - jb.w));
+      const bool near = gx * gx + gy * gy < 400.f;
+      mode = wrap ? (near ? 4 : (pad ? 3 : 2)) : (near ? 1 : 0);
+    }
+    using M0 = std::integral_constant<int, 0>;
+    using M1 = std::integral_constant<int, 1>;
+    using M2c = std::integral_constant<int, 2>;
+    using M3 = std::integral_constant<int, 3>;
+    using M4 = std::integral_constant<int, 4>;
+    if (t < tsym) {
+      if constexpr (PER) {
+        if (mode == 1) own_tile(M1());
+        else if (mode == 2) own_tile(M2c());
+        else if (mode == 3) own_tile(M3());
+        else if (mode == 4) own_tile(M4());
+        else own_tile(M0());
+      } else {
+        own_tile(M0());
+      }
+    } else {
+      if constexpr (PER) {
+        if (mode == 1) ring_tile(M1());
+        else if (mode == 2) ring_tile(M2c());
+        else if (mode == 3) ring_tile(M3());
+        else if (mode == 4) ring_tile(M4());
+        else ring_tile(M0());
+      } else {
+        ring_tile(M0());
       }
       __syncthreads();
       // j side of this tile: F_j += A[s_j][s_i] sum_i (r_j - r_i)/r^3
@@ -283,10 +507,18 @@ int bd_force_launches(int variant) { return variant >= 2 ? 2 : 1; }
 // variant 2: 4 warps x 4 disks per lane; variant 3: 2 warps x 8 disks per lane
 cudaError_t bd_launch_force_sym(const BdDev &d, const BdConst &c, int variant, cudaStream_t s) {
   if (c.n_sitems == 0) return cudaSuccess;
-  if (variant == 2)
-    k_force_long_sym<4, 2, 1, false, 2><<<c.n_sitems, 128, 0, s>>>(d, c);
-  else
-    k_force_long_sym<2, 4, 1, false, 2><<<c.n_sitems, 64, 0, s>>>(d, c);
+  // periodic boxes (any replica) take the form with minimum images
+  if (c.any_periodic) {
+    if (variant == 2)
+      k_force_long_sym<4, 2, 1, false, 2, true><<<c.n_sitems, 128, 0, s>>>(d, c);
+    else
+      k_force_long_sym<2, 4, 1, false, 2, true><<<c.n_sitems, 64, 0, s>>>(d, c);
+  } else {
+    if (variant == 2)
+      k_force_long_sym<4, 2, 1, false, 2, false><<<c.n_sitems, 128, 0, s>>>(d, c);
+    else
+      k_force_long_sym<2, 4, 1, false, 2, false><<<c.n_sitems, 64, 0, s>>>(d, c);
+  }
   k_force_sym_reduce<<<c.np / BD_RED_D, 4 * BD_RED_D, 0, s>>>(d, c);
   return cudaGetLastError();
 }
