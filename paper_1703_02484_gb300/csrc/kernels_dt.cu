@@ -509,10 +509,24 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           d.tv_snap[t] = vs;
           d.tn_snap[t] = nn;
         }
+        // corners loaded once: FP32 pairs, moved flags and re-entries serve the
+        // filters of triangles and edges that carry no image shift
+        const int vv[3] = {v.x, v.y, v.z};
+        const bool isd[3] = {v.x < x.np, v.y < x.np, v.z < x.np};
+        const bool flat = (v.w & BD_TRI_SHIFT_BITS) == 0;
+        float4 W[3];
+        uint8_t mvd[3], wr[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          W[k] = work_of(x, vv[k]);
+          mvd[k] = fresh ? d.moved[vv[k]] : (uint8_t)0;
+          wr[k] = isd[k] ? d.wrap[vv[k]] : (uint8_t)0;
+        }
         int fl = v.w & BD_TRI_FLAGS;
-        if (fresh && (d.moved[v.x] | d.moved[v.y] | d.moved[v.z])) {
-          const int o = orient_s(x, v.x, tshx<PER>(v.w, 0), tshy<PER>(v.w, 0), v.y, tshx<PER>(v.w, 1), tshy<PER>(v.w, 1), v.z,
-                                 tshx<PER>(v.w, 2), tshy<PER>(v.w, 2));
+        if (mvd[0] | mvd[1] | mvd[2]) {
+          const int o = flat ? orient_pre(x, isd[0] && isd[1] && isd[2], W[0], W[1], W[2], v.x, v.y, v.z)
+                             : orient_s(x, v.x, tshx<PER>(v.w, 0), tshy<PER>(v.w, 0), v.y, tshx<PER>(v.w, 1),
+                                        tshy<PER>(v.w, 1), v.z, tshx<PER>(v.w, 2), tshy<PER>(v.w, 2));
           fl = BD_TRI_DIRTY | (o <= 0 ? BD_TRI_INVERTED : 0);
           d.tv[t].w = (v.w & ~BD_TRI_FLAGS) | fl;
         }
@@ -524,39 +538,61 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           // each interior edge once: from its smaller corner, or from this side
           // when the neighbour is not visited by this pass
           if (o < 0 || (o <= cc && (full || cmark[o / 3] == gen))) continue;
-          const int u = vk(v, (k + 1) % 3), w = vk(v, (k + 2) % 3);
-          const bool disks = u < x.np && w < x.np;
-          const bool mv = fresh && (d.moved[u] | d.moved[w]);
+          const int ku = (k + 1) % 3, kw = (k + 2) % 3;
+          const int u = vv[ku], w = vv[kw];
+          const bool disks = isd[ku] && isd[kw];
+          const bool mv = (mvd[ku] | mvd[kw]) != 0;
           // image shift of w relative to u in this triangle (periodic box; 0 with walls)
           const int rsx = tshx<PER>(v.w, (k + 2) % 3) - tshx<PER>(v.w, (k + 1) % 3);
           const int rsy = tshy<PER>(v.w, (k + 2) % 3) - tshy<PER>(v.w, (k + 1) % 3);
           long long LQ = 0;
           if (rsx | rsy) LQ = rep_LQ(x, u);
+          const bool plain = (rsx | rsy) == 0;   // the edge carries no image shift
+          // r1 = r_w - r_u from the FP32 pairs (unshifted edges)
+          const float r1x = plain ? fdiff(W[kw].x, W[kw].z, W[ku].x, W[ku].z) : 0.f;
+          const float r1y = plain ? fdiff(W[kw].y, W[kw].w, W[ku].y, W[ku].w) : 0.f;
           if (disks && mv) {
-            // Sec. 4.3 first criterion: r0 . r1 < 0, exact on the grid (in a
-            // periodic box the edge's shift before the move is the present one
-            // less the re-entries of its end points)
+            // Sec. 4.3 first criterion: r0 . r1 < 0.  An unshifted edge whose
+            // ends did not re-enter is screened in FP32 from r1 and the moves,
+            // as with walls; otherwise, and near zero, exact on the grid (the
+            // edge's shift before the move is the present one less the
+            // re-entries of its end points)
+            int dec = 0;   // 1 reversed, -1 not, 0 undecided
+            if (plain && (wr[ku] | wr[kw]) == 0) {
+              const float2 mu = mvd[ku] ? d.dmove[u] : make_float2(0.f, 0.f);
+              const float2 mw = mvd[kw] ? d.dmove[w] : make_float2(0.f, 0.f);
+              const float r0x = __fsub_rn(r1x, __fsub_rn(mw.x, mu.x)), r0y = __fsub_rn(r1y, __fsub_rn(mw.y, mu.y));
+              const float dot = __fadd_rn(__fmul_rn(r0x, r1x), __fmul_rn(r0y, r1y));
+              const float S = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r0x, r0x), __fmul_rn(r0y, r0y)),
+                                                  __fadd_rn(__fmul_rn(r1x, r1x), __fmul_rn(r1y, r1y))),
+                                        __fadd_rn(__fadd_rn(__fmul_rn(mu.x, mu.x), __fmul_rn(mu.y, mu.y)),
+                                                  __fadd_rn(__fmul_rn(mw.x, mw.x), __fmul_rn(mw.y, mw.y))));
+              const float bound = 4e-6f * S;
+              dec = dot > bound ? -1 : (-dot > bound ? 1 : 0);
+            }
             int ox = rsx, oy = rsy;
-            {
-              const uint8_t wu = d.wrap[u], ww = d.wrap[w];
-              ox -= wrapx(ww) - wrapx(wu);
-              oy -= wrapy(ww) - wrapy(wu);
+            if (dec == 0) {
+              ox -= wrapx(wr[kw]) - wrapx(wr[ku]);
+              oy -= wrapy(wr[kw]) - wrapy(wr[ku]);
               if ((ox | oy) && LQ == 0) LQ = rep_LQ(x, u);
             }
-            if (reversed_exact(x, u, w, ox, oy, rsx, rsy, LQ)) {
+            if (dec == 1 || (dec == 0 && reversed_exact(x, u, w, ox, oy, rsx, rsy, LQ))) {
               ++rej;
               atomicExch(&ctl->st_fail_item, cc);
             }
           }
           if (inverted) continue;   // marks and scan wait for the repair
           const int4 v1 = d.tv[o / 3];
-          const bool d1 = (v1.w & BD_TRI_DIRTY) ||
-                          (fresh && (d.moved[v1.x] | d.moved[v1.y] | d.moved[v1.z]));
+          const int q = vk(v1, o % 3);
+          const bool d1 = (v1.w & BD_TRI_DIRTY) || (mvd[ku] | mvd[kw]) || (fresh && d.moved[q]);
           if ((fl & BD_TRI_DIRTY) || d1) {
-            const int q = vk(v1, o % 3);
             int sqx, sqy;
             opp_shift<PER>(v.w, k, v1.w, o % 3, sqx, sqy);
-            if (incircle_s<PER>(x, v, q, sqx, sqy) > 0) {
+            const int ic = (flat && (sqx | sqy) == 0)
+                               ? incircle_pre(x, isd[0] && isd[1] && isd[2] && q < x.np, W[0], W[1], W[2],
+                                              work_of(x, q), v.x, v.y, v.z, q)
+                               : incircle_s<PER>(x, v, q, sqx, sqy);
+            if (ic > 0) {
               claim6(x, t, k, nn, o, claim_key(epoch, cc));
               ++cand;
             }
@@ -565,11 +601,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
             // FP32 screen: a pair whose FP32 squared distance exceeds
             // sigma^2 (1 + 1e-5) is farther than sigma (FP32 error ~3e-7);
             // edges across a periodic box edge skip it
-            if ((rsx | rsy) == 0) {
-              const float4 wu = d.work[u], ww = d.work[w];
-              const float fdx = fdiff(ww.x, ww.z, wu.x, wu.z), fdy = fdiff(ww.y, ww.w, wu.y, wu.w);
-              if (__fadd_rn(__fmul_rn(fdx, fdx), __fmul_rn(fdy, fdy)) > x.sig2f) continue;
-            }
+            if (plain && __fadd_rn(__fmul_rn(r1x, r1x), __fmul_rn(r1y, r1y)) > x.sig2f) continue;
             const double2 pu = d.pos[u], pw = d.pos[w];
             // exact pre-test in grid units: |r_w - r_u|^2 <= (sigma/q)^2 (1 + 1e-9)
             const int64_t ix = bdpred::to_int(pw.x, x.g) - bdpred::to_int(pu.x, x.g) + rsx * LQ;
@@ -937,6 +969,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         if (PER && R.periodic) {
           // Algorithm 2 "applying the periodic boundary conditions": re-entry
           long long X = bdpred::to_int(y.x, x.g), Y = bdpred::to_int(y.y, x.g);
+          d.dmove[i] = make_float2(bdem::grid_to_float(X - bdpred::to_int(p.x, x.g), x.g.s),
+                                   bdem::grid_to_float(Y - bdpred::to_int(p.y, x.g), x.g.s));
           const int wr = bdem::wrap_grid(R.LQ, X, Y);
           d.wrap[i] = (uint8_t)wr;
           if (wr) ++nwrap;
@@ -947,7 +981,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         if (log_pidx >= 0) d.log_pflags[(size_t)log_pidx * x.np + i] = (uint8_t)(rfl | (capped ? 16 : 0));
         d.pos[i] = np2;
         d.work[i] = split_pos(np2);
-        if (!PER) {
+        if (!(PER && R.periodic)) {
           d.dmove[i] = make_float2(bdem::grid_to_float(bdpred::to_int(np2.x, x.g) - bdpred::to_int(p.x, x.g), x.g.s),
                                    bdem::grid_to_float(bdpred::to_int(np2.y, x.g) - bdpred::to_int(p.y, x.g), x.g.s));
         }

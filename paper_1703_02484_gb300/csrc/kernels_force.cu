@@ -558,7 +558,10 @@ __global__ void k_integrate(BdDev d, BdConst c, long long step, int log_step, in
     X = bdpred::to_int(y.x, g);
     Y = bdpred::to_int(y.y, g);
   }
+  const long long X0 = bdpred::to_int(p.x, g), Y0 = bdpred::to_int(p.y, g);
   if (R.periodic) {
+    // the move itself (before re-entry), for the triangulation's reversal screen
+    d.dmove[i] = make_float2(bdem::grid_to_float(X - X0, c.qshift), bdem::grid_to_float(Y - Y0, c.qshift));
     // re-entry at the opposite side (Sec. 2.1); the triangulation kernel
     // shifts the corners of the disks that re-entered
     const int wr = bdem::wrap_grid(R.LQ, X, Y);
@@ -568,8 +571,8 @@ __global__ void k_integrate(BdDev d, BdConst c, long long step, int log_step, in
     flags = bdem::reflect_grid(bdpred::to_int(R.wall_lo, g), bdpred::to_int(R.wall_hi, g), X, Y);
   }
   d.pos[i] = make_double2(bdem::grid_to_double(X, c.qshift), bdem::grid_to_double(Y, c.qshift));
-  d.dmove[i] = make_float2(bdem::grid_to_float(X - bdpred::to_int(p.x, g), c.qshift),
-                           bdem::grid_to_float(Y - bdpred::to_int(p.y, g), c.qshift));
+  if (!R.periodic)
+    d.dmove[i] = make_float2(bdem::grid_to_float(X - X0, c.qshift), bdem::grid_to_float(Y - Y0, c.qshift));
   const float2 sx = bdem::grid_split(X, c.qshift), sy = bdem::grid_split(Y, c.qshift);
   d.work[i] = make_float4(sx.x, sy.x, sx.y, sy.y);
   d.theta[i] = thn;

@@ -63,13 +63,21 @@ __global__ void k_state_in(BdDev d, BdConst c, int with_theta) {
     y = make_double2(fmin(R.wall_hi, fmax(R.wall_lo, snap_grid(p.x, c))),
                      fmin(R.wall_hi, fmax(R.wall_lo, snap_grid(p.y, c))));
   }
-  if (!R.periodic) {
+  {
     // the move from the previous positions, for the triangulation's FP32
-    // reversal screen (exact grid difference, one rounding to FP32)
+    // reversal screen (exact grid difference, one rounding to FP32; in a
+    // periodic box its minimum image, and a disk that crossed an edge has its
+    // edges tested exactly)
     const double2 o = d.pos[i];
     const bdpred::Grid g{c.q, c.inv_q, c.qshift};
-    d.dmove[i] = make_float2(bdem::grid_to_float(bdpred::to_int(y.x, g) - bdpred::to_int(o.x, g), c.qshift),
-                             bdem::grid_to_float(bdpred::to_int(y.y, g) - bdpred::to_int(o.y, g), c.qshift));
+    long long mx = bdpred::to_int(y.x, g) - bdpred::to_int(o.x, g);
+    long long my = bdpred::to_int(y.y, g) - bdpred::to_int(o.y, g);
+    if (R.periodic) {
+      const long long h = R.LQ / 2;
+      mx = mx > h ? mx - R.LQ : (mx < -h ? mx + R.LQ : mx);
+      my = my > h ? my - R.LQ : (my < -h ? my + R.LQ : my);
+    }
+    d.dmove[i] = make_float2(bdem::grid_to_float(mx, c.qshift), bdem::grid_to_float(my, c.qshift));
   }
   d.pos[i] = y;
   if (with_theta) d.theta[i] = d.xfer_th[e];
