@@ -216,10 +216,13 @@ int bd_get_replica(bd_handle *h, int32_t r, double *xy, float *theta, int32_t *t
                    int32_t *n, double *L);
 
 /* The all-pairs sweep's tuning: j tiles (256 disks each) per work item, the
- * kernel variant (0 scalar FP32, 1 packed f32x2, 2 symmetric packed f32x2:
- * each unordered pair once) and the number of work items.  bd_init picks the
- * FP32 variant and chunk size by timing the candidates on the device; the
- * environment variables BD_FORCE_VARIANT (0-2) and BD_FORCE_TILES fix them. */
+ * kernel variant (0 scalar FP32 one-sided, 1 packed f32x2 one-sided, 2 and 3
+ * symmetric packed f32x2 -- each unordered pair once -- with 4 warps x 4 or
+ * 2 warps x 8 disks per lane) and the number of work items.  Periodic boxes
+ * take the minimum-image forms of variants 0, 2 and 3 (1 falls back to 0).
+ * bd_init picks the FP32 variant and chunk size by timing the candidates on
+ * the device; the environment variables BD_FORCE_VARIANT (0-3) and
+ * BD_FORCE_TILES fix them. */
 int bd_get_tuning(bd_handle *h, int32_t *tiles_per_item, int32_t *variant, int32_t *n_items);
 
 /* Copy the current state to host memory ("Ensure P updated to current
