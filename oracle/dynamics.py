@@ -6,12 +6,13 @@ model of Sec. 7 adds V0 (cos theta, sin theta) dt to the displacement and
 diffuses the director as theta(t+dt) = theta + sqrt(2 D_r dt) n.
 
 Noise amplitude: Eq. (integration) prints sqrt(D dt) while the rotational
-update of Sec. 7 uses sqrt(2 D dt); this build reads the translational
-amplitude as sqrt(2 D dt) per component (mean-square displacement 4 D t in
-2D) and keeps the literal sqrt(D dt) behind `literal_amp=True`.
+update of Sec. 7 uses sqrt(2 D dt); the translational amplitude is read
+here as sqrt(2 D dt) per component (mean-square displacement 4 D t in
+2D); the literal sqrt(D dt) is kept behind `literal_amp=True`.
 
-Walls (the paper's box is periodic, Sec. 2.1; this build uses reflecting
-walls): centres live in [a, L - a]; a coordinate below a is mirrored to
+Walls (the paper's box is periodic, Sec. 2.1, kept as an option; the
+benchmark configurations use reflecting walls): centres live in
+[a, L - a]; a coordinate below a is mirrored to
 2a - x, one above L - a to 2(L - a) - x.
 """
 import math

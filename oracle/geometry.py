@@ -5,8 +5,8 @@
   expansion arithmetic (oracle/csrc).
 * The Delaunay triangulation (Sec. 4.1) of the disk centres together with
   fixed ghost points outside the box.  The paper's box is periodic and its
-  triangulation lives on a torus; with reflecting walls this build closes the
-  hull with four far corners and a ring of points just outside the walls
+  triangulation lives on a torus; with reflecting walls the hull is closed
+  with four far corners and a ring of points just outside the walls
   (layout in `ghost_points`).  Any pair of disks closer than sigma is a
   Delaunay edge of this point set (its diametral circle lies at y, x >= 0 and
   holds no other point), so the overlap search over triangulation edges still

@@ -14,8 +14,8 @@ the summed vector), and is reflected at the walls.  The pass repeats until
 no pair is closer than sigma.
 
 Which triangulation each pass uses: Algorithm 1 updates the triangulation
-before correcting, so its last pass sees a stale triangulation.  This build
-reads the stopping test as "no Delaunay edge of the *current* positions is
+before correcting, so its last pass sees a stale triangulation.  The stopping test is read
+as "no Delaunay edge of the *current* positions is
 shorter than sigma": the closest pair of a point set is a Delaunay edge, so
 that certifies that no pair anywhere overlaps.  The oracle therefore rebuilds
 the triangulation from scratch before every pass.

@@ -7,8 +7,8 @@ key by ten rounds; each round multiplies counter words 0 and 2 by fixed
 high halves with the other two counter words and the round key; the key is
 bumped by two Weyl constants between rounds.
 
-The paper draws its noise with cuRAND's XORWOW (Sec. 5); this build uses
-Philox so that every random number is a pure function of
+The paper draws its noise with cuRAND's XORWOW (Sec. 5); Philox is used
+here so that every random number is a pure function of
 (seed, particle, step) and the GPU and the oracle can draw identical streams
 independently.  Stream layout (both sides implement it on their own):
     key     = (seed mod 2^32, (seed >> 32) xor replica)

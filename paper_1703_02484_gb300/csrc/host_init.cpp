@@ -3,11 +3,11 @@
 //
 // Sec. 4.1: "the Delaunay triangulation of the particle positions is built
 // only once from scratch on the host" and then maintained on the device.
-// The paper uses CGAL's periodic triangulation; this build uses reflecting
-// walls and closes the hull with fixed ghost points outside the box (see
-// make_ghosts), and builds the triangulation by incremental insertion: each point
-// splits the triangle (or edge) that contains it and Lawson flips restore
-// the empty-circle property around it.  Predicates are exact (predicates.cuh).
+// The paper uses CGAL's periodic triangulation; with reflecting walls (the
+// benchmark configurations) the hull is closed with fixed ghost points
+// outside the box (see make_ghosts).  The triangulation is built by
+// incremental insertion: each point splits the triangle (or edge) that
+// contains it and Lawson flips restore the empty-circle property around it.  Predicates are exact (predicates.cuh).
 //
 // Layout ("corner table"): triangle t has corners 3t+0..3t+2 holding vertex
 // ids in counter-clockwise order; opp[3t+k] is the corner of the neighbouring

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA time step against the FP64 oracle, through the C ABI.
 
-Tolerances (stated by the task for this method): per-disk force error <= 1e-5
+Tolerances (the accuracy bar set for this method): per-disk force error <= 1e-5
 relative to the force norm (read as the RMS of |F_i| over the system), and
 position error <= 1e-5 a after one step; the Delaunay edge set must match
 exactly for points in general position."""
