@@ -243,7 +243,9 @@ def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind, v
 
 def cpu_baseline(cfg, xy, sp, th, periodic=False):
     """One full oracle step of the workload (exact all-pairs forces on all host
-    cores), the oracle as it stands."""
+    cores), the oracle as it stands; and a one-core figure: the same step with
+    its force sum timed on one thread for a sample of disks, scaled to all."""
+    from oracle import forces as of
     from oracle import step as ostep
     cores = os.cpu_count() or 1
     L = float(np.float32(cfg.L)) if periodic else cfg.L
@@ -252,9 +254,26 @@ def cpu_baseline(cfg, xy, sp, th, periodic=False):
     t0 = time.perf_counter()
     ostep.step(xy, th, sp, 0, op, threads=cores)
     t = time.perf_counter() - t0
-    return {"value": cfg.n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "one full FP64 oracle step of the N=1e5 workload (all-pairs forces with "
-                      "OpenMP over %d threads, Delaunay rebuilds and overlap correction): %.2f s" % (cores, t)}
+    out = {"value": cfg.n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "one full FP64 oracle step of the N=1e5 workload (all-pairs forces with "
+                     "OpenMP over %d threads, Delaunay rebuilds and overlap correction): %.2f s" % (cores, t)}
+    if cfg.law == 1 and cores > 1:
+        # the force sum of m disks on one thread and on all, scaled by N / m:
+        # the one-core step replaces the latter by the former
+        m = min(cfg.n, 2000)
+        Lp = L if periodic else None
+        t0 = time.perf_counter()
+        of.long_range(xy, sp, cfg.alpha, idx=np.arange(m), threads=1, L=Lp)
+        t1 = (time.perf_counter() - t0) * cfg.n / m
+        t0 = time.perf_counter()
+        of.long_range(xy, sp, cfg.alpha, idx=np.arange(m), threads=cores, L=Lp)
+        tc = (time.perf_counter() - t0) * cfg.n / m
+        t_one = t - tc + t1
+        out["value_1core"] = cfg.n / t_one
+        out["sample"] += ("; one core: the force sum of %d disks on 1 and on %d threads, scaled by N/%d "
+                          "(%.2f s and %.2f s), replaces the all-core force time in the step: %.2f s"
+                          % (m, cores, m, t1, tc, t_one))
+    return out
 
 
 def run_batched(args):
