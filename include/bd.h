@@ -111,12 +111,23 @@ typedef struct bd_params {
                               without ghost points (2n triangles, corners carry image shifts,
                               bd_get_tri_shifts).  L is rounded to the nearest FP32 value.
                               Periodic handles need n >= 16 and L >= 8 sigma; the all-pairs
-                              sweep uses its one-sided forms there; recorded rollouts
+                              sweeps use their minimum-image forms there; recorded rollouts
                               (bd_rollout) are walls-only. */
+  int32_t placement;       /* start positions when bd_init gets xy == NULL:
+                              BD_PLACE_RSA (default): random sequential addition of centres in
+                              [a, L - a]^2, pairwise at least sigma apart;
+                              BD_PLACE_LATTICE: the paper's start (Sec. 4.1): a triangular
+                              lattice over [a, L - a]^2 with N* >= n sites (the widest spacing
+                              s >= sigma that gives enough), n of them chosen by reservoir
+                              sampling, each moved by a uniform offset within (s - sigma)/2
+                              (kept in the box) so the set is in general position and no two
+                              centres come closer than sigma.  Both draw from Philox streams
+                              of `seed` (bd_place_disks gives the same positions). */
 } bd_params;
 
 enum { BD_OVERLAP_DELAUNAY = 0, BD_OVERLAP_VERLET = 1 };
 enum { BD_BOUNDARY_WALLS = 0, BD_BOUNDARY_PERIODIC = 1 };
+enum { BD_PLACE_RSA = 0, BD_PLACE_LATTICE = 1 };
 
 /* Counters of one bd_step call (the paper's per-step metrics, Sec. 6). */
 typedef struct bd_step_stats {
@@ -308,6 +319,14 @@ int64_t bd_last_launch_count(bd_handle *h);
  * integration kernels are separate launches (bd_force_timing covers the
  * force). */
 int bd_stage_times(bd_handle *h, int reset, double *ms, int64_t *phases);
+
+/* Start positions as bd_init draws them when it gets xy == NULL (Sec. 4.1
+ * placement, bd_params.placement): n centres in [a, L - a]^2, pairwise at
+ * least 2a apart, from the Philox streams of seed.  Host only (no GPU).
+ *   xy  receives 2n doubles.  Errors: BD_ERR_ARG (n < 1, L <= 2a, a <= 0,
+ *   unknown placement, or no placement found: the area fraction is too high
+ *   for the lattice, or random addition jammed). */
+int bd_place_disks(int32_t n, double L, double a, int32_t placement, uint64_t seed, double *xy);
 
 /* Host only: the fixed ghost points that close the triangulation of a box of
  * side L for disks of radius a.  The paper's periodic box needs none; with

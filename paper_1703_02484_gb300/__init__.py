@@ -4,5 +4,5 @@ The compute path is libbd_gb300.so (CUDA kernels for sm_103a behind the C ABI
 of include/bd.h); this package only marshals arguments to it."""
 from . import workloads  # noqa: F401
 from .binding import (BOUNDARY_PERIODIC, BOUNDARY_WALLS, LAW_LONG, LAW_NONE, LAW_SHORT, LOSS_HIST, LOSS_MSD,  # noqa: F401
-                      OVERLAP_DELAUNAY, OVERLAP_VERLET, BDError, System, load, make_params,
-                      params_from_config, rollout_loss)
+                      OVERLAP_DELAUNAY, OVERLAP_VERLET, PLACE_LATTICE, PLACE_RSA, BDError, System, load,
+                      make_params, params_from_config, place_disks, rollout_loss)

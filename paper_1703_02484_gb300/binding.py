@@ -18,6 +18,7 @@ ERRORS = {
 }
 LAW_NONE, LAW_LONG, LAW_SHORT = 0, 1, 2
 BOUNDARY_WALLS, BOUNDARY_PERIODIC = 0, 1
+PLACE_RSA, PLACE_LATTICE = 0, 1
 LOSS_MSD = 0
 LOSS_HIST = 1
 OVERLAP_DELAUNAY, OVERLAP_VERLET = 0, 1
@@ -37,6 +38,7 @@ class bd_params(ctypes.Structure):
         ("literal_noise", ctypes.c_int32), ("step0", ctypes.c_int64),
         ("overlap_mode", ctypes.c_int32), ("max_dt_halvings", ctypes.c_int32),
         ("boundary", ctypes.c_int32),
+        ("placement", ctypes.c_int32),
     ]
 
 
@@ -74,6 +76,8 @@ SIGNATURES = [
     ("bd_last_launch_count", ctypes.c_int64, [_P]),
     ("bd_triangulate", ctypes.c_int, [ctypes.c_int32, _P, ctypes.c_double, ctypes.c_double, _P, _P,
                                       ctypes.POINTER(ctypes.c_int32)]),
+    ("bd_place_disks", ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                       ctypes.c_uint64, _P]),
     ("bd_ghost_points", ctypes.c_int, [ctypes.c_double, ctypes.c_double, _P,
                                        ctypes.POINTER(ctypes.c_int32)]),
     ("bd_forces_noalloc", ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_double),
@@ -152,7 +156,7 @@ def _ptr(a):
 def make_params(n, L=None, rho=None, a=1.0, law=LAW_NONE, alpha=(0, 0, 0, 0), n_species=1,
                 eps=1.0, kappa=1.0, r_cut=5.0, skin=0.6, D=1.0, Dr=0.0, v0=0.0, dt=1e-4,
                 seed=0, replica=0, precision=0, max_corr_iters=1000, max_flip_rounds=4096,
-                literal_noise=0, step0=0, max_dt_halvings=0, boundary=BOUNDARY_WALLS):
+                literal_noise=0, step0=0, max_dt_halvings=0, boundary=BOUNDARY_WALLS, placement=PLACE_RSA):
     p = bd_params()
     _check(load().bd_default_params(ctypes.byref(p)), "bd_default_params")
     p.n, p.n_species, p.a = int(n), int(n_species), float(a)
@@ -170,6 +174,7 @@ def make_params(n, L=None, rho=None, a=1.0, law=LAW_NONE, alpha=(0, 0, 0, 0), n_
     p.literal_noise, p.step0 = int(literal_noise), int(step0)
     p.max_dt_halvings = int(max_dt_halvings)
     p.boundary = int(boundary)
+    p.placement = int(placement)
     return p
 
 
@@ -407,6 +412,14 @@ def _rollout_fn():
 
         _ROLLOUT_FN = RolloutLoss
     return _ROLLOUT_FN
+
+
+def place_disks(n, L, a=1.0, placement=PLACE_RSA, seed=0):
+    """Start positions as bd_init draws them for xy = None (bd_place_disks): (n, 2)."""
+    out = np.zeros((int(n), 2), dtype=np.float64)
+    _check(load().bd_place_disks(int(n), float(L), float(a), int(placement), int(seed), _ptr(out)),
+           "bd_place_disks")
+    return out
 
 
 def ghost_points(L, a=1.0):

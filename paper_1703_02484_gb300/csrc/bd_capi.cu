@@ -31,6 +31,7 @@ int build_delaunay(const double *X, const double *Y, const bdpred::Grid &grid,
 void make_ghosts(double L, double a, std::vector<double> &gx, std::vector<double> &gy);
 double ghost_extent(double L, double a);
 int rsa_place(int n, double lo, double hi, double dmin, uint64_t seed, std::vector<double> &xy);
+int lattice_place(int n, double lo, double hi, double dmin, uint64_t seed, std::vector<double> &xy);
 int any_overlap(int n, const double *xy, double lo, double hi, double dmin);
 int any_overlap_periodic(int n, const double *xy, double L, double dmin);
 int build_torus_delaunay(const double *X, const double *Y, const std::vector<int> &ids, double L,
@@ -114,6 +115,7 @@ int validate(const bd_params *p) {
   if (p->overlap_mode == BD_OVERLAP_VERLET && p->law != BD_LAW_SHORT) return BD_ERR_UNSUPPORTED;
   if (p->max_dt_halvings < 0 || p->max_dt_halvings > 20) return BD_ERR_ARG;
   if (p->boundary < BD_BOUNDARY_WALLS || p->boundary > BD_BOUNDARY_PERIODIC) return BD_ERR_ARG;
+  if (p->placement < BD_PLACE_RSA || p->placement > BD_PLACE_LATTICE) return BD_ERR_ARG;
   if (p->boundary == BD_BOUNDARY_PERIODIC) {
     if (p->n < 16) return BD_ERR_UNSUPPORTED;
     const double L = box_side(*p);
@@ -417,7 +419,8 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     xy.resize(2 * (size_t)p.n);
     if (specs[r].xy) {
       memcpy(xy.data(), specs[r].xy, sizeof(double) * 2 * (size_t)p.n);
-    } else if (bdhost::rsa_place(p.n, p.a, RH.L - p.a, 2.0 * p.a, p.seed, xy) != 0) {
+    } else if ((p.placement == BD_PLACE_LATTICE ? bdhost::lattice_place(p.n, p.a, RH.L - p.a, 2.0 * p.a, p.seed, xy)
+                                                 : bdhost::rsa_place(p.n, p.a, RH.L - p.a, 2.0 * p.a, p.seed, xy)) != 0) {
       delete h;
       return BD_ERR_ARG;
     }
@@ -1599,6 +1602,17 @@ int bd_stage_times(bd_handle *h, int reset, double *ms, int64_t *phases) {
       h->stage_ns[k] = 0.0;
       h->stage_cnt[k] = 0;
     }
+  return BD_OK;
+}
+
+int bd_place_disks(int32_t n, double L, double a, int32_t placement, uint64_t seed, double *xy) {
+  if (n < 1 || !xy || !(a > 0) || !(L > 2.0 * a) || !isfinite(L)) return BD_ERR_ARG;
+  if (placement < BD_PLACE_RSA || placement > BD_PLACE_LATTICE) return BD_ERR_ARG;
+  std::vector<double> v;
+  const int rc = placement == BD_PLACE_LATTICE ? bdhost::lattice_place(n, a, L - a, 2.0 * a, seed, v)
+                                               : bdhost::rsa_place(n, a, L - a, 2.0 * a, seed, v);
+  if (rc != 0) return BD_ERR_ARG;
+  memcpy(xy, v.data(), sizeof(double) * 2 * (size_t)n);
   return BD_OK;
 }
 

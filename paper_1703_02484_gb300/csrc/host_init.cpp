@@ -505,6 +505,71 @@ int rsa_place(int n, double lo, double hi, double dmin, uint64_t seed, std::vect
   return 0;
 }
 
+// The paper's initial placement (Sec. 4.1): a triangular lattice over
+// [lo, hi]^2 with N* >= n sites (the widest spacing s >= dmin that gives
+// enough sites; rows s sqrt(3)/2 apart, odd rows offset by s/2), n of them
+// chosen by reservoir sampling (Vitter's algorithm R: the first n sites fill
+// the reservoir, site k >= n replaces a uniform slot j in [0, k] when j < n),
+// each moved by a uniform offset in the disk of radius (s - dmin)/2, so that
+// no two come closer than dmin and the set is in general position; an offset
+// that would leave [lo, hi] keeps the site.  Philox stream TAG_LATTICE.
+// Returns -1 when even spacing dmin gives fewer than n sites.
+int lattice_place(int n, double lo, double hi, double dmin, uint64_t seed, std::vector<double> &xy) {
+  const double W = hi - lo;
+  if (!(W > 0) || n < 1) return -1;
+  const double h3 = 0.5 * sqrt(3.0);
+  auto count = [&](double sp, int &nx0, int &nx1, int &ny) -> long long {
+    nx0 = (int)floor(W / sp) + 1;                                  // even rows
+    nx1 = W >= 0.5 * sp ? (int)floor((W - 0.5 * sp) / sp) + 1 : 0;  // odd rows
+    ny = (int)floor(W / (sp * h3)) + 1;
+    return (long long)((ny + 1) / 2) * nx0 + (long long)(ny / 2) * nx1;
+  };
+  int nx0 = 0, nx1 = 0, ny = 0;
+  if (count(dmin, nx0, nx1, ny) < n) return -1;
+  double s_lo = dmin, s_hi = std::max(dmin, W);   // count(s_lo) >= n
+  for (int it = 0; it < 100; ++it) {
+    const double mid = 0.5 * (s_lo + s_hi);
+    if (count(mid, nx0, nx1, ny) >= n) s_lo = mid; else s_hi = mid;
+  }
+  const double sp = s_lo;
+  const long long nsites = count(sp, nx0, nx1, ny);
+  auto site = [&](long long k, double &x, double &y) {
+    const long long pair = (long long)nx0 + nx1;
+    const long long r2 = k / pair, rem = k % pair;
+    const int row = (int)(2 * r2 + (rem < nx0 ? 0 : 1));
+    const int col = (int)(rem < nx0 ? rem : rem - nx0);
+    x = lo + (row & 1 ? 0.5 * sp : 0.0) + col * sp;
+    y = lo + row * sp * h3;
+  };
+  std::vector<long long> res((size_t)n);
+  for (int k = 0; k < n; ++k) res[k] = k;
+  for (long long k = n; k < nsites; ++k) {
+    bdrng::U4 r = bdrng::draw((uint32_t)(k & 0xFFFFFFFF), (int64_t)(k >> 32), seed, 0, bdrng::TAG_LATTICE);
+    const double u = ((double)r.x * 4294967296.0 + (double)r.y + 0.5) * (1.0 / 18446744073709551616.0);
+    const long long j = std::min(k, (long long)(u * (double)(k + 1)));
+    if (j < n) res[(size_t)j] = k;
+  }
+  std::sort(res.begin(), res.end());
+  const double jr = 0.5 * (sp - dmin);
+  xy.assign(2 * (size_t)n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double x, y;
+    site(res[i], x, y);
+    bdrng::U4 r = bdrng::draw((uint32_t)(res[i] & 0xFFFFFFFF), (int64_t)(res[i] >> 32), seed, 1u,
+                              bdrng::TAG_LATTICE);
+    const double u0 = ((double)r.x + 0.5) * (1.0 / 4294967296.0), u1 = ((double)r.y + 0.5) * (1.0 / 4294967296.0);
+    const double rad = jr * sqrt(u0), ang = 6.283185307179586 * u1;
+    const double jx = x + rad * cos(ang), jy = y + rad * sin(ang);
+    if (jx >= lo && jx <= hi && jy >= lo && jy <= hi) {
+      x = jx;
+      y = jy;
+    }
+    xy[2 * i] = x;
+    xy[2 * i + 1] = y;
+  }
+  return 0;
+}
+
 // minimum pair distance check with a cell grid: returns 1 if some pair is
 // closer than dmin
 int any_overlap(int n, const double *xy, double lo, double hi, double dmin) {

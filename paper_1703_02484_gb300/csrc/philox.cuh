@@ -52,7 +52,7 @@ BD_PHX_HD U4 philox(U4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
-enum : uint32_t { TAG_NOISE = 0u, TAG_PLACE = 0x504C4143u };
+enum : uint32_t { TAG_NOISE = 0u, TAG_PLACE = 0x504C4143u, TAG_LATTICE = 0x4C415454u };
 
 BD_PHX_HD U4 draw(uint32_t particle, int64_t step, uint64_t seed, uint32_t replica, uint32_t tag) {
   U4 c;

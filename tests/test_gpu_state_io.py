@@ -152,3 +152,21 @@ def test_set_state_rejects_bad_centres_and_keeps_state(case):
     assert np.array_equal(after["theta"], before["theta"])
     assert b.step(2)["steps_done"] == 2
     b.close()
+
+
+@pytest.mark.parametrize("placement", [bd.PLACE_RSA, bd.PLACE_LATTICE])
+def test_init_without_positions_uses_the_placement(placement):
+    # bd_init with no positions: the start is bd_place_disks's, rounded to the
+    # position grid (the lattice start at area fraction 0.5, Sec. 4.1)
+    cfg = workloads.CONFIGS["c3"]
+    n = 3000
+    p = bd.params_from_config(cfg, n=n)
+    p.placement = placement
+    s = bd.System(p, stream=stream())
+    q, L = s.geometry()
+    want = bd.place_disks(n, L, cfg.a, placement, seed=cfg.seed)
+    want = np.minimum(np.floor((L - cfg.a) / q) * q, np.maximum(np.ceil(cfg.a / q) * q, np.rint(want / q) * q))
+    got = s.state(want_tri=False)["xy"]
+    assert np.array_equal(got, want)
+    assert s.step(5)["steps_done"] == 5
+    s.close()
