@@ -233,7 +233,11 @@ int bd_get_replica(bd_handle *h, int32_t r, double *xy, float *theta, int32_t *t
  * take the minimum-image forms of variants 0, 2 and 3 (1 falls back to 0).
  * bd_init picks the FP32 variant and chunk size by timing the candidates on
  * the device; the environment variables BD_FORCE_VARIANT (0-3) and
- * BD_FORCE_TILES fix them. */
+ * BD_FORCE_TILES fix them (BD_NCHUNK = k: a single system's one-sided
+ * sweeps split each row of tiles into k chunks).  BD_TRI_LISTS selects the
+ * triangulation's check passes: 0 (default) the triangles of a list once a
+ * full pass has more than four triangles per thread, 1 always lists, 2
+ * always full passes. */
 int bd_get_tuning(bd_handle *h, int32_t *tiles_per_item, int32_t *variant, int32_t *n_items);
 
 /* Copy the current state to host memory ("Ensure P updated to current
