@@ -219,6 +219,14 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats);
 int bd_batch_init(int32_t R, const bd_params *p, const double *xy, const uint8_t *species,
                   const float *theta, void *stream, bd_handle **out);
 
+/* bd_step on a batched handle with per-replica counters (every replica
+ * advances the same steps in the same launches).  per_replica (R entries, or
+ * NULL) receives, for replica r: corr_iters (Algorithm 2 passes that moved a
+ * disk of r), flips (Lawson flips in r's triangulation) and inverted (its
+ * inverted triangles detected); the other fields are the batch's (steps done,
+ * overlap pairs, flip rounds, repair flips, rejection).  Returns as bd_step. */
+int bd_batch_step(bd_handle *h, int32_t nsteps, bd_step_stats *per_replica);
+
 /* One replica of a handle in its own numbering: xy (2n), theta (n), tri
  * (3*n_tri; disks 0..n-1, then its ghost points in bd_ghost_points order),
  * its disk count n and box side L.  Any output may be NULL.

@@ -94,6 +94,7 @@ SIGNATURES = [
     ("bd_rollout", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(bd_step_stats)]),
     ("bd_rollout_vjp", ctypes.c_int, [_P, _P]),
+    ("bd_batch_step", ctypes.c_int, [_P, ctypes.c_int32, _P]),
     ("bd_rollout_replay", ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     ("bd_rollout_positions", ctypes.c_int, [_P, ctypes.c_int32, _P]),
     ("bd_rollout_log_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -248,6 +249,12 @@ class System:
         _check(load().bd_get_state(self.h, _ptr(xy), _ptr(th), _ptr(sp), _ptr(tri),
                                    ctypes.byref(nt), ctypes.byref(stp)), "bd_get_state")
         return dict(xy=xy, theta=th, species=sp, tri=tri, n_tri=nt.value, step=stp.value)
+
+    def batch_step(self, nsteps=1):
+        """bd_batch_step: the per-replica stats of the call, as dicts (R entries)."""
+        arr = (bd_step_stats * self.R)()
+        _check(load().bd_batch_step(self.h, int(nsteps), ctypes.cast(arr, ctypes.c_void_p)), "bd_batch_step")
+        return [a.as_dict() for a in arr]
 
     def read_state(self, xy, theta=None, species=None):
         """Fill caller-owned arrays (C-contiguous; float64 (n, 2), float32 (n,), uint8 (n,))

@@ -755,6 +755,10 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     BD_TRY(dalloc(h, &d.xfer_sp, (size_t)std::max(1, h->n)));
     BD_TRY(dalloc(h, &d.moved, nv));
     BD_TRY(dalloc(h, &d.dmove, (size_t)np));
+    BD_TRY(dalloc(h, &d.rep_stats, 3 * (size_t)R));
+    BD_TRY(dalloc(h, &d.rep_mark, (size_t)R));
+    BD_TRY(cudaMemsetAsync(d.rep_stats, 0, 3 * (size_t)R * sizeof(long long), h->stream));
+    BD_TRY(cudaMemsetAsync(d.rep_mark, 0, (size_t)R * sizeof(unsigned), h->stream));
     if (c.any_periodic) {
       BD_TRY(dalloc(h, &d.wrap, (size_t)np));
       BD_TRY(cudaMemsetAsync(d.wrap, 0, (size_t)np, h->stream));
@@ -1423,6 +1427,28 @@ int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32
   if (n_tri) *n_tri = h->c.overlap_verlet ? 0 : h->nt;
   if (step) *step = h->step;
   return BD_OK;
+}
+
+int bd_batch_step(bd_handle *h, int32_t nsteps, bd_step_stats *per_replica) {
+  if (!h || nsteps < 0) return BD_ERR_ARG;
+  const int R = (int)h->reps.size();
+  cudaError_t e = cudaMemsetAsync(h->d.rep_stats, 0, 3 * (size_t)R * sizeof(long long), h->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  bd_step_stats tot;
+  const int rc = bd_step(h, nsteps, &tot);
+  if (per_replica) {
+    std::vector<long long> v(3 * (size_t)R);
+    e = cudaMemcpyAsync(v.data(), h->d.rep_stats, v.size() * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int r = 0; r < R; ++r) {
+      per_replica[r] = tot;
+      per_replica[r].corr_iters = v[3 * (size_t)r];
+      per_replica[r].flips = v[3 * (size_t)r + 1];
+      per_replica[r].inverted = v[3 * (size_t)r + 2];
+    }
+  }
+  return rc;
 }
 
 int bd_get_tri_shifts(bd_handle *h, int32_t r, int8_t *shifts) {

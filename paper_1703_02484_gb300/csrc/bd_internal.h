@@ -118,6 +118,9 @@ struct BdDev {
   uint8_t *xfer_sp;        //   species
   uint8_t *moved;
   float2 *dmove;           // position less prev, FP32 (disks with the moved flag; the reversal filter)
+  long long *rep_stats;    // [R][3] per-replica counters of a bd_batch_step call: correction passes that
+                           // moved the replica, Lawson flips, inverted triangles
+  unsigned *rep_mark;      // [R] the last correction pass counted for each replica
   uint8_t *wrap;           // periodic box: re-entries of the last move (bits 0-1 x, 2-3 y; 1 = -L, 3 = +L)
   double2 *disp;
   const BdRep *rep;        // [R]

@@ -366,6 +366,12 @@ __device__ __forceinline__ void push_tri(int *list, unsigned *mark, int *n, unsi
   if (add) list[base + __popc(want & ((1u << lane) - 1u))] = t;
 }
 
+// the replica of a triangle (its first disk corner; -1 if it has none)
+__device__ __forceinline__ int tri_rep(const BdDev &d, int np, const int4 &v) {
+  const int c = v.x < np ? v.x : (v.y < np ? v.y : (v.z < np ? v.z : -1));
+  return c < 0 ? -1 : d.rep_of[c];
+}
+
 __device__ __forceinline__ unsigned long long claim_key(unsigned long long epoch, int corner) {
   return (epoch << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)corner);
 }
@@ -532,6 +538,10 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         }
         const bool inverted = (fl & BD_TRI_INVERTED) != 0;
         inv += inverted ? 1 : 0;
+        if (inverted && d.rep_stats) {
+          const int rr = tri_rep(d, x.np, v);
+          if (rr >= 0) atomicAdd((unsigned long long *)&d.rep_stats[3 * rr + 2], 1ull);
+        }
         for (int k = 0; k < 3; ++k) {
           const int cc = 3 * t + k;
           const int o = vk(nn, k);
@@ -664,6 +674,10 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         }
         const bool inverted = (fl & BD_TRI_INVERTED) != 0;
         inv += inverted ? 1 : 0;
+        if (inverted && d.rep_stats) {
+          const int rr = tri_rep(d, x.np, v);
+          if (rr >= 0) atomicAdd((unsigned long long *)&d.rep_stats[3 * rr + 2], 1ull);
+        }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const int cc = 3 * t + k;
@@ -888,6 +902,14 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
                 }
                 flipped = true;
                 ++nf;
+                if (d.rep_stats) {
+                  // the four points of a flipped edge include a disk (ghost
+                  // points never move, so an edge among them stays legal); one
+                  // of the two new triangles may hold only ghost points
+                  int rr = tri_rep(d, x.np, d.tv[t]);
+                  if (rr < 0) rr = tri_rep(d, x.np, d.tv[o / 3]);
+                  if (rr >= 0) atomicAdd((unsigned long long *)&d.rep_stats[3 * rr + 1], 1ull);
+                }
               }
             }
             // claimed but not flipped: stays dirty, its edges are tested again
@@ -953,6 +975,13 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         d.prev[i] = p;
         const double2 dd = d.disp[i];
         if (PER) d.wrap[i] = 0;
+        if (dd.x != 0.0 || dd.y != 0.0) {
+          // the first disk of a replica moved by this pass counts the pass
+          const int rr = d.rep_of[i];
+          const unsigned stamp = ((unsigned)epoch << 1) | 1u;   // distinct per pass, never 0
+          if (d.rep_stats && atomicExch(&d.rep_mark[rr], stamp) != stamp)
+            atomicAdd((unsigned long long *)&d.rep_stats[3 * rr], 1ull);
+        }
         if (dd.x == 0.0 && dd.y == 0.0) {
           d.moved[i] = 0;
           if (log_pidx >= 0) d.log_pflags[(size_t)log_pidx * x.np + i] = 0;

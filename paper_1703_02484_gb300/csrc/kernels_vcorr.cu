@@ -81,6 +81,9 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
   const double sigma = c.sigma;
   const float sig2f = (float)(sigma * sigma * (1.0 + 1e-5));
   int status = 0, corr_iter = 0;
+  // launch counter (this kernel's use of the epoch word): stamps of the
+  // per-replica pass counts
+  const unsigned long long lbase = ctl->epoch;
   long long st_overlap = 0;
 
   for (;;) {
@@ -169,6 +172,13 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
         const double2 dd = d.disp[i];
         d.moved[i] = d.vc_hit[i];
         if (dd.x == 0.0 && dd.y == 0.0) continue;
+        if (d.rep_stats) {
+          // the first disk of a replica moved by this pass counts the pass
+          const int rr = d.rep_of[i];
+          const unsigned stamp = ((unsigned)(lbase * 4096ull + (unsigned long long)corr_iter) << 1) | 1u;
+          if (atomicExch(&d.rep_mark[rr], stamp) != stamp)
+            atomicAdd((unsigned long long *)&d.rep_stats[3 * rr], 1ull);
+        }
         const double2 p = d.pos[i];
         d.prev[i] = p;
         const double mag = sqrt(__dadd_rn(__dmul_rn(dd.x, dd.x), __dmul_rn(dd.y, dd.y)));
@@ -211,6 +221,7 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
     if (lead) atomicCAS(&ctl->status, 0, status);
   }
   if (lead) {
+    ctl->epoch = lbase + 1;
     ctl->st_corr_iters += corr_iter;
     ctl->st_overlap_pairs += st_overlap;
     ctl->st_barriers += b.gen;

@@ -129,3 +129,22 @@ def test_batch_mixes_walls_and_periodic_replicas():
         off += len(rep["tri"])
         alone.close()
     b.close()
+
+
+def test_batch_step_per_replica_counters():
+    # bd_batch_step: each replica's correction passes and Lawson flips equal
+    # those of the same replica run alone
+    cfgs, params, xys, sps, ths = small_batch(R=4, seed=17)
+    b = bd.System(params, np.concatenate(xys), np.concatenate(sps), np.concatenate(ths), stream=stream())
+    per = b.batch_step(6)
+    assert len(per) == 4 and all(p["steps_done"] == 6 for p in per)
+    tot_flips = 0
+    for r in range(4):
+        alone = bd.System(params[r], xys[r], sps[r], ths[r], stream=stream())
+        st = alone.step(6)
+        assert per[r]["corr_iters"] == st["corr_iters"], (r, per[r], st)
+        assert per[r]["flips"] == st["flips"], (r, per[r], st)
+        tot_flips += st["flips"]
+        alone.close()
+    assert tot_flips > 0
+    b.close()
