@@ -138,7 +138,7 @@ def record(xy0, th0, species, p, nsteps, step0=0, threads=1):
     ids = np.arange(n)
     sigma = 2.0 * p.a
     steps = []
-    tris = geometry.delaunay(xy, p.L)
+    tris = geometry.delaunay(xy, p.L, p.a)
     for t in range(nsteps):
         F = force(xy, sp, p.alpha, threads)
         y_raw, th_new = dynamics.em_move(xy, th, F, ids, step0 + t, p.seed, p.D, p.Dr, p.v0, p.dt,

@@ -79,7 +79,7 @@ def correct(xy, L, a, max_iters=10000, tris=None, record=None):
     total = 0
     while True:
         if tris is None:
-            tris = geometry.delaunay(xy, L)
+            tris = geometry.delaunay(xy, L, a)
         E = real_edges(tris, n)
         new, pairs, capped, disp = correction_pass(xy, E, sigma, a, L)
         if len(pairs) == 0:
@@ -93,7 +93,7 @@ def correct(xy, L, a, max_iters=10000, tris=None, record=None):
         xy = new
         tris = None
         if it >= max_iters:
-            return xy, geometry.delaunay(xy, L), it, total, REJ_NOT_CONVERGED
+            return xy, geometry.delaunay(xy, L, a), it, total, REJ_NOT_CONVERGED
 
 
 def close_pairs(xy, sigma, chunk=512):

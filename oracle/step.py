@@ -86,7 +86,7 @@ def _piece(xy, theta, species, step_index, p: Params, ids, tris, F, threads, rec
         return dict(xy=out, theta=th, tris=None, corr_iters=iters, overlap_pairs=pairs,
                     rejected=rej, F=F, xy_em=new)
     if tris is None:
-        tris = geometry.delaunay(xy, p.L)
+        tris = geometry.delaunay(xy, p.L, p.a)
     E0 = overlap.real_edges(tris, n)
     if len(overlap.reversed_edges(xy, new, E0)):
         return dict(xy=xy, theta=np.asarray(theta, np.float64), tris=tris, corr_iters=0,

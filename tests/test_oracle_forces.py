@@ -123,3 +123,46 @@ def test_factorised_table_matches_charges():
     np.fill_diagonal(r, np.inf)
     ref = mu[s][:, None] * np.einsum("k,ikc->ic", al[s], d / r[:, :, None] ** 3)
     assert np.allclose(F, ref, rtol=1e-11, atol=1e-14)
+
+
+# Literal values of the short-range law (WCA core 4 eps[(s/r)^12 - (s/r)^6] + eps
+# below 2^(1/6) s, Yukawa tail -eps (s/r) exp(-kappa (r - s)), s = 2a), worked
+# by hand.  Each catches one plausible slip: a wrong WCA coefficient, a missing
+# +eps shift, the WCA cut at s instead of 2^(1/6) s, a wrong Yukawa prefactor
+# (eps and kappa swapped, a missing 1/r^2 or kappa/r term).
+
+def test_short_range_contact_value():
+    # at r = s = 2, eps = kappa = 1: WCA 24/2 (2 - 1) = 12, Yukawa -2 (1/4 + 1/2) = -1.5
+    assert float(forces.short_range_magnitude(2.0, 1.0, 1.0, 2.0)) == pytest.approx(10.5, rel=1e-14)
+    # U(s) = 4 (1 - 1) + 1 - 1 = 0
+    assert abs(float(forces.short_range_potential(2.0, 1.0, 1.0, 2.0))) < 1e-15
+
+
+def test_short_range_wca_cut_and_shift():
+    # kappa = 200 makes the tail below 1e-17 beyond r = 2.2, leaving the WCA part
+    k = 200.0
+    rw = 2.0 ** (7.0 / 6.0)          # 2^(1/6) s = 2.2449...
+    # (10/11)^6 = 0.564473930, (10/11)^12 = 0.318630818:
+    # -U'(2.2) = (24/2.2)(2 x 0.318630818 - 0.564473930) = 10.9090909 x 0.072787706 = 0.79404770
+    assert float(forces.short_range_magnitude(2.2, 1.0, k, 2.0)) == pytest.approx(0.79404770, rel=2e-8)
+    # U(2.2) = 4 (0.318630818 - 0.564473930) + 1 = 0.016627552 (the +eps shift)
+    assert float(forces.short_range_potential(2.2, 1.0, k, 2.0)) == pytest.approx(0.016627552, rel=1e-7)
+    # the WCA part is exactly zero at and past 2^(1/6) s, and both force and
+    # potential are continuous there
+    for r in (rw, rw * (1 + 1e-12), 2.3, 3.0):
+        assert abs(float(forces.short_range_magnitude(r, 1.0, k, 2.0))) < 1e-15
+        assert abs(float(forces.short_range_potential(r, 1.0, k, 2.0))) < 1e-15
+    assert 0 < float(forces.short_range_magnitude(rw * (1 - 1e-9), 1.0, k, 2.0)) < 1e-6
+    assert abs(float(forces.short_range_potential(rw * (1 - 1e-9), 1.0, k, 2.0))) < 1e-15
+
+
+def test_short_range_yukawa_values():
+    # r = 4, eps = kappa = 1, s = 2: -U' = -2 e^-2 (1/16 + 1/4) = -0.625 e^-2,
+    # U = -(2/4) e^-2; e^-2 = 0.1353352832366127
+    assert float(forces.short_range_magnitude(4.0, 1.0, 1.0, 2.0)) == pytest.approx(-0.0845845520228829, rel=1e-13)
+    assert float(forces.short_range_potential(4.0, 1.0, 1.0, 2.0)) == pytest.approx(-0.06766764161830635, rel=1e-13)
+    # r = 3, eps = 2, kappa = 0.5: -U' = -(2 x 2) e^-0.5 (1/9 + 0.5/3) = -4 e^-0.5 (5/18),
+    # e^-0.5 = 0.6065306597126334
+    assert float(forces.short_range_magnitude(3.0, 2.0, 0.5, 2.0)) == pytest.approx(-0.6739229552362594, rel=1e-13)
+    # U = -2 (2/3) e^-0.5
+    assert float(forces.short_range_potential(3.0, 2.0, 0.5, 2.0)) == pytest.approx(-0.8087075462835112, rel=1e-13)
