@@ -155,6 +155,12 @@ typedef struct bd_step_stats {
   int64_t tri_visits;       /* triangles examined by the check passes (a pass after the
                                first of a move visits only the triangles near moved
                                disks, flips and overlaps) */
+  int64_t exact_tests;      /* orientation, in-circle and pair-reversal tests among disks
+                               that the FP32 filters left undecided and the exact
+                               integer path decided (near-degenerate inputs: nearly
+                               collinear or cocircular points, nearly perpendicular
+                               moves); tests with a ghost point are always exact and
+                               are not counted */
 } bd_step_stats;
 
 typedef struct bd_handle bd_handle;
@@ -197,6 +203,36 @@ int bd_init(const bd_params *p, const double *xy, const uint8_t *species, const 
  * stats->steps_done says how many steps completed), BD_ERR_DEVICE_TIMEOUT,
  * BD_ERR_CUDA, BD_ERR_ARG (nsteps < 0). */
 int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats);
+
+/* The counters of the last bd_step, bd_batch_step (the whole batch's) or
+ * bd_set_state call on h, in the form bd_step fills: for bd_set_state they
+ * describe the repair of the carried-over triangulation (inverted triangles
+ * found and repair flips, Sec. 4.3; Lawson flips; filter fall-throughs), with
+ * steps_done 0.  Errors: BD_ERR_ARG (NULL argument). */
+int bd_last_stats(bd_handle *h, bd_step_stats *stats);
+
+/* Change the caps on the device-side loops of later steps (bd_params
+ * max_corr_iters: Algorithm 2 passes per step, Sec. 4.4; max_flip_rounds:
+ * inversion-repair and Lawson flip rounds per triangulation update, Sec. 4.3).
+ * A step that reaches a cap is undone and bd_step returns
+ * BD_ERR_OVERLAP_NOT_CONVERGED or BD_ERR_FLIP_NOT_CONVERGED (repair rounds:
+ * BD_ERR_STEP_REJECTED).  Errors: BD_ERR_ARG (a cap below 1). */
+int bd_set_loop_caps(bd_handle *h, int32_t max_corr_iters, int32_t max_flip_rounds);
+
+/* Time limit of the device-side waits of h's persistent kernels (the grid
+ * barriers of the triangulation kernel and of the Verlet-list correction):
+ * a barrier that waits longer sets BD_ERR_DEVICE_TIMEOUT, every block leaves
+ * its kernel, and the call that launched it undoes the step (or the new
+ * positions of bd_set_state) from the snapshots and returns
+ * BD_ERR_DEVICE_TIMEOUT, the handle usable.  Default 2 s.
+ *   seconds       1e-3 .. 60.
+ *   hold_barrier  0 for normal use.  k > 0 makes the k-th grid barrier of every
+ *                 later launch of those kernels wait for one block more than
+ *                 the launch has, so that it runs out: a way to test the
+ *                 timeout path that faults nothing (each block gives up after
+ *                 `seconds`).  Set it back to 0 to step normally.
+ * Errors: BD_ERR_ARG, BD_ERR_CUDA. */
+int bd_set_wait_limit(bd_handle *h, double seconds, int32_t hold_barrier);
 
 /* Batched replicas (no counterpart in the paper; it serves ensembles of
  * independent systems).  R systems of possibly different N, box, law and
@@ -390,10 +426,12 @@ int bd_triangulate_periodic(int32_t n, const double *xy, double L, double *xy_gr
  * afford the device synchronisation of cudaMalloc/cudaFree, or whose device
  * footprint must be fixed when the library is loaded).
  *   n        number of disks, 1 <= n <= 65536 (larger n returns BD_ERR_ARG).
- *   xy       DEVICE pointer, 2n doubles (x0, y0, x1, y1, ...), caller-owned.
+ *   xy       DEVICE pointer, 2n doubles (x0, y0, x1, y1, ...), caller-owned,
+ *            16-byte aligned (read as pairs).
  *   species  DEVICE pointer, n bytes, 0 or non-zero (= species 1).
  *   alpha    HOST pointer, 4 doubles A[s_i][s_j] as in bd_params.alpha.
- *   F        DEVICE pointer, 2n doubles: receives F_i = sum_j A (r_i - r_j)/|r_ij|^3.
+ *   F        DEVICE pointer, 2n doubles, 16-byte aligned: receives
+ *            F_i = sum_j A (r_i - r_j)/|r_ij|^3.
  *   stream   cudaStream_t to queue on (NULL = legacy default stream); the call
  *            returns once the work is queued.
  * Allocates nothing: its scratch (about 9 MB) is a static device array that
@@ -401,7 +439,8 @@ int bd_triangulate_periodic(int32_t n, const double *xy, double L, double *xy_gr
  * looks up that array's device address (cudaGetSymbolAddress) with the device
  * current; make that first call before any stream capture.  Every call shares
  * the array: calls whose work overlaps on the GPU race and must be serialised.
- * Errors: BD_ERR_ARG (n out of range, NULL pointer), BD_ERR_CUDA. */
+ * Errors: BD_ERR_ARG (n out of range, NULL pointer, xy or F not 16-byte
+ * aligned), BD_ERR_CUDA. */
 int bd_forces_noalloc(int32_t n, const double *xy, const uint8_t *species, const double alpha[4],
                       double *F, void *stream);
 

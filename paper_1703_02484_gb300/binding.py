@@ -53,7 +53,7 @@ class bd_step_stats(ctypes.Structure):
         ("fail_item", ctypes.c_int32), ("fail_count", ctypes.c_int32),
         ("barriers", ctypes.c_int64),
         ("substeps", ctypes.c_int64), ("halvings", ctypes.c_int64),
-        ("tri_visits", ctypes.c_int64),
+        ("tri_visits", ctypes.c_int64), ("exact_tests", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -103,6 +103,9 @@ SIGNATURES = [
     ("bd_triangulate_periodic", ctypes.c_int, [ctypes.c_int32, _P, ctypes.c_double, _P, _P, _P,
                                                ctypes.POINTER(ctypes.c_int32)]),
     ("bd_struct_sizes", ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    ("bd_last_stats", ctypes.c_int, [_P, ctypes.POINTER(bd_step_stats)]),
+    ("bd_set_wait_limit", ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int32]),
+    ("bd_set_loop_caps", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("bd_free", None, [_P]),
     ("bd_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -286,6 +289,21 @@ class System:
         xy = np.ascontiguousarray(xy, dtype=np.float64)
         th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
         _check(load().bd_set_state(self.h, _ptr(xy), _ptr(th)), "bd_set_state")
+
+    def last_stats(self):
+        """Counters of the last bd_step / bd_batch_step / bd_set_state call (bd_last_stats)."""
+        st = bd_step_stats()
+        _check(load().bd_last_stats(self.h, ctypes.byref(st)), "bd_last_stats")
+        return st.as_dict()
+
+    def set_loop_caps(self, max_corr_iters=1000, max_flip_rounds=4096):
+        """bd_set_loop_caps: caps on correction passes and flip rounds of later steps."""
+        _check(load().bd_set_loop_caps(self.h, int(max_corr_iters), int(max_flip_rounds)), "bd_set_loop_caps")
+
+    def set_wait_limit(self, seconds=2.0, hold_barrier=0):
+        """bd_set_wait_limit: time limit of the device-side barrier waits; hold_barrier > 0
+        makes that barrier of every later launch run out (tests of the timeout path)."""
+        _check(load().bd_set_wait_limit(self.h, float(seconds), int(hold_barrier)), "bd_set_wait_limit")
 
     def forces(self):
         F = np.zeros((self.n, 2), dtype=np.float64)

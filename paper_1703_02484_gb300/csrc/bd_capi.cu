@@ -755,10 +755,16 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     BD_TRY(dalloc(h, &d.xfer_sp, (size_t)std::max(1, h->n)));
     BD_TRY(dalloc(h, &d.moved, nv));
     BD_TRY(dalloc(h, &d.dmove, (size_t)np));
-    BD_TRY(dalloc(h, &d.rep_stats, 3 * (size_t)R));
-    BD_TRY(dalloc(h, &d.rep_mark, (size_t)R));
-    BD_TRY(cudaMemsetAsync(d.rep_stats, 0, 3 * (size_t)R * sizeof(long long), h->stream));
-    BD_TRY(cudaMemsetAsync(d.rep_mark, 0, (size_t)R * sizeof(unsigned), h->stream));
+    // per-replica counters only for batches: a single system's are the
+    // call's own counters, and its kernels then skip the per-replica atomics
+    d.rep_stats = nullptr;
+    d.rep_mark = nullptr;
+    if (R > 1) {
+      BD_TRY(dalloc(h, &d.rep_stats, 3 * (size_t)R));
+      BD_TRY(dalloc(h, &d.rep_mark, (size_t)R));
+      BD_TRY(cudaMemsetAsync(d.rep_stats, 0, 3 * (size_t)R * sizeof(long long), h->stream));
+      BD_TRY(cudaMemsetAsync(d.rep_mark, 0, (size_t)R * sizeof(unsigned long long), h->stream));
+    }
     if (c.any_periodic) {
       BD_TRY(dalloc(h, &d.wrap, (size_t)np));
       BD_TRY(cudaMemsetAsync(d.wrap, 0, (size_t)np, h->stream));
@@ -988,13 +994,47 @@ void add_stage_times(bd_handle *h) {
 
 int finish_status(bd_handle *h, int status) {
   // clear the sticky status so the handle keeps working from the last good
-  // state; after a timed-out barrier also reset the barrier words
+  // state; after a timed-out barrier the kernel left without undoing its
+  // step: undo it from the snapshots, and reset the barrier words
   cudaStream_t st = h->stream;
-  if (status == BD_ERR_DEVICE_TIMEOUT) cudaMemsetAsync(h->d.ctl, 0, offsetof(BdCtl, epoch), st);
+  if (status == BD_ERR_DEVICE_TIMEOUT) {
+    bd_launch_restore_step(h->d, h->c, st);
+    cudaMemsetAsync(h->d.ctl, 0, offsetof(BdCtl, epoch), st);
+  }
   cudaMemsetAsync(&h->d.ctl->cnt[0][0], 0, sizeof(h->d.ctl->cnt), st);
   cudaMemsetAsync(&h->d.ctl->status, 0, sizeof(int), st);
   cudaStreamSynchronize(st);
   return status;
+}
+
+// the counters of the call whose control block read_ctl fetched last, as
+// bd_step reports them (h->last_stats, returned by bd_last_stats)
+void fill_stats(bd_handle *h, int status, int64_t halvings) {
+  const BdCtl &k = *h->h_ctl;
+  bd_step_stats &o = h->last_stats;
+  memset(&o, 0, sizeof(o));
+  o.steps_done = k.st_steps;
+  o.corr_iters = k.st_corr_iters;
+  o.overlap_pairs = k.st_overlap_pairs;
+  o.flip_rounds = k.st_flip_rounds;
+  o.flips = k.st_flips;
+  o.repair_flips = k.st_repair_flips;
+  o.inverted = k.st_inverted;
+  o.max_corr_iters = k.st_max_corr_iters;
+  o.verlet_rebuilds = (int32_t)k.st_verlet_rebuilds;
+  o.fail_phase = status ? k.st_fail_phase : 0;
+  o.fail_item = k.st_fail_item;
+  o.fail_count = k.st_fail_count;
+  o.barriers = k.st_barriers;
+  o.rejected = status != 0;
+  o.substeps = k.st_substeps;
+  o.tri_visits = k.st_tri_visits;
+  o.exact_tests = k.st_exact;
+  o.halvings = halvings;
+  double mo;
+  unsigned long long bits = k.st_max_overlap_bits;
+  memcpy(&mo, &bits, sizeof(mo));
+  o.max_overlap = mo;
 }
 
 }  // namespace bdcapi
@@ -1371,29 +1411,9 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
   const BdCtl &k = *h->h_ctl;
   add_stage_times(h);
   h->step = step_base + k.st_steps;
-  if (stats) {
-    stats->steps_done = k.st_steps;
-    stats->corr_iters = k.st_corr_iters;
-    stats->overlap_pairs = k.st_overlap_pairs;
-    stats->flip_rounds = k.st_flip_rounds;
-    stats->flips = k.st_flips;
-    stats->repair_flips = k.st_repair_flips;
-    stats->inverted = k.st_inverted;
-    stats->max_corr_iters = k.st_max_corr_iters;
-    stats->verlet_rebuilds = (int32_t)k.st_verlet_rebuilds;
-    stats->fail_phase = status ? k.st_fail_phase : 0;
-    stats->fail_item = k.st_fail_item;
-    stats->fail_count = k.st_fail_count;
-    stats->barriers = k.st_barriers;
-    stats->rejected = status != 0;
-    stats->substeps = k.st_substeps;
-    stats->tri_visits = k.st_tri_visits;
-    stats->halvings = halvings;
-    double mo;
-    unsigned long long bits = k.st_max_overlap_bits;
-    memcpy(&mo, &bits, sizeof(mo));
-    stats->max_overlap = mo;
-  }
+  if (k.status) status = k.status;
+  fill_stats(h, status, halvings);
+  if (stats) *stats = h->last_stats;
   if (k.status) return finish_status(h, k.status);
   return status;
 }
@@ -1432,9 +1452,15 @@ int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32
 int bd_batch_step(bd_handle *h, int32_t nsteps, bd_step_stats *per_replica) {
   if (!h || nsteps < 0) return BD_ERR_ARG;
   const int R = (int)h->reps.size();
+  bd_step_stats tot;
+  if (!h->d.rep_stats) {
+    // one replica: its counters are the call's
+    const int rc = bd_step(h, nsteps, &tot);
+    if (per_replica) per_replica[0] = tot;
+    return rc;
+  }
   cudaError_t e = cudaMemsetAsync(h->d.rep_stats, 0, 3 * (size_t)R * sizeof(long long), h->stream);
   if (e != cudaSuccess) return cuda_fail(e);
-  bd_step_stats tot;
   const int rc = bd_step(h, nsteps, &tot);
   if (per_replica) {
     std::vector<long long> v(3 * (size_t)R);
@@ -1538,8 +1564,41 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
   if (e != cudaSuccess) return cuda_fail(e);
   int rc = read_ctl(h);   // synchronises the stream
   if (rc) return rc;
+  fill_stats(h, h->h_ctl->status, 0);
   if (h->h_ctl->status) return finish_status(h, h->h_ctl->status);
   return BD_OK;
+}
+
+int bd_last_stats(bd_handle *h, bd_step_stats *stats) {
+  if (!h || !stats) return BD_ERR_ARG;
+  *stats = h->last_stats;
+  return BD_OK;
+}
+
+int bd_set_loop_caps(bd_handle *h, int32_t max_corr_iters, int32_t max_flip_rounds) {
+  if (!h || max_corr_iters < 1 || max_flip_rounds < 1) return BD_ERR_ARG;
+  // the caps are kernel arguments: the next step recaptures its graph
+  h->c.max_corr_iters = max_corr_iters;
+  h->c.max_flip_rounds = max_flip_rounds;
+  for (auto &r : h->reps) {
+    r.p.max_corr_iters = max_corr_iters;
+    r.p.max_flip_rounds = max_flip_rounds;
+  }
+  return BD_OK;
+}
+
+int bd_set_wait_limit(bd_handle *h, double seconds, int32_t hold_barrier) {
+  if (!h || !(seconds >= 1e-3 && seconds <= 60.0) || hold_barrier < 0) return BD_ERR_ARG;
+  // pinned host words: the copies are queued on the handle's stream
+  h->h_ctl->bar_hold = (unsigned)hold_barrier;
+  h->h_ctl->bar_limit_ns = (unsigned long long)(seconds * 1e9);
+  cudaError_t e = cudaMemcpyAsync(&h->d.ctl->bar_hold, &h->h_ctl->bar_hold, sizeof(unsigned),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h->d.ctl->bar_limit_ns, &h->h_ctl->bar_limit_ns, sizeof(unsigned long long),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? BD_OK : cuda_fail(e);
 }
 
 int bd_compute_forces(bd_handle *h, double *F) {

@@ -65,6 +65,7 @@ struct bd_handle {
   float *hs_theta = nullptr;
   int4 *hs_tv = nullptr, *hs_tn = nullptr;
   int *hs_vt = nullptr;
+  bd_step_stats last_stats = {};   // counters of the last bd_step / bd_batch_step / bd_set_state
   double stage_ns[5] = {0, 0, 0, 0, 0};   // triangulation-kernel stage times since the last reset
   int64_t stage_cnt[5] = {0, 0, 0, 0, 0};
 };
@@ -79,6 +80,7 @@ cudaError_t reset_stats(bd_handle *h);     // zero the per-call statistics
 int finish_status(bd_handle *h, int status);
 void rollout_release(bd_handle *h);        // free the rollout buffers
 void add_stage_times(bd_handle *h);        // accumulate the stage times of the last read_ctl
+void fill_stats(bd_handle *h, int status, int64_t halvings);   // h->last_stats from h_ctl
 }  // namespace bdcapi
 
 // adjoint kernels (adjoint.cu)

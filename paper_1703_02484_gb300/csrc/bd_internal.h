@@ -59,6 +59,8 @@ struct BdCtl {
   long long st_verlet_rebuilds;
   long long st_substeps;           // pieces of halved steps that completed
   long long st_tri_visits;         // triangles examined by the check passes
+  long long st_exact;              // orientation, in-circle and reversal tests that the FP32
+                                   // filters left undecided (decided by the exact grid path)
   long long st_barriers;           // grid barriers passed by the triangulation kernel
   int st_fail_item;                // an offending triangle (repair) or edge corner (reversal)
   int st_fail_count;               // inverted triangles / reversed edges at the failure
@@ -77,6 +79,13 @@ struct BdCtl {
                                    // by the triangulation kernel's shift pass; not a statistic)
   int act_n[3];                    // lengths of the rotating triangle lists (zeroed at kernel exit)
   unsigned act_gen;                // next list generation (grows across launches)
+  // set by the host (bd_set_wait_limit), kept across calls: the time limit of a
+  // grid barrier wait (0 = BD_BARRIER_TIMEOUT_NS) and, for tests of the
+  // timeout path, the generation of the barrier (1 = the first of a launch) that
+  // waits for one block more than the launch has (0 = none)
+  unsigned bar_hold;
+  unsigned bar_pad;
+  unsigned long long bar_limit_ns;
 };
 
 // counter slots within BdCtl::cnt[phase % 4]
@@ -120,7 +129,8 @@ struct BdDev {
   float2 *dmove;           // position less prev, FP32 (disks with the moved flag; the reversal filter)
   long long *rep_stats;    // [R][3] per-replica counters of a bd_batch_step call: correction passes that
                            // moved the replica, Lawson flips, inverted triangles
-  unsigned *rep_mark;      // [R] the last correction pass counted for each replica
+  unsigned long long *rep_mark;   // [R] the last correction pass counted for each replica (a stamp
+                                  // unique to the pass: never repeats within a handle's life)
   uint8_t *wrap;           // periodic box: re-entries of the last move (bits 0-1 x, 2-3 y; 1 = -L, 3 = +L)
   double2 *disp;
   const BdRep *rep;        // [R]
@@ -216,5 +226,10 @@ cudaError_t bd_launch_overlap_verlet(const BdDev &d, const BdConst &c, cudaStrea
                                      int advance = 1);
 // a halved step completed: advance the device step counter and the step count
 cudaError_t bd_launch_advance_step(const BdDev &d, cudaStream_t s);
+// after a timed-out grid barrier: undo the step (or the new positions of
+// bd_set_state) from the snapshots the persistent kernels take, as their own
+// failure path does, and clear the flip claims and list marks the abandoned
+// launch may have left
+cudaError_t bd_launch_restore_step(const BdDev &d, const BdConst &c, cudaStream_t s);
 int bd_vcorr_grid_for(int work_items, int *grid, int *block);
 int bd_force_launches(int variant);   // kernel launches of one long-range force evaluation

@@ -1,8 +1,9 @@
 // Grid-wide barrier and block-level helpers of the persistent kernels
 // (triangulation maintenance, Verlet-list overlap correction).  The kernels
 // are launched cooperatively (every block resident), and every wait is
-// bounded: a barrier that waits longer than BD_BARRIER_TIMEOUT_NS sets
-// BD_ERR_DEVICE_TIMEOUT and every block leaves.
+// bounded: a barrier that waits longer than its limit (BD_BARRIER_TIMEOUT_NS,
+// or the limit the host set in the control block) sets BD_ERR_DEVICE_TIMEOUT
+// and every block leaves.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -53,22 +54,27 @@ static __device__ bool grid_sync(BdCtl *ctl, Bar &b, int *bc = nullptr) {
       ok = 0;
     } else {
       unsigned target = b.gen + 1;
+      // host-set limit and test hold (read once per barrier by one thread)
+      const unsigned long long lim_set = *(volatile const unsigned long long *)&ctl->bar_limit_ns;
+      const unsigned long long limit = lim_set ? lim_set : BD_BARRIER_TIMEOUT_NS;
+      const unsigned hold = *(volatile const unsigned *)&ctl->bar_hold;
+      const unsigned last = gridDim.x - 1u + (hold != 0u && hold == target ? 1u : 0u);
       __threadfence();
       unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-      if (arrived == gridDim.x - 1) {
+      if (arrived == last) {
         atomicExch(&ctl->bar_count, 0u);
         __threadfence();
         atomicExch(&ctl->bar_gen, target);
       } else {
         // spin hot for a while (barriers are short), then back off; give up
-        // after BD_BARRIER_TIMEOUT_NS
+        // after the time limit
         unsigned long long t0 = 0;
         unsigned it = 0;
         while (ld_acquire(&ctl->bar_gen) != target) {
           ++it;
           if (it < 4096u) continue;
           if (t0 == 0) t0 = gtimer();
-          if ((it & 63u) == 0 && gtimer() - t0 > BD_BARRIER_TIMEOUT_NS) {
+          if ((it & 63u) == 0 && gtimer() - t0 > limit) {
             atomicExch(&ctl->status, BD_ERR_DEVICE_TIMEOUT);
             ok = 0;
             break;

@@ -114,6 +114,11 @@ __device__ __noinline__ int incircle_lifted(long long ax, long long ay, long lon
   return bdpred::incircle_int(ax, ay, bx, by, cx, cy, px, py);
 }
 
+// a test the FP32 filter could not decide (rare: near-degenerate inputs)
+__device__ __forceinline__ void count_exact(const Ctx &x) {
+  atomicAdd((unsigned long long *)&x.d.ctl->st_exact, 1ull);
+}
+
 // the filters on preloaded FP32 pairs (filt: all corners are disks, whose
 // pairs are loaded; ghost points have none)
 __device__ __forceinline__ int orient_pre(const Ctx &x, bool filt, const float4 &wa, const float4 &wb,
@@ -126,6 +131,7 @@ __device__ __forceinline__ int orient_pre(const Ctx &x, bool filt, const float4 
     const float bound = 1.5e-6f * __fadd_rn(fabsf(l), fabsf(r));
     if (det > bound) return 1;
     if (-det > bound) return -1;
+    count_exact(x);
   }
   return orient_exact(x.d.pos, x.g, a, b, c);
 }
@@ -150,6 +156,7 @@ __device__ __forceinline__ int incircle_pre(const Ctx &x, bool filt, const float
     const float bound = 4e-6f * perm;
     if (det > bound) return 1;
     if (-det > bound) return -1;
+    count_exact(x);
   }
   return incircle_exact(x.d.pos, x.g, a, b, c, p);
 }
@@ -579,6 +586,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
                                                   __fadd_rn(__fmul_rn(mw.x, mw.x), __fmul_rn(mw.y, mw.y))));
               const float bound = 4e-6f * S;
               dec = dot > bound ? -1 : (-dot > bound ? 1 : 0);
+              if (dec == 0) count_exact(x);
             }
             int ox = rsx, oy = rsy;
             if (dec == 0) {
@@ -708,7 +716,14 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
                                         __fadd_rn(__fadd_rn(__fmul_rn(mu.x, mu.x), __fmul_rn(mu.y, mu.y)),
                                                   __fadd_rn(__fmul_rn(mw.x, mw.x), __fmul_rn(mw.y, mw.y))));
               const float bound = 4e-6f * S;
-              rev = dot > bound ? false : (-dot > bound ? true : reversed_exact(x, u, w, 0, 0, 0, 0, 0));
+              if (dot > bound) {
+                rev = false;
+              } else if (-dot > bound) {
+                rev = true;
+              } else {
+                count_exact(x);
+                rev = reversed_exact(x, u, w, 0, 0, 0, 0, 0);
+              }
             }
             if (rev) {
               ++rej;
@@ -978,7 +993,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         if (dd.x != 0.0 || dd.y != 0.0) {
           // the first disk of a replica moved by this pass counts the pass
           const int rr = d.rep_of[i];
-          const unsigned stamp = ((unsigned)epoch << 1) | 1u;   // distinct per pass, never 0
+          const unsigned long long stamp = epoch;   // distinct per pass (grows across launches), never 0
           if (d.rep_stats && atomicExch(&d.rep_mark[rr], stamp) != stamp)
             atomicAdd((unsigned long long *)&d.rep_stats[3 * rr], 1ull);
         }
@@ -1092,6 +1107,52 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
     if (!status && mode == 0) ctl->step_dev += 1;
   }
   block_exit(ctl);
+}
+
+// Undo a step whose persistent kernel left at a timed-out barrier (the
+// kernel's own failure path did not run).  Every block of such a launch ends
+// its first pass -- the one that takes the snapshot -- before it reaches any
+// barrier, so the snapshot is whole; positions and directions come from
+// pos0 / theta0 (the step start, or the positions before bd_set_state).
+// bd_launch_restore_step runs it (the header above the launcher declares it).
+__global__ void k_restore_step(BdDev d, BdConst c) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  for (int i = tid; i < c.np; i += nth) {
+    if (d.ext_id[i] < 0) continue;
+    const double2 p0 = d.pos0[i];
+    d.pos[i] = p0;
+    d.prev[i] = p0;
+    d.work[i] = split_pos(p0);
+    d.theta[i] = d.theta0[i];
+    d.disp[i] = make_double2(0.0, 0.0);
+    d.moved[i] = 0;
+  }
+  if (!c.overlap_verlet) {
+    for (int t = tid; t < c.nt; t += nth) {
+      const int4 vs = d.tv_snap[t];
+      d.tv[t] = vs;
+      d.tn[t] = d.tn_snap[t];
+      d.vt[vs.x] = 3 * t;
+      d.vt[vs.y] = 3 * t + 1;
+      d.vt[vs.z] = 3 * t + 2;
+      // the abandoned launch did not publish the claim epochs and list
+      // generations it used (the next launch starts from the same ones):
+      // clear its claims (0 matches no epoch) and list marks (0 matches no
+      // generation after the first launch)
+      d.claim[t] = 0ull;
+      for (int l = 0; l < 3; ++l) d.act_mark[(size_t)l * c.nt + t] = 0u;
+    }
+  }
+}
+
+cudaError_t bd_launch_restore_step(const BdDev &d, const BdConst &c, cudaStream_t s) {
+  const int work = c.np > c.nt ? c.np : c.nt;
+  int blocks = (work + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 4096) blocks = 4096;
+  k_restore_step<<<blocks, 256, 0, s>>>(d, c);
+  return cudaGetLastError();
 }
 
 int bd_dt_grid_for(int work_items, int *grid, int *block) {

@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
         if (d.rep_stats) {
           // the first disk of a replica moved by this pass counts the pass
           const int rr = d.rep_of[i];
-          const unsigned stamp = ((unsigned)(lbase * 4096ull + (unsigned long long)corr_iter) << 1) | 1u;
+          // (launch, pass): launches are counted in 32 bits, passes below 2^31
+          const unsigned long long stamp = ((lbase + 1ull) << 32) | (unsigned long long)corr_iter;
           if (atomicExch(&d.rep_mark[rr], stamp) != stamp)
             atomicAdd((unsigned long long *)&d.rep_stats[3 * rr], 1ull);
         }

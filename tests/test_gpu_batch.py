@@ -1,5 +1,7 @@
 """GPU tests of batched replicas: R systems of different size, box and law
 advanced by one launch sequence per step."""
+from dataclasses import replace
+
 import numpy as np
 import pytest
 
@@ -148,3 +150,49 @@ def test_batch_step_per_replica_counters():
         alone.close()
     assert tot_flips > 0
     b.close()
+
+
+def test_batch_step_per_replica_counters_verlet_correction():
+    # Algorithm 2 over the Verlet lists (no triangulation): each replica's
+    # correction passes counted on the device equal its passes run alone; no
+    # triangulation, so no inverted triangles and no flips
+    R = 4
+    cfgs = [replace(workloads.CONFIGS["c3"], n=int(n), rho=0.45, seed=5) for n in (900, 1500, 2200, 700)]
+    params, xys, sps, ths = [], [], [], []
+    for r, cfg in enumerate(cfgs):
+        L = workloads.box_side(cfg.n, cfg.rho)
+        xy = workloads.near_contact_state(cfg.n, L, cfg.a, seed=40 + r, rho=cfg.rho)
+        _, sp, th = workloads.initial_state(cfg)
+        p = bd.params_from_config(cfg)
+        p.replica = r
+        p.overlap_mode = bd.OVERLAP_VERLET
+        params.append(p)
+        xys.append(xy)
+        sps.append(sp)
+        ths.append(th)
+    b = bd.System(params, np.concatenate(xys), np.concatenate(sps), np.concatenate(ths), stream=stream())
+    per = b.batch_step(5)
+    assert len(per) == R and all(p["steps_done"] == 5 for p in per)
+    tot = 0
+    for r in range(R):
+        alone = bd.System(params[r], xys[r], sps[r], ths[r], stream=stream())
+        st = alone.step(5)
+        assert per[r]["corr_iters"] == st["corr_iters"], (r, per[r], st)
+        assert per[r]["inverted"] == st["inverted"] == 0
+        assert per[r]["flips"] == st["flips"] == 0
+        tot += st["corr_iters"]
+        alone.close()
+    assert tot > 0
+    b.close()
+
+
+def test_single_replica_batch_step_counters():
+    # a batch of one replica keeps no per-replica device counters: its counters
+    # are the call's own
+    cfgs, params, xys, sps, ths = small_batch(R=1, seed=23)
+    b = bd.System(params, xys[0], sps[0], ths[0], stream=stream())
+    per = b.batch_step(4)
+    alone = bd.System(params[0], xys[0], sps[0], ths[0], stream=stream())
+    st = alone.step(4)
+    assert per[0]["corr_iters"] == st["corr_iters"] and per[0]["flips"] == st["flips"]
+    assert per[0]["steps_done"] == 4
