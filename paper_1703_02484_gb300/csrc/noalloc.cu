@@ -154,30 +154,40 @@ __global__ void k_na_sum(NaArgs g) {
 
 std::mutex g_na_mutex;
 void *g_na_ptr[256] = {nullptr};
+int g_na_sms[256] = {0};
 
 }  // namespace
 
 extern "C" int bd_forces_noalloc(int32_t n, const double *xy, const uint8_t *species,
                                  const double alpha[4], double *F, void *stream) {
   if (n < 1 || n > BD_NOALLOC_MAX_N || !xy || !species || !alpha || !F) return BD_ERR_ARG;
+  // positions and forces are read and written as 16-byte double2 pairs
+  if (((uintptr_t)xy & 15u) != 0 || ((uintptr_t)F & 15u) != 0) return BD_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return BD_ERR_CUDA;
   void *base = nullptr;
+  int sms = 0;
   {
     // once per device, with that device current: the device address of the
-    // scratch array (its host-side name is only a stand-in)
+    // scratch array (its host-side name is only a stand-in) and the SM count
     std::lock_guard<std::mutex> lk(g_na_mutex);
     if (!g_na_ptr[dev]) {
       void *p = nullptr;
+      int k = 0;
       if (cudaGetSymbolAddress(&p, bd_noalloc_scratch) != cudaSuccess || !p) return BD_ERR_CUDA;
+      if (cudaDeviceGetAttribute(&k, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || k < 1)
+        return BD_ERR_CUDA;
+      g_na_sms[dev] = k;
       g_na_ptr[dev] = p;
     }
     base = g_na_ptr[dev];
+    sms = g_na_sms[dev];
   }
   NaArgs g;
   g.n = n;
   int iblocks = (n + BD_NA_THREADS * BD_NA_IPT - 1) / (BD_NA_THREADS * BD_NA_IPT);
-  int nchunk = (2 * 152 + iblocks - 1) / iblocks;
+  // j chunks so that the grid fills about two waves of one block per SM
+  int nchunk = (2 * sms + iblocks - 1) / iblocks;
   nchunk = nchunk < 1 ? 1 : (nchunk > BD_NOALLOC_MAX_CHUNKS ? BD_NOALLOC_MAX_CHUNKS : nchunk);
   g.nchunk = nchunk;
   g.xy = (const double2 *)xy;
