@@ -140,57 +140,46 @@ def rank_params(bd, cfg, rank, modes=()):
 def run_reference(args):
     """The oracle (plain FP64 CPU restatement) on the same workload, host cores.
 
-    Each step is a bounded sample of the N = 1e5 step: exact all-pairs FP64
-    forces for `fsample` disks (time scaled by N / fsample), and the
-    Euler-Maruyama + Delaunay + overlap-correction stages on the disks of one
-    quarter of the box taken as a system of its own (time scaled by N / its
-    size; those stages are O(N))."""
+    Every timed step is one whole oracle step of the N = 1e5 system (exact
+    all-pairs FP64 forces with OpenMP over all host cores, Euler-Maruyama,
+    Delaunay triangulations and overlap correction), the state carried from
+    step to step.  At about 3.5 s a step the run is bounded: at most 20 timed
+    steps and 2 warm-up steps, and the line's `steps` / `warmup` say how many
+    ran."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    from oracle import forces as of
     from oracle import step as ostep
     from paper_1703_02484_gb300 import workloads
     cfg = workloads.CONFIGS["n1e5"]
     xy, sp, th = workloads.initial_state(cfg)
-    L = cfg.L
     cores = os.cpu_count() or 1
-    fsample = 1000
-    half = 0.5 * L
-    win = (xy[:, 0] < half - cfg.a) & (xy[:, 1] < half - cfg.a)
-    wxy, wsp, wth = xy[win].copy(), sp[win].copy(), th[win].copy()
-    nw = len(wxy)
-    op = ostep.Params(L=half, a=cfg.a, law=cfg.law, alpha=cfg.alpha, D=cfg.D, Dr=cfg.Dr,
+    op = ostep.Params(L=cfg.L, a=cfg.a, law=cfg.law, alpha=cfg.alpha, D=cfg.D, Dr=cfg.Dr,
                       v0=cfg.v0, dt=cfg.dt, seed=cfg.seed)
-    rng = np.random.default_rng(0)
-
-    def one(k, wxy, wth):
-        i0 = int(rng.integers(0, cfg.n - fsample))
-        t0 = time.perf_counter()
-        Fs = of.long_range(xy, sp, cfg.alpha, idx=np.arange(i0, i0 + fsample), threads=cores)
-        t_f = (time.perf_counter() - t0) * (cfg.n / fsample)
-        F = np.zeros((nw, 2))
-        F[: min(nw, fsample)] = Fs[: min(nw, fsample)]
-        t1 = time.perf_counter()
-        r = ostep.step(wxy, wth, wsp, k, op, F=F)
-        t_rest = (time.perf_counter() - t1) * (cfg.n / nw)
-        return r["xy"], r["theta"], t_f + t_rest
-
-    for k in range(args.warmup):
-        one(k, wxy, wth)
-    total = 0.0
-    for k in range(args.steps):
-        wxy, wth, t = one(k, wxy, wth)
-        total += t
-    ms = 1e3 * total / max(1, args.steps)
+    steps = max(1, min(args.steps, 20))
+    warm = min(args.warmup, 2)
+    th = th.astype(np.float64)
+    k = 0
+    for _ in range(warm):
+        r = ostep.step(xy, th, sp, k, op, threads=cores)
+        xy, th, k = r["xy"], r["theta"], k + 1
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        r = ostep.step(xy, th, sp, k, op, threads=cores)
+        if r["rejected"]:
+            raise RuntimeError("oracle step %d rejected" % k)
+        xy, th, k = r["xy"], r["theta"], k + 1
+    total = time.perf_counter() - t0
+    ms = 1e3 * total / steps
     value = cfg.n / (ms / 1e3)
-    sample = ("per step: exact all-pairs FP64 forces for %d of %d disks (time x N/%d) and the "
-              "Euler-Maruyama, Delaunay rebuilds and overlap correction of the %d disks of one "
-              "quarter of the box (time x N/%d)" % (fsample, cfg.n, fsample, nw, nw))
+    sample = ("%d whole FP64 oracle steps of the N=%d workload, state carried (all-pairs forces "
+              "with OpenMP over %d threads, Delaunay rebuilds and overlap correction), after %d "
+              "warm-up steps" % (steps, cfg.n, cores, warm))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": cfg.n, "seed": cfg.seed},
+            "config": {"workload": WORKLOAD, "N": cfg.n, "seed": cfg.seed, "same_config": True,
+                       "steps_requested": args.steps, "warmup_requested": args.warmup},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -241,11 +230,10 @@ def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind, v
                          "device-clock stage timers; %s" % (pk_kind, note)}
 
 
-def cpu_baseline(cfg, xy, sp, th, periodic=False):
-    """One full oracle step of the workload (exact all-pairs forces on all host
-    cores), the oracle as it stands; and a one-core figure: the same step with
-    its force sum timed on one thread for a sample of disks, scaled to all."""
-    from oracle import forces as of
+def cpu_baseline(cfg, xy, sp, th, periodic=False, one_core=True):
+    """The oracle as it stands, timed on the host cores: one whole step of the
+    workload with its all-pairs force sum in OpenMP over every core, and (for
+    `value_1core`) the same step on one thread."""
     from oracle import step as ostep
     cores = os.cpu_count() or 1
     L = float(np.float32(cfg.L)) if periodic else cfg.L
@@ -255,24 +243,15 @@ def cpu_baseline(cfg, xy, sp, th, periodic=False):
     ostep.step(xy, th, sp, 0, op, threads=cores)
     t = time.perf_counter() - t0
     out = {"value": cfg.n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": "one full FP64 oracle step of the N=1e5 workload (all-pairs forces with "
-                     "OpenMP over %d threads, Delaunay rebuilds and overlap correction): %.2f s" % (cores, t)}
-    if cfg.law == 1 and cores > 1:
-        # the force sum of m disks on one thread and on all, scaled by N / m:
-        # the one-core step replaces the latter by the former
-        m = min(cfg.n, 2000)
-        Lp = L if periodic else None
+           "sample": "one whole FP64 oracle step of the N=%d workload (all-pairs forces with "
+                     "OpenMP over %d threads, Delaunay rebuilds and overlap correction): %.2f s"
+                     % (cfg.n, cores, t)}
+    if one_core and cores > 1:
         t0 = time.perf_counter()
-        of.long_range(xy, sp, cfg.alpha, idx=np.arange(m), threads=1, L=Lp)
-        t1 = (time.perf_counter() - t0) * cfg.n / m
-        t0 = time.perf_counter()
-        of.long_range(xy, sp, cfg.alpha, idx=np.arange(m), threads=cores, L=Lp)
-        tc = (time.perf_counter() - t0) * cfg.n / m
-        t_one = t - tc + t1
-        out["value_1core"] = cfg.n / t_one
-        out["sample"] += ("; one core: the force sum of %d disks on 1 and on %d threads, scaled by N/%d "
-                          "(%.2f s and %.2f s), replaces the all-core force time in the step: %.2f s"
-                          % (m, cores, m, t1, tc, t_one))
+        ostep.step(xy, th, sp, 0, op, threads=1)
+        t1 = time.perf_counter() - t0
+        out["value_1core"] = cfg.n / t1
+        out["sample"] += "; the same step on one thread: %.2f s" % t1
     return out
 
 

@@ -118,14 +118,21 @@ __device__ __forceinline__ u64 min_image2_cmp(u64 dx, float Lf, float hLf) {
 // tell whether any pair component can exceed L/2, and only such tiles (those
 // near the block's antipode) take the per-pair minimum image: 3 packed
 // operations per coordinate, or compares when the tile holds inert slots.
-template <int NW, int NP, int NJ, bool COMB, int UR, bool PER>
-__global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) {
+// STAGE (walls only): 0 stage the next j tile through registers (re-centred
+// on the way to shared memory); 1 copy it raw with cp.async (no registers held
+// across the tile's arithmetic) and re-centre each j as it is read.
+// ACC: the i side's sum over an item's tiles, 2 in (hi, lo) float-float, 1 in
+// FP32 (half the registers).
+template <int NW, int NP, int NJ, bool COMB, int UR, bool PER, int STAGE = 0, int ACC = 2>
+__device__ __forceinline__ void force_long_sym_body(const BdDev &d, const BdConst &c) {
+  static_assert(!(PER && STAGE), "the periodic form stages exact minimum images through registers");
   if (ctl_failed(d.ctl)) return;
   constexpr int T = NW * 32;         // threads
   constexpr int NQ = 2 * NP;         // disks i per thread
   constexpr int NS = BD_TJ / T;      // j disks each thread stages per tile
   static_assert(BD_SB == T * NQ, "a block is BD_SB disks");
-  __shared__ float2 sjp[2][BD_TJ];   // j positions, re-centred (PER: the hi parts)
+  __shared__ float2 sjp[2][STAGE ? 1 : BD_TJ];   // j positions, re-centred (PER: the hi parts)
+  __shared__ __align__(16) float4 sraw[2][STAGE ? BD_TJ : 1];   // STAGE 1: j as stored (x_hi, y_hi, x_lo, y_lo)
   __shared__ float2 sjl[2][BD_TJ];   // PER: the lo parts
   __shared__ float2 shw[NW][BD_TJ];  // per-warp j-side sums of the current tile
   const int4 item = d.sitems[blockIdx.x];
@@ -158,7 +165,7 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
   __shared__ int sipad[NW];          //      and whether they include inert slots
   u64 xi2[NP], yi2[NP], ax2[NP], ay2[NP];
   u64 xl2[NP], yl2[NP];              // PER: lo parts of the disks i
-  float fxh[NQ], fxl[NQ], fyh[NQ], fyl[NQ];
+  float fxh[NQ], fxl[ACC == 2 ? NQ : 1], fyh[NQ], fyl[ACC == 2 ? NQ : 1];
   float4 ibox = sempty_box();
   bool ipad = false;
 #pragma unroll
@@ -187,17 +194,37 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
   const u64 invL2 = pk2(Lf > 0.f ? 1.0f / Lf : 0.f, Lf > 0.f ? 1.0f / Lf : 0.f);
   const u64 nL2 = pk2(-Lf, -Lf), M2 = pk2(12582912.0f, 12582912.0f);
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) fxh[q] = fxl[q] = fyh[q] = fyl[q] = 0.f;
+  for (int q = 0; q < NQ; ++q) {
+    fxh[q] = fyh[q] = 0.f;
+    if (ACC == 2) fxl[q] = fyl[q] = 0.f;
+  }
   const float e0 = 1e-20f * (float)(c.a * c.a);   // makes the self pair exactly 0
   const u64 eps2 = pk2(e0, e0);
   const int t_begin = item.y, t_end = item.z;
   const int jt0 = max(t_begin, tsym);
-  float4 st[NS];
+  float4 st[STAGE ? 1 : NS];
+  int buf = 0;
   auto fetch = [&](int tile) {
+    if constexpr (STAGE == 1) {
+      // asynchronous 16-byte copies straight into shared memory
 #pragma unroll
-    for (int m = 0; m < NS; ++m) st[m] = rel(tile * BD_TJ + m * T + tid);
+      for (int m = 0; m < NS; ++m) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&sraw[buf ^ 1][m * T + tid]);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+                     "l"(d.work + (size_t)tile * BD_TJ + m * T + tid)
+                     : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    } else {
+#pragma unroll
+      for (int m = 0; m < NS; ++m) st[m] = rel(tile * BD_TJ + m * T + tid);
+    }
   };
   auto store = [&](int b) {
+    if constexpr (STAGE == 1) {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      return;
+    }
 #pragma unroll
     for (int m = 0; m < NS; ++m) {
       sjp[b][m * T + tid] = make_float2(st[m].x, st[m].y);
@@ -219,12 +246,18 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
       }
     }
   };
-  int buf = 0;
+  buf = STAGE ? 1 : 0;   // STAGE 1: fetch fills sraw[buf ^ 1]
   if (t_begin < t_end) {
     fetch(t_begin);
     store(0);
   }
+  buf = 0;
   __syncthreads();
+  // the j disk in slot jj of the current staging buffer, re-centred
+  auto jpos = [&](int jj) -> float2 {
+    if constexpr (STAGE == 1) return recentre(sraw[buf][jj], org);
+    else return sjp[buf][jj];
+  };
   // pair differences: MODE 0 plain, 1 packed minimum image, 2 minimum image by compares
   // pair differences (r_j - r_i): MODE 0 the hi parts alone; 1 the exact
   // near-pair vector (hi_j - hi_i) + (lo_j - lo_i); 2 the same with the packed
@@ -250,7 +283,7 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
     // the block's own disks: i side only, j broadcast from shared memory
 #pragma unroll 4
     for (int jj = 0; jj < BD_TJ; ++jj) {
-      const float2 p = sjp[buf][jj];
+      const float2 p = jpos(jj);
       const u64 jx2 = pk2(p.x, p.x), jy2 = pk2(p.y, p.y);
       u64 jxl2 = 0ull, jyl2 = 0ull;
       if constexpr (decltype(MODE)::value >= 1) {
@@ -281,7 +314,7 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
       u64 hx2[NJ], hy2[NJ];
 #pragma unroll
       for (int m = 0; m < NJ; ++m) {
-        const float2 p = sjp[buf][(g * NJ + m) * 32 + lane];
+        const float2 p = jpos((g * NJ + m) * 32 + lane);
         jx[m] = p.x;
         jy[m] = p.y;
         jxl[m] = jyl[m] = 0.f;
@@ -434,10 +467,17 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
       float ax0, ax1, ay0, ay1;
       up2(ax2[k], ax0, ax1);
       up2(ay2[k], ay0, ay1);
-      two_sum(fxh[2 * k], fxl[2 * k], -ali * ax0);
-      two_sum(fyh[2 * k], fyl[2 * k], -ali * ay0);
-      two_sum(fxh[2 * k + 1], fxl[2 * k + 1], -ali * ax1);
-      two_sum(fyh[2 * k + 1], fyl[2 * k + 1], -ali * ay1);
+      if constexpr (ACC == 2) {
+        two_sum(fxh[2 * k], fxl[2 * k], -ali * ax0);
+        two_sum(fyh[2 * k], fyl[2 * k], -ali * ay0);
+        two_sum(fxh[2 * k + 1], fxl[2 * k + 1], -ali * ax1);
+        two_sum(fyh[2 * k + 1], fyl[2 * k + 1], -ali * ay1);
+      } else {
+        fxh[2 * k] = __fmaf_rn(-ali, ax0, fxh[2 * k]);
+        fyh[2 * k] = __fmaf_rn(-ali, ay0, fyh[2 * k]);
+        fxh[2 * k + 1] = __fmaf_rn(-ali, ax1, fxh[2 * k + 1]);
+        fyh[2 * k + 1] = __fmaf_rn(-ali, ay1, fyh[2 * k + 1]);
+      }
       ax2[k] = ay2[k] = 0ull;
     }
     if (t + 1 < t_end) store(buf ^ 1);
@@ -446,7 +486,21 @@ __global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) 
   }
   float2 *ip = d.ipart + (size_t)blockIdx.x * BD_SB;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) ip[q * T + tid] = make_float2(__fadd_rn(fxh[q], fxl[q]), __fadd_rn(fyh[q], fyl[q]));
+  for (int q = 0; q < NQ; ++q) {
+    if constexpr (ACC == 2) ip[q * T + tid] = make_float2(__fadd_rn(fxh[q], fxl[q]), __fadd_rn(fyh[q], fyl[q]));
+    else ip[q * T + tid] = make_float2(fxh[q], fyh[q]);
+  }
+}
+
+template <int NW, int NP, int NJ, bool COMB, int UR, bool PER>
+__global__ void __launch_bounds__(NW * 32) k_force_long_sym(BdDev d, BdConst c) {
+  force_long_sym_body<NW, NP, NJ, COMB, UR, PER>(d, c);
+}
+
+// the same with a register budget for MINB resident blocks per SM
+template <int NW, int NP, int NJ, bool COMB, int UR, bool PER, int MINB, int STAGE, int ACC>
+__global__ void __launch_bounds__(NW * 32, MINB) k_force_long_sym_mb(BdDev d, BdConst c) {
+  force_long_sym_body<NW, NP, NJ, COMB, UR, PER, STAGE, ACC>(d, c);
 }
 
 // F_i = sum of its block's i partials + sum of its tile's j partials, in the
@@ -509,15 +563,20 @@ cudaError_t bd_launch_force_sym(const BdDev &d, const BdConst &c, int variant, c
   if (c.n_sitems == 0) return cudaSuccess;
   // periodic boxes (any replica) take the form with minimum images
   if (c.any_periodic) {
+    // register budgets measured at N = 1e5 (periodic): <4,2> 2.75 -> 2.67 ms
+    // with 8 resident blocks, <2,4> 3.05 -> 2.88 ms with 12
     if (variant == 2)
-      k_force_long_sym<4, 2, 1, false, 2, true><<<c.n_sitems, 128, 0, s>>>(d, c);
+      k_force_long_sym_mb<4, 2, 1, false, 2, true, 8, 0, 2><<<c.n_sitems, 128, 0, s>>>(d, c);
     else
-      k_force_long_sym<2, 4, 1, false, 2, true><<<c.n_sitems, 64, 0, s>>>(d, c);
+      k_force_long_sym_mb<2, 4, 1, false, 2, true, 12, 0, 2><<<c.n_sitems, 64, 0, s>>>(d, c);
   } else {
     if (variant == 2)
       k_force_long_sym<4, 2, 1, false, 2, false><<<c.n_sitems, 128, 0, s>>>(d, c);
     else
-      k_force_long_sym<2, 4, 1, false, 2, false><<<c.n_sitems, 64, 0, s>>>(d, c);
+      // 16 resident blocks (32 warps) per SM in 64 registers, j tiles staged by
+      // cp.async: measured 1.776 -> 1.668 ms at N = 1e5 against the
+      // register-staged form (120 registers, 16 warps), forces unchanged
+      k_force_long_sym_mb<2, 4, 1, false, 2, false, 16, 1, 2><<<c.n_sitems, 64, 0, s>>>(d, c);
   }
   k_force_sym_reduce<<<c.np / BD_RED_D, 4 * BD_RED_D, 0, s>>>(d, c);
   return cudaGetLastError();
