@@ -171,23 +171,50 @@ struct SymPlan {
   int n_jtiles = 0;
 };
 
-void make_sym(const bd_handle *h, int tiles, SymPlan &S) {
+// Work items of the symmetric sweep: each row of block P (its tiles from 2P
+// on) in chunks of `tiles`.  The i side of an item is written as one partial
+// (512 disks x 8 B), so long chunks cut the partial traffic; the last part of
+// the work is cut into 2-tile items, placed at the end of the launch order, so
+// the final waves of resident blocks stay full.
+void make_sym(const bd_handle *h, int tiles, int variant, SymPlan &S) {
   const int nblocks = h->np / BD_SB, ntiles = h->np / BD_TJ;
   std::vector<std::vector<int>> bl(nblocks), tl(ntiles);
   S.items.clear();
   S.n_jtiles = 0;
+  struct Chunk {
+    int P, c0, c1;
+  };
+  std::vector<Chunk> ch;
   for (const RepHost &R : h->reps) {
     if (R.p.law != BD_LAW_LONG) continue;
     const int tb = R.tile_begin, te = R.tile_end;
     for (int P = tb / 2; P < te / 2; ++P)
-      for (int c0 = 2 * P; c0 < te; c0 += tiles) {
-        const int c1 = std::min(te, c0 + tiles), jt0 = std::max(c0, 2 * P + 2);
-        const int it = (int)S.items.size();
-        S.items.push_back(make_int4(P, c0, c1, S.n_jtiles));
-        bl[P].push_back(it);
-        for (int t = jt0; t < c1; ++t) tl[t].push_back(S.n_jtiles + (t - jt0));
-        S.n_jtiles += std::max(0, c1 - jt0);
-      }
+      for (int c0 = 2 * P; c0 < te; c0 += tiles) ch.push_back({P, c0, std::min(te, c0 + tiles)});
+  }
+  if (tiles > 2) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long slots = (long)sms * std::max(1, bd_force_sym_blocks_per_sm(variant, h->c.any_periodic));
+    long tail = 4 * slots;   // tile units: two waves of 2-tile items
+    std::vector<Chunk> small;
+    while (!ch.empty() && tail > 0) {
+      const Chunk c = ch.back();
+      ch.pop_back();
+      for (int s = c.c0; s < c.c1; s += 2) small.push_back({c.P, s, std::min(c.c1, s + 2)});
+      tail -= c.c1 - c.c0;
+    }
+    std::stable_sort(small.begin(), small.end(),
+                     [](const Chunk &a, const Chunk &b) { return a.c1 - a.c0 > b.c1 - b.c0; });
+    ch.insert(ch.end(), small.begin(), small.end());
+  }
+  for (const Chunk &c : ch) {
+    const int jt0 = std::max(c.c0, 2 * c.P + 2);
+    const int it = (int)S.items.size();
+    S.items.push_back(make_int4(c.P, c.c0, c.c1, S.n_jtiles));
+    bl[c.P].push_back(it);
+    for (int t = jt0; t < c.c1; ++t) tl[t].push_back(S.n_jtiles + (t - jt0));
+    S.n_jtiles += std::max(0, c.c1 - jt0);
   }
   auto flatten = [](const std::vector<std::vector<int>> &v, std::vector<int> &ptr, std::vector<int> &idx) {
     ptr.assign(v.size() + 1, 0);
@@ -299,7 +326,7 @@ cudaError_t use_variant(bd_handle *h, int variant, int tiles) {
   h->tune_tiles = tiles;
   if (variant >= 2) {
     SymPlan S;
-    make_sym(h, tiles, S);
+    make_sym(h, tiles, variant, S);
     return upload_sym(h, S);
   }
   std::vector<int4> items;

@@ -233,3 +233,4 @@ cudaError_t bd_launch_advance_step(const BdDev &d, cudaStream_t s);
 cudaError_t bd_launch_restore_step(const BdDev &d, const BdConst &c, cudaStream_t s);
 int bd_vcorr_grid_for(int work_items, int *grid, int *block);
 int bd_force_launches(int variant);   // kernel launches of one long-range force evaluation
+int bd_force_sym_blocks_per_sm(int variant, int periodic);   // resident blocks of the symmetric sweep

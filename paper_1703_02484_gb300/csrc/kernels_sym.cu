@@ -558,6 +558,22 @@ __global__ void __launch_bounds__(4 * BD_RED_D) k_force_sym_reduce(BdDev d, BdCo
 
 int bd_force_launches(int variant) { return variant >= 2 ? 2 : 1; }
 
+int bd_force_sym_blocks_per_sm(int variant, int periodic) {
+  int per = 0;
+  cudaError_t e;
+  if (periodic)
+    e = variant == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                           &per, k_force_long_sym_mb<4, 2, 1, false, 2, true, 8, 0, 2>, 128, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                           &per, k_force_long_sym_mb<2, 4, 1, false, 2, true, 12, 0, 2>, 64, 0);
+  else
+    e = variant == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                           &per, k_force_long_sym<4, 2, 1, false, 2, false>, 128, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                           &per, k_force_long_sym_mb<2, 4, 1, false, 2, false, 16, 1, 2>, 64, 0);
+  return e == cudaSuccess ? per : 0;
+}
+
 // variant 2: 4 warps x 4 disks per lane; variant 3: 2 warps x 8 disks per lane
 cudaError_t bd_launch_force_sym(const BdDev &d, const BdConst &c, int variant, cudaStream_t s) {
   if (c.n_sitems == 0) return cudaSuccess;
