@@ -211,6 +211,19 @@ int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats);
  * steps_done 0.  Errors: BD_ERR_ARG (NULL argument). */
 int bd_last_stats(bd_handle *h, bd_step_stats *stats);
 
+/* The time step's noise for given Philox counters, computed on the device by
+ * the same code the step uses (Sec. 2.4; Philox4x32-10 as the stream
+ * generator): key (seed mod 2^32, (seed >> 32) xor replica); counter i is
+ * counters[4i .. 4i+3] (the step uses (disk, step mod 2^32, step >> 32, tag)).
+ *   words      4n words out (NULL to skip): the Philox block of each counter.
+ *   normals32  3n floats out (NULL to skip): (xi_x, xi_y, n_theta), each
+ *              Box-Muller normal truncated to [-3, 3], as the FP32 step forms them.
+ *   normals64  3n doubles out (NULL to skip): the same as the FP64 step forms them.
+ * Host arrays; device scratch is allocated and freed inside; synchronous on
+ * the legacy default stream.  Errors: BD_ERR_ARG, BD_ERR_NOMEM, BD_ERR_CUDA. */
+int bd_noise_sample(uint64_t seed, int32_t replica, int32_t n, const uint32_t *counters, uint32_t *words,
+                    float *normals32, double *normals64);
+
 /* Change the caps on the device-side loops of later steps (bd_params
  * max_corr_iters: Algorithm 2 passes per step, Sec. 4.4; max_flip_rounds:
  * inversion-repair and Lawson flip rounds per triangulation update, Sec. 4.3).

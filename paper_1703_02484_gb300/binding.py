@@ -106,6 +106,7 @@ SIGNATURES = [
     ("bd_last_stats", ctypes.c_int, [_P, ctypes.POINTER(bd_step_stats)]),
     ("bd_set_wait_limit", ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int32]),
     ("bd_set_loop_caps", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    ("bd_noise_sample", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]),
     ("bd_free", None, [_P]),
     ("bd_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -437,6 +438,19 @@ def _rollout_fn():
 
         _ROLLOUT_FN = RolloutLoss
     return _ROLLOUT_FN
+
+
+def noise_sample(seed, replica, counters):
+    """bd_noise_sample: for counters (n, 4) uint32, the device's Philox words (n, 4) and
+    clamped normals (n, 3) in the FP32 and the FP64 forms of the step."""
+    c = np.ascontiguousarray(counters, dtype=np.uint32).reshape(-1, 4)
+    n = len(c)
+    words = np.zeros((n, 4), dtype=np.uint32)
+    z32 = np.zeros((n, 3), dtype=np.float32)
+    z64 = np.zeros((n, 3), dtype=np.float64)
+    _check(load().bd_noise_sample(int(seed), int(replica), n, _ptr(c), _ptr(words), _ptr(z32), _ptr(z64)),
+           "bd_noise_sample")
+    return words, z32, z64
 
 
 def place_disks(n, L, a=1.0, placement=PLACE_RSA, seed=0):

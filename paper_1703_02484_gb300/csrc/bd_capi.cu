@@ -1596,6 +1596,29 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
   return BD_OK;
 }
 
+int bd_noise_sample(uint64_t seed, int32_t replica, int32_t n, const uint32_t *counters, uint32_t *words,
+                    float *normals32, double *normals64) {
+  if (n < 0 || (n > 0 && !counters)) return BD_ERR_ARG;
+  if (n == 0) return BD_OK;
+  void *buf = nullptr;
+  const size_t nw = (size_t)n * 16, n32 = (size_t)n * 12, n64 = (size_t)n * 24;
+  const size_t off64 = (2 * nw + n32 + 7) / 8 * 8;   // the FP64 normals 8-byte aligned
+  cudaError_t e = cudaMalloc(&buf, off64 + n64);
+  if (e != cudaSuccess) return cuda_fail(e);
+  char *b = (char *)buf;
+  void *d_ctr = b, *d_words = b + nw;
+  float *d_z32 = (float *)(b + 2 * nw);
+  double *d_z64 = (double *)(b + off64);
+  e = cudaMemcpy(d_ctr, counters, nw, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = bd_launch_noise_sample(seed, (unsigned)replica, n, d_ctr, d_words, d_z32, d_z64, nullptr);
+  if (e == cudaSuccess && words) e = cudaMemcpy(words, d_words, nw, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && normals32) e = cudaMemcpy(normals32, d_z32, n32, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && normals64) e = cudaMemcpy(normals64, d_z64, n64, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(buf);
+  return e == cudaSuccess ? BD_OK : cuda_fail(e);
+}
+
 int bd_last_stats(bd_handle *h, bd_step_stats *stats) {
   if (!h || !stats) return BD_ERR_ARG;
   *stats = h->last_stats;

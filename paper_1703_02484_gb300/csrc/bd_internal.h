@@ -234,3 +234,6 @@ cudaError_t bd_launch_restore_step(const BdDev &d, const BdConst &c, cudaStream_
 int bd_vcorr_grid_for(int work_items, int *grid, int *block);
 int bd_force_launches(int variant);   // kernel launches of one long-range force evaluation
 int bd_force_sym_blocks_per_sm(int variant, int periodic);   // resident blocks of the symmetric sweep
+// Philox words and clamped normals (FP32 and FP64 forms) for n counters (uint4 each)
+cudaError_t bd_launch_noise_sample(unsigned long long seed, unsigned replica, int n, const void *ctr, void *words,
+                                   float *z32, double *z64, cudaStream_t s);

@@ -97,6 +97,34 @@ __device__ __forceinline__ uint32_t piece_tag(uint32_t node) {
 // depth of a piece in the heap numbering: its length is dt / 2^depth
 __device__ __forceinline__ int piece_depth(uint32_t node) { return node <= 1u ? 0 : 31 - __clz(node); }
 
+// Philox words -> three clamped standard normals, Sec. 2.4 option (b):
+// u = (x + 1/2) 2^-32, Box-Muller on (u0, u1) and (u2, u3), each value
+// truncated to [-3, 3]; (z0, z1) drive the translation, z2 the director.
+// FP32 form (the FP32 step) and FP64 form (the FP64 step).
+__device__ __forceinline__ float3 normals_f32(const bdrng::U4 &r) {
+  const float sc = 2.3283064365386963e-10f;  // 2^-32
+  float u0 = __fmaf_rn((float)r.x, sc, 0.5f * sc), u1 = __fmaf_rn((float)r.y, sc, 0.5f * sc);
+  float u2 = __fmaf_rn((float)r.z, sc, 0.5f * sc), u3 = __fmaf_rn((float)r.w, sc, 0.5f * sc);
+  float ra = sqrtf(-2.0f * logf(u0)), rb = sqrtf(-2.0f * logf(u2));
+  float s1, c1, s2, c2;
+  sincospif(2.0f * u1, &s1, &c1);
+  sincospif(2.0f * u3, &s2, &c2);
+  return make_float3(fminf(3.0f, fmaxf(-3.0f, ra * c1)), fminf(3.0f, fmaxf(-3.0f, ra * s1)),
+                     fminf(3.0f, fmaxf(-3.0f, rb * c2)));
+}
+
+__device__ __forceinline__ double3 normals_f64(const bdrng::U4 &r) {
+  const double sc = 2.3283064365386962890625e-10;
+  double u0 = ((double)r.x + 0.5) * sc, u1 = ((double)r.y + 0.5) * sc;
+  double u2 = ((double)r.z + 0.5) * sc, u3 = ((double)r.w + 0.5) * sc;
+  double ra = sqrt(-2.0 * log(u0)), rb = sqrt(-2.0 * log(u2));
+  double s1, c1, s2, c2;
+  sincospi(2.0 * u1, &s1, &c1);
+  sincospi(2.0 * u3, &s2, &c2);
+  return make_double3(fmin(3.0, fmax(-3.0, ra * c1)), fmin(3.0, fmax(-3.0, ra * s1)),
+                      fmin(3.0, fmax(-3.0, rb * c2)));
+}
+
 // FP32 move of piece `node` of step `step` in grid units (before
 // reflection): X = x/q + rint(dx/q) with the increment dx formed in FP32;
 // *thn = new angle
@@ -114,16 +142,8 @@ __device__ __forceinline__ void em_move_grid(const BdConst &c, const BdRep &R, u
     amp = (float)(R.amp * sc);
     amp_r = (float)(R.amp_r * sc);
   }
-  const float sc = 2.3283064365386963e-10f;  // 2^-32
-  float u0 = __fmaf_rn((float)r.x, sc, 0.5f * sc), u1 = __fmaf_rn((float)r.y, sc, 0.5f * sc);
-  float u2 = __fmaf_rn((float)r.z, sc, 0.5f * sc), u3 = __fmaf_rn((float)r.w, sc, 0.5f * sc);
-  float ra = sqrtf(-2.0f * logf(u0)), rb = sqrtf(-2.0f * logf(u2));
-  float s1, c1, s2, c2;
-  sincospif(2.0f * u1, &s1, &c1);
-  sincospif(2.0f * u3, &s2, &c2);
-  float z0 = fminf(3.0f, fmaxf(-3.0f, ra * c1));
-  float z1 = fminf(3.0f, fmaxf(-3.0f, ra * s1));
-  float z2 = fminf(3.0f, fmaxf(-3.0f, rb * c2));
+  const float3 z = normals_f32(r);
+  const float z0 = z.x, z1 = z.y, z2 = z.z;
   float st, ct;
   sincosf(th, &st, &ct);
   const float v0f = (float)v0;
@@ -153,16 +173,8 @@ __device__ __forceinline__ double2 em_move(const BdConst &c, const BdRep &R, uin
   const double amp_scale = depth ? sqrt(ldexp(1.0, -depth)) : 1.0;
   const double amp_p = R.amp * amp_scale, amp_rp = R.amp_r * amp_scale;
   // FP64 mode
-  const double sc = 2.3283064365386962890625e-10;
-  double u0 = ((double)r.x + 0.5) * sc, u1 = ((double)r.y + 0.5) * sc;
-  double u2 = ((double)r.z + 0.5) * sc, u3 = ((double)r.w + 0.5) * sc;
-  double ra = sqrt(-2.0 * log(u0)), rb = sqrt(-2.0 * log(u2));
-  double s1, c1, s2, c2;
-  sincospi(2.0 * u1, &s1, &c1);
-  sincospi(2.0 * u3, &s2, &c2);
-  double z0 = fmin(3.0, fmax(-3.0, ra * c1));
-  double z1 = fmin(3.0, fmax(-3.0, ra * s1));
-  double z2 = fmin(3.0, fmax(-3.0, rb * c2));
+  const double3 z = normals_f64(r);
+  const double z0 = z.x, z1 = z.y, z2 = z.z;
   double st, ct;
   sincos((double)th, &st, &ct);
   const double nx = p.x + dt_p * (F.x + v0 * ct) + amp_p * z0;

@@ -106,3 +106,31 @@ cudaError_t bd_launch_state_out(const BdDev &d, const BdConst &c, cudaStream_t s
   k_state_out<<<(c.np + 255) / 256, 256, 0, s>>>(d, c);
   return cudaGetLastError();
 }
+
+// The noise of the time step for given Philox counters (diagnostics and tests
+// of the generator): the raw words, and the clamped normals as the FP32 and
+// the FP64 step form them.
+__global__ void k_noise_sample(unsigned long long seed, unsigned replica, int n, const uint4 *ctr, uint4 *words,
+                               float *z32, double *z64) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = ctr[i];
+  bdrng::U4 u{c.x, c.y, c.z, c.w};
+  const bdrng::U4 r = bdrng::philox(u, (uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32) ^ replica);
+  words[i] = make_uint4(r.x, r.y, r.z, r.w);
+  const float3 a = bdem::normals_f32(r);
+  const double3 b = bdem::normals_f64(r);
+  z32[3 * i] = a.x;
+  z32[3 * i + 1] = a.y;
+  z32[3 * i + 2] = a.z;
+  z64[3 * i] = b.x;
+  z64[3 * i + 1] = b.y;
+  z64[3 * i + 2] = b.z;
+}
+
+cudaError_t bd_launch_noise_sample(unsigned long long seed, unsigned replica, int n, const void *ctr, void *words,
+                                   float *z32, double *z64, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_noise_sample<<<(n + 255) / 256, 256, 0, s>>>(seed, replica, n, (const uint4 *)ctr, (uint4 *)words, z32, z64);
+  return cudaGetLastError();
+}

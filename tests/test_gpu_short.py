@@ -218,3 +218,24 @@ def test_verlet_set_state_checks_overlaps_on_the_device(far):
     out = s.state(want_tri=False)
     assert len(cKDTree(out["xy"]).query_pairs(2.0 * (1 - 1e-12))) == 0
     s.close()
+
+
+def test_one_step_parity_full_size_c3():
+    # 2^20 disks at area fraction 0.5 (the paper's lattice start) with 5 % of
+    # them moved next to a neighbour: one step of the short-range law with the
+    # Delaunay overlap correction against the oracle's step
+    n = CFG.n
+    L = workloads.box_side(n, CFG.rho)
+    xy = workloads.near_contact_state(n, L, CFG.a, seed=5, rho=CFG.rho, frac=0.05)
+    _, sp, th = workloads.initial_state(CFG)
+    s = bd.System(bd.params_from_config(CFG), xy, sp, th, stream=stream())
+    st = s.step(1)
+    out = s.state()
+    op = ostep.Params(L=L, a=CFG.a, law=CFG.law, eps=CFG.eps, kappa=CFG.kappa, r_cut=CFG.r_cut, D=CFG.D,
+                      Dr=CFG.Dr, v0=CFG.v0, dt=CFG.dt, seed=CFG.seed)
+    import os
+    ref = ostep.step(xy, th, sp, 0, op, threads=max(1, os.cpu_count() or 1))
+    assert not ref["rejected"] and ref["corr_iters"] >= 1
+    assert np.max(np.abs(out["xy"] - ref["xy"])) <= 1e-5 * CFG.a
+    assert st["corr_iters"] == ref["corr_iters"]
+    assert np.array_equal(geometry.edges(out["tri"]), geometry.edges(ref["tris"]))

@@ -336,3 +336,25 @@ def test_reversal_test_near_perpendicular_moves(eps, turn):
         after = s.state()
         assert np.array_equal(after["xy"], before["xy"]) and np.array_equal(after["tri"], before["tri"])
     s.close()
+
+
+def test_one_step_parity_full_size_n1e5():
+    # the benchmark's system (N = 1e5, two species, active) from a near-contact
+    # start, in the configuration the benchmark times: one step against the
+    # oracle's (positions, passes of Algorithm 2, Delaunay edge set)
+    cfg = workloads.CONFIGS["n1e5"]
+    n = cfg.n
+    L = workloads.box_side(n, cfg.rho)
+    xy = workloads.near_contact_state(n, L, cfg.a, seed=21, frac=0.1)
+    _, sp, th = workloads.initial_state(cfg)
+    s = bd.System(bd.params_from_config(cfg), xy, sp, th, stream=stream())
+    st = s.step(1)
+    out = s.state()
+    ref = ostep.step(xy, th, sp, 0, oracle_params(cfg, L), threads=max(1, os.cpu_count() or 1))
+    assert not ref["rejected"] and ref["corr_iters"] >= 1
+    err = float(np.max(np.abs(out["xy"] - ref["xy"])))
+    assert err <= POS_TOL * cfg.a, err
+    assert st["corr_iters"] == ref["corr_iters"]
+    assert np.max(np.abs(out["theta"] - ref["theta"])) <= 1e-5
+    assert np.array_equal(geometry.edges(out["tri"]), geometry.edges(ref["tris"]))
+    assert len(cKDTree(out["xy"]).query_pairs(2 * cfg.a * (1 - 1e-12))) == 0
