@@ -27,7 +27,12 @@ def noise_amplitude(D, dt, literal_amp=False):
 
 
 def reflect(xy, a, L):
+    """Mirror centres into [a, L - a]; a is the radius, or one radius per disk
+    (polydisperse disks: each centre stays a_i from the walls)."""
     xy = np.array(xy, dtype=np.float64, copy=True)
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        a = a[:, None]
     lo, hi = a, L - a
     xy = np.where(xy < lo, 2.0 * lo - xy, xy)
     xy = np.where(xy > hi, 2.0 * hi - xy, xy)

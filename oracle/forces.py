@@ -101,23 +101,25 @@ def short_range_potential(r, eps, kappa, sigma_c):
     return wca + yuk
 
 
-def short_range_pairs(xy, pairs_i, pairs_j, eps, kappa, sigma_c, r_cut, L=None):
+def short_range_pairs(xy, pairs_i, pairs_j, eps, kappa, sigma_c, r_cut, L=None, radii=None):
     """Force on each i from its listed partners j (one row per listed pair):
     returns (n, 2) accumulated over the given ordered pairs (i <- j).
-    L: periodic box side (minimum image); None = walls."""
+    L: periodic box side (minimum image); None = walls.  radii: polydisperse
+    disks, the pair's length scale is then a_i + a_j (additive mixing)."""
     xy = np.asarray(xy, dtype=np.float64)
     d = xy[pairs_i] - xy[pairs_j]
     if L is not None:
         d = d - L * np.round(d / L)
     r = np.sqrt(np.einsum("ij,ij->i", d, d))
-    mag = np.where(r < r_cut, short_range_magnitude(r, eps, kappa, sigma_c), 0.0)
+    sc = sigma_c if radii is None else radii[pairs_i] + radii[pairs_j]
+    mag = np.where(r < r_cut, short_range_magnitude(r, eps, kappa, sc), 0.0)
     f = d * (mag / r)[:, None]
     out = np.zeros_like(xy)
     np.add.at(out, pairs_i, f)
     return out
 
 
-def short_range(xy, eps, kappa, sigma_c, r_cut, L=None):
+def short_range(xy, eps, kappa, sigma_c, r_cut, L=None, radii=None):
     """All-pairs evaluation of the truncated short-range force (candidate
     pairs from a k-d tree, periodic when L is given; the law is above)."""
     xy = np.asarray(xy, dtype=np.float64)
@@ -127,4 +129,4 @@ def short_range(xy, eps, kappa, sigma_c, r_cut, L=None):
     pairs = np.array(sorted(tree.query_pairs(r_cut * (1 + 1e-9))), dtype=np.int64).reshape(-1, 2)
     pi = np.concatenate([pairs[:, 0], pairs[:, 1]])
     pj = np.concatenate([pairs[:, 1], pairs[:, 0]])
-    return short_range_pairs(xy, pi, pj, eps, kappa, sigma_c, r_cut, L)
+    return short_range_pairs(xy, pi, pj, eps, kappa, sigma_c, r_cut, L, radii)

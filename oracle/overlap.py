@@ -35,27 +35,41 @@ def real_edges(tris, n):
     return e[(e[:, 0] < n) & (e[:, 1] < n)]
 
 
-def correction_pass(xy, E, sigma, a, L):
+def contact(sigma, radii, i, j):
+    """Contact distance of pairs (i, j): sigma for equal disks; a_i + a_j for
+    polydisperse disks (Sec. 2.3's extension)."""
+    return sigma if radii is None else radii[i] + radii[j]
+
+
+def caps(sigma, radii, n):
+    """Sec. 4.4's truncation, "sigma/4 (half the particle radius)": half of
+    each disk's own radius for polydisperse disks."""
+    return np.full(n, sigma / 4.0) if radii is None else 0.5 * np.asarray(radii, dtype=np.float64)
+
+
+def correction_pass(xy, E, sigma, a, L, radii=None):
     """One pass of Algorithm 2 over the edge list E (pairs i < j).
-    Returns (new xy, overlapping pairs (k,2), capped mask, raw displacement)."""
+    Returns (new xy, overlapping pairs (k,2), capped mask, raw displacement).
+    radii: one radius per disk (polydisperse), else every disk has radius a."""
     xy = np.asarray(xy, dtype=np.float64)
     i, j = E[:, 0], E[:, 1]
     d = xy[j] - xy[i]                          # r_j - r_i
     r = np.sqrt(d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1])
-    hit = r < sigma
+    sg = contact(sigma, radii, i, j)
+    hit = r < sg
     pairs = E[hit]
     disp = np.zeros_like(xy)
     if hit.any():
         nhat = d[hit] / r[hit][:, None]
-        delta = (sigma - r[hit])[:, None]
+        delta = ((sg[hit] if radii is not None else sigma) - r[hit])[:, None]
         np.add.at(disp, pairs[:, 0], -delta * nhat)
         np.add.at(disp, pairs[:, 1], delta * nhat)
     mag = np.sqrt(disp[:, 0] ** 2 + disp[:, 1] ** 2)
-    cap = sigma / 4.0
+    cap = caps(sigma, radii, len(xy))
     capped = mag > cap
     scale = np.where(capped, cap / np.where(mag > 0, mag, 1.0), 1.0)
     new = xy + disp * scale[:, None]
-    new = dynamics.reflect(new, a, L)
+    new = dynamics.reflect(new, a if radii is None else radii, L)
     return new, pairs, capped, disp
 
 
@@ -68,8 +82,10 @@ def reversed_edges(xy0, xy1, E):
     return E[dot < 0]
 
 
-def correct(xy, L, a, max_iters=10000, tris=None, record=None):
-    """Iterate Algorithm 2 until no Delaunay edge is shorter than sigma = 2a.
+def correct(xy, L, a, max_iters=10000, tris=None, record=None, radii=None):
+    """Iterate Algorithm 2 until no Delaunay edge is shorter than sigma = 2a
+    (polydisperse: than a_i + a_j; a is then the largest radius, which lays
+    out the ghost points).
     Returns (xy, tris of final positions, iterations that moved disks,
     total overlapping edges seen, rejection reason REJ_*: false when none)."""
     sigma = 2.0 * a
@@ -81,7 +97,7 @@ def correct(xy, L, a, max_iters=10000, tris=None, record=None):
         if tris is None:
             tris = geometry.delaunay(xy, L, a)
         E = real_edges(tris, n)
-        new, pairs, capped, disp = correction_pass(xy, E, sigma, a, L)
+        new, pairs, capped, disp = correction_pass(xy, E, sigma, a, L, radii)
         if len(pairs) == 0:
             return xy, tris, it, total, REJ_NONE
         if record is not None:
@@ -96,8 +112,9 @@ def correct(xy, L, a, max_iters=10000, tris=None, record=None):
             return xy, geometry.delaunay(xy, L, a), it, total, REJ_NOT_CONVERGED
 
 
-def close_pairs(xy, sigma, chunk=512):
-    """Every pair i < j with |r_j - r_i| < sigma, by brute force (chunked)."""
+def close_pairs(xy, sigma, chunk=512, radii=None):
+    """Every pair i < j with |r_j - r_i| < sigma (polydisperse: < a_i + a_j),
+    by brute force (chunked)."""
     xy = np.asarray(xy, dtype=np.float64)
     n = len(xy)
     out = []
@@ -105,7 +122,8 @@ def close_pairs(xy, sigma, chunk=512):
         c1 = min(n, c0 + chunk)
         d = xy[None, :, :] - xy[c0:c1, None, :]          # r_j - r_i
         r = np.sqrt(d[:, :, 0] * d[:, :, 0] + d[:, :, 1] * d[:, :, 1])
-        ii, jj = np.nonzero(r < sigma)
+        lim = sigma if radii is None else radii[c0:c1, None] + radii[None, :]
+        ii, jj = np.nonzero(r < lim)
         ii = ii + c0
         keep = jj > ii
         if keep.any():
@@ -113,7 +131,7 @@ def close_pairs(xy, sigma, chunk=512):
     return np.concatenate(out) if out else np.zeros((0, 2), dtype=np.int64)
 
 
-def correct_allpairs(xy, L, a, max_iters=10000, record=None):
+def correct_allpairs(xy, L, a, max_iters=10000, record=None, radii=None):
     """Algorithm 2 over every pair of disks (the short-range path of Sec. 5,
     where the neighbour lists, not a triangulation, supply the pairs): each
     pass takes every pair closer than sigma, sums the displacements Jacobi
@@ -125,10 +143,10 @@ def correct_allpairs(xy, L, a, max_iters=10000, record=None):
     it = 0
     total = 0
     while True:
-        E = close_pairs(xy, sigma)
+        E = close_pairs(xy, sigma, radii=radii)
         if len(E) == 0:
             return xy, it, total, REJ_NONE
-        new, pairs, capped, disp = correction_pass(xy, E, sigma, a, L)
+        new, pairs, capped, disp = correction_pass(xy, E, sigma, a, L, radii)
         if record is not None:
             record.append({"pairs": pairs, "capped": capped, "disp": disp, "xy": xy})
         total += len(pairs)
@@ -146,22 +164,23 @@ def correct_allpairs(xy, L, a, max_iters=10000, record=None):
 # conditions").
 
 
-def correction_pass_periodic(xy, K, sigma, L):
+def correction_pass_periodic(xy, K, sigma, L, radii=None):
     """One pass of Algorithm 2 over torus edges K.  Returns (new positions
     before wrapping, overlapping keys, capped mask, raw displacement)."""
     xy = np.asarray(xy, dtype=np.float64)
     d = periodic.edge_vectors(xy, K, L)
     r = np.sqrt(d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1])
-    hit = r < sigma
+    sg = contact(sigma, radii, K[:, 0], K[:, 1])
+    hit = r < sg
     pairs = K[hit]
     disp = np.zeros_like(xy)
     if hit.any():
         nhat = d[hit] / r[hit][:, None]
-        delta = (sigma - r[hit])[:, None]
+        delta = ((sg[hit] if radii is not None else sigma) - r[hit])[:, None]
         np.add.at(disp, pairs[:, 0], -delta * nhat)
         np.add.at(disp, pairs[:, 1], delta * nhat)
     mag = np.sqrt(disp[:, 0] ** 2 + disp[:, 1] ** 2)
-    cap = sigma / 4.0
+    cap = caps(sigma, radii, len(xy))
     capped = mag > cap
     scale = np.where(capped, cap / np.where(mag > 0, mag, 1.0), 1.0)
     return xy + disp * scale[:, None], pairs, capped, disp
@@ -176,7 +195,7 @@ def reversed_keys(xy0, xy1, K, L):
     return K[dot < 0]
 
 
-def correct_periodic(xy, L, a, max_iters=10000, record=None):
+def correct_periodic(xy, L, a, max_iters=10000, record=None, radii=None):
     """Algorithm 2 over the edges of the torus Delaunay triangulation of the
     current positions until none is shorter than sigma (as correct()).
     Returns (xy, (tri, shift) of the final positions, passes, overlapping
@@ -188,7 +207,7 @@ def correct_periodic(xy, L, a, max_iters=10000, record=None):
     while True:
         tri, sh = periodic.delaunay_torus(xy, L)
         K = periodic.edge_keys(tri, sh)
-        new, pairs, capped, disp = correction_pass_periodic(xy, K, sigma, L)
+        new, pairs, capped, disp = correction_pass_periodic(xy, K, sigma, L, radii)
         if len(pairs) == 0:
             return xy, (tri, sh), it, total, REJ_NONE
         if record is not None:
@@ -202,17 +221,17 @@ def correct_periodic(xy, L, a, max_iters=10000, record=None):
             return xy, periodic.delaunay_torus(xy, L), it, total, REJ_NOT_CONVERGED
 
 
-def correct_allpairs_periodic(xy, L, a, max_iters=10000, record=None):
+def correct_allpairs_periodic(xy, L, a, max_iters=10000, record=None, radii=None):
     """correct_allpairs() in a periodic box (minimum-image pairs)."""
     sigma = 2.0 * a
     xy = np.asarray(xy, dtype=np.float64)
     it = 0
     total = 0
     while True:
-        K = periodic.close_pairs(xy, sigma, L)
+        K = periodic.close_pairs(xy, sigma, L, radii=radii)
         if len(K) == 0:
             return xy, it, total, REJ_NONE
-        new, pairs, capped, disp = correction_pass_periodic(xy, K, sigma, L)
+        new, pairs, capped, disp = correction_pass_periodic(xy, K, sigma, L, radii)
         if record is not None:
             record.append({"pairs": pairs, "capped": capped, "disp": disp, "xy": xy})
         total += len(pairs)

@@ -103,9 +103,10 @@ def lifted(xy, tri, shift, L):
     return np.asarray(xy, dtype=np.float64)[tri] + L * shift
 
 
-def close_pairs(xy, sigma, L, chunk=512):
-    """Every pair i < j whose minimum-image distance is below sigma, with the
-    image shift of j: rows (i, j, sx, sy)."""
+def close_pairs(xy, sigma, L, chunk=512, radii=None):
+    """Every pair i < j whose minimum-image distance is below sigma
+    (polydisperse: below a_i + a_j), with the image shift of j: rows
+    (i, j, sx, sy)."""
     xy = np.asarray(xy, dtype=np.float64)
     n = len(xy)
     out = []
@@ -115,7 +116,8 @@ def close_pairs(xy, sigma, L, chunk=512):
         s = -np.round(d / L)
         d = d + L * s
         r = np.sqrt(d[:, :, 0] ** 2 + d[:, :, 1] ** 2)
-        ii, jj = np.nonzero(r < sigma)
+        lim = sigma if radii is None else radii[c0:c1, None] + radii[None, :]
+        ii, jj = np.nonzero(r < lim)
         ii = ii + c0
         keep = jj > ii
         if keep.any():

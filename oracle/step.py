@@ -17,6 +17,12 @@ final triangulation itself.
 Periodic box (Params.periodic, Sec. 2.1): minimum-image forces, moves that
 wrap, and the torus triangulation of oracle.periodic.
 
+Polydisperse disks (Params.radii, Sec. 2.3 "radii [that] do not differ too
+much"): a pair overlaps when closer than a_i + a_j, each disk of an
+overlapping pair moves a_i + a_j - r, a disk's summed displacement is
+truncated at half its own radius, centres are reflected a_i from the walls,
+and the short-range law takes a_i + a_j as its length scale.
+
 Rejected moves (Sec. 4.3): when a pair passes through each other "the last
 positions are discarded and integration is repeated with a lower dt".  With
 Params.max_halvings = H > 0 a rejected move is replaced by two moves of half
@@ -54,6 +60,7 @@ class Params:
     literal_amp: bool = False
     max_halvings: int = 0
     periodic: bool = False
+    radii: object = None     # polydisperse disks: one radius per disk (a is then the largest)
 
 
 def compute_forces(xy, species, p: Params, threads=1):
@@ -63,8 +70,12 @@ def compute_forces(xy, species, p: Params, threads=1):
             return forces.long_range_numpy(xy, species, p.alpha, L=Lp)
         return forces.long_range(xy, species, p.alpha, threads=threads, L=Lp)
     if p.law == LAW_SHORT:
-        return forces.short_range(xy, p.eps, p.kappa, 2.0 * p.a, p.r_cut, L=Lp)
+        return forces.short_range(xy, p.eps, p.kappa, 2.0 * p.a, p.r_cut, L=Lp, radii=_radii(p))
     return np.zeros_like(np.asarray(xy, dtype=np.float64))
+
+
+def _radii(p):
+    return None if p.radii is None else np.asarray(p.radii, dtype=np.float64)
 
 
 def _piece(xy, theta, species, step_index, p: Params, ids, tris, F, threads, record, pairs_from,
@@ -78,11 +89,13 @@ def _piece(xy, theta, species, step_index, p: Params, ids, tris, F, threads, rec
     dt = p.dt / float(2 ** (int(node).bit_length() - 1))
     if p.periodic:
         return _piece_periodic(xy, theta, F, step_index, p, ids, tris, record, pairs_from, node, dt)
+    rad = _radii(p)
     new, th = dynamics.em_step(xy, theta, F, ids, step_index, p.seed, p.D, p.Dr, p.v0, dt,
-                               p.a, p.L, p.replica, p.literal_amp, philox.substep_tag(node))
+                               p.a if rad is None else rad, p.L, p.replica, p.literal_amp,
+                               philox.substep_tag(node))
     if pairs_from == "allpairs":
         out, iters, pairs, rej = overlap.correct_allpairs(new, p.L, p.a, p.max_corr_iters,
-                                                              record=record)
+                                                          record=record, radii=rad)
         return dict(xy=out, theta=th, tris=None, corr_iters=iters, overlap_pairs=pairs,
                     rejected=rej, F=F, xy_em=new)
     if tris is None:
@@ -92,7 +105,7 @@ def _piece(xy, theta, species, step_index, p: Params, ids, tris, F, threads, rec
         return dict(xy=xy, theta=np.asarray(theta, np.float64), tris=tris, corr_iters=0,
                     overlap_pairs=0, rejected=overlap.REJ_REVERSAL, F=F)
     out, tris1, iters, pairs, rej = overlap.correct(new, p.L, p.a, p.max_corr_iters,
-                                                    record=record)
+                                                    record=record, radii=rad)
     return dict(xy=out, theta=th, tris=tris1, corr_iters=iters, overlap_pairs=pairs,
                 rejected=rej, F=F, xy_em=new)
 
@@ -104,9 +117,10 @@ def _piece_periodic(xy, theta, F, step_index, p, ids, tris, record, pairs_from, 
     moved, th = dynamics.em_move(xy, theta, F, ids, step_index, p.seed, p.D, p.Dr, p.v0, dt,
                                  p.replica, p.literal_amp, philox.substep_tag(node))
     new = periodic.wrap(moved, p.L)
+    rad = _radii(p)
     if pairs_from == "allpairs":
         out, iters, pairs, rej = overlap.correct_allpairs_periodic(new, p.L, p.a, p.max_corr_iters,
-                                                                   record=record)
+                                                                   record=record, radii=rad)
         return dict(xy=out, theta=th, tris=None, corr_iters=iters, overlap_pairs=pairs,
                     rejected=rej, F=F, xy_em=new)
     if tris is None:
@@ -116,7 +130,7 @@ def _piece_periodic(xy, theta, F, step_index, p, ids, tris, record, pairs_from, 
         return dict(xy=xy, theta=np.asarray(theta, np.float64), tris=tris, corr_iters=0,
                     overlap_pairs=0, rejected=overlap.REJ_REVERSAL, F=F)
     out, tris1, iters, pairs, rej = overlap.correct_periodic(new, p.L, p.a, p.max_corr_iters,
-                                                             record=record)
+                                                             record=record, radii=rad)
     return dict(xy=out, theta=th, tris=tris1, corr_iters=iters, overlap_pairs=pairs,
                 rejected=rej, F=F, xy_em=new)
 

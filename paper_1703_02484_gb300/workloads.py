@@ -272,3 +272,75 @@ def batch_configs(R: int = 256, seed: int = 3, n_lo: int = 512, n_hi: int = 6553
         out.append(replace(base, name="c4r%d" % r, n=int(ns[r]), rho=float(rhos[r]), seed=seed,
                            precision=0, extra={"replica": r}))
     return out
+
+
+# ---------------------------------------------------------------- polydisperse disks
+
+def poly_radii(n: int, a_max: float = 1.0, ratio: float = 1.3, seed: int = 0) -> np.ndarray:
+    """Radii drawn uniformly from [a_max / ratio, a_max] (slightly polydisperse
+    disks, largest radius a_max)."""
+    rng = np.random.default_rng(np.random.PCG64([seed, 0x52414449]))
+    return rng.uniform(a_max / ratio, a_max, size=n)
+
+
+def poly_positions(radii, L: float, seed: int, near_frac: float = 0.0, gap: float = 0.02):
+    """Random sequential addition of disks with the given radii in the box
+    [0, L]^2 (centre i in [a_i, L - a_i], pairs at least a_i + a_j apart); with
+    near_frac > 0 that fraction of the disks is then moved next to its nearest
+    neighbour, leaving a surface gap in (0, gap] (a start with overlaps to
+    correct after the first move)."""
+    radii = np.asarray(radii, dtype=np.float64)
+    n = len(radii)
+    rng = np.random.default_rng(np.random.PCG64([seed, 0x504F4C59]))
+    amax = float(radii.max())
+    cs = 2.0 * amax
+    nc = max(1, int(L // cs))
+    cs = L / nc
+    grid = {}
+    xy = np.empty((n, 2))
+
+    def key(p):
+        return (int(p[0] // cs), int(p[1] // cs))
+
+    def conflicts(p, r, skip=-1):
+        cx, cy = key(p)
+        for gx in (cx - 1, cx, cx + 1):
+            for gy in (cy - 1, cy, cy + 1):
+                for k in grid.get((gx, gy), ()):
+                    if k != skip and (xy[k, 0] - p[0]) ** 2 + (xy[k, 1] - p[1]) ** 2 < (r + radii[k]) ** 2:
+                        return True
+        return False
+
+    for i in range(n):
+        for _ in range(200000):
+            p = rng.uniform(radii[i], L - radii[i], size=2)
+            if not conflicts(p, radii[i]):
+                break
+        else:
+            raise RuntimeError("random addition did not place disk %d" % i)
+        xy[i] = p
+        grid.setdefault(key(p), set()).add(i)
+    for i in rng.permutation(n)[: int(near_frac * n)]:
+        i = int(i)
+        cx, cy = key(xy[i])
+        best, bj = None, -1
+        for gx in (cx - 1, cx, cx + 1):
+            for gy in (cy - 1, cy, cy + 1):
+                for k in grid.get((gx, gy), ()):
+                    if k == i:
+                        continue
+                    dd = math.hypot(*(xy[k] - xy[i]))
+                    if best is None or dd < best:
+                        best, bj = dd, k
+        if bj < 0:
+            continue
+        v = xy[i] - xy[bj]
+        cand = xy[bj] + v / math.hypot(*v) * (radii[i] + radii[bj] + rng.uniform(0.1, 1.0) * gap)
+        if not (radii[i] <= cand[0] <= L - radii[i] and radii[i] <= cand[1] <= L - radii[i]):
+            continue
+        if conflicts(cand, radii[i], skip=i):
+            continue
+        grid[key(xy[i])].discard(i)
+        xy[i] = cand
+        grid.setdefault(key(cand), set()).add(i)
+    return xy
