@@ -247,6 +247,29 @@ int bd_set_loop_caps(bd_handle *h, int32_t max_corr_iters, int32_t max_flip_roun
  * Errors: BD_ERR_ARG, BD_ERR_CUDA. */
 int bd_set_wait_limit(bd_handle *h, double seconds, int32_t hold_barrier);
 
+/* bd_init for polydisperse disks (Sec. 2.3: the method extends directly to
+ * disks whose radii do not differ too much).  Disk i has radius radii[i] in
+ * (0, p->a] (p->a is the largest radius; it lays out the ghost points and
+ * sizes the cell grids).  A pair overlaps when closer than a_i + a_j; each disk
+ * of an overlapping pair moves a_i + a_j - r (Eq. (overlaps)); a disk's summed
+ * correction is truncated at half its own radius (Sec. 4.4); centres stay in
+ * [a_i, L - a_i] with walls; the short-range law's length scale is a_i + a_j;
+ * the long-range law does not involve radii.
+ * With BD_OVERLAP_DELAUNAY the radii must satisfy max <= sqrt(2) min: then the
+ * overlapping pair with the smallest centre distance is a Delaunay edge (a
+ * disk inside its diametral disk would make a closer overlapping pair), so
+ * the loop over Delaunay edges still proves that no pair overlaps; wider
+ * ratios need BD_OVERLAP_VERLET (short-range law), which tests every listed
+ * pair.  Single-system handles; bd_rollout returns BD_ERR_UNSUPPORTED.
+ *   xy      required (2n doubles), radii required (n doubles, caller order);
+ *           the other arguments as bd_init.
+ * Errors: as bd_init; BD_ERR_ARG (a radius outside (0, a], NULL xy or radii),
+ * BD_ERR_UNSUPPORTED (radius ratio above sqrt(2) with the Delaunay overlap
+ * correction), BD_ERR_INIT_OVERLAP (a pair closer than a_i + a_j, or a centre
+ * outside [a_i, L - a_i]). */
+int bd_init_radii(const bd_params *p, const double *xy, const uint8_t *species, const float *theta,
+                  const double *radii, void *stream, bd_handle **out);
+
 /* Batched replicas (no counterpart in the paper; it serves ensembles of
  * independent systems).  R systems of possibly different N, box, law and
  * parameters advance together: every kernel launch of a step works on all of

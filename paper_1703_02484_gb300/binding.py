@@ -65,6 +65,7 @@ _P = ctypes.c_void_p
 SIGNATURES = [
     ("bd_default_params", ctypes.c_int, [ctypes.POINTER(bd_params)]),
     ("bd_init", ctypes.c_int, [ctypes.POINTER(bd_params), _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    ("bd_init_radii", ctypes.c_int, [ctypes.POINTER(bd_params), _P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     ("bd_step", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(bd_step_stats)]),
     ("bd_get_state", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int64)]),
@@ -193,7 +194,7 @@ def params_from_config(cfg, n=None, seed=None):
 class System:
     """One simulated system (or a batch of replicas) behind a bd_handle."""
 
-    def __init__(self, params, xy=None, species=None, theta=None, stream=None):
+    def __init__(self, params, xy=None, species=None, theta=None, stream=None, radii=None):
         lib = load()
         batch = isinstance(params, (list, tuple))
         plist = list(params) if batch else [params]
@@ -209,6 +210,10 @@ class System:
             self._plist = arr
             _check(lib.bd_batch_init(self.R, arr, _ptr(self._xy), _ptr(self._sp), _ptr(self._th),
                                      st, ctypes.byref(h)), "bd_batch_init")
+        elif radii is not None:
+            self._rad = np.ascontiguousarray(radii, dtype=np.float64)
+            _check(lib.bd_init_radii(ctypes.byref(params), _ptr(self._xy), _ptr(self._sp), _ptr(self._th),
+                                     _ptr(self._rad), st, ctypes.byref(h)), "bd_init_radii")
         else:
             _check(lib.bd_init(ctypes.byref(params), _ptr(self._xy), _ptr(self._sp),
                                _ptr(self._th), st, ctypes.byref(h)), "bd_init")

@@ -32,8 +32,8 @@ void make_ghosts(double L, double a, std::vector<double> &gx, std::vector<double
 double ghost_extent(double L, double a);
 int rsa_place(int n, double lo, double hi, double dmin, uint64_t seed, std::vector<double> &xy);
 int lattice_place(int n, double lo, double hi, double dmin, uint64_t seed, std::vector<double> &xy);
-int any_overlap(int n, const double *xy, double lo, double hi, double dmin);
-int any_overlap_periodic(int n, const double *xy, double L, double dmin);
+int any_overlap(int n, const double *xy, double lo, double hi, double dmin, const double *rad = nullptr);
+int any_overlap_periodic(int n, const double *xy, double L, double dmin, const double *rad = nullptr);
 int build_torus_delaunay(const double *X, const double *Y, const std::vector<int> &ids, double L,
                          const bdpred::Grid &grid, std::vector<int> &V, std::vector<int> &S,
                          std::vector<int> &N);
@@ -389,6 +389,7 @@ struct Spec {
   const double *xy;
   const uint8_t *sp;
   const float *th;
+  const double *rad = nullptr;   // polydisperse disks: one radius each (bd_init_radii)
 };
 
 int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out);
@@ -411,6 +412,19 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
         s.p.max_flip_rounds != specs[0].p.max_flip_rounds || s.p.overlap_mode != specs[0].p.overlap_mode)
       return BD_ERR_ARG;   // one disk radius, precision, loop caps and overlap mode per handle
     if (R > 1 && s.p.max_dt_halvings > 0) return BD_ERR_UNSUPPORTED;   // halving: one system per handle
+    if (s.rad) {
+      // polydisperse disks: every radius in (0, a]; over the Delaunay edges
+      // the overlap certificate needs a_max <= sqrt(2) a_min
+      if (R > 1 || !s.xy) return BD_ERR_ARG;
+      double lo = 1e300, hi = 0.0;
+      for (int i = 0; i < s.p.n; ++i) {
+        const double r = s.rad[i];
+        if (!(r > 0.0) || !(r <= s.p.a)) return BD_ERR_ARG;
+        lo = std::min(lo, r);
+        hi = std::max(hi, r);
+      }
+      if (s.p.overlap_mode == BD_OVERLAP_DELAUNAY && hi > 1.4142135623730951 * lo) return BD_ERR_UNSUPPORTED;
+    }
   }
   bd_handle *h = new (std::nothrow) bd_handle();
   if (!h) return BD_ERR_NOMEM;
@@ -442,6 +456,10 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     RH.wall_lo = RH.periodic ? 0.0 : ceil(p.a * inv_q) * q;
     RH.wall_hi = RH.periodic ? RH.L : floor((RH.L - p.a) * inv_q) * q;
     if (!(RH.wall_hi > RH.wall_lo)) { delete h; return BD_ERR_ARG; }
+    const double *rad = specs[r].rad;
+    // a disk's own walls (polydisperse: a_i from each wall), on the grid
+    auto wlo = [&](int i) { return rad && !RH.periodic ? ceil(rad[i] * inv_q) * q : RH.wall_lo; };
+    auto whi = [&](int i) { return rad && !RH.periodic ? floor((RH.L - rad[i]) * inv_q) * q : RH.wall_hi; };
     std::vector<double> &xy = xyr[r];
     xy.resize(2 * (size_t)p.n);
     if (specs[r].xy) {
@@ -457,22 +475,24 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
         if (!isfinite(xy[k])) { delete h; return BD_ERR_INIT_OVERLAP; }
         xy[k] = periodic_coord(xy[k], RH.L, q, inv_q);
       }
-      if (bdhost::any_overlap_periodic(p.n, xy.data(), RH.L, 2.0 * p.a * (1.0 - 1e-12))) {
+      if (bdhost::any_overlap_periodic(p.n, xy.data(), RH.L, 2.0 * p.a * (1.0 - 1e-12), rad)) {
         delete h;
         return BD_ERR_INIT_OVERLAP;
       }
     } else {
-      for (size_t k = 0; k < xy.size(); ++k)
-        if (!isfinite(xy[k]) || xy[k] < p.a - 1e-9 * RH.L || xy[k] > RH.L - p.a + 1e-9 * RH.L) {
+      for (size_t k = 0; k < xy.size(); ++k) {
+        const double ak = rad ? rad[k / 2] : p.a;
+        if (!isfinite(xy[k]) || xy[k] < ak - 1e-9 * RH.L || xy[k] > RH.L - ak + 1e-9 * RH.L) {
           delete h;
           return BD_ERR_INIT_OVERLAP;
         }
-      if (bdhost::any_overlap(p.n, xy.data(), 0.0, RH.L, 2.0 * p.a * (1.0 - 1e-12))) {
+      }
+      if (bdhost::any_overlap(p.n, xy.data(), 0.0, RH.L, 2.0 * p.a * (1.0 - 1e-12), rad)) {
         delete h;
         return BD_ERR_INIT_OVERLAP;
       }
       for (size_t k = 0; k < xy.size(); ++k)
-        xy[k] = std::min(RH.wall_hi, std::max(RH.wall_lo, snap_host(xy[k], q, inv_q)));
+        xy[k] = std::min(whi((int)(k / 2)), std::max(wlo((int)(k / 2)), snap_host(xy[k], q, inv_q)));
     }
     spr[r].assign(p.n, 0);
     if (specs[r].sp)
@@ -797,6 +817,25 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
       BD_TRY(cudaMemsetAsync(d.wrap, 0, (size_t)np, h->stream));
     }
     BD_TRY(dalloc(h, &d.disp, (size_t)np));
+    d.rad = nullptr;
+    d.wall = nullptr;
+    if (specs[0].rad) {
+      // polydisperse disks (one replica): radius and grid walls per slot
+      const RepHost &RH = h->reps[0];
+      const double *rad = specs[0].rad;
+      std::vector<double> rs((size_t)np, a);
+      std::vector<double2> ws((size_t)np, make_double2(RH.wall_lo, RH.wall_hi));
+      for (int sl = 0; sl < np; ++sl) {
+        if (slot_rep[sl] < 0) continue;
+        const double ri = rad[slot_local[sl]];
+        rs[sl] = ri;
+        if (!RH.periodic) ws[sl] = make_double2(ceil(ri * inv_q) * q, floor((RH.L - ri) * inv_q) * q);
+      }
+      BD_TRY(dalloc(h, &d.rad, (size_t)np));
+      BD_TRY(dalloc(h, &d.wall, (size_t)np));
+      BD_TRY(cudaMemcpy(d.rad, rs.data(), rs.size() * sizeof(double), cudaMemcpyHostToDevice));
+      BD_TRY(cudaMemcpy(d.wall, ws.data(), ws.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    }
     {
       BdRep *rp = nullptr;
       BD_TRY(dalloc(h, &rp, (size_t)R));
@@ -1379,6 +1418,14 @@ int bd_init(const bd_params *p, const double *xy, const uint8_t *species, const 
   if (!out || !p) return BD_ERR_ARG;
   std::vector<Spec> specs(1);
   specs[0] = {*p, xy, species, theta};
+  return build_handle(specs, stream, out);
+}
+
+int bd_init_radii(const bd_params *p, const double *xy, const uint8_t *species, const float *theta,
+                  const double *radii, void *stream, bd_handle **out) {
+  if (!out || !p || !xy || !radii) return BD_ERR_ARG;
+  std::vector<Spec> specs(1);
+  specs[0] = {*p, xy, species, theta, radii};
   return build_handle(specs, stream, out);
 }
 

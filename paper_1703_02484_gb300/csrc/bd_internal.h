@@ -133,6 +133,10 @@ struct BdDev {
                                   // unique to the pass: never repeats within a handle's life)
   uint8_t *wrap;           // periodic box: re-entries of the last move (bits 0-1 x, 2-3 y; 1 = -L, 3 = +L)
   double2 *disp;
+  // polydisperse disks (null when every disk has radius a): per slot its
+  // radius and its wall bounds (lo, hi) on the position grid
+  double *rad;
+  double2 *wall;
   const BdRep *rep;        // [R]
   // triangulation (corner table), all replicas
   int4 *tv, *tn, *tv_snap, *tn_snap;

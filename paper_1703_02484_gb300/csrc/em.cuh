@@ -183,6 +183,23 @@ __device__ __forceinline__ double2 em_move(const BdConst &c, const BdRep &R, uin
   return make_double2(snapd(nx, c.q, c.inv_q), snapd(ny, c.q, c.inv_q));
 }
 
+// the walls (lo, hi) that disk i's centre stays between: its own for
+// polydisperse disks (a_i from each wall), else the replica's
+__device__ __forceinline__ double2 walls_of(const BdDev &d, const BdRep &R, int i) {
+  return d.wall ? d.wall[i] : make_double2(R.wall_lo, R.wall_hi);
+}
+
+// mirror reflection between walls w = (lo, hi); flags as reflect()
+__device__ __forceinline__ double2 reflect_w(double2 w, double2 y, int *flags) {
+  int f = 0;
+  if (y.x < w.x) { y.x = 2.0 * w.x - y.x; f |= 1; }
+  if (y.x > w.y) { y.x = 2.0 * w.y - y.x; f |= 2; }
+  if (y.y < w.x) { y.y = 2.0 * w.x - y.y; f |= 4; }
+  if (y.y > w.y) { y.y = 2.0 * w.y - y.y; f |= 8; }
+  *flags = f;
+  return y;
+}
+
 // mirror reflection at the walls; flags bits: 1 x<lo, 2 x>hi, 4 y<lo, 8 y>hi
 __device__ __forceinline__ double2 reflect(const BdRep &R, double2 y, int *flags) {
   int f = 0;

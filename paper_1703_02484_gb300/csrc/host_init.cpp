@@ -431,9 +431,18 @@ static void cell_sort(int n, const double *xy, double lo, double cs, int nc, std
   for (int i = 0; i < n; ++i) order[fill[cell[i]]++] = i;
 }
 
+// a pair's overlap test: closer than dmin, or for polydisperse disks (rad
+// given) closer than (rad_i + rad_j)(1 - 1e-12); dmin is then the largest
+// contact distance (the cell size)
+static inline bool too_close(double d2, double dmin, const double *rad, int i, int j) {
+  if (!rad) return d2 < dmin * dmin;
+  const double s = (rad[i] + rad[j]) * (1.0 - 1e-12);
+  return d2 < s * s;
+}
+
 // periodic minimum-image overlap check (centres in [0, L)): 1 if some pair
-// is closer than dmin
-int any_overlap_periodic(int n, const double *xy, double L, double dmin) {
+// is closer than dmin (polydisperse: than rad_i + rad_j)
+int any_overlap_periodic(int n, const double *xy, double L, double dmin, const double *rad) {
   int nc = std::max(1, std::min(4096, (int)floor(L / dmin)));
   if (nc < 3) {
     for (int i = 0; i < n; ++i)
@@ -441,7 +450,7 @@ int any_overlap_periodic(int n, const double *xy, double L, double dmin) {
         double dx = xy[2 * j] - xy[2 * i], dy = xy[2 * j + 1] - xy[2 * i + 1];
         dx -= L * nearbyint(dx / L);
         dy -= L * nearbyint(dy / L);
-        if (dx * dx + dy * dy < dmin * dmin) return 1;
+        if (too_close(dx * dx + dy * dy, dmin, rad, i, j)) return 1;
       }
     return 0;
   }
@@ -459,7 +468,7 @@ int any_overlap_periodic(int n, const double *xy, double L, double dmin) {
           double dx = xy[2 * j] - xy[2 * i], dy = xy[2 * j + 1] - xy[2 * i + 1];
           dx -= L * nearbyint(dx / L);
           dy -= L * nearbyint(dy / L);
-          if (dx * dx + dy * dy < dmin * dmin) return 1;
+          if (too_close(dx * dx + dy * dy, dmin, rad, i, j)) return 1;
         }
       }
   }
@@ -571,8 +580,8 @@ int lattice_place(int n, double lo, double hi, double dmin, uint64_t seed, std::
 }
 
 // minimum pair distance check with a cell grid: returns 1 if some pair is
-// closer than dmin
-int any_overlap(int n, const double *xy, double lo, double hi, double dmin) {
+// closer than dmin (polydisperse: than rad_i + rad_j)
+int any_overlap(int n, const double *xy, double lo, double hi, double dmin, const double *rad) {
   double W = hi - lo;
   int nc = std::max(1, std::min(4096, (int)floor(W / dmin)));
   double cs = W / nc;
@@ -587,7 +596,7 @@ int any_overlap(int n, const double *xy, double lo, double hi, double dmin) {
           const int j = order[k];
           if (j >= i) continue;
           const double dx = xy[2 * j] - xy[2 * i], dy = xy[2 * j + 1] - xy[2 * i + 1];
-          if (dx * dx + dy * dy < dmin * dmin) return 1;
+          if (too_close(dx * dx + dy * dy, dmin, rad, i, j)) return 1;
         }
       }
   }

@@ -632,8 +632,9 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
               const double dx = bdem::grid_to_double(ix, x.g.s), dy = bdem::grid_to_double(iy, x.g.s);
               const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
               const double r = sqrt(r2);
-              if (r < sigma) {
-                const double del = sigma - r;
+              const double sg = d.rad ? d.rad[u] + d.rad[w] : sigma;   // polydisperse: a_u + a_w
+              if (r < sg) {
+                const double del = sg - r;
                 const double nx = dx / r, ny = dy / r;
                 atomicAdd(&d.disp[u].x, -del * nx);
                 atomicAdd(&d.disp[u].y, -del * ny);
@@ -756,8 +757,9 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
               const double dx = bdem::grid_to_double(ix, x.g.s), dy = bdem::grid_to_double(iy, x.g.s);
               const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
               const double r = sqrt(r2);
-              if (r < sigma) {
-                const double del = sigma - r;
+              const double sg = d.rad ? d.rad[u] + d.rad[w] : sigma;   // polydisperse: a_u + a_w
+              if (r < sg) {
+                const double del = sg - r;
                 const double nx = dx / r, ny = dy / r;
                 atomicAdd(&d.disp[u].x, -del * nx);
                 atomicAdd(&d.disp[u].y, -del * ny);
@@ -982,7 +984,6 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
     // ---------------- A: apply (capped at sigma/4) ----------------
     phase_begin(ctl, b);
     {
-      const double cap = 0.25 * sigma;
       int nwrap = 0;
       for (int i = tid; i < x.np; i += nth) {
         if (d.ext_id[i] < 0) continue;
@@ -1003,6 +1004,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           continue;
         }
         const double mag = sqrt(__dadd_rn(__dmul_rn(dd.x, dd.x), __dmul_rn(dd.y, dd.y)));
+        // Sec. 4.4: sigma/4, half the disk's radius (its own for polydisperse disks)
+        const double cap = d.rad ? 0.5 * d.rad[i] : 0.25 * sigma;
         const bool capped = mag > cap;
         const double sc = capped ? cap / mag : 1.0;
         const double2 y = make_double2(snap(__dadd_rn(p.x, __dmul_rn(dd.x, sc)), x.g),
@@ -1020,7 +1023,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           if (wr) ++nwrap;
           np2 = make_double2(bdem::grid_to_double(X, x.g.s), bdem::grid_to_double(Y, x.g.s));
         } else {
-          np2 = bdem::reflect(R, y, &rfl);
+          np2 = bdem::reflect_w(bdem::walls_of(d, R, i), y, &rfl);
         }
         if (log_pidx >= 0) d.log_pflags[(size_t)log_pidx * x.np + i] = (uint8_t)(rfl | (capped ? 16 : 0));
         d.pos[i] = np2;

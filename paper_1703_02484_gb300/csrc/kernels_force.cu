@@ -568,7 +568,8 @@ __global__ void k_integrate(BdDev d, BdConst c, long long step, int log_step, in
     d.wrap[i] = (uint8_t)wr;
     if (wr && !c.overlap_verlet) atomicAdd(&d.ctl->n_wrapped, 1);
   } else {
-    flags = bdem::reflect_grid(bdpred::to_int(R.wall_lo, g), bdpred::to_int(R.wall_hi, g), X, Y);
+    const double2 w = bdem::walls_of(d, R, i);
+    flags = bdem::reflect_grid(bdpred::to_int(w.x, g), bdpred::to_int(w.y, g), X, Y);
   }
   d.pos[i] = make_double2(bdem::grid_to_double(X, c.qshift), bdem::grid_to_double(Y, c.qshift));
   if (!R.periodic)

@@ -30,6 +30,7 @@ __device__ __forceinline__ double periodic_grid(double v, double L, const BdCons
 }
 
 // a centre must be finite and, with walls, lie in [a, L - a] up to 1e-9 L
+// (a_i for polydisperse disks)
 __global__ void k_state_check(BdDev d, BdConst c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= c.np) return;
@@ -40,7 +41,8 @@ __global__ void k_state_check(BdDev d, BdConst c) {
   bool bad = !isfinite(p.x) || !isfinite(p.y);
   if (!R.periodic) {
     const double tol = __dmul_rn(1e-9, R.L);
-    const double lo = __dsub_rn(c.a, tol), hi = __dadd_rn(__dsub_rn(R.L, c.a), tol);
+    const double ai = d.rad ? d.rad[i] : c.a;
+    const double lo = __dsub_rn(ai, tol), hi = __dadd_rn(__dsub_rn(R.L, ai), tol);
     bad = bad || p.x < lo || p.x > hi || p.y < lo || p.y > hi;
   }
   if (bad) atomicCAS(&d.ctl->status, 0, BD_ERR_INIT_OVERLAP);
@@ -60,8 +62,8 @@ __global__ void k_state_in(BdDev d, BdConst c, int with_theta) {
   if (R.periodic) {
     y = make_double2(periodic_grid(p.x, R.L, c), periodic_grid(p.y, R.L, c));
   } else {
-    y = make_double2(fmin(R.wall_hi, fmax(R.wall_lo, snap_grid(p.x, c))),
-                     fmin(R.wall_hi, fmax(R.wall_lo, snap_grid(p.y, c))));
+    const double2 w = bdem::walls_of(d, R, i);
+    y = make_double2(fmin(w.y, fmax(w.x, snap_grid(p.x, c))), fmin(w.y, fmax(w.x, snap_grid(p.y, c))));
   }
   {
     // the move from the previous positions, for the triangulation's FP32

@@ -302,8 +302,9 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
   const double2 pi = d.pos[i];
   const int m = d.vl_cnt[i];
   const float rc2 = (float)(R.r_cut * R.r_cut);
-  const float sg = (float)c.sigma, eps = (float)R.eps, kap = (float)R.kappa;
-  const float rwca2 = (float)(1.2599210498948732 * c.sigma * c.sigma);  // (2^(1/6) s)^2
+  const float eps = (float)R.eps, kap = (float)R.kappa;
+  // the law's length scale s: 2a, or a_i + a_j for polydisperse disks
+  const double ai = d.rad ? d.rad[i] : 0.0;
   float fx = 0.f, fy = 0.f;      // Yukawa tail, FP32
   ff gx = {0.f, 0.f}, gy = {0.f, 0.f};   // WCA core, float-float sums
   // four list entries at a time: their index loads, then their position
@@ -341,6 +342,9 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
       const float dx = __fadd_rn(hx, lx);
       const float dy = __fadd_rn(hy, ly);
       const float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+      const double sd = d.rad ? ai + d.rad[j] : c.sigma;
+      const float sg = (float)sd;
+      const float rwca2 = (float)(1.2599210498948732 * sd * sd);  // (2^(1/6) s)^2
       if (fabsf(r2 - rc2) < 1e-5f * rc2) {
         // at the cut-off the force jumps: decide as the FP64 reference does
         const double2 pj = d.pos[j];
@@ -364,7 +368,8 @@ __global__ void k_force_verlet(BdDev d, BdConst c) {
         ff ex = ff_make(hx, lx);
         ff ey = ff_make(hy, ly);
         ff q2 = ff_add(ff_mul(ex, ex), ff_mul(ey, ey));
-        ff s2 = ff_div({sg * sg, 0.f}, q2);
+        const float sh = (float)(sd * sd);
+        ff s2 = ff_div({sh, (float)(sd * sd - (double)sh)}, q2);   // s^2 as a float-float pair
         ff s6 = ff_mul(ff_mul(s2, s2), s2);
         ff t = ff_add(ff_scale(ff_mul(s6, s6), 2.0f), {-s6.hi, -s6.lo});
         ff cw = ff_div(ff_scale(t, 24.0f * eps), q2);

@@ -122,8 +122,9 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
           const double dx = bdem::grid_to_double(imin_image(bdpred::to_int(pj.x, g) - bdpred::to_int(pi.x, g), R), c.qshift);
           const double dy = bdem::grid_to_double(imin_image(bdpred::to_int(pj.y, g) - bdpred::to_int(pi.y, g), R), c.qshift);
           const double r = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-          if (r < sigma) {
-            const double del = sigma - r;
+          const double sg = d.rad ? d.rad[i] + d.rad[j] : sigma;   // polydisperse: a_i + a_j
+          if (r < sg) {
+            const double del = sg - r;
             sx -= del * (dx / r);
             sy -= del * (dy / r);
             hit = 1;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
     // ---------------- apply (capped at sigma/4), reflect ----------------
     phase_begin(ctl, b);
     {
-      const double cap = 0.25 * sigma;
+      const double cap_eq = 0.25 * sigma;
       for (int i = tid; i < c.np; i += nth) {
         if (d.ext_id[i] < 0) continue;
         const double2 dd = d.disp[i];
@@ -183,6 +184,7 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
         const double2 p = d.pos[i];
         d.prev[i] = p;
         const double mag = sqrt(__dadd_rn(__dmul_rn(dd.x, dd.x), __dmul_rn(dd.y, dd.y)));
+        const double cap = d.rad ? 0.5 * d.rad[i] : cap_eq;   // half the disk's own radius
         const double sc = mag > cap ? cap / mag : 1.0;
         const double2 y = make_double2(bdem::snapd(__dadd_rn(p.x, __dmul_rn(dd.x, sc)), c.q, c.inv_q),
                                        bdem::snapd(__dadd_rn(p.y, __dmul_rn(dd.y, sc)), c.q, c.inv_q));
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(BD_VC_THREADS) k_overlap_verlet(BdDev d, BdCon
           bdem::wrap_grid(R.LQ, X, Y);
           pn = make_double2(bdem::grid_to_double(X, c.qshift), bdem::grid_to_double(Y, c.qshift));
         } else {
-          pn = bdem::reflect(R, y, &rfl);
+          pn = bdem::reflect_w(bdem::walls_of(d, R, i), y, &rfl);
         }
         d.pos[i] = pn;
         d.work[i] = bdem::split(pn);

@@ -351,7 +351,7 @@ int bd_rollout(bd_handle *h, int32_t nsteps, int32_t ckpt_every, int32_t loss_ki
   if (stats) memset(stats, 0, sizeof(*stats));
   if (loss_kind != BD_LOSS_MSD && loss_kind != BD_LOSS_HIST) return BD_ERR_UNSUPPORTED;
   if (h->reps.size() != 1 || h->reps[0].p.law != BD_LAW_LONG || h->reps[0].periodic ||
-      h->reps[0].p.n_species > 2)
+      h->reps[0].p.n_species > 2 || h->d.rad)
     return BD_ERR_UNSUPPORTED;
   if (!h->ro) {
     h->ro = new (std::nothrow) BdRollout;
