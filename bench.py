@@ -137,6 +137,34 @@ def rank_params(bd, cfg, rank, modes=()):
     return p
 
 
+def shard_replicas(ns, laws, world, short_cost=3000.0):
+    """Cost-balanced assignment of independent replicas to ranks (greedy:
+    largest cost first, each to the least-loaded rank).  A long-range replica
+    costs N^2 (all pairs), a short-range one short_cost * N (its per-disk work
+    measured against the all-pairs sweep's per-pair work on one GPU: about
+    0.5 ns per disk-step at 2^20 disks against 1.65e-4 ns per pair at
+    N = 1e5).  Returns one ascending list of replica indices per rank."""
+    cost = [float(n) * n if law == 1 else short_cost * float(n) for n, law in zip(ns, laws)]
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for r in sorted(range(len(cost)), key=lambda k: (-cost[k], k)):
+        w = min(range(world), key=lambda k: (load[k], k))
+        out[w].append(r)
+        load[w] += cost[r]
+    return [sorted(v) for v in out]
+
+
+def sharded_step(system, F, ws):
+    """One step of a system whose all-pairs sweep is shared among the ranks:
+    this rank's partial forces into F, one sum over the ranks, then the move
+    and the correction with the summed forces on every rank."""
+    system.step_begin(F.data_ptr())
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(F)
+    return system.step_end(F.data_ptr())
+
+
 def run_reference(args):
     """The oracle (plain FP64 CPU restatement) on the same workload, host cores.
 
@@ -261,14 +289,22 @@ def run_batched(args):
     import torch
     import paper_1703_02484_gb300 as bd
     from paper_1703_02484_gb300 import workloads
-    torch.cuda.set_device(0)
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     cfgs = workloads.batch_configs(256)
-    params = []
+    params_all = []
     for r, cfg in enumerate(cfgs):
         p = bd.params_from_config(cfg)
         p.replica = r
         p.seed = 3 + 1000 * r
-        params.append(p)
+        params_all.append(p)
+    # N > 1: the replicas are shared out by cost (strong scaling: the same 256)
+    mine = shard_replicas([p.n for p in params_all], [p.law for p in params_all], ws)[rank]
+    params = [params_all[r] for r in mine]
+    N_all = sum(p.n for p in params_all)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     b = bd.System(params, stream=stream.cuda_stream)
@@ -277,15 +313,31 @@ def run_batched(args):
     for _ in range(args.warmup):
         b.step(1)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(0) as clk:
+    with ClockSampler(local) as clk:
         ev0.record(stream)
         st = b.step(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    if ws > 1:
+        dist.barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws, "cuda") / args.steps
     tune = b.tuning()
     b.close()
+    if ws > 1:
+        if rank == 0:
+            line = {"metric": "particle-steps/s (c4: 256 batched replicas)", "value": N_all / (ms / 1e3),
+                    "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                    "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+                    "data": "synthetic",
+                    "config": {"workload": "c4: 256 replicas shared out by cost over %d ranks" % ws, "N": N_all,
+                               "replicas_rank0": len(mine), "disks_rank0": N, "tuning_rank0": tune},
+                    "clocks": clk.summary(), "gpu_launches": None}
+            print(json.dumps(line), flush=True)
+        dist.destroy_process_group()
+        return
     # the same replicas one handle at a time (sampled: every 8th replica)
     sample = list(range(0, 256, 8))
     alone_ms = 0.0
@@ -315,6 +367,53 @@ def run_batched(args):
                        "steps_done": st["steps_done"], "rejected": st["rejected"]},
             "clocks": clk.summary(), "gpu_launches": None}
     print(json.dumps(line), flush=True)
+
+
+def run_sharded(args):
+    """The N = 1e5 system on N ranks at once: each rank computes its share of
+    the all-pairs sweep, the partial forces are summed by one all-reduce per
+    step, and every rank advances the whole system (strong scaling: one
+    system, N = 1e5 whatever the rank count)."""
+    import torch
+    import paper_1703_02484_gb300 as bd
+    from paper_1703_02484_gb300 import workloads
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cfg = workloads.CONFIGS["n1e5"]
+    xy, sp, th = workloads.initial_state(cfg)
+    stream = torch.cuda.current_stream()
+    system = bd.System(bd.params_from_config(cfg), xy, sp, th, stream=stream.cuda_stream)
+    system.set_force_shard(rank, ws)
+    F = torch.empty(2 * system.force_slots(), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        sharded_step(system, F, ws)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            sharded_step(system, F, ws)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws, "cuda") / args.steps
+    if rank == 0:
+        line = {"metric": "particle-steps/s (n1e5, all-pairs sweep shared over the ranks)",
+                "value": cfg.n / (ms / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD + "; force sweep sharded over %d ranks, one FP64 all-reduce of "
+                                                  "%d bytes per step" % (ws, F.numel() * 8),
+                           "N": cfg.n, "seed": cfg.seed, "parallelism": "force-shard%d" % ws},
+                "clocks": clk.summary(), "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    system.close()
+    if ws > 1:
+        dist.destroy_process_group()
 
 
 def run_adjoint(args):
@@ -384,7 +483,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--workload", default="n1e5",
-                    help="configuration name (n1e5 is the headline; c1, c2, c3, c5, c4 (batched), "
+                    help="configuration name (n1e5 is the headline; n1e5-shard (its all-pairs sweep shared "
+                         "over the ranks); c1, c2, c3, c5, c4 (batched), "
                          "c5-grad (differentiated rollout, MSD loss; c5-grad-hist: histogram loss); suffixes -verlet (overlap correction over "
                          "the Verlet lists) and -periodic (periodic box), e.g. c3-verlet, n1e5-periodic)")
     args = ap.parse_args()
@@ -397,6 +497,9 @@ def main():
         return
     if args.workload in ("c5-grad", "c5-grad-hist"):
         run_adjoint(args)
+        return
+    if args.workload == "n1e5-shard":
+        run_sharded(args)
         return
 
     import torch

@@ -247,6 +247,35 @@ int bd_set_loop_caps(bd_handle *h, int32_t max_corr_iters, int32_t max_flip_roun
  * Errors: BD_ERR_ARG, BD_ERR_CUDA. */
 int bd_set_wait_limit(bd_handle *h, double seconds, int32_t hold_barrier);
 
+/* ---- Force sharding over several GPUs (no counterpart in the paper) ----
+ * Of one step only the all-pairs force sum divides cleanly among processes:
+ * the triangulation stages need every position.  A sharded system runs on
+ * every rank in full, each rank computing its share of the symmetric
+ * sweep's work items (split by pair count) and all ranks adding their
+ * partial forces with one all-reduce per step; every rank then advances the
+ * same state with the same forces (the correction's sums are
+ * order-independent), so the ranks stay identical.  Per step:
+ *   bd_step_begin(h, F)            this rank's partial forces into F,
+ *   all-reduce (sum) of F over the ranks (e.g. NCCL, by the caller),
+ *   bd_step_end(h, F, stats)       the move and the correction with F.
+ *
+ * bd_set_force_shard: make h rank `rank` of `world` (world = 1: the whole
+ * sweep).  Single-system handles with the long-range law in FP32, without
+ * step halving (BD_ERR_UNSUPPORTED otherwise); a one-sided sweep is replaced
+ * by the symmetric one.  While world > 1 bd_step returns BD_ERR_UNSUPPORTED
+ * and bd_compute_forces returns this rank's partial force.
+ * bd_force_slots: the length of F in double2 entries (the handle's internal
+ * disk slots, padding included; the layout is the library's).
+ * bd_step_begin: F is a DEVICE pointer to 2 * slots doubles, caller-owned;
+ *   returns when F holds the partial forces.
+ * bd_step_end: F as summed over the ranks (DEVICE, 2 * slots doubles); one
+ *   time step as bd_step takes it, with these forces.  Returns as bd_step.
+ * Errors: BD_ERR_ARG, BD_ERR_UNSUPPORTED, BD_ERR_CUDA and bd_step's. */
+int bd_set_force_shard(bd_handle *h, int32_t rank, int32_t world);
+int bd_force_slots(bd_handle *h, int32_t *slots);
+int bd_step_begin(bd_handle *h, double *forces);
+int bd_step_end(bd_handle *h, const double *forces, bd_step_stats *stats);
+
 /* bd_init for polydisperse disks (Sec. 2.3: the method extends directly to
  * disks whose radii do not differ too much).  Disk i has radius radii[i] in
  * (0, p->a] (p->a is the largest radius; it lays out the ghost points and

@@ -108,6 +108,10 @@ SIGNATURES = [
     ("bd_set_wait_limit", ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int32]),
     ("bd_set_loop_caps", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("bd_noise_sample", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P]),
+    ("bd_set_force_shard", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    ("bd_force_slots", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    ("bd_step_begin", ctypes.c_int, [_P, _P]),
+    ("bd_step_end", ctypes.c_int, [_P, _P, ctypes.POINTER(bd_step_stats)]),
     ("bd_free", None, [_P]),
     ("bd_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -295,6 +299,27 @@ class System:
         xy = np.ascontiguousarray(xy, dtype=np.float64)
         th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
         _check(load().bd_set_state(self.h, _ptr(xy), _ptr(th)), "bd_set_state")
+
+    # ---- force sharding (one system on several ranks) ----
+    def set_force_shard(self, rank, world):
+        """bd_set_force_shard: compute this rank's share of the all-pairs sweep."""
+        _check(load().bd_set_force_shard(self.h, int(rank), int(world)), "bd_set_force_shard")
+
+    def force_slots(self):
+        """Length (double2 entries) of the force buffer of bd_step_begin / bd_step_end."""
+        k = ctypes.c_int32()
+        _check(load().bd_force_slots(self.h, ctypes.byref(k)), "bd_force_slots")
+        return k.value
+
+    def step_begin(self, forces_dev_ptr):
+        """bd_step_begin: this rank's partial forces into the device buffer."""
+        _check(load().bd_step_begin(self.h, ctypes.c_void_p(int(forces_dev_ptr))), "bd_step_begin")
+
+    def step_end(self, forces_dev_ptr):
+        """bd_step_end: one step with the summed forces in the device buffer."""
+        st = bd_step_stats()
+        _check(load().bd_step_end(self.h, ctypes.c_void_p(int(forces_dev_ptr)), ctypes.byref(st)), "bd_step_end")
+        return st.as_dict()
 
     def last_stats(self):
         """Counters of the last bd_step / bd_batch_step / bd_set_state call (bd_last_stats)."""

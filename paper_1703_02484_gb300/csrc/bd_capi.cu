@@ -702,6 +702,17 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
   c.inv_q = inv_q;
   c.qshift = s_shift;
   {
+    // fixed-point displacement sums: up to 128 contributions of at most sigma
+    // (in grid units below 2^51 * 2 sigma / E) fit in 62 bits with F fraction
+    // bits below the grid (F >= 4)
+    const double lim = 128.0 * 2.0 * a * inv_q;
+    int F = 62 - (int)ceil(log2(std::max(lim, 2.0)));
+    F = std::max(4, std::min(F, 40));
+    c.disp_scale = ldexp(1.0, s_shift + F);
+    c.disp_unscale = ldexp(1.0, -(s_shift + F));
+  }
+  c.sitem0 = 0;
+  {
     // (sigma/q)^2 (1 + 1e-9), rounded up, as a 128-bit integer
     long double sq = (long double)(2.0 * a) * (long double)inv_q;
     long double v = sq * sq * (1.0L + 1e-9L);
@@ -1444,6 +1455,7 @@ int bd_batch_init(int32_t R, const bd_params *p, const double *xy, const uint8_t
 
 int bd_step(bd_handle *h, int32_t nsteps, bd_step_stats *stats) {
   if (!h || nsteps < 0) return BD_ERR_ARG;
+  if (h->shard_world > 1) return BD_ERR_UNSUPPORTED;   // a force shard steps by bd_step_begin / bd_step_end
   if (stats) memset(stats, 0, sizeof(*stats));
   cudaError_t e = reset_stats(h);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -1664,6 +1676,76 @@ int bd_noise_sample(uint64_t seed, int32_t replica, int32_t n, const uint32_t *c
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(buf);
   return e == cudaSuccess ? BD_OK : cuda_fail(e);
+}
+
+int bd_set_force_shard(bd_handle *h, int32_t rank, int32_t world) {
+  if (!h || world < 1 || rank < 0 || rank >= world) return BD_ERR_ARG;
+  if (h->reps.size() != 1 || !h->c.any_long || h->c.precision != 0 || h->max_halvings > 0)
+    return BD_ERR_UNSUPPORTED;
+  cudaError_t e = cudaSuccess;
+  if (h->c.force_variant < 2) e = use_variant(h, 3, 8);   // shards cut the symmetric sweep's plan
+  if (e != cudaSuccess) return cuda_fail(e);
+  // the plan as uploaded (make_sym is deterministic); an item's cost is its
+  // number of j tiles (pairs of a 512-disk block with a 256-disk tile)
+  SymPlan S;
+  make_sym(h, h->tune_tiles, h->c.force_variant, S);
+  const int ni = (int)S.items.size();
+  std::vector<double> cum(ni + 1, 0.0);
+  for (int k = 0; k < ni; ++k) cum[k + 1] = cum[k] + (S.items[k].z - S.items[k].y);
+  // rank r: the items whose cumulative cost starts in [r T / W, (r + 1) T / W)
+  auto first = [&](int r) {
+    const double target = cum[ni] * r / world;
+    return (int)(std::lower_bound(cum.begin(), cum.end() - 1, target) - cum.begin());
+  };
+  const int b0 = rank == 0 ? 0 : first(rank), b1 = rank + 1 == world ? ni : first(rank + 1);
+  // partials of items that are not this rank's stay zero in the reduction
+  e = cudaMemsetAsync(h->d.ipart, 0, (size_t)ni * BD_SB * sizeof(float2), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d.jpart, 0, (size_t)S.n_jtiles * BD_TJ * sizeof(float2), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  h->c.sitem0 = b0;
+  h->c.n_sitems = b1 - b0;
+  h->shard_rank = rank;
+  h->shard_world = world;
+  return BD_OK;
+}
+
+int bd_force_slots(bd_handle *h, int32_t *slots) {
+  if (!h || !slots) return BD_ERR_ARG;
+  *slots = h->np;
+  return BD_OK;
+}
+
+int bd_step_begin(bd_handle *h, double *forces) {
+  if (!h || !forces || h->reps.size() != 1 || !h->c.any_long || h->c.precision != 0) return BD_ERR_ARG;
+  cudaStream_t st = h->stream;
+  cudaError_t e = reset_stats(h);
+  if (e == cudaSuccess) e = bd_launch_force_long(h->d, h->c, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(forces, h->d.fpart, (size_t)h->np * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? BD_OK : cuda_fail(e);
+}
+
+int bd_step_end(bd_handle *h, const double *forces, bd_step_stats *stats) {
+  if (!h || !forces || h->reps.size() != 1 || !h->c.any_long || h->c.precision != 0) return BD_ERR_ARG;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  cudaStream_t st = h->stream;
+  const int64_t step_base = h->step;
+  cudaError_t e = cudaMemcpyAsync(h->d.fpart, forces, (size_t)h->np * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = bd_launch_integrate(h->d, h->c, h->step, -1, st);
+  if (e == cudaSuccess) e = launch_correction(h, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  h->last_launches = 2;
+  int rc = read_ctl(h);
+  if (rc) return rc;
+  const BdCtl &k = *h->h_ctl;
+  add_stage_times(h);
+  h->step = step_base + k.st_steps;
+  fill_stats(h, k.status, 0);
+  if (stats) *stats = h->last_stats;
+  if (k.status) return finish_status(h, k.status);
+  return BD_OK;
 }
 
 int bd_last_stats(bd_handle *h, bd_step_stats *stats) {

@@ -66,6 +66,7 @@ struct bd_handle {
   int4 *hs_tv = nullptr, *hs_tn = nullptr;
   int *hs_vt = nullptr;
   bd_step_stats last_stats = {};   // counters of the last bd_step / bd_batch_step / bd_set_state
+  int shard_rank = 0, shard_world = 1;   // force sharding (bd_set_force_shard)
   double stage_ns[5] = {0, 0, 0, 0, 0};   // triangulation-kernel stage times since the last reset
   int64_t stage_cnt[5] = {0, 0, 0, 0, 0};
 };

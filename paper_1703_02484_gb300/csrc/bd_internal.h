@@ -184,6 +184,13 @@ struct BdConst {
   double a, sigma;
   double q, inv_q;
   int qshift;              // q = 2^-qshift
+  // Algorithm 2's displacement sums over the triangulation edges are added as
+  // fixed-point integers (order-independent, so every run sums to the same
+  // bits): a value v is held as rint(v * disp_scale), disp_scale = 2^(qshift + F)
+  double disp_scale, disp_unscale;
+  // force sharding (bd_set_force_shard): the symmetric sweep runs work items
+  // [sitem0, sitem0 + n_sitems) of the plan
+  int sitem0;
   unsigned long long sig2q_hi, sig2q_lo;  // ceil((sigma/q)^2 (1 + 1e-9)) as 128-bit
   int max_corr_iters, max_flip_rounds;
   int force_variant;       // 0: scalar FP32 sweep, 1: packed f32x2 sweep, 2, 3: symmetric packed sweeps

@@ -15,7 +15,8 @@
 //      rounds repeat until none is left.  Only edges touching a triangle that
 //      moved or flipped are re-tested.
 //   A  overlap correction (Algorithm 2): every real edge with r < sigma adds
-//      -+ (sigma - r) r_hat to its end points' FP64 displacement (atomics); each
+//      -+ (sigma - r) r_hat to its end points' displacement (fixed-point
+//      integer atomics: the sums do not depend on the order); each
 //      disk then moves by its sum capped at sigma/4 (Sec. 4.4) and reflects at
 //      the walls.  Then P-R-F run again on the moved disks, and the loop ends
 //      when a pass over the Delaunay edges of the current positions finds no
@@ -112,6 +113,21 @@ __device__ __noinline__ int orient_lifted(long long ax, long long ay, long long 
 __device__ __noinline__ int incircle_lifted(long long ax, long long ay, long long bx, long long by, long long cx,
                                             long long cy, long long px, long long py) {
   return bdpred::incircle_int(ax, ay, bx, by, cx, cy, px, py);
+}
+
+// Algorithm 2's per-disk displacement sums as fixed-point integers in the
+// disp words: integer adds are associative, so the sum (and every position
+// after the pass) does not depend on the order the edges arrive in.  A
+// contribution is rounded to disp_unscale (a small fraction of the position
+// grid) once; zero is the same bit pattern in both readings of the words.
+__device__ __forceinline__ void disp_add(const Ctx &x, int i, double vx, double vy) {
+  long long *w = (long long *)&x.d.disp[i];
+  atomicAdd((unsigned long long *)&w[0], (unsigned long long)__double2ll_rn(__dmul_rn(vx, x.c.disp_scale)));
+  atomicAdd((unsigned long long *)&w[1], (unsigned long long)__double2ll_rn(__dmul_rn(vy, x.c.disp_scale)));
+}
+__device__ __forceinline__ double2 disp_get(const Ctx &x, int i) {
+  const longlong2 w = *(const longlong2 *)&x.d.disp[i];
+  return make_double2(__dmul_rn((double)w.x, x.c.disp_unscale), __dmul_rn((double)w.y, x.c.disp_unscale));
 }
 
 // a test the FP32 filter could not decide (rare: near-degenerate inputs)
@@ -636,10 +652,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
               if (r < sg) {
                 const double del = sg - r;
                 const double nx = dx / r, ny = dy / r;
-                atomicAdd(&d.disp[u].x, -del * nx);
-                atomicAdd(&d.disp[u].y, -del * ny);
-                atomicAdd(&d.disp[w].x, del * nx);
-                atomicAdd(&d.disp[w].y, del * ny);
+                disp_add(x, u, -del * nx, -del * ny);
+                disp_add(x, w, del * nx, del * ny);
                 if (use_lists) push_tri(nlist, nmark, ncount, ngen, t);   // checked again in the next pass
                 const int k_ov = atomicAdd(cnt(ctl, b.ph, C_OVERLAP), 1);
                 if (logging) {
@@ -761,10 +775,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
               if (r < sg) {
                 const double del = sg - r;
                 const double nx = dx / r, ny = dy / r;
-                atomicAdd(&d.disp[u].x, -del * nx);
-                atomicAdd(&d.disp[u].y, -del * ny);
-                atomicAdd(&d.disp[w].x, del * nx);
-                atomicAdd(&d.disp[w].y, del * ny);
+                disp_add(x, u, -del * nx, -del * ny);
+                disp_add(x, w, del * nx, del * ny);
                 if (use_lists) push_tri(nlist, nmark, ncount, ngen, t);   // checked again in the next pass
                 const int k_ov = atomicAdd(cnt(ctl, b.ph, C_OVERLAP), 1);
                 if (logging) {
@@ -989,7 +1001,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         if (d.ext_id[i] < 0) continue;
         const double2 p = d.pos[i];
         d.prev[i] = p;
-        const double2 dd = d.disp[i];
+        const double2 dd = disp_get(x, i);
         if (PER) d.wrap[i] = 0;
         if (dd.x != 0.0 || dd.y != 0.0) {
           // the first disk of a replica moved by this pass counts the pass

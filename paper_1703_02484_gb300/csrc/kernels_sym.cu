@@ -135,7 +135,8 @@ __device__ __forceinline__ void force_long_sym_body(const BdDev &d, const BdCons
   __shared__ __align__(16) float4 sraw[2][STAGE ? BD_TJ : 1];   // STAGE 1: j as stored (x_hi, y_hi, x_lo, y_lo)
   __shared__ float2 sjl[2][BD_TJ];   // PER: the lo parts
   __shared__ float2 shw[NW][BD_TJ];  // per-warp j-side sums of the current tile
-  const int4 item = d.sitems[blockIdx.x];
+  const int item_id = c.sitem0 + (int)blockIdx.x;   // this launch's share of the plan (force sharding)
+  const int4 item = d.sitems[item_id];
   const int P = item.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int base = P * BD_SB;
   const int tsym = 2 * P + 2;        // first tile met from both sides
@@ -484,7 +485,7 @@ __device__ __forceinline__ void force_long_sym_body(const BdDev &d, const BdCons
     __syncthreads();
     buf ^= 1;
   }
-  float2 *ip = d.ipart + (size_t)blockIdx.x * BD_SB;
+  float2 *ip = d.ipart + (size_t)item_id * BD_SB;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     if constexpr (ACC == 2) ip[q * T + tid] = make_float2(__fadd_rn(fxh[q], fxl[q]), __fadd_rn(fyh[q], fyl[q]));
