@@ -829,6 +829,7 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     }
     BD_TRY(dalloc(h, &d.disp, (size_t)np));
     d.rad = nullptr;
+    d.radf = nullptr;
     d.wall = nullptr;
     if (specs[0].rad) {
       // polydisperse disks (one replica): radius and grid walls per slot
@@ -842,8 +843,15 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
         rs[sl] = ri;
         if (!RH.periodic) ws[sl] = make_double2(ceil(ri * inv_q) * q, floor((RH.L - ri) * inv_q) * q);
       }
+      std::vector<float2> rf((size_t)np);
+      for (int sl = 0; sl < np; ++sl) {
+        const float hi = (float)rs[sl];
+        rf[sl] = make_float2(hi, (float)(rs[sl] - (double)hi));
+      }
       BD_TRY(dalloc(h, &d.rad, (size_t)np));
+      BD_TRY(dalloc(h, &d.radf, (size_t)np));
       BD_TRY(dalloc(h, &d.wall, (size_t)np));
+      BD_TRY(cudaMemcpy(d.radf, rf.data(), rf.size() * sizeof(float2), cudaMemcpyHostToDevice));
       BD_TRY(cudaMemcpy(d.rad, rs.data(), rs.size() * sizeof(double), cudaMemcpyHostToDevice));
       BD_TRY(cudaMemcpy(d.wall, ws.data(), ws.size() * sizeof(double2), cudaMemcpyHostToDevice));
     }

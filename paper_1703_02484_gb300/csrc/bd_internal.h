@@ -136,6 +136,7 @@ struct BdDev {
   // polydisperse disks (null when every disk has radius a): per slot its
   // radius and its wall bounds (lo, hi) on the position grid
   double *rad;
+  float2 *radf;            // the radius as an FP32 (hi, lo) pair (the short-range law's length scale)
   double2 *wall;
   const BdRep *rep;        // [R]
   // triangulation (corner table), all replicas

@@ -424,7 +424,8 @@ __device__ __forceinline__ int key_corner(unsigned long long key) {
 // Three resident blocks per SM (at most 80 registers): the passes are
 // latency-bound chains of dependent loads, and the spills this costs sit in
 // the exact-predicate fallbacks (measured: 3 blocks 20 % faster than 2 on
-// 2^20 disks; 4 blocks slower at 1e5).
+// 2^20 disks; 4 blocks (64 registers) 1.5 % faster on 2^20 disks but 16 %
+// slower in the check passes at 1e5; 5 blocks slower on both).
 template <bool PER>
 __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdConst c, int mode,
                                                                  int log_step) {

@@ -592,7 +592,11 @@ cudaError_t bd_launch_force_sym(const BdDev &d, const BdConst &c, int variant, c
     else
       // 16 resident blocks (32 warps) per SM in 64 registers, j tiles staged by
       // cp.async: measured 1.776 -> 1.668 ms at N = 1e5 against the
-      // register-staged form (120 registers, 16 warps), forces unchanged
+      // register-staged form (120 registers, 16 warps), forces unchanged.
+      // Other shapes in the same budget measured slower at N = 1e5: ring
+      // unrolled 1 or 4 steps deep (+1.7 %, +1.1 %), two j disks per lane
+      // (+1.9 %), folded j accumulators (+3.5 %), one warp of 16 disks per
+      // lane (+2.7 %)
       k_force_long_sym_mb<2, 4, 1, false, 2, false, 16, 1, 2><<<c.n_sitems, 64, 0, s>>>(d, c);
   }
   k_force_sym_reduce<<<c.np / BD_RED_D, 4 * BD_RED_D, 0, s>>>(d, c);
