@@ -120,8 +120,8 @@ typedef struct bd_params {
                               lattice over [a, L - a]^2 with N* >= n sites (the widest spacing
                               s >= sigma that gives enough), n of them chosen by reservoir
                               sampling, each moved by a uniform offset within (s - sigma)/2
-                              (kept in the box) so the set is in general position and no two
-                              centres come closer than sigma.  Both draw from Philox streams
+                              (mirrored when it would leave the box) so the set is in general
+                              position and no two centres come closer than sigma.  Both draw from Philox streams
                               of `seed` (bd_place_disks gives the same positions). */
 } bd_params;
 
@@ -436,9 +436,12 @@ int bd_stage_times(bd_handle *h, int reset, double *ms, int64_t *phases);
 /* Start positions as bd_init draws them when it gets xy == NULL (Sec. 4.1
  * placement, bd_params.placement): n centres in [a, L - a]^2, pairwise at
  * least 2a apart, from the Philox streams of seed.  Host only (no GPU).
- *   xy  receives 2n doubles.  Errors: BD_ERR_ARG (n < 1, L <= 2a, a <= 0,
- *   unknown placement, or no placement found: the area fraction is too high
- *   for the lattice, or random addition jammed). */
+ *   xy  receives 2n doubles.  With the lattice every site is jittered (an
+ *   offset that would leave the box is mirrored), so the start is in general
+ *   position.  Errors: BD_ERR_ARG (n < 1, L <= 2a, a <= 0, unknown
+ *   placement, or no placement found: the area fraction is too high for the
+ *   lattice -- its spacing must exceed 2a by at least 2e-6 a so that the
+ *   sites can be jittered -- or random addition jammed). */
 int bd_place_disks(int32_t n, double L, double a, int32_t placement, uint64_t seed, double *xy);
 
 /* Host only: the fixed ghost points that close the triangulation of a box of

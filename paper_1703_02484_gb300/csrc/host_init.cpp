@@ -560,6 +560,10 @@ int lattice_place(int n, double lo, double hi, double dmin, uint64_t seed, std::
   }
   std::sort(res.begin(), res.end());
   const double jr = 0.5 * (sp - dmin);
+  // an (almost) unjittered triangular lattice has four sites on one circle
+  // everywhere: too close to the lattice's packing limit for a start in
+  // general position
+  if (!(jr >= 1e-6 * dmin)) return -1;
   xy.assign(2 * (size_t)n, 0.0);
   for (int i = 0; i < n; ++i) {
     double x, y;
@@ -568,11 +572,13 @@ int lattice_place(int n, double lo, double hi, double dmin, uint64_t seed, std::
                               bdrng::TAG_LATTICE);
     const double u0 = ((double)r.x + 0.5) * (1.0 / 4294967296.0), u1 = ((double)r.y + 0.5) * (1.0 / 4294967296.0);
     const double rad = jr * sqrt(u0), ang = 6.283185307179586 * u1;
-    const double jx = x + rad * cos(ang), jy = y + rad * sin(ang);
-    if (jx >= lo && jx <= hi && jy >= lo && jy <= hi) {
-      x = jx;
-      y = jy;
-    }
+    // an offset that would leave the box is mirrored (same length, so every
+    // pair stays at least dmin apart and every site is jittered)
+    double ox = rad * cos(ang), oy = rad * sin(ang);
+    if (x + ox < lo || x + ox > hi) ox = -ox;
+    if (y + oy < lo || y + oy > hi) oy = -oy;
+    x += ox;
+    y += oy;
     xy[2 * i] = x;
     xy[2 * i + 1] = y;
   }

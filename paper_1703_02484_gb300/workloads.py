@@ -169,10 +169,10 @@ def _lattice(n: int, L: float, a: float, rng: np.random.Generator):
     jr = 0.45 * (s - 2.0 * a)
     rr = jr * np.sqrt(rng.uniform(0.0, 1.0, size=n))
     ph = rng.uniform(0.0, 2.0 * math.pi, size=n)
-    moved = pts + np.stack([rr * np.cos(ph), rr * np.sin(ph)], axis=1)
-    inside = np.all((moved >= lo) & (moved <= hi), axis=1)
-    pts[inside] = moved[inside]       # a site whose jitter leaves the box keeps its place
-    return pts
+    off = np.stack([rr * np.cos(ph), rr * np.sin(ph)], axis=1)
+    # an offset that would leave the box is mirrored, so every site is jittered
+    off = np.where((pts + off < lo) | (pts + off > hi), -off, off)
+    return pts + off
 
 
 def initial_positions(n: int, L: float, a: float, rho: float, seed: int) -> np.ndarray:

@@ -62,3 +62,37 @@ def test_placement_argument_errors():
         with pytest.raises(bd.BDError) as e:
             bd.place_disks(*args, seed=0)
         assert e.value.code == -1
+
+
+def _lattice_sites(L, a):
+    # the number of triangular-lattice sites of spacing 2a over [a, L - a]^2
+    W = L - 2 * a
+    s = 2 * a
+    nx0 = int(math.floor(W / s)) + 1
+    nx1 = int(math.floor((W - 0.5 * s) / s)) + 1
+    ny = int(math.floor(W / (s * math.sqrt(3) / 2))) + 1
+    return ((ny + 1) // 2) * nx0 + (ny // 2) * nx1
+
+
+def test_lattice_at_its_packing_limit_is_refused():
+    # a box whose width is a whole number of spacings 2a (W = 40) and exactly
+    # as many disks as lattice sites of spacing 2a: any wider spacing has
+    # fewer sites, so there is no room to jitter and the start would be a
+    # perfect lattice (four sites on every circle)
+    L = 42.0
+    n = _lattice_sites(L, 1.0)
+    with pytest.raises(bd.BDError) as e:
+        bd.place_disks(n, L, 1.0, bd.PLACE_LATTICE, seed=2)
+    assert e.value.code == -1
+
+
+def test_lattice_near_its_limit_is_in_general_position():
+    # a few sites to spare: every site, border rows included, is jittered, so
+    # no four centres are cocircular (the Delaunay triangulation is unique)
+    from oracle import geometry
+    L = 41.3
+    n = _lattice_sites(L, 1.0) - 3
+    xy = bd.place_disks(n, L, 1.0, bd.PLACE_LATTICE, seed=2)
+    _check_valid(xy, n, L, 1.0)
+    tris = geometry.delaunay(xy, L, 1.0)
+    assert geometry.general_position(geometry.with_ghosts(xy, L, 1.0), tris)
