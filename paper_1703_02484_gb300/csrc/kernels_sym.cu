@@ -37,7 +37,6 @@
 #include "bd_internal.h"
 #include "em.cuh"
 #include "f32x2.cuh"
-#include "predicates.cuh"
 
 using namespace bdf;
 
@@ -47,22 +46,28 @@ __device__ __forceinline__ float2 recentre(float4 w, float2 org) {
   return make_float2(__fadd_rn(__fsub_rn(w.x, org.x), w.z), __fadd_rn(__fsub_rn(w.y, org.y), w.w));
 }
 
-// periodic box: disk j about the block origin (ox, oy) as its minimum image,
-// formed exactly in grid units and kept as an FP32 (hi, lo) pair (LQ = 0:
-// walls, no wrap); inert slots far away
-__device__ __forceinline__ float4 rel_grid(const BdDev &d, const BdConst &c, int j, long long ox, long long oy,
-                                           long long LQ) {
-  if (d.ext_id[j] < 0) return make_float4(1.0e18f, 1.0e18f, 0.f, 0.f);
-  const bdpred::Grid g{c.q, c.inv_q, c.qshift};
-  const double2 p = d.pos[j];
-  long long X = bdpred::to_int(p.x, g) - ox, Y = bdpred::to_int(p.y, g) - oy;
-  if (LQ > 0) {
-    const long long h = LQ / 2;
-    X = X > h ? X - LQ : (X < -h ? X + LQ : X);
-    Y = Y > h ? Y - LQ : (Y < -h ? Y + LQ : Y);
-  }
-  const float2 sx = bdem::grid_split(X, c.qshift), sy = bdem::grid_split(Y, c.qshift);
-  return make_float4(sx.x, sy.x, sx.y, sy.y);
+// the same from the stored (x_hi, y_hi, x_lo, y_lo) of disk j, for tiles
+// copied to shared memory as they are: per coordinate the rounded difference
+// s = x_hi - o and its error e (TwoSum), s wrapped by L when beyond L/2
+// (exact: L/2 < |s| <= L), then (s, e + x_lo) renormalised (Fast2Sum), so
+// that the hi part is the rounded minimum image up to the rounding of the lo
+// part; L = 0 (walls): no wrap.  The i side takes the same form, which keeps
+// the self pair's difference exactly 0.
+__device__ __forceinline__ void rel_raw1(float h, float l, float o, float Lf, float hLf, float &hi, float &lo) {
+  const float s = __fsub_rn(h, o);
+  const float bb = __fsub_rn(s, h);
+  const float e = __fsub_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fadd_rn(o, bb));
+  const float w = s > hLf ? __fsub_rn(s, Lf) : (s < -hLf ? __fadd_rn(s, Lf) : s);
+  const float t = __fadd_rn(e, l);
+  hi = __fadd_rn(w, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, w));
+}
+__device__ __forceinline__ float4 rel_raw(float4 w, float2 org, float Lf, float hLf) {
+  if (w.x > 1.0e17f) return make_float4(1.0e18f, 1.0e18f, 0.f, 0.f);   // inert slot
+  float4 r;
+  rel_raw1(w.x, w.z, org.x, Lf, hLf, r.x, r.z);
+  rel_raw1(w.y, w.w, org.y, Lf, hLf, r.y, r.w);
+  return r;
 }
 
 // bounding box (x_min, x_max, y_min, y_max), inert slots (1e18) left out
@@ -102,6 +107,21 @@ __device__ __forceinline__ u64 min_image2_cmp(u64 dx, float Lf, float hLf) {
   return pk2(a, b);
 }
 
+// lo parts of the disks i, kept in the thread's local memory (read only by
+// the rare near tiles, so they hold no registers across the sweep)
+__device__ __forceinline__ void st_local4(float4 *p, float4 v) {
+  asm volatile("st.local.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(__cvta_generic_to_local(p)), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ float4 ld_local4(const float4 *p) {
+  float4 v;
+  asm volatile("ld.local.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(__cvta_generic_to_local(p)));
+  return v;
+}
+
 }  // namespace
 
 // NW warps per block, NP packed i pairs (2 NP disks) per lane, NJ disks j
@@ -113,28 +133,36 @@ __device__ __forceinline__ u64 min_image2_cmp(u64 dx, float Lf, float hLf) {
 // lane, folded halves and deeper unrolling measured within 3 % of these.)
 //
 // PER (periodic boxes, Sec. 2.1): every coordinate is re-centred on the block
-// origin as its minimum image, exactly in grid units (near pairs, across an
-// edge too, are then plain differences); per (block, tile) the bounding boxes
-// tell whether any pair component can exceed L/2, and only such tiles (those
-// near the block's antipode) take the per-pair minimum image: 3 packed
-// operations per coordinate, or compares when the tile holds inert slots.
-// STAGE (walls only): 0 stage the next j tile through registers (re-centred
-// on the way to shared memory); 1 copy it raw with cp.async (no registers held
-// across the tile's arithmetic) and re-centre each j as it is read.
+// origin as its minimum image, as an FP32 (hi, lo) pair (rel_raw); each warp
+// holds a contiguous quarter (half) of the block's disks i.  Per (warp, group
+// of 32 disks j) the warp's box of its disks i and the group's box (taken
+// about one of its disks, so a group across the antipode is not mistaken for
+// one spanning the box) tell which pair form every pair of the two may take
+// (pair_mode): hi parts alone; per-pair minimum image on one axis or both;
+// the exact vector for boxes closer than 20.
+// STAGE: 0 stage the next j tile through registers (re-centred on the way to
+// shared memory); 1 copy it raw with cp.async (no registers held across the
+// tile's arithmetic) and re-centre each j as it is read (walls), or, PER,
+// re-centre the tile in place once it has landed.  PER takes STAGE 1.
 // ACC: the i side's sum over an item's tiles, 2 in (hi, lo) float-float, 1 in
 // FP32 (half the registers).
 template <int NW, int NP, int NJ, bool COMB, int UR, bool PER, int STAGE = 0, int ACC = 2>
 __device__ __forceinline__ void force_long_sym_body(const BdDev &d, const BdConst &c) {
-  static_assert(!(PER && STAGE), "the periodic form stages exact minimum images through registers");
+  static_assert(!PER || STAGE == 1, "the periodic form re-centres tiles in shared memory");
   if (ctl_failed(d.ctl)) return;
   constexpr int T = NW * 32;         // threads
   constexpr int NQ = 2 * NP;         // disks i per thread
   constexpr int NS = BD_TJ / T;      // j disks each thread stages per tile
+  constexpr int NG = BD_TJ / 32;     // groups of 32 disks j per tile
   static_assert(BD_SB == T * NQ, "a block is BD_SB disks");
-  __shared__ float2 sjp[2][STAGE ? 1 : BD_TJ];   // j positions, re-centred (PER: the hi parts)
-  __shared__ __align__(16) float4 sraw[2][STAGE ? BD_TJ : 1];   // STAGE 1: j as stored (x_hi, y_hi, x_lo, y_lo)
-  __shared__ float2 sjl[2][BD_TJ];   // PER: the lo parts
+  __shared__ float2 sjp[2][STAGE ? 1 : BD_TJ];   // j positions, re-centred
+  __shared__ __align__(16) float4 sraw[2][STAGE ? BD_TJ : 1];   // STAGE 1: j as stored (x_hi, y_hi, x_lo, y_lo);
+                                                                // PER: re-centred in place (hi, lo)
   __shared__ float2 shw[NW][BD_TJ];  // per-warp j-side sums of the current tile
+  __shared__ float4 sgbox[2][PER ? NG : 1];   // PER: per-group boxes of the staged tile
+  __shared__ int sgpad[2][PER ? NG : 1];      //      and whether the group holds inert slots
+  __shared__ float4 sibox[PER ? NW : 1];      //      per-warp boxes of the block's disks i
+  __shared__ int sipad[PER ? NW : 1];         //      and whether they include inert slots
   const int item_id = c.sitem0 + (int)blockIdx.x;   // this launch's share of the plan (force sharding)
   const int4 item = d.sitems[item_id];
   const int P = item.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -144,39 +172,32 @@ __device__ __forceinline__ void force_long_sym_body(const BdDev &d, const BdCons
   const BdRep &R = d.rep[binfo.x];
   const int a = binfo.y;
   const float2 org = d.sorigin[P];
-  long long LQ = 0, ox = 0, oy = 0;
+  bool per = false;                  // this block's replica is periodic
   float Lf = 0.f, hLf = __int_as_float(0x7f800000);
-  if (PER) {
-    if (R.periodic) {
-      LQ = R.LQ;
-      Lf = R.Lf;
-      hLf = R.hLf;
-    }
-    ox = (long long)org.x * (1ll << c.qshift);   // integer origins: exact in grid units
-    oy = (long long)org.y * (1ll << c.qshift);
+  if (PER && R.periodic) {
+    per = true;
+    Lf = R.Lf;
+    hLf = R.hLf;
   }
   auto rel = [&](int j) -> float4 {
-    if (PER) return rel_grid(d, c, j, ox, oy, LQ);
+    if (PER) return rel_raw(d.work[j], org, Lf, hLf);
     const float2 v = recentre(d.work[j], org);
     return make_float4(v.x, v.y, 0.f, 0.f);
   };
-  __shared__ float4 sbox[2][NW];     // PER: per-warp boxes of the staged tile
-  __shared__ int spad[2][NW];        //      and whether it holds inert slots
-  __shared__ float4 sibox[NW];       //      per-warp boxes of the block's disks i
-  __shared__ int sipad[NW];          //      and whether they include inert slots
+  // slot (in the block) of this thread's disk i number q
+  auto islot = [&](int q) -> int { return PER ? warp * (BD_SB / NW) + q * 32 + lane : q * T + tid; };
   u64 xi2[NP], yi2[NP], ax2[NP], ay2[NP];
-  u64 xl2[NP], yl2[NP];              // PER: lo parts of the disks i
+  float4 ilo[PER ? NP : 1];          // PER: lo parts of the disks i (x0, y0, x1, y1), local memory
   float fxh[NQ], fxl[ACC == 2 ? NQ : 1], fyh[NQ], fyl[ACC == 2 ? NQ : 1];
   float4 ibox = sempty_box();
   bool ipad = false;
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
-    const float4 p0 = rel(base + (2 * k) * T + tid);
-    const float4 p1 = rel(base + (2 * k + 1) * T + tid);
+    const float4 p0 = rel(base + islot(2 * k));
+    const float4 p1 = rel(base + islot(2 * k + 1));
     xi2[k] = pk2(p0.x, p1.x);
     yi2[k] = pk2(p0.y, p1.y);
-    xl2[k] = pk2(p0.z, p1.z);
-    yl2[k] = pk2(p0.w, p1.w);
+    if (PER) st_local4(&ilo[k], make_float4(p0.z, p0.w, p1.z, p1.w));
     ax2[k] = ay2[k] = 0ull;
     if (PER) {
       sbox_add(ibox, p0.x, p0.y);
@@ -224,27 +245,41 @@ __device__ __forceinline__ void force_long_sym_body(const BdDev &d, const BdCons
   auto store = [&](int b) {
     if constexpr (STAGE == 1) {
       asm volatile("cp.async.wait_group 0;" ::: "memory");
-      return;
-    }
+      if constexpr (PER) {
+        // each thread re-centres the slots it copied (its own copies are
+        // visible to it after the wait), in place; the warp's 32 slots of
+        // stage m are group m NW + warp, whose box is taken about its first
+        // live disk (minimum images about it), then shifted back
 #pragma unroll
-    for (int m = 0; m < NS; ++m) {
-      sjp[b][m * T + tid] = make_float2(st[m].x, st[m].y);
-      if (PER) sjl[b][m * T + tid] = make_float2(st[m].z, st[m].w);
-    }
-    if (PER) {
-      float4 bx = sempty_box();
-      bool pad = false;
+        for (int m = 0; m < NS; ++m) {
+          const float4 v = rel_raw(sraw[b][m * T + tid], org, Lf, hLf);
+          sraw[b][m * T + tid] = v;
+          const bool live = v.x < 1.0e17f;
+          const unsigned bal = __ballot_sync(0xffffffffu, live);
+          float4 bx = sempty_box();
+          if (bal) {
+            const int src = __ffs(bal) - 1;
+            const float rx = __shfl_sync(0xffffffffu, v.x, src), ry = __shfl_sync(0xffffffffu, v.y, src);
+            if (live) {
+              float dx = __fsub_rn(v.x, rx), dy = __fsub_rn(v.y, ry);
+              if (per) {
+                dx = dx > hLf ? __fsub_rn(dx, Lf) : (dx < -hLf ? __fadd_rn(dx, Lf) : dx);
+                dy = dy > hLf ? __fsub_rn(dy, Lf) : (dy < -hLf ? __fadd_rn(dy, Lf) : dy);
+              }
+              bx = make_float4(dx, dx, dy, dy);
+            }
+            bx = swarp_box(bx);
+            bx = make_float4(__fadd_rn(rx, bx.x), __fadd_rn(rx, bx.y), __fadd_rn(ry, bx.z), __fadd_rn(ry, bx.w));
+          }
+          if (lane == 0) {
+            sgbox[b][m * NW + warp] = bx;
+            sgpad[b][m * NW + warp] = bal != 0xffffffffu ? 1 : 0;
+          }
+        }
+      }
+    } else {
 #pragma unroll
-      for (int m = 0; m < NS; ++m) {
-        sbox_add(bx, st[m].x, st[m].y);
-        pad = pad || st[m].x > 1.0e17f;
-      }
-      bx = swarp_box(bx);
-      pad = __any_sync(0xffffffffu, pad);
-      if (lane == 0) {
-        sbox[b][warp] = bx;
-        spad[b][warp] = pad ? 1 : 0;
-      }
+      for (int m = 0; m < NS; ++m) sjp[b][m * T + tid] = make_float2(st[m].x, st[m].y);
     }
   };
   buf = STAGE ? 1 : 0;   // STAGE 1: fetch fills sraw[buf ^ 1]
@@ -256,19 +291,25 @@ __device__ __forceinline__ void force_long_sym_body(const BdDev &d, const BdCons
   __syncthreads();
   // the j disk in slot jj of the current staging buffer, re-centred
   auto jpos = [&](int jj) -> float2 {
-    if constexpr (STAGE == 1) return recentre(sraw[buf][jj], org);
+    if constexpr (STAGE == 1 && PER) return make_float2(sraw[buf][jj].x, sraw[buf][jj].y);
+    else if constexpr (STAGE == 1) return recentre(sraw[buf][jj], org);
     else return sjp[buf][jj];
   };
-  // pair differences: MODE 0 plain, 1 packed minimum image, 2 minimum image by compares
-  // pair differences (r_j - r_i): MODE 0 the hi parts alone; 1 the exact
-  // near-pair vector (hi_j - hi_i) + (lo_j - lo_i); 2 the same with the packed
-  // minimum image of the hi difference; 3 with the minimum image by compares;
-  // 4 near pairs across the antipode (a block spanning the box): the hi
-  // difference, about L there, is formed exactly as s + e (TwoDiff), s takes
-  // the minimum image (exact: |s| in [L/2, 3L/2]), then e and the lo
-  // difference are added
-  auto diff = [&](auto MODE, u64 jh2, u64 ih2, u64 jl2, u64 il2) -> u64 {
-    constexpr int mode = decltype(MODE)::value;
+  // PER: its lo parts
+  auto jlo = [&](int jj) -> float2 { return make_float2(sraw[buf][jj].z, sraw[buf][jj].w); };
+  // pair differences (r_j - r_i), per axis AX (0: x, 1: y), by the pair form
+  // MODE: 0 the hi parts alone; 1 the exact near-pair vector (hi_j - hi_i) +
+  // (lo_j - lo_i); 2 the hi difference's packed minimum image on both axes;
+  // 3 the same by compares (inert slots, which must stay far away, take part);
+  // 5 / 6 the packed minimum image on x / y alone (an inert slot stays far
+  // away on the other axis); 4 near pairs across the antipode (boxes of a
+  // size near L/2): the hi difference, about L there, is formed exactly as
+  // s + e (TwoDiff), s takes the minimum image (exact: |s| in [L/2, 3L/2]),
+  // then e and the lo difference are added.  Far pairs (all forms but 1 and
+  // 4) drop the lo parts, as form 0 does.
+  auto diff = [&](auto MODE, auto AX, u64 jh2, u64 ih2, u64 jl2, u64 il2) -> u64 {
+    constexpr int m0 = decltype(MODE)::value, ax = decltype(AX)::value;
+    constexpr int mode = m0 == 5 ? (ax == 0 ? 2 : 0) : (m0 == 6 ? (ax == 1 ? 2 : 0) : m0);
     u64 dd = sub2(jh2, ih2);
     if constexpr (mode == 4) {
       const u64 v = sub2(dd, jh2);
@@ -277,25 +318,91 @@ __device__ __forceinline__ void force_long_sym_body(const BdDev &d, const BdCons
     }
     if constexpr (mode == 2) dd = min_image2(dd, invL2, nL2, M2);
     if constexpr (mode == 3) dd = min_image2_cmp(dd, Lf, hLf);
-    if constexpr (mode >= 1) dd = add2(dd, sub2(jl2, il2));
+    if constexpr (mode == 1) dd = add2(dd, sub2(jl2, il2));
     return dd;
   };
-  auto own_tile = [&](auto MODE) {
+  using AXX = std::integral_constant<int, 0>;
+  using AXY = std::integral_constant<int, 1>;
+  // PER: the pair form of this warp's disks i with the j groups g0 .. g0 +
+  // ng - 1 of the current tile.  Pair components range over [j_min - i_max,
+  // j_max - i_min]; a plain difference is the minimum image when that range
+  // and the j coordinates themselves lie inside (-L/2, L/2) (then each j is
+  // stored as the image its box describes), with a margin of 2^-16 L/2 for
+  // the rounding of the boxes.  Near: the range comes within 20 of 0 or L.
+  auto pair_mode = [&](int g0, int ng) -> int {
+    if constexpr (!PER) return 0;
+    const float4 ib = sibox[warp];
+    if (ib.x > ib.y) return 0;                 // the warp's disks i are all inert
+    float4 jb = sempty_box();
+    int pad = sipad[warp];
+    for (int u = 0; u < ng; ++u) {
+      jb = smerge_box(jb, sgbox[buf][g0 + u]);
+      pad |= sgpad[buf][g0 + u];
+    }
+    if (jb.x > jb.y) return 0;                 // inert disks j only: their pairs vanish
+    const float lox = __fsub_rn(jb.x, ib.y), hix = __fsub_rn(jb.y, ib.x);
+    const float loy = __fsub_rn(jb.z, ib.w), hiy = __fsub_rn(jb.w, ib.z);
+    const float hLm = __fmul_rn(hLf, 1.0f - 1.0f / 65536.0f);
+    const bool wx = per && (hix > hLm || lox < -hLm || jb.y > hLm || jb.x < -hLm);
+    const bool wy = per && (hiy > hLm || loy < -hLm || jb.w > hLm || jb.z < -hLm);
+    auto gap = [&](float lo, float hi) -> float {
+      float g = fmaxf(0.f, fmaxf(lo, -hi));
+      if (per) {
+        g = fminf(g, fmaxf(0.f, fmaxf(__fsub_rn(lo, Lf), -__fsub_rn(hi, Lf))));
+        g = fminf(g, fmaxf(0.f, fmaxf(__fadd_rn(lo, Lf), -__fadd_rn(hi, Lf))));
+      }
+      return g;
+    };
+    const float gx = gap(lox, hix), gy = gap(loy, hiy);
+    // boxes closer than 20: the exact vector keeps their pairs at FP32
+    // resolution of their separation (coordinates reach L/2 from the block
+    // origin, where one rounding costs ulp(L/2) / 2)
+    const bool near = gx * gx + gy * gy < 400.f;
+    return near ? (wx || wy ? 4 : 1) : (wx && wy ? (pad ? 3 : 2) : (wx ? 5 : (wy ? 6 : 0)));
+  };
+  using M0 = std::integral_constant<int, 0>;
+  using M1 = std::integral_constant<int, 1>;
+  using M2c = std::integral_constant<int, 2>;
+  using M3 = std::integral_constant<int, 3>;
+  using M4 = std::integral_constant<int, 4>;
+  using M5 = std::integral_constant<int, 5>;
+  using M6 = std::integral_constant<int, 6>;
+  auto dispatch = [&](int mode, auto &&fn) {
+    if constexpr (PER) {
+      if (mode == 1) fn(M1());
+      else if (mode == 2) fn(M2c());
+      else if (mode == 3) fn(M3());
+      else if (mode == 4) fn(M4());
+      else if (mode == 5) fn(M5());
+      else if (mode == 6) fn(M6());
+      else fn(M0());
+    } else {
+      fn(M0());
+    }
+  };
+  auto own_group = [&](auto MODE, int g) {
     // the block's own disks: i side only, j broadcast from shared memory
+    constexpr bool LO = decltype(MODE)::value == 1 || decltype(MODE)::value == 4;
 #pragma unroll 4
-    for (int jj = 0; jj < BD_TJ; ++jj) {
+    for (int jj = g * 32; jj < g * 32 + 32; ++jj) {
       const float2 p = jpos(jj);
       const u64 jx2 = pk2(p.x, p.x), jy2 = pk2(p.y, p.y);
       u64 jxl2 = 0ull, jyl2 = 0ull;
-      if constexpr (decltype(MODE)::value >= 1) {
-        const float2 pl = sjl[buf][jj];
+      if constexpr (LO) {
+        const float2 pl = jlo(jj);
         jxl2 = pk2(pl.x, pl.x);
         jyl2 = pk2(pl.y, pl.y);
       }
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
-        const u64 dx = diff(MODE, jx2, xi2[k], jxl2, xl2[k]);
-        const u64 dy = diff(MODE, jy2, yi2[k], jyl2, yl2[k]);
+        u64 ixl2 = 0ull, iyl2 = 0ull;
+        if constexpr (LO) {
+          const float4 il = ld_local4(&ilo[k]);
+          ixl2 = pk2(il.x, il.z);
+          iyl2 = pk2(il.y, il.w);
+        }
+        const u64 dx = diff(MODE, AXX(), jx2, xi2[k], jxl2, ixl2);
+        const u64 dy = diff(MODE, AXY(), jy2, yi2[k], jyl2, iyl2);
         u64 r2 = fma2(dx, dx, eps2);
         r2 = fma2(dy, dy, r2);
         float ra, rb;
@@ -307,146 +414,101 @@ __device__ __forceinline__ void force_long_sym_body(const BdDev &d, const BdCons
       }
     }
   };
-  auto ring_tile = [&](auto MODE) {
-    // a later tile: every pair once, both sides; each lane carries NJ disks j
-    for (int g = 0; g < BD_TJ / (32 * NJ); ++g) {
-      constexpr bool LO = decltype(MODE)::value >= 1;
-      float jx[NJ], jy[NJ], jxl[NJ], jyl[NJ];
-      u64 hx2[NJ], hy2[NJ];
+  auto ring_group = [&](auto MODE, int g) {
+    // a later tile's group g: every pair once, both sides; each lane carries NJ disks j
+    constexpr bool LO = decltype(MODE)::value == 1 || decltype(MODE)::value == 4;
+    float jx[NJ], jy[NJ], jxl[NJ], jyl[NJ];
+    u64 hx2[NJ], hy2[NJ];
 #pragma unroll
-      for (int m = 0; m < NJ; ++m) {
-        const float2 p = jpos((g * NJ + m) * 32 + lane);
-        jx[m] = p.x;
-        jy[m] = p.y;
-        jxl[m] = jyl[m] = 0.f;
-        if constexpr (LO) {
-          const float2 pl = sjl[buf][(g * NJ + m) * 32 + lane];
-          jxl[m] = pl.x;
-          jyl[m] = pl.y;
-        }
-        hx2[m] = hy2[m] = 0ull;
+    for (int m = 0; m < NJ; ++m) {
+      const float2 p = jpos((g * NJ + m) * 32 + lane);
+      jx[m] = p.x;
+      jy[m] = p.y;
+      jxl[m] = jyl[m] = 0.f;
+      if constexpr (LO) {
+        const float2 pl = jlo((g * NJ + m) * 32 + lane);
+        jxl[m] = pl.x;
+        jyl[m] = pl.y;
       }
+      hx2[m] = hy2[m] = 0ull;
+    }
 #pragma unroll UR
-      for (int rot = 0; rot < 32; ++rot) {
-        const int src = (lane + 1) & 31;
-#pragma unroll
-        for (int m = 0; m < NJ; ++m) {
-          const u64 jx2 = pk2(jx[m], jx[m]), jy2 = pk2(jy[m], jy[m]);
-          const u64 jxl2 = LO ? pk2(jxl[m], jxl[m]) : 0ull, jyl2 = LO ? pk2(jyl[m], jyl[m]) : 0ull;
-          // the next j position does not depend on this step's arithmetic
-          const float njx = __shfl_sync(0xffffffffu, jx[m], src);
-          const float njy = __shfl_sync(0xffffffffu, jy[m], src);
-          float njxl = 0.f, njyl = 0.f;
-          if constexpr (LO) {
-            njxl = __shfl_sync(0xffffffffu, jxl[m], src);
-            njyl = __shfl_sync(0xffffffffu, jyl[m], src);
-          }
-#pragma unroll
-          for (int k = 0; k < NP; ++k) {
-            const u64 dx = diff(MODE, jx2, xi2[k], jxl2, xl2[k]);
-            const u64 dy = diff(MODE, jy2, yi2[k], jyl2, yl2[k]);
-            u64 r2 = fma2(dx, dx, eps2);
-            r2 = fma2(dy, dy, r2);
-            float ra, rb;
-            up2(r2, ra, rb);
-            const u64 sv = pk2(rsqrt_apx(ra), rsqrt_apx(rb));
-            const u64 s3 = mul2(mul2(sv, sv), sv);
-            ax2[k] = fma2(dx, s3, ax2[k]);
-            ay2[k] = fma2(dy, s3, ay2[k]);
-            hx2[m] = fma2(dx, s3, hx2[m]);
-            hy2[m] = fma2(dy, s3, hy2[m]);
-          }
-          // pass the j accumulator one lane down the ring, after its disk
-          float h0, h1, h2, h3;
-          up2(hx2[m], h0, h1);
-          up2(hy2[m], h2, h3);
-          if (COMB) {
-            h0 = __shfl_sync(0xffffffffu, __fadd_rn(h0, h1), src);
-            h2 = __shfl_sync(0xffffffffu, __fadd_rn(h2, h3), src);
-            hx2[m] = pk2(h0, 0.f);
-            hy2[m] = pk2(h2, 0.f);
-          } else {
-            h0 = __shfl_sync(0xffffffffu, h0, src);
-            h1 = __shfl_sync(0xffffffffu, h1, src);
-            h2 = __shfl_sync(0xffffffffu, h2, src);
-            h3 = __shfl_sync(0xffffffffu, h3, src);
-            hx2[m] = pk2(h0, h1);
-            hy2[m] = pk2(h2, h3);
-          }
-          jx[m] = njx;
-          jy[m] = njy;
-          jxl[m] = njxl;
-          jyl[m] = njyl;
-        }
-      }
-      // after 32 passes every j is back in its own lane
+    for (int rot = 0; rot < 32; ++rot) {
+      const int src = (lane + 1) & 31;
 #pragma unroll
       for (int m = 0; m < NJ; ++m) {
+        const u64 jx2 = pk2(jx[m], jx[m]), jy2 = pk2(jy[m], jy[m]);
+        const u64 jxl2 = LO ? pk2(jxl[m], jxl[m]) : 0ull, jyl2 = LO ? pk2(jyl[m], jyl[m]) : 0ull;
+        // the next j position does not depend on this step's arithmetic
+        const float njx = __shfl_sync(0xffffffffu, jx[m], src);
+        const float njy = __shfl_sync(0xffffffffu, jy[m], src);
+        float njxl = 0.f, njyl = 0.f;
+        if constexpr (LO) {
+          njxl = __shfl_sync(0xffffffffu, jxl[m], src);
+          njyl = __shfl_sync(0xffffffffu, jyl[m], src);
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          u64 ixl2 = 0ull, iyl2 = 0ull;
+          if constexpr (LO) {
+            const float4 il = ld_local4(&ilo[k]);
+            ixl2 = pk2(il.x, il.z);
+            iyl2 = pk2(il.y, il.w);
+          }
+          const u64 dx = diff(MODE, AXX(), jx2, xi2[k], jxl2, ixl2);
+          const u64 dy = diff(MODE, AXY(), jy2, yi2[k], jyl2, iyl2);
+          u64 r2 = fma2(dx, dx, eps2);
+          r2 = fma2(dy, dy, r2);
+          float ra, rb;
+          up2(r2, ra, rb);
+          const u64 sv = pk2(rsqrt_apx(ra), rsqrt_apx(rb));
+          const u64 s3 = mul2(mul2(sv, sv), sv);
+          ax2[k] = fma2(dx, s3, ax2[k]);
+          ay2[k] = fma2(dy, s3, ay2[k]);
+          hx2[m] = fma2(dx, s3, hx2[m]);
+          hy2[m] = fma2(dy, s3, hy2[m]);
+        }
+        // pass the j accumulator one lane down the ring, after its disk
         float h0, h1, h2, h3;
         up2(hx2[m], h0, h1);
         up2(hy2[m], h2, h3);
-        shw[warp][(g * NJ + m) * 32 + lane] = make_float2(__fadd_rn(h0, h1), __fadd_rn(h2, h3));
+        if (COMB) {
+          h0 = __shfl_sync(0xffffffffu, __fadd_rn(h0, h1), src);
+          h2 = __shfl_sync(0xffffffffu, __fadd_rn(h2, h3), src);
+          hx2[m] = pk2(h0, 0.f);
+          hy2[m] = pk2(h2, 0.f);
+        } else {
+          h0 = __shfl_sync(0xffffffffu, h0, src);
+          h1 = __shfl_sync(0xffffffffu, h1, src);
+          h2 = __shfl_sync(0xffffffffu, h2, src);
+          h3 = __shfl_sync(0xffffffffu, h3, src);
+          hx2[m] = pk2(h0, h1);
+          hy2[m] = pk2(h2, h3);
+        }
+        jx[m] = njx;
+        jy[m] = njy;
+        jxl[m] = njxl;
+        jyl[m] = njyl;
       }
     }
-  };
-  float4 ibx = sempty_box();
-  int ipd = 0;   // inert slots among the disks i: the packed minimum image would
-                 // bring them near, so their tiles take the compares
-  if (PER) {
+    // after 32 passes every j is back in its own lane
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      ibx = smerge_box(ibx, sibox[w]);
-      ipd |= sipad[w];
+    for (int m = 0; m < NJ; ++m) {
+      float h0, h1, h2, h3;
+      up2(hx2[m], h0, h1);
+      up2(hy2[m], h2, h3);
+      shw[warp][(g * NJ + m) * 32 + lane] = make_float2(__fadd_rn(h0, h1), __fadd_rn(h2, h3));
     }
-  }
+  };
   for (int t = t_begin; t < t_end; ++t) {
     if (t + 1 < t_end) fetch(t + 1);
     const int b = d.tile_species[t];
-    int mode = 0;
-    if constexpr (PER) {
-      float4 jb = sempty_box();
-      int pad = ipd;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        jb = smerge_box(jb, sbox[buf][w]);
-        pad |= spad[buf][w];
-      }
-      // pair components range over [j_min - i_max, j_max - i_min]
-      const bool wrap = LQ > 0 && (jb.y - ibx.x > hLf || jb.x - ibx.y < -hLf || jb.w - ibx.z > hLf ||
-                                   jb.z - ibx.w < -hLf);
-      // boxes closer than 20: the exact vector keeps their pairs at FP32
-      // resolution of their separation (a 512-disk block puts coordinates up
-      // to L/2 from its origin, where one rounding costs ulp(L/2) / 2)
-      const float gx = fmaxf(0.f, fmaxf(jb.x - ibx.y, ibx.x - jb.y));
-      const float gy = fmaxf(0.f, fmaxf(jb.z - ibx.w, ibx.z - jb.w));
-      const bool near = gx * gx + gy * gy < 400.f;
-      mode = wrap ? (near ? 4 : (pad ? 3 : 2)) : (near ? 1 : 0);
-    }
-    using M0 = std::integral_constant<int, 0>;
-    using M1 = std::integral_constant<int, 1>;
-    using M2c = std::integral_constant<int, 2>;
-    using M3 = std::integral_constant<int, 3>;
-    using M4 = std::integral_constant<int, 4>;
     if (t < tsym) {
-      if constexpr (PER) {
-        if (mode == 1) own_tile(M1());
-        else if (mode == 2) own_tile(M2c());
-        else if (mode == 3) own_tile(M3());
-        else if (mode == 4) own_tile(M4());
-        else own_tile(M0());
-      } else {
-        own_tile(M0());
-      }
+      for (int g = 0; g < NG; ++g)
+        dispatch(pair_mode(g, 1), [&](auto M) { own_group(M, g); });
     } else {
-      if constexpr (PER) {
-        if (mode == 1) ring_tile(M1());
-        else if (mode == 2) ring_tile(M2c());
-        else if (mode == 3) ring_tile(M3());
-        else if (mode == 4) ring_tile(M4());
-        else ring_tile(M0());
-      } else {
-        ring_tile(M0());
-      }
+      for (int g = 0; g < BD_TJ / (32 * NJ); ++g)
+        dispatch(pair_mode(g * NJ, NJ), [&](auto M) { ring_group(M, g); });
       __syncthreads();
       // j side of this tile: F_j += A[s_j][s_i] sum_i (r_j - r_i)/r^3
       const float alj = R.alpha[BD_MAX_SPECIES * b + a];
@@ -488,8 +550,8 @@ __device__ __forceinline__ void force_long_sym_body(const BdDev &d, const BdCons
   float2 *ip = d.ipart + (size_t)item_id * BD_SB;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    if constexpr (ACC == 2) ip[q * T + tid] = make_float2(__fadd_rn(fxh[q], fxl[q]), __fadd_rn(fyh[q], fyl[q]));
-    else ip[q * T + tid] = make_float2(fxh[q], fyh[q]);
+    if constexpr (ACC == 2) ip[islot(q)] = make_float2(__fadd_rn(fxh[q], fxl[q]), __fadd_rn(fyh[q], fyl[q]));
+    else ip[islot(q)] = make_float2(fxh[q], fyh[q]);
   }
 }
 
@@ -564,9 +626,9 @@ int bd_force_sym_blocks_per_sm(int variant, int periodic) {
   cudaError_t e;
   if (periodic)
     e = variant == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                           &per, k_force_long_sym_mb<4, 2, 1, false, 2, true, 8, 0, 2>, 128, 0)
+                           &per, k_force_long_sym_mb<4, 2, 1, false, 2, true, 8, 1, 2>, 128, 0)
                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                           &per, k_force_long_sym_mb<2, 4, 1, false, 2, true, 12, 0, 2>, 64, 0);
+                           &per, k_force_long_sym_mb<2, 4, 1, false, 2, true, 12, 1, 2>, 64, 0);
   else
     e = variant == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                            &per, k_force_long_sym<4, 2, 1, false, 2, false>, 128, 0)
@@ -580,12 +642,15 @@ cudaError_t bd_launch_force_sym(const BdDev &d, const BdConst &c, int variant, c
   if (c.n_sitems == 0) return cudaSuccess;
   // periodic boxes (any replica) take the form with minimum images
   if (c.any_periodic) {
-    // register budgets measured at N = 1e5 (periodic): <4,2> 2.75 -> 2.67 ms
-    // with 8 resident blocks, <2,4> 3.05 -> 2.88 ms with 12
+    // measured at N = 1e5 (periodic), step times with pair forms chosen per
+    // (warp, group of 32 disks j): <2,4> 2.241 ms with 12 resident blocks
+    // (2.248 with 16, 2.288 with 10), <4,2> 2.464 ms with 8 (2.519 with 6);
+    // 2.86 ms before, with one form per (block, tile) and the tiles staged
+    // through registers
     if (variant == 2)
-      k_force_long_sym_mb<4, 2, 1, false, 2, true, 8, 0, 2><<<c.n_sitems, 128, 0, s>>>(d, c);
+      k_force_long_sym_mb<4, 2, 1, false, 2, true, 8, 1, 2><<<c.n_sitems, 128, 0, s>>>(d, c);
     else
-      k_force_long_sym_mb<2, 4, 1, false, 2, true, 12, 0, 2><<<c.n_sitems, 64, 0, s>>>(d, c);
+      k_force_long_sym_mb<2, 4, 1, false, 2, true, 12, 1, 2><<<c.n_sitems, 64, 0, s>>>(d, c);
   } else {
     if (variant == 2)
       k_force_long_sym<4, 2, 1, false, 2, false><<<c.n_sitems, 128, 0, s>>>(d, c);
