@@ -46,8 +46,9 @@ __device__ __forceinline__ float2 recentre(float4 w, float2 org) {
   return make_float2(__fadd_rn(__fsub_rn(w.x, org.x), w.z), __fadd_rn(__fsub_rn(w.y, org.y), w.w));
 }
 
-// the same from the stored (x_hi, y_hi, x_lo, y_lo) of disk j, for tiles
-// copied to shared memory as they are: per coordinate the rounded difference
+// periodic box: disk j about the integer block origin o as its minimum
+// image, from its stored (x_hi, y_hi, x_lo, y_lo) (tiles are copied to
+// shared memory as they are): per coordinate the rounded difference
 // s = x_hi - o and its error e (TwoSum), s wrapped by L when beyond L/2
 // (exact: L/2 < |s| <= L), then (s, e + x_lo) renormalised (Fast2Sum), so
 // that the hi part is the rounded minimum image up to the rounding of the lo
