@@ -865,6 +865,9 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     BD_TRY(dalloc(h, &d.tv_snap, (size_t)nt));
     BD_TRY(dalloc(h, &d.tn_snap, (size_t)nt));
     BD_TRY(dalloc(h, &d.claim, (size_t)nt));
+    BD_TRY(dalloc(h, &d.tinv, (size_t)nt));
+    BD_TRY(dalloc(h, &d.clist, (size_t)nt));
+    BD_TRY(cudaMemsetAsync(d.tinv, 0, (size_t)nt, h->stream));
     BD_TRY(dalloc(h, &d.vt, nv));
     BD_TRY(dalloc(h, &d.act, 3 * (size_t)nt));
     BD_TRY(dalloc(h, &d.act_mark, 3 * (size_t)nt));

@@ -24,10 +24,13 @@
 // threads (and i disks) per block of the all-pairs force adjoint
 #define BD_ADJ_T 128
 
-// triangle flag bits stored in tv[t].w
+// a check pass's verdict bits for the triangle it visits (held in registers)
 #define BD_TRI_INVERTED 1
 #define BD_TRI_DIRTY 2
-#define BD_TRI_FLAGS 3
+// tv[t].w bits 24-31: the low byte of the generation of the check pass that
+// must test the triangle's edges (set by flips and by flip candidates left
+// unresolved; a stale byte that happens to match only adds tests)
+#define BD_TRI_STAMP_SHIFT 24
 // periodic box: corner k of a triangle sits at pos[v_k] + L (sx_k, sy_k);
 // each component is a 2-bit two's-complement field of tv[t].w (0, 1 = +1,
 // 3 = -1): sx_k at bit 8 + 4k, sy_k at bit 10 + 4k.  Zero for walls.
@@ -89,7 +92,7 @@ struct BdCtl {
 };
 
 // counter slots within BdCtl::cnt[phase % 4]
-enum { C_INV = 0, C_REJECT = 1, C_FLIPS = 2, C_OVERLAP = 3, C_CAND = 4 };
+enum { C_INV = 0, C_REJECT = 1, C_FLIPS = 2, C_OVERLAP = 3, C_CAND = 4, C_CLIST = 5 };
 
 // Per-replica parameters (a handle advances R >= 1 independent systems; a
 // single system is R = 1).  Device-resident table read by the kernels.
@@ -143,6 +146,11 @@ struct BdDev {
   int4 *tv, *tn, *tv_snap, *tn_snap;
   unsigned long long *claim;
   int *vt;                 // per vertex: one corner holding it (kept by the flips)
+  // tinv = 1 while a triangle is inverted (set by a check pass, cleared by
+  // the triangle's flip); clist = the triangles that registered a flip
+  // candidate in the last check pass
+  uint8_t *tinv;
+  int *clist;
   int *act;                // 3 x nt: rotating lists of the triangles a check pass visits
   unsigned *act_mark;      // 3 x nt: generation at which a triangle joined each list
   // force sweep

@@ -224,6 +224,11 @@ template <bool PER>
 __device__ __forceinline__ int tshx(int w, int k) { return PER ? shx(w, k) : 0; }
 template <bool PER>
 __device__ __forceinline__ int tshy(int w, int k) { return PER ? shy(w, k) : 0; }
+// the check-pass stamp of a triangle (bits 24-31 of tv.w)
+__device__ __forceinline__ uint8_t tstamp(int w) { return (uint8_t)((unsigned)w >> BD_TRI_STAMP_SHIFT); }
+__device__ __forceinline__ int with_stamp(int w, uint8_t s) {
+  return (int)(((unsigned)w & ((1u << BD_TRI_STAMP_SHIFT) - 1u)) | ((unsigned)s << BD_TRI_STAMP_SHIFT));
+}
 __device__ __forceinline__ int put_shift(int k, int sx, int sy) {
   return ((sx & 3) << (8 + 4 * k)) | ((sy & 3) << (10 + 4 * k));
 }
@@ -316,7 +321,7 @@ __device__ __forceinline__ bool owns6(const Ctx &x, int t0, int k0, const int4 &
 // Quad a-b-d-c with t0 = (a, b, c), t1 = (d, c, b) becomes t0 = (b, d, a),
 // t1 = (c, a, d): the edge bc is replaced by ad.
 template <bool PER>
-__device__ void flip_owned(const Ctx &x, int c0, int o0) {
+__device__ void flip_owned(const Ctx &x, int c0, int o0, uint8_t stamp) {
   const int t0 = c0 / 3, k0 = c0 % 3, t1 = o0 / 3, k1 = o0 % 3;
   int4 V0 = x.d.tv[t0], V1 = x.d.tv[t1], N0 = x.d.tn[t0], N1 = x.d.tn[t1];
   const int a = vk(V0, k0), b = vk(V0, (k0 + 1) % 3), c = vk(V0, (k0 + 2) % 3), dd = vk(V1, k1);
@@ -337,7 +342,7 @@ __device__ void flip_owned(const Ctx &x, int c0, int o0) {
   // image shifts (periodic box): the new corners in t0's frame; d comes from
   // t1's frame, offset by b's shift difference between the two frames
   const int w0 = V0.w, w1 = V1.w;
-  int nw0 = BD_TRI_DIRTY, nw1 = BD_TRI_DIRTY;
+  int nw0 = 0, nw1 = 0;
   if (PER && ((w0 | w1) & BD_TRI_SHIFT_BITS)) {
     const int Ax = shx(w0, k0), Ay = shy(w0, k0);
     const int Bx = shx(w0, (k0 + 1) % 3), By = shy(w0, (k0 + 1) % 3);
@@ -356,12 +361,15 @@ __device__ void flip_owned(const Ctx &x, int c0, int o0) {
       nw1 |= put_shift(k, sx1[k] - sx1[0], sy1[k] - sy1[0]);
     }
   }
-  V0.w = nw0;
-  V1.w = nw1;
+  // both new triangles: their edges are tested by the next check pass
+  V0.w = with_stamp(nw0, stamp);
+  V1.w = with_stamp(nw1, stamp);
   x.d.tv[t0] = V0;
   x.d.tv[t1] = V1;
   x.d.tn[t0] = N0;
   x.d.tn[t1] = N1;
+  x.d.tinv[t0] = 0;
+  x.d.tinv[t1] = 0;
   // the four vertices' corners moved: t0 = (b, d, a), t1 = (c, a, d)
   x.d.vt[b] = 3 * t0 + k0;
   x.d.vt[dd] = 3 * t0 + (k0 + 1) % 3;
@@ -488,6 +496,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
     ++epoch;
     const int slot = kp % 3, nslot = (kp + 1) % 3;
     const unsigned gen = g0 + (unsigned)kp, ngen = gen + 1u;
+    const uint8_t gen8 = (uint8_t)gen, ngen8 = (uint8_t)ngen;   // check-pass stamps of this pass and the next
     const int *dom = d.act + (size_t)slot * x.T;
     const unsigned *cmark = d.act_mark + (size_t)slot * x.T;
     int *nlist = d.act + (size_t)nslot * x.T;
@@ -499,9 +508,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       for (int t = tid; t < x.T; t += nth) {
         const int4 v = d.tv[t];
         if (first) {
-          int4 vs = v;
-          vs.w = v.w & ~BD_TRI_FLAGS;
-          d.tv_snap[t] = vs;
+          d.tv_snap[t] = v;
           d.tn_snap[t] = d.tn[t];
         }
         const uint8_t w0 = d.wrap[v.x], w1 = d.wrap[v.y], w2 = d.wrap[v.z];
@@ -513,7 +520,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           sx[k] = tshx<PER>(v.w, k) + kx[k];
           sy[k] = tshy<PER>(v.w, k) + ky[k];
         }
-        int nw = v.w & BD_TRI_FLAGS;
+        int nw = with_stamp(0, tstamp(v.w));
         for (int k = 0; k < 3; ++k) nw |= put_shift(k, sx[k] - sx[0], sy[k] - sy[0]);
         d.tv[t].w = nw;
       }
@@ -534,9 +541,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         const int4 v = d.tv[t];
         const int4 nn = d.tn[t];
         if (first) {
-          int4 vs = v;
-          vs.w = v.w & ~BD_TRI_FLAGS;
-          d.tv_snap[t] = vs;
+          d.tv_snap[t] = v;
           d.tn_snap[t] = nn;
         }
         // corners loaded once: FP32 pairs, moved flags and re-entries serve the
@@ -552,16 +557,17 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           mvd[k] = fresh ? d.moved[vv[k]] : (uint8_t)0;
           wr[k] = isd[k] ? d.wrap[vv[k]] : (uint8_t)0;
         }
-        int fl = v.w & BD_TRI_FLAGS;
+        int fl = tstamp(v.w) == gen8 ? BD_TRI_DIRTY : 0;
         if (mvd[0] | mvd[1] | mvd[2]) {
           const int o = flat ? orient_pre(x, isd[0] && isd[1] && isd[2], W[0], W[1], W[2], v.x, v.y, v.z)
                              : orient_s(x, v.x, tshx<PER>(v.w, 0), tshy<PER>(v.w, 0), v.y, tshx<PER>(v.w, 1),
                                         tshy<PER>(v.w, 1), v.z, tshx<PER>(v.w, 2), tshy<PER>(v.w, 2));
           fl = BD_TRI_DIRTY | (o <= 0 ? BD_TRI_INVERTED : 0);
-          d.tv[t].w = (v.w & ~BD_TRI_FLAGS) | fl;
+          if (o <= 0) d.tinv[t] = 1;
         }
         const bool inverted = (fl & BD_TRI_INVERTED) != 0;
         inv += inverted ? 1 : 0;
+        bool owner = false;   // t registered a flip candidate
         if (inverted && d.rep_stats) {
           const int rr = tri_rep(d, x.np, v);
           if (rr >= 0) atomicAdd((unsigned long long *)&d.rep_stats[3 * rr + 2], 1ull);
@@ -619,8 +625,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           if (inverted) continue;   // marks and scan wait for the repair
           const int4 v1 = d.tv[o / 3];
           const int q = vk(v1, o % 3);
-          const bool d1 = (v1.w & BD_TRI_DIRTY) || (mvd[ku] | mvd[kw]) || (fresh && d.moved[q]);
-          if ((fl & BD_TRI_DIRTY) || d1) {
+          // the edge is tested when a triangle on either side is dirty or one
+          // of its four points moved
+          const bool d1 = (fl & BD_TRI_DIRTY) || tstamp(v1.w) == gen8 || (mvd[ku] | mvd[kw]) ||
+                          (fresh && d.moved[q]);
+          if (d1) {
             int sqx, sqy;
             opp_shift<PER>(v.w, k, v1.w, o % 3, sqx, sqy);
             const int ic = (flat && (sqx | sqy) == 0)
@@ -630,6 +639,10 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
             if (ic > 0) {
               claim6(x, t, k, nn, o, claim_key(epoch, cc));
               ++cand;
+              if (!owner) {   // t joins the candidate owners once (candidates are rare)
+                owner = true;
+                d.clist[atomicAdd(cnt(ctl, b.ph, C_CLIST), 1)] = t;
+              }
             }
           }
           if (disks) {
@@ -676,9 +689,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         const int4 v = d.tv[t];
         const int4 nn = d.tn[t];
         if (first) {
-          int4 vs = v;
-          vs.w = v.w & ~BD_TRI_FLAGS;
-          d.tv_snap[t] = vs;
+          d.tv_snap[t] = v;
           d.tn_snap[t] = nn;
         }
         const int vv[3] = {v.x, v.y, v.z};
@@ -690,14 +701,15 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           W[k] = work_of(x, vv[k]);
           mvd[k] = fresh ? d.moved[vv[k]] : (uint8_t)0;
         }
-        int fl = v.w & BD_TRI_FLAGS;
+        int fl = tstamp(v.w) == gen8 ? BD_TRI_DIRTY : 0;
         if (mvd[0] | mvd[1] | mvd[2]) {
           const int o = orient_pre(x, isd[0] && isd[1] && isd[2], W[0], W[1], W[2], v.x, v.y, v.z);
           fl = BD_TRI_DIRTY | (o <= 0 ? BD_TRI_INVERTED : 0);
-          d.tv[t].w = (v.w & ~BD_TRI_FLAGS) | fl;
+          if (o <= 0) d.tinv[t] = 1;
         }
         const bool inverted = (fl & BD_TRI_INVERTED) != 0;
         inv += inverted ? 1 : 0;
+        bool owner = false;   // t registered a flip candidate
         if (inverted && d.rep_stats) {
           const int rr = tri_rep(d, x.np, v);
           if (rr >= 0) atomicAdd((unsigned long long *)&d.rep_stats[3 * rr + 2], 1ull);
@@ -749,12 +761,19 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
           if (inverted) continue;   // marks and scan wait for the repair
           const int4 v1 = d.tv[o / 3];
           const int q = vk(v1, o % 3);
-          const bool d1 = (v1.w & BD_TRI_DIRTY) || (mvd[ku] | mvd[kw]) || (fresh && d.moved[q]);
-          if ((fl & BD_TRI_DIRTY) || d1) {
+          // the edge is tested when a triangle on either side is dirty or one
+          // of its four points moved
+          const bool d1 = (fl & BD_TRI_DIRTY) || tstamp(v1.w) == gen8 || (mvd[ku] | mvd[kw]) ||
+                          (fresh && d.moved[q]);
+          if (d1) {
             const bool filt = isd[0] && isd[1] && isd[2] && q < x.np;
             if (incircle_pre(x, filt, W[0], W[1], W[2], work_of(x, q), v.x, v.y, v.z, q) > 0) {
               claim6(x, t, k, nn, o, claim_key(epoch, cc));
               ++cand;
+              if (!owner) {   // t joins the candidate owners once (candidates are rare)
+                owner = true;
+                d.clist[atomicAdd(cnt(ctl, b.ph, C_CLIST), 1)] = t;
+              }
             }
           }
           if (disks) {
@@ -822,15 +841,18 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         phase_begin(ctl, b);
         {
           if (first_round) {
-            for (int i = tid; i < x.np; i += nth) {
-              d.disp[i] = make_double2(0.0, 0.0);
-              d.moved[i] = 0;
+            for (int i = tid; i < x.np; i += nth) d.disp[i] = make_double2(0.0, 0.0);
+            // the check pass skipped the marks (and the pass after the repair
+            // is not fresh): a triangle with a moved corner stays dirty for it
+            for (int t = tid; t < x.T; t += nth) {
+              const int4 v = d.tv[t];
+              if (d.moved[v.x] | d.moved[v.y] | d.moved[v.z]) d.tv[t].w = with_stamp(v.w, ngen8);
             }
           }
           int inv = 0, ncand = 0;
           for (int t = tid; t < x.T; t += nth) {
+            if (!d.tinv[t]) continue;
             const int4 v = d.tv[t];
-            if (!(v.w & BD_TRI_INVERTED)) continue;
             ++inv;
             atomicExch(&ctl->st_fail_item, t);
             const int4 nn = d.tn[t];
@@ -882,7 +904,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
             const int4 N0 = d.tn[t];
             const int o = vk(N0, cm % 3);
             if (!owns6(x, t, cm % 3, N0, o, key)) continue;
-            flip_owned<PER>(x, cm, o);   // both new triangles are counter-clockwise by the rule
+            flip_owned<PER>(x, cm, o, ngen8);   // both new triangles are counter-clockwise by the rule
             ++nf;
           }
           block_add(cnt(ctl, b.ph, C_FLIPS), nf);
@@ -913,19 +935,26 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
             if (fresh) d.moved[i] = 0;
           }
         int nf = 0;
-        // the same triangles as the pass that marked the edges: each candidate
-        // is owned by the triangle that tested it
-        for (int it = tid; it < dom_n; it += nth) {
-          const int t = full ? it : dom[it];
+        // the triangles that registered a candidate in the marking pass: each
+        // candidate is owned by the triangle that tested it.  A flip stamps
+        // its two triangles for the next pass; an owner whose flip lost a
+        // claim is stamped too, so its edges are tested again.  Every other
+        // edge the marking pass tested is legal, and keeps its verdict unless
+        // a flip changes it (then a stamped triangle holds it).
+        const int ncl = bc[BC_CNT + C_CLIST];
+        // consecutive entries go to different blocks (a few hundred flips on
+        // one SM would queue on its load/store unit)
+        for (int it = blockIdx.x + threadIdx.x * gridDim.x; it < ncl; it += nth) {
+          const int t = d.clist[it];
           const unsigned long long key = d.claim[t];
+          bool flipped = false;
           if ((key >> 32) == epoch) {
             const int cm = key_corner(key);
-            bool flipped = false;
             if (cm / 3 == t) {
               const int4 N0 = d.tn[t];
               const int o = vk(N0, cm % 3);
               if (owns6(x, t, cm % 3, N0, o, key)) {
-                flip_owned<PER>(x, cm, o);
+                flip_owned<PER>(x, cm, o, ngen8);
                 if (use_lists) {
                   push_tri(nlist, nmark, ncount, ngen, t);
                   push_tri(nlist, nmark, ncount, ngen, o / 3);
@@ -942,11 +971,10 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
                 }
               }
             }
-            // claimed but not flipped: stays dirty, its edges are tested again
-            if (use_lists && !flipped && (d.tv[t].w & BD_TRI_DIRTY)) push_tri(nlist, nmark, ncount, ngen, t);
-          } else {
-            const int tw = d.tv[t].w;
-            if (tw & BD_TRI_DIRTY) d.tv[t].w = tw & ~BD_TRI_FLAGS;   // every edge tested and legal
+          }
+          if (!flipped) {
+            d.tv[t].w = with_stamp(d.tv[t].w, ngen8);
+            if (use_lists) push_tri(nlist, nmark, ncount, ngen, t);
           }
         }
         block_add(cnt(ctl, b.ph, C_FLIPS), nf);
@@ -1061,12 +1089,6 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         }
       }
       if (PER) block_add(&ctl->n_wrapped, nwrap);
-      // flags left by the last check pass sit on the triangles it visited
-      for (int it = tid; it < dom_n; it += nth) {
-        const int t = full ? it : dom[it];
-        const int tw = d.tv[t].w;
-        if (tw & BD_TRI_FLAGS) d.tv[t].w = tw & ~BD_TRI_FLAGS;
-      }
     }
     if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
     if (lead) stage_tick(ctl, STAGE_A, t_mark);
@@ -1092,6 +1114,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       const int4 vs = d.tv_snap[t];
       d.tv[t] = vs;
       d.tn[t] = d.tn_snap[t];
+      d.tinv[t] = 0;
       // a corner per vertex of the restored triangulation (any one will do)
       d.vt[vs.x] = 3 * t;
       d.vt[vs.y] = 3 * t + 1;
@@ -1149,6 +1172,7 @@ __global__ void k_restore_step(BdDev d, BdConst c) {
       const int4 vs = d.tv_snap[t];
       d.tv[t] = vs;
       d.tn[t] = d.tn_snap[t];
+      d.tinv[t] = 0;
       d.vt[vs.x] = 3 * t;
       d.vt[vs.y] = 3 * t + 1;
       d.vt[vs.z] = 3 * t + 2;
