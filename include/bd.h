@@ -236,7 +236,7 @@ int bd_set_loop_caps(bd_handle *h, int32_t max_corr_iters, int32_t max_flip_roun
  * barriers of the triangulation kernel and of the Verlet-list correction):
  * a barrier that waits longer sets BD_ERR_DEVICE_TIMEOUT, every block leaves
  * its kernel, and the call that launched it undoes the step (or the new
- * positions of bd_set_state) from the snapshots and returns
+ * positions of bd_set_state) from its step-start copies and returns
  * BD_ERR_DEVICE_TIMEOUT, the handle usable.  Default 2 s.
  *   seconds       1e-3 .. 60.
  *   hold_barrier  0 for normal use.  k > 0 makes the k-th grid barrier of every

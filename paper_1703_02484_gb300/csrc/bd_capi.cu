@@ -862,8 +862,10 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     }
     BD_TRY(dalloc(h, &d.tv, (size_t)nt));
     BD_TRY(dalloc(h, &d.tn, (size_t)nt));
-    BD_TRY(dalloc(h, &d.tv_snap, (size_t)nt));
-    BD_TRY(dalloc(h, &d.tn_snap, (size_t)nt));
+    BD_TRY(dalloc(h, &d.jtv, (size_t)nt));
+    BD_TRY(dalloc(h, &d.jtn, (size_t)nt));
+    BD_TRY(dalloc(h, &d.jmark, (size_t)nt));
+    BD_TRY(cudaMemsetAsync(d.jmark, 0, (size_t)nt * sizeof(unsigned), h->stream));
     BD_TRY(dalloc(h, &d.claim, (size_t)nt));
     BD_TRY(dalloc(h, &d.tinv, (size_t)nt));
     BD_TRY(dalloc(h, &d.clist, (size_t)nt));
@@ -1083,7 +1085,7 @@ void add_stage_times(bd_handle *h) {
 int finish_status(bd_handle *h, int status) {
   // clear the sticky status so the handle keeps working from the last good
   // state; after a timed-out barrier the kernel left without undoing its
-  // step: undo it from the snapshots, and reset the barrier words
+  // step: undo it (step-start copies, undo journal), and reset the barrier words
   cudaStream_t st = h->stream;
   if (status == BD_ERR_DEVICE_TIMEOUT) {
     bd_launch_restore_step(h->d, h->c, st);

@@ -143,7 +143,12 @@ struct BdDev {
   double2 *wall;
   const BdRep *rep;        // [R]
   // triangulation (corner table), all replicas
-  int4 *tv, *tn, *tv_snap, *tn_snap;
+  int4 *tv, *tn;
+  // undo journal of a triangulation launch: jmark[t] = the launch's stamp
+  // (odd, so a cleared 0 matches no launch) once triangle t is journaled,
+  // (jtv[t], jtn[t]) its corners and neighbours before the launch changed it
+  int4 *jtv, *jtn;
+  unsigned *jmark;
   unsigned long long *claim;
   int *vt;                 // per vertex: one corner holding it (kept by the flips)
   // tinv = 1 while a triangle is inverted (set by a check pass, cleared by
@@ -247,7 +252,7 @@ cudaError_t bd_launch_overlap_verlet(const BdDev &d, const BdConst &c, cudaStrea
 // a halved step completed: advance the device step counter and the step count
 cudaError_t bd_launch_advance_step(const BdDev &d, cudaStream_t s);
 // after a timed-out grid barrier: undo the step (or the new positions of
-// bd_set_state) from the snapshots the persistent kernels take, as their own
+// bd_set_state) from the step-start copies and the undo journal, as their own
 // failure path does, and clear the flip claims and list marks the abandoned
 // launch may have left
 cudaError_t bd_launch_restore_step(const BdDev &d, const BdConst &c, cudaStream_t s);

@@ -35,7 +35,9 @@
 //
 // Grid-wide barriers spin with a time limit: a barrier that waits longer
 // than BD_BARRIER_TIMEOUT_NS sets BD_ERR_DEVICE_TIMEOUT and every block leaves.
-// On any failure the step is undone from the snapshot taken in the first P pass.
+// On any failure the step is undone from the launch's undo journal: the first
+// change a launch makes to a triangle (a flip, its back-pointers, a periodic
+// shift) records the triangle's corners and neighbours as they were.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -72,6 +74,7 @@ struct Ctx {
   int T;
   int np;
   float sig2f;   // sigma^2 (1 + 1e-5): FP32 screen of the overlap scan
+  unsigned jstamp;   // this launch's undo-journal mark (odd)
 };
 
 // FP32 filters in front of the exact integer predicates.  Every disk's
@@ -316,6 +319,33 @@ __device__ __forceinline__ bool owns6(const Ctx &x, int t0, int k0, const int4 &
   return true;
 }
 
+// Record triangle t, whose corners and neighbours are (V, N), in the undo
+// journal before the launch first changes it (in its own slot: no list and no
+// shared counter; an undo scans the marks).  A triangle is changed by one
+// thread per phase (flips own the triangles they touch; the shift pass visits
+// each triangle once), so the test of the mark needs no atomic.  A flip's
+// outer neighbours are not journaled: their one change, the back-pointer, is
+// rebuilt by the undo from the restored pair (they were adjacent before).
+__device__ __forceinline__ void journal(const Ctx &x, int t, const int4 &V, const int4 &N, unsigned mark) {
+  if (mark == x.jstamp) return;
+  x.d.jmark[t] = x.jstamp;
+  x.d.jtv[t] = V;
+  x.d.jtn[t] = N;
+}
+// undo of a journaled triangle t: its corners and neighbours as they were, a
+// corner for each of its vertices, and its neighbours' back-pointers
+__device__ __forceinline__ void unjournal(const BdDev &d, int t) {
+  const int4 vs = d.jtv[t], ns = d.jtn[t];
+  d.tv[t] = vs;
+  d.tn[t] = ns;
+  d.vt[vs.x] = 3 * t;
+  d.vt[vs.y] = 3 * t + 1;
+  d.vt[vs.z] = 3 * t + 2;
+  const int nk[3] = {ns.x, ns.y, ns.z};
+  for (int k = 0; k < 3; ++k)
+    if (nk[k] >= 0) ((int *)&d.tn[nk[k] / 3])[nk[k] % 3] = 3 * t + k;
+}
+
 // Flip the edge facing corner c0 in place (the two triangle slots are reused)
 // and point the four outer neighbours, owned by this flip, at the new corners.
 // Quad a-b-d-c with t0 = (a, b, c), t1 = (d, c, b) becomes t0 = (b, d, a),
@@ -323,7 +353,11 @@ __device__ __forceinline__ bool owns6(const Ctx &x, int t0, int k0, const int4 &
 template <bool PER>
 __device__ void flip_owned(const Ctx &x, int c0, int o0, uint8_t stamp) {
   const int t0 = c0 / 3, k0 = c0 % 3, t1 = o0 / 3, k1 = o0 % 3;
+  // the journal marks are loaded with the pair, and the pair's old values
+  // journaled after the flip's own stores (they are held in registers)
+  const unsigned m0 = x.d.jmark[t0], m1 = x.d.jmark[t1];
   int4 V0 = x.d.tv[t0], V1 = x.d.tv[t1], N0 = x.d.tn[t0], N1 = x.d.tn[t1];
+  const int4 oV0 = V0, oV1 = V1, oN0 = N0, oN1 = N1;
   const int a = vk(V0, k0), b = vk(V0, (k0 + 1) % 3), c = vk(V0, (k0 + 2) % 3), dd = vk(V1, k1);
   const int n_ca = vk(N0, (k0 + 1) % 3), n_ab = vk(N0, (k0 + 2) % 3);
   const int n_bd = vk(N1, (k1 + 1) % 3), n_dc = vk(N1, (k1 + 2) % 3);
@@ -379,6 +413,8 @@ __device__ void flip_owned(const Ctx &x, int c0, int o0, uint8_t stamp) {
   if (n_bd >= 0) ((int *)&x.d.tn[n_bd / 3])[n_bd % 3] = 3 * t0 + (k0 + 2) % 3;
   if (n_dc >= 0) ((int *)&x.d.tn[n_dc / 3])[n_dc % 3] = 3 * t1 + (k1 + 1) % 3;
   if (n_ca >= 0) ((int *)&x.d.tn[n_ca / 3])[n_ca % 3] = 3 * t1 + (k1 + 2) % 3;
+  journal(x, t0, oV0, oN0, m0);
+  journal(x, t1, oV1, oN1, m1);
 }
 
 // Append triangle t to a list once per generation (a list is visited by one
@@ -460,11 +496,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
   const int nth = gridDim.x * blockDim.x;
   const bool lead = (blockIdx.x == 0 && threadIdx.x == 0);
   unsigned long long epoch = ctl->epoch;   // written only at kernel end by the lead thread
+  x.jstamp = ((unsigned)epoch << 1) | 1u;   // distinct per launch: the epoch grows across launches
   const double sigma = c.sigma;
   int status = 0;
   int corr_iter = 0;
   long long st_overlap = 0, st_flips = 0, st_rflips = 0, st_inv = 0, st_rounds = 0;
-  bool first = true;       // take the rollback snapshot in the first pass
   bool fresh = true;       // the moved flags describe the latest move
   int lawson_rounds = 0;
   // rollout log (adjoint): committed passes and their overlapping pairs
@@ -507,12 +543,9 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       phase_begin(ctl, b);
       for (int t = tid; t < x.T; t += nth) {
         const int4 v = d.tv[t];
-        if (first) {
-          d.tv_snap[t] = v;
-          d.tn_snap[t] = d.tn[t];
-        }
         const uint8_t w0 = d.wrap[v.x], w1 = d.wrap[v.y], w2 = d.wrap[v.z];
         if ((w0 | w1 | w2) == 0) continue;
+        journal(x, t, v, d.tn[t], d.jmark[t]);
         // a corner stored L k lower than where it geometrically is: shift += k
         const int kx[3] = {wrapx(w0), wrapx(w1), wrapx(w2)}, ky[3] = {wrapy(w0), wrapy(w1), wrapy(w2)};
         int sx[3], sy[3];
@@ -526,7 +559,6 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       }
       if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
       if (lead) ctl->n_wrapped = 0;
-      first = false;
     }
     // ---------------- P: check, mark, scan ----------------
     const int dom_n = full ? x.T : bc[BC_ACT + slot];
@@ -540,10 +572,6 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         const int t = full ? it : dom[it];
         const int4 v = d.tv[t];
         const int4 nn = d.tn[t];
-        if (first) {
-          d.tv_snap[t] = v;
-          d.tn_snap[t] = nn;
-        }
         // corners loaded once: FP32 pairs, moved flags and re-entries serve the
         // filters of triangles and edges that carry no image shift
         const int vv[3] = {v.x, v.y, v.z};
@@ -688,10 +716,6 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         const int t = full ? it : dom[it];
         const int4 v = d.tv[t];
         const int4 nn = d.tn[t];
-        if (first) {
-          d.tv_snap[t] = v;
-          d.tn_snap[t] = nn;
-        }
         const int vv[3] = {v.x, v.y, v.z};
         const bool isd[3] = {v.x < x.np, v.y < x.np, v.z < x.np};
         float4 W[3];
@@ -820,7 +844,6 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       stage_tick(ctl, full ? STAGE_P : STAGE_PL, t_mark);
       ctl->act_n[(kp + 2) % 3] = 0;   // filled by the next pass
     }
-    first = false;
     const int n_inv = bc[BC_CNT + C_INV];
     const int n_rej = bc[BC_CNT + C_REJECT];
     const int n_cand = bc[BC_CNT + C_CAND];
@@ -1098,7 +1121,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
   }
 
   if (status) {
-    // undo the step: positions, directions and triangulation from the snapshot
+    // undo the step: positions and directions from the step start, the
+    // triangulation from the undo journal
     phase_begin(ctl, b);
     for (int i = tid; i < x.np; i += nth) {
       if (d.ext_id[i] < 0) continue;
@@ -1110,15 +1134,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       d.disp[i] = make_double2(0.0, 0.0);
       d.moved[i] = 0;
     }
+    // the journaled triangles as they were; a corner for each of their
+    // vertices (flips re-point only the vertices of the triangles they change)
     for (int t = tid; t < x.T; t += nth) {
-      const int4 vs = d.tv_snap[t];
-      d.tv[t] = vs;
-      d.tn[t] = d.tn_snap[t];
       d.tinv[t] = 0;
-      // a corner per vertex of the restored triangulation (any one will do)
-      d.vt[vs.x] = 3 * t;
-      d.vt[vs.y] = 3 * t + 1;
-      d.vt[vs.z] = 3 * t + 2;
+      if (d.jmark[t] == x.jstamp) unjournal(d, t);
     }
     if (lead) atomicCAS(&ctl->status, 0, status);
   } else {
@@ -1149,10 +1169,11 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
 }
 
 // Undo a step whose persistent kernel left at a timed-out barrier (the
-// kernel's own failure path did not run).  Every block of such a launch ends
-// its first pass -- the one that takes the snapshot -- before it reaches any
-// barrier, so the snapshot is whole; positions and directions come from
-// pos0 / theta0 (the step start, or the positions before bd_set_state).
+// kernel's own failure path did not run).  The launch journaled every
+// triangle before its first change to it, and all its blocks have finished
+// (this kernel runs after it in stream order), so replaying the journal
+// restores the triangulation; positions and directions come from pos0 /
+// theta0 (the step start, or the positions before bd_set_state).
 // bd_launch_restore_step runs it (the header above the launcher declares it).
 __global__ void k_restore_step(BdDev d, BdConst c) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1168,14 +1189,16 @@ __global__ void k_restore_step(BdDev d, BdConst c) {
     d.moved[i] = 0;
   }
   if (!c.overlap_verlet) {
+    // the journaled triangles as they were, a corner for each of their
+    // vertices; their marks cleared (the abandoned launch did not publish its
+    // epoch, so the next launch takes the same stamp)
+    const unsigned jstamp = ((unsigned)d.ctl->epoch << 1) | 1u;
     for (int t = tid; t < c.nt; t += nth) {
-      const int4 vs = d.tv_snap[t];
-      d.tv[t] = vs;
-      d.tn[t] = d.tn_snap[t];
       d.tinv[t] = 0;
-      d.vt[vs.x] = 3 * t;
-      d.vt[vs.y] = 3 * t + 1;
-      d.vt[vs.z] = 3 * t + 2;
+      if (d.jmark[t] == jstamp) {
+        unjournal(d, t);
+        d.jmark[t] = 0u;
+      }
       // the abandoned launch did not publish the claim epochs and list
       // generations it used (the next launch starts from the same ones):
       // clear its claims (0 matches no epoch) and list marks (0 matches no
