@@ -214,7 +214,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind, visits=None):
+def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind, visits=None, flips=0.0):
     """HBM roofline of the per-step correction kernel of the short-range path.
 
     Duration: the kernel's own device-clock stage timers (bd_stage_times),
@@ -223,10 +223,11 @@ def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind, v
     triangles the check passes visited (bd_step_stats.tri_visits, V):
       k_triangulation: a check pass reads the corner table of each triangle
         it visits (32 B) and, in the first pass of the step, each disk's moved
-        flag, FP32 position and FP32 move (25 B); the first pass also writes the rollback
-        snapshot (32 B per triangle); a flip round reads the claims and flags
-        of the triangles its pass visited (24 B each); an apply pass reads and
-        writes positions, displacements and flags (100 B per disk).
+        flag, FP32 position and FP32 move (25 B); a flip (bd_step_stats.flips)
+        reads its candidate entry, six claims and the pair's corner tables and
+        writes the pair, four back-pointers and the pair's undo journal (about
+        200 B); an apply pass reads and writes positions, displacements and
+        flags (100 B per disk).
       k_overlap_verlet: a scan pass reads each disk's count, flag, both
         position copies and its list with the neighbours' flags (38 + 5 m B
         per disk, m the mean list length) and writes its displacement and hit
@@ -245,7 +246,7 @@ def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind, v
         T = system.n_tri
         P, F, A = (stage_raw[k][1] / steps for k in ("check", "flip", "apply"))
         V = visits if visits else P * T
-        per = 32 * V + 25 * N + 32 * T + 24 * V * (F / max(P, 1.0)) + A * 100 * N
+        per = 32 * V + 25 * N + 200 * flips + A * 100 * N
         kernel = "k_triangulation"
         note = ("%.2f check passes visiting %.0f triangles, %.2f flip rounds, %.2f apply passes per "
                 "launch; %d triangles" % (P, V, F, A, T))
@@ -652,7 +653,8 @@ def main():
             # persistent correction kernel, bound by memory (gathers), so its
             # line is HBM bytes against the measured copy bandwidth
             line["roofline"] = correction_roofline(system, stage_raw, args.steps, N, verlet_mode, pk, pk_kind,
-                                                   stats_tot.get("tri_visits", 0) / args.steps)
+                                                   stats_tot.get("tri_visits", 0) / args.steps,
+                                                   stats_tot.get("flips", 0) / args.steps)
         elif cfg.precision == 1:
             # FP64 sweep (one disk per thread, 12 FP64 flops per ordered pair);
             # FP64 issues at 1/64 of the FP32 rate on this part
