@@ -302,7 +302,6 @@ __global__ void __launch_bounds__(256, 3) k_force_verlet(BdDev d, BdConst c) {
   if (!Rp || d.ext_id[i] < 0) return;
   const BdRep &R = *Rp;
   const float4 wi = d.work[i];
-  const double2 pi = d.pos[i];
   const int m = d.vl_cnt[i];
   const float rc2 = (float)(R.r_cut * R.r_cut);
   const float eps = (float)R.eps, kap = (float)R.kappa;
@@ -316,16 +315,22 @@ __global__ void __launch_bounds__(256, 3) k_force_verlet(BdDev d, BdConst c) {
   const float s2l0 = (float)(c.sigma * c.sigma - (double)s2h0);
   float fx = 0.f, fy = 0.f;      // Yukawa tail, FP32
   ff gx = {0.f, 0.f}, gy = {0.f, 0.f};   // WCA core, float-float sums
-  // four list entries at a time: their index loads, then their position
-  // gathers, are issued before any of them is used (the loop is bound by the
-  // latency of these dependent loads, not by arithmetic)
+  // four list entries at a time: their position gathers are issued before
+  // any of them is used, and the next four indices are loaded while these
+  // are evaluated (the loop is bound by the latency of these dependent loads,
+  // not by arithmetic)
+  int jn[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) jn[u] = u < m ? d.vl_idx[(size_t)u * c.np + i] : i;
   for (int t0 = 0; t0 < m; t0 += 4) {
     int jj[4];
     float4 wv[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) jj[u] = t0 + u < m ? d.vl_idx[(size_t)(t0 + u) * c.np + i] : i;
+    for (int u = 0; u < 4; ++u) jj[u] = jn[u];
 #pragma unroll
     for (int u = 0; u < 4; ++u) wv[u] = d.work[jj[u]];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) jn[u] = t0 + 4 + u < m ? d.vl_idx[(size_t)(t0 + 4 + u) * c.np + i] : i;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (t0 + u >= m) break;
@@ -338,7 +343,7 @@ __global__ void __launch_bounds__(256, 3) k_force_verlet(BdDev d, BdConst c) {
       float lx = __fsub_rn(wi.z, wj.z), ly = __fsub_rn(wi.w, wj.w);
       if (R.periodic && (fabsf(hx) > R.hLf || fabsf(hy) > R.hLf)) {
         const bdpred::Grid g{c.q, c.inv_q, c.qshift};
-        const double2 pj = d.pos[j];
+        const double2 pi = d.pos[i], pj = d.pos[j];
         long long X = bdpred::to_int(pi.x, g) - bdpred::to_int(pj.x, g);
         long long Y = bdpred::to_int(pi.y, g) - bdpred::to_int(pj.y, g);
         const long long h = R.LQ / 2;
@@ -363,7 +368,7 @@ __global__ void __launch_bounds__(256, 3) k_force_verlet(BdDev d, BdConst c) {
       }
       if (fabsf(r2 - rc2) < 1e-5f * rc2) {
         // at the cut-off the force jumps: decide as the FP64 reference does
-        const double2 pj = d.pos[j];
+        const double2 pi = d.pos[i], pj = d.pos[j];
         const double ex = dmin_image(__dsub_rn(pi.x, pj.x), R), ey = dmin_image(__dsub_rn(pi.y, pj.y), R);
         if (!(sqrt(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey))) < R.r_cut)) continue;
       } else if (r2 >= rc2) {
