@@ -242,6 +242,8 @@ __global__ void k_vl_build(BdDev d, BdConst c) {
     const BdRep &R = *Rp;
     const double2 p = d.pos[i];
     d.vl_ref[i] = p;
+    const float4 wi = d.work[i];
+    const float rl2f = (float)R.rl2;
     const int k = d.cell_of[i] - R.cell_base;
     const int cx = k % R.ncell, cy = k / R.ncell;
     int buf[BD_VL_MAX];
@@ -259,10 +261,28 @@ __global__ void k_vl_build(BdDev d, BdConst c) {
         for (int s = b; s < e; ++s) {
           int j = d.cell_idx[s];
           if (j == i) continue;
-          double2 q = d.pos[j];
-          double dx = dmin_image(__dsub_rn(p.x, q.x), R), dy = dmin_image(__dsub_rn(p.y, q.y), R);
-          double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-          if (r2 < R.rl2) {
+          // FP32 screen from the (hi, lo) pairs: the hi difference is exact
+          // (Sterbenz) or off by at most half an ulp of a coordinate below 12
+          // (4.8e-7), so the computed r^2 is within 1e-6 of the exact one
+          // relative to the reach; only pairs within 1e-5 of the reach (and
+          // pairs across a periodic edge) take the FP64 decision
+          const float4 wj = d.work[j];
+          const float hx = __fsub_rn(wi.x, wj.x), hy = __fsub_rn(wi.y, wj.y);
+          bool in;
+          bool exact = R.periodic && (fabsf(hx) > R.hLf || fabsf(hy) > R.hLf);
+          if (!exact) {
+            const float fx = __fadd_rn(hx, __fsub_rn(wi.z, wj.z)), fy = __fadd_rn(hy, __fsub_rn(wi.w, wj.w));
+            const float f2 = __fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy));
+            if (f2 < rl2f * 0.99999f) in = true;
+            else if (f2 > rl2f * 1.00001f) in = false;
+            else exact = true;
+          }
+          if (exact) {
+            const double2 q = d.pos[j];
+            const double dx = dmin_image(__dsub_rn(p.x, q.x), R), dy = dmin_image(__dsub_rn(p.y, q.y), R);
+            in = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) < R.rl2;
+          }
+          if (in) {
             if (m < BD_VL_MAX) {
               // insertion in sorted position
               int t = m++;
