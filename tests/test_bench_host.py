@@ -17,15 +17,15 @@ class _FakeSystem:
 
 
 def test_correction_roofline_counts_the_documented_bytes():
-    # 2 steps: 8 check passes visiting 9000 triangles, 4 flip rounds, 2 apply passes
+    # 2 steps: 8 check passes visiting 9000 triangles, 4 flip rounds with 60
+    # flips, 2 apply passes
     stage_raw = {"check": (0.8, 8), "repair": (0.0, 0), "flip": (0.2, 4), "apply": (0.1, 2),
                  "check_lists": (0.3, 6)}
-    N, steps, visits = 1000, 2, 4500.0
+    N, steps, visits, flips = 1000, 2, 4500.0, 30.0
     r = bench.correction_roofline(_FakeSystem(), stage_raw, steps, N, False, {"hbm_gbs": 5000.0},
-                                  "measured", visits=visits)
-    P, F, A = 4.0, 2.0, 1.0                    # per launch
-    T = _FakeSystem.n_tri
-    per = 32 * visits + 25 * N + 32 * T + 24 * visits * (F / P) + A * 100 * N
+                                  "measured", visits=visits, flips=flips)
+    A = 1.0                                    # apply passes per launch
+    per = 32 * visits + 25 * N + 200 * flips + A * 100 * N
     ms = (0.8 + 0.2 + 0.1) / steps             # check_lists is part of check
     assert r["algorithmic_bytes_per_launch"] == pytest.approx(per)
     assert r["avg_launch_ms"] == pytest.approx(ms)
