@@ -729,6 +729,8 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
   {
     const char *tl = getenv("BD_TRI_LISTS");
     c.tri_lists = tl ? std::min(2, std::max(0, atoi(tl))) : 0;
+    const char *tf = getenv("BD_TRI_FUSE");
+    c.tri_fuse = tf ? (atoi(tf) != 0 ? 1 : 0) : 1;
   }
   {
     // the lists hold every pair within r_cut + skin of the build positions, so
@@ -866,9 +868,11 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     BD_TRY(dalloc(h, &d.jtn, (size_t)nt));
     BD_TRY(dalloc(h, &d.jmark, (size_t)nt));
     BD_TRY(cudaMemsetAsync(d.jmark, 0, (size_t)nt * sizeof(unsigned), h->stream));
-    BD_TRY(dalloc(h, &d.claim, (size_t)nt));
+    BD_TRY(dalloc(h, &d.claim, 2 * (size_t)nt));
     BD_TRY(dalloc(h, &d.tinv, (size_t)nt));
-    BD_TRY(dalloc(h, &d.clist, (size_t)nt));
+    BD_TRY(dalloc(h, &d.clist, 3 * (size_t)nt));
+    BD_TRY(dalloc(h, &d.clmark, (size_t)nt));
+    BD_TRY(cudaMemsetAsync(d.clmark, 0, (size_t)nt * sizeof(unsigned), h->stream));
     BD_TRY(cudaMemsetAsync(d.tinv, 0, (size_t)nt, h->stream));
     BD_TRY(dalloc(h, &d.vt, nv));
     BD_TRY(dalloc(h, &d.act, 3 * (size_t)nt));
@@ -995,7 +999,7 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
       }
       BD_TRY(cudaMemcpy(d.vt, vt.data(), nv * sizeof(int), cudaMemcpyHostToDevice));
     }
-    BD_TRY(cudaMemsetAsync(d.claim, 0, nt * sizeof(unsigned long long), st));
+    BD_TRY(cudaMemsetAsync(d.claim, 0, 2 * nt * sizeof(unsigned long long), st));
     if (!iperm.empty())
       BD_TRY(cudaMemcpyAsync(d.iperm, iperm.data(), iperm.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     if (!iorg.empty())

@@ -81,6 +81,7 @@ struct BdCtl {
   int n_wrapped;                   // periodic box: disks that re-entered in the last move (consumed
                                    // by the triangulation kernel's shift pass; not a statistic)
   int act_n[3];                    // lengths of the rotating triangle lists (zeroed at kernel exit)
+  int cl_n[3];                     // lengths of the candidate lists (zeroed at kernel exit)
   unsigned act_gen;                // next list generation (grows across launches)
   // set by the host (bd_set_wait_limit), kept across calls: the time limit of a
   // grid barrier wait (0 = BD_BARRIER_TIMEOUT_NS) and, for tests of the
@@ -92,7 +93,7 @@ struct BdCtl {
 };
 
 // counter slots within BdCtl::cnt[phase % 4]
-enum { C_INV = 0, C_REJECT = 1, C_FLIPS = 2, C_OVERLAP = 3, C_CAND = 4, C_CLIST = 5 };
+enum { C_INV = 0, C_REJECT = 1, C_FLIPS = 2, C_OVERLAP = 3, C_CAND = 4, C_LOSE = 5, C_OVADJ = 6 };
 
 // Per-replica parameters (a handle advances R >= 1 independent systems; a
 // single system is R = 1).  Device-resident table read by the kernels.
@@ -149,13 +150,16 @@ struct BdDev {
   // (jtv[t], jtn[t]) its corners and neighbours before the launch changed it
   int4 *jtv, *jtn;
   unsigned *jmark;
+  // 2 x nt flip claims: the round of epoch e claims in half e % 2 (so a round
+  // can claim for the next while its own claims are read)
   unsigned long long *claim;
   int *vt;                 // per vertex: one corner holding it (kept by the flips)
   // tinv = 1 while a triangle is inverted (set by a check pass, cleared by
-  // the triangle's flip); clist = the triangles that registered a flip
-  // candidate in the last check pass
+  // the triangle's flip); clist = 3 x nt: the triangles that registered a flip
+  // candidate for the round of epoch e sit in list e % 3 (BdCtl::cl_n)
   uint8_t *tinv;
   int *clist;
+  unsigned *clmark;        // per triangle: the epoch of the candidate list it last joined
   int *act;                // 3 x nt: rotating lists of the triangles a check pass visits
   unsigned *act_mark;      // 3 x nt: generation at which a triangle joined each list
   // force sweep
@@ -213,6 +217,9 @@ struct BdConst {
   int tri_lists;           // check passes after the first of a move: 0 lists when a full pass
                            // is throughput-bound (many triangles per thread), 1 always lists,
                            // 2 always full (environment variable BD_TRI_LISTS at init)
+  int tri_fuse;            // 1: a Lawson round tests the outer edges of its flips and keeps the
+                           // overlap sums (no check pass between rounds); 0: a check pass after
+                           // every round (environment variable BD_TRI_FUSE at init)
   double vl_reach2;        // squared displacement since the list build below which the lists
                            // still hold every pair closer than sigma
   int log_pairs_cap, log_pass_cap;   // rollout log capacities

@@ -40,11 +40,12 @@ __device__ __forceinline__ int ld_status(const int *p) {
 // Words every thread needs after a barrier, read once per block by thread 0
 // and handed to the block through shared memory (116k threads reading one
 // global line would queue ~18k requests on one L2 slice per barrier).
-enum { BC_CNT = 0, BC_ACT = 8, BC_N = 11 };
+enum { BC_CNT = 0, BC_ACT = 8, BC_CL = 11, BC_N = 14 };
 
 // bounded grid barrier; returns false if the grid must stop.  With bc (block
 // shared, BC_N ints): bc[BC_CNT + k] = the counters of the phase that just
-// ended, bc[BC_ACT + l] = the lengths of the triangle lists.
+// ended, bc[BC_ACT + l] = the lengths of the triangle lists, bc[BC_CL + l]
+// those of the candidate lists.
 static __device__ bool grid_sync(BdCtl *ctl, Bar &b, int *bc = nullptr) {
   __shared__ int s_ok;
   __syncthreads();
@@ -88,6 +89,7 @@ static __device__ bool grid_sync(BdCtl *ctl, Bar &b, int *bc = nullptr) {
       const volatile int *row = ctl->cnt[b.ph & 3];
       for (int k = 0; k < 8; ++k) bc[BC_CNT + k] = row[k];
       for (int l = 0; l < 3; ++l) bc[BC_ACT + l] = ((const volatile int *)ctl->act_n)[l];
+      for (int l = 0; l < 3; ++l) bc[BC_CL + l] = ((const volatile int *)ctl->cl_n)[l];
     }
     s_ok = ok;
   }
@@ -110,7 +112,7 @@ static __device__ void block_exit(BdCtl *ctl) {
     if (k == gridDim.x - 1) {
       ctl->bar_count = 0;
       ctl->bar_gen = 0;
-      for (int l = 0; l < 3; ++l) ctl->act_n[l] = 0;
+      for (int l = 0; l < 3; ++l) ctl->act_n[l] = ctl->cl_n[l] = 0;
       for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 8; ++b) ctl->cnt[a][b] = 0;
       __threadfence();

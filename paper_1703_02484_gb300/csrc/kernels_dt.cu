@@ -133,6 +133,28 @@ __device__ __forceinline__ double2 disp_get(const Ctx &x, int i) {
   return make_double2(__dmul_rn((double)w.x, x.c.disp_unscale), __dmul_rn((double)w.y, x.c.disp_unscale));
 }
 
+// Algorithm 2's overlap test of the disk pair (u, w), w's image shifted by
+// (rsx, rsy) L: an exact pre-test in grid units, |r_w - r_u|^2 <= (sigma/q)^2
+// (1 + 1e-9), then the decision r < a_u + a_w in FP64 as the reference makes
+// it (the difference of two grid values is exact in FP64).  On overlap, v is
+// the push of w, (a_u + a_w - r) (r_w - r_u) / r; u's is -v.
+__device__ __forceinline__ bool edge_overlap(const Ctx &x, int u, int w, int rsx, int rsy, long long LQ, double2 &v,
+                                             double &del) {
+  const double2 pu = x.d.pos[u], pw = x.d.pos[w];
+  const int64_t ix = bdpred::to_int(pw.x, x.g) - bdpred::to_int(pu.x, x.g) + rsx * LQ;
+  const int64_t iy = bdpred::to_int(pw.y, x.g) - bdpred::to_int(pu.y, x.g) + rsy * LQ;
+  const bdpred::i128 ir2 = bdpred::add128(bdpred::smul64(ix, ix), bdpred::smul64(iy, iy));
+  const bool near = ir2.hi < x.c.sig2q_hi || (ir2.hi == x.c.sig2q_hi && ir2.lo <= x.c.sig2q_lo);
+  if (!near) return false;
+  const double dx = bdem::grid_to_double(ix, x.g.s), dy = bdem::grid_to_double(iy, x.g.s);
+  const double r = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+  const double sg = x.d.rad ? x.d.rad[u] + x.d.rad[w] : x.c.sigma;   // polydisperse: a_u + a_w
+  if (!(r < sg)) return false;
+  del = sg - r;
+  v = make_double2(del * (dx / r), del * (dy / r));
+  return true;
+}
+
 // a test the FP32 filter could not decide (rare: near-degenerate inputs)
 __device__ __forceinline__ void count_exact(const Ctx &x) {
   atomicAdd((unsigned long long *)&x.d.ctl->st_exact, 1ull);
@@ -297,25 +319,30 @@ __device__ __forceinline__ float4 split_pos(double2 p) {
 // the pair and the four triangles across its outer edges.  An edge that
 // holds all six claims owns them for the round, so its flip can rewrite the
 // neighbours' back-pointers directly.
-__device__ __forceinline__ void claim6(const Ctx &x, int t, int k, const int4 &nn, int o,
+// the claims of the round of epoch e
+__device__ __forceinline__ unsigned long long *claims(const Ctx &x, unsigned long long e) {
+  return x.d.claim + (size_t)(e & 1ull) * x.T;
+}
+
+__device__ __forceinline__ void claim6(const Ctx &x, unsigned long long *cb, int t, int k, const int4 &nn, int o,
                                        unsigned long long key) {
   const int t1 = o / 3, k1 = o % 3;
   const int4 nn1 = x.d.tn[t1];
-  atomicMax(&x.d.claim[t], key);
-  atomicMax(&x.d.claim[t1], key);
+  atomicMax(&cb[t], key);
+  atomicMax(&cb[t1], key);
   int e[4] = {vk(nn, (k + 1) % 3), vk(nn, (k + 2) % 3), vk(nn1, (k1 + 1) % 3), vk(nn1, (k1 + 2) % 3)};
   for (int m = 0; m < 4; ++m)
-    if (e[m] >= 0) atomicMax(&x.d.claim[e[m] / 3], key);
+    if (e[m] >= 0) atomicMax(&cb[e[m] / 3], key);
 }
 
-__device__ __forceinline__ bool owns6(const Ctx &x, int t0, int k0, const int4 &N0, int o0,
-                                      unsigned long long key) {
+__device__ __forceinline__ bool owns6(const Ctx &x, const unsigned long long *cb, int t0, int k0, const int4 &N0,
+                                      int o0, unsigned long long key) {
   const int t1 = o0 / 3, k1 = o0 % 3;
-  if (x.d.claim[t1] != key) return false;
+  if (cb[t1] != key) return false;
   const int4 N1 = x.d.tn[t1];
   int e[4] = {vk(N0, (k0 + 1) % 3), vk(N0, (k0 + 2) % 3), vk(N1, (k1 + 1) % 3), vk(N1, (k1 + 2) % 3)};
   for (int m = 0; m < 4; ++m)
-    if (e[m] >= 0 && x.d.claim[e[m] / 3] != key) return false;
+    if (e[m] >= 0 && cb[e[m] / 3] != key) return false;
   return true;
 }
 
@@ -351,7 +378,7 @@ __device__ __forceinline__ void unjournal(const BdDev &d, int t) {
 // Quad a-b-d-c with t0 = (a, b, c), t1 = (d, c, b) becomes t0 = (b, d, a),
 // t1 = (c, a, d): the edge bc is replaced by ad.
 template <bool PER>
-__device__ void flip_owned(const Ctx &x, int c0, int o0, uint8_t stamp) {
+__device__ void flip_owned(const Ctx &x, int c0, int o0, uint8_t stamp, bool stamp_pair = true) {
   const int t0 = c0 / 3, k0 = c0 % 3, t1 = o0 / 3, k1 = o0 % 3;
   // the journal marks are loaded with the pair, and the pair's old values
   // journaled after the flip's own stores (they are held in registers)
@@ -396,8 +423,8 @@ __device__ void flip_owned(const Ctx &x, int c0, int o0, uint8_t stamp) {
     }
   }
   // both new triangles: their edges are tested by the next check pass
-  V0.w = with_stamp(nw0, stamp);
-  V1.w = with_stamp(nw1, stamp);
+  V0.w = stamp_pair ? with_stamp(nw0, stamp) : with_stamp(nw0, tstamp(w0));
+  V1.w = stamp_pair ? with_stamp(nw1, stamp) : with_stamp(nw1, tstamp(w1));
   x.d.tv[t0] = V0;
   x.d.tv[t1] = V1;
   x.d.tn[t0] = N0;
@@ -431,6 +458,27 @@ __device__ __forceinline__ void push_tri(int *list, unsigned *mark, int *n, unsi
   if (lane == leader) base = atomicAdd(n, __popc(want));
   base = __shfl_sync(act, base, leader);
   if (add) list[base + __popc(want & ((1u << lane) - 1u))] = t;
+}
+
+// Register triangle t as a candidate owner for the round of epoch e, once:
+// the marking pass and the previous fused round both register owners for a
+// round, and an owner listed twice would be flipped by two threads at once.
+__device__ __forceinline__ void push_owner(const Ctx &x, unsigned long long e, int t) {
+  if (atomicExch(&x.d.clmark[t], (unsigned)e) == (unsigned)e) return;
+  const int l = (int)(e % 3);
+  x.d.clist[(size_t)l * x.T + atomicAdd(&x.d.ctl->cl_n[l], 1)] = t;
+}
+
+// Stamp triangle t for the check pass of generation byte s.  The word is
+// shared with the corners' image shifts, which a flip of t by another thread
+// may rewrite meanwhile: compare-and-swap keeps whichever shifts are current.
+__device__ __forceinline__ void stamp_tri(const Ctx &x, int t, uint8_t s) {
+  int *w = &x.d.tv[t].w;
+  int old = *(volatile int *)w, seen;
+  do {
+    seen = old;
+    old = atomicCAS(w, seen, with_stamp(seen, s));
+  } while (old != seen);
 }
 
 // the replica of a triangle (its first disk corner; -1 if it has none)
@@ -527,9 +575,20 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
   // disks, 1.8 per thread, 0.13 -> 0.17 ms).
   const bool use_lists = c.tri_lists == 1 || (c.tri_lists == 0 && x.T > 4 * nth);
   long long tri_visits = 0;
+  // the next iteration opens with a check pass (need_p) that scans the
+  // overlaps (scan); the overlapping edges of the current triangulation
+  // (ov_now); Lawson rounds fused with their re-tests (not while a rollout
+  // logs its pairs, which wants every pair of a pass from one scan)
+  bool need_p = true, scan = true;
+  int ov_now = 0;
+  const bool fuse = c.tri_fuse && !logging;
 
   for (;;) {
     ++epoch;
+    if (lead) {
+      ctl->cl_n[(epoch + 2) % 3] = 0;   // the candidate list two rounds ahead
+      ctl->act_n[(kp + 2) % 3] = 0;     // the triangle list two passes ahead
+    }
     const int slot = kp % 3, nslot = (kp + 1) % 3;
     const unsigned gen = g0 + (unsigned)kp, ngen = gen + 1u;
     const uint8_t gen8 = (uint8_t)gen, ngen8 = (uint8_t)ngen;   // check-pass stamps of this pass and the next
@@ -561,389 +620,369 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       if (lead) ctl->n_wrapped = 0;
     }
     // ---------------- P: check, mark, scan ----------------
+    // (skipped between fused Lawson rounds: their flips test the edges they
+    // change; a pass that follows such rounds only marks, scan = false, since
+    // the rounds keep the overlap sums of the triangulation they leave)
+    int n_ov = 0;
     const int dom_n = full ? x.T : bc[BC_ACT + slot];
-    if (lead) tri_visits += dom_n;
-    phase_begin(ctl, b);
-    {
-      int inv = 0, rej = 0, cand = 0, nov = 0;
-      double mx = 0.0;
-      if constexpr (PER)
-      for (int it = tid; it < dom_n; it += nth) {
-        const int t = full ? it : dom[it];
-        const int4 v = d.tv[t];
-        const int4 nn = d.tn[t];
-        // corners loaded once: FP32 pairs, moved flags and re-entries serve the
-        // filters of triangles and edges that carry no image shift
-        const int vv[3] = {v.x, v.y, v.z};
-        const bool isd[3] = {v.x < x.np, v.y < x.np, v.z < x.np};
-        const bool flat = (v.w & BD_TRI_SHIFT_BITS) == 0;
-        float4 W[3];
-        uint8_t mvd[3], wr[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          W[k] = work_of(x, vv[k]);
-          mvd[k] = fresh ? d.moved[vv[k]] : (uint8_t)0;
-          wr[k] = isd[k] ? d.wrap[vv[k]] : (uint8_t)0;
-        }
-        int fl = tstamp(v.w) == gen8 ? BD_TRI_DIRTY : 0;
-        if (mvd[0] | mvd[1] | mvd[2]) {
-          const int o = flat ? orient_pre(x, isd[0] && isd[1] && isd[2], W[0], W[1], W[2], v.x, v.y, v.z)
-                             : orient_s(x, v.x, tshx<PER>(v.w, 0), tshy<PER>(v.w, 0), v.y, tshx<PER>(v.w, 1),
-                                        tshy<PER>(v.w, 1), v.z, tshx<PER>(v.w, 2), tshy<PER>(v.w, 2));
-          fl = BD_TRI_DIRTY | (o <= 0 ? BD_TRI_INVERTED : 0);
-          if (o <= 0) d.tinv[t] = 1;
-        }
-        const bool inverted = (fl & BD_TRI_INVERTED) != 0;
-        inv += inverted ? 1 : 0;
-        bool owner = false;   // t registered a flip candidate
-        if (inverted && d.rep_stats) {
-          const int rr = tri_rep(d, x.np, v);
-          if (rr >= 0) atomicAdd((unsigned long long *)&d.rep_stats[3 * rr + 2], 1ull);
-        }
-        for (int k = 0; k < 3; ++k) {
-          const int cc = 3 * t + k;
-          const int o = vk(nn, k);
-          // each interior edge once: from its smaller corner, or from this side
-          // when the neighbour is not visited by this pass
-          if (o < 0 || (o <= cc && (full || cmark[o / 3] == gen))) continue;
-          const int ku = (k + 1) % 3, kw = (k + 2) % 3;
-          const int u = vv[ku], w = vv[kw];
-          const bool disks = isd[ku] && isd[kw];
-          const bool mv = (mvd[ku] | mvd[kw]) != 0;
-          // image shift of w relative to u in this triangle (periodic box; 0 with walls)
-          const int rsx = tshx<PER>(v.w, (k + 2) % 3) - tshx<PER>(v.w, (k + 1) % 3);
-          const int rsy = tshy<PER>(v.w, (k + 2) % 3) - tshy<PER>(v.w, (k + 1) % 3);
-          long long LQ = 0;
-          if (rsx | rsy) LQ = rep_LQ(x, u);
-          const bool plain = (rsx | rsy) == 0;   // the edge carries no image shift
-          // r1 = r_w - r_u from the FP32 pairs (unshifted edges)
-          const float r1x = plain ? fdiff(W[kw].x, W[kw].z, W[ku].x, W[ku].z) : 0.f;
-          const float r1y = plain ? fdiff(W[kw].y, W[kw].w, W[ku].y, W[ku].w) : 0.f;
-          if (disks && mv) {
-            // Sec. 4.3 first criterion: r0 . r1 < 0.  An unshifted edge whose
-            // ends did not re-enter is screened in FP32 from r1 and the moves,
-            // as with walls; otherwise, and near zero, exact on the grid (the
-            // edge's shift before the move is the present one less the
-            // re-entries of its end points)
-            int dec = 0;   // 1 reversed, -1 not, 0 undecided
-            if (plain && (wr[ku] | wr[kw]) == 0) {
-              const float2 mu = mvd[ku] ? d.dmove[u] : make_float2(0.f, 0.f);
-              const float2 mw = mvd[kw] ? d.dmove[w] : make_float2(0.f, 0.f);
-              const float r0x = __fsub_rn(r1x, __fsub_rn(mw.x, mu.x)), r0y = __fsub_rn(r1y, __fsub_rn(mw.y, mu.y));
-              const float dot = __fadd_rn(__fmul_rn(r0x, r1x), __fmul_rn(r0y, r1y));
-              const float S = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r0x, r0x), __fmul_rn(r0y, r0y)),
-                                                  __fadd_rn(__fmul_rn(r1x, r1x), __fmul_rn(r1y, r1y))),
-                                        __fadd_rn(__fadd_rn(__fmul_rn(mu.x, mu.x), __fmul_rn(mu.y, mu.y)),
-                                                  __fadd_rn(__fmul_rn(mw.x, mw.x), __fmul_rn(mw.y, mw.y))));
-              const float bound = 4e-6f * S;
-              dec = dot > bound ? -1 : (-dot > bound ? 1 : 0);
-              if (dec == 0) count_exact(x);
-            }
-            int ox = rsx, oy = rsy;
-            if (dec == 0) {
-              ox -= wrapx(wr[kw]) - wrapx(wr[ku]);
-              oy -= wrapy(wr[kw]) - wrapy(wr[ku]);
-              if ((ox | oy) && LQ == 0) LQ = rep_LQ(x, u);
-            }
-            if (dec == 1 || (dec == 0 && reversed_exact(x, u, w, ox, oy, rsx, rsy, LQ))) {
-              ++rej;
-              atomicExch(&ctl->st_fail_item, cc);
-            }
+    if (need_p) {
+      if (lead) tri_visits += dom_n;
+      phase_begin(ctl, b);
+      {
+        int inv = 0, rej = 0, cand = 0, nov = 0;
+        double mx = 0.0;
+        if constexpr (PER)
+        for (int it = tid; it < dom_n; it += nth) {
+          const int t = full ? it : dom[it];
+          const int4 v = d.tv[t];
+          const int4 nn = d.tn[t];
+          // corners loaded once: FP32 pairs, moved flags and re-entries serve the
+          // filters of triangles and edges that carry no image shift
+          const int vv[3] = {v.x, v.y, v.z};
+          const bool isd[3] = {v.x < x.np, v.y < x.np, v.z < x.np};
+          const bool flat = (v.w & BD_TRI_SHIFT_BITS) == 0;
+          float4 W[3];
+          uint8_t mvd[3], wr[3];
+  #pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            W[k] = work_of(x, vv[k]);
+            mvd[k] = fresh ? d.moved[vv[k]] : (uint8_t)0;
+            wr[k] = isd[k] ? d.wrap[vv[k]] : (uint8_t)0;
           }
-          if (inverted) continue;   // marks and scan wait for the repair
-          const int4 v1 = d.tv[o / 3];
-          const int q = vk(v1, o % 3);
-          // the edge is tested when a triangle on either side is dirty or one
-          // of its four points moved
-          const bool d1 = (fl & BD_TRI_DIRTY) || tstamp(v1.w) == gen8 || (mvd[ku] | mvd[kw]) ||
-                          (fresh && d.moved[q]);
-          if (d1) {
-            int sqx, sqy;
-            opp_shift<PER>(v.w, k, v1.w, o % 3, sqx, sqy);
-            const int ic = (flat && (sqx | sqy) == 0)
-                               ? incircle_pre(x, isd[0] && isd[1] && isd[2] && q < x.np, W[0], W[1], W[2],
-                                              work_of(x, q), v.x, v.y, v.z, q)
-                               : incircle_s<PER>(x, v, q, sqx, sqy);
-            if (ic > 0) {
-              claim6(x, t, k, nn, o, claim_key(epoch, cc));
-              ++cand;
-              if (!owner) {   // t joins the candidate owners once (candidates are rare)
-                owner = true;
-                d.clist[atomicAdd(cnt(ctl, b.ph, C_CLIST), 1)] = t;
+          int fl = tstamp(v.w) == gen8 ? BD_TRI_DIRTY : 0;
+          if (mvd[0] | mvd[1] | mvd[2]) {
+            const int o = flat ? orient_pre(x, isd[0] && isd[1] && isd[2], W[0], W[1], W[2], v.x, v.y, v.z)
+                               : orient_s(x, v.x, tshx<PER>(v.w, 0), tshy<PER>(v.w, 0), v.y, tshx<PER>(v.w, 1),
+                                          tshy<PER>(v.w, 1), v.z, tshx<PER>(v.w, 2), tshy<PER>(v.w, 2));
+            fl = BD_TRI_DIRTY | (o <= 0 ? BD_TRI_INVERTED : 0);
+            if (o <= 0) d.tinv[t] = 1;
+          }
+          const bool inverted = (fl & BD_TRI_INVERTED) != 0;
+          inv += inverted ? 1 : 0;
+          bool owner = false;   // t registered a flip candidate
+          if (inverted && d.rep_stats) {
+            const int rr = tri_rep(d, x.np, v);
+            if (rr >= 0) atomicAdd((unsigned long long *)&d.rep_stats[3 * rr + 2], 1ull);
+          }
+          for (int k = 0; k < 3; ++k) {
+            const int cc = 3 * t + k;
+            const int o = vk(nn, k);
+            // each interior edge once: from its smaller corner, or from this side
+            // when the neighbour is not visited by this pass
+            if (o < 0 || (o <= cc && (full || cmark[o / 3] == gen))) continue;
+            const int ku = (k + 1) % 3, kw = (k + 2) % 3;
+            const int u = vv[ku], w = vv[kw];
+            const bool disks = isd[ku] && isd[kw];
+            const bool mv = (mvd[ku] | mvd[kw]) != 0;
+            // image shift of w relative to u in this triangle (periodic box; 0 with walls)
+            const int rsx = tshx<PER>(v.w, (k + 2) % 3) - tshx<PER>(v.w, (k + 1) % 3);
+            const int rsy = tshy<PER>(v.w, (k + 2) % 3) - tshy<PER>(v.w, (k + 1) % 3);
+            long long LQ = 0;
+            if (rsx | rsy) LQ = rep_LQ(x, u);
+            const bool plain = (rsx | rsy) == 0;   // the edge carries no image shift
+            // r1 = r_w - r_u from the FP32 pairs (unshifted edges)
+            const float r1x = plain ? fdiff(W[kw].x, W[kw].z, W[ku].x, W[ku].z) : 0.f;
+            const float r1y = plain ? fdiff(W[kw].y, W[kw].w, W[ku].y, W[ku].w) : 0.f;
+            if (disks && mv) {
+              // Sec. 4.3 first criterion: r0 . r1 < 0.  An unshifted edge whose
+              // ends did not re-enter is screened in FP32 from r1 and the moves,
+              // as with walls; otherwise, and near zero, exact on the grid (the
+              // edge's shift before the move is the present one less the
+              // re-entries of its end points)
+              int dec = 0;   // 1 reversed, -1 not, 0 undecided
+              if (plain && (wr[ku] | wr[kw]) == 0) {
+                const float2 mu = mvd[ku] ? d.dmove[u] : make_float2(0.f, 0.f);
+                const float2 mw = mvd[kw] ? d.dmove[w] : make_float2(0.f, 0.f);
+                const float r0x = __fsub_rn(r1x, __fsub_rn(mw.x, mu.x)), r0y = __fsub_rn(r1y, __fsub_rn(mw.y, mu.y));
+                const float dot = __fadd_rn(__fmul_rn(r0x, r1x), __fmul_rn(r0y, r1y));
+                const float S = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r0x, r0x), __fmul_rn(r0y, r0y)),
+                                                    __fadd_rn(__fmul_rn(r1x, r1x), __fmul_rn(r1y, r1y))),
+                                          __fadd_rn(__fadd_rn(__fmul_rn(mu.x, mu.x), __fmul_rn(mu.y, mu.y)),
+                                                    __fadd_rn(__fmul_rn(mw.x, mw.x), __fmul_rn(mw.y, mw.y))));
+                const float bound = 4e-6f * S;
+                dec = dot > bound ? -1 : (-dot > bound ? 1 : 0);
+                if (dec == 0) count_exact(x);
+              }
+              int ox = rsx, oy = rsy;
+              if (dec == 0) {
+                ox -= wrapx(wr[kw]) - wrapx(wr[ku]);
+                oy -= wrapy(wr[kw]) - wrapy(wr[ku]);
+                if ((ox | oy) && LQ == 0) LQ = rep_LQ(x, u);
+              }
+              if (dec == 1 || (dec == 0 && reversed_exact(x, u, w, ox, oy, rsx, rsy, LQ))) {
+                ++rej;
+                atomicExch(&ctl->st_fail_item, cc);
               }
             }
-          }
-          if (disks) {
-            // FP32 screen: a pair whose FP32 squared distance exceeds
-            // sigma^2 (1 + 1e-5) is farther than sigma (FP32 error ~3e-7);
-            // edges across a periodic box edge skip it
-            if (plain && __fadd_rn(__fmul_rn(r1x, r1x), __fmul_rn(r1y, r1y)) > x.sig2f) continue;
-            const double2 pu = d.pos[u], pw = d.pos[w];
-            // exact pre-test in grid units: |r_w - r_u|^2 <= (sigma/q)^2 (1 + 1e-9)
-            const int64_t ix = bdpred::to_int(pw.x, x.g) - bdpred::to_int(pu.x, x.g) + rsx * LQ;
-            const int64_t iy = bdpred::to_int(pw.y, x.g) - bdpred::to_int(pu.y, x.g) + rsy * LQ;
-            const bdpred::i128 ir2 = bdpred::add128(bdpred::smul64(ix, ix), bdpred::smul64(iy, iy));
-            const bool near = ir2.hi < c.sig2q_hi || (ir2.hi == c.sig2q_hi && ir2.lo <= c.sig2q_lo);
-            if (near) {
-              // the decision itself as the FP64 reference makes it (the
-              // difference of two grid values is exact in FP64)
-              const double dx = bdem::grid_to_double(ix, x.g.s), dy = bdem::grid_to_double(iy, x.g.s);
-              const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-              const double r = sqrt(r2);
-              const double sg = d.rad ? d.rad[u] + d.rad[w] : sigma;   // polydisperse: a_u + a_w
-              if (r < sg) {
-                const double del = sg - r;
-                const double nx = dx / r, ny = dy / r;
-                disp_add(x, u, -del * nx, -del * ny);
-                disp_add(x, w, del * nx, del * ny);
-                if (use_lists) push_tri(nlist, nmark, ncount, ngen, t);   // checked again in the next pass
-                const int k_ov = atomicAdd(cnt(ctl, b.ph, C_OVERLAP), 1);
-                if (logging) {
-                  if (log_head + k_ov < c.log_pairs_cap) d.log_pairs[log_head + k_ov] = make_int2(u, w);
-                  else atomicExch(&ctl->log_overflow, 1);
-                }
-                mx = fmax(mx, del);
-              }
-            }
-          }
-        }
-      }
-      else
-      for (int it = tid; it < dom_n; it += nth) {
-        // walls: the three corners' FP32 pairs and moved flags are loaded once
-        // and serve the orientation, the reversal and in-circle filters and the
-        // overlap screen of all three edges
-        const int t = full ? it : dom[it];
-        const int4 v = d.tv[t];
-        const int4 nn = d.tn[t];
-        const int vv[3] = {v.x, v.y, v.z};
-        const bool isd[3] = {v.x < x.np, v.y < x.np, v.z < x.np};
-        float4 W[3];
-        uint8_t mvd[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          W[k] = work_of(x, vv[k]);
-          mvd[k] = fresh ? d.moved[vv[k]] : (uint8_t)0;
-        }
-        int fl = tstamp(v.w) == gen8 ? BD_TRI_DIRTY : 0;
-        if (mvd[0] | mvd[1] | mvd[2]) {
-          const int o = orient_pre(x, isd[0] && isd[1] && isd[2], W[0], W[1], W[2], v.x, v.y, v.z);
-          fl = BD_TRI_DIRTY | (o <= 0 ? BD_TRI_INVERTED : 0);
-          if (o <= 0) d.tinv[t] = 1;
-        }
-        const bool inverted = (fl & BD_TRI_INVERTED) != 0;
-        inv += inverted ? 1 : 0;
-        bool owner = false;   // t registered a flip candidate
-        if (inverted && d.rep_stats) {
-          const int rr = tri_rep(d, x.np, v);
-          if (rr >= 0) atomicAdd((unsigned long long *)&d.rep_stats[3 * rr + 2], 1ull);
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int cc = 3 * t + k;
-          const int o = vk(nn, k);
-          // each interior edge once: from its smaller corner, or from this side
-          // when the neighbour is not visited by this pass
-          if (o < 0 || (o <= cc && (full || cmark[o / 3] == gen))) continue;
-          const int ku = (k + 1) % 3, kw = (k + 2) % 3;
-          const int u = vv[ku], w = vv[kw];
-          const bool disks = isd[ku] && isd[kw];
-          // r1 = r_w - r_u from the FP32 pairs (one rounding)
-          const float r1x = fdiff(W[kw].x, W[kw].z, W[ku].x, W[ku].z);
-          const float r1y = fdiff(W[kw].y, W[kw].w, W[ku].y, W[ku].w);
-          if (disks && (mvd[ku] | mvd[kw])) {
-            // Sec. 4.3 first criterion r0 . r1 < 0; r0 = r1 - (move of w - move
-            // of u), screened in FP32, exact on the grid near zero
-            bool rev;
-            {
-              const float2 mu = mvd[ku] ? d.dmove[u] : make_float2(0.f, 0.f);
-              const float2 mw = mvd[kw] ? d.dmove[w] : make_float2(0.f, 0.f);
-              const float r0x = __fsub_rn(r1x, __fsub_rn(mw.x, mu.x)), r0y = __fsub_rn(r1y, __fsub_rn(mw.y, mu.y));
-              // every rounding above is relative (one FP32 rounding of a grid
-              // value or of a sum): the computed dot is within ~8 2^-24 S of
-              // the exact one, S = |r0|^2 + |r1|^2 + |m_u|^2 + |m_w|^2
-              const float dot = __fadd_rn(__fmul_rn(r0x, r1x), __fmul_rn(r0y, r1y));
-              const float S = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r0x, r0x), __fmul_rn(r0y, r0y)),
-                                                  __fadd_rn(__fmul_rn(r1x, r1x), __fmul_rn(r1y, r1y))),
-                                        __fadd_rn(__fadd_rn(__fmul_rn(mu.x, mu.x), __fmul_rn(mu.y, mu.y)),
-                                                  __fadd_rn(__fmul_rn(mw.x, mw.x), __fmul_rn(mw.y, mw.y))));
-              const float bound = 4e-6f * S;
-              if (dot > bound) {
-                rev = false;
-              } else if (-dot > bound) {
-                rev = true;
-              } else {
-                count_exact(x);
-                rev = reversed_exact(x, u, w, 0, 0, 0, 0, 0);
-              }
-            }
-            if (rev) {
-              ++rej;
-              atomicExch(&ctl->st_fail_item, cc);
-            }
-          }
-          if (inverted) continue;   // marks and scan wait for the repair
-          const int4 v1 = d.tv[o / 3];
-          const int q = vk(v1, o % 3);
-          // the edge is tested when a triangle on either side is dirty or one
-          // of its four points moved
-          const bool d1 = (fl & BD_TRI_DIRTY) || tstamp(v1.w) == gen8 || (mvd[ku] | mvd[kw]) ||
-                          (fresh && d.moved[q]);
-          if (d1) {
-            const bool filt = isd[0] && isd[1] && isd[2] && q < x.np;
-            if (incircle_pre(x, filt, W[0], W[1], W[2], work_of(x, q), v.x, v.y, v.z, q) > 0) {
-              claim6(x, t, k, nn, o, claim_key(epoch, cc));
-              ++cand;
-              if (!owner) {   // t joins the candidate owners once (candidates are rare)
-                owner = true;
-                d.clist[atomicAdd(cnt(ctl, b.ph, C_CLIST), 1)] = t;
-              }
-            }
-          }
-          if (disks) {
-            // FP32 screen: a pair whose FP32 squared distance exceeds
-            // sigma^2 (1 + 1e-5) is farther than sigma (FP32 error ~3e-7)
-            if (__fadd_rn(__fmul_rn(r1x, r1x), __fmul_rn(r1y, r1y)) > x.sig2f) continue;
-            const double2 pu = d.pos[u], pw = d.pos[w];
-            // exact pre-test in grid units: |r_w - r_u|^2 <= (sigma/q)^2 (1 + 1e-9)
-            const int64_t ix = bdpred::to_int(pw.x, x.g) - bdpred::to_int(pu.x, x.g);
-            const int64_t iy = bdpred::to_int(pw.y, x.g) - bdpred::to_int(pu.y, x.g);
-            const bdpred::i128 ir2 = bdpred::add128(bdpred::smul64(ix, ix), bdpred::smul64(iy, iy));
-            const bool near = ir2.hi < c.sig2q_hi || (ir2.hi == c.sig2q_hi && ir2.lo <= c.sig2q_lo);
-            if (near) {
-              // the decision itself as the FP64 reference makes it
-              const double dx = bdem::grid_to_double(ix, x.g.s), dy = bdem::grid_to_double(iy, x.g.s);
-              const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-              const double r = sqrt(r2);
-              const double sg = d.rad ? d.rad[u] + d.rad[w] : sigma;   // polydisperse: a_u + a_w
-              if (r < sg) {
-                const double del = sg - r;
-                const double nx = dx / r, ny = dy / r;
-                disp_add(x, u, -del * nx, -del * ny);
-                disp_add(x, w, del * nx, del * ny);
-                if (use_lists) push_tri(nlist, nmark, ncount, ngen, t);   // checked again in the next pass
-                const int k_ov = atomicAdd(cnt(ctl, b.ph, C_OVERLAP), 1);
-                if (logging) {
-                  if (log_head + k_ov < c.log_pairs_cap) d.log_pairs[log_head + k_ov] = make_int2(u, w);
-                  else atomicExch(&ctl->log_overflow, 1);
-                }
-                mx = fmax(mx, del);
-              }
-            }
-          }
-        }
-      }
-      block_add(cnt(ctl, b.ph, C_INV), inv);
-      block_add(cnt(ctl, b.ph, C_REJECT), rej);
-      block_add(cnt(ctl, b.ph, C_CAND), cand);
-      (void)nov;
-      if (mx > 0.0) atomicMax(&ctl->st_max_overlap_bits, (unsigned long long)__double_as_longlong(mx));
-    }
-    if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
-    if (lead) {
-      stage_tick(ctl, full ? STAGE_P : STAGE_PL, t_mark);
-      ctl->act_n[(kp + 2) % 3] = 0;   // filled by the next pass
-    }
-    const int n_inv = bc[BC_CNT + C_INV];
-    const int n_rej = bc[BC_CNT + C_REJECT];
-    const int n_cand = bc[BC_CNT + C_CAND];
-    const int n_ov = bc[BC_CNT + C_OVERLAP];
-    if (n_rej) {
-      status = BD_ERR_STEP_REJECTED;
-      if (lead) { ctl->st_fail_phase = 1; ctl->st_fail_count = n_rej; }
-      break;
-    }
-
-    if (n_inv > 0) {
-      // ---------------- R: inversion repair (this pass's marks and scan are void) ----------------
-      st_inv += n_inv;
-      int rounds = 0;
-      bool first_round = true;
-      for (;;) {
-        ++epoch;
-        phase_begin(ctl, b);
-        {
-          if (first_round) {
-            for (int i = tid; i < x.np; i += nth) d.disp[i] = make_double2(0.0, 0.0);
-            // the check pass skipped the marks (and the pass after the repair
-            // is not fresh): a triangle with a moved corner stays dirty for it
-            for (int t = tid; t < x.T; t += nth) {
-              const int4 v = d.tv[t];
-              if (d.moved[v.x] | d.moved[v.y] | d.moved[v.z]) d.tv[t].w = with_stamp(v.w, ngen8);
-            }
-          }
-          int inv = 0, ncand = 0;
-          for (int t = tid; t < x.T; t += nth) {
-            if (!d.tinv[t]) continue;
-            const int4 v = d.tv[t];
-            ++inv;
-            atomicExch(&ctl->st_fail_item, t);
-            const int4 nn = d.tn[t];
-            for (int k = 0; k < 3; ++k) {
-              const int o = vk(nn, k);
-              if (o < 0) continue;
-              const int p = vk(v, k), u = vk(v, (k + 1) % 3), w = vk(v, (k + 2) % 3);
-              const int4 v1 = d.tv[o / 3];
-              const int q = vk(v1, o % 3);
+            if (inverted) continue;   // marks and scan wait for the repair
+            const int4 v1 = d.tv[o / 3];
+            const int q = vk(v1, o % 3);
+            // the edge is tested when a triangle on either side is dirty or one
+            // of its four points moved
+            const bool d1 = (fl & BD_TRI_DIRTY) || tstamp(v1.w) == gen8 || (mvd[ku] | mvd[kw]) ||
+                            (fresh && d.moved[q]);
+            if (d1) {
               int sqx, sqy;
               opp_shift<PER>(v.w, k, v1.w, o % 3, sqx, sqy);
-              const int spx = tshx<PER>(v.w, k), spy = tshy<PER>(v.w, k);
-              const int sux = tshx<PER>(v.w, (k + 1) % 3), suy = tshy<PER>(v.w, (k + 1) % 3);
-              const int swx = tshx<PER>(v.w, (k + 2) % 3), swy = tshy<PER>(v.w, (k + 2) % 3);
-              // orientation form of Eq. (predicate): both triangles of the
-              // other diagonal strictly counter-clockwise
-              if (orient_s(x, u, sux, suy, q, sqx, sqy, p, spx, spy) > 0 &&
-                  orient_s(x, w, swx, swy, p, spx, spy, q, sqx, sqy) > 0) {
-                const int cm = min(3 * t + k, o);
-                const int tt = cm / 3, kk = cm % 3;
-                const int4 ncm = d.tn[tt];
-                claim6(x, tt, kk, ncm, vk(ncm, kk), claim_key(epoch, cm));
-                ++ncand;
+              const int ic = (flat && (sqx | sqy) == 0)
+                                 ? incircle_pre(x, isd[0] && isd[1] && isd[2] && q < x.np, W[0], W[1], W[2],
+                                                work_of(x, q), v.x, v.y, v.z, q)
+                                 : incircle_s<PER>(x, v, q, sqx, sqy);
+              if (ic > 0) {
+                claim6(x, claims(x, epoch), t, k, nn, o, claim_key(epoch, cc));
+                ++cand;
+                if (!owner) {   // t joins the candidate owners once (candidates are rare)
+                  owner = true;
+                  push_owner(x, epoch, t);
+                }
+              }
+            }
+            if (disks && scan) {
+              // FP32 screen: a pair whose FP32 squared distance exceeds
+              // sigma^2 (1 + 1e-5) is farther than sigma (FP32 error ~3e-7);
+              // edges across a periodic box edge skip it
+              if (plain && __fadd_rn(__fmul_rn(r1x, r1x), __fmul_rn(r1y, r1y)) > x.sig2f) continue;
+              double2 v;
+              double del;
+              if (edge_overlap(x, u, w, rsx, rsy, LQ, v, del)) {
+                disp_add(x, u, -v.x, -v.y);
+                disp_add(x, w, v.x, v.y);
+                if (use_lists) push_tri(nlist, nmark, ncount, ngen, t);   // checked again in the next pass
+                const int k_ov = atomicAdd(cnt(ctl, b.ph, C_OVERLAP), 1);
+                if (logging) {
+                  if (log_head + k_ov < c.log_pairs_cap) d.log_pairs[log_head + k_ov] = make_int2(u, w);
+                  else atomicExch(&ctl->log_overflow, 1);
+                }
+                mx = fmax(mx, del);
               }
             }
           }
-          block_add(cnt(ctl, b.ph, C_INV), inv);
-          block_add(cnt(ctl, b.ph, C_CAND), ncand);
         }
-        if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
-        if (lead) stage_tick(ctl, STAGE_R, t_mark);
-        first_round = false;
-        const int ni = bc[BC_CNT + C_INV];
-        const int nc = bc[BC_CNT + C_CAND];
-        if (ni == 0) break;
-        if (nc == 0 || rounds++ >= c.max_flip_rounds) {
-          status = BD_ERR_STEP_REJECTED;
-          if (lead) { ctl->st_fail_phase = nc == 0 ? 2 : 3; ctl->st_fail_count = ni; }
-          break;
-        }
-        phase_begin(ctl, b);
-        {
-          int nf = 0;
-          for (int t = tid; t < x.T; t += nth) {
-            const unsigned long long key = d.claim[t];
-            if ((key >> 32) != epoch) continue;
-            const int cm = key_corner(key);
-            if (cm / 3 != t) continue;
-            const int4 N0 = d.tn[t];
-            const int o = vk(N0, cm % 3);
-            if (!owns6(x, t, cm % 3, N0, o, key)) continue;
-            flip_owned<PER>(x, cm, o, ngen8);   // both new triangles are counter-clockwise by the rule
-            ++nf;
+        else
+        for (int it = tid; it < dom_n; it += nth) {
+          // walls: the three corners' FP32 pairs and moved flags are loaded once
+          // and serve the orientation, the reversal and in-circle filters and the
+          // overlap screen of all three edges
+          const int t = full ? it : dom[it];
+          const int4 v = d.tv[t];
+          const int4 nn = d.tn[t];
+          const int vv[3] = {v.x, v.y, v.z};
+          const bool isd[3] = {v.x < x.np, v.y < x.np, v.z < x.np};
+          float4 W[3];
+          uint8_t mvd[3];
+  #pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            W[k] = work_of(x, vv[k]);
+            mvd[k] = fresh ? d.moved[vv[k]] : (uint8_t)0;
           }
-          block_add(cnt(ctl, b.ph, C_FLIPS), nf);
+          int fl = tstamp(v.w) == gen8 ? BD_TRI_DIRTY : 0;
+          if (mvd[0] | mvd[1] | mvd[2]) {
+            const int o = orient_pre(x, isd[0] && isd[1] && isd[2], W[0], W[1], W[2], v.x, v.y, v.z);
+            fl = BD_TRI_DIRTY | (o <= 0 ? BD_TRI_INVERTED : 0);
+            if (o <= 0) d.tinv[t] = 1;
+          }
+          const bool inverted = (fl & BD_TRI_INVERTED) != 0;
+          inv += inverted ? 1 : 0;
+          bool owner = false;   // t registered a flip candidate
+          if (inverted && d.rep_stats) {
+            const int rr = tri_rep(d, x.np, v);
+            if (rr >= 0) atomicAdd((unsigned long long *)&d.rep_stats[3 * rr + 2], 1ull);
+          }
+  #pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const int cc = 3 * t + k;
+            const int o = vk(nn, k);
+            // each interior edge once: from its smaller corner, or from this side
+            // when the neighbour is not visited by this pass
+            if (o < 0 || (o <= cc && (full || cmark[o / 3] == gen))) continue;
+            const int ku = (k + 1) % 3, kw = (k + 2) % 3;
+            const int u = vv[ku], w = vv[kw];
+            const bool disks = isd[ku] && isd[kw];
+            // r1 = r_w - r_u from the FP32 pairs (one rounding)
+            const float r1x = fdiff(W[kw].x, W[kw].z, W[ku].x, W[ku].z);
+            const float r1y = fdiff(W[kw].y, W[kw].w, W[ku].y, W[ku].w);
+            if (disks && (mvd[ku] | mvd[kw])) {
+              // Sec. 4.3 first criterion r0 . r1 < 0; r0 = r1 - (move of w - move
+              // of u), screened in FP32, exact on the grid near zero
+              bool rev;
+              {
+                const float2 mu = mvd[ku] ? d.dmove[u] : make_float2(0.f, 0.f);
+                const float2 mw = mvd[kw] ? d.dmove[w] : make_float2(0.f, 0.f);
+                const float r0x = __fsub_rn(r1x, __fsub_rn(mw.x, mu.x)), r0y = __fsub_rn(r1y, __fsub_rn(mw.y, mu.y));
+                // every rounding above is relative (one FP32 rounding of a grid
+                // value or of a sum): the computed dot is within ~8 2^-24 S of
+                // the exact one, S = |r0|^2 + |r1|^2 + |m_u|^2 + |m_w|^2
+                const float dot = __fadd_rn(__fmul_rn(r0x, r1x), __fmul_rn(r0y, r1y));
+                const float S = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r0x, r0x), __fmul_rn(r0y, r0y)),
+                                                    __fadd_rn(__fmul_rn(r1x, r1x), __fmul_rn(r1y, r1y))),
+                                          __fadd_rn(__fadd_rn(__fmul_rn(mu.x, mu.x), __fmul_rn(mu.y, mu.y)),
+                                                    __fadd_rn(__fmul_rn(mw.x, mw.x), __fmul_rn(mw.y, mw.y))));
+                const float bound = 4e-6f * S;
+                if (dot > bound) {
+                  rev = false;
+                } else if (-dot > bound) {
+                  rev = true;
+                } else {
+                  count_exact(x);
+                  rev = reversed_exact(x, u, w, 0, 0, 0, 0, 0);
+                }
+              }
+              if (rev) {
+                ++rej;
+                atomicExch(&ctl->st_fail_item, cc);
+              }
+            }
+            if (inverted) continue;   // marks and scan wait for the repair
+            const int4 v1 = d.tv[o / 3];
+            const int q = vk(v1, o % 3);
+            // the edge is tested when a triangle on either side is dirty or one
+            // of its four points moved
+            const bool d1 = (fl & BD_TRI_DIRTY) || tstamp(v1.w) == gen8 || (mvd[ku] | mvd[kw]) ||
+                            (fresh && d.moved[q]);
+            if (d1) {
+              const bool filt = isd[0] && isd[1] && isd[2] && q < x.np;
+              if (incircle_pre(x, filt, W[0], W[1], W[2], work_of(x, q), v.x, v.y, v.z, q) > 0) {
+                claim6(x, claims(x, epoch), t, k, nn, o, claim_key(epoch, cc));
+                ++cand;
+                if (!owner) {   // t joins the candidate owners once (candidates are rare)
+                  owner = true;
+                  push_owner(x, epoch, t);
+                }
+              }
+            }
+            if (disks && scan) {
+              // FP32 screen: a pair whose FP32 squared distance exceeds
+              // sigma^2 (1 + 1e-5) is farther than sigma (FP32 error ~3e-7)
+              if (__fadd_rn(__fmul_rn(r1x, r1x), __fmul_rn(r1y, r1y)) > x.sig2f) continue;
+              double2 v;
+              double del;
+              if (edge_overlap(x, u, w, 0, 0, 0, v, del)) {
+                disp_add(x, u, -v.x, -v.y);
+                disp_add(x, w, v.x, v.y);
+                if (use_lists) push_tri(nlist, nmark, ncount, ngen, t);   // checked again in the next pass
+                const int k_ov = atomicAdd(cnt(ctl, b.ph, C_OVERLAP), 1);
+                if (logging) {
+                  if (log_head + k_ov < c.log_pairs_cap) d.log_pairs[log_head + k_ov] = make_int2(u, w);
+                  else atomicExch(&ctl->log_overflow, 1);
+                }
+                mx = fmax(mx, del);
+              }
+            }
+          }
         }
-        if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
-        if (lead) stage_tick(ctl, STAGE_R, t_mark);
-        st_rflips += bc[BC_CNT + C_FLIPS];
+        block_add(cnt(ctl, b.ph, C_INV), inv);
+        block_add(cnt(ctl, b.ph, C_REJECT), rej);
+        block_add(cnt(ctl, b.ph, C_CAND), cand);
+        (void)nov;
+        if (mx > 0.0) atomicMax(&ctl->st_max_overlap_bits, (unsigned long long)__double_as_longlong(mx));
       }
-      if (status) break;
-      fresh = false;
-      full = true;   // the repaired region's marks and scan were skipped: check everything
-      ++kp;
-      continue;
+      if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
+      if (lead) stage_tick(ctl, full ? STAGE_P : STAGE_PL, t_mark);
+      const int n_inv = bc[BC_CNT + C_INV];
+      const int n_rej = bc[BC_CNT + C_REJECT];
+      n_ov = bc[BC_CNT + C_OVERLAP];
+      if (n_rej) {
+        status = BD_ERR_STEP_REJECTED;
+        if (lead) { ctl->st_fail_phase = 1; ctl->st_fail_count = n_rej; }
+        break;
+      }
+
+      if (n_inv > 0) {
+        // ---------------- R: inversion repair (this pass's marks and scan are void) ----------------
+        st_inv += n_inv;
+        int rounds = 0;
+        bool first_round = true;
+        for (;;) {
+          ++epoch;
+          if (lead) ctl->cl_n[(epoch + 2) % 3] = 0;   // the candidate list two rounds ahead
+          phase_begin(ctl, b);
+          {
+            if (first_round) {
+              for (int i = tid; i < x.np; i += nth) d.disp[i] = make_double2(0.0, 0.0);
+              // the check pass skipped the marks (and the pass after the repair
+              // is not fresh): a triangle with a moved corner stays dirty for it
+              for (int t = tid; t < x.T; t += nth) {
+                const int4 v = d.tv[t];
+                if (d.moved[v.x] | d.moved[v.y] | d.moved[v.z]) d.tv[t].w = with_stamp(v.w, ngen8);
+              }
+            }
+            int inv = 0, ncand = 0;
+            for (int t = tid; t < x.T; t += nth) {
+              if (!d.tinv[t]) continue;
+              const int4 v = d.tv[t];
+              ++inv;
+              atomicExch(&ctl->st_fail_item, t);
+              const int4 nn = d.tn[t];
+              for (int k = 0; k < 3; ++k) {
+                const int o = vk(nn, k);
+                if (o < 0) continue;
+                const int p = vk(v, k), u = vk(v, (k + 1) % 3), w = vk(v, (k + 2) % 3);
+                const int4 v1 = d.tv[o / 3];
+                const int q = vk(v1, o % 3);
+                int sqx, sqy;
+                opp_shift<PER>(v.w, k, v1.w, o % 3, sqx, sqy);
+                const int spx = tshx<PER>(v.w, k), spy = tshy<PER>(v.w, k);
+                const int sux = tshx<PER>(v.w, (k + 1) % 3), suy = tshy<PER>(v.w, (k + 1) % 3);
+                const int swx = tshx<PER>(v.w, (k + 2) % 3), swy = tshy<PER>(v.w, (k + 2) % 3);
+                // orientation form of Eq. (predicate): both triangles of the
+                // other diagonal strictly counter-clockwise
+                if (orient_s(x, u, sux, suy, q, sqx, sqy, p, spx, spy) > 0 &&
+                    orient_s(x, w, swx, swy, p, spx, spy, q, sqx, sqy) > 0) {
+                  const int cm = min(3 * t + k, o);
+                  const int tt = cm / 3, kk = cm % 3;
+                  const int4 ncm = d.tn[tt];
+                  claim6(x, claims(x, epoch), tt, kk, ncm, vk(ncm, kk), claim_key(epoch, cm));
+                  ++ncand;
+                }
+              }
+            }
+            block_add(cnt(ctl, b.ph, C_INV), inv);
+            block_add(cnt(ctl, b.ph, C_CAND), ncand);
+          }
+          if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
+          if (lead) stage_tick(ctl, STAGE_R, t_mark);
+          first_round = false;
+          const int ni = bc[BC_CNT + C_INV];
+          const int nc = bc[BC_CNT + C_CAND];
+          if (ni == 0) break;
+          if (nc == 0 || rounds++ >= c.max_flip_rounds) {
+            status = BD_ERR_STEP_REJECTED;
+            if (lead) { ctl->st_fail_phase = nc == 0 ? 2 : 3; ctl->st_fail_count = ni; }
+            break;
+          }
+          phase_begin(ctl, b);
+          {
+            int nf = 0;
+            for (int t = tid; t < x.T; t += nth) {
+              const unsigned long long key = claims(x, epoch)[t];
+              if ((key >> 32) != epoch) continue;
+              const int cm = key_corner(key);
+              if (cm / 3 != t) continue;
+              const int4 N0 = d.tn[t];
+              const int o = vk(N0, cm % 3);
+              if (!owns6(x, claims(x, epoch), t, cm % 3, N0, o, key)) continue;
+              flip_owned<PER>(x, cm, o, ngen8);   // both new triangles are counter-clockwise by the rule
+              ++nf;
+            }
+            block_add(cnt(ctl, b.ph, C_FLIPS), nf);
+          }
+          if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
+          if (lead) stage_tick(ctl, STAGE_R, t_mark);
+          st_rflips += bc[BC_CNT + C_FLIPS];
+        }
+        if (status) break;
+        fresh = false;
+        full = true;   // the repaired region's marks and scan were skipped: check everything
+        need_p = scan = true;
+        ++kp;
+        continue;
+      }
+      if (scan) ov_now = n_ov;
     }
 
-    if (n_cand > 0) {
+    // candidates for this round: the marking pass's and those the previous
+    // fused round registered
+    if (bc[BC_CL + (int)(epoch % 3)] > 0) {
       // ---------------- F: owned Lawson flips ----------------
       if (lawson_rounds++ >= c.max_flip_rounds) {
         status = BD_ERR_FLIP_NOT_CONVERGED;
@@ -952,33 +991,89 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       }
       phase_begin(ctl, b);
       {
-        if (n_ov || fresh)
+        const bool voided = !fuse && n_ov;   // unfused: the marking pass's scan is void
+        if (voided || fresh)
           for (int i = tid; i < x.np; i += nth) {
-            if (n_ov) d.disp[i] = make_double2(0.0, 0.0);   // this pass's scan is void
+            if (voided) d.disp[i] = make_double2(0.0, 0.0);
             if (fresh) d.moved[i] = 0;
           }
-        int nf = 0;
-        // the triangles that registered a candidate in the marking pass: each
-        // candidate is owned by the triangle that tested it.  A flip stamps
-        // its two triangles for the next pass; an owner whose flip lost a
-        // claim is stamped too, so its edges are tested again.  Every other
-        // edge the marking pass tested is legal, and keeps its verdict unless
-        // a flip changes it (then a stamped triangle holds it).
-        const int ncl = bc[BC_CNT + C_CLIST];
+        int nf = 0, nlose = 0, adj = 0;
+        double fmx = 0.0;
+        // the triangles that registered a candidate for this round (in the
+        // marking pass, or in the previous fused round): each candidate is
+        // owned by the triangle that tested it.  An owner whose flip lost a
+        // claim is stamped, so its edges are tested again by a check pass.
+        // Unfused, a flip stamps its two triangles for the next pass, and
+        // every other edge the marking pass tested keeps its verdict unless a
+        // flip changes it.  Fused, a flip tests the four outer edges of its
+        // quadrilateral itself -- the six triangles it owns do not change
+        // during the round -- and registers the illegal ones for the next
+        // round (claims of the other parity, the next candidate list); it
+        // also withdraws the overlap of the diagonal it removes and adds that
+        // of the one it draws (exact fixed-point sums), so the sums stay those
+        // of the current triangulation.
+        const int cs = (int)(epoch % 3);
+        const int ncl = bc[BC_CL + cs];
+        const int *cl = d.clist + (size_t)cs * x.T;
+        unsigned long long *cb = claims(x, epoch), *nb = claims(x, epoch + 1);
+        // overlap of the disk-disk diagonal (u, w) of triangle V (w's image
+        // shifted by its corner shifts' difference) added with sign sg
+        auto diag = [&](const int4 &V, int ku, int kw, int sgn) {
+          const int u = vk(V, ku), w = vk(V, kw);
+          if (u >= x.np || w >= x.np) return;
+          const int sx = tshx<PER>(V.w, kw) - tshx<PER>(V.w, ku), sy = tshy<PER>(V.w, kw) - tshy<PER>(V.w, ku);
+          const long long LQ = (sx | sy) ? rep_LQ(x, u) : 0;
+          double2 v;
+          double del;
+          if (!edge_overlap(x, u, w, sx, sy, LQ, v, del)) return;
+          disp_add(x, u, -sgn * v.x, -sgn * v.y);
+          disp_add(x, w, sgn * v.x, sgn * v.y);
+          adj += sgn;
+          if (sgn > 0) fmx = fmax(fmx, del);
+        };
+        // the two outer edges of new triangle tt (corner kk faces the new
+        // diagonal): illegal ones become candidates of the next round
+        auto outer = [&](int tt, int kk) {
+          const int4 V = d.tv[tt], N = d.tn[tt];
+          bool reg = false;
+          for (int j = 1; j <= 2; ++j) {
+            const int k = (kk + j) % 3;
+            const int oo = vk(N, k);
+            if (oo < 0) continue;
+            const int4 v1 = d.tv[oo / 3];
+            const int q = vk(v1, oo % 3);
+            int sqx, sqy;
+            opp_shift<PER>(V.w, k, v1.w, oo % 3, sqx, sqy);
+            if (incircle_s<PER>(x, V, q, sqx, sqy) > 0) {
+              claim6(x, nb, tt, k, N, oo, claim_key(epoch + 1, 3 * tt + k));
+              if (!reg) {
+                reg = true;
+                push_owner(x, epoch + 1, tt);
+              }
+            }
+          }
+        };
         // consecutive entries go to different blocks (a few hundred flips on
         // one SM would queue on its load/store unit)
         for (int it = blockIdx.x + threadIdx.x * gridDim.x; it < ncl; it += nth) {
-          const int t = d.clist[it];
-          const unsigned long long key = d.claim[t];
+          const int t = cl[it];
+          const unsigned long long key = cb[t];
           bool flipped = false;
           if ((key >> 32) == epoch) {
             const int cm = key_corner(key);
             if (cm / 3 == t) {
               const int4 N0 = d.tn[t];
-              const int o = vk(N0, cm % 3);
-              if (owns6(x, t, cm % 3, N0, o, key)) {
-                flip_owned<PER>(x, cm, o, ngen8);
-                if (use_lists) {
+              const int k0 = cm % 3;
+              const int o = vk(N0, k0);
+              if (owns6(x, cb, t, k0, N0, o, key)) {
+                // old t = (a, b, c), new t = (b, d, a), new t1 = (c, a, d)
+                if (fuse) diag(d.tv[t], (k0 + 1) % 3, (k0 + 2) % 3, -1);
+                flip_owned<PER>(x, cm, o, ngen8, !fuse);
+                if (fuse) {
+                  diag(d.tv[t], (k0 + 2) % 3, (k0 + 1) % 3, 1);
+                  outer(t, k0);
+                  outer(o / 3, o % 3);
+                } else if (use_lists) {
                   push_tri(nlist, nmark, ncount, ngen, t);
                   push_tri(nlist, nmark, ncount, ngen, o / 3);
                 }
@@ -996,11 +1091,17 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
             }
           }
           if (!flipped) {
-            d.tv[t].w = with_stamp(d.tv[t].w, ngen8);
+            ++nlose;
+            stamp_tri(x, t, ngen8);
             if (use_lists) push_tri(nlist, nmark, ncount, ngen, t);
           }
         }
         block_add(cnt(ctl, b.ph, C_FLIPS), nf);
+        if (fuse) {
+          block_add(cnt(ctl, b.ph, C_LOSE), nlose);
+          block_add(cnt(ctl, b.ph, C_OVADJ), adj);
+          if (fmx > 0.0) atomicMax(&ctl->st_max_overlap_bits, (unsigned long long)__double_as_longlong(fmx));
+        }
       }
       if (!grid_sync(ctl, b, bc)) { block_exit(ctl); return; }
       if (lead) stage_tick(ctl, STAGE_F, t_mark);
@@ -1008,28 +1109,45 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
       st_rounds += 1;
       fresh = false;
       full = !use_lists;
-      ++kp;
-      continue;
+      if (!fuse) {
+        need_p = scan = true;   // the next pass marks and scans afresh
+        ++kp;
+        continue;
+      }
+      ov_now += bc[BC_CNT + C_OVADJ];
+      if (bc[BC_CNT + C_LOSE] > 0) {
+        need_p = true;          // a pass marks the losers' edges again
+        scan = false;
+        ++kp;
+        continue;
+      }
+      if (bc[BC_CL + (int)((epoch + 1) % 3)] > 0) {
+        need_p = false;         // the next round flips what this one registered
+        ++kp;
+        continue;
+      }
+      // no candidate left: the triangulation is Delaunay
     }
 
-    // Delaunay triangulation of the current positions: the scan is valid
+    // Delaunay triangulation of the current positions: the overlap sums (the
+    // last scan's, kept by the fused rounds) are Algorithm 2's
     if (mode == 1) {
       // new positions set from outside: they must not overlap (the scan of
       // this Delaunay triangulation finds the closest pair)
-      if (n_ov) {
+      if (ov_now) {
         status = BD_ERR_INIT_OVERLAP;
-        if (lead) { ctl->st_fail_phase = 7; ctl->st_fail_count = n_ov; }
+        if (lead) { ctl->st_fail_phase = 7; ctl->st_fail_count = ov_now; }
       }
       break;
     }
-    if (n_ov == 0) break;
+    if (ov_now == 0) break;
     if (corr_iter >= c.max_corr_iters) {
       status = BD_ERR_OVERLAP_NOT_CONVERGED;
       if (lead) ctl->st_fail_phase = 5;
       break;
     }
     ++corr_iter;
-    st_overlap += n_ov;
+    st_overlap += ov_now;
     lawson_rounds = 0;
     if (logging) {
       // commit this pass to the rollout log
@@ -1117,6 +1235,7 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
     if (lead) stage_tick(ctl, STAGE_A, t_mark);
     fresh = true;
     full = !use_lists;
+    need_p = scan = true;
     ++kp;
   }
 

@@ -393,7 +393,9 @@ def test_barrier_timeout_exit(hold):
     st, code = s.step(2, raise_on_error=False)
     assert code == -7 and st["steps_done"] == 0
     _assert_start_kept(s, before)
-    # bd_set_state under the same hold: refused, state kept
+    # bd_set_state under a hold of its first barrier (a repair that finds
+    # little to flip may not reach a later one): refused, state kept
+    s.set_wait_limit(0.05, hold_barrier=1)
     with pytest.raises(bd.BDError) as e:
         s.set_state(before["xy"] + 0.001)
     assert e.value.code == -7
