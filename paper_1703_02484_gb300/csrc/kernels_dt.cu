@@ -378,7 +378,7 @@ __device__ __forceinline__ void unjournal(const BdDev &d, int t) {
 // Quad a-b-d-c with t0 = (a, b, c), t1 = (d, c, b) becomes t0 = (b, d, a),
 // t1 = (c, a, d): the edge bc is replaced by ad.
 template <bool PER>
-__device__ void flip_owned(const Ctx &x, int c0, int o0, uint8_t stamp, bool stamp_pair = true) {
+__device__ void flip_owned(const Ctx &x, int c0, int o0, uint8_t stamp) {
   const int t0 = c0 / 3, k0 = c0 % 3, t1 = o0 / 3, k1 = o0 % 3;
   // the journal marks are loaded with the pair, and the pair's old values
   // journaled after the flip's own stores (they are held in registers)
@@ -423,8 +423,8 @@ __device__ void flip_owned(const Ctx &x, int c0, int o0, uint8_t stamp, bool sta
     }
   }
   // both new triangles: their edges are tested by the next check pass
-  V0.w = stamp_pair ? with_stamp(nw0, stamp) : with_stamp(nw0, tstamp(w0));
-  V1.w = stamp_pair ? with_stamp(nw1, stamp) : with_stamp(nw1, tstamp(w1));
+  V0.w = with_stamp(nw0, stamp);
+  V1.w = with_stamp(nw1, stamp);
   x.d.tv[t0] = V0;
   x.d.tv[t1] = V1;
   x.d.tn[t0] = N0;
@@ -444,20 +444,11 @@ __device__ void flip_owned(const Ctx &x, int c0, int o0, uint8_t stamp, bool sta
   journal(x, t1, oV1, oN1, m1);
 }
 
-// Append triangle t to a list once per generation (a list is visited by one
-// check pass; its generation tags the members).  The lanes of a warp that
-// append together reserve their slots with one atomic on the list length.
-__device__ __forceinline__ void push_tri(int *list, unsigned *mark, int *n, unsigned gen, int t) {
-  const bool add = atomicExch(&mark[t], gen) != gen;
-  const unsigned act = __activemask();
-  const unsigned want = __ballot_sync(act, add);
-  if (!want) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(want) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(n, __popc(want));
-  base = __shfl_sync(act, base, leader);
-  if (add) list[base + __popc(want & ((1u << lane) - 1u))] = t;
+__device__ __forceinline__ unsigned long long claim_key(unsigned long long epoch, int corner) {
+  return (epoch << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)corner);
+}
+__device__ __forceinline__ int key_corner(unsigned long long key) {
+  return (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
 }
 
 // Register triangle t as a candidate owner for the round of epoch e, once:
@@ -481,18 +472,168 @@ __device__ __forceinline__ void stamp_tri(const Ctx &x, int t, uint8_t s) {
   } while (old != seen);
 }
 
+// A fused Lawson round's flip of the edge facing corner c0 (pair and outer
+// neighbours owned).  Its loads are issued by level -- the pair and the
+// journal marks; the four outer neighbours' corner tables and the quad's
+// FP32 pairs; the opposite vertices' FP32 pairs -- before any store.  It
+// withdraws the overlap of diagonal bc, adds that of ad, flips, and tests the
+// four outer edges, registering the illegal ones (claims in nb, keys of
+// epoch ne, owners listed once).  Returns the change in overlapping edges
+// and the depth of an added overlap (0 if none).
+struct FusedOut {
+  int adj;
+  double mx;
+};
+template <bool PER>
+__device__ __forceinline__ FusedOut fused_flip(const Ctx &x, int c0, int o0, unsigned long long *nb,
+                                             unsigned long long ne) {
+  const BdDev &d = x.d;
+  const int t0 = c0 / 3, k0 = c0 % 3, t1 = o0 / 3, k1 = o0 % 3;
+  const unsigned m0 = d.jmark[t0], m1 = d.jmark[t1];
+  const int4 oV0 = d.tv[t0], oV1 = d.tv[t1], oN0 = d.tn[t0], oN1 = d.tn[t1];
+  const int a = vk(oV0, k0), b = vk(oV0, (k0 + 1) % 3), c = vk(oV0, (k0 + 2) % 3), dd = vk(oV1, k1);
+  const int n_ca = vk(oN0, (k0 + 1) % 3), n_ab = vk(oN0, (k0 + 2) % 3);
+  const int n_bd = vk(oN1, (k1 + 1) % 3), n_dc = vk(oN1, (k1 + 2) % 3);
+  // outer edges in the order (t0, facing k0+1), (t0, k0+2), (t1, k1+1), (t1, k1+2)
+  const int nbr[4] = {n_ab, n_bd, n_dc, n_ca};
+  int4 Wn[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) Wn[m] = nbr[m] >= 0 ? d.tv[nbr[m] / 3] : make_int4(0, 0, 0, 0);
+  const float4 Pa = work_of(x, a), Pb = work_of(x, b), Pc = work_of(x, c), Pd = work_of(x, dd);
+  int q[4];
+  float4 Pq[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    q[m] = nbr[m] >= 0 ? vk(Wn[m], nbr[m] % 3) : 0;
+    Pq[m] = nbr[m] >= 0 ? work_of(x, q[m]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  // the new pair: t0 = (b, d, a) at (k0, k0+1, k0+2), t1 = (c, a, d) at (k1, k1+1, k1+2)
+  int4 V0 = oV0, V1 = oV1, N0 = oN0, N1 = oN1;
+  set_vk(V0, k0, b);
+  set_vk(V0, (k0 + 1) % 3, dd);
+  set_vk(V0, (k0 + 2) % 3, a);
+  set_vk(V1, k1, c);
+  set_vk(V1, (k1 + 1) % 3, a);
+  set_vk(V1, (k1 + 2) % 3, dd);
+  set_vk(N0, k0, 3 * t1 + k1);
+  set_vk(N0, (k0 + 1) % 3, n_ab);
+  set_vk(N0, (k0 + 2) % 3, n_bd);
+  set_vk(N1, k1, 3 * t0 + k0);
+  set_vk(N1, (k1 + 1) % 3, n_dc);
+  set_vk(N1, (k1 + 2) % 3, n_ca);
+  const int w0 = oV0.w, w1 = oV1.w;
+  int nw0 = 0, nw1 = 0;
+  int Ax = 0, Ay = 0, Bx = 0, By = 0, Cx = 0, Cy = 0, Dx = 0, Dy = 0;
+  if (PER && ((w0 | w1) & BD_TRI_SHIFT_BITS)) {
+    Ax = shx(w0, k0); Ay = shy(w0, k0);
+    Bx = shx(w0, (k0 + 1) % 3); By = shy(w0, (k0 + 1) % 3);
+    Cx = shx(w0, (k0 + 2) % 3); Cy = shy(w0, (k0 + 2) % 3);
+    Dx = shx(w1, k1) + Bx - shx(w1, (k1 + 2) % 3); Dy = shy(w1, k1) + By - shy(w1, (k1 + 2) % 3);
+    int sx0[3], sy0[3], sx1[3], sy1[3];
+    sx0[k0] = Bx; sy0[k0] = By;
+    sx0[(k0 + 1) % 3] = Dx; sy0[(k0 + 1) % 3] = Dy;
+    sx0[(k0 + 2) % 3] = Ax; sy0[(k0 + 2) % 3] = Ay;
+    sx1[k1] = Cx; sy1[k1] = Cy;
+    sx1[(k1 + 1) % 3] = Ax; sy1[(k1 + 1) % 3] = Ay;
+    sx1[(k1 + 2) % 3] = Dx; sy1[(k1 + 2) % 3] = Dy;
+    for (int k = 0; k < 3; ++k) {
+      nw0 |= put_shift(k, sx0[k] - sx0[0], sy0[k] - sy0[0]);
+      nw1 |= put_shift(k, sx1[k] - sx1[0], sy1[k] - sy1[0]);
+    }
+  }
+  V0.w = with_stamp(nw0, tstamp(w0));
+  V1.w = with_stamp(nw1, tstamp(w1));
+  // overlaps of the old and the new diagonal (a shifted edge takes the exact
+  // test directly; a plain one is screened in FP32 first, as in a check pass)
+  FusedOut r = {0, 0.0};
+  auto diag = [&](int u, int w, const float4 &Pu, const float4 &Pw, int sx, int sy, int sgn) {
+    if (u >= x.np || w >= x.np) return;
+    if ((sx | sy) == 0) {
+      const float fx = fdiff(Pw.x, Pw.z, Pu.x, Pu.z), fy = fdiff(Pw.y, Pw.w, Pu.y, Pu.w);
+      if (__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)) > x.sig2f) return;
+    }
+    const long long LQ = (sx | sy) ? rep_LQ(x, u) : 0;
+    double2 v;
+    double del;
+    if (!edge_overlap(x, u, w, sx, sy, LQ, v, del)) return;
+    disp_add(x, u, -sgn * v.x, -sgn * v.y);
+    disp_add(x, w, sgn * v.x, sgn * v.y);
+    r.adj += sgn;
+    if (sgn > 0) r.mx = fmax(r.mx, del);
+  };
+  diag(b, c, Pb, Pc, Cx - Bx, Cy - By, -1);
+  diag(a, dd, Pa, Pd, Dx - Ax, Dy - Ay, 1);
+  // the flip
+  d.tv[t0] = V0;
+  d.tv[t1] = V1;
+  d.tn[t0] = N0;
+  d.tn[t1] = N1;
+  d.tinv[t0] = 0;
+  d.tinv[t1] = 0;
+  d.vt[b] = 3 * t0 + k0;
+  d.vt[dd] = 3 * t0 + (k0 + 1) % 3;
+  d.vt[a] = 3 * t0 + (k0 + 2) % 3;
+  d.vt[c] = 3 * t1 + k1;
+  if (n_ab >= 0) ((int *)&d.tn[n_ab / 3])[n_ab % 3] = 3 * t0 + (k0 + 1) % 3;
+  if (n_bd >= 0) ((int *)&d.tn[n_bd / 3])[n_bd % 3] = 3 * t0 + (k0 + 2) % 3;
+  if (n_dc >= 0) ((int *)&d.tn[n_dc / 3])[n_dc % 3] = 3 * t1 + (k1 + 1) % 3;
+  if (n_ca >= 0) ((int *)&d.tn[n_ca / 3])[n_ca % 3] = 3 * t1 + (k1 + 2) % 3;
+  journal(x, t0, oV0, oN0, m0);
+  journal(x, t1, oV1, oN1, m1);
+  // the four outer edges: the opposite vertex inside the new triangle's
+  // circumcircle makes the edge illegal (a candidate of the next round)
+  float4 W0[3], W1[3];
+  W0[k0] = Pb; W0[(k0 + 1) % 3] = Pd; W0[(k0 + 2) % 3] = Pa;
+  W1[k1] = Pc; W1[(k1 + 1) % 3] = Pa; W1[(k1 + 2) % 3] = Pd;
+  bool reg0 = false, reg1 = false;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    if (nbr[m] < 0) continue;
+    const bool first = m < 2;
+    const int tt = first ? t0 : t1, kt = first ? k0 : k1;
+    const int k = (kt + 1 + (m & 1)) % 3;
+    const int4 &V = first ? V0 : V1;
+    const float4 *Wt = first ? W0 : W1;
+    int sqx, sqy;
+    opp_shift<PER>(V.w, k, Wn[m].w, nbr[m] % 3, sqx, sqy);
+    const bool flat = (V.w & BD_TRI_SHIFT_BITS) == 0 && (sqx | sqy) == 0;
+    const int ic = flat ? incircle_pre(x, V.x < x.np && V.y < x.np && V.z < x.np && q[m] < x.np, Wt[0], Wt[1],
+                                       Wt[2], Pq[m], V.x, V.y, V.z, q[m])
+                        : incircle_s<PER>(x, V, q[m], sqx, sqy);
+    if (ic > 0) {
+      claim6(x, nb, tt, k, first ? N0 : N1, nbr[m], claim_key(ne, 3 * tt + k));
+      bool &reg = first ? reg0 : reg1;
+      if (!reg) {
+        reg = true;
+        push_owner(x, ne, tt);
+      }
+    }
+  }
+  return r;
+}
+
+// Append triangle t to a list once per generation (a list is visited by one
+// check pass; its generation tags the members).  The lanes of a warp that
+// append together reserve their slots with one atomic on the list length.
+__device__ __forceinline__ void push_tri(int *list, unsigned *mark, int *n, unsigned gen, int t) {
+  const bool add = atomicExch(&mark[t], gen) != gen;
+  const unsigned act = __activemask();
+  const unsigned want = __ballot_sync(act, add);
+  if (!want) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(want) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(n, __popc(want));
+  base = __shfl_sync(act, base, leader);
+  if (add) list[base + __popc(want & ((1u << lane) - 1u))] = t;
+}
+
 // the replica of a triangle (its first disk corner; -1 if it has none)
 __device__ __forceinline__ int tri_rep(const BdDev &d, int np, const int4 &v) {
   const int c = v.x < np ? v.x : (v.y < np ? v.y : (v.z < np ? v.z : -1));
   return c < 0 ? -1 : d.rep_of[c];
 }
 
-__device__ __forceinline__ unsigned long long claim_key(unsigned long long epoch, int corner) {
-  return (epoch << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)corner);
-}
-__device__ __forceinline__ int key_corner(unsigned long long key) {
-  return (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
-}
 
 }  // namespace
 
@@ -1016,43 +1157,6 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
         const int ncl = bc[BC_CL + cs];
         const int *cl = d.clist + (size_t)cs * x.T;
         unsigned long long *cb = claims(x, epoch), *nb = claims(x, epoch + 1);
-        // overlap of the disk-disk diagonal (u, w) of triangle V (w's image
-        // shifted by its corner shifts' difference) added with sign sg
-        auto diag = [&](const int4 &V, int ku, int kw, int sgn) {
-          const int u = vk(V, ku), w = vk(V, kw);
-          if (u >= x.np || w >= x.np) return;
-          const int sx = tshx<PER>(V.w, kw) - tshx<PER>(V.w, ku), sy = tshy<PER>(V.w, kw) - tshy<PER>(V.w, ku);
-          const long long LQ = (sx | sy) ? rep_LQ(x, u) : 0;
-          double2 v;
-          double del;
-          if (!edge_overlap(x, u, w, sx, sy, LQ, v, del)) return;
-          disp_add(x, u, -sgn * v.x, -sgn * v.y);
-          disp_add(x, w, sgn * v.x, sgn * v.y);
-          adj += sgn;
-          if (sgn > 0) fmx = fmax(fmx, del);
-        };
-        // the two outer edges of new triangle tt (corner kk faces the new
-        // diagonal): illegal ones become candidates of the next round
-        auto outer = [&](int tt, int kk) {
-          const int4 V = d.tv[tt], N = d.tn[tt];
-          bool reg = false;
-          for (int j = 1; j <= 2; ++j) {
-            const int k = (kk + j) % 3;
-            const int oo = vk(N, k);
-            if (oo < 0) continue;
-            const int4 v1 = d.tv[oo / 3];
-            const int q = vk(v1, oo % 3);
-            int sqx, sqy;
-            opp_shift<PER>(V.w, k, v1.w, oo % 3, sqx, sqy);
-            if (incircle_s<PER>(x, V, q, sqx, sqy) > 0) {
-              claim6(x, nb, tt, k, N, oo, claim_key(epoch + 1, 3 * tt + k));
-              if (!reg) {
-                reg = true;
-                push_owner(x, epoch + 1, tt);
-              }
-            }
-          }
-        };
         // consecutive entries go to different blocks (a few hundred flips on
         // one SM would queue on its load/store unit)
         for (int it = blockIdx.x + threadIdx.x * gridDim.x; it < ncl; it += nth) {
@@ -1066,14 +1170,14 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
               const int k0 = cm % 3;
               const int o = vk(N0, k0);
               if (owns6(x, cb, t, k0, N0, o, key)) {
-                // old t = (a, b, c), new t = (b, d, a), new t1 = (c, a, d)
-                if (fuse) diag(d.tv[t], (k0 + 1) % 3, (k0 + 2) % 3, -1);
-                flip_owned<PER>(x, cm, o, ngen8, !fuse);
                 if (fuse) {
-                  diag(d.tv[t], (k0 + 2) % 3, (k0 + 1) % 3, 1);
-                  outer(t, k0);
-                  outer(o / 3, o % 3);
-                } else if (use_lists) {
+                  const FusedOut fo = fused_flip<PER>(x, cm, o, nb, epoch + 1);
+                  adj += fo.adj;
+                  fmx = fmax(fmx, fo.mx);
+                } else {
+                  flip_owned<PER>(x, cm, o, ngen8);
+                }
+                if (!fuse && use_lists) {
                   push_tri(nlist, nmark, ncount, ngen, t);
                   push_tri(nlist, nmark, ncount, ngen, o / 3);
                 }
