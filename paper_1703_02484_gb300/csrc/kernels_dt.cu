@@ -13,12 +13,17 @@
 //   F  Lawson flips (Sec. 4.1, Navarro et al.): an edge whose opposite vertex
 //      lies strictly inside the circumcircle of the other triangle is flipped;
 //      rounds repeat until none is left.  Only edges touching a triangle that
-//      moved or flipped are re-tested.
+//      moved or flipped are re-tested: by the flip itself, which tests the
+//      four outer edges of its quadrilateral and registers the illegal ones
+//      for the next round (fused rounds), or by a check pass after the round.
 //   A  overlap correction (Algorithm 2): every real edge with r < sigma adds
 //      -+ (sigma - r) r_hat to its end points' displacement (fixed-point
 //      integer atomics: the sums do not depend on the order); each
 //      disk then moves by its sum capped at sigma/4 (Sec. 4.4) and reflects at
-//      the walls.  Then P-R-F run again on the moved disks, and the loop ends
+//      the walls.  The sums are those of the scan of P, kept through fused
+//      Lawson rounds (a flip withdraws the contribution of the diagonal it
+//      removes and adds that of the one it draws).  Then P-R-F run again on
+//      the moved disks, and the loop ends
 //      when a pass over the Delaunay edges of the current positions finds no
 //      overlap (the closest pair of a point set is a Delaunay edge, so no pair
 //      anywhere is closer than sigma).
@@ -652,7 +657,9 @@ __device__ __forceinline__ int tri_rep(const BdDev &d, int np, const int4 &v) {
 //      scanned is the Delaunay triangulation of the current positions.
 //   R  inversion repair rounds (candidate marks, owned flips) when P found an
 //      inverted triangle; then P again.
-//   F  owned Lawson flips of the marked edges; then P again.
+//   F  owned Lawson flips of the marked edges; fused: the next round at once
+//      with the candidates its flips registered, or, if a candidate lost a
+//      claim, P marking without a scan; unfused: P again.
 //   A  apply the capped displacements (Algorithm 2) and reflect; then P again.
 // Three resident blocks per SM (at most 80 registers): the passes are
 // latency-bound chains of dependent loads, and the spills this costs sit in
