@@ -1654,8 +1654,8 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(d.theta0, d.theta, (size_t)np * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d.xfer_xy, xy, (size_t)h->n * sizeof(double2), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && theta) e = cudaMemcpyAsync(d.xfer_th, theta, (size_t)h->n * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.moved, 0, (size_t)np, st);
   if (e == cudaSuccess) e = bd_launch_state_in(d, c, theta ? 1 : 0, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.moved, 1, (size_t)np, st);
   // periodic box: a new coordinate across an edge from the old one re-entered
   if (e == cudaSuccess && c.any_periodic) e = bd_launch_periodic_wraps(d, c, st);
   if (e == cudaSuccess) e = bd_launch_work_copy(d, c, st);

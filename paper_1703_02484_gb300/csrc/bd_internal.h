@@ -67,6 +67,7 @@ struct BdCtl {
   long long st_barriers;           // grid barriers passed by the triangulation kernel
   int st_fail_item;                // an offending triangle (repair) or edge corner (reversal)
   int st_fail_count;               // inverted triangles / reversed edges at the failure
+  int n_set_moved;                 // disks that bd_set_state moved (its repair runs only if any)
   // wall time of the triangulation kernel's stages as its lead thread sees
   // them (each stage's work plus its closing grid barrier): P check/mark/scan,
   // R inversion repair, F Lawson flips, A apply corrections

@@ -679,7 +679,8 @@ __global__ void __launch_bounds__(BD_DT_THREADS, 3) k_triangulation(BdDev d, BdC
   x.np = c.np;
   x.sig2f = (float)(c.sigma * c.sigma * (1.0 + 1e-5));
   BdCtl *ctl = d.ctl;
-  if (ld_status(&ctl->status) != 0) {
+  if (ld_status(&ctl->status) != 0 || (mode == 1 && *(volatile const int *)&ctl->n_set_moved == 0)) {
+    // (bd_set_state that moved no disk: the triangulation stands as it was)
     block_exit(ctl);
     return;
   }

@@ -80,6 +80,12 @@ __global__ void k_state_in(BdDev d, BdConst c, int with_theta) {
       my = my > h ? my - R.LQ : (my < -h ? my + R.LQ : my);
     }
     d.dmove[i] = make_float2(bdem::grid_to_float(mx, c.qshift), bdem::grid_to_float(my, c.qshift));
+    // only disks that moved mark their triangles for the repair; a state
+    // set back unchanged needs none
+    const bool changed = (mx | my) != 0;
+    d.moved[i] = changed ? 1 : 0;
+    const unsigned m = __ballot_sync(__activemask(), changed);
+    if (m && (int)(threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&d.ctl->n_set_moved, __popc(m));
   }
   d.pos[i] = y;
   if (with_theta) d.theta[i] = d.xfer_th[e];
