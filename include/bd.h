@@ -380,7 +380,9 @@ int bd_get_state(bd_handle *h, double *xy, float *theta, uint8_t *species, int32
  * than skin/2 from where they were built).  The arrays are copied to the device as they
  * are (page-locked arrays make it a direct transfer); the range checks (finite;
  * with walls a centre in [a, L-a] up to 1e-9 L), the rounding to the position
- * grid and the permutation to the internal order run there.  The call
+ * grid and the permutation to the internal order run there.  Only disks
+ * whose grid position changed count as moved: the repair re-tests their
+ * triangles, and a state set back unchanged needs no repair.  The call
  * returns when the new state is in place and checked.
  * Errors: BD_ERR_ARG, BD_ERR_INIT_OVERLAP (a centre outside the box, or a
  * pair closer than sigma; state unchanged), BD_ERR_STEP_REJECTED (repair
