@@ -150,6 +150,8 @@ void make_items(bd_handle *h, int tiles, std::vector<int4> &items, int &max_chun
     const int nt_r = R.tile_end - R.tile_begin;
     int nch = std::max(1, (nt_r + tiles - 1) / tiles);
     if (!h->fpart_cap.empty()) nch = std::min(nch, h->fpart_cap[r]);
+    // the FP64 sweep walks its chunk's slots, not the items: all its slots
+    if (h->c.precision == 1 && !h->fpart_cap.empty()) nch = h->fpart_cap[r];
     B.nchunk = nch;
     max_chunk = std::max(max_chunk, nch);
     for (int ib = 0; ib < R.n_iblocks; ++ib)
@@ -884,13 +886,19 @@ int build_handle(const std::vector<Spec> &specs, void *stream, bd_handle **out) 
     BD_TRY(dalloc(h, &d.ctl, 1));
     BD_TRY(dalloc(h, &h->d_fsum, (size_t)np));
     BD_TRY(cudaMallocHost((void **)&h->h_ctl, sizeof(BdCtl)));
-    // partial-force slots: enough for the finest chunking tried (at most 64)
+    // partial-force slots: enough for the finest chunking tried (at most 64).
+    // The FP64 sweep (one disk per thread) cuts j ranges finer than tiles:
+    // into enough chunks for about four blocks per SM
     {
-      int slots = 1;
+      int slots = 1, sms = 148, dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int f64_want = (4 * sms + (np + 127) / 128 - 1) / std::max(1, (np + 127) / 128);
       h->fpart_cap.assign(R, 1);
       for (int r = 0; r < R; ++r) {
         const int nt_r = h->reps[r].tile_end - h->reps[r].tile_begin;
-        const int cap = h->reps[r].p.law == BD_LAW_LONG ? std::min(64, std::max(1, nt_r)) : 1;
+        const int want = c.precision == 1 ? std::max(nt_r, f64_want) : nt_r;
+        const int cap = h->reps[r].p.law == BD_LAW_LONG ? std::min(64, std::max(1, want)) : 1;
         h->fpart_cap[r] = cap;
         slots = std::max(slots, cap);
       }
