@@ -1644,7 +1644,6 @@ int bd_get_replica(bd_handle *h, int32_t r, double *xy, float *theta, int32_t *t
 
 int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
   if (!h || !xy) return BD_ERR_ARG;
-  const int np = h->np;
   const BdConst &c = h->c;
   // The caller's arrays are copied as they are; the range checks, the
   // rounding to the grid and the permutation to slot order run on the device
@@ -1656,17 +1655,14 @@ int bd_set_state(bd_handle *h, const double *xy, const float *theta) {
   // in place.
   cudaStream_t st = h->stream;
   const BdDev &d = h->d;
+  // k_state_check also snapshots pos, prev and theta and clears the moved
+  // flags; k_state_in also writes the FP32 copy of what it stores
   cudaError_t e = reset_stats(h);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d.pos0, d.pos, (size_t)np * sizeof(double2), cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d.prev, d.pos, (size_t)np * sizeof(double2), cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d.theta0, d.theta, (size_t)np * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d.xfer_xy, xy, (size_t)h->n * sizeof(double2), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && theta) e = cudaMemcpyAsync(d.xfer_th, theta, (size_t)h->n * sizeof(float), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.moved, 0, (size_t)np, st);
   if (e == cudaSuccess) e = bd_launch_state_in(d, c, theta ? 1 : 0, st);
   // periodic box: a new coordinate across an edge from the old one re-entered
   if (e == cudaSuccess && c.any_periodic) e = bd_launch_periodic_wraps(d, c, st);
-  if (e == cudaSuccess) e = bd_launch_work_copy(d, c, st);
   if (e == cudaSuccess && !c.overlap_verlet) e = bd_launch_dt(d, c, 1, st, h->dt_grid, h->dt_block);
   if (e == cudaSuccess && c.overlap_verlet) {
     e = bd_launch_force_short(d, c, st);

@@ -30,10 +30,17 @@ __device__ __forceinline__ double periodic_grid(double v, double L, const BdCons
 }
 
 // a centre must be finite and, with walls, lie in [a, L - a] up to 1e-9 L
-// (a_i for polydisperse disks)
+// (a_i for polydisperse disks).  Every slot first takes its snapshots (the
+// start of the repair, and what a failed repair restores) and clears its
+// moved flag.
 __global__ void k_state_check(BdDev d, BdConst c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= c.np) return;
+  const double2 o = d.pos[i];
+  d.pos0[i] = o;
+  d.prev[i] = o;
+  d.theta0[i] = d.theta[i];
+  d.moved[i] = 0;
   const int e = d.ext_glob[i];
   if (e < 0) return;
   const BdRep &R = d.rep[d.rep_of[i]];
@@ -88,6 +95,7 @@ __global__ void k_state_in(BdDev d, BdConst c, int with_theta) {
     if (m && (int)(threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&d.ctl->n_set_moved, __popc(m));
   }
   d.pos[i] = y;
+  d.work[i] = bdem::split(y);   // the FP32 (hi, lo) copy the sweeps and filters read
   if (with_theta) d.theta[i] = d.xfer_th[e];
 }
 
