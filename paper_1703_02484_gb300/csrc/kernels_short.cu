@@ -56,11 +56,13 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
   return {h, __fsub_rn(lo, __fsub_rn(h, s.hi))};
 }
 __device__ __forceinline__ ff ff_scale(ff a, float b) { return ff_mul(a, {b, 0.f}); }
-// a / b: FP32 quotient refined by one float-float residual step
-__device__ __forceinline__ ff ff_div(ff a, ff b) {
-  float q1 = __fdiv_rn(a.hi, b.hi);
+// a / b given rb, 1 / b.hi to within a few ulps (the fast FP32 reciprocal):
+// the FP32 quotient a.hi rb (relative error ~2^-22) refined by one
+// float-float residual step, which leaves ~2^-44 relative error
+__device__ __forceinline__ ff ff_div_r(ff a, ff b, float rb) {
+  float q1 = __fmul_rn(a.hi, rb);
   ff r = ff_add(a, ff_scale(b, -q1));
-  float q2 = __fdiv_rn(r.hi, b.hi);
+  float q2 = __fmul_rn(r.hi, rb);
   float s = __fadd_rn(q1, q2);
   return {s, __fsub_rn(q2, __fsub_rn(s, q1))};
 }
@@ -409,10 +411,13 @@ __global__ void __launch_bounds__(256, 3) k_force_verlet(BdDev d, BdConst c) {
         ff ex = ff_make(hx, lx);
         ff ey = ff_make(hy, ly);
         ff q2 = ff_add(ff_mul(ex, ex), ff_mul(ey, ey));
-        ff s2 = ff_div({s2h, s2l}, q2);   // s^2 as a float-float pair
+        // 1 / r^2 once (one fast reciprocal, one residual step), then products
+        const ff iq2 = ff_div_r({1.0f, 0.f}, q2, __fdividef(1.0f, q2.hi));
+        ff s2 = ff_mul({s2h, s2l}, iq2);   // (s / r)^2 as a float-float pair
         ff s6 = ff_mul(ff_mul(s2, s2), s2);
-        ff t = ff_add(ff_scale(ff_mul(s6, s6), 2.0f), {-s6.hi, -s6.lo});
-        ff cw = ff_div(ff_scale(t, 24.0f * eps), q2);
+        ff s12 = ff_mul(s6, s6);
+        ff t = ff_add({2.0f * s12.hi, 2.0f * s12.lo}, {-s6.hi, -s6.lo});   // exact doubling
+        ff cw = ff_mul(ff_scale(t, 24.0f * eps), iq2);
         gx = ff_add(gx, ff_mul(cw, ex));
         gy = ff_add(gy, ff_mul(cw, ey));
       }
