@@ -29,10 +29,14 @@ import numpy as np  # noqa: E402
 METRIC = "particle-steps/s at N=1e5 (all-pairs + Delaunay repair)"
 UNIT = "particle-steps/s"
 WORKLOAD = "n1e5: N=100000 two-species ABP disks, rho=0.30, all-pairs 1/r^2 non-reciprocal, Delaunay overlap correction"
-FLOPS_PER_PAIR = 12      # 2 FADD + 2 FFMA(r^2) + 2 FMUL(s^3) + 2 FFMA(accumulate), FMA = 2 flops
-FP32_INST_PER_PAIR = 8   # the same work counted as FP32-pipe instructions (plus 1 MUFU rsqrt)
-# symmetric sweep: per unordered pair 2 FADD + 2 FFMA + 2 FMUL + 4 FFMA (both
-# sides) = 16 flops in 10 FP32 lane operations (+1 MUFU), i.e. per ordered pair:
+# algorithmic work of the all-pairs force per ordered pair (the count the
+# roofline's `achieved` uses for every sweep): 2 FADD + 2 FFMA (r^2) + 2 FMUL
+# (s^3) + 2 FFMA (accumulate) = 12 flops (FMA = 2) + 1 MUFU rsqrt
+FLOPS_PER_PAIR = 12
+FP32_INST_PER_PAIR = 8   # the same work counted as FP32-pipe instructions
+# work each sweep executes (frac_executed, fp32_pipe_frac).  Symmetric sweep:
+# per unordered pair 2 FADD + 2 FFMA + 2 FMUL + 4 FFMA (both sides) = 16 flops
+# in 10 FP32 lane operations (+1 MUFU), i.e. per ordered pair:
 FLOPS_PER_PAIR_SYM = 8
 LANES_PER_PAIR_SYM = 5
 # one-sided periodic sweep: per ordered pair 2 hi + 2 lo differences and 2 adds
@@ -568,12 +572,15 @@ def main():
         avg_force_s = float("nan")
     tune = system.tuning()
     variant = tune["variant"]
-    # algorithmic FP32 work of the chosen sweep, per ordered pair interaction
+    # FP32 work the chosen sweep executes, per ordered pair interaction
     flops_pp, lanes_pp = (FLOPS_PER_PAIR_SYM, LANES_PER_PAIR_SYM) if variant >= 2 else \
         (FLOPS_PER_PAIR, FP32_INST_PER_PAIR)
     if periodic_mode and variant < 2:
         flops_pp, lanes_pp = FLOPS_PER_PAIR_PER, LANES_PER_PAIR_PER
-    achieved = flops_pp * pairs / avg_force_s / 1e12
+    # achieved: the algorithmic count (12 flops per ordered pair over N(N-1)
+    # pairs, whatever the sweep executes); frac_executed: the sweep's own flops
+    achieved = FLOPS_PER_PAIR * pairs / avg_force_s / 1e12
+    executed = flops_pp * pairs / avg_force_s / 1e12
     pipe_frac = lanes_pp * pairs / avg_force_s / (sms * 128 * f_hz)
     kernel = {0: "k_force_long_f32", 1: "k_force_long_f32x2<4>",
               2: "k_force_long_sym<4,2> + k_force_sym_reduce",
@@ -632,12 +639,15 @@ def main():
             "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
                          "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                          "traffic": traffic, "fp32_pipe_frac": pipe_frac,
+                         "frac_executed": executed / peak_tflops,
                          "pair_interactions_per_s": pairs / avg_force_s,
                          "avg_launch_ms": avg_force_s * 1e3,
-                         "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s max clock); "
-                                      "flops counted per ordered pair: %d (%d FP32 lane ops), so frac "
-                                      "is capped at %.2f" % (sms, f_hz / 1e6, pk_kind, flops_pp, lanes_pp,
-                                                              flops_pp / (2.0 * lanes_pp))},
+                         "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s max clock); achieved "
+                                      "counts the algorithmic %d flops per ordered pair over N(N-1) pairs; "
+                                      "the sweep executes %d flops in %d FP32 lane ops per ordered pair "
+                                      "(frac_executed, capped at %.2f), so frac is capped at %.2f"
+                                      % (sms, f_hz / 1e6, pk_kind, FLOPS_PER_PAIR, flops_pp, lanes_pp,
+                                         flops_pp / (2.0 * lanes_pp), FLOPS_PER_PAIR / (2.0 * lanes_pp))},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
         }
         if args.workload != "n1e5":
