@@ -218,6 +218,43 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def force_kernel_name(variant, periodic):
+    """The all-pairs sweep (and its reduction) the autotuner's variant runs."""
+    kernel = {0: "k_force_long_f32", 1: "k_force_long_f32x2<4>",
+              2: "k_force_long_sym<4,2> + k_force_sym_reduce",
+              3: "k_force_long_sym<2,4> + k_force_sym_reduce"}[variant]
+    if periodic:
+        kernel = "k_force_long_per" if variant < 2 else kernel.replace("> +", ", periodic> +")
+    return kernel
+
+
+def force_roofline(N, avg_force_s, variant, periodic, sms, f_hz, pk_kind, traffic=None):
+    """FP32 roofline of the all-pairs force evaluation: achieved = the
+    algorithmic 12 flops per ordered pair over N(N-1) pairs per launch time;
+    frac_executed and fp32_pipe_frac from the flops and lane operations the
+    chosen sweep executes per ordered pair."""
+    peak_tflops = sms * 128 * 2 * f_hz / 1e12
+    pairs = N * (N - 1)
+    flops_pp, lanes_pp = (FLOPS_PER_PAIR_SYM, LANES_PER_PAIR_SYM) if variant >= 2 else \
+        (FLOPS_PER_PAIR, FP32_INST_PER_PAIR)
+    if periodic and variant < 2:
+        flops_pp, lanes_pp = FLOPS_PER_PAIR_PER, LANES_PER_PAIR_PER
+    achieved = FLOPS_PER_PAIR * pairs / avg_force_s / 1e12
+    executed = flops_pp * pairs / avg_force_s / 1e12
+    return {"bound": "alu", "kernel": force_kernel_name(variant, periodic), "achieved": achieved,
+            "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+            "traffic": traffic, "fp32_pipe_frac": lanes_pp * pairs / avg_force_s / (sms * 128 * f_hz),
+            "frac_executed": executed / peak_tflops,
+            "pair_interactions_per_s": pairs / avg_force_s,
+            "avg_launch_ms": avg_force_s * 1e3,
+            "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s max clock); achieved "
+                         "counts the algorithmic %d flops per ordered pair over N(N-1) pairs; "
+                         "the sweep executes %d flops in %d FP32 lane ops per ordered pair "
+                         "(frac_executed, capped at %.2f), so frac is capped at %.2f"
+                         % (sms, f_hz / 1e6, pk_kind, FLOPS_PER_PAIR, flops_pp, lanes_pp,
+                            flops_pp / (2.0 * lanes_pp), FLOPS_PER_PAIR / (2.0 * lanes_pp))}
+
+
 def correction_roofline(system, stage_raw, steps, N, verlet_mode, pk, pk_kind, visits=None, flips=0.0):
     """HBM roofline of the per-step correction kernel of the short-range path.
 
@@ -572,21 +609,7 @@ def main():
         avg_force_s = float("nan")
     tune = system.tuning()
     variant = tune["variant"]
-    # FP32 work the chosen sweep executes, per ordered pair interaction
-    flops_pp, lanes_pp = (FLOPS_PER_PAIR_SYM, LANES_PER_PAIR_SYM) if variant >= 2 else \
-        (FLOPS_PER_PAIR, FP32_INST_PER_PAIR)
-    if periodic_mode and variant < 2:
-        flops_pp, lanes_pp = FLOPS_PER_PAIR_PER, LANES_PER_PAIR_PER
-    # achieved: the algorithmic count (12 flops per ordered pair over N(N-1)
-    # pairs, whatever the sweep executes); frac_executed: the sweep's own flops
-    achieved = FLOPS_PER_PAIR * pairs / avg_force_s / 1e12
-    executed = flops_pp * pairs / avg_force_s / 1e12
-    pipe_frac = lanes_pp * pairs / avg_force_s / (sms * 128 * f_hz)
-    kernel = {0: "k_force_long_f32", 1: "k_force_long_f32x2<4>",
-              2: "k_force_long_sym<4,2> + k_force_sym_reduce",
-              3: "k_force_long_sym<2,4> + k_force_sym_reduce"}[variant]
-    if periodic_mode:
-        kernel = "k_force_long_per" if variant < 2 else kernel.replace("> +", ", periodic> +")
+    kernel = force_kernel_name(variant, periodic_mode)
     traffic = None
     # ncu DRAM bytes of one launch, used only while the kernel source is the
     # one the counters were taken on
@@ -636,18 +659,7 @@ def main():
                        "l2": "flushed between timed steps (256 MB write)",
                        "force_tuning": tune,
                        "per_step_stats": {k: v / args.steps for k, v in stats_tot.items()}},
-            "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
-                         "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                         "traffic": traffic, "fp32_pipe_frac": pipe_frac,
-                         "frac_executed": executed / peak_tflops,
-                         "pair_interactions_per_s": pairs / avg_force_s,
-                         "avg_launch_ms": avg_force_s * 1e3,
-                         "peak_note": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s max clock); achieved "
-                                      "counts the algorithmic %d flops per ordered pair over N(N-1) pairs; "
-                                      "the sweep executes %d flops in %d FP32 lane ops per ordered pair "
-                                      "(frac_executed, capped at %.2f), so frac is capped at %.2f"
-                                      % (sms, f_hz / 1e6, pk_kind, FLOPS_PER_PAIR, flops_pp, lanes_pp,
-                                         flops_pp / (2.0 * lanes_pp), FLOPS_PER_PAIR / (2.0 * lanes_pp))},
+            "roofline": force_roofline(N, avg_force_s, variant, periodic_mode, sms, f_hz, pk_kind, traffic),
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
         }
         if args.workload != "n1e5":

@@ -1,5 +1,5 @@
-"""The benchmark's host arithmetic, on the CPU: the correction kernel's
-algorithmic bytes and roofline fraction, and the CPU baseline's fields."""
+"""The benchmark's host arithmetic, on the CPU: the force sweep's and the
+correction kernel's roofline figures, and the CPU baseline's fields."""
 import os
 import sys
 
@@ -32,6 +32,33 @@ def test_correction_roofline_counts_the_documented_bytes():
     assert r["achieved"] == pytest.approx(per / (ms / 1e3) / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 5000.0)
     assert r["bound"] == "hbm" and r["kernel"] == "k_triangulation" and r["traffic"] is None
+
+
+@pytest.mark.parametrize("variant,periodic,lanes,executed", [
+    (3, False, 5, 8),      # symmetric sweep: 16 flops in 10 lane ops per unordered pair
+    (2, True, 5, 8),       # its periodic form counts the same
+    (1, False, 8, 12),     # one-sided packed sweep
+    (0, True, 12, 16),     # one-sided periodic sweep (exact near-pair vectors)
+])
+def test_force_roofline_counts_the_algorithmic_flops(variant, periodic, lanes, executed):
+    N, t, sms, f = 1000, 2.0e-5, 152, 2.07e9
+    r = bench.force_roofline(N, t, variant, periodic, sms, f, "measured", traffic=123)
+    pairs = N * (N - 1)
+    peak = sms * 128 * 2 * f / 1e12
+    # achieved: 12 flops per ordered pair whatever the sweep executes
+    assert r["achieved"] == pytest.approx(12 * pairs / t / 1e12)
+    assert r["peak"] == pytest.approx(peak)
+    assert r["frac"] == pytest.approx(r["achieved"] / peak)
+    assert r["frac_executed"] == pytest.approx(executed * pairs / t / 1e12 / peak)
+    assert r["fp32_pipe_frac"] == pytest.approx(lanes * pairs / t / (sms * 128 * f))
+    assert r["pair_interactions_per_s"] == pytest.approx(pairs / t)
+    assert r["avg_launch_ms"] == pytest.approx(t * 1e3)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["traffic"] == 123
+    # at a full FMA pipe (fp32_pipe_frac = 1) each fraction reaches its cap
+    scale = r["fp32_pipe_frac"]
+    assert r["frac"] / scale == pytest.approx(12 / (2 * lanes))
+    assert r["frac_executed"] / scale == pytest.approx(executed / (2 * lanes))
+    assert ("periodic" in r["kernel"] or "per" in r["kernel"]) == periodic
 
 
 def test_cpu_baseline_fields():
